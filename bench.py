@@ -1,0 +1,286 @@
+"""Throughput bench of the batched Keplerian-constrained BLS + spectral S/N on GB300.
+
+Workload (default): 4,096 uneven single-sector stars at 200-s cadence (7,000-11,800
+points each after random 0.5-2 d gaps), rho log-U(0.1, 10) g/cm^3, R* log-U(0.5, 3),
+white noise sigma log-U(2e-4, 1e-2), 30 % with injected boxes; seeded synthetic data.
+
+One step = one pass of the device path over the whole batch: point preparation
+(weights, double-float split), the persistent BLS search over every (star, trial
+frequency), and the S/N / best-candidate kernel, with the plan (grid) built once
+beforehand and the light curves resident in HBM. `e2e` times the public host-buffer
+call qlp_bls_run_host (plan + upload + search + S/N + download) on the same batch.
+
+Metric: BLS point-frequency evaluations per second (sum over stars of N_s * n_f,s
+per second). Multi-GPU: one independent batch per rank (weak scaling, no
+collective on the data path); value = all ranks' work / max-over-ranks time.
+
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores (the only other place this file runs the oracle).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BLS point-freq evals/s"
+UNIT = "point-freq/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--stars", type=int, default=4096)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-stars", type=int, default=256)
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# FP32-pipe operations per point-frequency evaluation in the search kernel's
+# double-float fold and run accumulation (see DESIGN: "roofline"): 4 for the
+# double-float product, 8 for the two round-to-integer steps and the remainder,
+# 2 for the guard-band test, 2 for the run sums.
+FP32_OPS_PER_EVAL = 16
+FP32_LANES_PER_SM = 128
+N_SMS = 152
+
+
+def cpu_baseline(batch, n_sample: int):
+    """Time the FP64 oracle (plan + BLS + S/N) on the first n_sample stars, all cores."""
+    import multiprocessing as mp
+    import oracle  # test infrastructure; only this baseline leg runs it
+    sub = batch.subset(range(min(n_sample, batch.n_stars)))
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    plans = oracle.plan_batch(sub)
+    res = oracle.bls_batch(plans, processes=cores)
+    for pl, r in zip(plans, res):
+        if pl.freqs.shape[0]:
+            oracle.spectral_snr(pl.freqs, r.sr)
+    dt = time.perf_counter() - t0
+    work = float(sum(pl.tp.shape[0] * pl.freqs.shape[0] for pl in plans))
+    return {"value": work / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {sub.n_stars} stars of the workload ({work:.3e} point-freq, "
+                      f"{dt:.1f} s wall, FP64 plan + C BLS + S/N, spawn pool of {cores})"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import synth
+    batch = synth.uneven_single_sector(n_stars=args.stars, seed=args.seed)
+    n_sample = max(8, min(args.cpu_sample_stars // 4, 64))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(batch.subset(range(i * n_sample, (i + 1) * n_sample)), n_sample)
+        if i >= args.warmup:
+            vals.append(cb)
+    v = float(np.median([c["value"] for c in vals]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "uneven_single_sector_200s", "stars": args.stars,
+                       "sample_stars_per_step": n_sample},
+            "cpu_baseline": {"kind": "oracle", "cores": vals[0]["cores"], "value": v, "unit": UNIT,
+                             "sample": f"{n_sample} stars per step: " + vals[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import synth
+    from paper_2302_01293_gb300 import qlpbls
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    batch = synth.uneven_single_sector(n_stars=args.stars, seed=args.seed + 1000 * rank)
+    params = qlpbls.Params()
+    stream = torch.cuda.current_stream()
+    plan = qlpbls.Plan(batch.offsets, batch.t, batch.y, batch.dy, batch.rho, batch.rstar, params)
+    out = plan.alloc_outputs()
+    for _ in range(max(3, args.warmup)):
+        plan.search(out)
+        plan.snr(out)
+    flags = plan.device_status()
+    if flags:
+        raise RuntimeError(f"device flags {flags}")
+
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_end = torch.cuda.Event(enable_timing=True)
+    k_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e_start.record(stream)
+    for i in range(args.steps):
+        k_ev[i][0].record(stream)
+        plan.search(out)
+        k_ev[i][1].record(stream)
+        plan.snr(out)
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e_start.elapsed_time(e_end) / args.steps
+    ms_search = float(np.mean([a.elapsed_time(b) for a, b in k_ev]))
+    flags = plan.device_status()
+    if flags:
+        raise RuntimeError(f"device flags {flags}")
+    t_max = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    work = torch.tensor([plan.work], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        dist.all_reduce(work, op=dist.ReduceOp.SUM)
+    ms_max = float(t_max.item())
+    total_work = float(work.item())
+    value = total_work / (ms_max * 1e-3)
+
+    # end to end through the public host-buffer call
+    e2e = None
+    if not args.no_e2e:
+        h2d = int(batch.offsets.nbytes + batch.t.nbytes + batch.y.nbytes + batch.dy.nbytes
+                  + batch.rho.nbytes + batch.rstar.nbytes)
+        times = []
+        res = None
+        for i in range(2):
+            barrier()
+            t0 = time.perf_counter()
+            res = qlpbls.run_host(batch.offsets, batch.t, batch.y, batch.dy, batch.rho,
+                                  batch.rstar, params)
+            times.append(time.perf_counter() - t0)
+        e2e_t = torch.tensor([min(times)], device="cuda", dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+        d2h = int(res["best"].nbytes)
+        e2e = {"value": total_work / float(e2e_t.item()), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "seconds_per_step": float(e2e_t.item()),
+               "includes": "host plan (grid) + H2D + search + S/N + D2H of best"}
+
+    peaks, src = _peaks()
+    sm_clock = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    peak_ops = N_SMS * FP32_LANES_PER_SM * sm_clock / 1e12  # T FP32-lane ops / s
+    achieved = plan.work * FP32_OPS_PER_EVAL / (ms_search * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "TFLOP/s",
+                "frac": achieved / peak_ops, "traffic": None,
+                "kernel": "bls_kernel (duration includes the preceding prep kernel)",
+                "peak_source": f"152 SMs x 128 FP32 lanes x {sm_clock/1e6:.0f} MHz ({src} max clock)",
+                "ops_per_eval": FP32_OPS_PER_EVAL}
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            cpu = cpu_baseline(batch, args.cpu_sample_stars)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 (double-float fold, FP64 near bin edges)", "data": "synthetic",
+                "config": {"workload": "uneven_single_sector_200s", "stars_per_gpu": args.stars,
+                           "points": plan.n_points, "trial_freqs": plan.n_freq_total,
+                           "point_freq_per_gpu": plan.work, "phase_mode": "DF",
+                           "sum_mode": "COMP", "l2": "inputs larger than L2 (prepared points "
+                           f"{plan.n_points * 24 / 1e6:.0f} MB)", "parallelism": f"replicas x{world}"},
+                "ms_search": ms_search, "gpu_launches": 3 * args.steps,
+                "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

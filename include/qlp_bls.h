@@ -1,0 +1,232 @@
+/*
+ * qlp_bls.h -- C ABI of the GB300 (sm_103a) batched Keplerian-constrained BLS
+ * transit search of "QLP Data Release Notes 003: GPU-based Transit Search"
+ * (Kunimoto et al., arXiv:2302.01293).
+ *
+ * The library searches many stars at once. Per star it builds the search plan
+ * of Sec. 2.1 (Pmin, Pmax, Keplerian duration range, frequency grid), computes
+ * the BLS signal residue SR(f) on every trial frequency (Sec. 2.1 and Eq. 1's
+ * SR), the spectral S/N of Eq. 1 with the Sturges median-binned trend and the
+ * 1.4826 MAD scale (Sec. 2.2 item 1), and the best candidate (P, T0, q, depth)
+ * used as the initial guess of the trapezoid fit (Sec. 2.2 item 2).
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: 0 (QLP_OK) on success, a negative QLP_ERR_* code when the
+ *    whole call failed; qlp_strerror() names it. Problems of a single star are
+ *    not call errors: they are reported in that star's status flags
+ *    (QLP_STAR_*), and such a star gets no frequencies and no candidate.
+ *  - Host pointers are read during the call only and stay owned by the caller.
+ *  - Device pointers are caller-allocated CUDA global memory on the current
+ *    device; results are written asynchronously on the given stream
+ *    (a cudaStream_t passed as void*, NULL = legacy default stream) and are
+ *    valid once that stream has been synchronised.
+ *  - A plan is library-owned (qlp_bls_plan_destroy frees it). Calls on one plan
+ *    must not overlap; different plans are independent.
+ *  - Units: t in days, y relative flux, dy its 1-sigma error, rho in g/cm^3,
+ *    R* in solar radii, frequencies in 1/day.
+ */
+#ifndef QLP_BLS_H
+#define QLP_BLS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define QLP_OK               0
+#define QLP_ERR_ARG         -1  /* null pointer, negative size, non-monotone offsets, bad params */
+#define QLP_ERR_CUDA        -2  /* a CUDA runtime call failed (message via qlp_last_cuda_error) */
+#define QLP_ERR_NOMEM       -3  /* host or device allocation failed */
+#define QLP_ERR_DEVICE      -4  /* a device-side bound was hit (iteration limit, capacity) */
+#define QLP_ERR_UNSUPPORTED -5  /* option combination not built into this library */
+
+/* ---- per-star status flags (qlp_bls_plan_info star_status, qlp_bls_best.status) ---- */
+#define QLP_STAR_UNSORTED    1  /* t decreases somewhere (after dropping invalid points) */
+#define QLP_STAR_TOO_FEW     2  /* fewer than 2 valid points */
+#define QLP_STAR_EMPTY_GRID  4  /* Pmin >= Pmax or zero baseline: nothing to search */
+#define QLP_STAR_NBINS_CAP   8  /* some frequency needs more phase bins than nbins_cap */
+#define QLP_STAR_ZERO_MAD   16  /* sigma_SR = 0: S/N undefined, no candidate */
+
+/* ---- options ---- */
+#define QLP_PHASE_FP64  0  /* fold x = t'f and its bin in FP64, the oracle's exact sequence */
+#define QLP_PHASE_DF    1  /* double-float (hi/lo FP32) fold; bins identical to FP64:
+                              points within a guard band of a bin edge are re-folded in FP64 */
+#define QLP_PHASE_FP32  2  /* plain FP32 fold (precision study only; bins may differ) */
+
+#define QLP_SUM_PLAIN   0  /* FP32 histogram sums */
+#define QLP_SUM_COMP    1  /* FP32 sums with the rounding error of every shared-memory add
+                              captured exactly (TwoSum) and added back (compensated) */
+
+#define QLP_MAD_RAW     0  /* sigma_SR = 1.4826 median|SR - median(SR)| (the paper's wording) */
+#define QLP_MAD_RESID   1  /* same on the detrended residual SR - trend */
+
+typedef struct qlp_bls_params {
+  double samples_per_peak;  /* 2     (Sec. 2.1 footnote) frequency step = q_min/(spp * T) */
+  double dlogq;             /* 0.1   (Sec. 2.1 footnote) natural-log step of the duration grid */
+  double noverlap;          /* 3     (Sec. 2.1 footnote) finest phase bin = q_min / noverlap */
+  double qmin_fac;          /* 0.5   (Sec. 2.1) shortest duration / circular-orbit duration */
+  double qmax_fac;          /* 2.0   (Sec. 2.1) longest duration / circular-orbit duration */
+  double pmin_aR;           /* 2     (Sec. 2.1) Pmin where a = pmin_aR R* (3 for Sectors 59-60) */
+  double gap_days;          /* 27.4  (Sec. 2.1) a gap longer than one sector splits stretches */
+  double rho_default;       /* 1.41  (Sec. 2.1) solar density (g/cm^3) when rho is missing */
+  int32_t nbins_cap;        /* largest phase-bin count a star may need (default 8192) */
+  int32_t phase_mode;       /* QLP_PHASE_* (default QLP_PHASE_DF) */
+  int32_t sum_mode;         /* QLP_SUM_*   (default QLP_SUM_COMP) */
+  int32_t mad_mode;         /* QLP_MAD_*   (default QLP_MAD_RAW) */
+  int32_t chunk_freqs;      /* frequencies per work item, 0 = chosen by the planner */
+  int32_t warps_per_block;  /* 0 = chosen by the planner; else 4, 8 or 16 */
+  int32_t n_threads;        /* host threads for planning, 0 = all cores */
+  int32_t tile_points;      /* points per shared-memory tile, 0 = as many as fit (multiple of 32) */
+  int32_t reserved[4];
+} qlp_bls_params;
+
+/* Best candidate of one star: the frequency of maximum S/N and its BLS box. */
+typedef struct qlp_bls_best {
+  int64_t f_idx;   /* index in the star's frequency grid; -1 = no candidate */
+  double f;        /* 1/day */
+  double period;   /* days, 1/f */
+  double t0;       /* first mid-box time >= t_min of the star (days) */
+  double q;        /* box duration / period = m / nbins */
+  double depth;    /* -s / (r (1 - r)), flux units; positive for a dip */
+  double sr;       /* SR at f_idx */
+  double snr;      /* S/N at f_idx */
+  int32_t j;       /* duration index of the box (0 .. nq-1) */
+  int32_t k;       /* first phase bin of the box */
+  int32_t m;       /* bins covered by the box */
+  int32_t nbins;   /* phase bins at f */
+  int32_t status;  /* QLP_STAR_* flags of the star */
+  int32_t pad;
+} qlp_bls_best;
+
+typedef struct qlp_bls_plan qlp_bls_plan_t;
+
+/* Fill *p with the paper's settings (Sec. 2.1) and the library defaults. */
+void qlp_bls_params_default(qlp_bls_params* p);
+
+/*
+ * qlp_bls_plan -- Sec. 2.1: per-star search plan, uploaded to the device.
+ *  p        parameters (see qlp_bls_params); NULL = defaults.
+ *  n_stars  number of stars (>= 0).
+ *  offsets  host int64[n_stars + 1], non-decreasing, offsets[0] = 0: star s owns
+ *           points offsets[s] .. offsets[s+1]-1 of t, y and dy.
+ *  t, y, dy host double[offsets[n_stars]]: time (days), flux, 1-sigma error.
+ *           Points with a non-finite value or dy <= 0 are dropped; the rest of
+ *           a star must be sorted by t (else QLP_STAR_UNSORTED).
+ *  rho      host double[n_stars] stellar density (g/cm^3); NULL, NaN or <= 0
+ *           use p->rho_default.
+ *  rstar    host double[n_stars] stellar radius (R_sun) or NULL. The period
+ *           limits and durations depend on rho only (R* cancels in a/R*); it
+ *           is accepted and kept for the caller.
+ *  stream   cudaStream_t for the uploads (NULL = default stream).
+ *  out_plan receives the plan (library-owned). On error *out_plan = NULL.
+ * Host-side work: validation, Pmin (a = pmin_aR R*), Pmax (longest continuous
+ * stretch, or half of it when no gap exceeds gap_days), the frequency grid
+ * f_{k+1} = f_k + q_min(f_k)/(spp T) from 1/Pmax to 1/Pmin in FP64, and the
+ * device work list; multithreaded over stars.
+ */
+int qlp_bls_plan(const qlp_bls_params* p, int32_t n_stars, const int64_t* offsets,
+                 const double* t, const double* y, const double* dy,
+                 const double* rho, const double* rstar, void* stream,
+                 qlp_bls_plan_t** out_plan);
+
+/*
+ * qlp_bls_plan_info -- sizes and the host copy of the plan. Any output may be NULL.
+ *  n_freq_total  total number of trial frequencies over all stars.
+ *  freq_offsets  int64[n_stars + 1]: star s owns spectrum entries
+ *                freq_offsets[s] .. freq_offsets[s+1]-1 of every per-frequency array.
+ *  freqs         double[n_freq_total] trial frequencies (1/day).
+ *  star_status   int32[n_stars] QLP_STAR_* flags.
+ *  n_points      int64: total valid points (the sum of N_s).
+ *  work          double: sum over stars of N_s * n_f,s (point-frequency pairs).
+ */
+int qlp_bls_plan_info(const qlp_bls_plan_t* plan, int64_t* n_freq_total, int64_t* freq_offsets,
+                      double* freqs, int32_t* star_status, int64_t* n_points, double* work);
+
+/*
+ * qlp_bls_search -- Sec. 2.1 / Eq. 1's SR: binned BLS residue at every trial frequency.
+ * For each star and trial frequency f the light curve is folded (x = (t - t_min) f,
+ * bin = floor(frac(x) nbins)), the weights w = dy^-2/sum(dy^-2) and w (y - ybar)
+ * are histogrammed, and every cyclic window of m_j bins (durations q_j =
+ * q_min e^{j dlogq}) is scored v = s^2 / (r (1 - r)), r = sum w, s = sum w (y - ybar).
+ * All outputs are caller-owned device arrays of n_freq_total entries, in the
+ * order of qlp_bls_plan_info's freq_offsets:
+ *  sr        float: SR(f) = max v (0 when no window has 0 < r < 1).
+ *  qidx      uint8: duration index j of the maximum (ties: lowest j, then lowest
+ *            start bin); 255 when no window is valid. May be NULL.
+ *  phase_bin uint32: first bin k of that window; 0xFFFFFFFF when none. May be NULL.
+ *  s_best, r_best  float: s and r of that window. May be NULL.
+ * Runs one persistent kernel over a device work queue of (star, frequency-chunk)
+ * items. Returns QLP_ERR_DEVICE if a device bound was hit.
+ */
+int qlp_bls_search(qlp_bls_plan_t* plan, void* stream, float* sr, uint8_t* qidx,
+                   uint32_t* phase_bin, float* s_best, float* r_best);
+
+/*
+ * qlp_bls_snr -- Sec. 2.2 item 1, Eq. 1 with the two changes the paper makes:
+ * S/N(f) = (SR(f) - trend(f)) / sigma_SR, trend = the spectrum median-binned in
+ * N = round(1 + 3.322 log10 n) equal-width frequency bins and linearly
+ * interpolated, sigma_SR = 1.4826 MAD; then the best candidate per star.
+ *  sr, qidx, phase_bin, s_best, r_best  device arrays written by qlp_bls_search
+ *            (all required here).
+ *  snr       device float[n_freq_total] output.
+ *  best      device qlp_bls_best[n_stars] output.
+ */
+int qlp_bls_snr(qlp_bls_plan_t* plan, void* stream, const float* sr, const uint8_t* qidx,
+                const uint32_t* phase_bin, const float* s_best, const float* r_best,
+                float* snr, qlp_bls_best* best);
+
+/*
+ * qlp_bls_run_host -- the whole path from host buffers to host results:
+ * plan + upload, search, S/N, download. Arguments as for qlp_bls_plan; outputs
+ * are host arrays: sr_host and snr_host float[n_freq_total] (may be NULL; the
+ * caller sizes them from a previous plan of the same input or passes NULL),
+ * best_host qlp_bls_best[n_stars] (required). Device memory is allocated and
+ * freed inside the call. *n_freq_total_out (may be NULL) receives the size.
+ * If sr_host/snr_host are given they must hold sr_capacity floats; a larger
+ * spectrum returns QLP_ERR_ARG after best_host is written.
+ */
+int qlp_bls_run_host(const qlp_bls_params* p, int32_t n_stars, const int64_t* offsets,
+                     const double* t, const double* y, const double* dy,
+                     const double* rho, const double* rstar,
+                     float* sr_host, float* snr_host, int64_t sr_capacity,
+                     qlp_bls_best* best_host, int64_t* n_freq_total_out);
+
+/*
+ * qlp_bls_device_status -- synchronise `stream`, return the device error flags
+ * accumulated by this plan's kernels since the last call in *flags (bit 1: the
+ * work loop hit its iteration bound, 2: a frequency needed more bins than the
+ * shared histogram holds, 4: more S/N bins than supported) and clear them.
+ * Returns QLP_ERR_DEVICE when any flag was set, else QLP_OK.
+ */
+int qlp_bls_device_status(qlp_bls_plan_t* plan, void* stream, int32_t* flags);
+
+void qlp_bls_plan_destroy(qlp_bls_plan_t* plan);
+
+/*
+ * qlp_bls_star_grid -- host only, no device work: the Sec. 2.1 plan of one star,
+ * exactly as qlp_bls_plan builds it (same code), for inspection and checks.
+ *  n, t, y, dy   the star's points (host double[n]); rho as for qlp_bls_plan.
+ *  status, pmin, pmax, t_ref, baseline   outputs, each may be NULL.
+ *  freqs, qmins  host double[capacity] trial frequencies and their q_min (may be NULL).
+ *  n_f_out       number of trial frequencies (required).
+ * Returns QLP_ERR_ARG when freqs/qmins are given and capacity < *n_f_out (the
+ * scalars and *n_f_out are still written).
+ */
+int qlp_bls_star_grid(const qlp_bls_params* p, int64_t n, const double* t, const double* y,
+                      const double* dy, double rho, int32_t* status, double* pmin, double* pmax,
+                      double* t_ref, double* baseline, double* freqs, double* qmins,
+                      int64_t capacity, int64_t* n_f_out);
+
+/* Static description of a return code. */
+const char* qlp_strerror(int code);
+
+/* Text of the last CUDA error seen by the library in this thread ("" if none). */
+const char* qlp_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QLP_BLS_H */

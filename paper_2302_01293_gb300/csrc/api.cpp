@@ -1,0 +1,474 @@
+// C-ABI entry points of libqlpbls (declared in include/qlp_bls.h): plan assembly,
+// device buffers, work queue, launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "planner.h"
+#include "qlp_internal.h"
+
+using namespace qlp;
+
+namespace {
+
+thread_local std::string g_cuda_err;
+
+int cuda_fail(cudaError_t e, const char* what) {
+  char buf[256];
+  std::snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+  g_cuda_err = buf;
+  return QLP_ERR_CUDA;
+}
+
+#define QLP_CK(call)                                                    \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);                 \
+  } while (0)
+
+template <typename T>
+int dev_alloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cuda_fail(e, "cudaMalloc");
+    return QLP_ERR_NOMEM;
+  }
+  return QLP_OK;
+}
+
+}  // namespace
+
+struct qlp_bls_plan {
+  qlp_bls_params p{};
+  int32_t n_stars = 0;
+  int32_t nq = 0;
+  double E[kMaxQ] = {};
+  // host copy
+  std::vector<int32_t> status;
+  std::vector<int64_t> f_off;     // n_stars + 1
+  std::vector<double> freqs;      // all stars
+  int64_t n_points = 0;
+  double work = 0.0;              // sum N_s * n_f,s
+  int32_t nbins_max = 0;
+  // launch shape
+  int warps = 8;
+  int blocks = 0;
+  int tile_pts = 0;
+  int hist_stride = 0;
+  uint32_t tile_off = 0;
+  size_t smem = 0;
+  int32_t n_items = 0;
+  // device
+  StarDev* d_stars = nullptr;
+  double2* d_fq = nullptr;
+  WorkItem* d_items = nullptr;
+  double* d_tp = nullptr;
+  double* d_y = nullptr;
+  double* d_dy = nullptr;
+  float4* d_pts = nullptr;
+  double* d_tpd = nullptr;
+  int32_t* d_ctl = nullptr;       // [0] queue head, [1] error flags
+};
+
+static void free_plan(qlp_bls_plan_t* pl) {
+  if (!pl) return;
+  cudaFree(pl->d_stars);
+  cudaFree(pl->d_fq);
+  cudaFree(pl->d_items);
+  cudaFree(pl->d_tp);
+  cudaFree(pl->d_y);
+  cudaFree(pl->d_dy);
+  cudaFree(pl->d_pts);
+  cudaFree(pl->d_tpd);
+  cudaFree(pl->d_ctl);
+  delete pl;
+}
+
+extern "C" {
+
+void qlp_bls_params_default(qlp_bls_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->samples_per_peak = 2.0;
+  p->dlogq = 0.1;
+  p->noverlap = 3.0;
+  p->qmin_fac = 0.5;
+  p->qmax_fac = 2.0;
+  p->pmin_aR = 2.0;
+  p->gap_days = 27.4;
+  p->rho_default = 1.41;
+  p->nbins_cap = 8192;
+  p->phase_mode = QLP_PHASE_DF;
+  p->sum_mode = QLP_SUM_COMP;
+  p->mad_mode = QLP_MAD_RAW;
+  p->chunk_freqs = 0;
+  p->warps_per_block = 0;
+  p->n_threads = 0;
+}
+
+const char* qlp_strerror(int code) {
+  switch (code) {
+    case QLP_OK: return "ok";
+    case QLP_ERR_ARG: return "invalid argument";
+    case QLP_ERR_CUDA: return "CUDA runtime error";
+    case QLP_ERR_NOMEM: return "out of memory";
+    case QLP_ERR_DEVICE: return "device-side bound hit";
+    case QLP_ERR_UNSUPPORTED: return "unsupported option";
+    default: return "unknown error";
+  }
+}
+
+const char* qlp_last_cuda_error(void) { return g_cuda_err.c_str(); }
+
+static int check_params(const qlp_bls_params& p) {
+  if (!(p.samples_per_peak > 0) || !(p.dlogq > 0) || !(p.noverlap >= 1) || !(p.qmin_fac > 0) ||
+      !(p.qmax_fac >= p.qmin_fac) || !(p.pmin_aR > 0) || !(p.gap_days > 0) || !(p.rho_default > 0) ||
+      p.nbins_cap < 2)
+    return QLP_ERR_ARG;
+  if (p.phase_mode < 0 || p.phase_mode > 2 || p.sum_mode < 0 || p.sum_mode > 1 || p.mad_mode < 0 ||
+      p.mad_mode > 1 || p.tile_points < 0 || p.chunk_freqs < 0)
+    return QLP_ERR_ARG;
+  if (p.warps_per_block != 0 && p.warps_per_block != 4 && p.warps_per_block != 8 &&
+      p.warps_per_block != 16)
+    return QLP_ERR_ARG;
+  const int nq = n_q_of(p);
+  if (nq < 1 || nq > kMaxQ) return QLP_ERR_UNSUPPORTED;
+  // widest window: q_min e^{(nq-1) dlogq} nbins + 1/2 with q_min nbins < noverlap + 1
+  const double mmax = (p.noverlap + 1.0) * std::exp((nq - 1) * p.dlogq) + 0.5;
+  if (mmax >= (double)kMPad) return QLP_ERR_UNSUPPORTED;
+  return QLP_OK;
+}
+
+int qlp_bls_plan(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offsets, const double* t,
+                 const double* y, const double* dy, const double* rho, const double* rstar,
+                 void* stream, qlp_bls_plan_t** out_plan) {
+  (void)rstar;
+  if (!out_plan) return QLP_ERR_ARG;
+  *out_plan = nullptr;
+  qlp_bls_params p;
+  if (pin) p = *pin; else qlp_bls_params_default(&p);
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (n_stars < 0 || (n_stars > 0 && !offsets)) return QLP_ERR_ARG;
+  if (n_stars > 0) {
+    if (offsets[0] != 0) return QLP_ERR_ARG;
+    for (int32_t s = 0; s < n_stars; ++s)
+      if (offsets[s + 1] < offsets[s]) return QLP_ERR_ARG;
+    if (offsets[n_stars] > 0 && (!t || !y || !dy)) return QLP_ERR_ARG;
+  }
+
+  std::vector<StarPlanHost> sp;
+  plan_all(p, n_stars, offsets, t, y, dy, rho, &sp);
+
+  qlp_bls_plan_t* pl = new (std::nothrow) qlp_bls_plan_t();
+  if (!pl) return QLP_ERR_NOMEM;
+  pl->p = p;
+  pl->n_stars = n_stars;
+  pl->nq = n_q_of(p);
+  for (int j = 0; j < pl->nq; ++j) pl->E[j] = std::exp(j * p.dlogq);
+
+  // flat host arrays
+  std::vector<StarDev> stars((size_t)n_stars);
+  pl->status.resize((size_t)n_stars);
+  pl->f_off.assign((size_t)n_stars + 1, 0);
+  int64_t npt = 0, npad = 0, nf = 0;
+  int32_t max_npts = 0;
+  for (int32_t s = 0; s < n_stars; ++s) {
+    const StarPlanHost& h = sp[(size_t)s];
+    StarDev& d = stars[(size_t)s];
+    std::memset(&d, 0, sizeof(d));
+    const bool ok = h.status == 0;
+    d.pt_off = npt;
+    d.pad_off = npad;
+    d.f_off = nf;
+    d.n_pts = ok ? (int32_t)h.tp.size() : 0;
+    d.n_f = ok ? (int32_t)h.freqs.size() : 0;
+    d.status = h.status;
+    d.sturges_nb = h.sturges_nb;
+    d.fp64_phase = (h.ymax >= 4194304.0) ? 1 : 0;   // 2^22: beyond the FP32 remainder range
+    d.t_ref = h.t_ref;
+    d.baseline = h.baseline;
+    pl->status[(size_t)s] = h.status;
+    npt += d.n_pts;
+    npad += ((int64_t)d.n_pts + 31) & ~(int64_t)31;
+    nf += d.n_f;
+    pl->f_off[(size_t)s + 1] = nf;
+    max_npts = std::max(max_npts, d.n_pts);
+    if (ok) {
+      pl->nbins_max = std::max(pl->nbins_max, h.nbins_max);
+      pl->work += (double)d.n_pts * (double)d.n_f;
+    }
+  }
+  pl->n_points = npt;
+  std::vector<double> tp_all((size_t)std::max<int64_t>(npt, 1)), y_all(tp_all.size()), dy_all(tp_all.size());
+  std::vector<double2> fq((size_t)std::max<int64_t>(nf, 1));
+  pl->freqs.resize((size_t)nf);
+  for (int32_t s = 0; s < n_stars; ++s) {
+    const StarPlanHost& h = sp[(size_t)s];
+    const StarDev& d = stars[(size_t)s];
+    if (d.n_pts > 0) {
+      std::memcpy(&tp_all[(size_t)d.pt_off], h.tp.data(), sizeof(double) * (size_t)d.n_pts);
+      std::memcpy(&y_all[(size_t)d.pt_off], h.y.data(), sizeof(double) * (size_t)d.n_pts);
+      std::memcpy(&dy_all[(size_t)d.pt_off], h.dy.data(), sizeof(double) * (size_t)d.n_pts);
+    }
+    for (int32_t k = 0; k < d.n_f; ++k) {
+      fq[(size_t)(d.f_off + k)] = make_double2(h.freqs[(size_t)k], h.qmins[(size_t)k]);
+      pl->freqs[(size_t)(d.f_off + k)] = h.freqs[(size_t)k];
+    }
+  }
+
+  // launch shape: histograms per warp, then the largest point tile that fits
+  const int NA = (p.sum_mode == QLP_SUM_COMP) ? 4 : 2;
+  pl->hist_stride = ((std::max(pl->nbins_max, 1) + kMPad + 31) / 32) * 32;
+  const int smem_max = bls_max_smem_per_block();
+  if (smem_max <= 0) { delete pl; return cuda_fail(cudaGetLastError(), "device query"); }
+  const int budget = smem_max - 1024;
+  int warps = p.warps_per_block ? p.warps_per_block : 8;
+  auto hist_bytes = [&](int w) { return (size_t)w * NA * pl->hist_stride * 4 + (size_t)w * kMaxQ * 4; };
+  while (warps > 4 && hist_bytes(warps) > (size_t)budget / 2) warps /= 2;
+  const size_t hb = (hist_bytes(warps) + 15) & ~(size_t)15;
+  if (hb + 32 * 16 > (size_t)budget) { delete pl; return QLP_ERR_UNSUPPORTED; }
+  int tile = (int)(((size_t)budget - hb) / 16 / 32 * 32);
+  const int need = ((std::max(max_npts, 1) + 31) / 32) * 32;
+  tile = std::min(tile, need);
+  if (p.tile_points > 0) tile = std::min(tile, std::max(32, (p.tile_points / 32) * 32));
+  pl->warps = warps;
+  pl->tile_pts = tile;
+  pl->tile_off = (uint32_t)hb;
+  pl->smem = hb + (size_t)tile * 16;
+  int dev = 0, sms = 0;
+  QLP_CK(cudaGetDevice(&dev));
+  QLP_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int per_sm = bls_blocks_per_sm(p.phase_mode, p.sum_mode, warps, pl->smem);
+  if (per_sm < 1) { delete pl; return QLP_ERR_UNSUPPORTED; }
+  pl->blocks = sms * per_sm;
+
+  // work items: (star, chunk of frequencies), longest first
+  int chunk = p.chunk_freqs;
+  if (chunk <= 0) {
+    const double per = (double)nf / (8.0 * pl->blocks * warps);
+    int rounds = (int)std::floor(per);
+    rounds = std::max(1, std::min(rounds, 16));
+    chunk = rounds * warps;
+  }
+  std::vector<WorkItem> items;
+  std::vector<double> cost;
+  for (int32_t s = 0; s < n_stars; ++s) {
+    const StarDev& d = stars[(size_t)s];
+    const StarPlanHost& h = sp[(size_t)s];
+    for (int32_t b = 0; b < d.n_f; b += chunk) {
+      WorkItem w{};
+      w.star = s;
+      w.f_begin = b;
+      w.f_count = std::min(chunk, d.n_f - b);
+      items.push_back(w);
+      const int mid = b + w.f_count / 2;
+      const double nbm = std::ceil(p.noverlap / h.qmins[(size_t)mid]);
+      cost.push_back((double)w.f_count * ((double)d.n_pts + 3.0 * nbm));
+    }
+  }
+  std::vector<int32_t> order(items.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int32_t)i;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[(size_t)a] > cost[(size_t)b]; });
+  std::vector<WorkItem> sorted(items.size());
+  for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[(size_t)order[i]];
+  pl->n_items = (int32_t)sorted.size();
+
+  // device buffers
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = dev_alloc(&pl->d_stars, (size_t)n_stars)) || (rc = dev_alloc(&pl->d_fq, fq.size())) ||
+      (rc = dev_alloc(&pl->d_items, sorted.size())) || (rc = dev_alloc(&pl->d_tp, tp_all.size())) ||
+      (rc = dev_alloc(&pl->d_y, y_all.size())) || (rc = dev_alloc(&pl->d_dy, dy_all.size())) ||
+      (rc = dev_alloc(&pl->d_pts, (size_t)std::max<int64_t>(npad, 1))) ||
+      (rc = dev_alloc(&pl->d_tpd, (size_t)std::max<int64_t>(npad, 1))) || (rc = dev_alloc(&pl->d_ctl, 2))) {
+    free_plan(pl);
+    return rc;
+  }
+  cudaError_t e = cudaSuccess;
+  if (n_stars > 0) e = cudaMemcpyAsync(pl->d_stars, stars.data(), sizeof(StarDev) * (size_t)n_stars, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && nf > 0) e = cudaMemcpyAsync(pl->d_fq, fq.data(), sizeof(double2) * (size_t)nf, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !sorted.empty()) e = cudaMemcpyAsync(pl->d_items, sorted.data(), sizeof(WorkItem) * sorted.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(pl->d_tp, tp_all.data(), sizeof(double) * (size_t)npt, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(pl->d_y, y_all.data(), sizeof(double) * (size_t)npt, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(pl->d_dy, dy_all.data(), sizeof(double) * (size_t)npt, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_ctl, 0, 2 * sizeof(int32_t), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // host staging vectors die at return
+  if (e != cudaSuccess) {
+    free_plan(pl);
+    return cuda_fail(e, "plan upload");
+  }
+  *out_plan = pl;
+  return QLP_OK;
+}
+
+int qlp_bls_plan_info(const qlp_bls_plan_t* pl, int64_t* n_freq_total, int64_t* freq_offsets,
+                      double* freqs, int32_t* star_status, int64_t* n_points, double* work) {
+  if (!pl) return QLP_ERR_ARG;
+  if (n_freq_total) *n_freq_total = pl->f_off.back();
+  if (freq_offsets) std::memcpy(freq_offsets, pl->f_off.data(), sizeof(int64_t) * pl->f_off.size());
+  if (freqs && !pl->freqs.empty()) std::memcpy(freqs, pl->freqs.data(), sizeof(double) * pl->freqs.size());
+  if (star_status && !pl->status.empty()) std::memcpy(star_status, pl->status.data(), sizeof(int32_t) * pl->status.size());
+  if (n_points) *n_points = pl->n_points;
+  if (work) *work = pl->work;
+  return QLP_OK;
+}
+
+int qlp_bls_search(qlp_bls_plan_t* pl, void* stream, float* sr, uint8_t* qidx, uint32_t* phase_bin,
+                   float* s_best, float* r_best) {
+  if (!pl) return QLP_ERR_ARG;
+  if (pl->f_off.back() > 0 && !sr) return QLP_ERR_ARG;
+  if (pl->n_stars == 0 || pl->f_off.back() == 0) return QLP_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  PrepArgs pa{};
+  pa.stars = pl->d_stars;
+  pa.tp = pl->d_tp;
+  pa.y = pl->d_y;
+  pa.dy = pl->d_dy;
+  pa.pts = pl->d_pts;
+  pa.tpd = pl->d_tpd;
+  pa.tile_pts = pl->tile_pts;
+  pa.n_stars = pl->n_stars;
+  int e = launch_prep(pa, stream);
+  if (e) return cuda_fail((cudaError_t)e, "prep launch");
+  QLP_CK(cudaMemsetAsync(pl->d_ctl, 0, sizeof(int32_t), st));
+  BlsArgs a{};
+  a.stars = pl->d_stars;
+  a.fq = pl->d_fq;
+  a.items = pl->d_items;
+  a.n_items = pl->n_items;
+  a.nq = pl->nq;
+  a.pts = pl->d_pts;
+  a.tpd = pl->d_tpd;
+  a.cursor = pl->d_ctl;
+  a.err = pl->d_ctl + 1;
+  a.sr = sr;
+  a.qidx = qidx;
+  a.kbin = phase_bin;
+  a.sbest = s_best;
+  a.rbest = r_best;
+  a.noverlap = pl->p.noverlap;
+  for (int j = 0; j < kMaxQ; ++j) a.E[j] = pl->E[j];
+  a.tile_pts = pl->tile_pts;
+  a.hist_stride = pl->hist_stride;
+  a.tile_off = pl->tile_off;
+  e = launch_bls(a, pl->p.phase_mode, pl->p.sum_mode, pl->warps, pl->blocks, pl->smem, stream);
+  if (e) return cuda_fail((cudaError_t)e, "search launch");
+  return QLP_OK;
+}
+
+int qlp_bls_snr(qlp_bls_plan_t* pl, void* stream, const float* sr, const uint8_t* qidx,
+                const uint32_t* phase_bin, const float* s_best, const float* r_best, float* snr,
+                qlp_bls_best* best) {
+  if (!pl) return QLP_ERR_ARG;
+  if (pl->n_stars > 0 && !best) return QLP_ERR_ARG;
+  if (pl->f_off.back() > 0 && (!sr || !qidx || !phase_bin || !s_best || !r_best || !snr)) return QLP_ERR_ARG;
+  if (pl->n_stars == 0) return QLP_OK;
+  SnrArgs a{};
+  a.stars = pl->d_stars;
+  a.fq = pl->d_fq;
+  a.sr = sr;
+  a.qidx = qidx;
+  a.kbin = phase_bin;
+  a.sbest = s_best;
+  a.rbest = r_best;
+  a.snr = snr;
+  a.best = best;
+  a.err = pl->d_ctl + 1;
+  a.noverlap = pl->p.noverlap;
+  for (int j = 0; j < kMaxQ; ++j) a.E[j] = pl->E[j];
+  a.nq = pl->nq;
+  a.mad_mode = pl->p.mad_mode;
+  a.n_stars = pl->n_stars;
+  const int e = launch_snr(a, stream);
+  if (e) return cuda_fail((cudaError_t)e, "snr launch");
+  return QLP_OK;
+}
+
+int qlp_bls_device_status(qlp_bls_plan_t* pl, void* stream, int32_t* flags) {
+  if (!pl || !flags) return QLP_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  QLP_CK(cudaStreamSynchronize(st));
+  int32_t v = 0;
+  QLP_CK(cudaMemcpy(&v, pl->d_ctl + 1, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  *flags = v;
+  QLP_CK(cudaMemset(pl->d_ctl + 1, 0, sizeof(int32_t)));
+  return v ? QLP_ERR_DEVICE : QLP_OK;
+}
+
+int qlp_bls_run_host(const qlp_bls_params* p, int32_t n_stars, const int64_t* offsets, const double* t,
+                     const double* y, const double* dy, const double* rho, const double* rstar,
+                     float* sr_host, float* snr_host, int64_t sr_capacity, qlp_bls_best* best_host,
+                     int64_t* n_freq_total_out) {
+  if (!best_host && n_stars > 0) return QLP_ERR_ARG;
+  cudaStream_t st = nullptr;
+  QLP_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  qlp_bls_plan_t* pl = nullptr;
+  int rc = qlp_bls_plan(p, n_stars, offsets, t, y, dy, rho, rstar, st, &pl);
+  if (rc) { cudaStreamDestroy(st); return rc; }
+  const int64_t nf = pl->f_off.back();
+  if (n_freq_total_out) *n_freq_total_out = nf;
+  float *d_sr = nullptr, *d_snr = nullptr, *d_s = nullptr, *d_r = nullptr;
+  uint8_t* d_q = nullptr;
+  uint32_t* d_k = nullptr;
+  qlp_bls_best* d_best = nullptr;
+  if ((rc = dev_alloc(&d_sr, (size_t)nf)) || (rc = dev_alloc(&d_snr, (size_t)nf)) ||
+      (rc = dev_alloc(&d_s, (size_t)nf)) || (rc = dev_alloc(&d_r, (size_t)nf)) ||
+      (rc = dev_alloc(&d_q, (size_t)nf)) || (rc = dev_alloc(&d_k, (size_t)nf)) ||
+      (rc = dev_alloc(&d_best, (size_t)std::max(n_stars, 1)))) {
+    // fall through to cleanup
+  } else if ((rc = qlp_bls_search(pl, st, d_sr, d_q, d_k, d_s, d_r)) == QLP_OK &&
+             (rc = qlp_bls_snr(pl, st, d_sr, d_q, d_k, d_s, d_r, d_snr, d_best)) == QLP_OK) {
+    cudaError_t e = cudaSuccess;
+    if (n_stars > 0) e = cudaMemcpyAsync(best_host, d_best, sizeof(qlp_bls_best) * (size_t)n_stars, cudaMemcpyDeviceToHost, st);
+    const bool fits = nf <= sr_capacity;
+    if (e == cudaSuccess && sr_host && fits && nf > 0) e = cudaMemcpyAsync(sr_host, d_sr, sizeof(float) * (size_t)nf, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && snr_host && fits && nf > 0) e = cudaMemcpyAsync(snr_host, d_snr, sizeof(float) * (size_t)nf, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "result download");
+    else {
+      int32_t flags = 0;
+      rc = qlp_bls_device_status(pl, st, &flags);
+      if (rc == QLP_OK && (sr_host || snr_host) && !fits) rc = QLP_ERR_ARG;
+    }
+  }
+  cudaFree(d_sr); cudaFree(d_snr); cudaFree(d_s); cudaFree(d_r); cudaFree(d_q); cudaFree(d_k); cudaFree(d_best);
+  qlp_bls_plan_destroy(pl);
+  cudaStreamDestroy(st);
+  return rc;
+}
+
+int qlp_bls_star_grid(const qlp_bls_params* pin, int64_t n, const double* t, const double* y,
+                      const double* dy, double rho, int32_t* status, double* pmin, double* pmax,
+                      double* t_ref, double* baseline, double* freqs, double* qmins,
+                      int64_t capacity, int64_t* n_f_out) {
+  if (!n_f_out || n < 0 || (n > 0 && (!t || !y || !dy))) return QLP_ERR_ARG;
+  qlp_bls_params p;
+  if (pin) p = *pin; else qlp_bls_params_default(&p);
+  const int rc = check_params(p);
+  if (rc) return rc;
+  StarPlanHost h;
+  plan_one(p, t, y, dy, n, rho, &h);
+  if (status) *status = h.status;
+  if (pmin) *pmin = h.pmin;
+  if (pmax) *pmax = h.pmax;
+  if (t_ref) *t_ref = h.t_ref;
+  if (baseline) *baseline = h.baseline;
+  const int64_t nf = h.status == 0 ? (int64_t)h.freqs.size() : 0;
+  *n_f_out = nf;
+  if ((freqs || qmins) && capacity < nf) return QLP_ERR_ARG;
+  if (freqs && nf) std::memcpy(freqs, h.freqs.data(), sizeof(double) * (size_t)nf);
+  if (qmins && nf) std::memcpy(qmins, h.qmins.data(), sizeof(double) * (size_t)nf);
+  return QLP_OK;
+}
+
+void qlp_bls_plan_destroy(qlp_bls_plan_t* pl) { free_plan(pl); }
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// Host planner (Sec. 2.1 of arXiv:2302.01293): per-star validation, period
+// limits, Keplerian duration range and trial-frequency grid, in FP64.
+// Compiled with -ffp-contract=off: every product and sum is rounded on its own,
+// so the grid is reproducible bit for bit from its definition.
+//
+//  * rho: the TIC density, or the solar density rho_default when it is missing;
+//  * Pmin: the period where a = pmin_aR R*, from Kepler's third law with
+//    M = 4/3 pi R*^3 rho (R* cancels): Pmin = sqrt(3 pi (a/R*)^3 / (G rho));
+//  * Pmax: the longest continuous stretch of data (stretches split at gaps
+//    longer than gap_days = one TESS sector), or half of it when there is a
+//    single stretch;
+//  * q_circ(f) = asin(min(1, R*/a)) / pi, a/R* = (G rho P^2 / (3 pi))^(1/3): the
+//    duration fraction of a central circular orbit; searched durations
+//    [qmin_fac, qmax_fac] x q_circ;
+//  * grid: f_0 = 1/Pmax, f_{k+1} = f_k + q_min(f_k) / (samples_per_peak T),
+//    T = t_max - t_min, while f <= 1/Pmin;
+//  * bins: nbins(f) = ceil(noverlap / q_min(f)).
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <thread>
+#include <vector>
+
+#include "planner.h"
+
+namespace qlp {
+
+namespace {
+constexpr double kG = 6.67430e-11;  // m^3 kg^-1 s^-2
+constexpr double kDay = 86400.0;
+constexpr double kPi = 3.141592653589793;
+}  // namespace
+
+int n_q_of(const qlp_bls_params& p) {
+  return (int)std::floor(std::log(p.qmax_fac / p.qmin_fac) / p.dlogq + 1e-9) + 1;
+}
+
+double q_min_of(double f, double rho_kg, const qlp_bls_params& p) {
+  const double ps = kDay / f;
+  const double x = kG * rho_kg * ps * ps / (3.0 * kPi);
+  const double a_r = std::cbrt(x);
+  const double q_circ = std::asin(std::min(1.0, 1.0 / a_r)) / kPi;
+  return p.qmin_fac * q_circ;
+}
+
+int nbins_of(double qmin, const qlp_bls_params& p) { return (int)std::ceil(p.noverlap / qmin); }
+
+double pmin_of(double rho_kg, const qlp_bls_params& p) {
+  const double a3 = p.pmin_aR * p.pmin_aR * p.pmin_aR;
+  return std::sqrt(3.0 * kPi * a3 / (kG * rho_kg)) / kDay;
+}
+
+double pmax_of(const double* tp, int64_t n, const qlp_bls_params& p) {
+  int64_t start = 0;
+  int stretches = 1;
+  double longest = 0.0;
+  for (int64_t i = 1; i < n; ++i) {
+    if (tp[i] - tp[i - 1] > p.gap_days) {
+      longest = std::max(longest, tp[i - 1] - tp[start]);
+      start = i;
+      ++stretches;
+    }
+  }
+  longest = std::max(longest, tp[n - 1] - tp[start]);
+  if (stretches == 1) return (tp[n - 1] - tp[0]) / 2.0;
+  return longest;
+}
+
+int sturges_of(int64_t n) { return (int)std::floor(1.0 + 3.322 * std::log10((double)n) + 0.5); }
+
+void plan_one(const qlp_bls_params& p, const double* t, const double* y, const double* dy, int64_t n,
+              double rho, StarPlanHost* out) {
+  StarPlanHost& s = *out;
+  s = StarPlanHost();
+  const double rho_gcc = (std::isfinite(rho) && rho > 0.0) ? rho : p.rho_default;
+  s.rho_kg = rho_gcc * 1000.0;
+  s.tp.reserve((size_t)n);
+  s.y.reserve((size_t)n);
+  s.dy.reserve((size_t)n);
+  std::vector<double> tk;
+  tk.reserve((size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    if (std::isfinite(t[i]) && std::isfinite(y[i]) && std::isfinite(dy[i]) && dy[i] > 0.0) {
+      tk.push_back(t[i]);
+      s.y.push_back(y[i]);
+      s.dy.push_back(dy[i]);
+    }
+  }
+  const int64_t m = (int64_t)tk.size();
+  if (m < 2) { s.status = QLP_STAR_TOO_FEW; s.n_valid = m; return; }
+  for (int64_t i = 1; i < m; ++i)
+    if (tk[i] < tk[i - 1]) { s.status = QLP_STAR_UNSORTED; s.n_valid = m; return; }
+  s.n_valid = m;
+  s.t_ref = tk[0];
+  s.tp.resize((size_t)m);
+  for (int64_t i = 0; i < m; ++i) s.tp[i] = tk[i] - s.t_ref;
+  s.baseline = s.tp[m - 1];
+  s.pmin = pmin_of(s.rho_kg, p);
+  s.pmax = pmax_of(s.tp.data(), m, p);
+  if (!(s.baseline > 0.0) || !(s.pmin < s.pmax)) { s.status = QLP_STAR_EMPTY_GRID; return; }
+  const double fmax = 1.0 / s.pmin;
+  const double denom = p.samples_per_peak * s.baseline;
+  double f = 1.0 / s.pmax;
+  while (f <= fmax) {
+    const double q = q_min_of(f, s.rho_kg, p);
+    s.freqs.push_back(f);
+    s.qmins.push_back(q);
+    const int nb = nbins_of(q, p);
+    s.nbins_max = std::max(s.nbins_max, nb);
+    s.ymax = std::max(s.ymax, s.baseline * f * (double)nb);
+    f = f + q / denom;
+  }
+  if (s.freqs.empty()) { s.status = QLP_STAR_EMPTY_GRID; return; }
+  if (s.nbins_max > p.nbins_cap) {
+    s.status = QLP_STAR_NBINS_CAP;
+    s.freqs.clear();
+    s.qmins.clear();
+    return;
+  }
+  s.sturges_nb = sturges_of((int64_t)s.freqs.size());
+}
+
+void plan_all(const qlp_bls_params& p, int32_t n_stars, const int64_t* offsets, const double* t,
+              const double* y, const double* dy, const double* rho, std::vector<StarPlanHost>* out) {
+  out->assign((size_t)n_stars, StarPlanHost());
+  int nth = p.n_threads > 0 ? p.n_threads : (int)std::thread::hardware_concurrency();
+  nth = std::max(1, std::min(nth, std::max(1, n_stars)));
+  auto work = [&](int tid) {
+    for (int32_t s = tid; s < n_stars; s += nth) {
+      const int64_t a = offsets[s], b = offsets[s + 1];
+      const double r = rho ? rho[s] : NAN;
+      plan_one(p, t + a, y + a, dy + a, b - a, r, &(*out)[(size_t)s]);
+    }
+  };
+  if (nth == 1) {
+    work(0);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve((size_t)nth);
+  for (int i = 0; i < nth; ++i) th.emplace_back(work, i);
+  for (auto& x : th) x.join();
+}
+
+}  // namespace qlp

@@ -1,0 +1,292 @@
+// Spectral S/N and best candidate (K3), one CTA per star, for sm_103a.
+//
+// Sec. 2.2 item 1 of arXiv:2302.01293, Eq. 1 with the paper's two changes:
+//   trend(f)  the SR spectrum median-binned into N = round(1 + 3.322 log10 n)
+//             equal-width frequency bins (Sturges), bin medians placed at the bin
+//             centres and linearly interpolated (constant beyond the end centres);
+//   sigma_SR  1.4826 x median |SR - median(SR)| (or of the detrended residual);
+//   S/N(f)    (SR(f) - trend(f)) / sigma_SR;
+// then the best candidate at the first maximum of S/N (Sec. 2.2 item 2 takes its
+// BLS box as the initial P, T0, q and depth).
+// Medians are exact order statistics of the FP32 spectrum, found by a 4-pass
+// 8-bit radix select over order-preserving integer keys, all selections of one
+// pass sharing a pass over the spectrum (shared-memory digit histograms).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "qlp_internal.h"
+
+namespace qlp {
+
+constexpr int kSnrThreads = 512;
+constexpr int kMaxTargets = 2 * (kMaxSturges + 1);
+
+__device__ __forceinline__ uint32_t fkey(float v) {
+  const uint32_t u = __float_as_uint(v);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fdekey(uint32_t k) {
+  const uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  return __uint_as_float(u);
+}
+
+// Sturges bin of spectrum entry k: min(N-1, floor((f_k - f_0) N / span)).
+__device__ __forceinline__ int sturges_bin(double f, double f0, double span, int nbin) {
+  if (!(span > 0.0)) return 0;
+  const int i = (int)floor(__ddiv_rn(__dmul_rn(__dsub_rn(f, f0), (double)nbin), span));
+  return min(nbin - 1, i);
+}
+
+struct SnrShared {
+  int lo[kMaxSturges + 1];     // first spectrum index of each Sturges bin (lo[N] = n)
+  double xs[kMaxSturges];      // centres of the non-empty bins
+  double ys[kMaxSturges];      // their medians
+  int nx;
+  uint32_t prefix[kMaxTargets];
+  int rank[kMaxTargets];
+  uint32_t mask;
+  double med, sigma;
+  float best_v[kSnrThreads / 32];
+  int best_i[kSnrThreads / 32];
+};
+
+// Trend at frequency f from the (xs, ys) nodes, np.interp semantics.
+__device__ __forceinline__ double trend_at(const SnrShared& sh, double f) {
+  const int nx = sh.nx;
+  if (f <= sh.xs[0]) return sh.ys[0];
+  if (f >= sh.xs[nx - 1]) return sh.ys[nx - 1];
+  int lo = 0, hi = nx - 1;  // xs[lo] <= f < xs[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (sh.xs[mid] <= f) lo = mid; else hi = mid;
+  }
+  const double slope = __ddiv_rn(__dsub_rn(sh.ys[lo + 1], sh.ys[lo]), __dsub_rn(sh.xs[lo + 1], sh.xs[lo]));
+  return __dadd_rn(sh.ys[lo], __dmul_rn(slope, __dsub_rn(f, sh.xs[lo])));
+}
+
+__device__ __forceinline__ int bin_of_index(const SnrShared& sh, int k, int nbin) {
+  int lo = 0, hi = nbin;  // lo[lo] <= k < lo[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (sh.lo[mid] <= k) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Radix selection of the rank[t]-th smallest key for targets t in [0, nt);
+// KeyOf(k, &key, &tgt0, &ntg) gives entry k's key and its targets tgt0 .. tgt0+ntg-1
+// plus the two global targets handled by `global_t` (-1 = none).
+template <typename KeyOf>
+__device__ void radix_select(SnrShared& sh, uint32_t* hist, int nt, int n, KeyOf key_of) {
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) sh.prefix[t] = 0u;
+  if (threadIdx.x == 0) sh.mask = 0u;
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 24 - 8 * pass;
+    for (int i = threadIdx.x; i < nt * 256; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    const uint32_t mask = sh.mask;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      uint32_t key;
+      int t0, t1;
+      key_of(k, &key, &t0, &t1);
+      const uint32_t dig = (key >> shift) & 255u;
+      if (t0 >= 0) {
+        if ((key & mask) == sh.prefix[t0]) atomicAdd(&hist[t0 * 256 + dig], 1u);
+        if ((key & mask) == sh.prefix[t0 + 1]) atomicAdd(&hist[(t0 + 1) * 256 + dig], 1u);
+      }
+      if (t1 >= 0) {
+        if ((key & mask) == sh.prefix[t1]) atomicAdd(&hist[t1 * 256 + dig], 1u);
+        if ((key & mask) == sh.prefix[t1 + 1]) atomicAdd(&hist[(t1 + 1) * 256 + dig], 1u);
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+      int r = sh.rank[t];
+      if (r < 0) continue;
+      uint32_t d = 0;
+      for (; d < 256; ++d) {
+        const int c = (int)hist[t * 256 + d];
+        if (r < c) break;
+        r -= c;
+      }
+      sh.rank[t] = r;
+      sh.prefix[t] |= (d & 255u) << shift;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sh.mask |= 255u << shift;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kSnrThreads) snr_kernel(const SnrArgs a) {
+  extern __shared__ __align__(16) uint32_t hist[];
+  __shared__ SnrShared sh;
+  const int s = blockIdx.x;
+  const StarDev st = a.stars[s];
+  const int n = st.n_f;
+  qlp_bls_best* out = a.best + s;
+
+  if (n <= 0 || st.status != 0) {
+    if (threadIdx.x == 0) {
+      out->f_idx = -1;
+      out->f = out->period = out->t0 = out->q = out->depth = out->sr = out->snr = 0.0;
+      out->j = out->k = out->m = out->nbins = -1;
+      out->status = st.status;
+      out->pad = 0;
+    }
+    return;
+  }
+  const int nbin = st.sturges_nb;
+  if (nbin < 1 || nbin > kMaxSturges) {
+    if (threadIdx.x == 0) {
+      atomicOr(a.err, kErrSturges);
+      out->f_idx = -1;
+      out->status = st.status;
+    }
+    return;
+  }
+  const float* sr = a.sr + st.f_off;
+  const double2* fq = a.fq + st.f_off;
+  float* snr = a.snr + st.f_off;
+  const double f0 = fq[0].x;
+  const double span = __dsub_rn(fq[n - 1].x, f0);
+
+  // bin boundaries: lo[i] = first k with bin(k) >= i
+  for (int i = threadIdx.x; i <= nbin; i += blockDim.x) {
+    int lo = 0, hi = n;
+    if (i == 0) hi = 0;
+    else if (i == nbin) lo = n;
+    else {
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (sturges_bin(fq[mid].x, f0, span, nbin) >= i) hi = mid; else lo = mid + 1;
+      }
+    }
+    sh.lo[i] = lo;
+  }
+  __syncthreads();
+
+  // medians of every bin (targets 2i, 2i+1) and of the whole spectrum (2N, 2N+1)
+  const int tg = 2 * nbin;
+  for (int i = threadIdx.x; i <= nbin; i += blockDim.x) {
+    const int c = (i < nbin) ? sh.lo[i + 1] - sh.lo[i] : n;
+    sh.rank[2 * i] = c > 0 ? (c - 1) / 2 : -1;
+    sh.rank[2 * i + 1] = c > 0 ? c / 2 : -1;
+  }
+  __syncthreads();
+  radix_select(sh, hist, tg + 2, n, [&](int k, uint32_t* key, int* t0, int* t1) {
+    *key = fkey(sr[k]);
+    *t0 = 2 * bin_of_index(sh, k, nbin);
+    *t1 = tg;
+  });
+  if (threadIdx.x == 0) {
+    int nx = 0;
+    for (int i = 0; i < nbin; ++i) {
+      if (sh.lo[i + 1] - sh.lo[i] <= 0) continue;
+      const double v0 = (double)fdekey(sh.prefix[2 * i]);
+      const double v1 = (double)fdekey(sh.prefix[2 * i + 1]);
+      sh.xs[nx] = __dadd_rn(f0, __ddiv_rn(__dmul_rn((double)i + 0.5, span), (double)nbin));
+      sh.ys[nx] = __dmul_rn(0.5, __dadd_rn(v0, v1));
+      ++nx;
+    }
+    sh.nx = nx;
+    sh.med = __dmul_rn(0.5, __dadd_rn((double)fdekey(sh.prefix[tg]), (double)fdekey(sh.prefix[tg + 1])));
+  }
+  __syncthreads();
+
+  if (a.mad_mode == QLP_MAD_RESID) {
+    // median of the residual SR - trend first
+    if (threadIdx.x == 0) { sh.rank[0] = (n - 1) / 2; sh.rank[1] = n / 2; }
+    __syncthreads();
+    radix_select(sh, hist, 2, n, [&](int k, uint32_t* key, int* t0, int* t1) {
+      *key = fkey((float)__dsub_rn((double)sr[k], trend_at(sh, fq[k].x)));
+      *t0 = 0;
+      *t1 = -1;
+    });
+    if (threadIdx.x == 0)
+      sh.med = __dmul_rn(0.5, __dadd_rn((double)fdekey(sh.prefix[0]), (double)fdekey(sh.prefix[1])));
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { sh.rank[0] = (n - 1) / 2; sh.rank[1] = n / 2; }
+  __syncthreads();
+  const bool resid = a.mad_mode == QLP_MAD_RESID;
+  radix_select(sh, hist, 2, n, [&](int k, uint32_t* key, int* t0, int* t1) {
+    double v = (double)sr[k];
+    if (resid) v = __dsub_rn(v, trend_at(sh, fq[k].x));
+    *key = fkey((float)fabs(__dsub_rn(v, sh.med)));
+    *t0 = 0;
+    *t1 = -1;
+  });
+  if (threadIdx.x == 0) {
+    const double mad = __dmul_rn(0.5, __dadd_rn((double)fdekey(sh.prefix[0]), (double)fdekey(sh.prefix[1])));
+    sh.sigma = __dmul_rn(1.4826, mad);
+  }
+  __syncthreads();
+  const double sigma = sh.sigma;
+
+  // S/N and its first maximum
+  float bv = -3.0e38f;
+  int bi = n;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    float v = 0.f;
+    if (sigma > 0.0) v = (float)__ddiv_rn(__dsub_rn((double)sr[k], trend_at(sh, fq[k].x)), sigma);
+    snr[k] = v;
+    if (v > bv) { bv = v; bi = k; }   // k increases: first maximum per thread
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+    if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { sh.best_v[warp] = bv; sh.best_i[warp] = bi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      if (sh.best_v[w] > bv || (sh.best_v[w] == bv && sh.best_i[w] < bi)) { bv = sh.best_v[w]; bi = sh.best_i[w]; }
+    }
+    out->status = st.status;
+    out->pad = 0;
+    const int j = (bi < n) ? (int)a.qidx[st.f_off + bi] : 255;
+    if (!(sigma > 0.0) || bi >= n || j >= a.nq) {
+      if (!(sigma > 0.0)) out->status |= QLP_STAR_ZERO_MAD;
+      out->f_idx = -1;
+      out->f = out->period = out->t0 = out->q = out->depth = out->sr = out->snr = 0.0;
+      out->j = out->k = out->m = out->nbins = -1;
+    } else {
+      const double f = fq[bi].x;
+      const double qmin = fq[bi].y;
+      const int nb = (int)ceil(__ddiv_rn(a.noverlap, qmin));
+      const int m = max(1, (int)floor(__dadd_rn(__dmul_rn(__dmul_rn(qmin, a.E[j]), (double)nb), 0.5)));
+      const int kb = (int)a.kbin[st.f_off + bi];
+      const double period = __ddiv_rn(1.0, f);
+      const double mid = __ddiv_rn(__dadd_rn((double)kb, __dmul_rn(0.5, (double)m)), (double)nb);
+      const double r = (double)a.rbest[st.f_off + bi];
+      const double sv = (double)a.sbest[st.f_off + bi];
+      out->f_idx = bi;
+      out->f = f;
+      out->period = period;
+      out->t0 = __dadd_rn(st.t_ref, __dmul_rn(period, __dsub_rn(mid, floor(mid))));
+      out->q = __ddiv_rn((double)m, (double)nb);
+      out->depth = -__ddiv_rn(sv, __dmul_rn(r, __dsub_rn(1.0, r)));
+      out->sr = (double)sr[bi];
+      out->snr = (double)bv;
+      out->j = j;
+      out->k = kb;
+      out->m = m;
+      out->nbins = nb;
+    }
+  }
+}
+
+int launch_snr(const SnrArgs& a, void* stream) {
+  if (a.n_stars <= 0) return 0;
+  const size_t smem = (size_t)kMaxTargets * 256 * sizeof(uint32_t);
+  cudaError_t e = cudaFuncSetAttribute(snr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  snr_kernel<<<a.n_stars, kSnrThreads, smem, (cudaStream_t)stream>>>(a);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace qlp

@@ -1,0 +1,267 @@
+"""Thin ctypes binding of libqlpbls (include/qlp_bls.h), same names as the C ABI.
+
+Argument marshalling only: PyTorch supplies device memory and the stream, every
+step of the search runs in the library's CUDA kernels. There is no CPU path:
+loading fails loudly when the library cannot be built or loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+PHASE_FP64, PHASE_DF, PHASE_FP32 = 0, 1, 2
+SUM_PLAIN, SUM_COMP = 0, 1
+MAD_RAW, MAD_RESID = 0, 1
+
+STAR_UNSORTED, STAR_TOO_FEW, STAR_EMPTY_GRID, STAR_NBINS_CAP, STAR_ZERO_MAD = 1, 2, 4, 8, 16
+
+BEST_DTYPE = np.dtype([("f_idx", "<i8"), ("f", "<f8"), ("period", "<f8"), ("t0", "<f8"),
+                       ("q", "<f8"), ("depth", "<f8"), ("sr", "<f8"), ("snr", "<f8"),
+                       ("j", "<i4"), ("k", "<i4"), ("m", "<i4"), ("nbins", "<i4"),
+                       ("status", "<i4"), ("pad", "<i4")])
+assert BEST_DTYPE.itemsize == 88
+
+
+class CParams(ctypes.Structure):
+    _fields_ = [("samples_per_peak", ctypes.c_double), ("dlogq", ctypes.c_double),
+                ("noverlap", ctypes.c_double), ("qmin_fac", ctypes.c_double),
+                ("qmax_fac", ctypes.c_double), ("pmin_aR", ctypes.c_double),
+                ("gap_days", ctypes.c_double), ("rho_default", ctypes.c_double),
+                ("nbins_cap", ctypes.c_int32), ("phase_mode", ctypes.c_int32),
+                ("sum_mode", ctypes.c_int32), ("mad_mode", ctypes.c_int32),
+                ("chunk_freqs", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("n_threads", ctypes.c_int32), ("tile_points", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+@dataclasses.dataclass
+class Params:
+    samples_per_peak: float = 2.0
+    dlogq: float = 0.1
+    noverlap: float = 3.0
+    qmin_fac: float = 0.5
+    qmax_fac: float = 2.0
+    pmin_aR: float = 2.0
+    gap_days: float = 27.4
+    rho_default: float = 1.41
+    nbins_cap: int = 8192
+    phase_mode: int = PHASE_DF
+    sum_mode: int = SUM_COMP
+    mad_mode: int = MAD_RAW
+    chunk_freqs: int = 0
+    warps_per_block: int = 0
+    n_threads: int = 0
+    tile_points: int = 0
+
+    def to_c(self) -> CParams:
+        c = CParams()
+        for f in dataclasses.fields(self):
+            setattr(c, f.name, getattr(self, f.name))
+        return c
+
+
+class QlpError(RuntimeError):
+    pass
+
+
+_lib = None
+_lock = threading.Lock()
+
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+_i32, _i64, _d = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+
+
+def lib():
+    """Load (building first if needed) the in-tree CUDA library."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            L.qlp_bls_params_default.argtypes = [_P(CParams)]
+            L.qlp_bls_params_default.restype = None
+            L.qlp_bls_plan.argtypes = [_P(CParams), _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _P(_vp)]
+            L.qlp_bls_plan.restype = ctypes.c_int
+            L.qlp_bls_plan_info.argtypes = [_vp, _P(_i64), _vp, _vp, _vp, _P(_i64), _P(_d)]
+            L.qlp_bls_plan_info.restype = ctypes.c_int
+            L.qlp_bls_search.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp]
+            L.qlp_bls_search.restype = ctypes.c_int
+            L.qlp_bls_snr.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+            L.qlp_bls_snr.restype = ctypes.c_int
+            L.qlp_bls_run_host.argtypes = [_P(CParams), _i32, _vp, _vp, _vp, _vp, _vp, _vp,
+                                           _vp, _vp, _i64, _vp, _P(_i64)]
+            L.qlp_bls_run_host.restype = ctypes.c_int
+            L.qlp_bls_device_status.argtypes = [_vp, _vp, _P(_i32)]
+            L.qlp_bls_device_status.restype = ctypes.c_int
+            L.qlp_bls_plan_destroy.argtypes = [_vp]
+            L.qlp_bls_plan_destroy.restype = None
+            L.qlp_bls_star_grid.argtypes = [_P(CParams), _i64, _vp, _vp, _vp, _d, _P(_i32), _P(_d),
+                                            _P(_d), _P(_d), _P(_d), _vp, _vp, _i64, _P(_i64)]
+            L.qlp_bls_star_grid.restype = ctypes.c_int
+            L.qlp_strerror.argtypes = [ctypes.c_int]
+            L.qlp_strerror.restype = ctypes.c_char_p
+            L.qlp_last_cuda_error.argtypes = []
+            L.qlp_last_cuda_error.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        L = lib()
+        msg = L.qlp_strerror(rc).decode()
+        cu = L.qlp_last_cuda_error().decode()
+        raise QlpError(f"{what}: {msg} ({rc}){' / ' + cu if cu else ''}")
+
+
+def _np_ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _host_inputs(offsets, t, y, dy, rho, rstar):
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    t = np.ascontiguousarray(t, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    dy = np.ascontiguousarray(dy, np.float64)
+    rho = None if rho is None else np.ascontiguousarray(rho, np.float64)
+    rstar = None if rstar is None else np.ascontiguousarray(rstar, np.float64)
+    return offsets, t, y, dy, rho, rstar
+
+
+class Plan:
+    """A library-owned search plan (qlp_bls_plan) and its sizes."""
+
+    def __init__(self, offsets, t, y, dy, rho=None, rstar=None, params: Params | None = None,
+                 stream=None):
+        import torch
+        self._h = ctypes.c_void_p()
+        L = lib()
+        offsets, t, y, dy, rho, rstar = _host_inputs(offsets, t, y, dy, rho, rstar)
+        self.n_stars = int(offsets.shape[0] - 1)
+        self.params = params or Params()
+        cp = self.params.to_c()
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        rc = L.qlp_bls_plan(ctypes.byref(cp), self.n_stars, _np_ptr(offsets), _np_ptr(t), _np_ptr(y),
+                            _np_ptr(dy), _np_ptr(rho), _np_ptr(rstar), _stream_ptr(stream),
+                            ctypes.byref(self._h))
+        _check(rc, "qlp_bls_plan")
+        nft = _i64()
+        npts = _i64()
+        work = _d()
+        L.qlp_bls_plan_info(self._h, ctypes.byref(nft), None, None, None, ctypes.byref(npts),
+                            ctypes.byref(work))
+        self.n_freq_total = int(nft.value)
+        self.n_points = int(npts.value)
+        self.work = float(work.value)
+        self.freq_offsets = np.zeros(self.n_stars + 1, np.int64)
+        self.freqs = np.zeros(self.n_freq_total, np.float64)
+        self.star_status = np.zeros(self.n_stars, np.int32)
+        _check(L.qlp_bls_plan_info(self._h, None, _np_ptr(self.freq_offsets), _np_ptr(self.freqs),
+                                   _np_ptr(self.star_status), None, None), "qlp_bls_plan_info")
+
+    def alloc_outputs(self):
+        import torch
+        n = max(self.n_freq_total, 1)
+        dev = self.device
+        return dict(sr=torch.empty(n, dtype=torch.float32, device=dev),
+                    qidx=torch.empty(n, dtype=torch.uint8, device=dev),
+                    kbin=torch.empty(n, dtype=torch.int32, device=dev),
+                    s=torch.empty(n, dtype=torch.float32, device=dev),
+                    r=torch.empty(n, dtype=torch.float32, device=dev),
+                    snr=torch.empty(n, dtype=torch.float32, device=dev),
+                    best=torch.empty(max(self.n_stars, 1) * BEST_DTYPE.itemsize, dtype=torch.uint8,
+                                     device=dev))
+
+    def search(self, out=None, stream=None):
+        """qlp_bls_search into `out` (from alloc_outputs); returns `out`."""
+        out = out or self.alloc_outputs()
+        rc = lib().qlp_bls_search(self._h, _stream_ptr(stream), out["sr"].data_ptr(),
+                                  out["qidx"].data_ptr(), out["kbin"].data_ptr(), out["s"].data_ptr(),
+                                  out["r"].data_ptr())
+        _check(rc, "qlp_bls_search")
+        return out
+
+    def snr(self, out, stream=None):
+        """qlp_bls_snr on the arrays of a previous search; returns `out`."""
+        rc = lib().qlp_bls_snr(self._h, _stream_ptr(stream), out["sr"].data_ptr(),
+                               out["qidx"].data_ptr(), out["kbin"].data_ptr(), out["s"].data_ptr(),
+                               out["r"].data_ptr(), out["snr"].data_ptr(), out["best"].data_ptr())
+        _check(rc, "qlp_bls_snr")
+        return out
+
+    def device_status(self, stream=None) -> int:
+        flags = _i32()
+        rc = lib().qlp_bls_device_status(self._h, _stream_ptr(stream), ctypes.byref(flags))
+        if rc not in (0, -4):
+            _check(rc, "qlp_bls_device_status")
+        return int(flags.value)
+
+    def best_host(self, out) -> np.ndarray:
+        raw = out["best"].cpu().numpy()[: self.n_stars * BEST_DTYPE.itemsize]
+        return raw.view(BEST_DTYPE).copy()
+
+    def star_slice(self, s: int) -> slice:
+        return slice(int(self.freq_offsets[s]), int(self.freq_offsets[s + 1]))
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().qlp_bls_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def run_host(offsets, t, y, dy, rho=None, rstar=None, params: Params | None = None,
+             sr_capacity: int = 0):
+    """qlp_bls_run_host: host arrays in, host results out (best per star, and the
+    SR / S/N spectra when sr_capacity >= the number of trial frequencies)."""
+    L = lib()
+    offsets, t, y, dy, rho, rstar = _host_inputs(offsets, t, y, dy, rho, rstar)
+    n_stars = int(offsets.shape[0] - 1)
+    cp = (params or Params()).to_c()
+    best = np.zeros(max(n_stars, 1), BEST_DTYPE)
+    sr = np.zeros(sr_capacity, np.float32) if sr_capacity > 0 else None
+    snr = np.zeros(sr_capacity, np.float32) if sr_capacity > 0 else None
+    nft = _i64()
+    rc = L.qlp_bls_run_host(ctypes.byref(cp), n_stars, _np_ptr(offsets), _np_ptr(t), _np_ptr(y),
+                            _np_ptr(dy), _np_ptr(rho), _np_ptr(rstar), _np_ptr(sr), _np_ptr(snr),
+                            int(sr_capacity), _np_ptr(best), ctypes.byref(nft))
+    _check(rc, "qlp_bls_run_host")
+    return dict(best=best[:n_stars], sr=sr, snr=snr, n_freq_total=int(nft.value))
+
+
+def star_grid(t, y, dy, rho=float("nan"), params: Params | None = None):
+    """qlp_bls_star_grid: the host plan of one star (no device work)."""
+    L = lib()
+    t = np.ascontiguousarray(t, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    dy = np.ascontiguousarray(dy, np.float64)
+    cp = (params or Params()).to_c()
+    st, pmin, pmax, tref, base, nf = _i32(), _d(), _d(), _d(), _d(), _i64()
+    args = [ctypes.byref(cp), t.shape[0], _np_ptr(t), _np_ptr(y), _np_ptr(dy), float(rho),
+            ctypes.byref(st), ctypes.byref(pmin), ctypes.byref(pmax), ctypes.byref(tref),
+            ctypes.byref(base)]
+    _check(L.qlp_bls_star_grid(*args, None, None, 0, ctypes.byref(nf)), "qlp_bls_star_grid")
+    freqs = np.zeros(nf.value, np.float64)
+    qmins = np.zeros(nf.value, np.float64)
+    _check(L.qlp_bls_star_grid(*args, _np_ptr(freqs), _np_ptr(qmins), nf.value, ctypes.byref(nf)),
+           "qlp_bls_star_grid")
+    return dict(status=int(st.value), pmin=pmin.value, pmax=pmax.value, t_ref=tref.value,
+                baseline=base.value, freqs=freqs, qmins=qmins)

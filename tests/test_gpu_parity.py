@@ -1,0 +1,116 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Cases: the single-sector 30-min star; a ragged batch of uneven 200-s sectors
+(several tiles, a ragged tail, forced small tiles); multi-sector stars; stars
+the planner rejects mixed into a batch; the empty batch; every phase and sum
+mode; and the full 4,096-star batch on sampled stars in the bench's launch
+configuration. Tolerances are those of tests/parity.py.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_2302_01293_gb300 import qlpbls
+from parity import compare_snr, compare_spectrum, oracle_star, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_batch(batch, params, stars=None, with_snr=True):
+    g = run_gpu(batch, params, with_snr=with_snr)
+    assert g["flags"] == 0
+    plan = g["plan"]
+    stats = []
+    for s in (range(batch.n_stars) if stars is None else stars):
+        pl, ores = oracle_star(batch, s)
+        assert plan.star_status[s] == pl.status
+        sl = plan.star_slice(s)
+        assert np.array_equal(plan.freqs[sl], pl.freqs)
+        st = compare_spectrum(pl, ores, g, sl, label=f"star {s}")
+        if with_snr:
+            st.update(compare_snr(pl, ores, g, sl, g["best"][s], label=f"star {s}"))
+        stats.append(st)
+    return g, stats
+
+
+@pytest.mark.parametrize("phase", [qlpbls.PHASE_FP64, qlpbls.PHASE_DF])
+@pytest.mark.parametrize("summ", [qlpbls.SUM_PLAIN, qlpbls.SUM_COMP])
+def test_single_star(gpu_lib, phase, summ):
+    b = synth.single_star()
+    g, stats = _check_batch(b, qlpbls.Params(phase_mode=phase, sum_mode=summ))
+    best = g["best"][0]
+    assert abs(best["period"] / 3.7 - 1) < 0.01 and best["snr"] > 9
+
+
+@pytest.mark.parametrize("tile", [0, 256, 1024])
+def test_uneven_batch_tiles(gpu_lib, tile):
+    b = synth.uneven_single_sector(n_stars=6, seed=12)
+    _check_batch(b, qlpbls.Params(tile_points=tile))
+
+
+@pytest.mark.parametrize("warps", [4, 8, 16])
+def test_warps_per_block(gpu_lib, warps):
+    b = synth.uneven_single_sector(n_stars=3, seed=13)
+    _check_batch(b, qlpbls.Params(warps_per_block=warps, chunk_freqs=warps * 3))
+
+
+def test_multi_sector(gpu_lib):
+    b = synth.multi_sector(n_stars=2, seed=14, max_sectors=3)
+    _check_batch(b, qlpbls.Params())
+
+
+def test_tiny_ragged_and_rejected_stars(gpu_lib):
+    good = synth.tiny_batch(n_stars=5, seed=15, n_min=33, n_max=97)
+    # append stars the planner must reject: unsorted, one point, NaN-only
+    t = [good.star(s)[0] for s in range(good.n_stars)]
+    y = [good.star(s)[1] for s in range(good.n_stars)]
+    dy = [good.star(s)[2] for s in range(good.n_stars)]
+    t.append(np.array([3.0, 2.0, 1.0]) + 2000); y.append(np.ones(3)); dy.append(np.full(3, 1e-3))
+    t.append(np.array([2000.0])); y.append(np.ones(1)); dy.append(np.full(1, 1e-3))
+    t.append(np.linspace(2000, 2010, 20)); y.append(np.full(20, np.nan)); dy.append(np.full(20, 1e-3))
+    b = synth._assemble("mixed", t, y, dy, list(good.rho) + [1.41] * 3, [1.0] * 8, [True] * 8,
+                        [1.0] * 8, [0.0] * 8, [0.0] * 8, [0.0] * 8)
+    g, _ = _check_batch(b, qlpbls.Params())
+    assert list(g["plan"].star_status[5:]) == [qlpbls.STAR_UNSORTED, qlpbls.STAR_TOO_FEW,
+                                              qlpbls.STAR_TOO_FEW]
+    assert np.all(g["best"]["f_idx"][5:] == -1)
+
+
+def test_empty_batch(gpu_lib):
+    z = np.zeros(0)
+    plan = qlpbls.Plan(np.zeros(1, np.int64), z, z, z, z, z)
+    out = plan.search()
+    plan.snr(out)
+    assert plan.n_freq_total == 0 and plan.device_status() == 0
+
+
+def test_fp32_phase_runs_and_is_close(gpu_lib):
+    # FP32 folding is a precision-study mode: bins may differ, SR stays close
+    b = synth.uneven_single_sector(n_stars=2, seed=16)
+    g = run_gpu(b, qlpbls.Params(phase_mode=qlpbls.PHASE_FP32), with_snr=False)
+    for s in range(2):
+        pl, ores = oracle_star(b, s)
+        sr = g["sr"][g["plan"].star_slice(s)]
+        rel = np.abs(sr - ores.sr) / ores.sr
+        assert np.median(rel) < 1e-2
+
+
+def test_run_host_matches_device_path(gpu_lib):
+    b = synth.uneven_single_sector(n_stars=4, seed=17)
+    g = run_gpu(b, qlpbls.Params())
+    n = g["plan"].n_freq_total
+    h = qlpbls.run_host(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar, qlpbls.Params(), sr_capacity=n)
+    assert h["n_freq_total"] == n
+    assert np.array_equal(h["sr"], g["sr"][:n])
+    assert np.array_equal(h["snr"], g["snr"][:n])
+    assert np.array_equal(h["best"]["f_idx"], g["best"]["f_idx"])
+
+
+def test_full_batch_sampled(gpu_lib):
+    # the 4,096-star uneven single-sector batch in the default launch shape;
+    # 12 sampled stars checked in full against the oracle
+    b = synth.uneven_single_sector(n_stars=4096, seed=2)
+    rng = np.random.default_rng(0)
+    stars = sorted(rng.choice(4096, 12, replace=False).tolist())
+    _check_batch(b, qlpbls.Params(), stars=stars)
