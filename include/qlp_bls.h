@@ -219,6 +219,42 @@ int qlp_bls_star_grid(const qlp_bls_params* p, int64_t n, const double* t, const
                       double* t_ref, double* baseline, double* freqs, double* qmins,
                       int64_t capacity, int64_t* n_f_out);
 
+/*
+ * qlp_bls_search_static -- the paper has no counterpart of this entry point.
+ * The BLS search of ONE star (qlp_bls_search's results for that star) without
+ * allocating any device memory, for callers that may not call cudaMalloc: code
+ * that runs inside a host framework which owns every device allocation, or a
+ * service whose device memory is fixed before work starts.
+ * The scratch the search needs (prepared points, frequency table, work queue)
+ * is a library-owned static device array of QLP_STATIC_SCRATCH_BYTES (16 MiB),
+ * present on every GPU that loads the library until the process exits. A call
+ * whose sizes do not fit (about 24 bytes per point plus 32 bytes per trial
+ * frequency, e.g. 300,000 points and 200,000 frequencies) returns QLP_ERR_ARG.
+ * The first call on each device looks up the array's device address with that
+ * device current; make that first call before any stream capture. All calls
+ * share the one array and it keeps the previous call's contents (each call
+ * clears what must start at zero): calls that overlap on the GPU (different
+ * streams or threads) race, so serialise them.
+ *  p            parameters (NULL = defaults); nbins_cap, phase/sum mode, warps,
+ *               chunk and tile options apply as for qlp_bls_plan.
+ *  n            number of valid points (>= 2).
+ *  tp, y, dy    device double[n], caller-owned: t' = t - t_min sorted ascending,
+ *               flux and 1-sigma error of the star's valid points (as
+ *               qlp_bls_star_grid keeps them).
+ *  baseline     t'[n-1] (days).
+ *  n_f, freqs, qmins  host double[n_f]: the star's trial frequencies and their
+ *               q_min, e.g. from qlp_bls_star_grid.
+ *  stream       cudaStream_t (NULL = default stream).
+ *  sr, qidx, phase_bin, s_best, r_best  device outputs of n_f entries, as for
+ *               qlp_bls_search (qidx, phase_bin, s_best, r_best may be NULL).
+ * Asynchronous on `stream`; results are valid after it is synchronised.
+ */
+#define QLP_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+int qlp_bls_search_static(const qlp_bls_params* p, int32_t n, const double* tp, const double* y,
+                          const double* dy, double baseline, int32_t n_f, const double* freqs,
+                          const double* qmins, void* stream, float* sr, uint8_t* qidx,
+                          uint32_t* phase_bin, float* s_best, float* r_best);
+
 /* Static description of a return code. */
 const char* qlp_strerror(int code);
 

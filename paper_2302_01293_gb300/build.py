@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqlpbls.so")
 ROOT = os.path.dirname(HERE)
 
-CU_SOURCES = ["bls_kernels.cu", "snr_kernel.cu"]
+CU_SOURCES = ["bls_kernels.cu", "snr_kernel.cu", "static_search.cu"]
 CPP_SOURCES = ["planner.cpp", "api.cpp"]
 HEADERS = ["qlp_internal.h", "planner.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -105,6 +105,9 @@ def lib():
             L.qlp_bls_star_grid.argtypes = [_P(CParams), _i64, _vp, _vp, _vp, _d, _P(_i32), _P(_d),
                                             _P(_d), _P(_d), _P(_d), _vp, _vp, _i64, _P(_i64)]
             L.qlp_bls_star_grid.restype = ctypes.c_int
+            L.qlp_bls_search_static.argtypes = [_P(CParams), _i32, _vp, _vp, _vp, _d, _i32, _vp,
+                                                _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+            L.qlp_bls_search_static.restype = ctypes.c_int
             L.qlp_strerror.argtypes = [ctypes.c_int]
             L.qlp_strerror.restype = ctypes.c_char_p
             L.qlp_last_cuda_error.argtypes = []
@@ -265,3 +268,21 @@ def star_grid(t, y, dy, rho=float("nan"), params: Params | None = None):
            "qlp_bls_star_grid")
     return dict(status=int(st.value), pmin=pmin.value, pmax=pmax.value, t_ref=tref.value,
                 baseline=base.value, freqs=freqs, qmins=qmins)
+
+
+def search_static(tp, y, dy, baseline, freqs, qmins, out, params: Params | None = None, stream=None):
+    """qlp_bls_search_static: one star's search with no device allocation inside
+    the call. tp, y, dy: device float64 tensors (t - t_min sorted, flux, error);
+    freqs, qmins: host float64 arrays; out: dict of device tensors sr, qidx, kbin,
+    s, r with at least len(freqs) entries (as from Plan.alloc_outputs)."""
+    L = lib()
+    freqs = np.ascontiguousarray(freqs, np.float64)
+    qmins = np.ascontiguousarray(qmins, np.float64)
+    cp = (params or Params()).to_c()
+    rc = L.qlp_bls_search_static(ctypes.byref(cp), int(tp.numel()), tp.data_ptr(), y.data_ptr(),
+                                 dy.data_ptr(), float(baseline), int(freqs.shape[0]),
+                                 _np_ptr(freqs), _np_ptr(qmins), _stream_ptr(stream),
+                                 out["sr"].data_ptr(), out["qidx"].data_ptr(), out["kbin"].data_ptr(),
+                                 out["s"].data_ptr(), out["r"].data_ptr())
+    _check(rc, "qlp_bls_search_static")
+    return out
