@@ -79,7 +79,10 @@ typedef struct qlp_bls_params {
   int32_t warps_per_block;  /* 0 = chosen by the planner; else 4, 8 or 16 */
   int32_t n_threads;        /* host threads for planning, 0 = all cores */
   int32_t tile_points;      /* points per shared-memory tile, 0 = as many as fit (multiple of 32) */
-  int32_t reserved[4];
+  int32_t method;           /* 0 = per star, the cheaper of the two search paths (default);
+                               1 = fold every point; 2 = bin edges on the cell table wherever the
+                               star allows it (same results: both give the FP64 bins) */
+  int32_t reserved[3];
 } qlp_bls_params;
 
 /* Best candidate of one star: the frequency of maximum S/N and its BLS box. */

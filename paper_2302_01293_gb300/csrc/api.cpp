@@ -66,16 +66,31 @@ struct qlp_bls_plan {
   uint32_t tile_off = 0;
   size_t smem = 0;
   int32_t n_items = 0;
+  // cell path launch shape
+  int c_warps = 8;
+  int c_blocks = 0;
+  int c_hist_stride = 0;
+  int c_cells_cap = 0;
+  uint32_t c_loc_off = 0, c_base_off = 0, c_hist_off = 0;
+  size_t c_smem = 0;
+  int32_t c_items = 0;
+  int32_t n_cell_stars = 0;
   // device
   StarDev* d_stars = nullptr;
   double2* d_fq = nullptr;
-  WorkItem* d_items = nullptr;
+  WorkItem* d_items = nullptr;    // per-point items, then cell items
   double* d_tp = nullptr;
   double* d_y = nullptr;
   double* d_dy = nullptr;
   float4* d_pts = nullptr;
   double* d_tpd = nullptr;
-  int32_t* d_ctl = nullptr;       // [0] queue head, [1] error flags
+  int32_t* d_cell_stars = nullptr;
+  double2* d_cpre = nullptr;
+  float* d_dt = nullptr;
+  float2* d_loc = nullptr;
+  float4* d_base = nullptr;
+  int32_t* d_gidx = nullptr;
+  int32_t* d_ctl = nullptr;       // [0] per-point queue head, [1] cell queue head, [2] error flags
 };
 
 static void free_plan(qlp_bls_plan_t* pl) {
@@ -88,6 +103,12 @@ static void free_plan(qlp_bls_plan_t* pl) {
   cudaFree(pl->d_dy);
   cudaFree(pl->d_pts);
   cudaFree(pl->d_tpd);
+  cudaFree(pl->d_cell_stars);
+  cudaFree(pl->d_cpre);
+  cudaFree(pl->d_dt);
+  cudaFree(pl->d_loc);
+  cudaFree(pl->d_base);
+  cudaFree(pl->d_gidx);
   cudaFree(pl->d_ctl);
   delete pl;
 }
@@ -112,6 +133,7 @@ void qlp_bls_params_default(qlp_bls_params* p) {
   p->chunk_freqs = 0;
   p->warps_per_block = 0;
   p->n_threads = 0;
+  p->method = 0;
 }
 
 const char* qlp_strerror(int code) {
@@ -134,7 +156,7 @@ static int check_params(const qlp_bls_params& p) {
       p.nbins_cap < 2)
     return QLP_ERR_ARG;
   if (p.phase_mode < 0 || p.phase_mode > 2 || p.sum_mode < 0 || p.sum_mode > 1 || p.mad_mode < 0 ||
-      p.mad_mode > 1 || p.tile_points < 0 || p.chunk_freqs < 0)
+      p.mad_mode > 1 || p.tile_points < 0 || p.chunk_freqs < 0 || p.method < 0 || p.method > 2)
     return QLP_ERR_ARG;
   if (p.warps_per_block != 0 && p.warps_per_block != 4 && p.warps_per_block != 8 &&
       p.warps_per_block != 16)
@@ -175,12 +197,37 @@ int qlp_bls_plan(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offs
   pl->nq = n_q_of(p);
   for (int j = 0; j < pl->nq; ++j) pl->E[j] = std::exp(j * p.dlogq);
 
+  const int NA = (p.sum_mode == QLP_SUM_COMP) ? 4 : 2;
+  const int smem_max = bls_max_smem_per_block();
+  if (smem_max <= 0) { delete pl; return cuda_fail(cudaGetLastError(), "device query"); }
+  const int budget = smem_max - 1024;
+  auto round32 = [](int64_t x) { return ((x + 31) / 32) * 32; };
+  auto align16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+
+  // method per star: the cell path needs one point per cell, its table and
+  // histograms in shared memory, and fewer bin edges than point-frequency pairs
+  const int cw = p.warps_per_block ? p.warps_per_block : 16;
+  // the table plus at least one warp's histogram for the star's largest bin count
+  auto cell_smem = [&](int64_t cells, int nbmax) {
+    return (size_t)cells_hist_offset((int)cells, cw) + (size_t)NA * (size_t)round32(nbmax + kMPad) * 4;
+  };
+  std::vector<int32_t> method((size_t)n_stars, kMethodPoints);
+  for (int32_t s = 0; s < n_stars; ++s) {
+    const StarPlanHost& h = sp[(size_t)s];
+    if (h.status != 0 || !h.cells_ok || p.method == 1 || p.phase_mode == QLP_PHASE_FP32) continue;
+    if (cell_smem(h.n_cells + 1, h.nbins_max) > (size_t)budget) continue;
+    const double pp_work = (double)h.freqs.size() * (double)round32((int64_t)h.tp.size());
+    if (p.method == 2 || h.cells_work < pp_work) method[(size_t)s] = kMethodCells;
+  }
+
   // flat host arrays
   std::vector<StarDev> stars((size_t)n_stars);
   pl->status.resize((size_t)n_stars);
   pl->f_off.assign((size_t)n_stars + 1, 0);
-  int64_t npt = 0, npad = 0, nf = 0;
-  int32_t max_npts = 0;
+  int64_t npt = 0, npad = 0, nf = 0, ncell = 0, nbase = 0, ncpre = 0;
+  int32_t max_npts = 0, nb_pp = 0, nb_c = 0;
+  int64_t cells_cap = 0;
+  std::vector<int32_t> cell_stars;
   for (int32_t s = 0; s < n_stars; ++s) {
     const StarPlanHost& h = sp[(size_t)s];
     StarDev& d = stars[(size_t)s];
@@ -194,20 +241,35 @@ int qlp_bls_plan(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offs
     d.status = h.status;
     d.sturges_nb = h.sturges_nb;
     d.fp64_phase = (h.ymax >= 4194304.0) ? 1 : 0;   // 2^22: beyond the FP32 remainder range
+    d.method = method[(size_t)s];
     d.t_ref = h.t_ref;
     d.baseline = h.baseline;
     pl->status[(size_t)s] = h.status;
     npt += d.n_pts;
-    npad += ((int64_t)d.n_pts + 31) & ~(int64_t)31;
     nf += d.n_f;
     pl->f_off[(size_t)s + 1] = nf;
-    max_npts = std::max(max_npts, d.n_pts);
-    if (ok) {
-      pl->nbins_max = std::max(pl->nbins_max, h.nbins_max);
-      pl->work += (double)d.n_pts * (double)d.n_f;
+    if (ok) pl->work += (double)d.n_pts * (double)d.n_f;
+    if (ok && d.method == kMethodCells) {
+      d.h = h.cell_h;
+      d.n_cells = (int32_t)h.n_cells;
+      d.cell_off = ncell;
+      d.base_off = nbase;
+      d.cpre_off = ncpre;
+      ncell += h.n_cells + 1;
+      nbase += (h.n_cells + 1 + 31) / 32;
+      ncpre += d.n_pts + 1;
+      cells_cap = std::max<int64_t>(cells_cap, h.n_cells + 1);
+      nb_c = std::max(nb_c, h.nbins_max);
+      cell_stars.push_back(s);
+    } else if (ok) {
+      npad += ((int64_t)d.n_pts + 31) & ~(int64_t)31;
+      max_npts = std::max(max_npts, d.n_pts);
+      nb_pp = std::max(nb_pp, h.nbins_max);
     }
+    if (ok) pl->nbins_max = std::max(pl->nbins_max, h.nbins_max);
   }
   pl->n_points = npt;
+  pl->n_cell_stars = (int32_t)cell_stars.size();
   std::vector<double> tp_all((size_t)std::max<int64_t>(npt, 1)), y_all(tp_all.size()), dy_all(tp_all.size());
   std::vector<double2> fq((size_t)std::max<int64_t>(nf, 1));
   pl->freqs.resize((size_t)nf);
@@ -225,62 +287,89 @@ int qlp_bls_plan(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offs
     }
   }
 
-  // launch shape: histograms per warp, then the largest point tile that fits
-  const int NA = (p.sum_mode == QLP_SUM_COMP) ? 4 : 2;
-  pl->hist_stride = ((std::max(pl->nbins_max, 1) + kMPad + 31) / 32) * 32;
-  const int smem_max = bls_max_smem_per_block();
-  if (smem_max <= 0) { delete pl; return cuda_fail(cudaGetLastError(), "device query"); }
-  const int budget = smem_max - 1024;
+  int dev = 0, sms = 0;
+  QLP_CK(cudaGetDevice(&dev));
+  QLP_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+
+  // per-point launch shape: histograms per warp, then the largest point tile that fits
+  pl->hist_stride = (int)round32(std::max(nb_pp, 1) + kMPad);
   int warps = p.warps_per_block ? p.warps_per_block : 8;
   auto hist_bytes = [&](int w) { return (size_t)w * NA * pl->hist_stride * 4 + (size_t)w * kMaxQ * 4; };
   while (warps > 4 && hist_bytes(warps) > (size_t)budget / 2) warps /= 2;
-  const size_t hb = (hist_bytes(warps) + 15) & ~(size_t)15;
+  const size_t hb = align16(hist_bytes(warps));
   if (hb + 32 * 16 > (size_t)budget) { delete pl; return QLP_ERR_UNSUPPORTED; }
   int tile = (int)(((size_t)budget - hb) / 16 / 32 * 32);
-  const int need = ((std::max(max_npts, 1) + 31) / 32) * 32;
-  tile = std::min(tile, need);
+  tile = std::min<int>(tile, (int)round32(std::max(max_npts, 1)));
   if (p.tile_points > 0) tile = std::min(tile, std::max(32, (p.tile_points / 32) * 32));
   pl->warps = warps;
   pl->tile_pts = tile;
   pl->tile_off = (uint32_t)hb;
   pl->smem = hb + (size_t)tile * 16;
-  int dev = 0, sms = 0;
-  QLP_CK(cudaGetDevice(&dev));
-  QLP_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   int per_sm = bls_blocks_per_sm(p.phase_mode, p.sum_mode, warps, pl->smem);
   if (per_sm < 1) { delete pl; return QLP_ERR_UNSUPPORTED; }
   pl->blocks = sms * per_sm;
 
-  // work items: (star, chunk of frequencies), longest first
-  int chunk = p.chunk_freqs;
-  if (chunk <= 0) {
-    const double per = (double)nf / (8.0 * pl->blocks * warps);
-    int rounds = (int)std::floor(per);
-    rounds = std::max(1, std::min(rounds, 16));
-    chunk = rounds * warps;
+  // cell launch shape: the whole shared-memory budget; each work item gets the
+  // histogram stride of its own largest bin count and as many warps as fit
+  (void)cells_cap;
+  (void)nb_c;
+  if (!cell_stars.empty()) {
+    pl->c_warps = cw;
+    pl->c_smem = (size_t)budget;
+    const int cper = cells_blocks_per_sm(p.sum_mode, cw, pl->c_smem);
+    if (cper < 1) { delete pl; return QLP_ERR_UNSUPPORTED; }
+    pl->c_blocks = sms * cper;
   }
-  std::vector<WorkItem> items;
-  std::vector<double> cost;
-  for (int32_t s = 0; s < n_stars; ++s) {
-    const StarDev& d = stars[(size_t)s];
-    const StarPlanHost& h = sp[(size_t)s];
-    for (int32_t b = 0; b < d.n_f; b += chunk) {
-      WorkItem w{};
-      w.star = s;
-      w.f_begin = b;
-      w.f_count = std::min(chunk, d.n_f - b);
-      items.push_back(w);
-      const int mid = b + w.f_count / 2;
-      const double nbm = std::ceil(p.noverlap / h.qmins[(size_t)mid]);
-      cost.push_back((double)w.f_count * ((double)d.n_pts + 3.0 * nbm));
+
+  // work items: (star, chunk of frequencies), longest first, one queue per path
+  auto make_items = [&](int32_t meth, int w, int blocks, std::vector<WorkItem>* outv) {
+    int64_t nf_m = 0;
+    for (int32_t s = 0; s < n_stars; ++s)
+      if (stars[(size_t)s].method == meth) nf_m += stars[(size_t)s].n_f;
+    int chunk = p.chunk_freqs;
+    if (chunk <= 0) {
+      int rounds = (int)std::floor((double)nf_m / (8.0 * std::max(blocks, 1) * w));
+      rounds = std::max(1, std::min(rounds, 16));
+      chunk = rounds * w;
     }
-  }
-  std::vector<int32_t> order(items.size());
-  for (size_t i = 0; i < order.size(); ++i) order[i] = (int32_t)i;
-  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[(size_t)a] > cost[(size_t)b]; });
-  std::vector<WorkItem> sorted(items.size());
-  for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[(size_t)order[i]];
-  pl->n_items = (int32_t)sorted.size();
+    std::vector<WorkItem> items;
+    std::vector<double> cost;
+    for (int32_t s = 0; s < n_stars; ++s) {
+      const StarDev& d = stars[(size_t)s];
+      if (d.method != meth) continue;
+      const StarPlanHost& h = sp[(size_t)s];
+      for (int32_t b = 0; b < d.n_f; b += chunk) {
+        WorkItem wi{};
+        wi.star = s;
+        wi.f_begin = b;
+        wi.f_count = std::min(chunk, d.n_f - b);
+        if (meth == kMethodCells) {
+          int nbm = 1;
+          for (int32_t k = b; k < b + wi.f_count; ++k)
+            nbm = std::max(nbm, (int)std::ceil(p.noverlap / h.qmins[(size_t)k]));
+          const int hs32 = (int)(round32(nbm + kMPad) / 32);
+          const size_t avail = (size_t)budget - cells_hist_offset(d.n_cells + 1, cw);
+          const int wact = (int)std::min<size_t>((size_t)cw, avail / ((size_t)NA * hs32 * 32 * 4));
+          wi.pad0 = hs32 | (std::max(wact, 1) << 16);
+        }
+        items.push_back(wi);
+        const int mid = b + wi.f_count / 2;
+        const double nbm = std::ceil(p.noverlap / h.qmins[(size_t)mid]);
+        const double per_f = meth == kMethodCells ? h.baseline * h.freqs[(size_t)mid] * nbm + 3.0 * nbm
+                                                  : (double)d.n_pts + 3.0 * nbm;
+        cost.push_back((double)wi.f_count * per_f);
+      }
+    }
+    std::vector<int32_t> order(items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int32_t)i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return cost[(size_t)a] > cost[(size_t)b]; });
+    for (size_t i = 0; i < order.size(); ++i) outv->push_back(items[(size_t)order[i]]);
+    return (int32_t)order.size();
+  };
+  std::vector<WorkItem> sorted;
+  pl->n_items = make_items(kMethodPoints, warps, pl->blocks, &sorted);
+  pl->c_items = make_items(kMethodCells, cw, pl->c_blocks, &sorted);
 
   // device buffers
   cudaStream_t st = (cudaStream_t)stream;
@@ -288,7 +377,13 @@ int qlp_bls_plan(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offs
       (rc = dev_alloc(&pl->d_items, sorted.size())) || (rc = dev_alloc(&pl->d_tp, tp_all.size())) ||
       (rc = dev_alloc(&pl->d_y, y_all.size())) || (rc = dev_alloc(&pl->d_dy, dy_all.size())) ||
       (rc = dev_alloc(&pl->d_pts, (size_t)std::max<int64_t>(npad, 1))) ||
-      (rc = dev_alloc(&pl->d_tpd, (size_t)std::max<int64_t>(npad, 1))) || (rc = dev_alloc(&pl->d_ctl, 2))) {
+      (rc = dev_alloc(&pl->d_tpd, (size_t)std::max<int64_t>(npad, 1))) ||
+      (rc = dev_alloc(&pl->d_cell_stars, std::max<size_t>(cell_stars.size(), 1))) ||
+      (rc = dev_alloc(&pl->d_cpre, (size_t)std::max<int64_t>(ncpre, 1))) ||
+      (rc = dev_alloc(&pl->d_dt, (size_t)std::max<int64_t>(ncell, 1))) ||
+      (rc = dev_alloc(&pl->d_loc, (size_t)std::max<int64_t>(ncell, 1))) ||
+      (rc = dev_alloc(&pl->d_gidx, (size_t)std::max<int64_t>(ncell, 1))) ||
+      (rc = dev_alloc(&pl->d_base, (size_t)std::max<int64_t>(nbase, 1))) || (rc = dev_alloc(&pl->d_ctl, 4))) {
     free_plan(pl);
     return rc;
   }
@@ -296,10 +391,11 @@ int qlp_bls_plan(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offs
   if (n_stars > 0) e = cudaMemcpyAsync(pl->d_stars, stars.data(), sizeof(StarDev) * (size_t)n_stars, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && nf > 0) e = cudaMemcpyAsync(pl->d_fq, fq.data(), sizeof(double2) * (size_t)nf, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !sorted.empty()) e = cudaMemcpyAsync(pl->d_items, sorted.data(), sizeof(WorkItem) * sorted.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !cell_stars.empty()) e = cudaMemcpyAsync(pl->d_cell_stars, cell_stars.data(), sizeof(int32_t) * cell_stars.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(pl->d_tp, tp_all.data(), sizeof(double) * (size_t)npt, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(pl->d_y, y_all.data(), sizeof(double) * (size_t)npt, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(pl->d_dy, dy_all.data(), sizeof(double) * (size_t)npt, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_ctl, 0, 2 * sizeof(int32_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_ctl, 0, 4 * sizeof(int32_t), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // host staging vectors die at return
   if (e != cudaSuccess) {
     free_plan(pl);
@@ -327,40 +423,81 @@ int qlp_bls_search(qlp_bls_plan_t* pl, void* stream, float* sr, uint8_t* qidx, u
   if (pl->f_off.back() > 0 && !sr) return QLP_ERR_ARG;
   if (pl->n_stars == 0 || pl->f_off.back() == 0) return QLP_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  PrepArgs pa{};
-  pa.stars = pl->d_stars;
-  pa.tp = pl->d_tp;
-  pa.y = pl->d_y;
-  pa.dy = pl->d_dy;
-  pa.pts = pl->d_pts;
-  pa.tpd = pl->d_tpd;
-  pa.tile_pts = pl->tile_pts;
-  pa.n_stars = pl->n_stars;
-  int e = launch_prep(pa, stream);
-  if (e) return cuda_fail((cudaError_t)e, "prep launch");
-  QLP_CK(cudaMemsetAsync(pl->d_ctl, 0, sizeof(int32_t), st));
-  BlsArgs a{};
-  a.stars = pl->d_stars;
-  a.fq = pl->d_fq;
-  a.items = pl->d_items;
-  a.n_items = pl->n_items;
-  a.nq = pl->nq;
-  a.pts = pl->d_pts;
-  a.tpd = pl->d_tpd;
-  a.cursor = pl->d_ctl;
-  a.err = pl->d_ctl + 1;
-  a.sr = sr;
-  a.qidx = qidx;
-  a.kbin = phase_bin;
-  a.sbest = s_best;
-  a.rbest = r_best;
-  a.noverlap = pl->p.noverlap;
-  for (int j = 0; j < kMaxQ; ++j) a.E[j] = pl->E[j];
-  a.tile_pts = pl->tile_pts;
-  a.hist_stride = pl->hist_stride;
-  a.tile_off = pl->tile_off;
-  e = launch_bls(a, pl->p.phase_mode, pl->p.sum_mode, pl->warps, pl->blocks, pl->smem, stream);
-  if (e) return cuda_fail((cudaError_t)e, "search launch");
+  QLP_CK(cudaMemsetAsync(pl->d_ctl, 0, 2 * sizeof(int32_t), st));
+  int e = 0;
+  if (pl->n_items > 0) {
+    PrepArgs pa{};
+    pa.stars = pl->d_stars;
+    pa.tp = pl->d_tp;
+    pa.y = pl->d_y;
+    pa.dy = pl->d_dy;
+    pa.pts = pl->d_pts;
+    pa.tpd = pl->d_tpd;
+    pa.tile_pts = pl->tile_pts;
+    pa.n_stars = pl->n_stars;
+    e = launch_prep(pa, stream);
+    if (e) return cuda_fail((cudaError_t)e, "prep launch");
+    BlsArgs a{};
+    a.stars = pl->d_stars;
+    a.fq = pl->d_fq;
+    a.items = pl->d_items;
+    a.n_items = pl->n_items;
+    a.nq = pl->nq;
+    a.pts = pl->d_pts;
+    a.tpd = pl->d_tpd;
+    a.cursor = pl->d_ctl;
+    a.err = pl->d_ctl + 2;
+    a.sr = sr;
+    a.qidx = qidx;
+    a.kbin = phase_bin;
+    a.sbest = s_best;
+    a.rbest = r_best;
+    a.noverlap = pl->p.noverlap;
+    for (int j = 0; j < kMaxQ; ++j) a.E[j] = pl->E[j];
+    a.tile_pts = pl->tile_pts;
+    a.hist_stride = pl->hist_stride;
+    a.tile_off = pl->tile_off;
+    e = launch_bls(a, pl->p.phase_mode, pl->p.sum_mode, pl->warps, pl->blocks, pl->smem, stream);
+    if (e) return cuda_fail((cudaError_t)e, "search launch");
+  }
+  if (pl->c_items > 0) {
+    PrepCellsArgs pc{};
+    pc.stars = pl->d_stars;
+    pc.cell_stars = pl->d_cell_stars;
+    pc.n = pl->n_cell_stars;
+    pc.tp = pl->d_tp;
+    pc.y = pl->d_y;
+    pc.dy = pl->d_dy;
+    pc.cpre = pl->d_cpre;
+    pc.dt = pl->d_dt;
+    pc.loc = pl->d_loc;
+    pc.base = pl->d_base;
+    pc.gidx = pl->d_gidx;
+    e = launch_prep_cells(pc, stream);
+    if (e) return cuda_fail((cudaError_t)e, "cell prep launch");
+    CellArgs c{};
+    c.stars = pl->d_stars;
+    c.fq = pl->d_fq;
+    c.items = pl->d_items + pl->n_items;
+    c.n_items = pl->c_items;
+    c.nq = pl->nq;
+    c.tp = pl->d_tp;
+    c.dt = pl->d_dt;
+    c.loc = pl->d_loc;
+    c.base = pl->d_base;
+    c.gidx = pl->d_gidx;
+    c.cursor = pl->d_ctl + 1;
+    c.err = pl->d_ctl + 2;
+    c.sr = sr;
+    c.qidx = qidx;
+    c.kbin = phase_bin;
+    c.sbest = s_best;
+    c.rbest = r_best;
+    c.noverlap = pl->p.noverlap;
+    for (int j = 0; j < kMaxQ; ++j) c.E[j] = pl->E[j];
+    e = launch_cells(c, pl->p.sum_mode, pl->c_warps, pl->c_blocks, pl->c_smem, stream);
+    if (e) return cuda_fail((cudaError_t)e, "cell search launch");
+  }
   return QLP_OK;
 }
 
@@ -381,7 +518,7 @@ int qlp_bls_snr(qlp_bls_plan_t* pl, void* stream, const float* sr, const uint8_t
   a.rbest = r_best;
   a.snr = snr;
   a.best = best;
-  a.err = pl->d_ctl + 1;
+  a.err = pl->d_ctl + 2;
   a.noverlap = pl->p.noverlap;
   for (int j = 0; j < kMaxQ; ++j) a.E[j] = pl->E[j];
   a.nq = pl->nq;
@@ -397,9 +534,9 @@ int qlp_bls_device_status(qlp_bls_plan_t* pl, void* stream, int32_t* flags) {
   cudaStream_t st = (cudaStream_t)stream;
   QLP_CK(cudaStreamSynchronize(st));
   int32_t v = 0;
-  QLP_CK(cudaMemcpy(&v, pl->d_ctl + 1, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  QLP_CK(cudaMemcpy(&v, pl->d_ctl + 2, sizeof(int32_t), cudaMemcpyDeviceToHost));
   *flags = v;
-  QLP_CK(cudaMemset(pl->d_ctl + 1, 0, sizeof(int32_t)));
+  QLP_CK(cudaMemset(pl->d_ctl + 2, 0, sizeof(int32_t)));
   return v ? QLP_ERR_DEVICE : QLP_OK;
 }
 

@@ -27,6 +27,7 @@
 
 #include <cstdint>
 
+#include "bls_device.cuh"
 #include "qlp_internal.h"
 
 namespace qlp {
@@ -50,7 +51,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepArgs a) {
   const int s = blockIdx.x;
   const StarDev st = a.stars[s];
   const int n = st.n_pts;
-  if (n <= 0) return;
+  if (n <= 0 || st.method != kMethodPoints) return;
   const double* tp = a.tp + st.pt_off;
   const double* y = a.y + st.pt_off;
   const double* dy = a.dy + st.pt_off;
@@ -92,101 +93,6 @@ int launch_prep(const PrepArgs& a, void* stream) {
 }
 
 // ------------------------------------------------------------------ K2 search
-
-// FP64 fold exactly as the plain definition: x = t' f, b = min(nb-1, floor(frac(x) nb)).
-__device__ __forceinline__ int fold_fp64(double t, double f, int nb, int* cyc) {
-  const double x = __dmul_rn(t, f);
-  const double c = floor(x);
-  const double ph = __dsub_rn(x, c);
-  int b = (int)floor(__dmul_rn(ph, (double)nb));
-  if (b > nb - 1) b = nb - 1;
-  *cyc = (int)c;
-  return b;
-}
-
-// Out-of-line so that the rare re-fold is a real branch, never predicated into the loop.
-__device__ __noinline__ int exact_global_bin(const double* tptr, double f, int nb) {
-  int c;
-  const int b = fold_fp64(*tptr, f, nb, &c);
-  return c * nb + b;
-}
-
-constexpr int kU = 4;
-constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: adding it rounds |x| < 2^22 to an integer
-constexpr int kMagicBits = 0x4B400000;
-
-// Shared-memory float reductions issued under a predicate (no branch): a lane
-// whose run did not end this step takes no part.
-__device__ __forceinline__ void red_add_if(float* addr, float v, bool p) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(addr);
-  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q red.shared.add.f32 [%0], %1;\n\t}"
-               :: "r"(a), "f"(v), "r"((int)p) : "memory");
-}
-__device__ __forceinline__ float atom_add_if(float* addr, float v, bool p) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(addr);
-  float old = 0.f;
-  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\t@q atom.shared.add.f32 %0, [%1], %2;\n\t}"
-               : "+f"(old) : "r"(a), "f"(v), "r"((int)p) : "memory");
-  return old;
-}
-
-// Exact rounding error of a + b (TwoSum, Knuth).
-__device__ __forceinline__ float two_sum_err(float a, float b, float s) {
-  const float bb = __fsub_rn(s, a);
-  return __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-template <int SUM>
-struct RunAcc {
-  float aw, ay, cw, cy;
-  __device__ __forceinline__ void reset() { aw = ay = cw = cy = 0.f; }
-  // start a new run with (w, wd) when `fresh`, else add them to the current run
-  __device__ __forceinline__ void add(bool fresh, float w, float wd) {
-    const float bw = fresh ? 0.f : aw, by = fresh ? 0.f : ay;
-    const float sw = __fadd_rn(bw, w), sy = __fadd_rn(by, wd);
-    if (SUM == QLP_SUM_COMP) {
-      cw = __fadd_rn(fresh ? 0.f : cw, two_sum_err(bw, w, sw));
-      cy = __fadd_rn(fresh ? 0.f : cy, two_sum_err(by, wd, sy));
-    }
-    aw = sw;
-    ay = sy;
-  }
-};
-
-// Add a finished run to bin b of the warp's histogram (when p); in COMP mode the
-// rounding error of each shared add, recovered from the value it replaced, goes to
-// the compensation arrays together with the run's own error terms.
-template <int SUM>
-__device__ __forceinline__ void flush_run(float* hw, float* hy, float* hwc, float* hyc, int b,
-                                          const RunAcc<SUM>& acc, bool p) {
-  if (SUM == QLP_SUM_COMP) {
-    const float ow = atom_add_if(hw + b, acc.aw, p);
-    const float oy = atom_add_if(hy + b, acc.ay, p);
-    const float ew = two_sum_err(ow, acc.aw, __fadd_rn(ow, acc.aw));
-    const float ey = two_sum_err(oy, acc.ay, __fadd_rn(oy, acc.ay));
-    red_add_if(hwc + b, __fadd_rn(ew, acc.cw), p);
-    red_add_if(hyc + b, __fadd_rn(ey, acc.cy), p);
-  } else {
-    red_add_if(hw + b, acc.aw, p);
-    red_add_if(hy + b, acc.ay, p);
-  }
-}
-
-struct BoxBest {
-  float s2, d, s, r;
-  int j, k;
-};
-
-// Strict "a beats b": larger s^2/d, then lower j, then lower k; s2 < 0 = no box.
-__device__ __forceinline__ bool beats(float s2a, float da, int ja, int ka, float s2b, float db,
-                                      int jb, int kb) {
-  if (s2a < 0.f) return false;
-  if (s2b < 0.f) return true;
-  const float lhs = s2a * db, rhs = s2b * da;
-  if (lhs != rhs) return lhs > rhs;
-  if (ja != jb) return ja < jb;
-  return ka < kb;
-}
 
 template <int PHASE, int SUM, int NW>
 __global__ void __launch_bounds__(NW * 32) bls_kernel(const BlsArgs a) {
@@ -378,69 +284,8 @@ __global__ void __launch_bounds__(NW * 32) bls_kernel(const BlsArgs a) {
       if (!active) continue;
       __syncwarp();
 
-      // wrap padding: window k .. k+m-1 reads bins k+o mod nb
-      for (int i = lane; i < kMPad; i += 32) {
-        const int src = i % nb;
-        hw[nb + i] = hw[src];
-        hy[nb + i] = hy[src];
-        if (SUM == QLP_SUM_COMP) { hwc[nb + i] = hwc[src]; hyc[nb + i] = hyc[src]; }
-      }
-      __syncwarp();
-
-      // widths present (bit o: some duration covers o+1 bins) and, per width, the
-      // lowest duration index j with it (4 bits each)
-      uint32_t wmask = 0u;
-      unsigned long long jlow = 0ull;
-      for (int j = nq - 1; j >= 0; --j) {
-        const int o = mtab[j] - 1;
-        wmask |= 1u << o;
-        jlow = (jlow & ~(0xfull << (4 * o))) | ((unsigned long long)j << (4 * o));
-      }
-      const int mmax = mtab[nq - 1];
-      float bs2 = -1.f, bd = 1.f, bsv = 0.f, brv = 0.f;
-      int bj = 255, bk = -1;
-      for (int k = lane; k < nb; k += 32) {
-        float rw = 0.f, ry = 0.f, rwc = 0.f, ryc = 0.f;
-        for (int o = 0; o < mmax; ++o) {
-          rw = __fadd_rn(rw, hw[k + o]);
-          ry = __fadd_rn(ry, hy[k + o]);
-          if (SUM == QLP_SUM_COMP) {
-            rwc = __fadd_rn(rwc, hwc[k + o]);
-            ryc = __fadd_rn(ryc, hyc[k + o]);
-          }
-          if ((wmask >> o) & 1u) {
-            const int j = (int)((jlow >> (4 * o)) & 0xfull);
-            const float r = (SUM == QLP_SUM_COMP) ? __fadd_rn(rw, rwc) : rw;
-            const float sv = (SUM == QLP_SUM_COMP) ? __fadd_rn(ry, ryc) : ry;
-            if (r > 0.f && r < 1.f) {
-              const float d = __fmul_rn(r, __fsub_rn(1.f, r));
-              const float s2 = __fmul_rn(sv, sv);
-              if (beats(s2, d, j, k, bs2, bd, bj, bk)) {
-                bs2 = s2; bd = d; bsv = sv; brv = r; bj = j; bk = k;
-              }
-            }
-          }
-        }
-      }
-      for (int off = 16; off > 0; off >>= 1) {
-        const float o_s2 = __shfl_xor_sync(0xffffffffu, bs2, off);
-        const float o_d = __shfl_xor_sync(0xffffffffu, bd, off);
-        const float o_s = __shfl_xor_sync(0xffffffffu, bsv, off);
-        const float o_r = __shfl_xor_sync(0xffffffffu, brv, off);
-        const int o_j = __shfl_xor_sync(0xffffffffu, bj, off);
-        const int o_k = __shfl_xor_sync(0xffffffffu, bk, off);
-        if (beats(o_s2, o_d, o_j, o_k, bs2, bd, bj, bk)) {
-          bs2 = o_s2; bd = o_d; bsv = o_s; brv = o_r; bj = o_j; bk = o_k;
-        }
-      }
-      if (lane == 0) {
-        const bool none = bs2 < 0.f;
-        a.sr[fidx] = none ? 0.f : __fdiv_rn(bs2, bd);
-        if (a.qidx) a.qidx[fidx] = none ? (uint8_t)255 : (uint8_t)bj;
-        if (a.kbin) a.kbin[fidx] = none ? 0xffffffffu : (uint32_t)bk;
-        if (a.sbest) a.sbest[fidx] = none ? 0.f : bsv;
-        if (a.rbest) a.rbest[fidx] = none ? 0.f : brv;
-      }
+      sweep_store<SUM>(hw, hy, hwc, hyc, mtab, nq, nb, lane, fidx, a.sr, a.qidx, a.kbin, a.sbest,
+                       a.rbest);
     }
   }
   if (!done && threadIdx.x == 0) atomicOr(a.err, kErrQueueBound);

@@ -1,0 +1,400 @@
+// Cell path of the BLS search (sm_103a): bins from prefix sums at bin edges.
+//
+// For a trial frequency f with nbins bins, let F = f nbins; the phase-bin edges
+// fall at times tau_G = G / F (G = 0, 1, ...: the global bin index of the fold
+// x = t' f, b = floor(frac(x) nbins) in Sec. 2.1's BLS). A point belongs to global
+// bin g when tau_g <= t' < tau_{g+1}, so with the prefix sums
+// C(tau) = (sum of w, sum of w d over points with t' < tau) every histogram bin is
+//     H[b] = sum over G = b mod nbins of C(tau_{G+1}) - C(tau_G),
+// one term per (cycle, bin) instead of one per point. For light curves sampled
+// much faster than a bin lasts (TESS 200-s cadence: 3-30 points per bin and
+// cycle) this is 3-10x less work than folding every point, needs no atomics and
+// is deterministic.
+//
+// C(tau) in O(1): the star's time axis is cut into cells of width h just below
+// the smallest point spacing, so each cell holds at most one point. Per cell the
+// table keeps C at the cell start (a per-32-cell double-float base plus an FP32
+// local part) and the offset dt of its point, so
+//     C(tau) = C(cell u start) + [dt_u < tau - u h] (w, w d) = C(start of cell u + [..]).
+// Near ties (|dt_u - (tau - u h)| within a guard band) are decided exactly by the
+// FP64 fold of that point: "point before edge G" is "its FP64 global bin < G".
+//
+// K1c prep_cells_kernel (1 CTA per cell-path star): weights as prep_kernel, FP64
+// prefix sums, the per-cell tables. K2c cells_kernel: persistent, work queue of
+// (star, frequency chunk), the star's tables staged in shared memory, one warp
+// per frequency, lanes on 32 consecutive edges (31 bins) per step; then the same
+// box sweep as the per-point kernel.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "bls_device.cuh"
+#include "qlp_internal.h"
+
+namespace qlp {
+
+// Cell of a point: u = floor(t'/h) adjusted so that t' - u h (in FP64) is in [0, h).
+__device__ __forceinline__ int cell_of(double t, double h) {
+  double q = floor(__ddiv_rn(t, h));
+  const double r = __dsub_rn(t, __dmul_rn(q, h));
+  if (r < 0.0) q -= 1.0;
+  else if (r >= h) q += 1.0;
+  return (int)q;
+}
+
+// ------------------------------------------------------------------ K1c
+
+__global__ void __launch_bounds__(256) prep_cells_kernel(const PrepCellsArgs a) {
+  __shared__ double red[32];
+  __shared__ double scan_w[256], scan_y[256];
+  const int s = a.cell_stars[blockIdx.x];
+  const StarDev st = a.stars[s];
+  const int n = st.n_pts;
+  if (n <= 0) return;
+  const double* tp = a.tp + st.pt_off;
+  const double* y = a.y + st.pt_off;
+  const double* dy = a.dy + st.pt_off;
+  const int tid = threadIdx.x;
+
+  double acc = 0.0;
+  for (int i = tid; i < n; i += blockDim.x) acc += 1.0 / (dy[i] * dy[i]);
+  // block sum (FP64)
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((tid & 31) == 0) red[tid >> 5] = acc;
+  __syncthreads();
+  double wsum = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) wsum += red[i];
+  __syncthreads();
+  acc = 0.0;
+  for (int i = tid; i < n; i += blockDim.x) acc += (1.0 / (dy[i] * dy[i])) / wsum * y[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((tid & 31) == 0) red[tid >> 5] = acc;
+  __syncthreads();
+  double ybar = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) ybar += red[i];
+
+  // prefix sums before each point: contiguous segment per thread, scan of totals
+  const int L = (n + blockDim.x - 1) / blockDim.x;
+  const int i0 = min(n, tid * L), i1 = min(n, i0 + L);
+  double sw = 0.0, sy = 0.0;
+  for (int i = i0; i < i1; ++i) {
+    const double ww = (1.0 / (dy[i] * dy[i])) / wsum;
+    sw += ww;
+    sy += ww * (y[i] - ybar);
+  }
+  scan_w[tid] = sw;
+  scan_y[tid] = sy;
+  __syncthreads();
+  if (tid == 0) {  // exclusive scan of 256 segment totals (FP64, sequential)
+    double rw = 0.0, ry = 0.0;
+    for (int k = 0; k < (int)blockDim.x; ++k) {
+      const double tw = scan_w[k], ty = scan_y[k];
+      scan_w[k] = rw;
+      scan_y[k] = ry;
+      rw += tw;
+      ry += ty;
+    }
+    a.cpre[st.cpre_off + n] = make_double2(rw, ry);
+  }
+  __syncthreads();
+  double cw = scan_w[tid], cy = scan_y[tid];
+  for (int i = i0; i < i1; ++i) {
+    a.cpre[st.cpre_off + i] = make_double2(cw, cy);
+    const double ww = (1.0 / (dy[i] * dy[i])) / wsum;
+    cw += ww;
+    cy += ww * (y[i] - ybar);
+  }
+
+  // first point at or after each cell start: point i fills cells (cell(i-1), cell(i)]
+  const int nc = st.n_cells;
+  const double h = st.h;
+  int32_t* first = a.gidx + st.cell_off;
+  for (int i = tid; i <= n; i += blockDim.x) {
+    const int up = (i == 0) ? -1 : cell_of(tp[i - 1], h);
+    const int ui = (i == n) ? nc : cell_of(tp[i], h);
+    for (int c = up + 1; c <= ui && c <= nc; ++c) first[c] = i;
+  }
+  __syncthreads();
+  for (int u = tid; u <= nc; u += blockDim.x) {
+    const int f = first[u];
+    const bool in_cell = (u < nc) && (f < n) && (cell_of(tp[f], h) == u);
+    a.dt[st.cell_off + u] = in_cell ? __double2float_rn(__dsub_rn(tp[f], __dmul_rn((double)u, h)))
+                                    : __int_as_float(0x7f800000);  // +inf
+    const double2 c = a.cpre[st.cpre_off + f];
+    const double2 cb = a.cpre[st.cpre_off + first[u & ~31]];
+    a.loc[st.cell_off + u] = make_float2(__double2float_rn(c.x - cb.x), __double2float_rn(c.y - cb.y));
+    if ((u & 31) == 0) {
+      const float wh = __double2float_rn(cb.x), yh = __double2float_rn(cb.y);
+      a.base[st.base_off + (u >> 5)] =
+          make_float4(wh, __double2float_rn(cb.x - (double)wh), yh, __double2float_rn(cb.y - (double)yh));
+    }
+  }
+}
+
+int launch_prep_cells(const PrepCellsArgs& a, void* stream) {
+  if (a.n <= 0) return 0;
+  prep_cells_kernel<<<a.n, 256, 0, (cudaStream_t)stream>>>(a);
+  return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ K2c
+
+// Exact "point of cell u lies before edge G" from the FP64 fold of that point.
+static __device__ __noinline__ int exact_before(const double* tp, int i, double f, int nb, int G) {
+  int c;
+  const int b = fold_fp64(tp[i], f, nb, &c);
+  return (c * nb + b) < G ? 1 : 0;
+}
+
+// Shared-memory layout of one star's cell table followed by the per-warp
+// duration tables and histograms (the histogram stride is chosen per work item).
+struct CellSmem {
+  uint32_t loc, base, mtab, hist;
+};
+__host__ __device__ __forceinline__ CellSmem cell_smem_layout(int ncs, int nw) {
+  CellSmem l;
+  l.loc = ((uint32_t)ncs * 4u + 15u) & ~15u;
+  l.base = l.loc + (((uint32_t)ncs * 8u + 15u) & ~15u);
+  l.mtab = l.base + ((((uint32_t)ncs + 31u) / 32u * 16u + 15u) & ~15u);
+  l.hist = l.mtab + (uint32_t)nw * kMaxQ * 4u;
+  return l;
+}
+
+// C(tau_G) for one edge: prefix sums (w, w d) of the points before tau_G = G D,
+// as (block base hi, lo; local part) for w and for w d.
+struct EdgeC {
+  float bwh, bwl, byh, byl, lw, ly;
+};
+
+__device__ __forceinline__ EdgeC edge_prefix(int G, float Dh, float Dl, float hh, float hl,
+                                             float inv_h, int nc, float band, const float* s_dt,
+                                             const float2* s_loc, const float4* s_base,
+                                             const double* tp, const int32_t* gidx, double f,
+                                             int nb) {
+  const float Gf = (float)G;
+  const float th = __fmul_rn(Gf, Dh);  // tau = G D as (th, te)
+  float te = __fmaf_rn(Gf, Dh, -th);
+  te = __fmaf_rn(Gf, Dl, te);
+  int u = (int)__fmul_rn(th, inv_h);
+  u = min(max(u, 0), nc);
+  const float uf = (float)u;  // dl = tau - u h
+  const float p = __fmul_rn(uf, hh);
+  float pe = __fmaf_rn(uf, hh, -p);
+  pe = __fmaf_rn(uf, hl, pe);
+  float dl = __fadd_rn(__fsub_rn(th, p), __fsub_rn(te, pe));
+  const bool lo_ = dl < 0.f && u > 0;
+  const bool hi_ = dl >= hh && u < nc;
+  u = lo_ ? u - 1 : (hi_ ? u + 1 : u);
+  dl = lo_ ? __fadd_rn(dl, hh) : (hi_ ? __fsub_rn(dl, hh) : dl);
+  const float diff = __fsub_rn(s_dt[u], dl);
+  int sel = diff < 0.f ? 1 : 0;
+  const bool need = fabsf(diff) <= band;
+  if (__any_sync(0xffffffffu, need)) {  // rare: decide by the exact FP64 fold
+    if (need) sel = exact_before(tp, gidx[u], f, nb, G);
+  }
+  const int v = min(u + sel, nc);
+  const float2 lc = s_loc[v];
+  const float4 bs = s_base[v >> 5];
+  EdgeC c;
+  c.bwh = bs.x; c.bwl = bs.y; c.byh = bs.z; c.byl = bs.w; c.lw = lc.x; c.ly = lc.y;
+  return c;
+}
+
+// Piece between this lane's edge and the next lane's: (w, w d) of the points in
+// one (cycle, bin).
+__device__ __forceinline__ float2 edge_piece(const EdgeC& c) {
+  const float nbwh = __shfl_down_sync(0xffffffffu, c.bwh, 1);
+  const float nbwl = __shfl_down_sync(0xffffffffu, c.bwl, 1);
+  const float nbyh = __shfl_down_sync(0xffffffffu, c.byh, 1);
+  const float nbyl = __shfl_down_sync(0xffffffffu, c.byl, 1);
+  const float nlw = __shfl_down_sync(0xffffffffu, c.lw, 1);
+  const float nly = __shfl_down_sync(0xffffffffu, c.ly, 1);
+  const float pw = __fadd_rn(__fadd_rn(__fsub_rn(nbwh, c.bwh), __fsub_rn(nbwl, c.bwl)), __fsub_rn(nlw, c.lw));
+  const float py = __fadd_rn(__fadd_rn(__fsub_rn(nbyh, c.byh), __fsub_rn(nbyl, c.byl)), __fsub_rn(nly, c.ly));
+  return make_float2(pw, py);
+}
+
+template <int SUM>
+__device__ __forceinline__ void add_piece(float* hw, float* hy, float* hwc, float* hyc, int b,
+                                          float2 pc, bool own, bool p) {
+  if (!p) return;
+  if (own) {  // lanes 0..30 hold distinct bins
+    if (SUM == QLP_SUM_COMP) {
+      float o = hw[b], sN = __fadd_rn(o, pc.x);
+      hwc[b] = __fadd_rn(hwc[b], two_sum_err(o, pc.x, sN));
+      hw[b] = sN;
+      o = hy[b];
+      sN = __fadd_rn(o, pc.y);
+      hyc[b] = __fadd_rn(hyc[b], two_sum_err(o, pc.y, sN));
+      hy[b] = sN;
+    } else {
+      hw[b] = __fadd_rn(hw[b], pc.x);
+      hy[b] = __fadd_rn(hy[b], pc.y);
+    }
+  } else {
+    atomicAdd(hw + b, pc.x);
+    atomicAdd(hy + b, pc.y);
+  }
+}
+
+template <int SUM, int NW>
+__global__ void __launch_bounds__(NW * 32) cells_kernel(const CellArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NA = (SUM == QLP_SUM_COMP) ? 4 : 2;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int nq = a.nq;
+  const float* s_dt = reinterpret_cast<const float*>(smem);
+
+  __shared__ int s_item;
+  __shared__ int s_star;
+  if (threadIdx.x == 0) s_star = -1;
+
+  bool done = false;
+  for (int iter = 0; iter <= a.n_items; ++iter) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(a.cursor, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= a.n_items) { done = true; break; }
+    const WorkItem wi = a.items[it];
+    const StarDev st = a.stars[wi.star];
+    const int nc = st.n_cells;  // sentinel index
+    const int ncs = nc + 1;
+    const CellSmem L = cell_smem_layout(ncs, NW);
+    const float2* s_loc = reinterpret_cast<const float2*>(smem + L.loc);
+    const float4* s_base = reinterpret_cast<const float4*>(smem + L.base);
+    if (s_star != wi.star) {  // block-uniform
+      __syncthreads();
+      const int nbk = (ncs + 31) >> 5;
+      float* d_dt = reinterpret_cast<float*>(smem);
+      float2* d_loc = reinterpret_cast<float2*>(smem + L.loc);
+      float4* d_base = reinterpret_cast<float4*>(smem + L.base);
+      for (int i = threadIdx.x; i < ncs; i += NW * 32) {
+        d_dt[i] = a.dt[st.cell_off + i];
+        d_loc[i] = a.loc[st.cell_off + i];
+      }
+      for (int i = threadIdx.x; i < nbk; i += NW * 32) d_base[i] = a.base[st.base_off + i];
+      if (threadIdx.x == 0) s_star = wi.star;
+      __syncthreads();
+    }
+    // per item: histogram stride (multiple of 32 floats) and the warps that fit
+    const int HS = (wi.pad0 & 0xffff) * 32;
+    const int wact = wi.pad0 >> 16;
+    if (warp >= wact) continue;  // no block barrier until the next item
+    int* mtab = reinterpret_cast<int*>(smem + L.mtab) + warp * kMaxQ;
+    float* hw = reinterpret_cast<float*>(smem + L.hist) + (size_t)warp * NA * HS;
+    float* hy = hw + HS;
+    float* hwc = hw + 2 * HS;
+    float* hyc = hw + 3 * HS;
+    const double* tp = a.tp + st.pt_off;
+    const int32_t* gidx = a.gidx + st.cell_off;
+    const double h = st.h;
+    const float hh = __double2float_rn(h);
+    const float hl = __double2float_rn(h - (double)hh);
+    const float inv_h = __double2float_rn(1.0 / h);
+
+    for (int fl = warp; fl < wi.f_count; fl += wact) {
+      const int64_t fidx = st.f_off + wi.f_begin + fl;
+      const double2 fq = a.fq[fidx];
+      const double f = fq.x;
+      const int nb = (int)ceil(__ddiv_rn(a.noverlap, fq.y));
+      if (nb + kMPad > HS || nb < 1) {
+        if (lane == 0) {
+          atomicOr(a.err, kErrNbins);
+          a.sr[fidx] = 0.f;
+          if (a.qidx) a.qidx[fidx] = 255;
+          if (a.kbin) a.kbin[fidx] = 0xffffffffu;
+          if (a.sbest) a.sbest[fidx] = 0.f;
+          if (a.rbest) a.rbest[fidx] = 0.f;
+        }
+        continue;
+      }
+      if (lane < nq)
+        mtab[lane] = max(1, (int)floor(__dadd_rn(__dmul_rn(__dmul_rn(fq.y, a.E[lane]), (double)nb), 0.5)));
+      for (int i = lane; i < nb + kMPad; i += 32) {
+        hw[i] = 0.f;
+        hy[i] = 0.f;
+        if (SUM == QLP_SUM_COMP) { hwc[i] = 0.f; hyc[i] = 0.f; }
+      }
+      const double F = __dmul_rn(f, (double)nb);
+      const double D = __ddiv_rn(1.0, F);  // bin duration (days)
+      const float Dh = __double2float_rn(D);
+      const float Dl = __double2float_rn(D - (double)Dh);
+      const double yT = __dmul_rn(st.baseline, F);
+      const int g_end = (int)floor(yT) + 2;  // edges 0 .. g_end; tau_{g_end} > T
+      // guard band in days: FP64 fold and double-float edge errors (in bins) / F,
+      // plus the FP32 rounding of dt
+      const float band = __double2float_rn((9.5367431640625e-07 + 9.094947017729282e-13 * yT) * D +
+                                           2.384185791015625e-07 * h);
+      __syncwarp();
+
+      const bool own = nb >= 31;  // the 31 pieces of one chunk fall in distinct bins
+      const int step = 31 % nb;
+      int b = lane % nb;  // bin of this lane's piece in the first chunk
+      for (int g0 = 0; g0 < g_end; g0 += 62) {
+        // two chunks of 31 pieces in flight: edges g0 .. g0+31 and g0+31 .. g0+62
+        const EdgeC c0 = edge_prefix(g0 + lane, Dh, Dl, hh, hl, inv_h, nc, band, s_dt, s_loc, s_base,
+                                     tp, gidx, f, nb);
+        const EdgeC c1 = edge_prefix(g0 + 31 + lane, Dh, Dl, hh, hl, inv_h, nc, band, s_dt, s_loc,
+                                     s_base, tp, gidx, f, nb);
+        const float2 p0 = edge_piece(c0);
+        const float2 p1 = edge_piece(c1);
+        int b1 = b + step;
+        if (b1 >= nb) b1 -= nb;
+        add_piece<SUM>(hw, hy, hwc, hyc, b, p0, own, lane < 31 && g0 + lane < g_end);
+        add_piece<SUM>(hw, hy, hwc, hyc, b1, p1, own, lane < 31 && g0 + 31 + lane < g_end);
+        b = b1 + step;
+        if (b >= nb) b -= nb;
+      }
+      __syncwarp();
+      sweep_store<SUM>(hw, hy, hwc, hyc, mtab, nq, nb, lane, fidx, a.sr, a.qidx, a.kbin, a.sbest,
+                       a.rbest);
+    }
+  }
+  if (!done && threadIdx.x == 0) atomicOr(a.err, kErrQueueBound);
+}
+
+template <int SUM, int NW>
+static int launch_cells_t(const CellArgs& a, int blocks, size_t smem, void* stream) {
+  auto kern = cells_kernel<SUM, NW>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  kern<<<blocks, NW * 32, smem, (cudaStream_t)stream>>>(a);
+  return (int)cudaGetLastError();
+}
+
+template <int SUM, int NW>
+static int occ_cells_t(size_t smem) {
+  auto kern = cells_kernel<SUM, NW>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NW * 32, smem) != cudaSuccess) return 0;
+  return nb;
+}
+
+#define QLP_CELLS_DISPATCH(FN, ...)                                \
+  switch (sum_mode * 10 + (warps == 4 ? 0 : warps == 8 ? 1 : 2)) { \
+    case 0: return FN<0, 4>(__VA_ARGS__);                          \
+    case 1: return FN<0, 8>(__VA_ARGS__);                          \
+    case 2: return FN<0, 16>(__VA_ARGS__);                         \
+    case 10: return FN<1, 4>(__VA_ARGS__);                         \
+    case 11: return FN<1, 8>(__VA_ARGS__);                         \
+    case 12: return FN<1, 16>(__VA_ARGS__);                        \
+    default: break;                                                \
+  }
+
+int launch_cells(const CellArgs& a, int sum_mode, int warps, int blocks, size_t smem, void* stream) {
+  QLP_CELLS_DISPATCH(launch_cells_t, a, blocks, smem, stream)
+  return (int)cudaErrorInvalidValue;
+}
+
+uint32_t cells_hist_offset(int ncs, int nw) { return cell_smem_layout(ncs, nw).hist; }
+
+int cells_blocks_per_sm(int sum_mode, int warps, size_t smem) {
+  QLP_CELLS_DISPATCH(occ_cells_t, smem)
+  return 0;
+}
+
+}  // namespace qlp

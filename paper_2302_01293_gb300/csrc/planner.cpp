@@ -66,6 +66,15 @@ double pmax_of(const double* tp, int64_t n, const qlp_bls_params& p) {
   return longest;
 }
 
+// Cell of a point: u = floor(t'/h), adjusted so that t' - u h (FP64) lies in [0, h).
+int64_t cell_of(double tp, double h) {
+  double q = std::floor(tp / h);
+  const double r = tp - q * h;
+  if (r < 0.0) q -= 1.0;
+  else if (r >= h) q += 1.0;
+  return (int64_t)q;
+}
+
 int sturges_of(int64_t n) { return (int)std::floor(1.0 + 3.322 * std::log10((double)n) + 0.5); }
 
 void plan_one(const qlp_bls_params& p, const double* t, const double* y, const double* dy, int64_t n,
@@ -118,6 +127,29 @@ void plan_one(const qlp_bls_params& p, const double* t, const double* y, const d
     return;
   }
   s.sturges_nb = sturges_of((int64_t)s.freqs.size());
+
+  // cell path: smallest spacing, cells just narrower, one point per cell
+  double min_gap = INFINITY;
+  for (int64_t i = 1; i < m; ++i) min_gap = std::min(min_gap, s.tp[i] - s.tp[i - 1]);
+  if (min_gap > 0.0 && std::isfinite(min_gap) && s.baseline / min_gap < 4.0e6) {
+    const double h = min_gap * 0.999;
+    bool ok = true;
+    int64_t prev = -1;
+    for (int64_t i = 0; i < m && ok; ++i) {
+      const int64_t u = cell_of(s.tp[i], h);
+      ok = u > prev;
+      prev = u;
+    }
+    if (ok) {
+      s.cells_ok = true;
+      s.cell_h = h;
+      s.n_cells = prev + 1;
+      double work = 0.0;
+      for (size_t k = 0; k < s.freqs.size(); ++k)
+        work += std::floor(s.baseline * s.freqs[k] * std::ceil(p.noverlap / s.qmins[k])) + 3.0;
+      s.cells_work = work;
+    }
+  }
 }
 
 void plan_all(const qlp_bls_params& p, int32_t n_stars, const int64_t* offsets, const double* t,

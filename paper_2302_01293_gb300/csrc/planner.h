@@ -22,7 +22,15 @@ struct StarPlanHost {
   int32_t nbins_max = 0;
   double ymax = 0.0;               // max over f of T f nbins(f)
   int32_t sturges_nb = 0;
+  // cell path: cells of width h (just below the smallest point spacing) hold at
+  // most one point each; cells_ok when that holds for the FP64 cell assignment
+  bool cells_ok = false;
+  double cell_h = 0.0;
+  int64_t n_cells = 0;
+  double cells_work = 0.0;         // sum over f of the bin edges across the baseline
 };
+
+int64_t cell_of(double tp, double h);
 
 int n_q_of(const qlp_bls_params& p);
 double q_min_of(double f, double rho_kg, const qlp_bls_params& p);

@@ -23,17 +23,29 @@ struct StarDev {
   int32_t status;      // QLP_STAR_* flags from the planner
   int32_t sturges_nb;  // S/N trend bins, round(1 + 3.322 log10 n_f)
   int32_t fp64_phase;  // 1: fold this star in FP64 whatever the phase mode
-  int32_t pad0;
+  int32_t method;      // kMethodPoints or kMethodCells
   double t_ref;        // t_min of the valid points
   double baseline;     // t_max - t_min
+  // cell path (method == kMethodCells): time axis cut into cells of width h,
+  // each holding at most one point; cells 0 .. n_cells-1 cover [0, n_cells h),
+  // cell n_cells is a sentinel past the last point
+  double h;
+  int32_t n_cells;
+  int32_t pad1;
+  int64_t cell_off;    // first entry in the per-cell arrays (n_cells + 1 entries)
+  int64_t base_off;    // first entry in the per-32-cell base array
+  int64_t cpre_off;    // first entry in the prefix-sum array (N + 1 entries)
 };
+
+constexpr int32_t kMethodPoints = 0;
+constexpr int32_t kMethodCells = 1;
 
 // (star, frequency chunk) unit of the device work queue.
 struct WorkItem {
   int32_t star;
   int32_t f_begin;     // first frequency, relative to the star
   int32_t f_count;
-  int32_t pad0;
+  int32_t pad0;        // cell path: histogram stride / 32 (low 16 bits), active warps (high 16)
 };
 
 struct BlsArgs {
@@ -57,6 +69,44 @@ struct BlsArgs {
   int32_t hist_stride;     // floats per histogram array of one warp (>= nbins_max + kMPad)
   uint32_t tile_off;       // byte offset of the point tile in dynamic shared memory
   int32_t pad0;
+};
+
+// Cell search (cells_kernels.cu): boundaries of phase bins instead of points.
+struct CellArgs {
+  const StarDev* stars;
+  const double2* fq;
+  const WorkItem* items;
+  int32_t n_items;
+  int32_t nq;
+  const double* tp;        // raw t' (CSR by pt_off), for the exact decision near ties
+  const float* dt;         // per cell: offset of its point from the cell start, +inf if empty
+  const float2* loc;       // per cell: prefix sums (w, w d) before the cell, minus the block base
+  const float4* base;      // per 32 cells: block base prefix sums as (w_hi, w_lo, y_hi, y_lo)
+  const int32_t* gidx;     // per cell: index of the first point at or after the cell start
+  int32_t* cursor;
+  int32_t* err;
+  float* sr;
+  uint8_t* qidx;
+  uint32_t* kbin;
+  float* sbest;
+  float* rbest;
+  double noverlap;
+  double E[kMaxQ];
+};
+
+struct PrepCellsArgs {
+  const StarDev* stars;
+  const int32_t* cell_stars;  // stars on the cell path
+  int32_t n;
+  int32_t pad0;
+  const double* tp;
+  const double* y;
+  const double* dy;
+  double2* cpre;              // prefix sums (sum w, sum w d) before each point, N + 1 per star
+  float* dt;
+  float2* loc;
+  float4* base;
+  int32_t* gidx;
 };
 
 struct PrepArgs {
@@ -100,6 +150,12 @@ int launch_prep(const PrepArgs& a, void* stream);
 int launch_bls(const BlsArgs& a, int phase_mode, int sum_mode, int warps, int blocks,
                size_t smem_bytes, void* stream);
 int launch_snr(const SnrArgs& a, void* stream);
+int launch_prep_cells(const PrepCellsArgs& a, void* stream);
+int launch_cells(const CellArgs& a, int sum_mode, int warps, int blocks, size_t smem, void* stream);
+// bytes of shared memory before the histograms of the cell kernel for a star with
+// ncs cells (incl. sentinel) and nw warps
+uint32_t cells_hist_offset(int ncs, int nw);
+int cells_blocks_per_sm(int sum_mode, int warps, size_t smem);
 int bls_max_smem_per_block();
 int bls_blocks_per_sm(int phase_mode, int sum_mode, int warps, size_t smem_bytes);
 

@@ -18,6 +18,7 @@ from . import build as _build
 PHASE_FP64, PHASE_DF, PHASE_FP32 = 0, 1, 2
 SUM_PLAIN, SUM_COMP = 0, 1
 MAD_RAW, MAD_RESID = 0, 1
+METHOD_AUTO, METHOD_POINTS, METHOD_CELLS = 0, 1, 2
 
 STAR_UNSORTED, STAR_TOO_FEW, STAR_EMPTY_GRID, STAR_NBINS_CAP, STAR_ZERO_MAD = 1, 2, 4, 8, 16
 
@@ -37,7 +38,7 @@ class CParams(ctypes.Structure):
                 ("sum_mode", ctypes.c_int32), ("mad_mode", ctypes.c_int32),
                 ("chunk_freqs", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("n_threads", ctypes.c_int32), ("tile_points", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("method", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 @dataclasses.dataclass
@@ -58,6 +59,7 @@ class Params:
     warps_per_block: int = 0
     n_threads: int = 0
     tile_points: int = 0
+    method: int = 0
 
     def to_c(self) -> CParams:
         c = CParams()

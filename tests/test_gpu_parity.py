@@ -43,16 +43,32 @@ def test_single_star(gpu_lib, phase, summ):
     assert abs(best["period"] / 3.7 - 1) < 0.01 and best["snr"] > 9
 
 
+@pytest.mark.parametrize("method", [qlpbls.METHOD_POINTS, qlpbls.METHOD_CELLS])
+@pytest.mark.parametrize("summ", [qlpbls.SUM_PLAIN, qlpbls.SUM_COMP])
+def test_uneven_batch_both_paths(gpu_lib, method, summ):
+    b = synth.uneven_single_sector(n_stars=5, seed=22)
+    _check_batch(b, qlpbls.Params(method=method, sum_mode=summ))
+
+
+@pytest.mark.parametrize("warps", [4, 8, 16])
+def test_cell_path_single_star_and_warps(gpu_lib, warps):
+    # 30-min cadence: the cell path is forced (the planner would fold points here)
+    b = synth.single_star()
+    _check_batch(b, qlpbls.Params(method=qlpbls.METHOD_CELLS, warps_per_block=warps,
+                                  chunk_freqs=warps * 2))
+
+
 @pytest.mark.parametrize("tile", [0, 256, 1024])
 def test_uneven_batch_tiles(gpu_lib, tile):
     b = synth.uneven_single_sector(n_stars=6, seed=12)
-    _check_batch(b, qlpbls.Params(tile_points=tile))
+    _check_batch(b, qlpbls.Params(tile_points=tile, method=qlpbls.METHOD_POINTS))
 
 
 @pytest.mark.parametrize("warps", [4, 8, 16])
 def test_warps_per_block(gpu_lib, warps):
     b = synth.uneven_single_sector(n_stars=3, seed=13)
-    _check_batch(b, qlpbls.Params(warps_per_block=warps, chunk_freqs=warps * 3))
+    _check_batch(b, qlpbls.Params(warps_per_block=warps, chunk_freqs=warps * 3,
+                                  method=qlpbls.METHOD_POINTS))
 
 
 def test_multi_sector(gpu_lib):
