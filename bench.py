@@ -113,12 +113,20 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# FP32-pipe operations per point-frequency evaluation in the search kernel's
-# double-float fold and run accumulation (see DESIGN: "roofline"): 4 for the
-# double-float product, 8 for the two round-to-integer steps and the remainder,
-# 2 for the guard-band test, 2 for the run sums.
+# Algorithmic work per unit of the two search kernels:
+#  point path, per point-frequency evaluation: 16 FP32-pipe lane operations
+#    (double-float product 4, two round-to-integer steps and the remainder 8,
+#    guard-band test 2, run sums 2);
+#  cell path, per bin edge: 20 lane operations with plain sums (fixed-point edge
+#    location 6, comparison and band test 4, prefix differences 8, bin update 2)
+#    and 30 with compensated sums (TwoSum on both bin updates); shared-memory
+#    traffic per edge 44 B plain / 60 B compensated (dt 4 + prefix 8 + base 16 of
+#    gathers, then the bin read-modify-write).
 FP32_OPS_PER_EVAL = 16
+CELL_OPS_PER_EDGE = {0: 20, 1: 30}
+CELL_SMEM_BYTES_PER_EDGE = {0: 44, 1: 60}
 FP32_LANES_PER_SM = 128
+SMEM_BYTES_PER_CLK_PER_SM = 128
 N_SMS = 152
 
 
@@ -254,13 +262,27 @@ def main():
 
     peaks, src = _peaks()
     sm_clock = peaks.get("sm_max_mhz", 2070.0) * 1e6
-    peak_ops = N_SMS * FP32_LANES_PER_SM * sm_clock / 1e12  # T FP32-lane ops / s
-    achieved = plan.work * FP32_OPS_PER_EVAL / (ms_search * 1e-3) / 1e12
+    peak_ops = N_SMS * FP32_LANES_PER_SM * sm_clock / 1e12  # T lane ops / s
+    peak_smem = N_SMS * SMEM_BYTES_PER_CLK_PER_SM * sm_clock / 1e9  # GB/s
+    cells_dominant = plan.work_cells >= plan.work_points
+    if cells_dominant:
+        ops = plan.edges * CELL_OPS_PER_EDGE[params.sum_mode]
+        achieved = ops / (ms_search * 1e-3) / 1e12
+        smem_gbs = plan.edges * CELL_SMEM_BYTES_PER_EDGE[params.sum_mode] / (ms_search * 1e-3) / 1e9
+        kernel = "cells_kernel (search-call duration: includes prep_cells)"
+        unit_note = f"{plan.edges:.4e} bin edges x {CELL_OPS_PER_EDGE[params.sum_mode]} ops"
+    else:
+        achieved = plan.work * FP32_OPS_PER_EVAL / (ms_search * 1e-3) / 1e12
+        smem_gbs = None
+        kernel = "bls_kernel (search-call duration: includes prep)"
+        unit_note = f"{plan.work:.4e} point-freq x {FP32_OPS_PER_EVAL} ops"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "TFLOP/s",
-                "frac": achieved / peak_ops, "traffic": None,
-                "kernel": "bls_kernel (duration includes the preceding prep kernel)",
+                "frac": achieved / peak_ops, "traffic": None, "kernel": kernel,
+                "algorithmic": unit_note,
                 "peak_source": f"152 SMs x 128 FP32 lanes x {sm_clock/1e6:.0f} MHz ({src} max clock)",
-                "ops_per_eval": FP32_OPS_PER_EVAL}
+                "smem": None if smem_gbs is None else
+                {"achieved_gbs": smem_gbs, "peak_gbs": peak_smem, "frac": smem_gbs / peak_smem,
+                 "peak_source": "152 SMs x 128 B/clk x max clock"}}
 
     if rank == 0:
         cpu = None
@@ -269,13 +291,16 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32 (double-float fold, FP64 near bin edges)", "data": "synthetic",
+                "dtype": "f32 sums, FP64 prefix sums, FP64 bin decisions", "data": "synthetic",
                 "config": {"workload": "uneven_single_sector_200s", "stars_per_gpu": args.stars,
                            "points": plan.n_points, "trial_freqs": plan.n_freq_total,
-                           "point_freq_per_gpu": plan.work, "phase_mode": "DF",
-                           "sum_mode": "COMP", "l2": "inputs larger than L2 (prepared points "
-                           f"{plan.n_points * 24 / 1e6:.0f} MB)", "parallelism": f"replicas x{world}"},
-                "ms_search": ms_search, "gpu_launches": 3 * args.steps,
+                           "point_freq_per_gpu": plan.work, "bin_edges": plan.edges,
+                           "cell_path_stars": plan.n_cell_stars, "phase_mode": "DF",
+                           "sum_mode": "COMP" if params.sum_mode else "PLAIN",
+                           "l2": "inputs larger than L2 (light curves "
+                           f"{plan.n_points * 24 / 1e6:.0f} MB FP64)", "parallelism": f"replicas x{world}"},
+                "ms_search": ms_search,
+                "gpu_launches": args.steps * (1 + 2 * (plan.work_points > 0) + 2 * (plan.work_cells > 0)),
                 "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e}
         print(json.dumps(line), flush=True)
     if world > 1:

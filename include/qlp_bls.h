@@ -76,7 +76,8 @@ typedef struct qlp_bls_params {
   int32_t sum_mode;         /* QLP_SUM_*   (default QLP_SUM_COMP) */
   int32_t mad_mode;         /* QLP_MAD_*   (default QLP_MAD_RAW) */
   int32_t chunk_freqs;      /* frequencies per work item, 0 = chosen by the planner */
-  int32_t warps_per_block;  /* 0 = chosen by the planner; else 4, 8 or 16 */
+  int32_t warps_per_block;  /* 0 = chosen by the planner; else 4, 8, 16 or 32 (32: cell path only,
+                               the point path uses at most 16) */
   int32_t n_threads;        /* host threads for planning, 0 = all cores */
   int32_t tile_points;      /* points per shared-memory tile, 0 = as many as fit (multiple of 32) */
   int32_t method;           /* 0 = per star, the cheaper of the two search paths (default);
@@ -146,6 +147,18 @@ int qlp_bls_plan(const qlp_bls_params* p, int32_t n_stars, const int64_t* offset
  */
 int qlp_bls_plan_info(const qlp_bls_plan_t* plan, int64_t* n_freq_total, int64_t* freq_offsets,
                       double* freqs, int32_t* star_status, int64_t* n_points, double* work);
+
+/*
+ * qlp_bls_plan_stats -- how the plan splits the work between the two search
+ * paths (both give the same FP64-binned results, Sec. 2.1). Any output may be NULL.
+ *  work_points   point-frequency pairs of stars whose points are folded one by one.
+ *  work_cells    point-frequency pairs of stars searched by bin edges on the cell table.
+ *  edges         bin edges the cell path evaluates (sum over its stars and
+ *                frequencies of floor(T f nbins) + 3).
+ *  n_cell_stars  stars on the cell path.
+ */
+int qlp_bls_plan_stats(const qlp_bls_plan_t* plan, double* work_points, double* work_cells,
+                       double* edges, int32_t* n_cell_stars);
 
 /*
  * qlp_bls_search -- Sec. 2.1 / Eq. 1's SR: binned BLS residue at every trial frequency.

@@ -57,6 +57,9 @@ struct qlp_bls_plan {
   std::vector<double> freqs;      // all stars
   int64_t n_points = 0;
   double work = 0.0;              // sum N_s * n_f,s
+  double work_points = 0.0;       // point-frequency pairs folded by the point path
+  double work_cells = 0.0;        // point-frequency pairs served by the cell path
+  double edges = 0.0;             // bin edges the cell path evaluates
   int32_t nbins_max = 0;
   // launch shape
   int warps = 8;
@@ -86,7 +89,7 @@ struct qlp_bls_plan {
   double* d_tpd = nullptr;
   int32_t* d_cell_stars = nullptr;
   double2* d_cpre = nullptr;
-  float* d_dt = nullptr;
+  uint32_t* d_dt = nullptr;
   float2* d_loc = nullptr;
   float4* d_base = nullptr;
   int32_t* d_gidx = nullptr;
@@ -159,7 +162,7 @@ static int check_params(const qlp_bls_params& p) {
       p.mad_mode > 1 || p.tile_points < 0 || p.chunk_freqs < 0 || p.method < 0 || p.method > 2)
     return QLP_ERR_ARG;
   if (p.warps_per_block != 0 && p.warps_per_block != 4 && p.warps_per_block != 8 &&
-      p.warps_per_block != 16)
+      p.warps_per_block != 16 && p.warps_per_block != 32)
     return QLP_ERR_ARG;
   const int nq = n_q_of(p);
   if (nq < 1 || nq > kMaxQ) return QLP_ERR_UNSUPPORTED;
@@ -206,7 +209,7 @@ int qlp_bls_plan(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offs
 
   // method per star: the cell path needs one point per cell, its table and
   // histograms in shared memory, and fewer bin edges than point-frequency pairs
-  const int cw = p.warps_per_block ? p.warps_per_block : 16;
+  const int cw = p.warps_per_block ? p.warps_per_block : 32;
   // the table plus at least one warp's histogram for the star's largest bin count
   auto cell_smem = [&](int64_t cells, int nbmax) {
     return (size_t)cells_hist_offset((int)cells, cw) + (size_t)NA * (size_t)round32(nbmax + kMPad) * 4;
@@ -250,6 +253,8 @@ int qlp_bls_plan(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offs
     pl->f_off[(size_t)s + 1] = nf;
     if (ok) pl->work += (double)d.n_pts * (double)d.n_f;
     if (ok && d.method == kMethodCells) {
+      pl->work_cells += (double)d.n_pts * (double)d.n_f;
+      pl->edges += h.cells_work;
       d.h = h.cell_h;
       d.n_cells = (int32_t)h.n_cells;
       d.cell_off = ncell;
@@ -262,6 +267,7 @@ int qlp_bls_plan(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offs
       nb_c = std::max(nb_c, h.nbins_max);
       cell_stars.push_back(s);
     } else if (ok) {
+      pl->work_points += (double)d.n_pts * (double)d.n_f;
       npad += ((int64_t)d.n_pts + 31) & ~(int64_t)31;
       max_npts = std::max(max_npts, d.n_pts);
       nb_pp = std::max(nb_pp, h.nbins_max);
@@ -293,7 +299,7 @@ int qlp_bls_plan(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offs
 
   // per-point launch shape: histograms per warp, then the largest point tile that fits
   pl->hist_stride = (int)round32(std::max(nb_pp, 1) + kMPad);
-  int warps = p.warps_per_block ? p.warps_per_block : 8;
+  int warps = p.warps_per_block ? std::min(p.warps_per_block, 16) : 8;
   auto hist_bytes = [&](int w) { return (size_t)w * NA * pl->hist_stride * 4 + (size_t)w * kMaxQ * 4; };
   while (warps > 4 && hist_bytes(warps) > (size_t)budget / 2) warps /= 2;
   const size_t hb = align16(hist_bytes(warps));
@@ -414,6 +420,16 @@ int qlp_bls_plan_info(const qlp_bls_plan_t* pl, int64_t* n_freq_total, int64_t* 
   if (star_status && !pl->status.empty()) std::memcpy(star_status, pl->status.data(), sizeof(int32_t) * pl->status.size());
   if (n_points) *n_points = pl->n_points;
   if (work) *work = pl->work;
+  return QLP_OK;
+}
+
+int qlp_bls_plan_stats(const qlp_bls_plan_t* pl, double* work_points, double* work_cells,
+                       double* edges, int32_t* n_cell_stars) {
+  if (!pl) return QLP_ERR_ARG;
+  if (work_points) *work_points = pl->work_points;
+  if (work_cells) *work_cells = pl->work_cells;
+  if (edges) *edges = pl->edges;
+  if (n_cell_stars) *n_cell_stars = pl->n_cell_stars;
   return QLP_OK;
 }
 

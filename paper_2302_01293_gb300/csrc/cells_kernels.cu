@@ -14,7 +14,8 @@
 // C(tau) in O(1): the star's time axis is cut into cells of width h just below
 // the smallest point spacing, so each cell holds at most one point. Per cell the
 // table keeps C at the cell start (a per-32-cell double-float base plus an FP32
-// local part) and the offset dt of its point, so
+// local part) and the offset dt of its point (a 32-bit fraction of the cell); an
+// edge's cell and position come from tau/h = G D/h in 2^-56 fixed point, so
 //     C(tau) = C(cell u start) + [dt_u < tau - u h] (w, w d) = C(start of cell u + [..]).
 // Near ties (|dt_u - (tau - u h)| within a guard band) are decided exactly by the
 // FP64 fold of that point: "point before edge G" is "its FP64 global bin < G".
@@ -118,8 +119,13 @@ __global__ void __launch_bounds__(256) prep_cells_kernel(const PrepCellsArgs a) 
   for (int u = tid; u <= nc; u += blockDim.x) {
     const int f = first[u];
     const bool in_cell = (u < nc) && (f < n) && (cell_of(tp[f], h) == u);
-    a.dt[st.cell_off + u] = in_cell ? __double2float_rn(__dsub_rn(tp[f], __dmul_rn((double)u, h)))
-                                    : __int_as_float(0x7f800000);  // +inf
+    // offset of the cell's point as a 32-bit fraction of the cell, empty = 0xFFFFFFFF
+    uint32_t q = 0xffffffffu;
+    if (in_cell) {
+      const double fr = __ddiv_rn(__dsub_rn(tp[f], __dmul_rn((double)u, h)), h);
+      q = (uint32_t)fmin(floor(__dmul_rn(fr, 4294967296.0)), 4294967294.0);
+    }
+    a.dt[st.cell_off + u] = q;
     const double2 c = a.cpre[st.cpre_off + f];
     const double2 cb = a.cpre[st.cpre_off + first[u & ~31]];
     a.loc[st.cell_off + u] = make_float2(__double2float_rn(c.x - cb.x), __double2float_rn(c.y - cb.y));
@@ -166,29 +172,20 @@ struct EdgeC {
   float bwh, bwl, byh, byl, lw, ly;
 };
 
-__device__ __forceinline__ EdgeC edge_prefix(int G, float Dh, float Dl, float hh, float hl,
-                                             float inv_h, int nc, float band, const float* s_dt,
+__device__ __forceinline__ EdgeC edge_prefix(int G, uint32_t k_lo, uint32_t k_hi, int nc,
+                                             uint32_t band_q, const uint32_t* s_dt,
                                              const float2* s_loc, const float4* s_base,
                                              const double* tp, const int32_t* gidx, double f,
                                              int nb) {
-  const float Gf = (float)G;
-  const float th = __fmul_rn(Gf, Dh);  // tau = G D as (th, te)
-  float te = __fmaf_rn(Gf, Dh, -th);
-  te = __fmaf_rn(Gf, Dl, te);
-  int u = (int)__fmul_rn(th, inv_h);
-  u = min(max(u, 0), nc);
-  const float uf = (float)u;  // dl = tau - u h
-  const float p = __fmul_rn(uf, hh);
-  float pe = __fmaf_rn(uf, hh, -p);
-  pe = __fmaf_rn(uf, hl, pe);
-  float dl = __fadd_rn(__fsub_rn(th, p), __fsub_rn(te, pe));
-  const bool lo_ = dl < 0.f && u > 0;
-  const bool hi_ = dl >= hh && u < nc;
-  u = lo_ ? u - 1 : (hi_ ? u + 1 : u);
-  dl = lo_ ? __fadd_rn(dl, hh) : (hi_ ? __fsub_rn(dl, hh) : dl);
-  const float diff = __fsub_rn(s_dt[u], dl);
-  int sel = diff < 0.f ? 1 : 0;
-  const bool need = fabsf(diff) <= band;
+  // tau_G / h in 2^-56 fixed point: G (32 bits) x K (64 bits) -> 96 bits
+  const unsigned long long lo = (unsigned long long)(uint32_t)G * k_lo;
+  const unsigned long long hi = (unsigned long long)(uint32_t)G * k_hi + (lo >> 32);
+  const int u = (int)min((unsigned long long)nc, hi >> 24);          // cell
+  const uint32_t fr = ((uint32_t)hi << 8) | ((uint32_t)lo >> 24);   // position in the cell, 2^-32
+  const uint32_t dq = s_dt[u];
+  int sel = dq < fr ? 1 : 0;                                          // the cell's point is before tau
+  const bool need = (dq != 0xffffffffu) && (hi >> 24) <= (unsigned long long)nc &&
+                    (uint32_t)(dq - fr + band_q) <= 2u * band_q;
   if (__any_sync(0xffffffffu, need)) {  // rare: decide by the exact FP64 fold
     if (need) sel = exact_before(tp, gidx[u], f, nb, G);
   }
@@ -244,7 +241,7 @@ __global__ void __launch_bounds__(NW * 32) cells_kernel(const CellArgs a) {
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int nq = a.nq;
-  const float* s_dt = reinterpret_cast<const float*>(smem);
+  const uint32_t* s_dt = reinterpret_cast<const uint32_t*>(smem);
 
   __shared__ int s_item;
   __shared__ int s_star;
@@ -267,7 +264,7 @@ __global__ void __launch_bounds__(NW * 32) cells_kernel(const CellArgs a) {
     if (s_star != wi.star) {  // block-uniform
       __syncthreads();
       const int nbk = (ncs + 31) >> 5;
-      float* d_dt = reinterpret_cast<float*>(smem);
+      uint32_t* d_dt = reinterpret_cast<uint32_t*>(smem);
       float2* d_loc = reinterpret_cast<float2*>(smem + L.loc);
       float4* d_base = reinterpret_cast<float4*>(smem + L.base);
       for (int i = threadIdx.x; i < ncs; i += NW * 32) {
@@ -290,9 +287,6 @@ __global__ void __launch_bounds__(NW * 32) cells_kernel(const CellArgs a) {
     const double* tp = a.tp + st.pt_off;
     const int32_t* gidx = a.gidx + st.cell_off;
     const double h = st.h;
-    const float hh = __double2float_rn(h);
-    const float hl = __double2float_rn(h - (double)hh);
-    const float inv_h = __double2float_rn(1.0 / h);
 
     for (int fl = warp; fl < wi.f_count; fl += wact) {
       const int64_t fidx = st.f_off + wi.f_begin + fl;
@@ -319,14 +313,16 @@ __global__ void __launch_bounds__(NW * 32) cells_kernel(const CellArgs a) {
       }
       const double F = __dmul_rn(f, (double)nb);
       const double D = __ddiv_rn(1.0, F);  // bin duration (days)
-      const float Dh = __double2float_rn(D);
-      const float Dl = __double2float_rn(D - (double)Dh);
       const double yT = __dmul_rn(st.baseline, F);
       const int g_end = (int)floor(yT) + 2;  // edges 0 .. g_end; tau_{g_end} > T
-      // guard band in days: FP64 fold and double-float edge errors (in bins) / F,
-      // plus the FP32 rounding of dt
-      const float band = __double2float_rn((9.5367431640625e-07 + 9.094947017729282e-13 * yT) * D +
-                                           2.384185791015625e-07 * h);
+      // edge step in cells, 2^-56 fixed point (D/h < 2^8)
+      const unsigned long long K = __double2ull_rn(__dmul_rn(__ddiv_rn(D, h), 72057594037927936.0));
+      const uint32_t k_lo = (uint32_t)K, k_hi = (uint32_t)(K >> 32);
+      // guard band in 2^-32 cell units: the FP64 fold's and this fixed-point edge's
+      // errors (2^-20 + 2^-40 T F bins, converted) plus the table's quantisation
+      const uint32_t band_q = (uint32_t)fmin(
+          __dmul_rn(__ddiv_rn(__dmul_rn(9.5367431640625e-07 + 9.094947017729282e-13 * yT, D), h),
+                    4294967296.0) + 64.0, 1073741824.0);
       __syncwarp();
 
       const bool own = nb >= 31;  // the 31 pieces of one chunk fall in distinct bins
@@ -334,10 +330,10 @@ __global__ void __launch_bounds__(NW * 32) cells_kernel(const CellArgs a) {
       int b = lane % nb;  // bin of this lane's piece in the first chunk
       for (int g0 = 0; g0 < g_end; g0 += 62) {
         // two chunks of 31 pieces in flight: edges g0 .. g0+31 and g0+31 .. g0+62
-        const EdgeC c0 = edge_prefix(g0 + lane, Dh, Dl, hh, hl, inv_h, nc, band, s_dt, s_loc, s_base,
-                                     tp, gidx, f, nb);
-        const EdgeC c1 = edge_prefix(g0 + 31 + lane, Dh, Dl, hh, hl, inv_h, nc, band, s_dt, s_loc,
-                                     s_base, tp, gidx, f, nb);
+        const EdgeC c0 = edge_prefix(g0 + lane, k_lo, k_hi, nc, band_q, s_dt, s_loc, s_base, tp, gidx,
+                                     f, nb);
+        const EdgeC c1 = edge_prefix(g0 + 31 + lane, k_lo, k_hi, nc, band_q, s_dt, s_loc, s_base, tp,
+                                     gidx, f, nb);
         const float2 p0 = edge_piece(c0);
         const float2 p1 = edge_piece(c1);
         int b1 = b + step;
@@ -374,15 +370,17 @@ static int occ_cells_t(size_t smem) {
   return nb;
 }
 
-#define QLP_CELLS_DISPATCH(FN, ...)                                \
-  switch (sum_mode * 10 + (warps == 4 ? 0 : warps == 8 ? 1 : 2)) { \
-    case 0: return FN<0, 4>(__VA_ARGS__);                          \
-    case 1: return FN<0, 8>(__VA_ARGS__);                          \
-    case 2: return FN<0, 16>(__VA_ARGS__);                         \
-    case 10: return FN<1, 4>(__VA_ARGS__);                         \
-    case 11: return FN<1, 8>(__VA_ARGS__);                         \
-    case 12: return FN<1, 16>(__VA_ARGS__);                        \
-    default: break;                                                \
+#define QLP_CELLS_DISPATCH(FN, ...)                                                   \
+  switch (sum_mode * 10 + (warps == 4 ? 0 : warps == 8 ? 1 : warps == 16 ? 2 : 3)) { \
+    case 0: return FN<0, 4>(__VA_ARGS__);                                             \
+    case 1: return FN<0, 8>(__VA_ARGS__);                                             \
+    case 2: return FN<0, 16>(__VA_ARGS__);                                            \
+    case 3: return FN<0, 32>(__VA_ARGS__);                                            \
+    case 10: return FN<1, 4>(__VA_ARGS__);                                            \
+    case 11: return FN<1, 8>(__VA_ARGS__);                                            \
+    case 12: return FN<1, 16>(__VA_ARGS__);                                           \
+    case 13: return FN<1, 32>(__VA_ARGS__);                                           \
+    default: break;                                                                   \
   }
 
 int launch_cells(const CellArgs& a, int sum_mode, int warps, int blocks, size_t smem, void* stream) {

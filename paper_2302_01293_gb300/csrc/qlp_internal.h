@@ -79,7 +79,7 @@ struct CellArgs {
   int32_t n_items;
   int32_t nq;
   const double* tp;        // raw t' (CSR by pt_off), for the exact decision near ties
-  const float* dt;         // per cell: offset of its point from the cell start, +inf if empty
+  const uint32_t* dt;      // per cell: its point's offset, 2^-32 of the cell; 0xFFFFFFFF if empty
   const float2* loc;       // per cell: prefix sums (w, w d) before the cell, minus the block base
   const float4* base;      // per 32 cells: block base prefix sums as (w_hi, w_lo, y_hi, y_lo)
   const int32_t* gidx;     // per cell: index of the first point at or after the cell start
@@ -103,7 +103,7 @@ struct PrepCellsArgs {
   const double* y;
   const double* dy;
   double2* cpre;              // prefix sums (sum w, sum w d) before each point, N + 1 per star
-  float* dt;
+  uint32_t* dt;
   float2* loc;
   float4* base;
   int32_t* gidx;

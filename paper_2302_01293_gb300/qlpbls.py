@@ -93,6 +93,8 @@ def lib():
             L.qlp_bls_plan.restype = ctypes.c_int
             L.qlp_bls_plan_info.argtypes = [_vp, _P(_i64), _vp, _vp, _vp, _P(_i64), _P(_d)]
             L.qlp_bls_plan_info.restype = ctypes.c_int
+            L.qlp_bls_plan_stats.argtypes = [_vp, _P(_d), _P(_d), _P(_d), _P(_i32)]
+            L.qlp_bls_plan_stats.restype = ctypes.c_int
             L.qlp_bls_search.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp]
             L.qlp_bls_search.restype = ctypes.c_int
             L.qlp_bls_snr.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
@@ -176,6 +178,11 @@ class Plan:
         self.star_status = np.zeros(self.n_stars, np.int32)
         _check(L.qlp_bls_plan_info(self._h, None, _np_ptr(self.freq_offsets), _np_ptr(self.freqs),
                                    _np_ptr(self.star_status), None, None), "qlp_bls_plan_info")
+        wp, wc, ed, nc = _d(), _d(), _d(), _i32()
+        _check(L.qlp_bls_plan_stats(self._h, ctypes.byref(wp), ctypes.byref(wc), ctypes.byref(ed),
+                                    ctypes.byref(nc)), "qlp_bls_plan_stats")
+        self.work_points, self.work_cells, self.edges = wp.value, wc.value, ed.value
+        self.n_cell_stars = int(nc.value)
 
     def alloc_outputs(self):
         import torch
