@@ -144,6 +144,7 @@ constexpr int32_t kErrQueueBound = 1;   // work loop exceeded its iteration boun
 constexpr int32_t kErrNbins = 2;        // a frequency needed more bins than the histogram holds
 constexpr int32_t kErrSturges = 4;      // more S/N bins than the kernel supports
 constexpr int32_t kErrSelect = 8;       // median selection failed to converge
+constexpr int32_t kErrMmaWait = 16;     // a tensor-core completion wait hit its bound
 
 // launchers (bls_kernels.cu / snr_kernel.cu); return cudaError_t as int
 int launch_prep(const PrepArgs& a, void* stream);
@@ -157,6 +158,10 @@ int launch_cells(const CellArgs& a, int sum_mode, int warps, int blocks, size_t 
 uint32_t cells_hist_offset(int ncs, int nw);
 int cells_blocks_per_sm(int sum_mode, int warps, size_t smem);
 int bls_max_smem_per_block();
+int launch_conv64(const void* x, const void* wpack, const float* bias, const void* mask, void* y,
+                  int32_t* err, int batch, int len, int relu, void* stream);
+int launch_pack_w64(const float* w, void* out, int transpose, void* stream);
+int conv64_smem_bytes();
 int bls_blocks_per_sm(int phase_mode, int sum_mode, int warps, size_t smem_bytes);
 
 }  // namespace qlp

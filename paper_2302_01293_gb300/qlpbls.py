@@ -112,6 +112,10 @@ def lib():
             L.qlp_bls_search_static.argtypes = [_P(CParams), _i32, _vp, _vp, _vp, _d, _i32, _vp,
                                                 _vp, _vp, _vp, _vp, _vp, _vp, _vp]
             L.qlp_bls_search_static.restype = ctypes.c_int
+            L.qlp_cnn_pack_w64.argtypes = [_vp, _vp, _i32, _vp]
+            L.qlp_cnn_pack_w64.restype = ctypes.c_int
+            L.qlp_cnn_conv64.argtypes = [_vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]
+            L.qlp_cnn_conv64.restype = ctypes.c_int
             L.qlp_strerror.argtypes = [ctypes.c_int]
             L.qlp_strerror.restype = ctypes.c_char_p
             L.qlp_last_cuda_error.argtypes = []
