@@ -289,6 +289,43 @@ int qlp_cnn_pack_w64(const float* w, void* wpack, int32_t transpose, void* strea
 int qlp_cnn_conv64(const void* x, const void* wpack, const float* bias, const void* mask, void* y,
                    int32_t batch, int32_t len, int32_t relu, int32_t* err, void* stream);
 
+/*
+ * The network: input x0 BF16 [batch][len][2] (channel 0 the coarse S/N, channel 1
+ * the valid-bin mask), conv(2->64)+ReLU, 4 x [conv(64->64)+ReLU], conv(64->1): one
+ * logit per bin, kernel 9, zero padding, len a multiple of 128.
+ * Parameters (FP32, qlp_cnn_n_params() of them) in the order
+ *   W1 [9][64][2], b1 [64], (W_k [9][64][64], b_k [64]) for k = 2..5, W6 [9][64], b6,
+ * with W[tap][out channel][in channel]. Weights are the FP32 masters of Adam; the
+ * 64->64 layers compute with BF16 copies on the tensor cores, activations are
+ * BF16, accumulation FP32.
+ * qlp_cnn_create     network for batches of up to max_batch, He-normal initial
+ *                    weights from `seed` (counter-based generator), output bias -4.
+ * qlp_cnn_forward    logits (device FP32 [batch][len], may be NULL: kept inside).
+ * qlp_cnn_backward   forward, then the weighted BCE with logits averaged over
+ *                    batch x len (labels device FP32 [batch][len] in {0, 1};
+ *                    positives weighted by pos_weight) and every parameter
+ *                    gradient, kept inside the network.
+ * qlp_cnn_adam_step  Adam (beta 0.9, 0.999, eps 1e-8, bias-corrected) on the masters.
+ * qlp_cnn_train_step backward + Adam.
+ * qlp_cnn_loss       synchronises `stream`; last loss and the device error bits.
+ * qlp_cnn_get_params / qlp_cnn_set_params  host copies of the parameters (and of
+ *                    the last gradients); set resets Adam's moments.
+ */
+typedef struct qlp_cnn qlp_cnn_t;
+int32_t qlp_cnn_n_params(void);
+int qlp_cnn_create(int32_t max_batch, int32_t len, uint64_t seed, qlp_cnn_t** out);
+void qlp_cnn_destroy(qlp_cnn_t* net);
+int qlp_cnn_set_params(qlp_cnn_t* net, const float* host, void* stream);
+int qlp_cnn_get_params(const qlp_cnn_t* net, float* host, float* grads_host, void* stream);
+int qlp_cnn_forward(qlp_cnn_t* net, const void* x0, int32_t batch, float* logits, void* stream);
+int qlp_cnn_backward(qlp_cnn_t* net, const void* x0, const float* labels, int32_t batch,
+                     float pos_weight, void* stream);
+int qlp_cnn_adam_step(qlp_cnn_t* net, float lr, void* stream);
+int qlp_cnn_train_step(qlp_cnn_t* net, const void* x0, const float* labels, int32_t batch,
+                       float pos_weight, float lr, void* stream);
+int qlp_cnn_loss(qlp_cnn_t* net, float* loss_host, int32_t* err_host, void* stream);
+const char* qlp_cnn_last_error(void);
+
 /* Static description of a return code. */
 const char* qlp_strerror(int code);
 

@@ -625,19 +625,3 @@ int qlp_bls_star_grid(const qlp_bls_params* pin, int64_t n, const double* t, con
 void qlp_bls_plan_destroy(qlp_bls_plan_t* pl) { free_plan(pl); }
 
 }  // extern "C"
-
-// ---------------------------------------------------------------- learned path
-
-extern "C" int qlp_cnn_pack_w64(const float* w, void* wpack, int32_t transpose, void* stream) {
-  if (!w || !wpack) return QLP_ERR_ARG;
-  const int e = launch_pack_w64(w, wpack, transpose, stream);
-  return e ? cuda_fail((cudaError_t)e, "pack launch") : QLP_OK;
-}
-
-extern "C" int qlp_cnn_conv64(const void* x, const void* wpack, const float* bias, const void* mask,
-                              void* y, int32_t batch, int32_t len, int32_t relu, int32_t* err,
-                              void* stream) {
-  if (!x || !wpack || !y || !err || batch < 0 || len <= 0 || len % 128 != 0) return QLP_ERR_ARG;
-  const int e = launch_conv64(x, wpack, bias, mask, y, err, batch, len, relu, stream);
-  return e ? cuda_fail((cudaError_t)e, "conv64 launch") : QLP_OK;
-}

@@ -211,4 +211,312 @@ int launch_pack_w64(const float* w, void* out, int transpose, void* stream) {
   return (int)cudaGetLastError();
 }
 
+
+// ------------------------------------------------------------------ other layers
+// First layer 2 -> 64 channels and last layer 64 -> 1 channel (kernel 9, same
+// padding) on the CUDA cores; their weight gradients and the bias gradients as
+// two-stage reductions (per-CTA partial sums, then a sum over CTAs); BCE with
+// logits; Adam with FP32 master weights.
+
+// x0 [B][L][2] BF16 -> a1 [B][L][64] BF16 = relu(b1 + conv(x0, W1)), W1 [9][64][2]
+__global__ void __launch_bounds__(128) conv_in_kernel(const __nv_bfloat16* x0, const float* w1,
+                                                      const float* b1, __nv_bfloat16* a1, int batch,
+                                                      int len) {
+  __shared__ float sw[kTaps * kC * 2];
+  __shared__ float sb[kC];
+  for (int i = threadIdx.x; i < kTaps * kC * 2; i += blockDim.x) sw[i] = w1[i];
+  for (int i = threadIdx.x; i < kC; i += blockDim.x) sb[i] = b1[i];
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= batch * len) return;
+  const int b = p / len, l = p - b * len;
+  float xv[kTaps][2];
+#pragma unroll
+  for (int kk = 0; kk < kTaps; ++kk) {
+    const int ll = l + kk - kTaps / 2;
+    const bool in = ll >= 0 && ll < len;
+    xv[kk][0] = in ? __bfloat162float(x0[((size_t)b * len + ll) * 2 + 0]) : 0.f;
+    xv[kk][1] = in ? __bfloat162float(x0[((size_t)b * len + ll) * 2 + 1]) : 0.f;
+  }
+  __nv_bfloat16* out = a1 + (size_t)p * kC;
+#pragma unroll
+  for (int c0 = 0; c0 < kC; c0 += 8) {
+    __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int co = c0 + e;
+      float z = sb[co];
+#pragma unroll
+      for (int kk = 0; kk < kTaps; ++kk)
+        z += sw[(kk * kC + co) * 2 + 0] * xv[kk][0] + sw[(kk * kC + co) * 2 + 1] * xv[kk][1];
+      o[e] = __float2bfloat16_rn(fmaxf(z, 0.f));
+    }
+    *reinterpret_cast<uint4*>(out + c0) = *reinterpret_cast<const uint4*>(o);
+  }
+}
+
+__device__ __forceinline__ void bf16x8_to_f32(uint4 u, float* f) {
+  const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&u);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) f[e] = __bfloat162float(h[e]);
+}
+
+// a5 [B][L][64] BF16 -> logit [B][L] FP32 = b6 + conv(a5, W6), W6 [9][64]
+__global__ void __launch_bounds__(128) conv_out_kernel(const __nv_bfloat16* a5, const float* w6,
+                                                       const float* b6, float* logit, int batch, int len) {
+  __shared__ float sw[kTaps * kC];
+  for (int i = threadIdx.x; i < kTaps * kC; i += blockDim.x) sw[i] = w6[i];
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= batch * len) return;
+  const int b = p / len, l = p - b * len;
+  float z = b6[0];
+#pragma unroll 1
+  for (int kk = 0; kk < kTaps; ++kk) {
+    const int ll = l + kk - kTaps / 2;
+    if (ll < 0 || ll >= len) continue;
+    const uint4* row = reinterpret_cast<const uint4*>(a5 + ((size_t)b * len + ll) * kC);
+#pragma unroll
+    for (int q = 0; q < kC / 8; ++q) {
+      float f[8];
+      bf16x8_to_f32(row[q], f);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) z += sw[kk * kC + 8 * q + e] * f[e];
+    }
+  }
+  logit[p] = z;
+}
+
+// Weighted BCE with logits, mean over B L: loss_i = pw y softplus(-z) + (1-y) softplus(z);
+// dlogit_i = (pw y (sigmoid(z) - 1) + (1 - y) sigmoid(z)) / (B L).
+__global__ void __launch_bounds__(256) bce_kernel(const float* logit, const float* label, float* dlogit,
+                                                  float* loss, int n, float pos_weight) {
+  __shared__ float red[8];
+  float acc = 0.f;
+  const float inv = 1.f / (float)n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float z = logit[i], y = label[i];
+    const float sp_pos = fmaxf(z, 0.f) + log1pf(expf(-fabsf(z)));  // softplus(z)
+    const float sp_neg = sp_pos - z;                                // softplus(-z)
+    acc += pos_weight * y * sp_neg + (1.f - y) * sp_pos;
+    const float sg = 1.f / (1.f + expf(-z));
+    dlogit[i] = (pos_weight * y * (sg - 1.f) + (1.f - y) * sg) * inv;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    atomicAdd(loss, s * inv);
+  }
+}
+
+// da5[b][l][ci] = (a5 > 0) * sum_kk W6[kk][ci] dlogit[b][l - kk + 4]
+__global__ void __launch_bounds__(128) conv_out_bwd_kernel(const float* dlogit, const float* w6,
+                                                           const __nv_bfloat16* a5, __nv_bfloat16* da5,
+                                                           int batch, int len) {
+  __shared__ float sw[kTaps * kC];
+  for (int i = threadIdx.x; i < kTaps * kC; i += blockDim.x) sw[i] = w6[i];
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= batch * len) return;
+  const int b = p / len, l = p - b * len;
+  float g[kTaps];
+#pragma unroll
+  for (int kk = 0; kk < kTaps; ++kk) {
+    const int ll = l - kk + kTaps / 2;
+    g[kk] = (ll >= 0 && ll < len) ? dlogit[(size_t)b * len + ll] : 0.f;
+  }
+  const uint4* arow = reinterpret_cast<const uint4*>(a5 + (size_t)p * kC);
+  uint4* drow = reinterpret_cast<uint4*>(da5 + (size_t)p * kC);
+#pragma unroll
+  for (int q = 0; q < kC / 8; ++q) {
+    float av[8];
+    bf16x8_to_f32(arow[q], av);
+    __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      float s = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < kTaps; ++kk) s += sw[kk * kC + 8 * q + e] * g[kk];
+      o[e] = __float2bfloat16_rn(av[e] > 0.f ? s : 0.f);
+    }
+    drow[q] = *reinterpret_cast<const uint4*>(o);
+  }
+}
+
+// Partial weight and bias gradients of a 64 -> 64 layer over 32-position tiles:
+// dW[kk][co][ci] = sum_p dY[p][co] X[p + kk - 4][ci], db[co] = sum_p dY[p][co].
+// Thread (co, 8-channel group) keeps 9 x 8 accumulators.
+constexpr int kDwOut = kTaps * kC * kC + kC;
+__global__ void __launch_bounds__(512) dw64_kernel(const __nv_bfloat16* dy, const __nv_bfloat16* x,
+                                                   float* partial, int batch, int len) {
+  __shared__ __align__(16) float sdy[32][kC];
+  __shared__ __align__(16) float sx[32 + kTaps - 1][kC];
+  const int t = threadIdx.x;
+  const int co = t >> 3, cg = t & 7;
+  float acc[kTaps][8];
+#pragma unroll
+  for (int kk = 0; kk < kTaps; ++kk)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[kk][c] = 0.f;
+  float accb = 0.f;
+  const int n_tiles = batch * len / 32;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int p0 = tile * 32;
+    const int b = p0 / len, l0 = p0 - b * len;
+    for (int i = t; i < 32 * kC; i += blockDim.x)
+      sdy[i / kC][i % kC] = __bfloat162float(dy[((size_t)b * len + l0) * kC + i]);
+    for (int i = t; i < (32 + kTaps - 1) * kC; i += blockDim.x) {
+      const int r = i / kC, c = i % kC;
+      const int l = l0 - kTaps / 2 + r;
+      sx[r][c] = (l >= 0 && l < len) ? __bfloat162float(x[((size_t)b * len + l) * kC + c]) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int p = 0; p < 32; ++p) {
+      const float g = sdy[p][co];
+      accb += g;
+#pragma unroll
+      for (int kk = 0; kk < kTaps; ++kk) {
+        const float4* xr = reinterpret_cast<const float4*>(&sx[p + kk][8 * cg]);
+        const float4 v0 = xr[0], v1 = xr[1];
+        acc[kk][0] += g * v0.x; acc[kk][1] += g * v0.y; acc[kk][2] += g * v0.z; acc[kk][3] += g * v0.w;
+        acc[kk][4] += g * v1.x; acc[kk][5] += g * v1.y; acc[kk][6] += g * v1.z; acc[kk][7] += g * v1.w;
+      }
+    }
+    __syncthreads();
+  }
+  float* out = partial + (size_t)blockIdx.x * kDwOut;
+#pragma unroll
+  for (int kk = 0; kk < kTaps; ++kk)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) out[(kk * kC + co) * kC + 8 * cg + c] = acc[kk][c];
+  if (cg == 0) out[kTaps * kC * kC + co] = accb;
+}
+
+// Partial gradients of a small layer: n_co x n_ci channels (first layer 64 x 2 with
+// dY BF16, last layer 1 x 64 with dY FP32). One thread per (kk, co, ci) output
+// plus n_co bias outputs; each CTA covers a range of positions.
+template <typename TY>
+__global__ void __launch_bounds__(256) dw_small_kernel(const TY* dy, const __nv_bfloat16* x, float* partial,
+                                                       int batch, int len, int n_co, int n_ci, int per_cta) {
+  const int n_w = kTaps * n_co * n_ci;
+  const int n_out = n_w + n_co;
+  const int total = batch * len;
+  const int p_begin = blockIdx.x * per_cta;
+  const int p_end = min(total, p_begin + per_cta);
+  for (int o = threadIdx.x; o < n_out; o += blockDim.x) {
+    float acc = 0.f;
+    if (o < n_w) {
+      const int kk = o / (n_co * n_ci), co = (o / n_ci) % n_co, ci = o % n_ci;
+      for (int p = p_begin; p < p_end; ++p) {
+        const int b = p / len, l = p - b * len;
+        const int ll = l + kk - kTaps / 2;
+        if (ll < 0 || ll >= len) continue;
+        acc += (float)dy[(size_t)p * n_co + co] * __bfloat162float(x[((size_t)b * len + ll) * n_ci + ci]);
+      }
+    } else {
+      const int co = o - n_w;
+      for (int p = p_begin; p < p_end; ++p) acc += (float)dy[(size_t)p * n_co + co];
+    }
+    partial[(size_t)blockIdx.x * n_out + o] = acc;
+  }
+}
+
+__global__ void reduce_partials_kernel(const float* partial, int n_parts, int n_out, float* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_out) return;
+  float s = 0.f;
+  for (int g = 0; g < n_parts; ++g) s += partial[(size_t)g * n_out + i];
+  out[i] = s;
+}
+
+__global__ void adam_kernel(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// ------------------------------------------------------------------ launchers
+
+int launch_conv_in(const void* x0, const float* w1, const float* b1, void* a1, int batch, int len, void* s) {
+  const int n = batch * len;
+  conv_in_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)s>>>(
+      static_cast<const __nv_bfloat16*>(x0), w1, b1, static_cast<__nv_bfloat16*>(a1), batch, len);
+  return (int)cudaGetLastError();
+}
+
+int launch_conv_out(const void* a5, const float* w6, const float* b6, float* logit, int batch, int len, void* s) {
+  const int n = batch * len;
+  conv_out_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)s>>>(static_cast<const __nv_bfloat16*>(a5), w6, b6,
+                                                                  logit, batch, len);
+  return (int)cudaGetLastError();
+}
+
+int launch_bce(const float* logit, const float* label, float* dlogit, float* loss, int n, float pw, void* s) {
+  const int blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+  bce_kernel<<<blocks, 256, 0, (cudaStream_t)s>>>(logit, label, dlogit, loss, n, pw);
+  return (int)cudaGetLastError();
+}
+
+int launch_conv_out_bwd(const float* dlogit, const float* w6, const void* a5, void* da5, int batch, int len,
+                        void* s) {
+  const int n = batch * len;
+  conv_out_bwd_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)s>>>(
+      dlogit, w6, static_cast<const __nv_bfloat16*>(a5), static_cast<__nv_bfloat16*>(da5), batch, len);
+  return (int)cudaGetLastError();
+}
+
+int dw64_parts(int batch, int len) {
+  const int tiles = batch * len / 32;
+  return tiles < 304 ? tiles : 304;
+}
+int dw_small_parts(int batch, int len) {
+  const int total = batch * len;
+  return (total + 1023) / 1024 < 512 ? (total + 1023) / 1024 : 512;
+}
+
+// dW and db of a 64 -> 64 layer into out[kDwOut] (dW [9][64][64] then db [64])
+int launch_dw64(const void* dy, const void* x, float* partial, float* out, int batch, int len, void* s) {
+  const int parts = dw64_parts(batch, len);
+  dw64_kernel<<<parts, 512, 0, (cudaStream_t)s>>>(static_cast<const __nv_bfloat16*>(dy),
+                                                   static_cast<const __nv_bfloat16*>(x), partial, batch, len);
+  reduce_partials_kernel<<<(kDwOut + 255) / 256, 256, 0, (cudaStream_t)s>>>(partial, parts, kDwOut, out);
+  return (int)cudaGetLastError();
+}
+
+// dW and db of the first (dy BF16 [B][L][64], x BF16 [B][L][2]) or last (dy FP32
+// [B][L], x BF16 [B][L][64]) layer into out[9 co ci + co]
+int launch_dw_small(const void* dy, int dy_is_f32, const void* x, float* partial, float* out, int batch,
+                    int len, int n_co, int n_ci, void* s) {
+  const int total = batch * len;
+  const int parts = dw_small_parts(batch, len);
+  const int per = (total + parts - 1) / parts;
+  const int n_out = kTaps * n_co * n_ci + n_co;
+  if (dy_is_f32)
+    dw_small_kernel<float><<<parts, 256, 0, (cudaStream_t)s>>>(static_cast<const float*>(dy),
+                                                                static_cast<const __nv_bfloat16*>(x), partial,
+                                                                batch, len, n_co, n_ci, per);
+  else
+    dw_small_kernel<__nv_bfloat16><<<parts, 256, 0, (cudaStream_t)s>>>(
+        static_cast<const __nv_bfloat16*>(dy), static_cast<const __nv_bfloat16*>(x), partial, batch, len, n_co,
+        n_ci, per);
+  reduce_partials_kernel<<<(n_out + 255) / 256, 256, 0, (cudaStream_t)s>>>(partial, parts, n_out, out);
+  return (int)cudaGetLastError();
+}
+
+int launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps,
+                float c1, float c2, void* s) {
+  adam_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)s>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+  return (int)cudaGetLastError();
+}
+
 }  // namespace qlp

@@ -116,6 +116,28 @@ def lib():
             L.qlp_cnn_pack_w64.restype = ctypes.c_int
             L.qlp_cnn_conv64.argtypes = [_vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]
             L.qlp_cnn_conv64.restype = ctypes.c_int
+            L.qlp_cnn_n_params.argtypes = []
+            L.qlp_cnn_n_params.restype = ctypes.c_int32
+            L.qlp_cnn_create.argtypes = [_i32, _i32, ctypes.c_uint64, _P(_vp)]
+            L.qlp_cnn_create.restype = ctypes.c_int
+            L.qlp_cnn_destroy.argtypes = [_vp]
+            L.qlp_cnn_destroy.restype = None
+            L.qlp_cnn_set_params.argtypes = [_vp, _vp, _vp]
+            L.qlp_cnn_set_params.restype = ctypes.c_int
+            L.qlp_cnn_get_params.argtypes = [_vp, _vp, _vp, _vp]
+            L.qlp_cnn_get_params.restype = ctypes.c_int
+            L.qlp_cnn_forward.argtypes = [_vp, _vp, _i32, _vp, _vp]
+            L.qlp_cnn_forward.restype = ctypes.c_int
+            L.qlp_cnn_backward.argtypes = [_vp, _vp, _vp, _i32, ctypes.c_float, _vp]
+            L.qlp_cnn_backward.restype = ctypes.c_int
+            L.qlp_cnn_adam_step.argtypes = [_vp, ctypes.c_float, _vp]
+            L.qlp_cnn_adam_step.restype = ctypes.c_int
+            L.qlp_cnn_train_step.argtypes = [_vp, _vp, _vp, _i32, ctypes.c_float, ctypes.c_float, _vp]
+            L.qlp_cnn_train_step.restype = ctypes.c_int
+            L.qlp_cnn_loss.argtypes = [_vp, _P(ctypes.c_float), _P(_i32), _vp]
+            L.qlp_cnn_loss.restype = ctypes.c_int
+            L.qlp_cnn_last_error.argtypes = []
+            L.qlp_cnn_last_error.restype = ctypes.c_char_p
             L.qlp_strerror.argtypes = [ctypes.c_int]
             L.qlp_strerror.restype = ctypes.c_char_p
             L.qlp_last_cuda_error.argtypes = []
@@ -299,3 +321,68 @@ def search_static(tp, y, dy, baseline, freqs, qmins, out, params: Params | None 
                                  out["s"].data_ptr(), out["r"].data_ptr())
     _check(rc, "qlp_bls_search_static")
     return out
+
+
+class CNN:
+    """The proposal network (qlp_cnn_*): BF16 inputs [B][L][2] and FP32 labels
+    [B][L] as device tensors; parameters as a host float32 array."""
+
+    def __init__(self, max_batch: int, length: int = 4096, seed: int = 0):
+        L = lib()
+        self._h = ctypes.c_void_p()
+        self.max_batch, self.length = int(max_batch), int(length)
+        rc = L.qlp_cnn_create(self.max_batch, self.length, int(seed), ctypes.byref(self._h))
+        _check(rc, "qlp_cnn_create")
+        self.n_params = int(L.qlp_cnn_n_params())
+
+    def _chk(self, rc, what):
+        if rc != 0:
+            msg = lib().qlp_cnn_last_error().decode()
+            raise QlpError(f"{what}: {lib().qlp_strerror(rc).decode()} ({rc}) {msg}")
+
+    def params(self, with_grads: bool = False):
+        p = np.zeros(self.n_params, np.float32)
+        g = np.zeros(self.n_params, np.float32) if with_grads else None
+        self._chk(lib().qlp_cnn_get_params(self._h, _np_ptr(p), _np_ptr(g), _stream_ptr(None)),
+                  "qlp_cnn_get_params")
+        return (p, g) if with_grads else p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        assert p.shape[0] == self.n_params
+        self._chk(lib().qlp_cnn_set_params(self._h, _np_ptr(p), _stream_ptr(None)), "qlp_cnn_set_params")
+
+    def forward(self, x0, out=None, stream=None):
+        import torch
+        B = int(x0.shape[0])
+        out = out if out is not None else torch.empty(B, self.length, dtype=torch.float32, device=x0.device)
+        self._chk(lib().qlp_cnn_forward(self._h, x0.data_ptr(), B, out.data_ptr(), _stream_ptr(stream)),
+                  "qlp_cnn_forward")
+        return out
+
+    def backward(self, x0, labels, pos_weight: float, stream=None):
+        self._chk(lib().qlp_cnn_backward(self._h, x0.data_ptr(), labels.data_ptr(), int(x0.shape[0]),
+                                         float(pos_weight), _stream_ptr(stream)), "qlp_cnn_backward")
+
+    def train_step(self, x0, labels, pos_weight: float, lr: float, stream=None):
+        self._chk(lib().qlp_cnn_train_step(self._h, x0.data_ptr(), labels.data_ptr(), int(x0.shape[0]),
+                                           float(pos_weight), float(lr), _stream_ptr(stream)),
+                  "qlp_cnn_train_step")
+
+    def loss(self, stream=None) -> float:
+        v = ctypes.c_float()
+        e = _i32()
+        rc = lib().qlp_cnn_loss(self._h, ctypes.byref(v), ctypes.byref(e), _stream_ptr(stream))
+        self._chk(rc, "qlp_cnn_loss")
+        return float(v.value)
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().qlp_cnn_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -73,3 +73,68 @@ def test_conv64_input_gradient_matches_autograd(gpu_lib):
     ref = xf.grad.permute(0, 2, 1) * (mask.float() > 0)
     dx = _run_conv(gpu_lib.lib(), dy, w, None, mask, False, True).float()
     assert (dx - ref).abs().max().item() <= 1e-2 * ref.abs().max().item()
+
+
+def test_network_gradients_match_oracle(gpu_lib):
+    """Full forward + backward of the 6-layer network on the GPU vs the oracle taken
+    in the GPU's precision (BF16 activations, activation gradients and middle-layer
+    weights; FP64 elsewhere): loss to 1e-3, every parameter tensor's gradient to
+    2e-2 relative L2 and cosine >= 0.999. Against the all-FP64 oracle the loss
+    agrees to 1e-2 and every gradient keeps cosine >= 0.99."""
+    import torch
+    from oracle import cnn as oc
+    B, L = 2, 256
+    rng = np.random.default_rng(4)
+    snr = rng.normal(size=(B, L)).astype(np.float32)
+    mask = (rng.uniform(size=(B, L)) > 0.1).astype(np.float32)
+    x0 = np.stack([snr, mask], axis=-1)
+    x0 = torch.tensor(x0).to(torch.bfloat16)
+    labels = np.zeros((B, L), np.float32)
+    labels[0, 40:43] = 1.0
+    labels[1, 200:203] = 1.0
+    params = oc.init_params(3).astype(np.float32)
+    net = gpu_lib.CNN(max_batch=B, length=L, seed=1)
+    net.set_params(params)
+    net.backward(x0.cuda(), torch.tensor(labels).cuda(), 30.0)
+    gloss = net.loss()
+    _, ggrad = net.params(with_grads=True)
+    # oracle on the same BF16-rounded input and FP32 parameters
+    xx = x0.float().numpy().astype(np.float64)
+    loss, ograd = oc.backward(params.astype(np.float64), xx, labels, 30.0, bf16=True)
+    loss64, ograd64 = oc.backward(params.astype(np.float64), xx, labels, 30.0)
+    assert gloss == pytest.approx(loss, rel=1e-3)
+    assert gloss == pytest.approx(loss64, rel=1e-2)
+    o = 0
+    for name, shp in oc.SHAPES:
+        n = int(np.prod(shp))
+        a, b, c = ggrad[o:o + n].astype(np.float64), ograd[o:o + n], ograd64[o:o + n]
+        o += n
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        cos = float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30))
+        cos64 = float(a @ c / max(np.linalg.norm(a) * np.linalg.norm(c), 1e-30))
+        assert rel <= 2e-2 and cos >= 0.999 and cos64 >= 0.99, (name, rel, cos, cos64)
+    net.close()
+
+
+def test_training_reduces_loss(gpu_lib):
+    """A few Adam steps on a fixed batch lower the loss (the update is wired)."""
+    import torch
+    B, L = 4, 512
+    rng = np.random.default_rng(8)
+    snr = rng.normal(size=(B, L)).astype(np.float32)
+    labels = np.zeros((B, L), np.float32)
+    for b in range(B):
+        k = int(rng.integers(20, L - 20))
+        snr[b, k - 1:k + 2] += 8.0
+        labels[b, k - 1:k + 2] = 1.0
+    x0 = torch.tensor(np.stack([snr, np.ones_like(snr)], -1)).to(torch.bfloat16).cuda()
+    lab = torch.tensor(labels).cuda()
+    net = gpu_lib.CNN(max_batch=B, length=L, seed=2)
+    net.backward(x0, lab, 20.0)
+    l0 = net.loss()
+    for _ in range(30):
+        net.train_step(x0, lab, 20.0, 2e-3)
+    net.backward(x0, lab, 20.0)
+    l1 = net.loss()
+    assert l1 < 0.5 * l0
+    net.close()
