@@ -83,7 +83,14 @@ typedef struct qlp_bls_params {
   int32_t method;           /* 0 = per star, the cheaper of the two search paths (default);
                                1 = fold every point; 2 = bin edges on the cell table wherever the
                                star allows it (same results: both give the FP64 bins) */
-  int32_t reserved[3];
+  int32_t grid_mode;        /* 0 = the frequency grid of Sec. 2.1 (default); 1 = the coarse grid of
+                               the learned proposal: coarse_bins periods log-spaced from coarse_pmin
+                               to coarse_pmax, P_k = pmin (pmax/pmin)^(k/(bins-1)), those within the
+                               star's [Pmin, Pmax], in increasing frequency */
+  int32_t coarse_bins;      /* 4096 */
+  int32_t reserved0;
+  double coarse_pmin;       /* 0.1 d */
+  double coarse_pmax;       /* 400 d */
 } qlp_bls_params;
 
 /* Best candidate of one star: the frequency of maximum S/N and its BLS box. */
@@ -192,6 +199,37 @@ int qlp_bls_search(qlp_bls_plan_t* plan, void* stream, float* sr, uint8_t* qidx,
 int qlp_bls_snr(qlp_bls_plan_t* plan, void* stream, const float* sr, const uint8_t* qidx,
                 const uint32_t* phase_bin, const float* s_best, const float* r_best,
                 float* snr, qlp_bls_best* best);
+
+/*
+ * Learned-proposal variants (not in the paper):
+ * qlp_bls_plan_windows -- as qlp_bls_plan (grid_mode 0 only), keeping only the
+ *   grid frequencies inside the star's windows: star s owns windows
+ *   win_offsets[s] .. win_offsets[s+1]-1 of win_flo / win_fhi (host doubles, 1/day,
+ *   inclusive). A star with no frequency inside its windows gets QLP_STAR_EMPTY_GRID.
+ * qlp_bls_snr_trend -- qlp_bls_snr with an optional per-star trend record
+ *   (QLP_TREND_DOUBLES doubles: node count, sigma_SR, median, bin centres, bin
+ *   medians) written to trend_out, or, when trend_in is given, the S/N computed
+ *   from that trend and sigma instead of the spectrum's own (device arrays,
+ *   n_stars records, same star order).
+ * qlp_bls_coarse_tensor -- for a grid_mode 1 plan: the network input, device BF16
+ *   [n_stars][n_bins][2] = (S/N, 1) on the star's searched coarse bins, 0 elsewhere;
+ *   n_bins must equal coarse_bins.
+ * qlp_cnn_topk -- indices (device int32 [batch][k]) of the k largest logits of each
+ *   row among bins whose x0 channel 1 is positive, largest first; -1 past the last
+ *   valid bin.
+ */
+#define QLP_TREND_DOUBLES 84
+int qlp_bls_plan_windows(const qlp_bls_params* p, int32_t n_stars, const int64_t* offsets,
+                         const double* t, const double* y, const double* dy, const double* rho,
+                         const double* rstar, const int64_t* win_offsets, const double* win_flo,
+                         const double* win_fhi, void* stream, qlp_bls_plan_t** out_plan);
+int qlp_bls_snr_trend(qlp_bls_plan_t* plan, void* stream, const float* sr, const uint8_t* qidx,
+                      const uint32_t* phase_bin, const float* s_best, const float* r_best,
+                      const double* trend_in, double* trend_out, float* snr, qlp_bls_best* best);
+int qlp_bls_coarse_tensor(qlp_bls_plan_t* plan, void* stream, const float* snr, int32_t n_bins,
+                          void* out);
+int qlp_cnn_topk(const float* logits, const void* x0, int32_t batch, int32_t len, int32_t k,
+                 int32_t* out, void* stream);
 
 /*
  * qlp_bls_run_host -- the whole path from host buffers to host results:

@@ -54,6 +54,11 @@ class Params:
     gap_days: float = 27.4
     rho_default: float = 1.41
     nbins_cap: int = 16384
+    # learned proposal (not in the paper): coarse log-period grid
+    grid_mode: int = 0
+    coarse_bins: int = 4096
+    coarse_pmin: float = 0.1
+    coarse_pmax: float = 400.0
 
 
 @dataclasses.dataclass
@@ -71,6 +76,7 @@ class StarPlan:
     qmin: np.ndarray        # q_min at each frequency
     nbins: np.ndarray       # int32
     m: np.ndarray           # int32 [n_f, n_q]
+    grid_k0: int = -1       # coarse grid: bin index of the first (lowest) frequency
 
 
 def n_q(p: Params) -> int:
@@ -97,6 +103,26 @@ def freq_grid(pmin: float, pmax: float, baseline: float, rho_kg: float, p: Param
         out.append(f)
         f = f + q_min(f, rho_kg, p) / denom
     return out
+
+
+def coarse_grid(pmin: float, pmax: float, p: Params):
+    """Coarse log-period grid of the learned proposal: P_k = coarse_pmin
+    (coarse_pmax/coarse_pmin)^(k/(bins-1)), kept when Pmin <= P_k <= Pmax, returned
+    in increasing frequency with the bin index of the first entry (-1 if none)."""
+    ratio = p.coarse_pmax / p.coarse_pmin
+    out, k0 = [], -1
+    for k in range(p.coarse_bins - 1, -1, -1):
+        per = p.coarse_pmin * (ratio ** (k / (p.coarse_bins - 1)))
+        if per < pmin or per > pmax:
+            continue
+        if k0 < 0:
+            k0 = k
+        out.append(1.0 / per)
+    return out, k0
+
+
+def in_windows(f: float, windows) -> bool:
+    return any(lo <= f <= hi for lo, hi in windows)
 
 
 def nbins_of(qmin: float, p: Params) -> int:
@@ -132,7 +158,7 @@ def pmax_days(tp: np.ndarray, p: Params) -> float:
     return max(float(tp[e - 1]) - float(tp[s]) for s, e in zip(starts, ends))
 
 
-def plan_star(t, y, dy, rho, rstar, p: Params = Params()) -> StarPlan:
+def plan_star(t, y, dy, rho, rstar, p: Params = Params(), windows=None) -> StarPlan:
     t = np.asarray(t, np.float64); y = np.asarray(y, np.float64); dy = np.asarray(dy, np.float64)
     ok = np.isfinite(t) & np.isfinite(y) & np.isfinite(dy) & (dy > 0)
     t, y, dy = t[ok], y[ok], dy[ok]
@@ -155,7 +181,13 @@ def plan_star(t, y, dy, rho, rstar, p: Params = Params()) -> StarPlan:
         st = bad(ST_EMPTY_GRID, t_ref)
         st.pmin, st.pmax, st.baseline = pmin, pmax, baseline
         return st
-    freqs = freq_grid(pmin, pmax, baseline, rho_kg, p)
+    k0 = -1
+    if p.grid_mode == 1:
+        freqs, k0 = coarse_grid(pmin, pmax, p)
+    else:
+        freqs = freq_grid(pmin, pmax, baseline, rho_kg, p)
+        if windows is not None:
+            freqs = [f for f in freqs if in_windows(f, windows)]
     qm = [q_min(f, rho_kg, p) for f in freqs]
     nb = [nbins_of(q, p) for q in qm]
     m = [m_of(q, b, p) for q, b in zip(qm, nb)]
@@ -170,7 +202,7 @@ def plan_star(t, y, dy, rho, rstar, p: Params = Params()) -> StarPlan:
         return st
     return StarPlan(0, t_ref, baseline, pmin, pmax, rho_kg, tp, y, dy,
                     np.asarray(freqs, np.float64), np.asarray(qm, np.float64),
-                    np.asarray(nb, np.int32), np.asarray(m, np.int32).reshape(len(freqs), n_q(p)))
+                    np.asarray(nb, np.int32), np.asarray(m, np.int32).reshape(len(freqs), n_q(p)), k0)
 
 
 def plan_batch(batch, p: Params = Params()) -> List[StarPlan]:

@@ -125,3 +125,13 @@ def best_candidate(plan, bls, snr, sigma):
     r, s = float(bls.r[k]), float(bls.s[k])
     return dict(f_idx=k, f=f, period=period, t0=t0, q=m / nb, depth=-s / (r * (1.0 - r)),
                 sr=float(bls.sr[k]), snr=float(snr[k]), j=j, k=kb, m=m, nbins=nb)
+
+
+def snr_from_trend(freqs, sr, xs, ys, sigma):
+    """S/N of a spectrum against a given trend (nodes xs, ys, np.interp semantics)
+    and sigma: the refined search of the learned proposal scores its few
+    frequencies against the coarse spectrum's trend and sigma_SR."""
+    if sigma == 0.0 or len(xs) == 0:
+        return np.zeros(len(sr))
+    trend = np.interp(np.asarray(freqs, np.float64), xs, ys)
+    return (np.asarray(sr, np.float64) - trend) / sigma

@@ -137,6 +137,11 @@ void qlp_bls_params_default(qlp_bls_params* p) {
   p->warps_per_block = 0;
   p->n_threads = 0;
   p->method = 0;
+  p->grid_mode = 0;
+  p->coarse_bins = 4096;
+  p->reserved0 = 0;
+  p->coarse_pmin = 0.1;
+  p->coarse_pmax = 400.0;
 }
 
 const char* qlp_strerror(int code) {
@@ -159,7 +164,9 @@ static int check_params(const qlp_bls_params& p) {
       p.nbins_cap < 2)
     return QLP_ERR_ARG;
   if (p.phase_mode < 0 || p.phase_mode > 2 || p.sum_mode < 0 || p.sum_mode > 1 || p.mad_mode < 0 ||
-      p.mad_mode > 1 || p.tile_points < 0 || p.chunk_freqs < 0 || p.method < 0 || p.method > 2)
+      p.mad_mode > 1 || p.tile_points < 0 || p.chunk_freqs < 0 || p.method < 0 || p.method > 2 ||
+      p.grid_mode < 0 || p.grid_mode > 1 ||
+      (p.grid_mode == 1 && (p.coarse_bins < 2 || !(p.coarse_pmin > 0) || !(p.coarse_pmax > p.coarse_pmin))))
     return QLP_ERR_ARG;
   if (p.warps_per_block != 0 && p.warps_per_block != 4 && p.warps_per_block != 8 &&
       p.warps_per_block != 16 && p.warps_per_block != 32)
@@ -172,9 +179,35 @@ static int check_params(const qlp_bls_params& p) {
   return QLP_OK;
 }
 
+static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offsets, const double* t,
+                     const double* y, const double* dy, const double* rho, const double* rstar,
+                     const int64_t* win_off, const double* win_lo, const double* win_hi, void* stream,
+                     qlp_bls_plan_t** out_plan);
+
 int qlp_bls_plan(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offsets, const double* t,
                  const double* y, const double* dy, const double* rho, const double* rstar,
                  void* stream, qlp_bls_plan_t** out_plan) {
+  return plan_impl(pin, n_stars, offsets, t, y, dy, rho, rstar, nullptr, nullptr, nullptr, stream, out_plan);
+}
+
+int qlp_bls_plan_windows(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offsets,
+                         const double* t, const double* y, const double* dy, const double* rho,
+                         const double* rstar, const int64_t* win_offsets, const double* win_flo,
+                         const double* win_fhi, void* stream, qlp_bls_plan_t** out_plan) {
+  if (!win_offsets || (n_stars > 0 && win_offsets[n_stars] > 0 && (!win_flo || !win_fhi)))
+    return QLP_ERR_ARG;
+  for (int32_t s = 0; s < n_stars; ++s)
+    if (win_offsets[s + 1] < win_offsets[s]) return QLP_ERR_ARG;
+  qlp_bls_params p;
+  if (pin) p = *pin; else qlp_bls_params_default(&p);
+  if (p.grid_mode != 0) return QLP_ERR_ARG;
+  return plan_impl(&p, n_stars, offsets, t, y, dy, rho, rstar, win_offsets, win_flo, win_fhi, stream, out_plan);
+}
+
+static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offsets, const double* t,
+                     const double* y, const double* dy, const double* rho, const double* rstar,
+                     const int64_t* win_off, const double* win_lo, const double* win_hi, void* stream,
+                     qlp_bls_plan_t** out_plan) {
   (void)rstar;
   if (!out_plan) return QLP_ERR_ARG;
   *out_plan = nullptr;
@@ -191,7 +224,7 @@ int qlp_bls_plan(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offs
   }
 
   std::vector<StarPlanHost> sp;
-  plan_all(p, n_stars, offsets, t, y, dy, rho, &sp);
+  plan_all(p, n_stars, offsets, t, y, dy, rho, &sp, win_off, win_lo, win_hi);
 
   qlp_bls_plan_t* pl = new (std::nothrow) qlp_bls_plan_t();
   if (!pl) return QLP_ERR_NOMEM;
@@ -247,6 +280,7 @@ int qlp_bls_plan(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offs
     d.method = method[(size_t)s];
     d.t_ref = h.t_ref;
     d.baseline = h.baseline;
+    d.grid_k0 = h.grid_k0;
     pl->status[(size_t)s] = h.status;
     npt += d.n_pts;
     nf += d.n_f;
@@ -517,9 +551,33 @@ int qlp_bls_search(qlp_bls_plan_t* pl, void* stream, float* sr, uint8_t* qidx, u
   return QLP_OK;
 }
 
+int qlp_bls_snr_trend(qlp_bls_plan_t* pl, void* stream, const float* sr, const uint8_t* qidx,
+                      const uint32_t* phase_bin, const float* s_best, const float* r_best,
+                      const double* trend_in, double* trend_out, float* snr, qlp_bls_best* best);
+
 int qlp_bls_snr(qlp_bls_plan_t* pl, void* stream, const float* sr, const uint8_t* qidx,
                 const uint32_t* phase_bin, const float* s_best, const float* r_best, float* snr,
                 qlp_bls_best* best) {
+  return qlp_bls_snr_trend(pl, stream, sr, qidx, phase_bin, s_best, r_best, nullptr, nullptr, snr, best);
+}
+
+int qlp_bls_coarse_tensor(qlp_bls_plan_t* pl, void* stream, const float* snr, int32_t n_bins, void* out) {
+  if (!pl || !out || n_bins <= 0 || (pl->f_off.back() > 0 && !snr)) return QLP_ERR_ARG;
+  if (pl->p.grid_mode != 1 || n_bins != pl->p.coarse_bins) return QLP_ERR_ARG;
+  const int e = launch_coarse_tensor(pl->d_stars, pl->n_stars, snr, n_bins, out, stream);
+  return e ? cuda_fail((cudaError_t)e, "coarse tensor launch") : QLP_OK;
+}
+
+int qlp_cnn_topk(const float* logits, const void* x0, int32_t batch, int32_t len, int32_t k, int32_t* out,
+                 void* stream) {
+  if (!logits || !x0 || !out || batch < 0 || len <= 0 || k <= 0 || k > len) return QLP_ERR_ARG;
+  const int e = launch_topk(logits, x0, batch, len, k, out, stream);
+  return e ? cuda_fail((cudaError_t)e, "topk launch") : QLP_OK;
+}
+
+int qlp_bls_snr_trend(qlp_bls_plan_t* pl, void* stream, const float* sr, const uint8_t* qidx,
+                      const uint32_t* phase_bin, const float* s_best, const float* r_best,
+                      const double* trend_in, double* trend_out, float* snr, qlp_bls_best* best) {
   if (!pl) return QLP_ERR_ARG;
   if (pl->n_stars > 0 && !best) return QLP_ERR_ARG;
   if (pl->f_off.back() > 0 && (!sr || !qidx || !phase_bin || !s_best || !r_best || !snr)) return QLP_ERR_ARG;
@@ -534,6 +592,8 @@ int qlp_bls_snr(qlp_bls_plan_t* pl, void* stream, const float* sr, const uint8_t
   a.rbest = r_best;
   a.snr = snr;
   a.best = best;
+  a.trend_in = trend_in;
+  a.trend_out = trend_out;
   a.err = pl->d_ctl + 2;
   a.noverlap = pl->p.noverlap;
   for (int j = 0; j < kMaxQ; ++j) a.E[j] = pl->E[j];

@@ -78,7 +78,7 @@ int64_t cell_of(double tp, double h) {
 int sturges_of(int64_t n) { return (int)std::floor(1.0 + 3.322 * std::log10((double)n) + 0.5); }
 
 void plan_one(const qlp_bls_params& p, const double* t, const double* y, const double* dy, int64_t n,
-              double rho, StarPlanHost* out) {
+              double rho, StarPlanHost* out, const Windows* win) {
   StarPlanHost& s = *out;
   s = StarPlanHost();
   const double rho_gcc = (std::isfinite(rho) && rho > 0.0) ? rho : p.rho_default;
@@ -107,17 +107,37 @@ void plan_one(const qlp_bls_params& p, const double* t, const double* y, const d
   s.pmin = pmin_of(s.rho_kg, p);
   s.pmax = pmax_of(s.tp.data(), m, p);
   if (!(s.baseline > 0.0) || !(s.pmin < s.pmax)) { s.status = QLP_STAR_EMPTY_GRID; return; }
-  const double fmax = 1.0 / s.pmin;
-  const double denom = p.samples_per_peak * s.baseline;
-  double f = 1.0 / s.pmax;
-  while (f <= fmax) {
+  auto keep = [&](double f) {
+    if (!win) return true;
+    for (int64_t i = 0; i < win->n; ++i)
+      if (f >= win->lo[i] && f <= win->hi[i]) return true;
+    return false;
+  };
+  auto add = [&](double f) {
     const double q = q_min_of(f, s.rho_kg, p);
     s.freqs.push_back(f);
     s.qmins.push_back(q);
     const int nb = nbins_of(q, p);
     s.nbins_max = std::max(s.nbins_max, nb);
     s.ymax = std::max(s.ymax, s.baseline * f * (double)nb);
-    f = f + q / denom;
+  };
+  if (p.grid_mode == 1) {
+    // coarse log-period grid, increasing frequency = decreasing bin index
+    const double ratio = p.coarse_pmax / p.coarse_pmin;
+    for (int k = p.coarse_bins - 1; k >= 0; --k) {
+      const double per = p.coarse_pmin * std::pow(ratio, (double)k / (double)(p.coarse_bins - 1));
+      if (per < s.pmin || per > s.pmax) continue;
+      if (s.grid_k0 < 0) s.grid_k0 = k;
+      add(1.0 / per);
+    }
+  } else {
+    const double fmax = 1.0 / s.pmin;
+    const double denom = p.samples_per_peak * s.baseline;
+    double f = 1.0 / s.pmax;
+    while (f <= fmax) {
+      if (keep(f)) add(f);
+      f = f + q_min_of(f, s.rho_kg, p) / denom;
+    }
   }
   if (s.freqs.empty()) { s.status = QLP_STAR_EMPTY_GRID; return; }
   if (s.nbins_max > p.nbins_cap) {
@@ -153,7 +173,8 @@ void plan_one(const qlp_bls_params& p, const double* t, const double* y, const d
 }
 
 void plan_all(const qlp_bls_params& p, int32_t n_stars, const int64_t* offsets, const double* t,
-              const double* y, const double* dy, const double* rho, std::vector<StarPlanHost>* out) {
+              const double* y, const double* dy, const double* rho, std::vector<StarPlanHost>* out,
+              const int64_t* win_off, const double* win_lo, const double* win_hi) {
   out->assign((size_t)n_stars, StarPlanHost());
   int nth = p.n_threads > 0 ? p.n_threads : (int)std::thread::hardware_concurrency();
   nth = std::max(1, std::min(nth, std::max(1, n_stars)));
@@ -161,7 +182,13 @@ void plan_all(const qlp_bls_params& p, int32_t n_stars, const int64_t* offsets, 
     for (int32_t s = tid; s < n_stars; s += nth) {
       const int64_t a = offsets[s], b = offsets[s + 1];
       const double r = rho ? rho[s] : NAN;
-      plan_one(p, t + a, y + a, dy + a, b - a, r, &(*out)[(size_t)s]);
+      Windows w;
+      if (win_off) {
+        w.lo = win_lo + win_off[s];
+        w.hi = win_hi + win_off[s];
+        w.n = win_off[s + 1] - win_off[s];
+      }
+      plan_one(p, t + a, y + a, dy + a, b - a, r, &(*out)[(size_t)s], win_off ? &w : nullptr);
     }
   };
   if (nth == 1) {

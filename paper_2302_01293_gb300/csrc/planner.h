@@ -28,6 +28,14 @@ struct StarPlanHost {
   double cell_h = 0.0;
   int64_t n_cells = 0;
   double cells_work = 0.0;         // sum over f of the bin edges across the baseline
+  int32_t grid_k0 = -1;            // coarse grid: bin index of the first (lowest) frequency
+};
+
+// Frequency windows [lo, hi] of one star (1/day) that restrict its grid.
+struct Windows {
+  const double* lo = nullptr;
+  const double* hi = nullptr;
+  int64_t n = 0;
 };
 
 int64_t cell_of(double tp, double h);
@@ -39,8 +47,10 @@ double pmin_of(double rho_kg, const qlp_bls_params& p);
 double pmax_of(const double* tp, int64_t n, const qlp_bls_params& p);
 int sturges_of(int64_t n);
 void plan_one(const qlp_bls_params& p, const double* t, const double* y, const double* dy, int64_t n,
-              double rho, StarPlanHost* out);
+              double rho, StarPlanHost* out, const Windows* win = nullptr);
 void plan_all(const qlp_bls_params& p, int32_t n_stars, const int64_t* offsets, const double* t,
-              const double* y, const double* dy, const double* rho, std::vector<StarPlanHost>* out);
+              const double* y, const double* dy, const double* rho, std::vector<StarPlanHost>* out,
+              const int64_t* win_off = nullptr, const double* win_lo = nullptr,
+              const double* win_hi = nullptr);
 
 }  // namespace qlp

@@ -31,7 +31,7 @@ struct StarDev {
   // cell n_cells is a sentinel past the last point
   double h;
   int32_t n_cells;
-  int32_t pad1;
+  int32_t grid_k0;     // coarse grid: bin index of the star's first (lowest) frequency
   int64_t cell_off;    // first entry in the per-cell arrays (n_cells + 1 entries)
   int64_t base_off;    // first entry in the per-32-cell base array
   int64_t cpre_off;    // first entry in the prefix-sum array (N + 1 entries)
@@ -120,6 +120,10 @@ struct PrepArgs {
   int32_t n_stars;
 };
 
+// Trend record of one star (the S/N kernel writes or reads it): node count,
+// sigma_SR, median, the bin centres and bin medians of the median-binned trend.
+constexpr int kTrendDoubles = 4 + 2 * kMaxSturges;
+
 struct SnrArgs {
   const StarDev* stars;
   const double2* fq;
@@ -131,6 +135,8 @@ struct SnrArgs {
   float* snr;
   qlp_bls_best* best;
   int32_t* err;
+  double* trend_out;         // per star kTrendDoubles, or null
+  const double* trend_in;    // per star: use this trend and sigma instead of computing them
   double noverlap;
   double E[kMaxQ];
   int32_t nq;
@@ -151,6 +157,9 @@ int launch_prep(const PrepArgs& a, void* stream);
 int launch_bls(const BlsArgs& a, int phase_mode, int sum_mode, int warps, int blocks,
                size_t smem_bytes, void* stream);
 int launch_snr(const SnrArgs& a, void* stream);
+int launch_coarse_tensor(const StarDev* stars, int n_stars, const float* snr, int n_bins, void* out,
+                         void* stream);
+int launch_topk(const float* logits, const void* x0, int batch, int len, int k, int32_t* out, void* stream);
 int launch_prep_cells(const PrepCellsArgs& a, void* stream);
 int launch_cells(const CellArgs& a, int sum_mode, int warps, int blocks, size_t smem, void* stream);
 // bytes of shared memory before the histograms of the cell kernel for a star with

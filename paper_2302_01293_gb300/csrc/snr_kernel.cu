@@ -11,6 +11,7 @@
 // Medians are exact order statistics of the FP32 spectrum, found by a 4-pass
 // 8-bit radix select over order-preserving integer keys, all selections of one
 // pass sharing a pass over the spectrum (shared-memory digit histograms).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -128,6 +129,8 @@ __global__ void __launch_bounds__(kSnrThreads) snr_kernel(const SnrArgs a) {
   qlp_bls_best* out = a.best + s;
 
   if (n <= 0 || st.status != 0) {
+    if (threadIdx.x == 0 && a.trend_out)
+      for (int i = 0; i < kTrendDoubles; ++i) a.trend_out[(size_t)s * kTrendDoubles + i] = 0.0;
     if (threadIdx.x == 0) {
       out->f_idx = -1;
       out->f = out->period = out->t0 = out->q = out->depth = out->sr = out->snr = 0.0;
@@ -152,6 +155,31 @@ __global__ void __launch_bounds__(kSnrThreads) snr_kernel(const SnrArgs a) {
   const double f0 = fq[0].x;
   const double span = __dsub_rn(fq[n - 1].x, f0);
 
+  if (a.trend_in) {
+    // S/N from a given trend and sigma (the refined search of the learned proposal)
+    const double* tr = a.trend_in + (size_t)s * kTrendDoubles;
+    for (int i = threadIdx.x; i < kMaxSturges; i += blockDim.x) {
+      sh.xs[i] = tr[4 + i];
+      sh.ys[i] = tr[4 + kMaxSturges + i];
+    }
+    if (threadIdx.x == 0) {
+      sh.nx = (int)tr[0];
+      sh.sigma = tr[1];
+      sh.med = tr[2];
+    }
+    __syncthreads();
+    if (sh.nx < 1) {
+      if (threadIdx.x == 0) {
+        out->f_idx = -1;
+        out->status = st.status | QLP_STAR_ZERO_MAD;
+        out->f = out->period = out->t0 = out->q = out->depth = out->sr = out->snr = 0.0;
+        out->j = out->k = out->m = out->nbins = -1;
+        out->pad = 0;
+      }
+      for (int k = threadIdx.x; k < n; k += blockDim.x) snr[k] = 0.f;
+      return;
+    }
+  } else {
   // bin boundaries: lo[i] = first k with bin(k) >= i
   for (int i = threadIdx.x; i <= nbin; i += blockDim.x) {
     int lo = 0, hi = n;
@@ -221,8 +249,20 @@ __global__ void __launch_bounds__(kSnrThreads) snr_kernel(const SnrArgs a) {
   if (threadIdx.x == 0) {
     const double mad = __dmul_rn(0.5, __dadd_rn((double)fdekey(sh.prefix[0]), (double)fdekey(sh.prefix[1])));
     sh.sigma = __dmul_rn(1.4826, mad);
+    if (a.trend_out) {
+      double* tr = a.trend_out + (size_t)s * kTrendDoubles;
+      tr[0] = (double)sh.nx;
+      tr[1] = sh.sigma;
+      tr[2] = sh.med;
+      tr[3] = 0.0;
+      for (int i = 0; i < kMaxSturges; ++i) {
+        tr[4 + i] = i < sh.nx ? sh.xs[i] : 0.0;
+        tr[4 + kMaxSturges + i] = i < sh.nx ? sh.ys[i] : 0.0;
+      }
+    }
   }
   __syncthreads();
+  }  // trend computed here
   const double sigma = sh.sigma;
 
   // S/N and its first maximum
@@ -278,6 +318,76 @@ __global__ void __launch_bounds__(kSnrThreads) snr_kernel(const SnrArgs a) {
       out->nbins = nb;
     }
   }
+}
+
+// Coarse spectrum of the learned proposal as the network input: out[s][k] =
+// (S/N, 1) for the star's searched coarse bins k (entry i of its spectrum is bin
+// grid_k0 - i), (0, 0) elsewhere; BF16 [n_stars][n_bins][2].
+__global__ void coarse_tensor_kernel(const StarDev* stars, const float* snr, int n_bins, __nv_bfloat16* out) {
+  const int s = blockIdx.x;
+  const StarDev st = stars[s];
+  __nv_bfloat16* row = out + (size_t)s * n_bins * 2;
+  for (int k = threadIdx.x; k < n_bins; k += blockDim.x) {
+    row[2 * k] = __float2bfloat16_rn(0.f);
+    row[2 * k + 1] = __float2bfloat16_rn(0.f);
+  }
+  __syncthreads();
+  if (st.status != 0) return;
+  for (int i = threadIdx.x; i < st.n_f; i += blockDim.x) {
+    const int k = st.grid_k0 - i;
+    if (k < 0 || k >= n_bins) continue;
+    row[2 * k] = __float2bfloat16_rn(snr[st.f_off + i]);
+    row[2 * k + 1] = __float2bfloat16_rn(1.f);
+  }
+}
+
+int launch_coarse_tensor(const StarDev* stars, int n_stars, const float* snr, int n_bins, void* out,
+                         void* stream) {
+  if (n_stars <= 0) return 0;
+  coarse_tensor_kernel<<<n_stars, 256, 0, (cudaStream_t)stream>>>(stars, snr, n_bins,
+                                                                   static_cast<__nv_bfloat16*>(out));
+  return (int)cudaGetLastError();
+}
+
+// The k largest logits of each row among valid bins (x0 channel 1 > 0), largest
+// first, ties to the lower bin; -1 when fewer than k bins are valid.
+__global__ void __launch_bounds__(256) topk_kernel(const float* logits, const __nv_bfloat16* x0, int len,
+                                                   int k, int32_t* out) {
+  extern __shared__ unsigned char taken[];
+  __shared__ float bv[8];
+  __shared__ int bi[8];
+  const int s = blockIdx.x;
+  const float* z = logits + (size_t)s * len;
+  const __nv_bfloat16* m = x0 + (size_t)s * len * 2;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) taken[i] = __bfloat162float(m[2 * i + 1]) > 0.f ? 0 : 1;
+  __syncthreads();
+  for (int r = 0; r < k; ++r) {
+    float v = -3.0e38f;
+    int idx = len;
+    for (int i = threadIdx.x; i < len; i += blockDim.x)
+      if (!taken[i] && (z[i] > v || (z[i] == v && i < idx))) { v = z[i]; idx = i; }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = v; bi[threadIdx.x >> 5] = idx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < 8; ++w)
+        if (bv[w] > v || (bv[w] == v && bi[w] < idx)) { v = bv[w]; idx = bi[w]; }
+      out[(size_t)s * k + r] = idx < len ? idx : -1;
+      if (idx < len) taken[idx] = 1;
+    }
+    __syncthreads();
+  }
+}
+
+int launch_topk(const float* logits, const void* x0, int batch, int len, int k, int32_t* out, void* stream) {
+  if (batch <= 0) return 0;
+  topk_kernel<<<batch, 256, len, (cudaStream_t)stream>>>(logits, static_cast<const __nv_bfloat16*>(x0), len, k,
+                                                          out);
+  return (int)cudaGetLastError();
 }
 
 int launch_snr(const SnrArgs& a, void* stream) {

@@ -19,6 +19,7 @@ PHASE_FP64, PHASE_DF, PHASE_FP32 = 0, 1, 2
 SUM_PLAIN, SUM_COMP = 0, 1
 MAD_RAW, MAD_RESID = 0, 1
 METHOD_AUTO, METHOD_POINTS, METHOD_CELLS = 0, 1, 2
+TREND_DOUBLES = 84
 
 STAR_UNSORTED, STAR_TOO_FEW, STAR_EMPTY_GRID, STAR_NBINS_CAP, STAR_ZERO_MAD = 1, 2, 4, 8, 16
 
@@ -38,7 +39,9 @@ class CParams(ctypes.Structure):
                 ("sum_mode", ctypes.c_int32), ("mad_mode", ctypes.c_int32),
                 ("chunk_freqs", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("n_threads", ctypes.c_int32), ("tile_points", ctypes.c_int32),
-                ("method", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("method", ctypes.c_int32), ("grid_mode", ctypes.c_int32),
+                ("coarse_bins", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("coarse_pmin", ctypes.c_double), ("coarse_pmax", ctypes.c_double)]
 
 
 @dataclasses.dataclass
@@ -60,6 +63,11 @@ class Params:
     n_threads: int = 0
     tile_points: int = 0
     method: int = 0
+    grid_mode: int = 0
+    coarse_bins: int = 4096
+    reserved0: int = 0
+    coarse_pmin: float = 0.1
+    coarse_pmax: float = 400.0
 
     def to_c(self) -> CParams:
         c = CParams()
@@ -138,6 +146,15 @@ def lib():
             L.qlp_cnn_loss.restype = ctypes.c_int
             L.qlp_cnn_last_error.argtypes = []
             L.qlp_cnn_last_error.restype = ctypes.c_char_p
+            L.qlp_bls_plan_windows.argtypes = [_P(CParams), _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                               _vp, _vp, _vp, _P(_vp)]
+            L.qlp_bls_plan_windows.restype = ctypes.c_int
+            L.qlp_bls_snr_trend.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+            L.qlp_bls_snr_trend.restype = ctypes.c_int
+            L.qlp_bls_coarse_tensor.argtypes = [_vp, _vp, _vp, _i32, _vp]
+            L.qlp_bls_coarse_tensor.restype = ctypes.c_int
+            L.qlp_cnn_topk.argtypes = [_vp, _vp, _i32, _i32, _i32, _vp, _vp]
+            L.qlp_cnn_topk.restype = ctypes.c_int
             L.qlp_strerror.argtypes = [ctypes.c_int]
             L.qlp_strerror.restype = ctypes.c_char_p
             L.qlp_last_cuda_error.argtypes = []
@@ -178,7 +195,9 @@ class Plan:
     """A library-owned search plan (qlp_bls_plan) and its sizes."""
 
     def __init__(self, offsets, t, y, dy, rho=None, rstar=None, params: Params | None = None,
-                 stream=None):
+                 stream=None, windows=None):
+        """windows: optional (win_offsets int64 [n_stars+1], f_lo, f_hi) restricting
+        each star's grid (qlp_bls_plan_windows)."""
         import torch
         self._h = ctypes.c_void_p()
         L = lib()
@@ -187,10 +206,19 @@ class Plan:
         self.params = params or Params()
         cp = self.params.to_c()
         self.device = torch.device("cuda", torch.cuda.current_device())
-        rc = L.qlp_bls_plan(ctypes.byref(cp), self.n_stars, _np_ptr(offsets), _np_ptr(t), _np_ptr(y),
-                            _np_ptr(dy), _np_ptr(rho), _np_ptr(rstar), _stream_ptr(stream),
-                            ctypes.byref(self._h))
-        _check(rc, "qlp_bls_plan")
+        if windows is None:
+            rc = L.qlp_bls_plan(ctypes.byref(cp), self.n_stars, _np_ptr(offsets), _np_ptr(t), _np_ptr(y),
+                                _np_ptr(dy), _np_ptr(rho), _np_ptr(rstar), _stream_ptr(stream),
+                                ctypes.byref(self._h))
+            _check(rc, "qlp_bls_plan")
+        else:
+            wo = np.ascontiguousarray(windows[0], np.int64)
+            wl = np.ascontiguousarray(windows[1], np.float64)
+            wh = np.ascontiguousarray(windows[2], np.float64)
+            rc = L.qlp_bls_plan_windows(ctypes.byref(cp), self.n_stars, _np_ptr(offsets), _np_ptr(t),
+                                        _np_ptr(y), _np_ptr(dy), _np_ptr(rho), _np_ptr(rstar), _np_ptr(wo),
+                                        _np_ptr(wl), _np_ptr(wh), _stream_ptr(stream), ctypes.byref(self._h))
+            _check(rc, "qlp_bls_plan_windows")
         nft = _i64()
         npts = _i64()
         work = _d()
@@ -232,13 +260,37 @@ class Plan:
         _check(rc, "qlp_bls_search")
         return out
 
-    def snr(self, out, stream=None):
-        """qlp_bls_snr on the arrays of a previous search; returns `out`."""
-        rc = lib().qlp_bls_snr(self._h, _stream_ptr(stream), out["sr"].data_ptr(),
-                               out["qidx"].data_ptr(), out["kbin"].data_ptr(), out["s"].data_ptr(),
-                               out["r"].data_ptr(), out["snr"].data_ptr(), out["best"].data_ptr())
-        _check(rc, "qlp_bls_snr")
+    def snr(self, out, stream=None, trend_in=None, trend_out=None):
+        """qlp_bls_snr (or qlp_bls_snr_trend when a trend tensor is given) on the
+        arrays of a previous search; returns `out`."""
+        if trend_in is None and trend_out is None:
+            rc = lib().qlp_bls_snr(self._h, _stream_ptr(stream), out["sr"].data_ptr(),
+                                   out["qidx"].data_ptr(), out["kbin"].data_ptr(), out["s"].data_ptr(),
+                                   out["r"].data_ptr(), out["snr"].data_ptr(), out["best"].data_ptr())
+            _check(rc, "qlp_bls_snr")
+        else:
+            rc = lib().qlp_bls_snr_trend(self._h, _stream_ptr(stream), out["sr"].data_ptr(),
+                                         out["qidx"].data_ptr(), out["kbin"].data_ptr(), out["s"].data_ptr(),
+                                         out["r"].data_ptr(),
+                                         trend_in.data_ptr() if trend_in is not None else None,
+                                         trend_out.data_ptr() if trend_out is not None else None,
+                                         out["snr"].data_ptr(), out["best"].data_ptr())
+            _check(rc, "qlp_bls_snr_trend")
         return out
+
+    def alloc_trend(self):
+        import torch
+        return torch.zeros(max(self.n_stars, 1) * TREND_DOUBLES, dtype=torch.float64, device=self.device)
+
+    def coarse_tensor(self, out, stream=None):
+        """qlp_bls_coarse_tensor: BF16 [n_stars, coarse_bins, 2] network input."""
+        import torch
+        nb = self.params.coarse_bins
+        x0 = torch.empty(max(self.n_stars, 1), nb, 2, dtype=torch.bfloat16, device=self.device)
+        rc = lib().qlp_bls_coarse_tensor(self._h, _stream_ptr(stream), out["snr"].data_ptr(), nb,
+                                         x0.data_ptr())
+        _check(rc, "qlp_bls_coarse_tensor")
+        return x0[: self.n_stars]
 
     def device_status(self, stream=None) -> int:
         flags = _i32()
@@ -386,3 +438,14 @@ class CNN:
             self.close()
         except Exception:
             pass
+
+
+def topk(logits, x0, k: int, stream=None):
+    """qlp_cnn_topk: device int32 [batch, k] indices of the largest valid logits."""
+    import torch
+    B, L = int(logits.shape[0]), int(logits.shape[1])
+    out = torch.empty(B, k, dtype=torch.int32, device=logits.device)
+    rc = lib().qlp_cnn_topk(logits.data_ptr(), x0.data_ptr(), B, L, int(k), out.data_ptr(),
+                            _stream_ptr(stream))
+    _check(rc, "qlp_cnn_topk")
+    return out

@@ -217,3 +217,34 @@ def sector_counts_geometric(n_stars: int, seed: int, mean: float = 3.0, cap: int
     """Sector count per star, geometric with the given mean, capped."""
     rng = np.random.default_rng(seed)
     return np.minimum(rng.geometric(1.0 / mean, n_stars), cap)
+
+
+def proposal_set(n_stars: int, seed: int, min_sectors: int = 1, max_sectors: int = 4,
+                 frac_injected: float = 0.5, depth_range=(1e-4, 1e-2), period_range=(0.5, 100.0),
+                 sigma_range=(2e-4, 2e-3)) -> Batch:
+    """Light curves for the learned period proposal: 1-4 contiguous sectors at 200-s
+    cadence with 1-d gaps, rho log-U(0.1, 10), R* log-U(0.5, 3), white noise,
+    injected boxes (P log-U(0.5, 100) d, depth log-U(1e-4, 1e-2), duration the
+    circular one times U(0.5, 2)) in half of the stars."""
+    rng = np.random.default_rng(seed)
+    nsec = rng.integers(min_sectors, max_sectors + 1, n_stars)
+    rho = _loguniform(rng, 0.1, 10.0, n_stars)
+    rstar = _loguniform(rng, 0.5, 3.0, n_stars)
+    sig = _loguniform(rng, sigma_range[0], sigma_range[1], n_stars)
+    inj = rng.uniform(size=n_stars) < frac_injected
+    per = np.where(inj, _loguniform(rng, period_range[0], period_range[1], n_stars), np.nan)
+    dep = np.where(inj, _loguniform(rng, depth_range[0], depth_range[1], n_stars), np.nan)
+    dur = np.where(inj, circular_duration_days(np.nan_to_num(per, nan=1.0), rho, rstar)
+                   * rng.uniform(0.5, 2.0, n_stars), np.nan)
+    t0 = np.full(n_stars, np.nan)
+    grids = {k: _sector_cadences(0.0, CADENCE_200S, k) for k in range(min_sectors, max_sectors + 1)}
+    ts, ys, dys = [], [], []
+    start = T_START + rng.uniform(0.0, 1.0, n_stars)
+    for s in range(n_stars):
+        t = start[s] + grids[int(nsec[s])]
+        y = 1.0 + rng.normal(0.0, sig[s], t.shape[0])
+        if inj[s]:
+            t0[s] = start[s] + rng.uniform(0.0, per[s])
+            y -= dep[s] * box_mask(t, per[s], t0[s], dur[s])
+        ts.append(t); ys.append(y); dys.append(np.full(t.shape[0], sig[s]))
+    return _assemble("proposal_set", ts, ys, dys, rho, rstar, inj, per, t0, dep, dur)

@@ -40,7 +40,8 @@ def test_params_default_matches_paper_settings():
     L.qlp_bls_params_default(ctypes.byref(p))
     assert (p.samples_per_peak, p.dlogq, p.noverlap) == (2.0, 0.1, 3.0)
     assert (p.qmin_fac, p.qmax_fac, p.pmin_aR, p.gap_days, p.rho_default) == (0.5, 2.0, 2.0, 27.4, 1.41)
-    assert ctypes.sizeof(qlpbls.CParams) == 112
+    assert ctypes.sizeof(qlpbls.CParams) == 128
+    assert (p.grid_mode, p.coarse_bins, p.coarse_pmin, p.coarse_pmax) == (0, 4096, 0.1, 400.0)
 
 
 def test_strerror():
@@ -100,3 +101,14 @@ def test_invalid_params_rejected():
                          qlpbls.Params(samples_per_peak=0.0))
     with pytest.raises(qlpbls.QlpError):
         qlpbls.star_grid(t, np.ones(50), np.full(50, 1e-3), 1.41, qlpbls.Params(phase_mode=7))
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_coarse_grid_is_bit_identical_to_oracle(seed):
+    from oracle import plan as op
+    b = synth.uneven_single_sector(n_stars=3, seed=seed)
+    for s in range(b.n_stars):
+        t, y, dy = b.star(s)
+        g = qlpbls.star_grid(t, y, dy, float(b.rho[s]), qlpbls.Params(grid_mode=1))
+        o = oracle.plan_star(t, y, dy, float(b.rho[s]), 1.0, op.Params(grid_mode=1))
+        assert np.array_equal(g["freqs"], o.freqs) and np.array_equal(g["qmins"], o.qmin)

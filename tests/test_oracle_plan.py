@@ -164,3 +164,29 @@ def test_status_flags():
     assert pl.rho_kg == 1410.0                      # solar density when missing
     small = op.Params(nbins_cap=50)
     assert op.plan_star(t, y, dy, 1.41, 1.0, small).status & op.ST_NBINS_CAP
+
+
+def test_coarse_grid_log_spacing_and_clipping():
+    p = op.Params(grid_mode=1)
+    freqs, k0 = op.coarse_grid(0.3, 14.0, p)
+    per = 1.0 / np.asarray(freqs)
+    assert np.all(np.diff(freqs) > 0)
+    assert per.min() >= 0.3 and per.max() <= 14.0
+    # constant ratio between neighbours: (400 / 0.1)^(1/4095)
+    r = per[:-1] / per[1:]
+    np.testing.assert_allclose(r, 4000.0 ** (1 / 4095), rtol=1e-12)
+    # the first entry is bin k0: P = 0.1 * 4000^(k0/4095)
+    assert per[0] == pytest.approx(0.1 * 4000.0 ** (k0 / 4095), rel=1e-14)
+    full, _ = op.coarse_grid(0.0, 1e9, p)
+    assert len(full) == 4096 and 1.0 / full[-1] == pytest.approx(0.1) and 1.0 / full[0] == pytest.approx(400.0)
+
+
+def test_windows_select_a_subset_of_the_grid():
+    import synth
+    b = synth.single_star()
+    t, y, dy = b.star(0)
+    full = oracle.plan_star(t, y, dy, 1.41, 1.0)
+    wins = [(0.27, 0.2712), (1.0, 1.004)]
+    sub = oracle.plan_star(t, y, dy, 1.41, 1.0, windows=wins)
+    expect = [f for f in full.freqs if any(lo <= f <= hi for lo, hi in wins)]
+    assert sub.freqs.tolist() == expect and len(expect) > 0
