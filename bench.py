@@ -32,7 +32,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "BLS point-freq evals/s"
+METRIC = "BLS point-freq evals/s; stars/hr learned vs full-grid BLS at >=99% recall"
 UNIT = "point-freq/s"
 
 
@@ -47,6 +47,9 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-stars", type=int, default=256)
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learned-train", type=int, default=8192)
+    ap.add_argument("--learned-eval", type=int, default=512)
     return ap.parse_args()
 
 
@@ -128,6 +131,61 @@ CELL_SMEM_BYTES_PER_EDGE = {0: 44, 1: 60}
 FP32_LANES_PER_SM = 128
 SMEM_BYTES_PER_CLK_PER_SM = 128
 N_SMS = 152
+
+
+def learned_comparison(args):
+    """Stars per hour of the learned proposal vs the full-grid search on the same
+    held-out multi-sector stars, with the recall of the full grid's recoveries.
+
+    The network is trained here from scratch on seeded coarse spectra (no stored
+    weights). Both paths are timed wall-clock from host arrays to best records
+    (planning, uploads, searches, S/N, network), on one GPU."""
+    import torch
+    import synth
+    from paper_2302_01293_gb300 import learned, qlpbls
+    t0 = time.perf_counter()
+    batches = []
+    for c in range(0, args.learned_train, 2048):
+        tb = synth.proposal_set(min(2048, args.learned_train - c), seed=100 + c)
+        cs = learned.CoarseStage(tb)
+        batches.append((cs.x0.clone(), learned.labels(tb, cs.params, "cuda")))
+        del cs
+    net = qlpbls.CNN(max_batch=128, length=4096, seed=0)
+    losses = learned.train(net, batches, epochs=4, lr=3e-4, pos_weight=16.0)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    test = synth.proposal_set(args.learned_eval, seed=999)
+    # warm both paths once (library load, allocator), then time
+    for timed in (False, True):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan = qlpbls.Plan(test.offsets, test.t, test.y, test.dy, test.rho, test.rstar)
+        out = plan.search()
+        plan.snr(out)
+        best_full = plan.best_host(out)
+        t_full = time.perf_counter() - t0
+        del plan, out
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        best_l, coarse, _ = learned.search_learned(test, net, k=32)
+        torch.cuda.synchronize()
+        t_learned = time.perf_counter() - t0
+    rf = learned.recovered(best_full, test)
+    rl = learned.recovered(best_l, test)
+    best_a, _, _ = learned.search_learned(test, net, k=32,
+                                          bins=learned.propose_without_network(coarse, 32))
+    ra = learned.recovered(best_a, test)
+    n = test.n_stars
+    return {"workload": f"{n} held-out stars, 1-4 sectors at 200 s, 50 % injected "
+                        "(P log-U(0.5, 100) d, depth log-U(1e-4, 1e-2))",
+            "train_stars": args.learned_train, "epochs": 4, "train_seconds": t_train,
+            "final_loss": losses[-1], "K": 32,
+            "full_recovered": int(rf.sum()), "injected": int(test.inj.sum()),
+            "recall": float((rl & rf).sum() / max(rf.sum(), 1)),
+            "recall_coarse_snr_topk_without_network": float((ra & rf).sum() / max(rf.sum(), 1)),
+            "stars_per_hour_full": n / t_full * 3600.0,
+            "stars_per_hour_learned": n / t_learned * 3600.0,
+            "speedup": t_full / t_learned}
 
 
 def cpu_baseline(batch, n_sample: int):
@@ -288,6 +346,9 @@ def main():
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             cpu = cpu_baseline(batch, args.cpu_sample_stars)
+        learned_line = None
+        if not args.no_learned and world == 1:
+            learned_line = learned_comparison(args)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -301,7 +362,8 @@ def main():
                            f"{plan.n_points * 24 / 1e6:.0f} MB FP64)", "parallelism": f"replicas x{world}"},
                 "ms_search": ms_search,
                 "gpu_launches": args.steps * (1 + 2 * (plan.work_points > 0) + 2 * (plan.work_cells > 0)),
-                "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e}
+                "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "learned": learned_line}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -212,8 +212,8 @@ int qlp_bls_snr(qlp_bls_plan_t* plan, void* stream, const float* sr, const uint8
  *   from that trend and sigma instead of the spectrum's own (device arrays,
  *   n_stars records, same star order).
  * qlp_bls_coarse_tensor -- for a grid_mode 1 plan: the network input, device BF16
- *   [n_stars][n_bins][2] = (S/N, 1) on the star's searched coarse bins, 0 elsewhere;
- *   n_bins must equal coarse_bins.
+ *   [n_stars][n_bins][2] = (asinh(S/N / 4), 1) on the star's searched coarse bins,
+ *   (0, 0) elsewhere; n_bins must equal coarse_bins.
  * qlp_cnn_topk -- indices (device int32 [batch][k]) of the k largest logits of each
  *   row among bins whose x0 channel 1 is positive, largest first; -1 past the last
  *   valid bin.

@@ -321,8 +321,10 @@ __global__ void __launch_bounds__(kSnrThreads) snr_kernel(const SnrArgs a) {
 }
 
 // Coarse spectrum of the learned proposal as the network input: out[s][k] =
-// (S/N, 1) for the star's searched coarse bins k (entry i of its spectrum is bin
-// grid_k0 - i), (0, 0) elsewhere; BF16 [n_stars][n_bins][2].
+// (asinh(S/N / 4), 1) for the star's searched coarse bins k (entry i of its
+// spectrum is bin grid_k0 - i), (0, 0) elsewhere; BF16 [n_stars][n_bins][2]. The
+// monotone asinh compression keeps the ordering of the S/N while bounding the
+// range the network sees (S/N from -5 to 10^4 maps to about -1.1 to 8.5).
 __global__ void coarse_tensor_kernel(const StarDev* stars, const float* snr, int n_bins, __nv_bfloat16* out) {
   const int s = blockIdx.x;
   const StarDev st = stars[s];
@@ -336,7 +338,7 @@ __global__ void coarse_tensor_kernel(const StarDev* stars, const float* snr, int
   for (int i = threadIdx.x; i < st.n_f; i += blockDim.x) {
     const int k = st.grid_k0 - i;
     if (k < 0 || k >= n_bins) continue;
-    row[2 * k] = __float2bfloat16_rn(snr[st.f_off + i]);
+    row[2 * k] = __float2bfloat16_rn(asinhf(0.25f * snr[st.f_off + i]));
     row[2 * k + 1] = __float2bfloat16_rn(1.f);
   }
 }
