@@ -88,7 +88,9 @@ typedef struct qlp_bls_params {
                                to coarse_pmax, P_k = pmin (pmax/pmin)^(k/(bins-1)), those within the
                                star's [Pmin, Pmax], in increasing frequency */
   int32_t coarse_bins;      /* 4096 */
-  int32_t reserved0;
+  int32_t cell_window;      /* cell path: cells of the time table a block holds in shared memory at
+                               once, 0 = the whole table when it fits, else as many as fill half
+                               of it; a star whose table is longer is searched window by window */
   double coarse_pmin;       /* 0.1 d */
   double coarse_pmax;       /* 400 d */
 } qlp_bls_params;
@@ -163,9 +165,11 @@ int qlp_bls_plan_info(const qlp_bls_plan_t* plan, int64_t* n_freq_total, int64_t
  *  edges         bin edges the cell path evaluates (sum over its stars and
  *                frequencies of floor(T f nbins) + 3).
  *  n_cell_stars  stars on the cell path.
+ *  n_windowed    of those, stars whose cell table is searched in several time
+ *                windows (a table longer than one block's shared memory).
  */
 int qlp_bls_plan_stats(const qlp_bls_plan_t* plan, double* work_points, double* work_cells,
-                       double* edges, int32_t* n_cell_stars);
+                       double* edges, int32_t* n_cell_stars, int32_t* n_windowed);
 
 /*
  * qlp_bls_search -- Sec. 2.1 / Eq. 1's SR: binned BLS residue at every trial frequency.

@@ -78,6 +78,7 @@ struct qlp_bls_plan {
   size_t c_smem = 0;
   int32_t c_items = 0;
   int32_t n_cell_stars = 0;
+  int32_t n_windowed = 0;
   // device
   StarDev* d_stars = nullptr;
   double2* d_fq = nullptr;
@@ -139,7 +140,7 @@ void qlp_bls_params_default(qlp_bls_params* p) {
   p->method = 0;
   p->grid_mode = 0;
   p->coarse_bins = 4096;
-  p->reserved0 = 0;
+  p->cell_window = 0;
   p->coarse_pmin = 0.1;
   p->coarse_pmax = 400.0;
 }
@@ -165,7 +166,7 @@ static int check_params(const qlp_bls_params& p) {
     return QLP_ERR_ARG;
   if (p.phase_mode < 0 || p.phase_mode > 2 || p.sum_mode < 0 || p.sum_mode > 1 || p.mad_mode < 0 ||
       p.mad_mode > 1 || p.tile_points < 0 || p.chunk_freqs < 0 || p.method < 0 || p.method > 2 ||
-      p.grid_mode < 0 || p.grid_mode > 1 ||
+      p.grid_mode < 0 || p.grid_mode > 1 || p.cell_window < 0 ||
       (p.grid_mode == 1 && (p.coarse_bins < 2 || !(p.coarse_pmin > 0) || !(p.coarse_pmax > p.coarse_pmin))))
     return QLP_ERR_ARG;
   if (p.warps_per_block != 0 && p.warps_per_block != 4 && p.warps_per_block != 8 &&
@@ -247,11 +248,38 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   auto cell_smem = [&](int64_t cells, int nbmax) {
     return (size_t)cells_hist_offset((int)cells, cw) + (size_t)NA * (size_t)round32(nbmax + kMPad) * 4;
   };
+  // A table longer than shared memory is cut into windows of win_cells cells;
+  // window w owns the cells from w win_cells and stages from the 32-aligned cell
+  // below its start to win_ovl cells past its end (one bin duration plus the
+  // cells an edge and the point after it can reach).
+  struct CellWin {
+    int32_t n_win = 1, cells = 0, ovl = 0, cap = 0;
+  };
   std::vector<int32_t> method((size_t)n_stars, kMethodPoints);
+  std::vector<CellWin> cwin((size_t)n_stars);
   for (int32_t s = 0; s < n_stars; ++s) {
     const StarPlanHost& h = sp[(size_t)s];
     if (h.status != 0 || !h.cells_ok || p.method == 1 || p.phase_mode == QLP_PHASE_FP32) continue;
-    if (cell_smem(h.n_cells + 1, h.nbins_max) > (size_t)budget) continue;
+    CellWin& W = cwin[(size_t)s];
+    const double ovl = std::ceil(h.bin_dmax / h.cell_h) + 4.0;
+    if (!(ovl < 1.0e6)) continue;
+    W.ovl = (int32_t)ovl;
+    const bool whole = p.cell_window > 0 ? p.cell_window >= h.n_cells
+                                          : cell_smem(h.n_cells + 1, h.nbins_max) <= (size_t)budget;
+    if (whole) {
+      W.cells = (int32_t)h.n_cells;
+      W.cap = (int32_t)h.n_cells + 1;
+    } else {
+      int64_t c = p.cell_window;
+      if (c <= 0) {  // the largest multiple of 32 whose staged window fills at most half the budget
+        c = 32;
+        while (cells_hist_offset((int)(c + 32 + W.ovl + 33), cw) <= (size_t)budget / 2) c += 32;
+      }
+      W.cells = (int32_t)c;
+      W.cap = (int32_t)std::min<int64_t>(h.n_cells + 1, c + W.ovl + 33);
+      W.n_win = (int32_t)((h.n_cells + c - 1) / c);
+    }
+    if (cell_smem(W.cap, h.nbins_max) > (size_t)budget) continue;
     const double pp_work = (double)h.freqs.size() * (double)round32((int64_t)h.tp.size());
     if (p.method == 2 || h.cells_work < pp_work) method[(size_t)s] = kMethodCells;
   }
@@ -291,6 +319,11 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
       pl->edges += h.cells_work;
       d.h = h.cell_h;
       d.n_cells = (int32_t)h.n_cells;
+      d.n_win = cwin[(size_t)s].n_win;
+      d.win_cells = cwin[(size_t)s].cells;
+      d.win_ovl = cwin[(size_t)s].ovl;
+      d.win_cap = cwin[(size_t)s].cap;
+      if (d.n_win > 1) pl->n_windowed++;
       d.cell_off = ncell;
       d.base_off = nbase;
       d.cpre_off = ncpre;
@@ -388,7 +421,7 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
           for (int32_t k = b; k < b + wi.f_count; ++k)
             nbm = std::max(nbm, (int)std::ceil(p.noverlap / h.qmins[(size_t)k]));
           const int hs32 = (int)(round32(nbm + kMPad) / 32);
-          const size_t avail = (size_t)budget - cells_hist_offset(d.n_cells + 1, cw);
+          const size_t avail = (size_t)budget - cells_hist_offset(d.win_cap, cw);
           const int wact = (int)std::min<size_t>((size_t)cw, avail / ((size_t)NA * hs32 * 32 * 4));
           wi.pad0 = hs32 | (std::max(wact, 1) << 16);
         }
@@ -458,8 +491,9 @@ int qlp_bls_plan_info(const qlp_bls_plan_t* pl, int64_t* n_freq_total, int64_t* 
 }
 
 int qlp_bls_plan_stats(const qlp_bls_plan_t* pl, double* work_points, double* work_cells,
-                       double* edges, int32_t* n_cell_stars) {
+                       double* edges, int32_t* n_cell_stars, int32_t* n_windowed) {
   if (!pl) return QLP_ERR_ARG;
+  if (n_windowed) *n_windowed = pl->n_windowed;
   if (work_points) *work_points = pl->work_points;
   if (work_cells) *work_cells = pl->work_cells;
   if (edges) *edges = pl->edges;

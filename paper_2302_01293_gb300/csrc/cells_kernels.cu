@@ -172,26 +172,28 @@ struct EdgeC {
   float bwh, bwl, byh, byl, lw, ly;
 };
 
-__device__ __forceinline__ EdgeC edge_prefix(int G, uint32_t k_lo, uint32_t k_hi, int nc,
-                                             uint32_t band_q, const uint32_t* s_dt,
+// Prefix sums at edge G from the staged table window [lo, lo + n_loc): cells
+// outside it are clamped (only lanes whose result is discarded reach them).
+__device__ __forceinline__ EdgeC edge_prefix(int G, bool valid, uint32_t k_lo, uint32_t k_hi, int nc,
+                                             int lo, int n_loc, uint32_t band_q, const uint32_t* s_dt,
                                              const float2* s_loc, const float4* s_base,
                                              const double* tp, const int32_t* gidx, double f,
                                              int nb) {
   // tau_G / h in 2^-56 fixed point: G (32 bits) x K (64 bits) -> 96 bits
-  const unsigned long long lo = (unsigned long long)(uint32_t)G * k_lo;
-  const unsigned long long hi = (unsigned long long)(uint32_t)G * k_hi + (lo >> 32);
-  const int u = (int)min((unsigned long long)nc, hi >> 24);          // cell
-  const uint32_t fr = ((uint32_t)hi << 8) | ((uint32_t)lo >> 24);   // position in the cell, 2^-32
-  const uint32_t dq = s_dt[u];
-  int sel = dq < fr ? 1 : 0;                                          // the cell's point is before tau
-  const bool need = (dq != 0xffffffffu) && (hi >> 24) <= (unsigned long long)nc &&
-                    (uint32_t)(dq - fr + band_q) <= 2u * band_q;
+  const unsigned long long lo64 = (unsigned long long)(uint32_t)G * k_lo;
+  const unsigned long long hi64 = (unsigned long long)(uint32_t)G * k_hi + (lo64 >> 32);
+  const int u = (int)min((unsigned long long)nc, hi64 >> 24);          // cell (global)
+  const uint32_t fr = ((uint32_t)hi64 << 8) | ((uint32_t)lo64 >> 24);  // position in the cell, 2^-32
+  const int ul = min(max(u - lo, 0), n_loc - 1);                        // cell in the window
+  const uint32_t dq = s_dt[ul];
+  int sel = dq < fr ? 1 : 0;                                             // the cell's point is before tau
+  const bool need = valid && (dq != 0xffffffffu) && (uint32_t)(dq - fr + band_q) <= 2u * band_q;
   if (__any_sync(0xffffffffu, need)) {  // rare: decide by the exact FP64 fold
-    if (need) sel = exact_before(tp, gidx[u], f, nb, G);
+    if (need) sel = exact_before(tp, gidx[lo + ul], f, nb, G);
   }
-  const int v = min(u + sel, nc);
-  const float2 lc = s_loc[v];
-  const float4 bs = s_base[v >> 5];
+  const int vl = min(ul + sel, n_loc - 1);
+  const float2 lc = s_loc[vl];
+  const float4 bs = s_base[((lo + vl) >> 5) - (lo >> 5)];
   EdgeC c;
   c.bwh = bs.x; c.bwl = bs.y; c.byh = bs.z; c.byl = bs.w; c.lw = lc.x; c.ly = lc.y;
   return c;
@@ -245,7 +247,8 @@ __global__ void __launch_bounds__(NW * 32) cells_kernel(const CellArgs a) {
 
   __shared__ int s_item;
   __shared__ int s_star;
-  if (threadIdx.x == 0) s_star = -1;
+  __shared__ int s_win;
+  if (threadIdx.x == 0) { s_star = -1; s_win = -1; }
 
   bool done = false;
   for (int iter = 0; iter <= a.n_items; ++iter) {
@@ -257,28 +260,13 @@ __global__ void __launch_bounds__(NW * 32) cells_kernel(const CellArgs a) {
     const WorkItem wi = a.items[it];
     const StarDev st = a.stars[wi.star];
     const int nc = st.n_cells;  // sentinel index
-    const int ncs = nc + 1;
-    const CellSmem L = cell_smem_layout(ncs, NW);
+    const int n_win = st.n_win;
+    const CellSmem L = cell_smem_layout(st.win_cap, NW);
     const float2* s_loc = reinterpret_cast<const float2*>(smem + L.loc);
     const float4* s_base = reinterpret_cast<const float4*>(smem + L.base);
-    if (s_star != wi.star) {  // block-uniform
-      __syncthreads();
-      const int nbk = (ncs + 31) >> 5;
-      uint32_t* d_dt = reinterpret_cast<uint32_t*>(smem);
-      float2* d_loc = reinterpret_cast<float2*>(smem + L.loc);
-      float4* d_base = reinterpret_cast<float4*>(smem + L.base);
-      for (int i = threadIdx.x; i < ncs; i += NW * 32) {
-        d_dt[i] = a.dt[st.cell_off + i];
-        d_loc[i] = a.loc[st.cell_off + i];
-      }
-      for (int i = threadIdx.x; i < nbk; i += NW * 32) d_base[i] = a.base[st.base_off + i];
-      if (threadIdx.x == 0) s_star = wi.star;
-      __syncthreads();
-    }
     // per item: histogram stride (multiple of 32 floats) and the warps that fit
     const int HS = (wi.pad0 & 0xffff) * 32;
     const int wact = wi.pad0 >> 16;
-    if (warp >= wact) continue;  // no block barrier until the next item
     int* mtab = reinterpret_cast<int*>(smem + L.mtab) + warp * kMaxQ;
     float* hw = reinterpret_cast<float*>(smem + L.hist) + (size_t)warp * NA * HS;
     float* hy = hw + HS;
@@ -288,64 +276,101 @@ __global__ void __launch_bounds__(NW * 32) cells_kernel(const CellArgs a) {
     const int32_t* gidx = a.gidx + st.cell_off;
     const double h = st.h;
 
-    for (int fl = warp; fl < wi.f_count; fl += wact) {
-      const int64_t fidx = st.f_off + wi.f_begin + fl;
-      const double2 fq = a.fq[fidx];
-      const double f = fq.x;
-      const int nb = (int)ceil(__ddiv_rn(a.noverlap, fq.y));
-      if (nb + kMPad > HS || nb < 1) {
-        if (lane == 0) {
-          atomicOr(a.err, kErrNbins);
-          a.sr[fidx] = 0.f;
-          if (a.qidx) a.qidx[fidx] = 255;
-          if (a.kbin) a.kbin[fidx] = 0xffffffffu;
-          if (a.sbest) a.sbest[fidx] = 0.f;
-          if (a.rbest) a.rbest[fidx] = 0.f;
+    for (int r0 = 0; r0 < wi.f_count; r0 += wact) {  // every warp runs every round (barriers)
+      const int fl = r0 + warp;
+      const bool active = warp < wact && fl < wi.f_count;
+      const int64_t fidx = st.f_off + wi.f_begin + (active ? fl : 0);
+      double f = 0.0, F = 1.0;
+      int nb = 1, g_end = 0;
+      uint32_t k_lo = 0, k_hi = 0, band_q = 0;
+      bool go = active;
+      if (active) {
+        const double2 fq = a.fq[fidx];
+        f = fq.x;
+        nb = (int)ceil(__ddiv_rn(a.noverlap, fq.y));
+        if (nb + kMPad > HS || nb < 1) {
+          if (lane == 0) {
+            atomicOr(a.err, kErrNbins);
+            a.sr[fidx] = 0.f;
+            if (a.qidx) a.qidx[fidx] = 255;
+            if (a.kbin) a.kbin[fidx] = 0xffffffffu;
+            if (a.sbest) a.sbest[fidx] = 0.f;
+            if (a.rbest) a.rbest[fidx] = 0.f;
+          }
+          go = false;
+        } else {
+          if (lane < nq)
+            mtab[lane] = max(1, (int)floor(__dadd_rn(__dmul_rn(__dmul_rn(fq.y, a.E[lane]), (double)nb), 0.5)));
+          for (int i = lane; i < nb + kMPad; i += 32) {
+            hw[i] = 0.f;
+            hy[i] = 0.f;
+            if (SUM == QLP_SUM_COMP) { hwc[i] = 0.f; hyc[i] = 0.f; }
+          }
+          F = __dmul_rn(f, (double)nb);
+          const double D = __ddiv_rn(1.0, F);  // bin duration (days)
+          const double yT = __dmul_rn(st.baseline, F);
+          g_end = (int)floor(yT) + 2;  // edges 0 .. g_end; tau_{g_end} > T
+          // edge step in cells, 2^-56 fixed point (D/h < 2^8)
+          const unsigned long long K = __double2ull_rn(__dmul_rn(__ddiv_rn(D, h), 72057594037927936.0));
+          k_lo = (uint32_t)K;
+          k_hi = (uint32_t)(K >> 32);
+          // guard band in 2^-32 cell units: the FP64 fold's and this fixed-point edge's
+          // errors (2^-20 + 2^-40 T F bins, converted) plus the table's quantisation
+          band_q = (uint32_t)fmin(
+              __dmul_rn(__ddiv_rn(__dmul_rn(9.5367431640625e-07 + 9.094947017729282e-13 * yT, D), h),
+                        4294967296.0) + 64.0, 1073741824.0);
         }
-        continue;
       }
-      if (lane < nq)
-        mtab[lane] = max(1, (int)floor(__dadd_rn(__dmul_rn(__dmul_rn(fq.y, a.E[lane]), (double)nb), 0.5)));
-      for (int i = lane; i < nb + kMPad; i += 32) {
-        hw[i] = 0.f;
-        hy[i] = 0.f;
-        if (SUM == QLP_SUM_COMP) { hwc[i] = 0.f; hyc[i] = 0.f; }
-      }
-      const double F = __dmul_rn(f, (double)nb);
-      const double D = __ddiv_rn(1.0, F);  // bin duration (days)
-      const double yT = __dmul_rn(st.baseline, F);
-      const int g_end = (int)floor(yT) + 2;  // edges 0 .. g_end; tau_{g_end} > T
-      // edge step in cells, 2^-56 fixed point (D/h < 2^8)
-      const unsigned long long K = __double2ull_rn(__dmul_rn(__ddiv_rn(D, h), 72057594037927936.0));
-      const uint32_t k_lo = (uint32_t)K, k_hi = (uint32_t)(K >> 32);
-      // guard band in 2^-32 cell units: the FP64 fold's and this fixed-point edge's
-      // errors (2^-20 + 2^-40 T F bins, converted) plus the table's quantisation
-      const uint32_t band_q = (uint32_t)fmin(
-          __dmul_rn(__ddiv_rn(__dmul_rn(9.5367431640625e-07 + 9.094947017729282e-13 * yT, D), h),
-                    4294967296.0) + 64.0, 1073741824.0);
       __syncwarp();
-
       const bool own = nb >= 31;  // the 31 pieces of one chunk fall in distinct bins
       const int step = 31 % nb;
-      int b = lane % nb;  // bin of this lane's piece in the first chunk
-      for (int g0 = 0; g0 < g_end; g0 += 62) {
-        // two chunks of 31 pieces in flight: edges g0 .. g0+31 and g0+31 .. g0+62
-        const EdgeC c0 = edge_prefix(g0 + lane, k_lo, k_hi, nc, band_q, s_dt, s_loc, s_base, tp, gidx,
-                                     f, nb);
-        const EdgeC c1 = edge_prefix(g0 + 31 + lane, k_lo, k_hi, nc, band_q, s_dt, s_loc, s_base, tp,
-                                     gidx, f, nb);
-        const float2 p0 = edge_piece(c0);
-        const float2 p1 = edge_piece(c1);
-        int b1 = b + step;
-        if (b1 >= nb) b1 -= nb;
-        add_piece<SUM>(hw, hy, hwc, hyc, b, p0, own, lane < 31 && g0 + lane < g_end);
-        add_piece<SUM>(hw, hy, hwc, hyc, b1, p1, own, lane < 31 && g0 + 31 + lane < g_end);
-        b = b1 + step;
-        if (b >= nb) b -= nb;
+
+      for (int w = 0; w < n_win; ++w) {
+        const int cstart = w * st.win_cells;  // first cell owned by window w
+        const int lo = (n_win == 1) ? 0 : max(0, ((cstart - 1) >> 5) << 5);
+        const int hi = (w == n_win - 1) ? nc : min(nc, (w + 1) * st.win_cells + st.win_ovl);
+        const int n_loc = hi - lo + 1;
+        if (s_star != wi.star || s_win != w) {  // block-uniform
+          __syncthreads();
+          uint32_t* d_dt = reinterpret_cast<uint32_t*>(smem);
+          float2* d_loc = reinterpret_cast<float2*>(smem + L.loc);
+          float4* d_base = reinterpret_cast<float4*>(smem + L.base);
+          for (int i = threadIdx.x; i < n_loc; i += NW * 32) {
+            d_dt[i] = a.dt[st.cell_off + lo + i];
+            d_loc[i] = a.loc[st.cell_off + lo + i];
+          }
+          const int b0 = lo >> 5, b1 = hi >> 5;
+          for (int i = threadIdx.x; i <= b1 - b0; i += NW * 32) d_base[i] = a.base[st.base_off + b0 + i];
+          if (threadIdx.x == 0) { s_star = wi.star; s_win = w; }
+          __syncthreads();
+        }
+        if (!go) continue;
+        // pieces [gs, ge) of this window: edges from the first at or after its start
+        const int gs = (w == 0) ? 0 : (int)ceil(__dmul_rn(__dmul_rn((double)cstart, h), F));
+        const int ge = (w == n_win - 1) ? g_end
+                                        : (int)ceil(__dmul_rn(__dmul_rn((double)((w + 1) * st.win_cells), h), F));
+        int b = (gs + lane) % nb;  // bin of this lane's piece in the first chunk
+        for (int g0 = gs; g0 < ge; g0 += 62) {
+          // two chunks of 31 pieces in flight: edges g0 .. g0+31 and g0+31 .. g0+62
+          const EdgeC c0 = edge_prefix(g0 + lane, g0 + lane <= ge, k_lo, k_hi, nc, lo, n_loc, band_q, s_dt,
+                                       s_loc, s_base, tp, gidx, f, nb);
+          const EdgeC c1 = edge_prefix(g0 + 31 + lane, g0 + 31 + lane <= ge, k_lo, k_hi, nc, lo, n_loc,
+                                       band_q, s_dt, s_loc, s_base, tp, gidx, f, nb);
+          const float2 p0 = edge_piece(c0);
+          const float2 p1 = edge_piece(c1);
+          int b1 = b + step;
+          if (b1 >= nb) b1 -= nb;
+          add_piece<SUM>(hw, hy, hwc, hyc, b, p0, own, lane < 31 && g0 + lane < ge);
+          add_piece<SUM>(hw, hy, hwc, hyc, b1, p1, own, lane < 31 && g0 + 31 + lane < ge);
+          b = b1 + step;
+          if (b >= nb) b -= nb;
+        }
       }
-      __syncwarp();
-      sweep_store<SUM>(hw, hy, hwc, hyc, mtab, nq, nb, lane, fidx, a.sr, a.qidx, a.kbin, a.sbest,
-                       a.rbest);
+      if (go) {
+        __syncwarp();
+        sweep_store<SUM>(hw, hy, hwc, hyc, mtab, nq, nb, lane, fidx, a.sr, a.qidx, a.kbin, a.sbest,
+                         a.rbest);
+      }
     }
   }
   if (!done && threadIdx.x == 0) atomicOr(a.err, kErrQueueBound);

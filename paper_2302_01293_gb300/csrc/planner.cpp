@@ -164,10 +164,14 @@ void plan_one(const qlp_bls_params& p, const double* t, const double* y, const d
       s.cells_ok = true;
       s.cell_h = h;
       s.n_cells = prev + 1;
-      double work = 0.0;
-      for (size_t k = 0; k < s.freqs.size(); ++k)
-        work += std::floor(s.baseline * s.freqs[k] * std::ceil(p.noverlap / s.qmins[k])) + 3.0;
+      double work = 0.0, dmax = 0.0;
+      for (size_t k = 0; k < s.freqs.size(); ++k) {
+        const double nb = std::ceil(p.noverlap / s.qmins[k]);
+        work += std::floor(s.baseline * s.freqs[k] * nb) + 3.0;
+        dmax = std::max(dmax, 1.0 / (s.freqs[k] * nb));
+      }
       s.cells_work = work;
+      s.bin_dmax = dmax;
     }
   }
 }

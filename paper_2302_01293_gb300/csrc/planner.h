@@ -28,6 +28,7 @@ struct StarPlanHost {
   double cell_h = 0.0;
   int64_t n_cells = 0;
   double cells_work = 0.0;         // sum over f of the bin edges across the baseline
+  double bin_dmax = 0.0;           // longest bin duration 1/(f nbins) over the grid (days)
   int32_t grid_k0 = -1;            // coarse grid: bin index of the first (lowest) frequency
 };
 

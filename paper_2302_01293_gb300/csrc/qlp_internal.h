@@ -35,6 +35,13 @@ struct StarDev {
   int64_t cell_off;    // first entry in the per-cell arrays (n_cells + 1 entries)
   int64_t base_off;    // first entry in the per-32-cell base array
   int64_t cpre_off;    // first entry in the prefix-sum array (N + 1 entries)
+  // time windows of the cell table when it does not fit in shared memory at once:
+  // window w owns cells [w win_cells, (w+1) win_cells) and stages them from the
+  // 32-aligned cell below its start to win_ovl cells past its end
+  int32_t n_win;
+  int32_t win_cells;
+  int32_t win_ovl;
+  int32_t win_cap;     // cells the shared table holds (one window, or the whole table)
 };
 
 constexpr int32_t kMethodPoints = 0;

@@ -40,7 +40,7 @@ class CParams(ctypes.Structure):
                 ("chunk_freqs", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("n_threads", ctypes.c_int32), ("tile_points", ctypes.c_int32),
                 ("method", ctypes.c_int32), ("grid_mode", ctypes.c_int32),
-                ("coarse_bins", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("coarse_bins", ctypes.c_int32), ("cell_window", ctypes.c_int32),
                 ("coarse_pmin", ctypes.c_double), ("coarse_pmax", ctypes.c_double)]
 
 
@@ -65,7 +65,7 @@ class Params:
     method: int = 0
     grid_mode: int = 0
     coarse_bins: int = 4096
-    reserved0: int = 0
+    cell_window: int = 0
     coarse_pmin: float = 0.1
     coarse_pmax: float = 400.0
 
@@ -101,7 +101,7 @@ def lib():
             L.qlp_bls_plan.restype = ctypes.c_int
             L.qlp_bls_plan_info.argtypes = [_vp, _P(_i64), _vp, _vp, _vp, _P(_i64), _P(_d)]
             L.qlp_bls_plan_info.restype = ctypes.c_int
-            L.qlp_bls_plan_stats.argtypes = [_vp, _P(_d), _P(_d), _P(_d), _P(_i32)]
+            L.qlp_bls_plan_stats.argtypes = [_vp, _P(_d), _P(_d), _P(_d), _P(_i32), _P(_i32)]
             L.qlp_bls_plan_stats.restype = ctypes.c_int
             L.qlp_bls_search.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp]
             L.qlp_bls_search.restype = ctypes.c_int
@@ -232,11 +232,12 @@ class Plan:
         self.star_status = np.zeros(self.n_stars, np.int32)
         _check(L.qlp_bls_plan_info(self._h, None, _np_ptr(self.freq_offsets), _np_ptr(self.freqs),
                                    _np_ptr(self.star_status), None, None), "qlp_bls_plan_info")
-        wp, wc, ed, nc = _d(), _d(), _d(), _i32()
+        wp, wc, ed, nc, nw = _d(), _d(), _d(), _i32(), _i32()
         _check(L.qlp_bls_plan_stats(self._h, ctypes.byref(wp), ctypes.byref(wc), ctypes.byref(ed),
-                                    ctypes.byref(nc)), "qlp_bls_plan_stats")
+                                    ctypes.byref(nc), ctypes.byref(nw)), "qlp_bls_plan_stats")
         self.work_points, self.work_cells, self.edges = wp.value, wc.value, ed.value
         self.n_cell_stars = int(nc.value)
+        self.n_windowed = int(nw.value)
 
     def alloc_outputs(self):
         import torch

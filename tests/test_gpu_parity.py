@@ -76,6 +76,24 @@ def test_multi_sector(gpu_lib):
     _check_batch(b, qlpbls.Params())
 
 
+def test_multi_sector_cell_path_in_windows(gpu_lib):
+    # tables of 3-4 contiguous sectors exceed shared memory: searched window by window
+    b = synth.multi_sector(n_stars=3, seed=4, max_sectors=4)
+    g, _ = _check_batch(b, qlpbls.Params(method=qlpbls.METHOD_CELLS))
+    assert g["plan"].n_cell_stars == 3 and g["plan"].n_windowed >= 2
+
+
+@pytest.mark.parametrize("window", [64, 700, 4000])
+@pytest.mark.parametrize("summ", [qlpbls.SUM_PLAIN, qlpbls.SUM_COMP])
+def test_cell_windows_forced(gpu_lib, window, summ):
+    # forced short windows: many window boundaries per frequency, windows shorter
+    # than one bin (64 cells) and a ragged last window
+    b = synth.uneven_single_sector(n_stars=3, seed=23)
+    g, _ = _check_batch(b, qlpbls.Params(method=qlpbls.METHOD_CELLS, cell_window=window,
+                                         sum_mode=summ))
+    assert g["plan"].n_windowed == 3
+
+
 def test_tiny_ragged_and_rejected_stars(gpu_lib):
     good = synth.tiny_batch(n_stars=5, seed=15, n_min=33, n_max=97)
     # append stars the planner must reject: unsorted, one point, NaN-only
