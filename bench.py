@@ -167,13 +167,13 @@ def learned_comparison(args):
         del plan, out
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        best_l, coarse, _ = learned.search_learned(test, net, k=32)
+        best_l, _ = learned.search_learned(test, net, k=32)
         torch.cuda.synchronize()
         t_learned = time.perf_counter() - t0
     rf = learned.recovered(best_full, test)
     rl = learned.recovered(best_l, test)
-    best_a, _, _ = learned.search_learned(test, net, k=32,
-                                          bins=learned.propose_without_network(coarse, 32))
+    coarse = learned.CoarseStage(test)
+    best_a = learned.search_with_bins(test, coarse, learned.propose_without_network(coarse, 32))
     ra = learned.recovered(best_a, test)
     n = test.n_stars
     return {"workload": f"{n} held-out stars, 1-4 sectors at 200 s, 50 % injected "

@@ -368,6 +368,43 @@ int qlp_cnn_train_step(qlp_cnn_t* net, const void* x0, const float* labels, int3
 int qlp_cnn_loss(qlp_cnn_t* net, float* loss_host, int32_t* err_host, void* stream);
 const char* qlp_cnn_last_error(void);
 
+/*
+ * qlp_cnn_shape  the max_batch and len the network was created with.
+ * qlp_cnn_save   checkpoint to a file: the parameters, Adam's two moment vectors
+ *                and its step count (FP32 little-endian after a short header);
+ *                synchronises `stream`. QLP_ERR_ARG when the file cannot be written.
+ * qlp_cnn_load   restore a checkpoint written by qlp_cnn_save into a network of
+ *                any max_batch and len (the parameters do not depend on them);
+ *                training resumes where it stopped. QLP_ERR_ARG for a missing file
+ *                or one of another layout; the network is unchanged then.
+ */
+int qlp_cnn_shape(const qlp_cnn_t* net, int32_t* max_batch, int32_t* len);
+int qlp_cnn_save(const qlp_cnn_t* net, const char* path, void* stream);
+int qlp_cnn_load(qlp_cnn_t* net, const char* path, void* stream);
+
+/*
+ * qlp_bls_search_learned -- the learned period proposal (an addition to the
+ * paper: it narrows the full-grid search of Sec. 2.1 to the periods a network
+ * proposes). From host light curves (arguments as for qlp_bls_plan):
+ *   1. the coarse spectrum: plan with grid_mode 1 (p's coarse_* fields), search,
+ *      S/N with its trend record (Sec. 2.2 item 1), the network input tensor;
+ *   2. the network's logits and each star's top-k valid coarse bins;
+ *   3. frequency windows [1/P(k_b + half_width), 1/P(k_b - half_width)] around each
+ *      proposed bin k_b, P(x) = coarse_pmin (coarse_pmax/coarse_pmin)^(x/(coarse_bins-1));
+ *   4. the paper's grid (grid_mode 0) restricted to those windows, searched, and
+ *      scored with the coarse trend and sigma_SR.
+ * net must have len == coarse_bins. best_host (n_stars records, required) gets the
+ * best candidate of step 4 (f_idx indexes the windowed grid; a star with no grid
+ * frequency in its windows gets f_idx -1 and QLP_STAR_EMPTY_GRID). bins_host
+ * (int32 [n_stars][k], optional) gets the proposed bins, -1 past a star's last
+ * valid bin. Device scratch is allocated on `stream` and freed before return; the
+ * call synchronises `stream`. QLP_ERR_DEVICE when a kernel raised an error flag.
+ */
+int qlp_bls_search_learned(const qlp_bls_params* p, int32_t n_stars, const int64_t* offsets,
+                           const double* t, const double* y, const double* dy, const double* rho,
+                           const double* rstar, qlp_cnn_t* net, int32_t k, double half_width,
+                           void* stream, qlp_bls_best* best_host, int32_t* bins_host);
+
 /* Static description of a return code. */
 const char* qlp_strerror(int code);
 

@@ -31,6 +31,13 @@ int cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);                 \
   } while (0)
 
+}  // namespace
+
+// Records a CUDA failure for qlp_last_cuda_error (other translation units).
+int qlp::record_cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+
+namespace {
+
 template <typename T>
 int dev_alloc(T** p, size_t count) {
   *p = nullptr;

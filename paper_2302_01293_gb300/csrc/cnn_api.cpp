@@ -183,6 +183,64 @@ int qlp_cnn_set_params(qlp_cnn_t* n, const float* host, void* stream) {
   return QLP_OK;
 }
 
+int qlp_cnn_shape(const qlp_cnn_t* n, int32_t* max_batch, int32_t* len) {
+  if (!n) return QLP_ERR_ARG;
+  if (max_batch) *max_batch = n->max_batch;
+  if (len) *len = n->len;
+  return QLP_OK;
+}
+
+// Checkpoint file: 8-byte tag, int32 parameter count, int32 zero, int64 Adam step,
+// then the FP32 parameters, Adam's first and second moments (little-endian).
+static const char kTag[8] = {'Q', 'L', 'P', 'C', 'N', 'N', '0', '1'};
+
+int qlp_cnn_save(const qlp_cnn_t* n, const char* path, void* stream) {
+  if (!n || !path) return QLP_ERR_ARG;
+  std::vector<float> buf((size_t)kNParams * 3);
+  CK(cudaMemcpyAsync(buf.data(), n->params, sizeof(float) * kNParams, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  CK(cudaMemcpyAsync(buf.data() + kNParams, n->m, sizeof(float) * kNParams, cudaMemcpyDeviceToHost,
+                     (cudaStream_t)stream));
+  CK(cudaMemcpyAsync(buf.data() + 2 * (size_t)kNParams, n->v, sizeof(float) * kNParams, cudaMemcpyDeviceToHost,
+                     (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) { g_err = std::string("cannot open ") + path; return QLP_ERR_ARG; }
+  const int32_t hdr[2] = {kNParams, 0};
+  const int64_t step = n->step;
+  bool ok = std::fwrite(kTag, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+            std::fwrite(&step, sizeof(step), 1, f) == 1 &&
+            std::fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) { g_err = std::string("write failed: ") + path; return QLP_ERR_ARG; }
+  return QLP_OK;
+}
+
+int qlp_cnn_load(qlp_cnn_t* n, const char* path, void* stream) {
+  if (!n || !path) return QLP_ERR_ARG;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) { g_err = std::string("cannot open ") + path; return QLP_ERR_ARG; }
+  char tag[8];
+  int32_t hdr[2];
+  int64_t step = 0;
+  std::vector<float> buf((size_t)kNParams * 3);
+  bool ok = std::fread(tag, 1, 8, f) == 8 && std::memcmp(tag, kTag, 8) == 0 &&
+            std::fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == kNParams &&
+            std::fread(&step, sizeof(step), 1, f) == 1 && step >= 0 &&
+            std::fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  std::fclose(f);
+  if (!ok) { g_err = std::string("not a checkpoint of this network: ") + path; return QLP_ERR_ARG; }
+  CK(cudaMemcpyAsync(n->params, buf.data(), sizeof(float) * kNParams, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+  CK(cudaMemcpyAsync(n->m, buf.data() + kNParams, sizeof(float) * kNParams, cudaMemcpyHostToDevice,
+                     (cudaStream_t)stream));
+  CK(cudaMemcpyAsync(n->v, buf.data() + 2 * (size_t)kNParams, sizeof(float) * kNParams, cudaMemcpyHostToDevice,
+                     (cudaStream_t)stream));
+  n->step = step;
+  const int rc = repack(n, stream);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return QLP_OK;
+}
+
 int qlp_cnn_get_params(const qlp_cnn_t* n, float* host, float* grads_host, void* stream) {
   if (!n) return QLP_ERR_ARG;
   if (host) CK(cudaMemcpyAsync(host, n->params, sizeof(float) * kNParams, cudaMemcpyDeviceToHost, (cudaStream_t)stream));

@@ -3,6 +3,7 @@
 
 #include <cstdint>
 
+#include <cuda_runtime_api.h>
 #include <vector_types.h>
 
 #include "../../include/qlp_bls.h"
@@ -171,6 +172,7 @@ int launch_prep_cells(const PrepCellsArgs& a, void* stream);
 int launch_cells(const CellArgs& a, int sum_mode, int warps, int blocks, size_t smem, void* stream);
 // bytes of shared memory before the histograms of the cell kernel for a star with
 // ncs cells (incl. sentinel) and nw warps
+int record_cuda_error(cudaError_t e, const char* what);
 uint32_t cells_hist_offset(int ncs, int nw);
 int cells_blocks_per_sm(int sum_mode, int warps, size_t smem);
 int bls_max_smem_per_block();

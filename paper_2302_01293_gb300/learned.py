@@ -6,7 +6,8 @@ against the coarse spectrum's trend and sigma_SR.
 
 Every numeric step runs in the CUDA library (coarse plan, search, S/N, input
 tensor, CNN, top-K, windowed plan, search, S/N); this module only sequences the
-calls and turns bin indices into frequency windows.
+calls and turns bin indices into frequency windows; the same sequence runs
+inside the library behind qlp_bls_search_learned.
 """
 from __future__ import annotations
 
@@ -104,14 +105,21 @@ def propose_without_network(coarse: CoarseStage, k: int, stream=None):
 
 
 def search_learned(batch, net, k: int = 32, base: qlpbls.Params | None = None, stream=None,
-                   bins=None):
-    """The learned path end to end; returns (best records, coarse stage, proposed bins)."""
-    coarse = CoarseStage(batch, base, stream=stream)
-    if bins is None:
-        bins = propose(net, coarse.x0, k, stream=stream)
-    win = windows_from_bins(bins.cpu().numpy(), coarse.params)
+                   half_width: float = 1.0):
+    """The learned path end to end in one library call (qlp_bls_search_learned);
+    returns (best records, proposed bins [n_stars, k])."""
+    return qlpbls.search_learned(batch.offsets, batch.t, batch.y, batch.dy, batch.rho, batch.rstar,
+                                 net, k, half_width, coarse_params(base), stream=stream)
+
+
+def search_with_bins(batch, coarse: CoarseStage, bins, base: qlpbls.Params | None = None, stream=None,
+                     half_width: float = 1.0):
+    """Windows around given coarse bins, refined and scored with the coarse trend:
+    the last two stages of the learned path for proposals made elsewhere."""
+    win = windows_from_bins(bins.cpu().numpy() if hasattr(bins, "cpu") else np.asarray(bins),
+                            coarse.params, half_width)
     plan, out = refine(batch, win, coarse.trend, base, stream=stream)
-    return plan.best_host(out), coarse, bins
+    return plan.best_host(out)
 
 
 def train(net, batches, epochs: int = 2, lr: float = 1e-3, pos_weight: float = 64.0, stream=None):

@@ -155,6 +155,15 @@ def lib():
             L.qlp_bls_coarse_tensor.restype = ctypes.c_int
             L.qlp_cnn_topk.argtypes = [_vp, _vp, _i32, _i32, _i32, _vp, _vp]
             L.qlp_cnn_topk.restype = ctypes.c_int
+            L.qlp_cnn_shape.argtypes = [_vp, _P(_i32), _P(_i32)]
+            L.qlp_cnn_shape.restype = ctypes.c_int
+            L.qlp_cnn_save.argtypes = [_vp, ctypes.c_char_p, _vp]
+            L.qlp_cnn_save.restype = ctypes.c_int
+            L.qlp_cnn_load.argtypes = [_vp, ctypes.c_char_p, _vp]
+            L.qlp_cnn_load.restype = ctypes.c_int
+            L.qlp_bls_search_learned.argtypes = [_P(CParams), _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                                 _i32, ctypes.c_double, _vp, _vp, _vp]
+            L.qlp_bls_search_learned.restype = ctypes.c_int
             L.qlp_strerror.argtypes = [ctypes.c_int]
             L.qlp_strerror.restype = ctypes.c_char_p
             L.qlp_last_cuda_error.argtypes = []
@@ -429,6 +438,12 @@ class CNN:
         self._chk(rc, "qlp_cnn_loss")
         return float(v.value)
 
+    def save(self, path: str, stream=None):
+        self._chk(lib().qlp_cnn_save(self._h, os.fsencode(path), _stream_ptr(stream)), "qlp_cnn_save")
+
+    def load(self, path: str, stream=None):
+        self._chk(lib().qlp_cnn_load(self._h, os.fsencode(path), _stream_ptr(stream)), "qlp_cnn_load")
+
     def close(self):
         if self._h and self._h.value:
             lib().qlp_cnn_destroy(self._h)
@@ -450,3 +465,20 @@ def topk(logits, x0, k: int, stream=None):
                             _stream_ptr(stream))
     _check(rc, "qlp_cnn_topk")
     return out
+
+
+def search_learned(offsets, t, y, dy, rho, rstar, net: CNN, k: int = 32, half_width: float = 1.0,
+                   params: Params | None = None, stream=None):
+    """qlp_bls_search_learned: host light curves in, the learned path's best
+    candidate per star and the proposed coarse bins [n_stars, k] out."""
+    L = lib()
+    offsets, t, y, dy, rho, rstar = _host_inputs(offsets, t, y, dy, rho, rstar)
+    n_stars = int(offsets.shape[0] - 1)
+    cp = (params or Params()).to_c()
+    best = np.zeros(max(n_stars, 1), BEST_DTYPE)
+    bins = np.zeros((max(n_stars, 1), int(k)), np.int32)
+    rc = L.qlp_bls_search_learned(ctypes.byref(cp), n_stars, _np_ptr(offsets), _np_ptr(t), _np_ptr(y),
+                                  _np_ptr(dy), _np_ptr(rho), _np_ptr(rstar), net._h, int(k),
+                                  float(half_width), _stream_ptr(stream), _np_ptr(best), _np_ptr(bins))
+    _check(rc, "qlp_bls_search_learned")
+    return best[:n_stars], bins[:n_stars]

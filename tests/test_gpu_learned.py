@@ -120,8 +120,41 @@ def test_learned_path_recall(gpu_lib):
     out = plan.search()
     plan.snr(out)
     rf = learned.recovered(plan.best_host(out), test)
-    best_l, _, _ = learned.search_learned(test, net, k=32)
+    best_l, bins = learned.search_learned(test, net, k=32)
     rl = learned.recovered(best_l, test)
     assert rf.sum() >= 40
     assert (rl & rf).sum() >= 0.97 * rf.sum()
+    # the library's one-call path equals the same stages sequenced from Python
+    cs = learned.CoarseStage(test)
+    bins_py = learned.propose(net, cs.x0, 32).cpu().numpy()
+    assert np.array_equal(bins, bins_py)
+    best_py = learned.search_with_bins(test, cs, bins_py)
+    assert np.array_equal(best_py["f_idx"], best_l["f_idx"])
+    np.testing.assert_array_equal(best_py["snr"], best_l["snr"])
     net.close()
+
+
+def test_cnn_checkpoint_roundtrip(gpu_lib, tmp_path):
+    import torch
+    b = synth.proposal_set(64, seed=61)
+    cs = learned.CoarseStage(b)
+    lab = learned.labels(b, cs.params, "cuda")
+    net = qlpbls.CNN(max_batch=32, length=4096, seed=1)
+    learned.train(net, [(cs.x0, lab)], epochs=1, lr=1e-3)
+    path = str(tmp_path / "net.ckpt")
+    net.save(path)
+    other = qlpbls.CNN(max_batch=16, length=4096, seed=2)
+    other.load(path)
+    assert np.array_equal(net.params(), other.params())
+    x = cs.x0[:16].contiguous()
+    assert torch.equal(net.forward(x), other.forward(x))
+    # training resumes identically: same Adam moments and step
+    learned.train(net, [(cs.x0[:16].contiguous(), lab[:16].contiguous())], epochs=1, lr=1e-3)
+    learned.train(other, [(cs.x0[:16].contiguous(), lab[:16].contiguous())], epochs=1, lr=1e-3)
+    assert np.array_equal(net.params(), other.params())
+    bad = tmp_path / "bad.ckpt"
+    bad.write_bytes(b"not a checkpoint")
+    with pytest.raises(qlpbls.QlpError):
+        other.load(str(bad))
+    net.close()
+    other.close()
