@@ -4,10 +4,13 @@ Workload (default): 4,096 uneven single-sector stars at 200-s cadence (7,000-11,
 points each after random 0.5-2 d gaps), rho log-U(0.1, 10) g/cm^3, R* log-U(0.5, 3),
 white noise sigma log-U(2e-4, 1e-2), 30 % with injected boxes; seeded synthetic data.
 
-One step = one pass of the device path over the whole batch: point preparation
-(weights, double-float split), the persistent BLS search over every (star, trial
+One step = one pass of the device path over the whole batch: the preparation
+kernels (weights, prefix sums and cell tables; double-float points for stars
+folded point by point), the persistent BLS search over every (star, trial
 frequency), and the S/N / best-candidate kernel, with the plan (grid) built once
-beforehand and the light curves resident in HBM. `e2e` times the public host-buffer
+beforehand and the light curves resident in HBM. The launch settings come from
+the library's autotuner (run once, untimed), and each step replays two CUDA
+graphs (search, S/N) captured from the plan. `e2e` times the public host-buffer
 call qlp_bls_run_host (plan + upload + search + S/N + download) on the same batch.
 
 Metric: BLS point-frequency evaluations per second (sum over stars of N_s * n_f,s
@@ -50,6 +53,7 @@ def _args():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--learned-train", type=int, default=8192)
     ap.add_argument("--learned-eval", type=int, default=512)
+    ap.add_argument("--tune-sample", type=int, default=512)
     return ap.parse_args()
 
 
@@ -253,13 +257,20 @@ def main():
             dist.barrier()
 
     batch = synth.uneven_single_sector(n_stars=args.stars, seed=args.seed + 1000 * rank)
-    params = qlpbls.Params()
     stream = torch.cuda.current_stream()
+    # launch settings from the autotuner (timed on a sample of the batch; untimed here)
+    t0 = time.perf_counter()
+    params, _ = qlpbls.autotune(batch.offsets, batch.t, batch.y, batch.dy, batch.rho, batch.rstar,
+                                qlpbls.Params(), sample_stars=args.tune_sample)
+    t_tune = time.perf_counter() - t0
     plan = qlpbls.Plan(batch.offsets, batch.t, batch.y, batch.dy, batch.rho, batch.rstar, params)
     out = plan.alloc_outputs()
+    # the step as two CUDA graphs: the search (prep + persistent kernels), the S/N
+    plan.graph_capture(out, parts=1)
+    plan.graph_capture(out, parts=2)
     for _ in range(max(3, args.warmup)):
-        plan.search(out)
-        plan.snr(out)
+        plan.graph_launch(1)
+        plan.graph_launch(2)
     flags = plan.device_status()
     if flags:
         raise RuntimeError(f"device flags {flags}")
@@ -275,9 +286,9 @@ def main():
     e_start.record(stream)
     for i in range(args.steps):
         k_ev[i][0].record(stream)
-        plan.search(out)
+        plan.graph_launch(1)
         k_ev[i][1].record(stream)
-        plan.snr(out)
+        plan.graph_launch(2)
     e_end.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -357,6 +368,11 @@ def main():
                            "points": plan.n_points, "trial_freqs": plan.n_freq_total,
                            "point_freq_per_gpu": plan.work, "bin_edges": plan.edges,
                            "cell_path_stars": plan.n_cell_stars, "phase_mode": "DF",
+                           "autotuned": {"warps_per_block": params.warps_per_block,
+                                         "chunk_freqs": params.chunk_freqs,
+                                         "cell_window": params.cell_window,
+                                         "sample_stars": args.tune_sample, "seconds": t_tune},
+                           "launch": "CUDA graphs (search, S/N) per step",
                            "sum_mode": "COMP" if params.sum_mode else "PLAIN",
                            "l2": "inputs larger than L2 (light curves "
                            f"{plan.n_points * 24 / 1e6:.0f} MB FP64)", "parallelism": f"replicas x{world}"},

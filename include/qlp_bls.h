@@ -263,6 +263,24 @@ int qlp_bls_device_status(qlp_bls_plan_t* plan, void* stream, int32_t* flags);
 void qlp_bls_plan_destroy(qlp_bls_plan_t* plan);
 
 /*
+ * qlp_bls_graph_capture -- record calls of this plan, with these output buffers
+ * (device, as for qlp_bls_search / qlp_bls_snr), as a CUDA graph kept by the
+ * plan: parts = 1 one qlp_bls_search, 2 one qlp_bls_snr, 3 the search followed by
+ * the S/N (snr and best may be NULL for parts = 1). Each value of parts has its
+ * own slot; capturing again replaces that slot's graph. Nothing runs on the GPU
+ * during the capture, which uses a private stream of the plan.
+ * qlp_bls_graph_launch -- replay the graph of slot `parts` on `stream` (any
+ * stream, including the legacy default one): the same work and results as the
+ * recorded calls, from one launch call. QLP_ERR_ARG if that slot is empty.
+ * The output buffers must stay allocated while a graph may run; replays on
+ * different streams must not overlap (they share the plan's work queues).
+ */
+int qlp_bls_graph_capture(qlp_bls_plan_t* plan, int32_t parts, float* sr, uint8_t* qidx,
+                          uint32_t* phase_bin, float* s_best, float* r_best, float* snr,
+                          qlp_bls_best* best);
+int qlp_bls_graph_launch(qlp_bls_plan_t* plan, int32_t parts, void* stream);
+
+/*
  * qlp_bls_star_grid -- host only, no device work: the Sec. 2.1 plan of one star,
  * exactly as qlp_bls_plan builds it (same code), for inspection and checks.
  *  n, t, y, dy   the star's points (host double[n]); rho as for qlp_bls_plan.

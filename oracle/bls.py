@@ -100,6 +100,16 @@ def bls_star(plan) -> StarBLS:
     return StarBLS(sr, jb, kb, sb, rb)
 
 
+def restrict(plan, idx):
+    """The same star plan with only the trial frequencies plan.freqs[idx] (each
+    frequency's search is independent of the others, Sec. 2.1), so that long
+    multi-sector stars can be checked on sampled frequencies."""
+    import dataclasses
+    idx = np.asarray(idx, np.int64)
+    return dataclasses.replace(plan, freqs=plan.freqs[idx], qmin=plan.qmin[idx],
+                               nbins=plan.nbins[idx], m=plan.m[idx])
+
+
 def box_value(plan, fidx: int, j: int, k: int) -> float:
     """Residue of box (j, k) at frequency index fidx (-1 when the window is invalid)."""
     w, d, _ = weights(plan.y, plan.dy)

@@ -53,7 +53,7 @@ class Params:
     pmin_aR: float = 2.0
     gap_days: float = 27.4
     rho_default: float = 1.41
-    nbins_cap: int = 16384
+    nbins_cap: int = 8192
     # learned proposal (not in the paper): coarse log-period grid
     grid_mode: int = 0
     coarse_bins: int = 4096

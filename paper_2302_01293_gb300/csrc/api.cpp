@@ -79,9 +79,6 @@ struct qlp_bls_plan {
   // cell path launch shape
   int c_warps = 8;
   int c_blocks = 0;
-  int c_hist_stride = 0;
-  int c_cells_cap = 0;
-  uint32_t c_loc_off = 0, c_base_off = 0, c_hist_off = 0;
   size_t c_smem = 0;
   int32_t c_items = 0;
   int32_t n_cell_stars = 0;
@@ -102,10 +99,20 @@ struct qlp_bls_plan {
   float4* d_base = nullptr;
   int32_t* d_gidx = nullptr;
   int32_t* d_ctl = nullptr;       // [0] per-point queue head, [1] cell queue head, [2] error flags
+  // search + S/N captured as one CUDA graph (qlp_bls_graph_capture)
+  // slot parts-1: parts = 1 search, 2 S/N, 3 both
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph[3] = {};
+  cudaGraphExec_t gexec[3] = {};
 };
 
 static void free_plan(qlp_bls_plan_t* pl) {
   if (!pl) return;
+  for (int i = 0; i < 3; ++i) {
+    if (pl->gexec[i]) cudaGraphExecDestroy(pl->gexec[i]);
+    if (pl->graph[i]) cudaGraphDestroy(pl->graph[i]);
+  }
+  if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
   cudaFree(pl->d_stars);
   cudaFree(pl->d_fq);
   cudaFree(pl->d_items);
@@ -724,5 +731,36 @@ int qlp_bls_star_grid(const qlp_bls_params* pin, int64_t n, const double* t, con
 }
 
 void qlp_bls_plan_destroy(qlp_bls_plan_t* pl) { free_plan(pl); }
+
+int qlp_bls_graph_capture(qlp_bls_plan_t* pl, int32_t parts, float* sr, uint8_t* qidx, uint32_t* phase_bin,
+                          float* s_best, float* r_best, float* snr, qlp_bls_best* best) {
+  if (!pl || parts < 1 || parts > 3) return QLP_ERR_ARG;
+  if (pl->f_off.back() > 0 && (!sr || !qidx || !phase_bin || !s_best || !r_best)) return QLP_ERR_ARG;
+  if ((parts & 2) && ((pl->f_off.back() > 0 && !snr) || (pl->n_stars > 0 && !best))) return QLP_ERR_ARG;
+  if (!pl->cap_stream) QLP_CK(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
+  const int slot = parts - 1;
+  if (pl->gexec[slot]) { cudaGraphExecDestroy(pl->gexec[slot]); pl->gexec[slot] = nullptr; }
+  if (pl->graph[slot]) { cudaGraphDestroy(pl->graph[slot]); pl->graph[slot] = nullptr; }
+  QLP_CK(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = QLP_OK;
+  if (parts & 1) rc = qlp_bls_search(pl, pl->cap_stream, sr, qidx, phase_bin, s_best, r_best);
+  if (rc == QLP_OK && (parts & 2)) rc = qlp_bls_snr(pl, pl->cap_stream, sr, qidx, phase_bin, s_best, r_best, snr, best);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(pl->cap_stream, &g);
+  if (rc != QLP_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  pl->graph[slot] = g;
+  QLP_CK(cudaGraphInstantiate(&pl->gexec[slot], g, 0));
+  return QLP_OK;
+}
+
+int qlp_bls_graph_launch(qlp_bls_plan_t* pl, int32_t parts, void* stream) {
+  if (!pl || parts < 1 || parts > 3 || !pl->gexec[parts - 1]) return QLP_ERR_ARG;
+  QLP_CK(cudaGraphLaunch(pl->gexec[parts - 1], (cudaStream_t)stream));
+  return QLP_OK;
+}
 
 }  // extern "C"

@@ -75,6 +75,10 @@ class Params:
             setattr(c, f.name, getattr(self, f.name))
         return c
 
+    @classmethod
+    def from_c(cls, c: CParams) -> "Params":
+        return cls(**{f.name: getattr(c, f.name) for f in dataclasses.fields(cls)})
+
 
 class QlpError(RuntimeError):
     pass
@@ -164,6 +168,13 @@ def lib():
             L.qlp_bls_search_learned.argtypes = [_P(CParams), _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                                  _i32, ctypes.c_double, _vp, _vp, _vp]
             L.qlp_bls_search_learned.restype = ctypes.c_int
+            L.qlp_bls_autotune.argtypes = [_P(CParams), _i32, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp,
+                                           _P(CParams), _P(_i32)]
+            L.qlp_bls_autotune.restype = ctypes.c_int
+            L.qlp_bls_graph_capture.argtypes = [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+            L.qlp_bls_graph_capture.restype = ctypes.c_int
+            L.qlp_bls_graph_launch.argtypes = [_vp, _i32, _vp]
+            L.qlp_bls_graph_launch.restype = ctypes.c_int
             L.qlp_strerror.argtypes = [ctypes.c_int]
             L.qlp_strerror.restype = ctypes.c_char_p
             L.qlp_last_cuda_error.argtypes = []
@@ -309,6 +320,18 @@ class Plan:
             _check(rc, "qlp_bls_device_status")
         return int(flags.value)
 
+    def graph_capture(self, out, parts: int = 3):
+        """qlp_bls_graph_capture: record the search (parts 1), the S/N (2) or both
+        (3) into `out` (from alloc_outputs) as a CUDA graph of this plan."""
+        _check(lib().qlp_bls_graph_capture(self._h, int(parts), out["sr"].data_ptr(), out["qidx"].data_ptr(),
+                                           out["kbin"].data_ptr(), out["s"].data_ptr(), out["r"].data_ptr(),
+                                           out["snr"].data_ptr(), out["best"].data_ptr()),
+               "qlp_bls_graph_capture")
+        return out
+
+    def graph_launch(self, parts: int = 3, stream=None):
+        _check(lib().qlp_bls_graph_launch(self._h, int(parts), _stream_ptr(stream)), "qlp_bls_graph_launch")
+
     def best_host(self, out) -> np.ndarray:
         raw = out["best"].cpu().numpy()[: self.n_stars * BEST_DTYPE.itemsize]
         return raw.view(BEST_DTYPE).copy()
@@ -345,6 +368,21 @@ def run_host(offsets, t, y, dy, rho=None, rstar=None, params: Params | None = No
                             int(sr_capacity), _np_ptr(best), ctypes.byref(nft))
     _check(rc, "qlp_bls_run_host")
     return dict(best=best[:n_stars], sr=sr, snr=snr, n_freq_total=int(nft.value))
+
+
+def autotune(offsets, t, y, dy, rho=None, rstar=None, params: Params | None = None,
+             sample_stars: int = 256, stream=None):
+    """qlp_bls_autotune: (tuned Params, whether the process cache answered)."""
+    L = lib()
+    offsets, t, y, dy, rho, rstar = _host_inputs(offsets, t, y, dy, rho, rstar)
+    cp = (params or Params()).to_c()
+    out = CParams()
+    cached = _i32()
+    rc = L.qlp_bls_autotune(ctypes.byref(cp), int(offsets.shape[0] - 1), _np_ptr(offsets), _np_ptr(t),
+                            _np_ptr(y), _np_ptr(dy), _np_ptr(rho), _np_ptr(rstar), int(sample_stars),
+                            _stream_ptr(stream), ctypes.byref(out), ctypes.byref(cached))
+    _check(rc, "qlp_bls_autotune")
+    return Params.from_c(out), bool(cached.value)
 
 
 def star_grid(t, y, dy, rho=float("nan"), params: Params | None = None):

@@ -148,3 +148,38 @@ def test_full_batch_sampled(gpu_lib):
     rng = np.random.default_rng(0)
     stars = sorted(rng.choice(4096, 12, replace=False).tolist())
     _check_batch(b, qlpbls.Params(), stars=stars)
+
+
+def test_graph_replay_matches_oracle(gpu_lib):
+    # search + S/N captured as CUDA graphs (together, and one graph each), replayed
+    # on the current stream
+    import torch
+    b = synth.uneven_single_sector(n_stars=4, seed=31)
+    plan = qlpbls.Plan(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar)
+    out = plan.graph_capture(plan.alloc_outputs())
+    plan.graph_capture(out, parts=1)
+    plan.graph_capture(out, parts=2)
+    for launches in ([3], [3], [1, 2]):
+        for v in out.values():
+            v.fill_(0)
+        for parts in launches:
+            plan.graph_launch(parts)
+        torch.cuda.synchronize()
+        g = {k: v.cpu().numpy() for k, v in out.items() if k != "best"}
+        best = plan.best_host(out)
+        for s in range(b.n_stars):
+            pl, ores = oracle_star(b, s)
+            sl = plan.star_slice(s)
+            compare_spectrum(pl, ores, g, sl, label=f"graph star {s}")
+            compare_snr(pl, ores, g, sl, best[s], label=f"graph star {s}")
+    assert plan.device_status() == 0
+
+
+def test_autotune_choice_is_cached_and_exact(gpu_lib):
+    b = synth.uneven_single_sector(n_stars=96, seed=32)
+    tuned, cached = qlpbls.autotune(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar, sample_stars=48)
+    again, cached2 = qlpbls.autotune(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar, sample_stars=48)
+    assert not cached and cached2 and again == tuned
+    assert tuned.warps_per_block in (0, 8, 16) and tuned.chunk_freqs >= 0
+    # the tuned settings change speed only: parity on a few stars of the batch
+    _check_batch(b.subset(range(3)), tuned)

@@ -1,0 +1,79 @@
+"""Precision study on multi-sector stars (up to 13 contiguous sectors, AR(1) red
+noise): the phase reduction x = t'f in FP64, in double-float (hi/lo FP32 with an
+FP64 re-fold near bin edges) and in plain FP32 on the point path, and the cell
+path's fixed-point edges, each against the FP64 oracle on sampled trial
+frequencies (evenly spaced, plus every mode's own SR maximum).
+
+Reported per mode: the largest relative SR error and the agreement of the
+per-frequency box (duration index j, start bin k) and of the sampled maximum.
+FP64, double-float and the cell path must meet the parity tolerances; plain FP32
+is reported only (its bins move once t'f reaches ~10^4 cycles). Set
+QLP_PRECISION_REPORT to a file name to get the table as JSON."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import bls as ob
+from paper_2302_01293_gb300 import qlpbls
+from parity import SR_RTOL, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+MODES = {
+    "cell path (fixed-point edges, FP64 ties)": qlpbls.Params(method=qlpbls.METHOD_CELLS),
+    "points, FP64 phase": qlpbls.Params(method=qlpbls.METHOD_POINTS, phase_mode=qlpbls.PHASE_FP64),
+    "points, double-float phase": qlpbls.Params(method=qlpbls.METHOD_POINTS, phase_mode=qlpbls.PHASE_DF),
+    "points, FP32 phase": qlpbls.Params(method=qlpbls.METHOD_POINTS, phase_mode=qlpbls.PHASE_FP32),
+}
+EXACT = {k for k in MODES if "FP32" not in k}
+
+
+def test_multi_sector_precision(gpu_lib):
+    b = synth.multi_sector(n_stars=8, seed=7, max_sectors=13)
+    runs = {name: run_gpu(b, p, with_snr=False) for name, p in MODES.items()}
+    stats = {name: {"max_sr_rel": 0.0, "box_agree": 0, "box_near_tie": 0, "sampled": 0,
+                    "best_agree": 0} for name in MODES}
+    max_cycles = 0.0
+    for s in range(b.n_stars):
+        t, y, dy = b.star(s)
+        pl = oracle.plan_star(t, y, dy, float(b.rho[s]), float(b.rstar[s]))
+        nf = pl.freqs.shape[0]
+        max_cycles = max(max_cycles, pl.baseline * pl.freqs[-1])
+        sl = {name: g["plan"].star_slice(s) for name, g in runs.items()}
+        idx = set(np.linspace(0, nf - 1, 96).astype(int).tolist())
+        for name, g in runs.items():
+            assert np.array_equal(g["plan"].freqs[sl[name]], pl.freqs)
+            idx.add(int(np.argmax(g["sr"][sl[name]])))
+        idx = np.array(sorted(idx))
+        sub = ob.restrict(pl, idx)
+        o = ob.bls_star(sub)
+        for name, g in runs.items():
+            st = stats[name]
+            sr = g["sr"][sl[name]][idx].astype(np.float64)
+            q = g["qidx"][sl[name]][idx].astype(np.int64)
+            k = g["kbin"][sl[name]][idx].view(np.uint32).astype(np.int64)
+            rel = np.abs(sr - o.sr) / np.maximum(o.sr, 1e-300)
+            st["max_sr_rel"] = max(st["max_sr_rel"], float(rel.max()))
+            same = (q == o.j) & (k == o.k)
+            st["box_agree"] += int(same.sum())
+            st["sampled"] += len(idx)
+            for i in np.nonzero(~same)[0]:
+                v = ob.box_value(sub, int(i), int(q[i]), int(k[i]))
+                if v >= o.sr[i] * (1 - SR_RTOL):
+                    st["box_near_tie"] += 1
+            st["best_agree"] += int(np.argmax(sr) == np.argmax(o.sr))
+    report = {"stars": b.n_stars, "points": int(b.offsets[-1]), "max_cycles_t_f": max_cycles,
+              "modes": stats}
+    print(json.dumps(report, indent=1))
+    if os.environ.get("QLP_PRECISION_REPORT"):
+        with open(os.environ["QLP_PRECISION_REPORT"], "w") as f:
+            json.dump(report, f, indent=1)
+    for name in EXACT:
+        st = stats[name]
+        assert st["max_sr_rel"] <= SR_RTOL, (name, st)
+        assert st["box_agree"] + st["box_near_tie"] == st["sampled"], (name, st)
+        assert st["best_agree"] == b.n_stars, (name, st)

@@ -160,3 +160,17 @@ def test_single_star_recovers_injection():
     # mid-transit within a bin of the truth, depth within the binning dilution
     assert abs(best["t0"] - b.t0[0]) < 2 * best["period"] / best["nbins"]
     assert 0.6 * 2e-3 < best["depth"] < 1.2 * 2e-3
+
+
+def test_restricted_plan_equals_full_search_at_those_frequencies():
+    import synth
+    from oracle import bls as ob
+    b = synth.tiny_batch(n_stars=2, seed=8)
+    for s in range(2):
+        t, y, dy = b.star(s)
+        pl = oracle.plan_star(t, y, dy, float(b.rho[s]), 1.0)
+        full = oracle.bls_star(pl)
+        idx = np.arange(0, pl.freqs.shape[0], 7)
+        sub = ob.bls_star(ob.restrict(pl, idx))
+        assert np.array_equal(sub.sr, full.sr[idx])
+        assert np.array_equal(sub.j, full.j[idx]) and np.array_equal(sub.k, full.k[idx])
