@@ -52,8 +52,9 @@ def _args():
     ap.add_argument("--cpu-sample-stars", type=int, default=256)
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--learned-train", type=int, default=8192)
-    ap.add_argument("--learned-eval", type=int, default=512)
+    ap.add_argument("--learned-eval", type=int, default=2048)
     ap.add_argument("--tune-sample", type=int, default=512)
+    ap.add_argument("--no-tune", action="store_true", help="library defaults instead of the autotuner")
     return ap.parse_args()
 
 
@@ -158,6 +159,8 @@ def learned_comparison(args):
     losses = learned.train(net, batches, epochs=4, lr=3e-4, pos_weight=16.0)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
+    peaks, _ = _peaks()
+    cnn = cnn_throughput(net, batches[0][0], batches[0][1], peaks.get("bf16_tflops", 1900.0))
     test = synth.proposal_set(args.learned_eval, seed=999)
     # warm both paths once (library load, allocator), then time
     for timed in (False, True):
@@ -189,7 +192,61 @@ def learned_comparison(args):
             "recall_coarse_snr_topk_without_network": float((ra & rf).sum() / max(rf.sum(), 1)),
             "stars_per_hour_full": n / t_full * 3600.0,
             "stars_per_hour_learned": n / t_learned * 3600.0,
-            "speedup": t_full / t_learned}
+            "speedup": t_full / t_learned, "cnn": cnn}
+
+
+# CNN FLOPs per input bin (kernel 9, 64 channels): conv 2->64, four 64->64, 64->1
+CNN_FWD_FLOP_PER_BIN = 2 * 9 * (2 * 64 + 4 * 64 * 64 + 64)
+CONV64_FLOP_PER_BIN = 2 * 9 * 64 * 64
+# training step: forward, input gradients of layers 6..2 (not of layer 1), all
+# weight gradients (as many FLOPs as the forward)
+CNN_TRAIN_FLOP_PER_BIN = 2 * CNN_FWD_FLOP_PER_BIN + 2 * 9 * (4 * 64 * 64 + 64)
+
+
+def cnn_throughput(net, x0, labels, peak_tflops):
+    """Device time of the network's kernels on one full batch (CUDA events): the
+    tensor-core conv64 alone, the forward pass, and one training step."""
+    import torch
+    from paper_2302_01293_gb300 import qlpbls
+    B, L = net.max_batch, net.length
+    x0 = x0[:B].contiguous()
+    labels = labels[:B].contiguous()
+    g = torch.Generator(device="cpu").manual_seed(5)
+    x = (torch.randn(B, L, 64, generator=g) * 0.5).to(torch.bfloat16).cuda()
+    w = (torch.randn(9, 64, 64, generator=g) * 0.05).cuda()
+    bias = torch.zeros(64, device="cuda")
+    wp = qlpbls.pack_w64(w)
+    y = torch.empty_like(x)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps * 1e-3
+
+    t_conv = timed(lambda: qlpbls.conv64(x, wp, bias, None, True, out=y, err=err), 50)
+    t_fwd = timed(lambda: net.forward(x0), 20)
+    params = net.params()
+    t_train = timed(lambda: net.train_step(x0, labels, 16.0, 0.0), 10)
+    net.set_params(params)  # the timed steps used lr = 0 but advanced Adam's state
+    assert int(err.item()) == 0
+    conv_tf = B * L * CONV64_FLOP_PER_BIN / t_conv / 1e12
+    return {"batch": B, "bins": L,
+            "conv64": {"bound": "tensor", "achieved": conv_tf, "peak": peak_tflops, "unit": "TFLOP/s",
+                       "frac": conv_tf / peak_tflops, "ms": t_conv * 1e3,
+                       "algorithmic": f"{B} x {L} bins x {CONV64_FLOP_PER_BIN} FLOP (BF16 in, FP32 acc)"},
+            "forward_tflops": B * L * CNN_FWD_FLOP_PER_BIN / t_fwd / 1e12, "forward_ms": t_fwd * 1e3,
+            "train_step_tflops": B * L * CNN_TRAIN_FLOP_PER_BIN / t_train / 1e12,
+            "train_step_ms": t_train * 1e3,
+            "peak_source": "bf16_tflops (burst) of MEASURED_PEAKS.json"}
 
 
 def cpu_baseline(batch, n_sample: int):
@@ -260,8 +317,10 @@ def main():
     stream = torch.cuda.current_stream()
     # launch settings from the autotuner (timed on a sample of the batch; untimed here)
     t0 = time.perf_counter()
-    params, _ = qlpbls.autotune(batch.offsets, batch.t, batch.y, batch.dy, batch.rho, batch.rstar,
-                                qlpbls.Params(), sample_stars=args.tune_sample)
+    params = qlpbls.Params()
+    if not args.no_tune:
+        params, _ = qlpbls.autotune(batch.offsets, batch.t, batch.y, batch.dy, batch.rho, batch.rstar,
+                                    params, sample_stars=args.tune_sample)
     t_tune = time.perf_counter() - t0
     plan = qlpbls.Plan(batch.offsets, batch.t, batch.y, batch.dy, batch.rho, batch.rstar, params)
     out = plan.alloc_outputs()
@@ -371,7 +430,8 @@ def main():
                            "autotuned": {"warps_per_block": params.warps_per_block,
                                          "chunk_freqs": params.chunk_freqs,
                                          "cell_window": params.cell_window,
-                                         "sample_stars": args.tune_sample, "seconds": t_tune},
+                                         "sample_stars": None if args.no_tune else args.tune_sample,
+                                         "seconds": t_tune},
                            "launch": "CUDA graphs (search, S/N) per step",
                            "sum_mode": "COMP" if params.sum_mode else "PLAIN",
                            "l2": "inputs larger than L2 (light curves "

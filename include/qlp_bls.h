@@ -206,10 +206,13 @@ int qlp_bls_snr(qlp_bls_plan_t* plan, void* stream, const float* sr, const uint8
 
 /*
  * Learned-proposal variants (not in the paper):
- * qlp_bls_plan_windows -- as qlp_bls_plan (grid_mode 0 only), keeping only the
- *   grid frequencies inside the star's windows: star s owns windows
+ * qlp_bls_plan_windows -- as qlp_bls_plan (grid_mode 0 only), with trial
+ *   frequencies only inside the star's windows: star s owns windows
  *   win_offsets[s] .. win_offsets[s+1]-1 of win_flo / win_fhi (host doubles, 1/day,
- *   inclusive). A star with no frequency inside its windows gets QLP_STAR_EMPTY_GRID.
+ *   inclusive). Overlapping or touching windows are merged; in each merged window,
+ *   clipped to [1/Pmax, 1/Pmin], the Sec. 2.1 spacing f <- f + q_min(f)/(spp T)
+ *   is walked from the window's low edge while f stays inside it. A star with no
+ *   frequency inside its windows gets QLP_STAR_EMPTY_GRID.
  * qlp_bls_snr_trend -- qlp_bls_snr with an optional per-star trend record
  *   (QLP_TREND_DOUBLES doubles: node count, sigma_SR, median, bin centres, bin
  *   medians) written to trend_out, or, when trend_in is given, the S/N computed
@@ -285,13 +288,16 @@ int qlp_bls_graph_launch(qlp_bls_plan_t* plan, int32_t parts, void* stream);
  * exactly as qlp_bls_plan builds it (same code), for inspection and checks.
  *  n, t, y, dy   the star's points (host double[n]); rho as for qlp_bls_plan.
  *  status, pmin, pmax, t_ref, baseline   outputs, each may be NULL.
+ *  n_win, win_flo, win_fhi  optional frequency windows as for qlp_bls_plan_windows
+ *                (win_flo NULL = the whole grid).
  *  freqs, qmins  host double[capacity] trial frequencies and their q_min (may be NULL).
  *  n_f_out       number of trial frequencies (required).
  * Returns QLP_ERR_ARG when freqs/qmins are given and capacity < *n_f_out (the
  * scalars and *n_f_out are still written).
  */
 int qlp_bls_star_grid(const qlp_bls_params* p, int64_t n, const double* t, const double* y,
-                      const double* dy, double rho, int32_t* status, double* pmin, double* pmax,
+                      const double* dy, double rho, int64_t n_win, const double* win_flo,
+                      const double* win_fhi, int32_t* status, double* pmin, double* pmax,
                       double* t_ref, double* baseline, double* freqs, double* qmins,
                       int64_t capacity, int64_t* n_f_out);
 

@@ -121,8 +121,33 @@ def coarse_grid(pmin: float, pmax: float, p: Params):
     return out, k0
 
 
-def in_windows(f: float, windows) -> bool:
-    return any(lo <= f <= hi for lo, hi in windows)
+def merge_windows(windows):
+    """Union of frequency intervals [lo, hi]: sorted, with overlapping or touching
+    intervals joined (empty or NaN intervals dropped)."""
+    out = []
+    for lo, hi in sorted((float(a), float(b)) for a, b in windows if a <= b):
+        if out and lo <= out[-1][1]:
+            out[-1][1] = max(out[-1][1], hi)
+        else:
+            out.append([lo, hi])
+    return out
+
+
+def window_grid(windows, pmin: float, pmax: float, baseline: float, rho_kg: float, p: Params) -> List[float]:
+    """Full-resolution grid inside frequency windows (the learned proposal's
+    refinement, not in the paper): in each merged window, clipped to
+    [1/Pmax, 1/Pmin], the Sec. 2.1 spacing f <- f + q_min(f) / (spp * T) walked
+    from the window's low edge while f stays inside it."""
+    fmin, fmax = 1.0 / pmax, 1.0 / pmin
+    denom = p.samples_per_peak * baseline
+    out = []
+    for lo, hi in merge_windows(windows):
+        f = max(lo, fmin)
+        end = min(hi, fmax)
+        while f <= end:
+            out.append(f)
+            f = f + q_min(f, rho_kg, p) / denom
+    return out
 
 
 def nbins_of(qmin: float, p: Params) -> int:
@@ -185,9 +210,10 @@ def plan_star(t, y, dy, rho, rstar, p: Params = Params(), windows=None) -> StarP
     if p.grid_mode == 1:
         freqs, k0 = coarse_grid(pmin, pmax, p)
     else:
-        freqs = freq_grid(pmin, pmax, baseline, rho_kg, p)
         if windows is not None:
-            freqs = [f for f in freqs if in_windows(f, windows)]
+            freqs = window_grid(windows, pmin, pmax, baseline, rho_kg, p)
+        else:
+            freqs = freq_grid(pmin, pmax, baseline, rho_kg, p)
     qm = [q_min(f, rho_kg, p) for f in freqs]
     nb = [nbins_of(q, p) for q in qm]
     m = [m_of(q, b, p) for q, b in zip(qm, nb)]

@@ -707,16 +707,23 @@ int qlp_bls_run_host(const qlp_bls_params* p, int32_t n_stars, const int64_t* of
 }
 
 int qlp_bls_star_grid(const qlp_bls_params* pin, int64_t n, const double* t, const double* y,
-                      const double* dy, double rho, int32_t* status, double* pmin, double* pmax,
+                      const double* dy, double rho, int64_t n_win, const double* win_flo,
+                      const double* win_fhi, int32_t* status, double* pmin, double* pmax,
                       double* t_ref, double* baseline, double* freqs, double* qmins,
                       int64_t capacity, int64_t* n_f_out) {
   if (!n_f_out || n < 0 || (n > 0 && (!t || !y || !dy))) return QLP_ERR_ARG;
+  if (win_flo && (n_win < 0 || (n_win > 0 && !win_fhi))) return QLP_ERR_ARG;
   qlp_bls_params p;
   if (pin) p = *pin; else qlp_bls_params_default(&p);
   const int rc = check_params(p);
   if (rc) return rc;
+  if (win_flo && p.grid_mode != 0) return QLP_ERR_ARG;
   StarPlanHost h;
-  plan_one(p, t, y, dy, n, rho, &h);
+  Windows w;
+  w.lo = win_flo;
+  w.hi = win_fhi;
+  w.n = n_win;
+  plan_one(p, t, y, dy, n, rho, &h, win_flo ? &w : nullptr);
   if (status) *status = h.status;
   if (pmin) *pmin = h.pmin;
   if (pmax) *pmax = h.pmax;

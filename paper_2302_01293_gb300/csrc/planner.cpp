@@ -17,6 +17,7 @@
 //  * bins: nbins(f) = ceil(noverlap / q_min(f)).
 #include <algorithm>
 #include <cmath>
+#include <utility>
 #include <cstdint>
 #include <thread>
 #include <vector>
@@ -107,12 +108,6 @@ void plan_one(const qlp_bls_params& p, const double* t, const double* y, const d
   s.pmin = pmin_of(s.rho_kg, p);
   s.pmax = pmax_of(s.tp.data(), m, p);
   if (!(s.baseline > 0.0) || !(s.pmin < s.pmax)) { s.status = QLP_STAR_EMPTY_GRID; return; }
-  auto keep = [&](double f) {
-    if (!win) return true;
-    for (int64_t i = 0; i < win->n; ++i)
-      if (f >= win->lo[i] && f <= win->hi[i]) return true;
-    return false;
-  };
   auto add = [&](double f) {
     const double q = q_min_of(f, s.rho_kg, p);
     s.freqs.push_back(f);
@@ -130,12 +125,36 @@ void plan_one(const qlp_bls_params& p, const double* t, const double* y, const d
       if (s.grid_k0 < 0) s.grid_k0 = k;
       add(1.0 / per);
     }
+  } else if (win) {
+    // windows: the spacing rule walked from each merged window's low edge,
+    // clipped to [1/Pmax, 1/Pmin]
+    std::vector<std::pair<double, double>> w;
+    for (int64_t i = 0; i < win->n; ++i)
+      if (win->lo[i] <= win->hi[i]) w.emplace_back(win->lo[i], win->hi[i]);
+    std::sort(w.begin(), w.end());
+    std::vector<std::pair<double, double>> merged;
+    for (const auto& iv : w) {
+      if (!merged.empty() && iv.first <= merged.back().second)
+        merged.back().second = std::max(merged.back().second, iv.second);
+      else
+        merged.push_back(iv);
+    }
+    const double fmin = 1.0 / s.pmax, fmax = 1.0 / s.pmin;
+    const double denom = p.samples_per_peak * s.baseline;
+    for (const auto& iv : merged) {
+      double f = std::max(iv.first, fmin);
+      const double end = std::min(iv.second, fmax);
+      while (f <= end) {
+        add(f);
+        f = f + q_min_of(f, s.rho_kg, p) / denom;
+      }
+    }
   } else {
     const double fmax = 1.0 / s.pmin;
     const double denom = p.samples_per_peak * s.baseline;
     double f = 1.0 / s.pmax;
     while (f <= fmax) {
-      if (keep(f)) add(f);
+      add(f);
       f = f + q_min_of(f, s.rho_kg, p) / denom;
     }
   }

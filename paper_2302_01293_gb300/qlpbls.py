@@ -118,8 +118,9 @@ def lib():
             L.qlp_bls_device_status.restype = ctypes.c_int
             L.qlp_bls_plan_destroy.argtypes = [_vp]
             L.qlp_bls_plan_destroy.restype = None
-            L.qlp_bls_star_grid.argtypes = [_P(CParams), _i64, _vp, _vp, _vp, _d, _P(_i32), _P(_d),
-                                            _P(_d), _P(_d), _P(_d), _vp, _vp, _i64, _P(_i64)]
+            L.qlp_bls_star_grid.argtypes = [_P(CParams), _i64, _vp, _vp, _vp, _d, _i64, _vp, _vp,
+                                            _P(_i32), _P(_d), _P(_d), _P(_d), _P(_d), _vp, _vp, _i64,
+                                            _P(_i64)]
             L.qlp_bls_star_grid.restype = ctypes.c_int
             L.qlp_bls_search_static.argtypes = [_P(CParams), _i32, _vp, _vp, _vp, _d, _i32, _vp,
                                                 _vp, _vp, _vp, _vp, _vp, _vp, _vp]
@@ -385,15 +386,21 @@ def autotune(offsets, t, y, dy, rho=None, rstar=None, params: Params | None = No
     return Params.from_c(out), bool(cached.value)
 
 
-def star_grid(t, y, dy, rho=float("nan"), params: Params | None = None):
-    """qlp_bls_star_grid: the host plan of one star (no device work)."""
+def star_grid(t, y, dy, rho=float("nan"), params: Params | None = None, windows=None):
+    """qlp_bls_star_grid: the host plan of one star (no device work); windows is an
+    optional list of (f_lo, f_hi) frequency windows."""
     L = lib()
     t = np.ascontiguousarray(t, np.float64)
     y = np.ascontiguousarray(y, np.float64)
     dy = np.ascontiguousarray(dy, np.float64)
     cp = (params or Params()).to_c()
+    wlo = whi = None
+    if windows is not None:
+        w = np.asarray(windows, np.float64).reshape(-1, 2)
+        wlo, whi = np.ascontiguousarray(w[:, 0]), np.ascontiguousarray(w[:, 1])
     st, pmin, pmax, tref, base, nf = _i32(), _d(), _d(), _d(), _d(), _i64()
     args = [ctypes.byref(cp), t.shape[0], _np_ptr(t), _np_ptr(y), _np_ptr(dy), float(rho),
+            0 if wlo is None else wlo.shape[0], _np_ptr(wlo), _np_ptr(whi),
             ctypes.byref(st), ctypes.byref(pmin), ctypes.byref(pmax), ctypes.byref(tref),
             ctypes.byref(base)]
     _check(L.qlp_bls_star_grid(*args, None, None, 0, ctypes.byref(nf)), "qlp_bls_star_grid")
@@ -492,6 +499,28 @@ class CNN:
             self.close()
         except Exception:
             pass
+
+
+def pack_w64(w, transpose: bool = False, stream=None):
+    """qlp_cnn_pack_w64: FP32 weights [9][64][64] (device) -> the tensor-core
+    operand layout (device uint8 [73728])."""
+    import torch
+    wpack = torch.empty(73728, dtype=torch.uint8, device=w.device)
+    _check(lib().qlp_cnn_pack_w64(w.data_ptr(), wpack.data_ptr(), int(transpose), _stream_ptr(stream)),
+           "qlp_cnn_pack_w64")
+    return wpack
+
+
+def conv64(x, wpack, bias=None, mask=None, relu: bool = True, out=None, err=None, stream=None):
+    """qlp_cnn_conv64: y = conv(x) (+ bias, ReLU) for BF16 x [B][L][64] on the tensor cores."""
+    import torch
+    y = out if out is not None else torch.empty_like(x)
+    err = err if err is not None else torch.zeros(1, dtype=torch.int32, device=x.device)
+    _check(lib().qlp_cnn_conv64(x.data_ptr(), wpack.data_ptr(), bias.data_ptr() if bias is not None else None,
+                                mask.data_ptr() if mask is not None else None, y.data_ptr(), int(x.shape[0]),
+                                int(x.shape[1]), int(relu), err.data_ptr(), _stream_ptr(stream)),
+           "qlp_cnn_conv64")
+    return y
 
 
 def topk(logits, x0, k: int, stream=None):

@@ -112,3 +112,16 @@ def test_coarse_grid_is_bit_identical_to_oracle(seed):
         g = qlpbls.star_grid(t, y, dy, float(b.rho[s]), qlpbls.Params(grid_mode=1))
         o = oracle.plan_star(t, y, dy, float(b.rho[s]), 1.0, op.Params(grid_mode=1))
         assert np.array_equal(g["freqs"], o.freqs) and np.array_equal(g["qmins"], o.qmin)
+
+
+def test_window_grid_is_bit_identical_to_oracle():
+    b = synth.uneven_single_sector(n_stars=2, seed=3)
+    rng = np.random.default_rng(4)
+    for s in range(b.n_stars):
+        t, y, dy = b.star(s)
+        lo = np.sort(rng.uniform(0.08, 2.5, 12))
+        wins = [(x, x * 1.004) for x in lo] + [(lo[0], lo[0] * 1.001)]
+        g = qlpbls.star_grid(t, y, dy, float(b.rho[s]), windows=wins)
+        o = oracle.plan_star(t, y, dy, float(b.rho[s]), 1.0, windows=wins)
+        assert g["status"] == o.status
+        assert np.array_equal(g["freqs"], o.freqs) and np.array_equal(g["qmins"], o.qmin)

@@ -181,12 +181,41 @@ def test_coarse_grid_log_spacing_and_clipping():
     assert len(full) == 4096 and 1.0 / full[-1] == pytest.approx(0.1) and 1.0 / full[0] == pytest.approx(400.0)
 
 
-def test_windows_select_a_subset_of_the_grid():
+def test_window_grid_spacing_and_edges():
+    # inside each window: starts at the window's low edge, steps q_min(f)/(spp T)
+    # (q_min in SI units here), stops before leaving the window
+    import synth
+    b = synth.single_star()
+    t, y, dy = b.star(0)
+    p = op.Params()
+    wins = [(0.27, 0.2712), (1.0, 1.004)]
+    sub = oracle.plan_star(t, y, dy, 1.41, 1.0, windows=wins)
+    T = sub.baseline
+    f = np.asarray(sub.freqs)
+    for lo, hi in wins:
+        fw = f[(f >= lo) & (f <= hi)]
+        assert fw[0] == lo and len(fw) > 3
+        step = np.array([_qmin_si(x, 1.41, p) / (p.samples_per_peak * T) for x in fw])
+        np.testing.assert_allclose(np.diff(fw), step[:-1], rtol=1e-9)
+        assert fw[-1] + step[-1] > hi * (1 - 1e-12)
+    assert len(f) == sum(((f >= lo) & (f <= hi)).sum() for lo, hi in wins)
+
+
+def test_window_grid_merges_and_clips():
     import synth
     b = synth.single_star()
     t, y, dy = b.star(0)
     full = oracle.plan_star(t, y, dy, 1.41, 1.0)
-    wins = [(0.27, 0.2712), (1.0, 1.004)]
-    sub = oracle.plan_star(t, y, dy, 1.41, 1.0, windows=wins)
-    expect = [f for f in full.freqs if any(lo <= f <= hi for lo, hi in wins)]
-    assert sub.freqs.tolist() == expect and len(expect) > 0
+    fmin, fmax = full.freqs[0], 1.0 / full.pmin
+    # one window over the whole range (and beyond) is the plain grid
+    whole = oracle.plan_star(t, y, dy, 1.41, 1.0, windows=[(0.0, 100.0)])
+    assert whole.freqs.tolist() == full.freqs.tolist()
+    # overlapping and touching windows act as their union; empty or reversed ones vanish
+    a = oracle.plan_star(t, y, dy, 1.41, 1.0, windows=[(0.5, 0.52), (0.51, 0.53), (0.53, 0.54), (0.9, 0.8)])
+    u = oracle.plan_star(t, y, dy, 1.41, 1.0, windows=[(0.5, 0.54)])
+    assert a.freqs.tolist() == u.freqs.tolist() and a.freqs[0] == 0.5
+    # a window below 1/Pmax starts at 1/Pmax, one above 1/Pmin is empty
+    c = oracle.plan_star(t, y, dy, 1.41, 1.0, windows=[(fmin / 2, fmin * 1.01)])
+    assert c.freqs[0] == fmin
+    e = oracle.plan_star(t, y, dy, 1.41, 1.0, windows=[(fmax * 1.01, fmax * 2)])
+    assert e.status == op.ST_EMPTY_GRID
