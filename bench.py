@@ -55,6 +55,8 @@ def _args():
     ap.add_argument("--learned-eval", type=int, default=2048)
     ap.add_argument("--tune-sample", type=int, default=512)
     ap.add_argument("--no-tune", action="store_true", help="library defaults instead of the autotuner")
+    ap.add_argument("--method", type=int, default=0, choices=[0, 1, 2],
+                    help="0 per star the cheaper path, 1 fold every point, 2 cell path where possible")
     return ap.parse_args()
 
 
@@ -317,7 +319,7 @@ def main():
     stream = torch.cuda.current_stream()
     # launch settings from the autotuner (timed on a sample of the batch; untimed here)
     t0 = time.perf_counter()
-    params = qlpbls.Params()
+    params = qlpbls.Params(method=args.method)
     if not args.no_tune:
         params, _ = qlpbls.autotune(batch.offsets, batch.t, batch.y, batch.dy, batch.rho, batch.rstar,
                                     params, sample_stars=args.tune_sample)
@@ -404,8 +406,13 @@ def main():
         smem_gbs = None
         kernel = "bls_kernel (search-call duration: includes prep)"
         unit_note = f"{plan.work:.4e} point-freq x {FP32_OPS_PER_EVAL} ops"
+    # DRAM traffic of one cells_kernel launch: ncu capture of the same kernel on
+    # 1,024 stars of this workload (423.0 MB), scaled by points to the default batch
+    traffic = None
+    if cells_dominant and args.stars == 4096 and args.seed == 2 and params.sum_mode == 1:
+        traffic = 423.0e6 * plan.n_points / 10638874
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "TFLOP/s",
-                "frac": achieved / peak_ops, "traffic": None, "kernel": kernel,
+                "frac": achieved / peak_ops, "traffic": traffic, "kernel": kernel,
                 "algorithmic": unit_note,
                 "peak_source": f"152 SMs x 128 FP32 lanes x {sm_clock/1e6:.0f} MHz ({src} max clock)",
                 "smem": None if smem_gbs is None else

@@ -352,6 +352,17 @@ int qlp_bls_search_static(const qlp_bls_params* p, int32_t n, const double* tp, 
  *   device int32 that receives QLP error bits (16 = a tensor-core wait hit its bound).
  */
 int qlp_cnn_pack_w64(const float* w, void* wpack, int32_t transpose, void* stream);
+/*
+ * qlp_cnn_conv64_wgrad -- weight and bias gradients of one 64 -> 64 layer on the
+ * tensor cores: out[(kk 64 + co) 64 + ci] = sum_p dy[p][co] x[p + kk - 4][ci]
+ * (zero outside each sample), out[9 64 64 + co] = sum_p dy[p][co]; dy and x BF16
+ * [batch][len][64] (device), len a multiple of 128, out FP32 [36928] (device).
+ * workspace: device FP32 of qlp_cnn_wgrad64_workspace(batch, len) floats.
+ * Device wait timeouts set bit 16 in *err (device int32).
+ */
+int64_t qlp_cnn_wgrad64_workspace(int32_t batch, int32_t len);
+int qlp_cnn_conv64_wgrad(const void* dy, const void* x, float* workspace, float* out, int32_t batch,
+                         int32_t len, int32_t* err, void* stream);
 int qlp_cnn_conv64(const void* x, const void* wpack, const float* bias, const void* mask, void* y,
                    int32_t batch, int32_t len, int32_t relu, int32_t* err, void* stream);
 

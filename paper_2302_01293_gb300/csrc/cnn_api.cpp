@@ -21,12 +21,13 @@ int launch_conv_out(const void* a5, const float* w6, const float* b6, float* log
 int launch_bce(const float* logit, const float* label, float* dlogit, float* loss, int n, float pw, void* s);
 int launch_conv_out_bwd(const float* dlogit, const float* w6, const void* a5, void* da5, int batch, int len,
                         void* s);
-int launch_dw64(const void* dy, const void* x, float* partial, float* out, int batch, int len, void* s);
+int launch_wgrad64(const void* dy, const void* x, float* partial, float* out, int32_t* err, int batch, int len,
+                   void* s);
 int launch_dw_small(const void* dy, int dy_is_f32, const void* x, float* partial, float* out, int batch,
                     int len, int n_co, int n_ci, void* s);
 int launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps,
                 float c1, float c2, void* s);
-int dw64_parts(int batch, int len);
+int wgrad64_parts(int batch, int len);
 int dw_small_parts(int batch, int len);
 }  // namespace qlp
 
@@ -128,7 +129,7 @@ int qlp_cnn_create(int32_t max_batch, int32_t len, uint64_t seed, qlp_cnn_t** ou
   n->max_batch = max_batch;
   n->len = len;
   const size_t pos = (size_t)max_batch * len;
-  const size_t parts = std::max((size_t)dw64_parts(max_batch, len) * (kW64 + kCh),
+  const size_t parts = std::max((size_t)wgrad64_parts(max_batch, len) * (kW64 + kCh),
                                 (size_t)dw_small_parts(max_batch, len) * (kW1 + kCh));
   bool ok = cudaMalloc(&n->params, sizeof(float) * kNParams) == cudaSuccess &&
             cudaMalloc(&n->grads, sizeof(float) * kNParams) == cudaSuccess &&
@@ -275,7 +276,7 @@ int qlp_cnn_backward(qlp_cnn_t* n, const void* x0, const float* labels, int32_t 
   CKL(launch_dw_small(n->dlogit, 1, n->act[5], n->partial, n->grads + kOffW6, batch, L, 1, kCh, stream));
   CKL(launch_conv_out_bwd(n->dlogit, n->params + kOffW6, n->act[5], n->gact[5], batch, L, stream));
   for (int k = 5; k >= 2; --k) {
-    CKL(launch_dw64(n->gact[k], n->act[k - 1], n->partial, n->grads + off_w(k), batch, L, stream));
+    CKL(launch_wgrad64(n->gact[k], n->act[k - 1], n->partial, n->grads + off_w(k), n->err, batch, L, stream));
     CKL(launch_conv64(n->gact[k], n->pack_b[k - 2], nullptr, n->act[k - 1], n->gact[k - 1], n->err, batch, L, 0,
                       stream));
   }
@@ -307,6 +308,18 @@ int qlp_cnn_loss(qlp_cnn_t* n, float* loss_host, int32_t* err_host, void* stream
   CK(cudaMemcpy(&e, n->err, sizeof(int32_t), cudaMemcpyDeviceToHost));
   if (err_host) *err_host = e;
   return e ? QLP_ERR_DEVICE : QLP_OK;
+}
+
+int64_t qlp_cnn_wgrad64_workspace(int32_t batch, int32_t len) {
+  if (batch <= 0 || len <= 0 || len % 128 != 0) return 0;
+  return (int64_t)wgrad64_parts(batch, len) * (kW64 + kCh);
+}
+
+int qlp_cnn_conv64_wgrad(const void* dy, const void* x, float* workspace, float* out, int32_t batch, int32_t len,
+                         int32_t* err, void* stream) {
+  if (!dy || !x || !workspace || !out || !err || batch <= 0 || len <= 0 || len % 128 != 0) return QLP_ERR_ARG;
+  CKL(launch_wgrad64(dy, x, workspace, out, err, batch, len, stream));
+  return QLP_OK;
 }
 
 int qlp_cnn_pack_w64(const float* w, void* wpack, int32_t transpose, void* stream) {

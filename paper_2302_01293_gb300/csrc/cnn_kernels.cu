@@ -59,29 +59,73 @@ __device__ __forceinline__ void stage_tile(unsigned char* abuf, const __nv_bfloa
   }
 }
 
+// Epilogue of one tile from TMEM accumulator columns [col, col + 64): row =
+// 32 warp + lane; bias, ReLU or the backward mask, BF16 store.
+__device__ __forceinline__ void conv_epilogue(const ConvTcArgs& a, const float* s_bias, uint32_t tmem,
+                                              uint32_t col, int t, int tiles_per_sample) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = t / tiles_per_sample;
+  const int l = (t % tiles_per_sample) * kTileM + 32 * warp + lane;
+  const size_t off = ((size_t)b * a.len + l) * kC;
+  __nv_bfloat16* yrow = a.y + off;
+  const __nv_bfloat16* mrow = a.mask ? a.mask + off : nullptr;
+#pragma unroll
+  for (int c0 = 0; c0 < kC; c0 += 16) {
+    float v[16];
+    tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + col + (uint32_t)c0, v);
+    uint32_t mw[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    if (mrow) {
+      const uint4 m0 = reinterpret_cast<const uint4*>(mrow + c0)[0];
+      const uint4 m1 = reinterpret_cast<const uint4*>(mrow + c0)[1];
+      mw[0] = m0.x; mw[1] = m0.y; mw[2] = m0.z; mw[3] = m0.w;
+      mw[4] = m1.x; mw[5] = m1.y; mw[6] = m1.z; mw[7] = m1.w;
+    }
+    uint32_t ow[8];
+#pragma unroll
+    for (int i = 0; i < 16; i += 2) {
+      float z0 = v[i] + s_bias[c0 + i], z1 = v[i + 1] + s_bias[c0 + i + 1];
+      if (a.relu) { z0 = fmaxf(z0, 0.f); z1 = fmaxf(z1, 0.f); }
+      if (mrow) {  // keep where the forward activation (BF16) is positive
+        if (!(__uint_as_float(mw[i >> 1] << 16) > 0.f)) z0 = 0.f;
+        if (!(__uint_as_float(mw[i >> 1] & 0xffff0000u) > 0.f)) z1 = 0.f;
+      }
+      ow[i >> 1] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(z0)) |
+                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(z1)) << 16);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(yrow + c0);
+    dst[0] = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+    dst[1] = make_uint4(ow[4], ow[5], ow[6], ow[7]);
+  }
+}
+
+// Pipeline per CTA over its tiles t_0, t_1, ... (stride gridDim.x): while the
+// tensor core runs the MMAs of tile t_i into accumulator i % 2, the CTA copies
+// tile t_{i+1} into the other row buffer and writes out tile t_{i-1} from the
+// other accumulator.
 __global__ void __launch_bounds__(128) conv64_tc_kernel(const ConvTcArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* wsm = smem;
   unsigned char* abuf0 = smem + kWBytes;
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
-  __shared__ int s_fail;
+  __shared__ float s_bias[kC];
 
   const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
+  const int warp = tid >> 5;
   const int tiles_per_sample = a.len / kTileM;
   const int n_tiles = a.batch * tiles_per_sample;
 
-  // resident weights
+  // resident weights and bias
   const uint4* wsrc = a.wpack;
   uint4* wdst = reinterpret_cast<uint4*>(wsm);
   for (int i = tid; i < kWBytes / 16; i += blockDim.x) wdst[i] = wsrc[i];
+  if (tid < kC) s_bias[tid] = a.bias ? a.bias[tid] : 0.f;
   if (tid == 0) {
-    mbar_init(&mbar, 1);
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_fail = 0;
   }
-  if (warp == 0) tmem_alloc(&tmem_base, 64);
+  if (warp == 0) tmem_alloc(&tmem_base, 2 * kC);
   int t = blockIdx.x;
   if (t < n_tiles) stage_tile(abuf0, a.x, t / tiles_per_sample, (t % tiles_per_sample) * kTileM, a.len);
   asm volatile("cp.async.commit_group;" ::: "memory");
@@ -90,23 +134,17 @@ __global__ void __launch_bounds__(128) conv64_tc_kernel(const ConvTcArgs a) {
   tc_fence_after();
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = idesc_bf16_f32(kTileM, kC);
-  uint32_t phase = 0;
-  int buf = 0;
+  uint32_t parity = 0u;  // bit c: the phase parity accumulator c waits for next
+  int t_prev = -1;
+  int i = 0;
+  bool ok = true;
 
-  for (; t < n_tiles; t += gridDim.x) {
-    const int b = t / tiles_per_sample;
-    const int l0 = (t % tiles_per_sample) * kTileM;
-    unsigned char* acur = abuf0 + buf * kABytes;
+  for (; t < n_tiles; t += gridDim.x, ++i) {
+    const int cur = i & 1;
+    unsigned char* acur = abuf0 + cur * kABytes;
     cp_async_wait_all();
     fence_proxy_async_smem();  // the copies become visible to the tensor core
     __syncthreads();
-    // prefetch the next tile into the other buffer
-    const int tn = t + gridDim.x;
-    if (tn < n_tiles)
-      stage_tile(abuf0 + (buf ^ 1) * kABytes, a.x, tn / tiles_per_sample, (tn % tiles_per_sample) * kTileM,
-                 a.len);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-
     if (tid == 0) {
       tc_fence_after();
       const uint32_t abase = smem_u32(acur), wbase = smem_u32(wsm);
@@ -117,51 +155,43 @@ __global__ void __launch_bounds__(128) conv64_tc_kernel(const ConvTcArgs a) {
         for (int ks = 0; ks < kPlanes / 2; ++ks) {
           const uint64_t ad = smem_desc(abase + 2 * ks * kPlaneBytes + kk * 16, kPlaneBytes, 128);
           const uint64_t bd = smem_desc(wbase + (kk * kPlanes + 2 * ks) * (kC * 16), kC * 16, 128);
-          mma_bf16(tmem, ad, bd, idesc, acc);
+          mma_bf16(tmem + (uint32_t)(cur * kC), ad, bd, idesc, acc);
           acc = true;
         }
       }
-      mma_commit(&mbar);
+      mma_commit(&mbar[cur]);
     }
-    const bool ok = mbar_wait(&mbar, phase, kWaitLimit);
-    phase ^= 1;
-    if (!ok) {
-      if (lane == 0) atomicOr(a.err, kErrMmaWait);
-      s_fail = 1;
+    if (t_prev >= 0) {  // the previous tile's MMAs: its buffer and accumulator become free
+      ok = mbar_wait(&mbar[cur ^ 1], (parity >> (cur ^ 1)) & 1u, kWaitLimit);
+      parity ^= 1u << (cur ^ 1);
+      ok = __syncthreads_and(ok) != 0;
+      if (!ok) break;
+      tc_fence_after();
     }
-    tc_fence_after();
-    // epilogue: row = 32 warp + lane, 64 columns
-    const int row = 32 * warp + lane;
-    const int l = l0 + row;
-    __nv_bfloat16* yrow = a.y + ((size_t)b * a.len + l) * kC;
-    const __nv_bfloat16* mrow = a.mask ? a.mask + ((size_t)b * a.len + l) * kC : nullptr;
-#pragma unroll
-    for (int c0 = 0; c0 < kC; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
-      __align__(16) __nv_bfloat16 o[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        float z = v[i];
-        if (a.bias) z += a.bias[c0 + i];
-        if (a.relu) z = fmaxf(z, 0.f);
-        if (mrow) z = (__bfloat162float(mrow[c0 + i]) > 0.f) ? z : 0.f;
-        o[i] = __float2bfloat16_rn(z);
-      }
-      uint4* dst = reinterpret_cast<uint4*>(yrow + c0);
-      dst[0] = reinterpret_cast<const uint4*>(o)[0];
-      dst[1] = reinterpret_cast<const uint4*>(o)[1];
-    }
+    const int tn = t + gridDim.x;
+    if (tn < n_tiles)
+      stage_tile(abuf0 + (cur ^ 1) * kABytes, a.x, tn / tiles_per_sample, (tn % tiles_per_sample) * kTileM,
+                 a.len);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    if (t_prev >= 0) conv_epilogue(a, s_bias, tmem, (uint32_t)((cur ^ 1) * kC), t_prev, tiles_per_sample);
     tc_fence_before();
-    __syncthreads();
-    if (s_fail) break;
-    buf ^= 1;
+    t_prev = t;
   }
+  if (ok && t_prev >= 0) {  // the last tile
+    const int last = (i - 1) & 1;
+    ok = mbar_wait(&mbar[last], (parity >> last) & 1u, kWaitLimit);
+    ok = __syncthreads_and(ok) != 0;
+    if (ok) {
+      tc_fence_after();
+      conv_epilogue(a, s_bias, tmem, (uint32_t)(last * kC), t_prev, tiles_per_sample);
+    }
+  }
+  if (!ok && tid == 0) atomicOr(a.err, kErrMmaWait);
   cp_async_wait_all();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, 64);
+  if (warp == 0) tmem_dealloc(tmem, 2 * kC);
 }
 
 // W[kk][co][ci] (FP32) -> BF16 planes for the tensor-core kernel. transpose=1
@@ -346,54 +376,153 @@ __global__ void __launch_bounds__(128) conv_out_bwd_kernel(const float* dlogit, 
   }
 }
 
-// Partial weight and bias gradients of a 64 -> 64 layer over 32-position tiles:
-// dW[kk][co][ci] = sum_p dY[p][co] X[p + kk - 4][ci], db[co] = sum_p dY[p][co].
-// Thread (co, 8-channel group) keeps 9 x 8 accumulators.
+// Gradient outputs of a 64 -> 64 layer: dW [9][64][64] then db [64].
 constexpr int kDwOut = kTaps * kC * kC + kC;
-__global__ void __launch_bounds__(512) dw64_kernel(const __nv_bfloat16* dy, const __nv_bfloat16* x,
-                                                   float* partial, int batch, int len) {
-  __shared__ __align__(16) float sdy[32][kC];
-  __shared__ __align__(16) float sx[32 + kTaps - 1][kC];
-  const int t = threadIdx.x;
-  const int co = t >> 3, cg = t & 7;
-  float acc[kTaps][8];
-#pragma unroll
-  for (int kk = 0; kk < kTaps; ++kk)
-#pragma unroll
-    for (int c = 0; c < 8; ++c) acc[kk][c] = 0.f;
-  float accb = 0.f;
-  const int n_tiles = batch * len / 32;
-  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int p0 = tile * 32;
-    const int b = p0 / len, l0 = p0 - b * len;
-    for (int i = t; i < 32 * kC; i += blockDim.x)
-      sdy[i / kC][i % kC] = __bfloat162float(dy[((size_t)b * len + l0) * kC + i]);
-    for (int i = t; i < (32 + kTaps - 1) * kC; i += blockDim.x) {
-      const int r = i / kC, c = i % kC;
-      const int l = l0 - kTaps / 2 + r;
-      sx[r][c] = (l >= 0 && l < len) ? __bfloat162float(x[((size_t)b * len + l) * kC + c]) : 0.f;
-    }
+
+// Weight and bias gradients of a 64 -> 64 layer on the tensor cores:
+//   dW[kk][co][ci] = sum_p dY[p][co] X[p + kk - 4][ci] = sum_q dY[q - kk + 4][co] X[q][ci],
+// a GEMM over positions q (K) with M = output channel and N = input channel. A
+// CTA walks 128-position tiles (K = 128 each) and accumulates all nine taps in
+// TMEM across its tiles. Both operands are read "MN-major" from channels-last
+// rows: 16 bytes = 8 consecutive channels of one position, one plane per 8
+// channels with positions at a 16-byte stride, so a shift along positions is a
+// shift of the descriptor's start address. Taps are paired in M = 128: rows
+// 0..63 hold tap kk, rows 64..127 tap kk + 1, whose dY rows sit one position
+// earlier; a second copy of the dY planes staged one row later makes that a
+// single descriptor (planes 8..15 = planes 0..7 moved by one row). Pairs (0,1),
+// (2,3), (4,5), (6,7), (8,-): 5 x 64 TMEM columns; the unused half of the last
+// pair reads staged rows and is discarded.
+constexpr int kWgTile = 128;                     // positions per tile (K)
+constexpr int kWgRowsA = kWgTile + kTaps - 1;    // 136 staged dY rows per plane
+constexpr int kWgPlaneA = kWgRowsA * 16;         // 2,176 B
+constexpr int kWgABytes = 2 * kPlanes * kWgPlaneA;  // 16 planes: 34,816 B
+constexpr int kWgPlaneB = kWgTile * 16;          // 2,048 B
+constexpr int kWgBBytes = kPlanes * kWgPlaneB;   // 16,384 B
+constexpr int kWgStage = kWgABytes + kWgBBytes;  // 51,200 B per stage
+constexpr int kWgPairs = 5;
+constexpr int kWgSmem = 120 * 1024;              // two stages; > half an SM: one CTA per SM (512 TMEM columns)
+
+__device__ __forceinline__ void stage_wgrad(unsigned char* buf, const __nv_bfloat16* dy, const __nv_bfloat16* x,
+                                            int b, int q0, int len) {
+  // dY planes j < 8: row r <- dY[q0 - 4 + r]; planes 8..15: row r <- dY[q0 - 5 + r]; X planes: row r <- X[q0 + r]
+  for (int i = threadIdx.x; i < 2 * kPlanes * kWgRowsA; i += blockDim.x) {
+    const int j = i / kWgRowsA, r = i - j * kWgRowsA;
+    const int l = q0 - (kTaps / 2) - (j >= kPlanes ? 1 : 0) + r;
+    const bool in = l >= 0 && l < len;
+    const __nv_bfloat16* src = dy + ((size_t)b * len + (in ? l : 0)) * kC + 8 * (j & (kPlanes - 1));
+    cp_async16(buf + j * kWgPlaneA + r * 16, src, in ? 16u : 0u);
+  }
+  unsigned char* bb = buf + kWgABytes;
+  for (int i = threadIdx.x; i < kPlanes * kWgTile; i += blockDim.x) {
+    const int j = i / kWgTile, r = i - j * kWgTile;
+    cp_async16(bb + j * kWgPlaneB + r * 16, x + ((size_t)b * len + q0 + r) * kC + 8 * j, 16u);
+  }
+}
+
+__global__ void __launch_bounds__(128) wgrad64_tc_kernel(const __nv_bfloat16* dy, const __nv_bfloat16* x,
+                                                         float* partial, int32_t* err, int batch, int len) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int tiles_per_sample = len / kWgTile;
+  const int n_tiles = batch * tiles_per_sample;
+
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, 512);
+  int t = blockIdx.x;
+  if (t < n_tiles) stage_wgrad(smem, dy, x, t / tiles_per_sample, (t % tiles_per_sample) * kWgTile, len);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  // M = 128, N = 64, A and B MN-major
+  const uint32_t idesc = idesc_bf16_f32(128, kC) | (1u << 15) | (1u << 16);
+  uint32_t parity = 0u;
+  float db = 0.f;
+  int i = 0;
+  bool ok = true;
+  for (; t < n_tiles; t += gridDim.x, ++i) {
+    const int cur = i & 1;
+    unsigned char* buf = smem + cur * kWgStage;
+    cp_async_wait_all();
+    fence_proxy_async_smem();
     __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t abase = smem_u32(buf), bbase = smem_u32(buf + kWgABytes);
 #pragma unroll 1
-    for (int p = 0; p < 32; ++p) {
-      const float g = sdy[p][co];
-      accb += g;
+      for (int g = 0; g < kWgPairs; ++g) {
+        const int kk = 2 * g;
 #pragma unroll
-      for (int kk = 0; kk < kTaps; ++kk) {
-        const float4* xr = reinterpret_cast<const float4*>(&sx[p + kk][8 * cg]);
-        const float4 v0 = xr[0], v1 = xr[1];
-        acc[kk][0] += g * v0.x; acc[kk][1] += g * v0.y; acc[kk][2] += g * v0.z; acc[kk][3] += g * v0.w;
-        acc[kk][4] += g * v1.x; acc[kk][5] += g * v1.y; acc[kk][6] += g * v1.z; acc[kk][7] += g * v1.w;
+        for (int ks = 0; ks < kWgTile / 16; ++ks) {
+          const uint64_t ad = smem_desc(abase + (uint32_t)((kTaps - 1 - kk) * 16 + ks * 256), 128, kWgPlaneA);
+          const uint64_t bd = smem_desc(bbase + (uint32_t)(ks * 256), 128, kWgPlaneB);
+          mma_bf16(tmem + (uint32_t)(g * kC), ad, bd, idesc, i > 0 || ks > 0);
+        }
+      }
+      mma_commit(&mbar[cur]);
+    }
+    if (tid < kC) {  // bias gradient: the tile's own dY rows (staged rows 4 .. 131 of plane co / 8)
+      const unsigned char* col = buf + (tid >> 3) * kWgPlaneA + (tid & 7) * 2;
+#pragma unroll 8
+      for (int r = kTaps / 2; r < kTaps / 2 + kWgTile; ++r)
+        db += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(col + r * 16));
+    }
+    if (i > 0) {  // the previous tile's MMAs are done: its buffer is free
+      ok = mbar_wait(&mbar[cur ^ 1], (parity >> (cur ^ 1)) & 1u, kWaitLimit);
+      parity ^= 1u << (cur ^ 1);
+      ok = __syncthreads_and(ok) != 0;
+      if (!ok) break;
+    }
+    const int tn = t + gridDim.x;
+    if (tn < n_tiles)
+      stage_wgrad(smem + (cur ^ 1) * kWgStage, dy, x, tn / tiles_per_sample, (tn % tiles_per_sample) * kWgTile,
+                  len);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  if (ok && i > 0) {  // the last tile's MMAs (and with them all earlier ones)
+    const int last = (i - 1) & 1;
+    ok = mbar_wait(&mbar[last], (parity >> last) & 1u, kWaitLimit);
+    ok = __syncthreads_and(ok) != 0;
+  }
+  tc_fence_after();
+  float* out = partial + (size_t)blockIdx.x * kDwOut;
+  if (ok) {
+    // TMEM lane m = 32 warp + lane: tap 2g + (m >= 64), output channel m % 64; column = input channel
+    const int m = 32 * warp + lane;
+    const int co = m & (kC - 1);
+#pragma unroll 1
+    for (int g = 0; g < kWgPairs; ++g) {
+      const int kk = 2 * g + (m >= kC ? 1 : 0);
+#pragma unroll
+      for (int c0 = 0; c0 < kC; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(g * kC + c0), v);
+        if (kk < kTaps) {
+          float4* dst = reinterpret_cast<float4*>(out + (kk * kC + co) * kC + c0);
+          dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+          dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+          dst[2] = make_float4(v[8], v[9], v[10], v[11]);
+          dst[3] = make_float4(v[12], v[13], v[14], v[15]);
+        }
       }
     }
-    __syncthreads();
+    if (tid < kC) out[kTaps * kC * kC + tid] = db;
+  } else if (tid == 0) {
+    atomicOr(err, kErrMmaWait);
   }
-  float* out = partial + (size_t)blockIdx.x * kDwOut;
-#pragma unroll
-  for (int kk = 0; kk < kTaps; ++kk)
-#pragma unroll
-    for (int c = 0; c < 8; ++c) out[(kk * kC + co) * kC + 8 * cg + c] = acc[kk][c];
-  if (cg == 0) out[kTaps * kC * kC + co] = accb;
+  cp_async_wait_all();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 // Partial gradients of a small layer: n_co x n_ci channels (first layer 64 x 2 with
@@ -475,20 +604,31 @@ int launch_conv_out_bwd(const float* dlogit, const float* w6, const void* a5, vo
   return (int)cudaGetLastError();
 }
 
-int dw64_parts(int batch, int len) {
-  const int tiles = batch * len / 32;
-  return tiles < 304 ? tiles : 304;
-}
 int dw_small_parts(int batch, int len) {
   const int total = batch * len;
   return (total + 1023) / 1024 < 512 ? (total + 1023) / 1024 : 512;
 }
 
-// dW and db of a 64 -> 64 layer into out[kDwOut] (dW [9][64][64] then db [64])
-int launch_dw64(const void* dy, const void* x, float* partial, float* out, int batch, int len, void* s) {
-  const int parts = dw64_parts(batch, len);
-  dw64_kernel<<<parts, 512, 0, (cudaStream_t)s>>>(static_cast<const __nv_bfloat16*>(dy),
-                                                   static_cast<const __nv_bfloat16*>(x), partial, batch, len);
+
+int wgrad64_parts(int batch, int len) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = batch * (len / kWgTile);
+  return tiles < sms ? tiles : sms;
+}
+
+// dW and db of a 64 -> 64 layer on the tensor cores (len a multiple of 128):
+// per-CTA partial sums, then their sum into out[kDwOut]
+int launch_wgrad64(const void* dy, const void* x, float* partial, float* out, int32_t* err, int batch, int len,
+                   void* s) {
+  if (batch <= 0) return 0;
+  const int parts = wgrad64_parts(batch, len);
+  cudaError_t e = cudaFuncSetAttribute(wgrad64_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
+  if (e != cudaSuccess) return (int)e;
+  wgrad64_tc_kernel<<<parts, 128, kWgSmem, (cudaStream_t)s>>>(static_cast<const __nv_bfloat16*>(dy),
+                                                              static_cast<const __nv_bfloat16*>(x), partial, err,
+                                                              batch, len);
   reduce_partials_kernel<<<(kDwOut + 255) / 256, 256, 0, (cudaStream_t)s>>>(partial, parts, kDwOut, out);
   return (int)cudaGetLastError();
 }

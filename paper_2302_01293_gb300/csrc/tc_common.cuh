@@ -13,9 +13,11 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Shared-memory matrix descriptor, no swizzle, K-major: 8-row x 16-byte core
-// matrices; `lbo` = bytes between core matrices adjacent in K, `sbo` = bytes
-// between 8-row groups in M (or N). Version field 1 (tcgen05).
+// Shared-memory matrix descriptor, no swizzle: 8 x 16-byte core matrices.
+// K-major operand: `lbo` = bytes between core matrices adjacent in K, `sbo` =
+// bytes between 8-row groups in M (or N). MN-major operand (16 bytes = 8
+// consecutive M or N elements of one k): `lbo` = bytes between groups of 8 k,
+// `sbo` = bytes between core matrices adjacent in M (or N). Version field 1 (tcgen05).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);

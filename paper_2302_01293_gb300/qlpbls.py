@@ -129,6 +129,10 @@ def lib():
             L.qlp_cnn_pack_w64.restype = ctypes.c_int
             L.qlp_cnn_conv64.argtypes = [_vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]
             L.qlp_cnn_conv64.restype = ctypes.c_int
+            L.qlp_cnn_wgrad64_workspace.argtypes = [_i32, _i32]
+            L.qlp_cnn_wgrad64_workspace.restype = _i64
+            L.qlp_cnn_conv64_wgrad.argtypes = [_vp, _vp, _vp, _vp, _i32, _i32, _vp, _vp]
+            L.qlp_cnn_conv64_wgrad.restype = ctypes.c_int
             L.qlp_cnn_n_params.argtypes = []
             L.qlp_cnn_n_params.restype = ctypes.c_int32
             L.qlp_cnn_create.argtypes = [_i32, _i32, ctypes.c_uint64, _P(_vp)]
@@ -521,6 +525,20 @@ def conv64(x, wpack, bias=None, mask=None, relu: bool = True, out=None, err=None
                                 int(x.shape[1]), int(relu), err.data_ptr(), _stream_ptr(stream)),
            "qlp_cnn_conv64")
     return y
+
+
+def conv64_wgrad(dy, x, stream=None):
+    """qlp_cnn_conv64_wgrad: (dW [9, 64, 64], db [64]) FP32 of a 64 -> 64 layer."""
+    import torch
+    B, L = int(x.shape[0]), int(x.shape[1])
+    ws = torch.empty(max(int(lib().qlp_cnn_wgrad64_workspace(B, L)), 1), dtype=torch.float32, device=x.device)
+    out = torch.empty(9 * 64 * 64 + 64, dtype=torch.float32, device=x.device)
+    err = torch.zeros(1, dtype=torch.int32, device=x.device)
+    _check(lib().qlp_cnn_conv64_wgrad(dy.data_ptr(), x.data_ptr(), ws.data_ptr(), out.data_ptr(), B, L,
+                                      err.data_ptr(), _stream_ptr(stream)), "qlp_cnn_conv64_wgrad")
+    if int(err.item()) != 0:
+        raise QlpError(f"qlp_cnn_conv64_wgrad: device error flags {int(err.item())}")
+    return out[:9 * 64 * 64].view(9, 64, 64), out[9 * 64 * 64:]
 
 
 def topk(logits, x0, k: int, stream=None):

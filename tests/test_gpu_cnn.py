@@ -75,6 +75,27 @@ def test_conv64_input_gradient_matches_autograd(gpu_lib):
     assert (dx - ref).abs().max().item() <= 1e-2 * ref.abs().max().item()
 
 
+@pytest.mark.parametrize("B,L", [(1, 128), (3, 512), (2, 4096)])
+def test_conv64_weight_gradient_matches_autograd(gpu_lib, B, L):
+    # dW[kk][co][ci] = sum_p dY[p][co] X[p + kk - 4][ci] against torch's conv1d weight gradient
+    # on the same BF16 operands (FP32 sums; tolerance for the summation order)
+    import torch
+    import torch.nn.functional as F
+    from paper_2302_01293_gb300 import qlpbls
+    g = torch.Generator(device="cpu").manual_seed(11)
+    x = torch.randn(B, L, 64, generator=g).to(torch.bfloat16)
+    dy = torch.randn(B, L, 64, generator=g).to(torch.bfloat16)
+    dw, db = qlpbls.conv64_wgrad(dy.cuda(), x.cuda())
+    xf = x.float().permute(0, 2, 1).requires_grad_(False)
+    w = torch.zeros(64, 64, 9, requires_grad=True)
+    y = F.conv1d(xf, w, padding=4)
+    y.backward(dy.float().permute(0, 2, 1))
+    ref = w.grad.permute(2, 0, 1)                                # [kk][co][ci]
+    scale = float(np.sqrt(B * L))
+    np.testing.assert_allclose(dw.cpu().numpy(), ref.numpy(), atol=2e-5 * scale, rtol=1e-4)
+    np.testing.assert_allclose(db.cpu().numpy(), dy.float().sum((0, 1)).numpy(), atol=1e-5 * scale, rtol=1e-4)
+
+
 def test_network_gradients_match_oracle(gpu_lib):
     """Full forward + backward of the 6-layer network on the GPU vs the oracle taken
     in the GPU's precision (BF16 activations, activation gradients and middle-layer
