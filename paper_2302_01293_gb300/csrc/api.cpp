@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -357,10 +358,15 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   }
   pl->n_points = npt;
   pl->n_cell_stars = (int32_t)cell_stars.size();
-  std::vector<double> tp_all((size_t)std::max<int64_t>(npt, 1)), y_all(tp_all.size()), dy_all(tp_all.size());
-  std::vector<double2> fq((size_t)std::max<int64_t>(nf, 1));
+  // staging buffers without zero fill, filled star by star in parallel
+  const size_t npt_alloc = (size_t)std::max<int64_t>(npt, 1), nf_alloc = (size_t)std::max<int64_t>(nf, 1);
+  std::unique_ptr<double[]> tp_all(new (std::nothrow) double[npt_alloc]);
+  std::unique_ptr<double[]> y_all(new (std::nothrow) double[npt_alloc]);
+  std::unique_ptr<double[]> dy_all(new (std::nothrow) double[npt_alloc]);
+  std::unique_ptr<double2[]> fq(new (std::nothrow) double2[nf_alloc]);
+  if (!tp_all || !y_all || !dy_all || !fq) { delete pl; return QLP_ERR_NOMEM; }
   pl->freqs.resize((size_t)nf);
-  for (int32_t s = 0; s < n_stars; ++s) {
+  parallel_stars(p, n_stars, [&](int32_t s) {
     const StarPlanHost& h = sp[(size_t)s];
     const StarDev& d = stars[(size_t)s];
     if (d.n_pts > 0) {
@@ -372,7 +378,7 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
       fq[(size_t)(d.f_off + k)] = make_double2(h.freqs[(size_t)k], h.qmins[(size_t)k]);
       pl->freqs[(size_t)(d.f_off + k)] = h.freqs[(size_t)k];
     }
-  }
+  });
 
   int dev = 0, sms = 0;
   QLP_CK(cudaGetDevice(&dev));
@@ -432,8 +438,7 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
         wi.f_count = std::min(chunk, d.n_f - b);
         if (meth == kMethodCells) {
           int nbm = 1;
-          for (int32_t k = b; k < b + wi.f_count; ++k)
-            nbm = std::max(nbm, (int)std::ceil(p.noverlap / h.qmins[(size_t)k]));
+          for (int32_t k = b; k < b + wi.f_count; ++k) nbm = std::max(nbm, h.nbins[(size_t)k]);
           const int hs32 = (int)(round32(nbm + kMPad) / 32);
           const size_t avail = (size_t)budget - cells_hist_offset(d.win_cap, cw);
           const int wact = (int)std::min<size_t>((size_t)cw, avail / ((size_t)NA * hs32 * 32 * 4));
@@ -441,7 +446,7 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
         }
         items.push_back(wi);
         const int mid = b + wi.f_count / 2;
-        const double nbm = std::ceil(p.noverlap / h.qmins[(size_t)mid]);
+        const double nbm = (double)h.nbins[(size_t)mid];
         const double per_f = meth == kMethodCells ? h.baseline * h.freqs[(size_t)mid] * nbm + 3.0 * nbm
                                                   : (double)d.n_pts + 3.0 * nbm;
         cost.push_back((double)wi.f_count * per_f);
@@ -460,9 +465,9 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
 
   // device buffers
   cudaStream_t st = (cudaStream_t)stream;
-  if ((rc = dev_alloc(&pl->d_stars, (size_t)n_stars)) || (rc = dev_alloc(&pl->d_fq, fq.size())) ||
-      (rc = dev_alloc(&pl->d_items, sorted.size())) || (rc = dev_alloc(&pl->d_tp, tp_all.size())) ||
-      (rc = dev_alloc(&pl->d_y, y_all.size())) || (rc = dev_alloc(&pl->d_dy, dy_all.size())) ||
+  if ((rc = dev_alloc(&pl->d_stars, (size_t)n_stars)) || (rc = dev_alloc(&pl->d_fq, nf_alloc)) ||
+      (rc = dev_alloc(&pl->d_items, sorted.size())) || (rc = dev_alloc(&pl->d_tp, npt_alloc)) ||
+      (rc = dev_alloc(&pl->d_y, npt_alloc)) || (rc = dev_alloc(&pl->d_dy, npt_alloc)) ||
       (rc = dev_alloc(&pl->d_pts, (size_t)std::max<int64_t>(npad, 1))) ||
       (rc = dev_alloc(&pl->d_tpd, (size_t)std::max<int64_t>(npad, 1))) ||
       (rc = dev_alloc(&pl->d_cell_stars, std::max<size_t>(cell_stars.size(), 1))) ||
@@ -476,12 +481,12 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   }
   cudaError_t e = cudaSuccess;
   if (n_stars > 0) e = cudaMemcpyAsync(pl->d_stars, stars.data(), sizeof(StarDev) * (size_t)n_stars, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && nf > 0) e = cudaMemcpyAsync(pl->d_fq, fq.data(), sizeof(double2) * (size_t)nf, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && nf > 0) e = cudaMemcpyAsync(pl->d_fq, fq.get(), sizeof(double2) * (size_t)nf, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !sorted.empty()) e = cudaMemcpyAsync(pl->d_items, sorted.data(), sizeof(WorkItem) * sorted.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !cell_stars.empty()) e = cudaMemcpyAsync(pl->d_cell_stars, cell_stars.data(), sizeof(int32_t) * cell_stars.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(pl->d_tp, tp_all.data(), sizeof(double) * (size_t)npt, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(pl->d_y, y_all.data(), sizeof(double) * (size_t)npt, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(pl->d_dy, dy_all.data(), sizeof(double) * (size_t)npt, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(pl->d_tp, tp_all.get(), sizeof(double) * (size_t)npt, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(pl->d_y, y_all.get(), sizeof(double) * (size_t)npt, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(pl->d_dy, dy_all.get(), sizeof(double) * (size_t)npt, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_ctl, 0, 4 * sizeof(int32_t), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // host staging vectors die at return
   if (e != cudaSuccess) {

@@ -113,6 +113,7 @@ void plan_one(const qlp_bls_params& p, const double* t, const double* y, const d
     s.freqs.push_back(f);
     s.qmins.push_back(q);
     const int nb = nbins_of(q, p);
+    s.nbins.push_back(nb);
     s.nbins_max = std::max(s.nbins_max, nb);
     s.ymax = std::max(s.ymax, s.baseline * f * (double)nb);
   };
@@ -163,6 +164,7 @@ void plan_one(const qlp_bls_params& p, const double* t, const double* y, const d
     s.status = QLP_STAR_NBINS_CAP;
     s.freqs.clear();
     s.qmins.clear();
+    s.nbins.clear();
     return;
   }
   s.sturges_nb = sturges_of((int64_t)s.freqs.size());
@@ -185,7 +187,7 @@ void plan_one(const qlp_bls_params& p, const double* t, const double* y, const d
       s.n_cells = prev + 1;
       double work = 0.0, dmax = 0.0;
       for (size_t k = 0; k < s.freqs.size(); ++k) {
-        const double nb = std::ceil(p.noverlap / s.qmins[k]);
+        const double nb = (double)s.nbins[k];
         work += std::floor(s.baseline * s.freqs[k] * nb) + 3.0;
         dmax = std::max(dmax, 1.0 / (s.freqs[k] * nb));
       }
@@ -195,33 +197,37 @@ void plan_one(const qlp_bls_params& p, const double* t, const double* y, const d
   }
 }
 
-void plan_all(const qlp_bls_params& p, int32_t n_stars, const int64_t* offsets, const double* t,
-              const double* y, const double* dy, const double* rho, std::vector<StarPlanHost>* out,
-              const int64_t* win_off, const double* win_lo, const double* win_hi) {
-  out->assign((size_t)n_stars, StarPlanHost());
+void parallel_stars(const qlp_bls_params& p, int32_t n_stars, const std::function<void(int32_t)>& fn) {
   int nth = p.n_threads > 0 ? p.n_threads : (int)std::thread::hardware_concurrency();
   nth = std::max(1, std::min(nth, std::max(1, n_stars)));
-  auto work = [&](int tid) {
-    for (int32_t s = tid; s < n_stars; s += nth) {
-      const int64_t a = offsets[s], b = offsets[s + 1];
-      const double r = rho ? rho[s] : NAN;
-      Windows w;
-      if (win_off) {
-        w.lo = win_lo + win_off[s];
-        w.hi = win_hi + win_off[s];
-        w.n = win_off[s + 1] - win_off[s];
-      }
-      plan_one(p, t + a, y + a, dy + a, b - a, r, &(*out)[(size_t)s], win_off ? &w : nullptr);
-    }
-  };
   if (nth == 1) {
-    work(0);
+    for (int32_t s = 0; s < n_stars; ++s) fn(s);
     return;
   }
   std::vector<std::thread> th;
   th.reserve((size_t)nth);
-  for (int i = 0; i < nth; ++i) th.emplace_back(work, i);
+  for (int i = 0; i < nth; ++i)
+    th.emplace_back([&, i]() {
+      for (int32_t s = i; s < n_stars; s += nth) fn(s);
+    });
   for (auto& x : th) x.join();
+}
+
+void plan_all(const qlp_bls_params& p, int32_t n_stars, const int64_t* offsets, const double* t,
+              const double* y, const double* dy, const double* rho, std::vector<StarPlanHost>* out,
+              const int64_t* win_off, const double* win_lo, const double* win_hi) {
+  out->assign((size_t)n_stars, StarPlanHost());
+  parallel_stars(p, n_stars, [&](int32_t s) {
+    const int64_t a = offsets[s], b = offsets[s + 1];
+    const double r = rho ? rho[s] : NAN;
+    Windows w;
+    if (win_off) {
+      w.lo = win_lo + win_off[s];
+      w.hi = win_hi + win_off[s];
+      w.n = win_off[s + 1] - win_off[s];
+    }
+    plan_one(p, t + a, y + a, dy + a, b - a, r, &(*out)[(size_t)s], win_off ? &w : nullptr);
+  });
 }
 
 }  // namespace qlp

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <functional>
 #include <vector>
 
 #include "../../include/qlp_bls.h"
@@ -19,6 +20,7 @@ struct StarPlanHost {
   std::vector<double> tp, y, dy;   // valid points, t' = t - t_ref
   std::vector<double> freqs;       // trial frequencies (1/day)
   std::vector<double> qmins;       // q_min at each frequency
+  std::vector<int32_t> nbins;      // nbins at each frequency
   int32_t nbins_max = 0;
   double ymax = 0.0;               // max over f of T f nbins(f)
   int32_t sturges_nb = 0;
@@ -49,6 +51,9 @@ double pmax_of(const double* tp, int64_t n, const qlp_bls_params& p);
 int sturges_of(int64_t n);
 void plan_one(const qlp_bls_params& p, const double* t, const double* y, const double* dy, int64_t n,
               double rho, StarPlanHost* out, const Windows* win = nullptr);
+// Runs fn(s) for every star s on the planner's threads (p.n_threads, 0 = all cores).
+void parallel_stars(const qlp_bls_params& p, int32_t n_stars, const std::function<void(int32_t)>& fn);
+
 void plan_all(const qlp_bls_params& p, int32_t n_stars, const int64_t* offsets, const double* t,
               const double* y, const double* dy, const double* rho, std::vector<StarPlanHost>* out,
               const int64_t* win_off = nullptr, const double* win_lo = nullptr,
