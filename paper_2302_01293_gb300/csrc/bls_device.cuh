@@ -179,4 +179,88 @@ __device__ __forceinline__ void sweep_store(float* hw, float* hy, float* hwc, fl
   }
 }
 
+// Histogram of the cell path: one record per bin, (w, w-compensation, w d,
+// w d-compensation) as float4 in COMP mode, (w, w d) as float2 in PLAIN mode, so
+// that a bin's update and the sweep's read are one 16- or 8-byte access.
+template <int SUM>
+struct PackedBin {
+  using T = float2;
+  __device__ static float w(const T& v) { return v.x; }
+  __device__ static float y(const T& v) { return v.y; }
+  __device__ static float wc(const T&) { return 0.f; }
+  __device__ static float yc(const T&) { return 0.f; }
+};
+template <>
+struct PackedBin<QLP_SUM_COMP> {
+  using T = float4;
+  __device__ static float w(const T& v) { return v.x; }
+  __device__ static float y(const T& v) { return v.z; }
+  __device__ static float wc(const T& v) { return v.y; }
+  __device__ static float yc(const T& v) { return v.w; }
+};
+
+// sweep_store over a packed histogram: the same window sums, in the same order,
+// as sweep_store over separate arrays (bit-identical results).
+template <int SUM>
+__device__ __forceinline__ void sweep_store_packed(typename PackedBin<SUM>::T* h, const int* mtab, int nq, int nb,
+                                                   int lane, int64_t fidx, float* sr, uint8_t* qidx,
+                                                   uint32_t* kbin, float* sbest, float* rbest) {
+  using PB = PackedBin<SUM>;
+  for (int i = lane; i < kMPad; i += 32) h[nb + i] = h[i % nb];
+  __syncwarp();
+  uint32_t wmask = 0u;
+  unsigned long long jlow = 0ull;
+  for (int j = nq - 1; j >= 0; --j) {
+    const int o = mtab[j] - 1;
+    wmask |= 1u << o;
+    jlow = (jlow & ~(0xfull << (4 * o))) | ((unsigned long long)j << (4 * o));
+  }
+  const int mmax = mtab[nq - 1];
+  float bs2 = -1.f, bd = 1.f, bsv = 0.f, brv = 0.f;
+  int bj = 255, bk = -1;
+  for (int k = lane; k < nb; k += 32) {
+    float rw = 0.f, ry = 0.f, rwc = 0.f, ryc = 0.f;
+    for (int o = 0; o < mmax; ++o) {
+      const typename PB::T v = h[k + o];
+      rw = __fadd_rn(rw, PB::w(v));
+      ry = __fadd_rn(ry, PB::y(v));
+      if (SUM == QLP_SUM_COMP) {
+        rwc = __fadd_rn(rwc, PB::wc(v));
+        ryc = __fadd_rn(ryc, PB::yc(v));
+      }
+      if ((wmask >> o) & 1u) {
+        const int j = (int)((jlow >> (4 * o)) & 0xfull);
+        const float r = (SUM == QLP_SUM_COMP) ? __fadd_rn(rw, rwc) : rw;
+        const float sv = (SUM == QLP_SUM_COMP) ? __fadd_rn(ry, ryc) : ry;
+        if (r > 0.f && r < 1.f) {
+          const float d = __fmul_rn(r, __fsub_rn(1.f, r));
+          const float s2 = __fmul_rn(sv, sv);
+          if (beats(s2, d, j, k, bs2, bd, bj, bk)) {
+            bs2 = s2; bd = d; bsv = sv; brv = r; bj = j; bk = k;
+          }
+        }
+      }
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const float o_s2 = __shfl_xor_sync(0xffffffffu, bs2, off);
+    const float o_d = __shfl_xor_sync(0xffffffffu, bd, off);
+    const float o_s = __shfl_xor_sync(0xffffffffu, bsv, off);
+    const float o_r = __shfl_xor_sync(0xffffffffu, brv, off);
+    const int o_j = __shfl_xor_sync(0xffffffffu, bj, off);
+    const int o_k = __shfl_xor_sync(0xffffffffu, bk, off);
+    if (beats(o_s2, o_d, o_j, o_k, bs2, bd, bj, bk)) {
+      bs2 = o_s2; bd = o_d; bsv = o_s; brv = o_r; bj = o_j; bk = o_k;
+    }
+  }
+  if (lane == 0) {
+    const bool none = bs2 < 0.f;
+    sr[fidx] = none ? 0.f : __fdiv_rn(bs2, bd);
+    if (qidx) qidx[fidx] = none ? (uint8_t)255 : (uint8_t)bj;
+    if (kbin) kbin[fidx] = none ? 0xffffffffu : (uint32_t)bk;
+    if (sbest) sbest[fidx] = none ? 0.f : bsv;
+    if (rbest) rbest[fidx] = none ? 0.f : brv;
+  }
+}
+
 }  // namespace qlp

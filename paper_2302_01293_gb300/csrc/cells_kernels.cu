@@ -193,7 +193,7 @@ __device__ __forceinline__ EdgeC edge_prefix(int G, bool valid, uint32_t k_lo, u
   }
   const int vl = min(ul + sel, n_loc - 1);
   const float2 lc = s_loc[vl];
-  const float4 bs = s_base[((lo + vl) >> 5) - (lo >> 5)];
+  const float4 bs = s_base[vl >> 5];  // lo is a multiple of 32
   EdgeC c;
   c.bwh = bs.x; c.bwl = bs.y; c.byh = bs.z; c.byl = bs.w; c.lw = lc.x; c.ly = lc.y;
   return c;
@@ -214,25 +214,26 @@ __device__ __forceinline__ float2 edge_piece(const EdgeC& c) {
 }
 
 template <int SUM>
-__device__ __forceinline__ void add_piece(float* hw, float* hy, float* hwc, float* hyc, int b,
-                                          float2 pc, bool own, bool p) {
+__device__ __forceinline__ void add_piece(typename PackedBin<SUM>::T* h, int b, float2 pc, bool own, bool p) {
   if (!p) return;
   if (own) {  // lanes 0..30 hold distinct bins
-    if (SUM == QLP_SUM_COMP) {
-      float o = hw[b], sN = __fadd_rn(o, pc.x);
-      hwc[b] = __fadd_rn(hwc[b], two_sum_err(o, pc.x, sN));
-      hw[b] = sN;
-      o = hy[b];
-      sN = __fadd_rn(o, pc.y);
-      hyc[b] = __fadd_rn(hyc[b], two_sum_err(o, pc.y, sN));
-      hy[b] = sN;
+    typename PackedBin<SUM>::T v = h[b];
+    if constexpr (SUM == QLP_SUM_COMP) {
+      float sN = __fadd_rn(v.x, pc.x);
+      v.y = __fadd_rn(v.y, two_sum_err(v.x, pc.x, sN));
+      v.x = sN;
+      sN = __fadd_rn(v.z, pc.y);
+      v.w = __fadd_rn(v.w, two_sum_err(v.z, pc.y, sN));
+      v.z = sN;
     } else {
-      hw[b] = __fadd_rn(hw[b], pc.x);
-      hy[b] = __fadd_rn(hy[b], pc.y);
+      v.x = __fadd_rn(v.x, pc.x);
+      v.y = __fadd_rn(v.y, pc.y);
     }
+    h[b] = v;
   } else {
-    atomicAdd(hw + b, pc.x);
-    atomicAdd(hy + b, pc.y);
+    float* f = reinterpret_cast<float*>(h + b);
+    atomicAdd(f, pc.x);
+    atomicAdd(f + (SUM == QLP_SUM_COMP ? 2 : 1), pc.y);
   }
 }
 
@@ -268,10 +269,8 @@ __global__ void __launch_bounds__(NW * 32) cells_kernel(const CellArgs a) {
     const int HS = (wi.pad0 & 0xffff) * 32;
     const int wact = wi.pad0 >> 16;
     int* mtab = reinterpret_cast<int*>(smem + L.mtab) + warp * kMaxQ;
-    float* hw = reinterpret_cast<float*>(smem + L.hist) + (size_t)warp * NA * HS;
-    float* hy = hw + HS;
-    float* hwc = hw + 2 * HS;
-    float* hyc = hw + 3 * HS;
+    using HT = typename PackedBin<SUM>::T;
+    HT* hist = reinterpret_cast<HT*>(reinterpret_cast<float*>(smem + L.hist) + (size_t)warp * NA * HS);
     const double* tp = a.tp + st.pt_off;
     const int32_t* gidx = a.gidx + st.cell_off;
     const double h = st.h;
@@ -302,9 +301,7 @@ __global__ void __launch_bounds__(NW * 32) cells_kernel(const CellArgs a) {
           if (lane < nq)
             mtab[lane] = max(1, (int)floor(__dadd_rn(__dmul_rn(__dmul_rn(fq.y, a.E[lane]), (double)nb), 0.5)));
           for (int i = lane; i < nb + kMPad; i += 32) {
-            hw[i] = 0.f;
-            hy[i] = 0.f;
-            if (SUM == QLP_SUM_COMP) { hwc[i] = 0.f; hyc[i] = 0.f; }
+            hist[i] = HT{};
           }
           F = __dmul_rn(f, (double)nb);
           const double D = __ddiv_rn(1.0, F);  // bin duration (days)
@@ -360,15 +357,15 @@ __global__ void __launch_bounds__(NW * 32) cells_kernel(const CellArgs a) {
           const float2 p1 = edge_piece(c1);
           int b1 = b + step;
           if (b1 >= nb) b1 -= nb;
-          add_piece<SUM>(hw, hy, hwc, hyc, b, p0, own, lane < 31 && g0 + lane < ge);
-          add_piece<SUM>(hw, hy, hwc, hyc, b1, p1, own, lane < 31 && g0 + 31 + lane < ge);
+          add_piece<SUM>(hist, b, p0, own, lane < 31 && g0 + lane < ge);
+          add_piece<SUM>(hist, b1, p1, own, lane < 31 && g0 + 31 + lane < ge);
           b = b1 + step;
           if (b >= nb) b -= nb;
         }
       }
       if (go) {
         __syncwarp();
-        sweep_store<SUM>(hw, hy, hwc, hyc, mtab, nq, nb, lane, fidx, a.sr, a.qidx, a.kbin, a.sbest,
+        sweep_store_packed<SUM>(hist, mtab, nq, nb, lane, fidx, a.sr, a.qidx, a.kbin, a.sbest,
                          a.rbest);
       }
     }
