@@ -182,8 +182,17 @@ def learned_comparison(args):
     rf = learned.recovered(best_full, test)
     rl = learned.recovered(best_l, test)
     coarse = learned.CoarseStage(test)
-    best_a = learned.search_with_bins(test, coarse, learned.propose_without_network(coarse, 32))
+    bins_a = learned.propose_without_network(coarse, 32).cpu().numpy()
+    best_a = learned.search_with_bins(test, coarse, bins_a)
     ra = learned.recovered(best_a, test)
+    # recall with fewer proposals: the network's ranking against the coarse S/N's own
+    bins_n = learned.propose(net, coarse.x0, 32).cpu().numpy()
+    at_k = {}
+    for k in (1, 4):
+        rn = learned.recovered(learned.search_with_bins(test, coarse, bins_n[:, :k]), test)
+        rk = learned.recovered(learned.search_with_bins(test, coarse, bins_a[:, :k]), test)
+        at_k[str(k)] = {"network": float((rn & rf).sum() / max(rf.sum(), 1)),
+                        "coarse_snr_without_network": float((rk & rf).sum() / max(rf.sum(), 1))}
     n = test.n_stars
     return {"workload": f"{n} held-out stars, 1-4 sectors at 200 s, 50 % injected "
                         "(P log-U(0.5, 100) d, depth log-U(1e-4, 1e-2))",
@@ -192,6 +201,7 @@ def learned_comparison(args):
             "full_recovered": int(rf.sum()), "injected": int(test.inj.sum()),
             "recall": float((rl & rf).sum() / max(rf.sum(), 1)),
             "recall_coarse_snr_topk_without_network": float((ra & rf).sum() / max(rf.sum(), 1)),
+            "recall_at_k": at_k,
             "stars_per_hour_full": n / t_full * 3600.0,
             "stars_per_hour_learned": n / t_learned * 3600.0,
             "speedup": t_full / t_learned, "cnn": cnn}
