@@ -14,7 +14,9 @@ It is a plain, slow, step-by-step restatement of the method:
   trial frequency (Sec. 2.1, 2.2 item 1; BLS of Kovacs et al. 2002), in plain
   C with FP64 arithmetic, one frequency at a time, direct window sums;
 * ``snr``   -- the spectral S/N of Eq. 1 with the Sturges median-binned trend
-  and sigma = 1.4826 MAD (Sec. 2.2 item 1) and the best-candidate record.
+  and sigma = 1.4826 MAD (Sec. 2.2 item 1) and the best-candidate record;
+* ``stats`` -- the post-BLS statistics of Sec. 2.2 items 2-5 (trapezoid fit,
+  white and red noise, signal-to-pink noise, transit counts, detection).
 
 Parity pins live in ``tests/test_oracle_*.py``.
 """
