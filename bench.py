@@ -369,6 +369,19 @@ def main():
     flags = plan.device_status()
     if flags:
         raise RuntimeError(f"device flags {flags}")
+    # post-BLS statistics of every star's best candidate (Sec. 2.2 items 2-5), timed apart
+    stats_buf = plan.candidate_stats(out)
+    s_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    torch.cuda.synchronize()
+    s_ev[0].record(stream)
+    for _ in range(3):
+        plan.candidate_stats(out, stats_buf)
+    s_ev[1].record(stream)
+    torch.cuda.synchronize()
+    st_host = plan.stats_host(stats_buf)
+    cand_stats = {"ms": s_ev[0].elapsed_time(s_ev[1]) / 3, "stars": int(plan.n_stars),
+                  "fitted": int(np.sum(st_host["status"] == 0)), "detected": int(np.sum(st_host["detected"])),
+                  "what": "trapezoid fit, white/red noise, S/N_pink, counts, detection per star (one launch)"}
     # all ranks' work over the slowest rank's time (each rank searched its own stars)
     total_work, ms_max = shard.job_totals(plan.work, ms)
     value = total_work / (ms_max * 1e-3)
@@ -449,6 +462,7 @@ def main():
                 "ms_search": ms_search,
                 "gpu_launches": args.steps * (1 + 2 * (plan.work_points > 0) + 2 * (plan.work_cells > 0)),
                 "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "candidate_stats": cand_stats,
                 "learned": learned_line}
         print(json.dumps(line), flush=True)
     if world > 1:

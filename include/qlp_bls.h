@@ -266,6 +266,65 @@ int qlp_bls_device_status(qlp_bls_plan_t* plan, void* stream, int32_t* flags);
 void qlp_bls_plan_destroy(qlp_bls_plan_t* plan);
 
 /*
+ * qlp_bls_autotune -- choose the search's launch settings for a batch (an
+ * implementation concern; the paper has no counterpart). Settings in *p left at
+ * 0 (warps_per_block, chunk_freqs, cell_window) are tried over a small candidate
+ * set; each candidate plans and searches an evenly spaced sample of up to
+ * sample_stars stars (host arrays as for qlp_bls_plan) on `stream`, timed with
+ * CUDA events (best of two runs after one warm-up). *out gets *p with the fastest
+ * candidate's settings; results of a search never depend on them. The choice is
+ * cached for the process, keyed by the device, p's other options and log2 of
+ * the star count and of the median and longest star; *cached (optional) is 1
+ * when the cache answered. Synchronises `stream`. Device errors as for the search.
+ */
+int qlp_bls_autotune(const qlp_bls_params* p, int32_t n_stars, const int64_t* offsets,
+                     const double* t, const double* y, const double* dy, const double* rho,
+                     const double* rstar, int32_t sample_stars, void* stream, qlp_bls_params* out,
+                     int32_t* cached);
+
+/*
+ * qlp_bls_candidate_stats -- post-BLS statistics of every star's best candidate
+ * (Sec. 2.2 items 2-5): a trapezoid fit with the period fixed to the BLS period
+ * (epoch, depth, q, ingress fraction q_in, out-of-transit level z; points within
+ * two BLS durations of the transit centre, weights dy^-2, 1e-6 <= q <= 1 and
+ * 1e-3 <= q_in <= 0.5, Levenberg-Marquardt from the BLS box), white and red noise
+ * of the residuals on the transit-duration timescale, the signal-to-pink noise
+ * of Eq. 2 with the depth replaced by the trapezoid's mean depth
+ * depth (1 - q_in), the point and transit counts, and the detection criteria
+ * (at least two transits, S/N_pink > 9, S/N > 9).
+ *  best  device qlp_bls_best[n_stars] from qlp_bls_snr / qlp_bls_snr_trend of this plan.
+ *  out   device qlp_bls_cand_stats[n_stars].
+ * The first call allocates an int32 scratch array of the plan's point count
+ * (kept by the plan). Runs on `stream`; results are valid after it.
+ */
+#define QLP_STATS_OK             0
+#define QLP_STATS_NO_CANDIDATE   1  /* the star has no best candidate */
+#define QLP_STATS_FEW_POINTS     2  /* fewer than 6 points within two durations of the transits */
+#define QLP_STATS_NOT_CONVERGED  4  /* 100 iterations without meeting the stopping rule */
+typedef struct qlp_bls_cand_stats {
+  double t0;          /* fitted epoch: a mid-transit time (days, same scale as t) */
+  double depth;       /* fitted depth delta: model y = z - delta s */
+  double q;           /* fitted duration / period */
+  double q_in;        /* fitted ingress duration / transit duration */
+  double z;           /* fitted out-of-transit level */
+  double chi2;        /* weighted chi^2 over the fit window */
+  double sigma_w;     /* RMS of the residuals of all points */
+  double sigma_r;     /* red noise on the timescale of one fitted duration */
+  double depth_mean;  /* depth (1 - q_in): the trapezoid's mean depth over the transit */
+  double snr_pink;    /* depth_mean / sqrt(sigma_w^2 / n_in + sigma_r^2 / n_transits) */
+  int32_t n_fit;      /* points in the fit window */
+  int32_t n_in;       /* points in transit (within half a fitted duration of a mid-transit time) */
+  int32_t n_before;   /* points 0.5 to 2 durations before a mid-transit time */
+  int32_t n_after;    /* points 0.5 to 2 durations after a mid-transit time */
+  int32_t n_transits; /* transits with data within 0.5 durations of their mid-transit time */
+  int32_t iterations; /* Levenberg-Marquardt iterations */
+  int32_t status;     /* QLP_STATS_* */
+  int32_t detected;   /* 1 when the detection criteria hold */
+} qlp_bls_cand_stats;
+int qlp_bls_candidate_stats(qlp_bls_plan_t* plan, void* stream, const qlp_bls_best* best,
+                            qlp_bls_cand_stats* out);
+
+/*
  * qlp_bls_graph_capture -- record calls of this plan, with these output buffers
  * (device, as for qlp_bls_search / qlp_bls_snr), as a CUDA graph kept by the
  * plan: parts = 1 one qlp_bls_search, 2 one qlp_bls_snr, 3 the search followed by

@@ -102,6 +102,7 @@ struct qlp_bls_plan {
   int32_t* d_ctl = nullptr;       // [0] per-point queue head, [1] cell queue head, [2] error flags
   // search + S/N captured as one CUDA graph (qlp_bls_graph_capture)
   // slot parts-1: parts = 1 search, 2 S/N, 3 both
+  int32_t* d_widx = nullptr;      // candidate statistics scratch (allocated on first use)
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph[3] = {};
   cudaGraphExec_t gexec[3] = {};
@@ -128,6 +129,7 @@ static void free_plan(qlp_bls_plan_t* pl) {
   cudaFree(pl->d_loc);
   cudaFree(pl->d_base);
   cudaFree(pl->d_gidx);
+  cudaFree(pl->d_widx);
   cudaFree(pl->d_ctl);
   delete pl;
 }
@@ -743,6 +745,27 @@ int qlp_bls_star_grid(const qlp_bls_params* pin, int64_t n, const double* t, con
 }
 
 void qlp_bls_plan_destroy(qlp_bls_plan_t* pl) { free_plan(pl); }
+
+int qlp_bls_candidate_stats(qlp_bls_plan_t* pl, void* stream, const qlp_bls_best* best, qlp_bls_cand_stats* out) {
+  if (!pl) return QLP_ERR_ARG;
+  if (pl->n_stars > 0 && (!best || !out)) return QLP_ERR_ARG;
+  if (pl->n_stars == 0) return QLP_OK;
+  if (!pl->d_widx) {
+    const int rc = dev_alloc(&pl->d_widx, (size_t)std::max<int64_t>(pl->n_points, 1));
+    if (rc) return rc;
+  }
+  StatsArgs a{};
+  a.stars = pl->d_stars;
+  a.n_stars = pl->n_stars;
+  a.tp = pl->d_tp;
+  a.y = pl->d_y;
+  a.dy = pl->d_dy;
+  a.best = best;
+  a.out = out;
+  a.widx = pl->d_widx;
+  const int e = launch_stats(a, stream);
+  return e ? cuda_fail((cudaError_t)e, "stats launch") : QLP_OK;
+}
 
 int qlp_bls_graph_capture(qlp_bls_plan_t* pl, int32_t parts, float* sr, uint8_t* qidx, uint32_t* phase_bin,
                           float* s_best, float* r_best, float* snr, qlp_bls_best* best) {

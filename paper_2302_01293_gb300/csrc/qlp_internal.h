@@ -172,6 +172,17 @@ int launch_prep_cells(const PrepCellsArgs& a, void* stream);
 int launch_cells(const CellArgs& a, int sum_mode, int warps, int blocks, size_t smem, void* stream);
 // bytes of shared memory before the histograms of the cell kernel for a star with
 // ncs cells (incl. sentinel) and nw warps
+struct StatsArgs {
+  const StarDev* stars;
+  int32_t n_stars;
+  const double* tp;
+  const double* y;
+  const double* dy;
+  const qlp_bls_best* best;
+  qlp_bls_cand_stats* out;
+  int32_t* widx;  // scratch: window point indices, CSR by pt_off
+};
+int launch_stats(const StatsArgs& a, void* stream);
 int record_cuda_error(cudaError_t e, const char* what);
 uint32_t cells_hist_offset(int ncs, int nw);
 int cells_blocks_per_sm(int sum_mode, int warps, size_t smem);

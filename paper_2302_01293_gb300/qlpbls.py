@@ -29,6 +29,14 @@ BEST_DTYPE = np.dtype([("f_idx", "<i8"), ("f", "<f8"), ("period", "<f8"), ("t0",
                        ("status", "<i4"), ("pad", "<i4")])
 assert BEST_DTYPE.itemsize == 88
 
+# qlp_bls_cand_stats
+STATS_DTYPE = np.dtype([("t0", "<f8"), ("depth", "<f8"), ("q", "<f8"), ("q_in", "<f8"), ("z", "<f8"),
+                        ("chi2", "<f8"), ("sigma_w", "<f8"), ("sigma_r", "<f8"), ("depth_mean", "<f8"),
+                        ("snr_pink", "<f8"), ("n_fit", "<i4"), ("n_in", "<i4"), ("n_before", "<i4"),
+                        ("n_after", "<i4"), ("n_transits", "<i4"), ("iterations", "<i4"), ("status", "<i4"),
+                        ("detected", "<i4")])
+assert STATS_DTYPE.itemsize == 112
+
 
 class CParams(ctypes.Structure):
     _fields_ = [("samples_per_peak", ctypes.c_double), ("dlogq", ctypes.c_double),
@@ -180,6 +188,8 @@ def lib():
             L.qlp_bls_graph_capture.restype = ctypes.c_int
             L.qlp_bls_graph_launch.argtypes = [_vp, _i32, _vp]
             L.qlp_bls_graph_launch.restype = ctypes.c_int
+            L.qlp_bls_candidate_stats.argtypes = [_vp, _vp, _vp, _vp]
+            L.qlp_bls_candidate_stats.restype = ctypes.c_int
             L.qlp_strerror.argtypes = [ctypes.c_int]
             L.qlp_strerror.restype = ctypes.c_char_p
             L.qlp_last_cuda_error.argtypes = []
@@ -336,6 +346,20 @@ class Plan:
 
     def graph_launch(self, parts: int = 3, stream=None):
         _check(lib().qlp_bls_graph_launch(self._h, int(parts), _stream_ptr(stream)), "qlp_bls_graph_launch")
+
+    def candidate_stats(self, out, stats=None, stream=None):
+        """qlp_bls_candidate_stats on the best records in `out` (after snr); returns
+        the device buffer of n_stars STATS_DTYPE records."""
+        import torch
+        if stats is None:
+            stats = torch.empty(max(self.n_stars, 1) * STATS_DTYPE.itemsize, dtype=torch.uint8, device=self.device)
+        _check(lib().qlp_bls_candidate_stats(self._h, _stream_ptr(stream), out["best"].data_ptr(), stats.data_ptr()),
+               "qlp_bls_candidate_stats")
+        return stats
+
+    def stats_host(self, stats) -> np.ndarray:
+        raw = stats.cpu().numpy()[: self.n_stars * STATS_DTYPE.itemsize]
+        return raw.view(STATS_DTYPE).copy()
 
     def best_host(self, out) -> np.ndarray:
         raw = out["best"].cpu().numpy()[: self.n_stars * BEST_DTYPE.itemsize]

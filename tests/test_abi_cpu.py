@@ -34,6 +34,15 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(L, n), n
 
 
+def test_every_exported_function_is_declared():
+    import subprocess
+    from paper_2302_01293_gb300 import build
+    so = build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True, check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.split() and ln.split()[-1].startswith("qlp_")}
+    assert exported and exported <= _declared(), sorted(exported - _declared())
+
+
 def test_params_default_matches_paper_settings():
     L = qlpbls.lib()
     p = qlpbls.CParams()

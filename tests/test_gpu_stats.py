@@ -1,0 +1,86 @@
+"""GPU post-BLS statistics (Sec. 2.2 items 2-5) against the oracle, both fed
+the GPU's best record so that only the statistics are compared: the fitted
+trapezoid, noise, signal-to-pink noise, counts and detection flags on stars
+whose injected transit the search recovered; validity of every record on the
+rest (noise-only candidates, where the fit is ill-conditioned)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import stats as ost
+from paper_2302_01293_gb300 import qlpbls
+
+pytestmark = pytest.mark.gpu
+
+PAR_RTOL = 1e-6
+
+
+def _run(batch, params=None):
+    import torch
+    plan = qlpbls.Plan(batch.offsets, batch.t, batch.y, batch.dy, batch.rho, batch.rstar, params)
+    out = plan.search()
+    plan.snr(out)
+    st = plan.candidate_stats(out)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    return plan, plan.best_host(out), plan.stats_host(st)
+
+
+def _check(batch, params=None, min_checked=1):
+    plan, best, stats = _run(batch, params)
+    checked = 0
+    for s in range(batch.n_stars):
+        g = stats[s]
+        b = best[s]
+        if b["f_idx"] < 0:
+            assert g["status"] == ost.ST_NO_CANDIDATE
+            continue
+        assert g["status"] in (ost.ST_OK, ost.ST_FEW_POINTS, ost.ST_NOT_CONVERGED)
+        assert np.isfinite([g["t0"], g["depth"], g["q"], g["q_in"], g["z"], g["sigma_w"], g["sigma_r"],
+                            g["snr_pink"]]).all()
+        t, y, dy = batch.star(s)
+        pl = oracle.plan_star(t, y, dy, float(batch.rho[s]), float(batch.rstar[s]))
+        bd = dict(period=float(b["period"]), t0=float(b["t0"]), q=float(b["q"]), depth=float(b["depth"]),
+                  snr=float(b["snr"]))
+        o = ost.star_stats(pl, bd)
+        assert g["n_fit"] == o["n_fit"], s
+        recovered = bool(batch.inj[s]) and abs(b["period"] / batch.period[s] - 1) < 0.01 and b["snr"] > 9
+        if not recovered:
+            continue
+        checked += 1
+        assert g["status"] == o["status"] == ost.ST_OK, (s, g["status"], o["status"])
+        per = float(b["period"])
+        assert abs(g["t0"] - o["t0"]) <= PAR_RTOL * per, s
+        for k in ("depth", "q", "q_in", "z", "sigma_w", "sigma_r", "depth_mean", "snr_pink"):
+            assert g[k] == pytest.approx(o[k], rel=PAR_RTOL, abs=1e-12), (s, k, g[k], o[k])
+        assert g["chi2"] == pytest.approx(o["chi2"], rel=1e-8), s
+        for k in ("n_in", "n_before", "n_after", "n_transits", "detected"):
+            assert g[k] == o[k], (s, k, g[k], o[k])
+    assert checked >= min_checked
+    return plan, best, stats
+
+
+def test_single_star_stats():
+    _, best, stats = _check(synth.single_star())
+    assert stats[0]["detected"] == 1 and stats[0]["n_transits"] >= 5
+    assert stats[0]["depth"] == pytest.approx(2e-3, rel=0.3)
+
+
+def test_uneven_batch_stats_both_paths():
+    b = synth.uneven_single_sector(n_stars=24, seed=41)
+    for method in (qlpbls.METHOD_CELLS, qlpbls.METHOD_POINTS):
+        _check(b, qlpbls.Params(method=method), min_checked=3)
+
+
+def test_multi_sector_stats():
+    _check(synth.multi_sector(n_stars=4, seed=5, max_sectors=4, frac_injected=1.0), min_checked=1)
+
+
+def test_tiny_and_rejected_stars_have_valid_records():
+    b = synth.tiny_batch(n_stars=6, seed=15)
+    plan, best, stats = _run(b)
+    for s in range(b.n_stars):
+        assert stats[s]["status"] in (0, 1, 2, 4)
+        if best[s]["f_idx"] < 0:
+            assert stats[s]["status"] == ost.ST_NO_CANDIDATE
