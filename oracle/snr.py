@@ -135,3 +135,24 @@ def snr_from_trend(freqs, sr, xs, ys, sigma):
         return np.zeros(len(sr))
     trend = np.interp(np.asarray(freqs, np.float64), xs, ys)
     return (np.asarray(sr, np.float64) - trend) / sigma
+
+
+def top_peaks(freqs, snr, n: int, sep: float = 0.01):
+    """The n strongest peaks of an S/N spectrum (not in the paper; the basis of
+    multiple candidates per star): repeatedly take the index of the largest S/N
+    (ties: lowest index) among the frequencies not yet excluded, then exclude
+    every frequency with |f / f_pick - 1| < sep. Returns up to n indices."""
+    f = np.asarray(freqs, np.float64)
+    v = np.asarray(snr, np.float64)
+    alive = np.ones(len(v), bool)
+    out = []
+    for _ in range(n):
+        if not alive.any():
+            break
+        cand = np.where(alive, v, -np.inf)
+        k = int(np.argmax(cand))
+        if not alive[k]:
+            break
+        out.append(k)
+        alive &= ~(np.abs(f / f[k] - 1.0) < sep)
+    return out

@@ -89,3 +89,29 @@ def test_linear_spectrum_detrends_to_spikes():
     snr, trend, sigma = osn.spectral_snr(f, sr, mad_mode="resid")
     top = np.argsort(snr)[-3:]
     assert sorted(top.tolist()) == [500, 2000, 3500]
+
+
+def test_top_peaks_separated_bumps_and_invariants():
+    from oracle import snr as osn
+    f = np.linspace(0.1, 3.0, 20000)
+    centres = [0.35, 0.9, 1.7, 2.6]
+    heights = [12.0, 30.0, 18.0, 9.0]
+    v = sum(h * np.exp(-0.5 * ((f - c) / 0.004) ** 2) for c, h in zip(centres, heights))
+    picks = osn.top_peaks(f, v, 4, sep=0.01)
+    # the bumps' maxima in order of height
+    order = np.argsort(heights)[::-1]
+    assert [round(f[k], 2) for k in picks] == [round(centres[i], 2) for i in order]
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        v = rng.normal(size=3000)
+        f = np.sort(rng.uniform(0.1, 3, 3000))
+        picks = osn.top_peaks(f, v, 8, sep=0.02)
+        assert picks[0] == int(np.argmax(v))
+        for a_ in range(len(picks)):
+            for b_ in range(a_ + 1, len(picks)):
+                assert abs(f[picks[b_]] / f[picks[a_]] - 1) >= 0.02
+        # every pick is the maximum of what its predecessors left
+        alive = np.ones(3000, bool)
+        for k in picks:
+            assert v[k] == v[alive].max()
+            alive &= ~(np.abs(f / f[k] - 1) < 0.02)
