@@ -283,6 +283,18 @@ int qlp_bls_autotune(const qlp_bls_params* p, int32_t n_stars, const int64_t* of
                      int32_t* cached);
 
 /*
+ * qlp_bls_top_peaks -- the n_peaks strongest peaks of each star's S/N spectrum
+ * (an extension: the paper keeps one candidate per star). Repeatedly the largest
+ * S/N (ties: the lowest index) among the frequencies not excluded yet is taken,
+ * and every frequency with |f / f_pick - 1| < sep is excluded (sep = 0.01 keeps
+ * peaks 1 % apart in period). out: device int32 [n_stars][n_peaks], indices in
+ * the star's grid, strongest first, -1 past the last. snr: device S/N from
+ * qlp_bls_snr of this plan. 1 <= n_peaks <= 64.
+ */
+int qlp_bls_top_peaks(const qlp_bls_plan_t* plan, void* stream, const float* snr, int32_t n_peaks,
+                      double sep, int32_t* out);
+
+/*
  * qlp_bls_candidate_stats -- post-BLS statistics of every star's best candidate
  * (Sec. 2.2 items 2-5): a trapezoid fit with the period fixed to the BLS period
  * (epoch, depth, q, ingress fraction q_in, out-of-transit level z; points within
@@ -323,6 +335,24 @@ typedef struct qlp_bls_cand_stats {
 } qlp_bls_cand_stats;
 int qlp_bls_candidate_stats(qlp_bls_plan_t* plan, void* stream, const qlp_bls_best* best,
                             qlp_bls_cand_stats* out);
+
+/*
+ * qlp_bls_search_multi -- several candidates per star by iterative masking (an
+ * extension: the paper reports one candidate per star). Round r runs the whole
+ * search (qlp_bls_plan, qlp_bls_search, qlp_bls_snr, qlp_bls_candidate_stats) on
+ * the points still kept, then removes every point within one fitted transit
+ * duration of the candidate's mid-transit times, |dt| < q P (fitted epoch and q
+ * when the fit ran, else the BLS box); a star that finds nothing stops.
+ * Arguments as for qlp_bls_plan (host arrays); outputs are host arrays:
+ *  best_host   qlp_bls_best[n_planets][n_stars] (f_idx -1 after a star stopped),
+ *  stats_host  qlp_bls_cand_stats[n_planets][n_stars],
+ *  n_found     int32[n_stars] candidates per star (optional).
+ * Device memory is allocated on `stream` and freed per round; synchronises it.
+ */
+int qlp_bls_search_multi(const qlp_bls_params* p, int32_t n_stars, const int64_t* offsets,
+                         const double* t, const double* y, const double* dy, const double* rho,
+                         const double* rstar, int32_t n_planets, void* stream, qlp_bls_best* best_host,
+                         qlp_bls_cand_stats* stats_host, int32_t* n_found);
 
 /*
  * qlp_bls_graph_capture -- record calls of this plan, with these output buffers

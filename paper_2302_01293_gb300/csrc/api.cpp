@@ -746,6 +746,14 @@ int qlp_bls_star_grid(const qlp_bls_params* pin, int64_t n, const double* t, con
 
 void qlp_bls_plan_destroy(qlp_bls_plan_t* pl) { free_plan(pl); }
 
+int qlp_bls_top_peaks(const qlp_bls_plan_t* pl, void* stream, const float* snr, int32_t n_peaks, double sep,
+                      int32_t* out) {
+  if (!pl || n_peaks < 1 || n_peaks > 64 || !(sep >= 0.0)) return QLP_ERR_ARG;
+  if (pl->n_stars > 0 && (!out || (pl->f_off.back() > 0 && !snr))) return QLP_ERR_ARG;
+  const int e = launch_peaks(pl->d_stars, pl->n_stars, pl->d_fq, snr, n_peaks, sep, out, stream);
+  return e ? cuda_fail((cudaError_t)e, "peaks launch") : QLP_OK;
+}
+
 int qlp_bls_candidate_stats(qlp_bls_plan_t* pl, void* stream, const qlp_bls_best* best, qlp_bls_cand_stats* out) {
   if (!pl) return QLP_ERR_ARG;
   if (pl->n_stars > 0 && (!best || !out)) return QLP_ERR_ARG;

@@ -182,6 +182,8 @@ struct StatsArgs {
   qlp_bls_cand_stats* out;
   int32_t* widx;  // scratch: window point indices, CSR by pt_off
 };
+int launch_peaks(const StarDev* stars, int n_stars, const double2* fq, const float* snr, int n_peaks, double sep,
+                 int32_t* out, void* stream);
 int launch_stats(const StatsArgs& a, void* stream);
 int record_cuda_error(cudaError_t e, const char* what);
 uint32_t cells_hist_offset(int ncs, int nw);

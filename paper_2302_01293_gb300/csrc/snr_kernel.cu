@@ -392,6 +392,87 @@ int launch_topk(const float* logits, const void* x0, int batch, int len, int k, 
   return (int)cudaGetLastError();
 }
 
+// The n strongest S/N peaks of each star: repeatedly the largest S/N (ties: the
+// lowest index) among the frequencies not excluded yet, then every frequency
+// with |f / f_pick - 1| < sep is excluded. The ratio is monotone along the
+// ascending grid, so each exclusion is one index range, found by binary search.
+constexpr int kMaxPeaks = 64;
+
+__device__ __forceinline__ bool near_pick(double f, double fp, double sep) {
+  return fabs(__dsub_rn(__ddiv_rn(f, fp), 1.0)) < sep;
+}
+
+__global__ void __launch_bounds__(256) peaks_kernel(const StarDev* stars, const double2* fq, const float* snr,
+                                                    int n_peaks, double sep, int32_t* out) {
+  __shared__ int s_lo[kMaxPeaks], s_hi[kMaxPeaks];
+  __shared__ float bv[8];
+  __shared__ int bi[8];
+  __shared__ int s_pick;
+  const int s = blockIdx.x;
+  const StarDev st = stars[s];
+  const int nf = st.n_f;
+  const float* v = snr + st.f_off;
+  const double2* f = fq + st.f_off;
+  int32_t* o = out + (size_t)s * n_peaks;
+  for (int r = threadIdx.x; r < n_peaks; r += blockDim.x) o[r] = -1;
+  for (int r = 0; r < n_peaks; ++r) {
+    float best = 0.f;
+    int bidx = 0x7fffffff;
+    for (int k = threadIdx.x; k < nf; k += blockDim.x) {
+      bool ex = false;
+      for (int i = 0; i < r; ++i) ex |= (k >= s_lo[i] && k <= s_hi[i]);
+      if (ex) continue;
+      const float x = v[k];
+      if (bidx == 0x7fffffff || x > best || (x == best && k < bidx)) { best = x; bidx = k; }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
+      if (oi != 0x7fffffff && (bidx == 0x7fffffff || ov > best || (ov == best && oi < bidx))) {
+        best = ov;
+        bidx = oi;
+      }
+    }
+    if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = bidx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < 8; ++w)
+        if (bi[w] != 0x7fffffff && (bidx == 0x7fffffff || bv[w] > best || (bv[w] == best && bi[w] < bidx))) {
+          best = bv[w];
+          bidx = bi[w];
+        }
+      s_pick = bidx;
+      if (bidx != 0x7fffffff) {
+        o[r] = bidx;
+        const double fp = f[bidx].x;
+        int a = 0, b = bidx;  // first index near the pick
+        while (a < b) {
+          const int m = (a + b) >> 1;
+          if (near_pick(f[m].x, fp, sep)) b = m; else a = m + 1;
+        }
+        s_lo[r] = a;
+        a = bidx;
+        b = nf - 1;  // last index near the pick
+        while (a < b) {
+          const int m = (a + b + 1) >> 1;
+          if (near_pick(f[m].x, fp, sep)) a = m; else b = m - 1;
+        }
+        s_hi[r] = a;
+      }
+    }
+    __syncthreads();
+    if (s_pick == 0x7fffffff) break;
+  }
+}
+
+int launch_peaks(const StarDev* stars, int n_stars, const double2* fq, const float* snr, int n_peaks, double sep,
+                 int32_t* out, void* stream) {
+  if (n_stars <= 0) return 0;
+  if (n_peaks < 1 || n_peaks > kMaxPeaks) return (int)cudaErrorInvalidValue;
+  peaks_kernel<<<n_stars, 256, 0, (cudaStream_t)stream>>>(stars, fq, snr, n_peaks, sep, out);
+  return (int)cudaGetLastError();
+}
+
 int launch_snr(const SnrArgs& a, void* stream) {
   if (a.n_stars <= 0) return 0;
   const size_t smem = (size_t)kMaxTargets * 256 * sizeof(uint32_t);

@@ -190,6 +190,11 @@ def lib():
             L.qlp_bls_graph_launch.restype = ctypes.c_int
             L.qlp_bls_candidate_stats.argtypes = [_vp, _vp, _vp, _vp]
             L.qlp_bls_candidate_stats.restype = ctypes.c_int
+            L.qlp_bls_top_peaks.argtypes = [_vp, _vp, _vp, _i32, ctypes.c_double, _vp]
+            L.qlp_bls_top_peaks.restype = ctypes.c_int
+            L.qlp_bls_search_multi.argtypes = [_P(CParams), _i32, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp,
+                                               _vp]
+            L.qlp_bls_search_multi.restype = ctypes.c_int
             L.qlp_strerror.argtypes = [ctypes.c_int]
             L.qlp_strerror.restype = ctypes.c_char_p
             L.qlp_last_cuda_error.argtypes = []
@@ -356,6 +361,14 @@ class Plan:
         _check(lib().qlp_bls_candidate_stats(self._h, _stream_ptr(stream), out["best"].data_ptr(), stats.data_ptr()),
                "qlp_bls_candidate_stats")
         return stats
+
+    def top_peaks(self, out, n: int, sep: float = 0.01, stream=None):
+        """qlp_bls_top_peaks on out["snr"]: device int32 [n_stars, n]."""
+        import torch
+        idx = torch.empty(max(self.n_stars, 1), int(n), dtype=torch.int32, device=self.device)
+        _check(lib().qlp_bls_top_peaks(self._h, _stream_ptr(stream), out["snr"].data_ptr(), int(n), float(sep),
+                                       idx.data_ptr()), "qlp_bls_top_peaks")
+        return idx
 
     def stats_host(self, stats) -> np.ndarray:
         raw = stats.cpu().numpy()[: self.n_stars * STATS_DTYPE.itemsize]
@@ -591,3 +604,20 @@ def search_learned(offsets, t, y, dy, rho, rstar, net: CNN, k: int = 32, half_wi
                                   float(half_width), _stream_ptr(stream), _np_ptr(best), _np_ptr(bins))
     _check(rc, "qlp_bls_search_learned")
     return best[:n_stars], bins[:n_stars]
+
+
+def search_multi(offsets, t, y, dy, rho=None, rstar=None, n_planets: int = 3, params: Params | None = None,
+                 stream=None):
+    """qlp_bls_search_multi: (best [n_planets, n_stars], stats [n_planets, n_stars], n_found [n_stars])."""
+    L = lib()
+    offsets, t, y, dy, rho, rstar = _host_inputs(offsets, t, y, dy, rho, rstar)
+    n_stars = int(offsets.shape[0] - 1)
+    cp = (params or Params()).to_c()
+    best = np.zeros((int(n_planets), max(n_stars, 1)), BEST_DTYPE)
+    stats = np.zeros((int(n_planets), max(n_stars, 1)), STATS_DTYPE)
+    found = np.zeros(max(n_stars, 1), np.int32)
+    rc = L.qlp_bls_search_multi(ctypes.byref(cp), n_stars, _np_ptr(offsets), _np_ptr(t), _np_ptr(y), _np_ptr(dy),
+                                _np_ptr(rho), _np_ptr(rstar), int(n_planets), _stream_ptr(stream), _np_ptr(best),
+                                _np_ptr(stats), _np_ptr(found))
+    _check(rc, "qlp_bls_search_multi")
+    return best[:, :n_stars], stats[:, :n_stars], found[:n_stars]

@@ -84,3 +84,51 @@ def test_tiny_and_rejected_stars_have_valid_records():
         assert stats[s]["status"] in (0, 1, 2, 4)
         if best[s]["f_idx"] < 0:
             assert stats[s]["status"] == ost.ST_NO_CANDIDATE
+
+
+def _two_planet_batch(n_stars, seed):
+    rng = np.random.default_rng(seed)
+    ts, ys, dys, inj, per, t0s, deps, durs = [], [], [], [], [], [], [], []
+    for s in range(n_stars):
+        t = synth.T_START + np.arange(0.0, 27.4, 1.0 / 48.0)
+        y = 1.0 + rng.normal(0.0, 1e-3, t.shape)
+        p1, p2 = rng.uniform(1.5, 4.0), rng.uniform(5.0, 9.0)
+        for p_, d_ in ((p1, 4e-3), (p2, 3e-3)):
+            y -= d_ * synth.box_mask(t, p_, synth.T_START + rng.uniform(0, p_),
+                                     synth.circular_duration_days(p_, 1.41, 1.0))
+        ts.append(t); ys.append(y); dys.append(np.full(t.shape, 1e-3))
+        inj.append(True); per.append(p1); t0s.append(0.0); deps.append(4e-3); durs.append(0.1)
+    return synth._assemble("two_planets", ts, ys, dys, [1.41] * n_stars, [1.0] * n_stars, inj, per, t0s,
+                           deps, durs)
+
+
+def test_multi_planet_search_matches_oracle():
+    from oracle import multi
+    b = _two_planet_batch(3, 7)
+    best, stats, found = qlpbls.search_multi(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar, n_planets=3)
+    for s in range(b.n_stars):
+        t, y, dy = b.star(s)
+        o = multi.search_multi(t, y, dy, 1.41, 1.0, 3)
+        assert found[s] == len(o)
+        for r, (ob, ost_) in enumerate(o[:2]):
+            g = best[r, s]
+            assert g["f_idx"] == ob["f_idx"], (s, r)
+            assert g["period"] == ob["period"]
+            assert stats[r, s]["n_transits"] == ost_["n_transits"]
+            assert stats[r, s]["q"] == pytest.approx(ost_["q"], rel=PAR_RTOL)
+
+
+def test_top_peaks_match_oracle_selection():
+    from oracle import snr as osn
+    import torch
+    b = _two_planet_batch(2, 9)
+    plan = qlpbls.Plan(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar)
+    out = plan.search()
+    plan.snr(out)
+    idx = plan.top_peaks(out, 8, 0.01).cpu().numpy()
+    snr = out["snr"].cpu().numpy()
+    for s in range(b.n_stars):
+        sl = plan.star_slice(s)
+        ref = osn.top_peaks(plan.freqs[sl], snr[sl].astype(np.float64), 8, 0.01)
+        assert idx[s][:len(ref)].tolist() == ref and np.all(idx[s][len(ref):] == -1)
+        assert idx[s][0] == plan.best_host(out)[s]["f_idx"]
