@@ -48,12 +48,21 @@ extern "C" {
 #define QLP_STAR_EMPTY_GRID  4  /* Pmin >= Pmax or zero baseline: nothing to search */
 #define QLP_STAR_NBINS_CAP   8  /* some frequency needs more phase bins than nbins_cap */
 #define QLP_STAR_ZERO_MAD   16  /* sigma_SR = 0: S/N undefined, no candidate */
+#define QLP_STAR_UNSUPPORTED 32 /* the star cannot be searched with these options (bin_mode
+                                   QLP_BIN_PER_Q needs the cell path: one point per cell) */
 
 /* ---- options ---- */
 #define QLP_PHASE_FP64  0  /* fold x = t'f and its bin in FP64, the oracle's exact sequence */
 #define QLP_PHASE_DF    1  /* double-float (hi/lo FP32) fold; bins identical to FP64:
                               points within a guard band of a bin edge are re-folded in FP64 */
 #define QLP_PHASE_FP32  2  /* plain FP32 fold (precision study only; bins may differ) */
+
+#define QLP_BIN_SHARED  0  /* Sec. 2.1 footnote reading: one histogram of bins q_min / noverlap
+                              per frequency; every duration q_j is a window of m_j of its bins */
+#define QLP_BIN_PER_Q   1  /* variant: a histogram of bins q_j / noverlap for each duration q_j
+                              (ceil(noverlap / q_j) bins), each box a window of noverlap bins
+                              (noverlap must be an integer); reported j and k refer to
+                              histogram j. Cell path only. */
 
 #define QLP_SUM_PLAIN   0  /* FP32 histogram sums */
 #define QLP_SUM_COMP    1  /* FP32 sums with the rounding error of every shared-memory add
@@ -93,6 +102,8 @@ typedef struct qlp_bls_params {
                                of it; a star whose table is longer is searched window by window */
   double coarse_pmin;       /* 0.1 d */
   double coarse_pmax;       /* 400 d */
+  int32_t bin_mode;         /* QLP_BIN_* (default QLP_BIN_SHARED) */
+  int32_t reserved1;
 } qlp_bls_params;
 
 /* Best candidate of one star: the frequency of maximum S/N and its BLS box. */

@@ -100,6 +100,29 @@ def bls_star(plan) -> StarBLS:
     return StarBLS(sr, jb, kb, sb, rb)
 
 
+def bls_star_per_q(plan, noverlap: float = 3.0, dlogq: float = 0.1) -> StarBLS:
+    """The per-duration binning variant: for each duration q_j = q_min e^{j dlogq}
+    its own histogram of ceil(noverlap / q_j) bins (bin width q_j / noverlap) and
+    boxes of noverlap consecutive bins; SR(f) = the largest residue over j and k
+    (ties: lower j, then lower k); j and k of the result refer to histogram j.
+    Each histogram is the plain BLS of this module with one box width."""
+    import dataclasses
+    nf = plan.freqs.shape[0]
+    nq = plan.m.shape[1]
+    m_int = int(noverlap)
+    sr = np.zeros(nf); sb = np.zeros(nf); rb = np.zeros(nf)
+    jb = np.full(nf, -1, np.int32); kb = np.full(nf, -1, np.int32)
+    for j in range(nq):
+        e = math.exp(j * dlogq)
+        nbj = np.array([int(math.ceil(noverlap / (q * e))) for q in plan.qmin], np.int32)
+        sub = dataclasses.replace(plan, nbins=nbj, m=np.full((nf, 1), m_int, np.int32))
+        r = bls_star(sub)
+        take = (r.j >= 0) & ((jb < 0) | (r.sr > sr))
+        sr[take] = r.sr[take]; sb[take] = r.s[take]; rb[take] = r.r[take]
+        jb[take] = j; kb[take] = r.k[take]
+    return StarBLS(sr, jb, kb, sb, rb)
+
+
 def restrict(plan, idx):
     """The same star plan with only the trial frequencies plan.freqs[idx] (each
     frequency's search is independent of the others, Sec. 2.1), so that long

@@ -106,8 +106,10 @@ def spectral_snr(freqs, sr, mad_mode: str = "raw"):
     return (sr - trend) / sigma, trend, sigma
 
 
-def best_candidate(plan, bls, snr, sigma):
-    """Best (P, T0, q, depth) at the S/N maximum, or None when there is none."""
+def best_candidate(plan, bls, snr, sigma, per_q=None):
+    """Best (P, T0, q, depth) at the S/N maximum, or None when there is none.
+    per_q = (noverlap, dlogq) for a spectrum of the per-duration binning variant,
+    whose box j, k lies on histogram j (ceil(noverlap / q_j) bins, noverlap wide)."""
     n = len(snr)
     if n == 0 or sigma == 0.0:
         return None
@@ -116,8 +118,13 @@ def best_candidate(plan, bls, snr, sigma):
     if j < 0:
         return None
     f = float(plan.freqs[k])
-    nb = int(plan.nbins[k])
-    m = int(plan.m[k, j])
+    if per_q is None:
+        nb = int(plan.nbins[k])
+        m = int(plan.m[k, j])
+    else:
+        noverlap, dlogq = per_q
+        nb = int(math.ceil(noverlap / (float(plan.qmin[k]) * math.exp(j * dlogq))))
+        m = int(noverlap)
     kb = int(bls.k[k])
     period = 1.0 / f
     mid = (kb + 0.5 * m) / nb

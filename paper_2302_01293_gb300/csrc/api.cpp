@@ -160,6 +160,8 @@ void qlp_bls_params_default(qlp_bls_params* p) {
   p->cell_window = 0;
   p->coarse_pmin = 0.1;
   p->coarse_pmax = 400.0;
+  p->bin_mode = QLP_BIN_SHARED;
+  p->reserved1 = 0;
 }
 
 const char* qlp_strerror(int code) {
@@ -183,7 +185,9 @@ static int check_params(const qlp_bls_params& p) {
     return QLP_ERR_ARG;
   if (p.phase_mode < 0 || p.phase_mode > 2 || p.sum_mode < 0 || p.sum_mode > 1 || p.mad_mode < 0 ||
       p.mad_mode > 1 || p.tile_points < 0 || p.chunk_freqs < 0 || p.method < 0 || p.method > 2 ||
-      p.grid_mode < 0 || p.grid_mode > 1 || p.cell_window < 0 ||
+      p.grid_mode < 0 || p.grid_mode > 1 || p.cell_window < 0 || p.bin_mode < 0 || p.bin_mode > 1 ||
+      (p.bin_mode == QLP_BIN_PER_Q && (p.noverlap != std::floor(p.noverlap) || p.phase_mode == QLP_PHASE_FP32 ||
+                                       p.method == 1)) ||
       (p.grid_mode == 1 && (p.coarse_bins < 2 || !(p.coarse_pmin > 0) || !(p.coarse_pmax > p.coarse_pmin))))
     return QLP_ERR_ARG;
   if (p.warps_per_block != 0 && p.warps_per_block != 4 && p.warps_per_block != 8 &&
@@ -298,8 +302,11 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
     }
     if (cell_smem(W.cap, h.nbins_max) > (size_t)budget) continue;
     const double pp_work = (double)h.freqs.size() * (double)round32((int64_t)h.tp.size());
-    if (p.method == 2 || h.cells_work < pp_work) method[(size_t)s] = kMethodCells;
+    if (p.method == 2 || p.bin_mode == QLP_BIN_PER_Q || h.cells_work < pp_work) method[(size_t)s] = kMethodCells;
   }
+  if (p.bin_mode == QLP_BIN_PER_Q)  // per-duration histograms exist on the cell path only
+    for (int32_t s = 0; s < n_stars; ++s)
+      if (sp[(size_t)s].status == 0 && method[(size_t)s] != kMethodCells) sp[(size_t)s].status = QLP_STAR_UNSUPPORTED;
 
   // flat host arrays
   std::vector<StarDev> stars((size_t)n_stars);
@@ -599,6 +606,8 @@ int qlp_bls_search(qlp_bls_plan_t* pl, void* stream, float* sr, uint8_t* qidx, u
     c.sbest = s_best;
     c.rbest = r_best;
     c.noverlap = pl->p.noverlap;
+    c.per_q = pl->p.bin_mode == QLP_BIN_PER_Q ? 1 : 0;
+    c.m_perq = (int32_t)pl->p.noverlap;
     for (int j = 0; j < kMaxQ; ++j) c.E[j] = pl->E[j];
     e = launch_cells(c, pl->p.sum_mode, pl->c_warps, pl->c_blocks, pl->c_smem, stream);
     if (e) return cuda_fail((cudaError_t)e, "cell search launch");
@@ -655,6 +664,8 @@ int qlp_bls_snr_trend(qlp_bls_plan_t* pl, void* stream, const float* sr, const u
   a.nq = pl->nq;
   a.mad_mode = pl->p.mad_mode;
   a.n_stars = pl->n_stars;
+  a.per_q = pl->p.bin_mode == QLP_BIN_PER_Q ? 1 : 0;
+  a.m_perq = (int32_t)pl->p.noverlap;
   const int e = launch_snr(a, stream);
   if (e) return cuda_fail((cudaError_t)e, "snr launch");
   return QLP_OK;

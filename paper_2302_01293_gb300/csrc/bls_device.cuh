@@ -199,12 +199,12 @@ struct PackedBin<QLP_SUM_COMP> {
   __device__ static float yc(const T& v) { return v.w; }
 };
 
-// sweep_store over a packed histogram: the same window sums, in the same order,
-// as sweep_store over separate arrays (bit-identical results).
+// The box sweep over a packed histogram: the same window sums, in the same
+// order, as sweep_store over separate arrays (bit-identical results); every lane
+// returns the warp's best box.
 template <int SUM>
-__device__ __forceinline__ void sweep_store_packed(typename PackedBin<SUM>::T* h, const int* mtab, int nq, int nb,
-                                                   int lane, int64_t fidx, float* sr, uint8_t* qidx,
-                                                   uint32_t* kbin, float* sbest, float* rbest) {
+__device__ __forceinline__ BoxBest sweep_best_packed(typename PackedBin<SUM>::T* h, const int* mtab, int nq, int nb,
+                                                     int lane) {
   using PB = PackedBin<SUM>;
   for (int i = lane; i < kMPad; i += 32) h[nb + i] = h[i % nb];
   __syncwarp();
@@ -253,14 +253,22 @@ __device__ __forceinline__ void sweep_store_packed(typename PackedBin<SUM>::T* h
       bs2 = o_s2; bd = o_d; bsv = o_s; brv = o_r; bj = o_j; bk = o_k;
     }
   }
-  if (lane == 0) {
-    const bool none = bs2 < 0.f;
-    sr[fidx] = none ? 0.f : __fdiv_rn(bs2, bd);
-    if (qidx) qidx[fidx] = none ? (uint8_t)255 : (uint8_t)bj;
-    if (kbin) kbin[fidx] = none ? 0xffffffffu : (uint32_t)bk;
-    if (sbest) sbest[fidx] = none ? 0.f : bsv;
-    if (rbest) rbest[fidx] = none ? 0.f : brv;
-  }
+  BoxBest o;
+  o.s2 = bs2; o.d = bd; o.s = bsv; o.r = brv; o.j = bj; o.k = bk;
+  return o;
+}
+
+// Lane 0 stores a frequency's best box: SR = s^2/d, j, k, s, r (SR 0, j 255,
+// k 0xFFFFFFFF when no window was valid).
+__device__ __forceinline__ void store_box(const BoxBest& b, int lane, int64_t fidx, float* sr, uint8_t* qidx,
+                                          uint32_t* kbin, float* sbest, float* rbest) {
+  if (lane != 0) return;
+  const bool none = b.s2 < 0.f;
+  sr[fidx] = none ? 0.f : __fdiv_rn(b.s2, b.d);
+  if (qidx) qidx[fidx] = none ? (uint8_t)255 : (uint8_t)b.j;
+  if (kbin) kbin[fidx] = none ? 0xffffffffu : (uint32_t)b.k;
+  if (sbest) sbest[fidx] = none ? 0.f : b.s;
+  if (rbest) rbest[fidx] = none ? 0.f : b.r;
 }
 
 }  // namespace qlp

@@ -279,94 +279,113 @@ __global__ void __launch_bounds__(NW * 32) cells_kernel(const CellArgs a) {
       const int fl = r0 + warp;
       const bool active = warp < wact && fl < wi.f_count;
       const int64_t fidx = st.f_off + wi.f_begin + (active ? fl : 0);
-      double f = 0.0, F = 1.0;
-      int nb = 1, g_end = 0;
-      uint32_t k_lo = 0, k_hi = 0, band_q = 0;
-      bool go = active;
+      // one pass over the shared histogram, or one per duration (per-duration bins)
+      const int n_pass = a.per_q ? nq : 1;
+      BoxBest acc;
+      acc.s2 = -1.f; acc.d = 1.f; acc.s = 0.f; acc.r = 0.f; acc.j = 255; acc.k = -1;
+      bool failed = false;
+      for (int pass = 0; pass < n_pass; ++pass) {
+        double f = 0.0, F = 1.0;
+        int nb = 1, g_end = 0;
+        uint32_t k_lo = 0, k_hi = 0, band_q = 0;
+        bool go = active && !failed;
+        if (go) {
+          const double2 fq = a.fq[fidx];
+          f = fq.x;
+          const double qb = a.per_q ? __dmul_rn(fq.y, a.E[pass]) : fq.y;  // bin = qb / noverlap
+          nb = (int)ceil(__ddiv_rn(a.noverlap, qb));
+          if (nb + kMPad > HS || nb < 1) {
+            if (lane == 0) atomicOr(a.err, kErrNbins);
+            go = false;
+            failed = true;
+          } else {
+            if (a.per_q) {
+              if (lane == 0) mtab[0] = a.m_perq;
+            } else if (lane < nq) {
+              mtab[lane] = max(1, (int)floor(__dadd_rn(__dmul_rn(__dmul_rn(fq.y, a.E[lane]), (double)nb), 0.5)));
+            }
+            for (int i = lane; i < nb + kMPad; i += 32) hist[i] = HT{};
+            F = __dmul_rn(f, (double)nb);
+            const double D = __ddiv_rn(1.0, F);  // bin duration (days)
+            const double yT = __dmul_rn(st.baseline, F);
+            g_end = (int)floor(yT) + 2;  // edges 0 .. g_end; tau_{g_end} > T
+            // edge step in cells, 2^-56 fixed point (D/h < 2^8)
+            const unsigned long long K = __double2ull_rn(__dmul_rn(__ddiv_rn(D, h), 72057594037927936.0));
+            k_lo = (uint32_t)K;
+            k_hi = (uint32_t)(K >> 32);
+            // guard band in 2^-32 cell units: the FP64 fold's and this fixed-point edge's
+            // errors (2^-20 + 2^-40 T F bins, converted) plus the table's quantisation
+            band_q = (uint32_t)fmin(
+                __dmul_rn(__ddiv_rn(__dmul_rn(9.5367431640625e-07 + 9.094947017729282e-13 * yT, D), h),
+                          4294967296.0) + 64.0, 1073741824.0);
+          }
+        }
+        __syncwarp();
+        const bool own = nb >= 31;  // the 31 pieces of one chunk fall in distinct bins
+        const int step = 31 % nb;
+
+        for (int w = 0; w < n_win; ++w) {
+          const int cstart = w * st.win_cells;  // first cell owned by window w
+          const int lo = (n_win == 1) ? 0 : max(0, ((cstart - 1) >> 5) << 5);
+          const int hi = (w == n_win - 1) ? nc : min(nc, (w + 1) * st.win_cells + st.win_ovl);
+          const int n_loc = hi - lo + 1;
+          if (s_star != wi.star || s_win != w) {  // block-uniform
+            __syncthreads();
+            uint32_t* d_dt = reinterpret_cast<uint32_t*>(smem);
+            float2* d_loc = reinterpret_cast<float2*>(smem + L.loc);
+            float4* d_base = reinterpret_cast<float4*>(smem + L.base);
+            for (int i = threadIdx.x; i < n_loc; i += NW * 32) {
+              d_dt[i] = a.dt[st.cell_off + lo + i];
+              d_loc[i] = a.loc[st.cell_off + lo + i];
+            }
+            const int b0 = lo >> 5, b1 = hi >> 5;
+            for (int i = threadIdx.x; i <= b1 - b0; i += NW * 32) d_base[i] = a.base[st.base_off + b0 + i];
+            if (threadIdx.x == 0) { s_star = wi.star; s_win = w; }
+            __syncthreads();
+          }
+          if (!go) continue;
+          // pieces [gs, ge) of this window: edges from the first at or after its start
+          const int gs = (w == 0) ? 0 : (int)ceil(__dmul_rn(__dmul_rn((double)cstart, h), F));
+          const int ge = (w == n_win - 1) ? g_end
+                                          : (int)ceil(__dmul_rn(__dmul_rn((double)((w + 1) * st.win_cells), h), F));
+          int b = (gs + lane) % nb;  // bin of this lane's piece in the first chunk
+          for (int g0 = gs; g0 < ge; g0 += 62) {
+            // two chunks of 31 pieces in flight: edges g0 .. g0+31 and g0+31 .. g0+62
+            const EdgeC c0 = edge_prefix(g0 + lane, g0 + lane <= ge, k_lo, k_hi, nc, lo, n_loc, band_q, s_dt,
+                                         s_loc, s_base, tp, gidx, f, nb);
+            const EdgeC c1 = edge_prefix(g0 + 31 + lane, g0 + 31 + lane <= ge, k_lo, k_hi, nc, lo, n_loc,
+                                         band_q, s_dt, s_loc, s_base, tp, gidx, f, nb);
+            const float2 p0 = edge_piece(c0);
+            const float2 p1 = edge_piece(c1);
+            int b1 = b + step;
+            if (b1 >= nb) b1 -= nb;
+            add_piece<SUM>(hist, b, p0, own, lane < 31 && g0 + lane < ge);
+            add_piece<SUM>(hist, b1, p1, own, lane < 31 && g0 + 31 + lane < ge);
+            b = b1 + step;
+            if (b >= nb) b -= nb;
+          }
+        }
+        if (go) {
+          __syncwarp();
+          BoxBest bb = sweep_best_packed<SUM>(hist, mtab, a.per_q ? 1 : nq, nb, lane);
+          if (a.per_q && bb.s2 >= 0.f) bb.j = pass;  // the duration of this histogram
+          // across passes: a later (longer) duration must beat the earlier ones strictly
+          if (beats(bb.s2, bb.d, bb.j, bb.k, acc.s2, acc.d, acc.j, acc.k)) acc = bb;
+          __syncwarp();
+        }
+      }
       if (active) {
-        const double2 fq = a.fq[fidx];
-        f = fq.x;
-        nb = (int)ceil(__ddiv_rn(a.noverlap, fq.y));
-        if (nb + kMPad > HS || nb < 1) {
+        if (failed) {
           if (lane == 0) {
-            atomicOr(a.err, kErrNbins);
             a.sr[fidx] = 0.f;
             if (a.qidx) a.qidx[fidx] = 255;
             if (a.kbin) a.kbin[fidx] = 0xffffffffu;
             if (a.sbest) a.sbest[fidx] = 0.f;
             if (a.rbest) a.rbest[fidx] = 0.f;
           }
-          go = false;
         } else {
-          if (lane < nq)
-            mtab[lane] = max(1, (int)floor(__dadd_rn(__dmul_rn(__dmul_rn(fq.y, a.E[lane]), (double)nb), 0.5)));
-          for (int i = lane; i < nb + kMPad; i += 32) {
-            hist[i] = HT{};
-          }
-          F = __dmul_rn(f, (double)nb);
-          const double D = __ddiv_rn(1.0, F);  // bin duration (days)
-          const double yT = __dmul_rn(st.baseline, F);
-          g_end = (int)floor(yT) + 2;  // edges 0 .. g_end; tau_{g_end} > T
-          // edge step in cells, 2^-56 fixed point (D/h < 2^8)
-          const unsigned long long K = __double2ull_rn(__dmul_rn(__ddiv_rn(D, h), 72057594037927936.0));
-          k_lo = (uint32_t)K;
-          k_hi = (uint32_t)(K >> 32);
-          // guard band in 2^-32 cell units: the FP64 fold's and this fixed-point edge's
-          // errors (2^-20 + 2^-40 T F bins, converted) plus the table's quantisation
-          band_q = (uint32_t)fmin(
-              __dmul_rn(__ddiv_rn(__dmul_rn(9.5367431640625e-07 + 9.094947017729282e-13 * yT, D), h),
-                        4294967296.0) + 64.0, 1073741824.0);
+          store_box(acc, lane, fidx, a.sr, a.qidx, a.kbin, a.sbest, a.rbest);
         }
-      }
-      __syncwarp();
-      const bool own = nb >= 31;  // the 31 pieces of one chunk fall in distinct bins
-      const int step = 31 % nb;
-
-      for (int w = 0; w < n_win; ++w) {
-        const int cstart = w * st.win_cells;  // first cell owned by window w
-        const int lo = (n_win == 1) ? 0 : max(0, ((cstart - 1) >> 5) << 5);
-        const int hi = (w == n_win - 1) ? nc : min(nc, (w + 1) * st.win_cells + st.win_ovl);
-        const int n_loc = hi - lo + 1;
-        if (s_star != wi.star || s_win != w) {  // block-uniform
-          __syncthreads();
-          uint32_t* d_dt = reinterpret_cast<uint32_t*>(smem);
-          float2* d_loc = reinterpret_cast<float2*>(smem + L.loc);
-          float4* d_base = reinterpret_cast<float4*>(smem + L.base);
-          for (int i = threadIdx.x; i < n_loc; i += NW * 32) {
-            d_dt[i] = a.dt[st.cell_off + lo + i];
-            d_loc[i] = a.loc[st.cell_off + lo + i];
-          }
-          const int b0 = lo >> 5, b1 = hi >> 5;
-          for (int i = threadIdx.x; i <= b1 - b0; i += NW * 32) d_base[i] = a.base[st.base_off + b0 + i];
-          if (threadIdx.x == 0) { s_star = wi.star; s_win = w; }
-          __syncthreads();
-        }
-        if (!go) continue;
-        // pieces [gs, ge) of this window: edges from the first at or after its start
-        const int gs = (w == 0) ? 0 : (int)ceil(__dmul_rn(__dmul_rn((double)cstart, h), F));
-        const int ge = (w == n_win - 1) ? g_end
-                                        : (int)ceil(__dmul_rn(__dmul_rn((double)((w + 1) * st.win_cells), h), F));
-        int b = (gs + lane) % nb;  // bin of this lane's piece in the first chunk
-        for (int g0 = gs; g0 < ge; g0 += 62) {
-          // two chunks of 31 pieces in flight: edges g0 .. g0+31 and g0+31 .. g0+62
-          const EdgeC c0 = edge_prefix(g0 + lane, g0 + lane <= ge, k_lo, k_hi, nc, lo, n_loc, band_q, s_dt,
-                                       s_loc, s_base, tp, gidx, f, nb);
-          const EdgeC c1 = edge_prefix(g0 + 31 + lane, g0 + 31 + lane <= ge, k_lo, k_hi, nc, lo, n_loc,
-                                       band_q, s_dt, s_loc, s_base, tp, gidx, f, nb);
-          const float2 p0 = edge_piece(c0);
-          const float2 p1 = edge_piece(c1);
-          int b1 = b + step;
-          if (b1 >= nb) b1 -= nb;
-          add_piece<SUM>(hist, b, p0, own, lane < 31 && g0 + lane < ge);
-          add_piece<SUM>(hist, b1, p1, own, lane < 31 && g0 + 31 + lane < ge);
-          b = b1 + step;
-          if (b >= nb) b -= nb;
-        }
-      }
-      if (go) {
-        __syncwarp();
-        sweep_store_packed<SUM>(hist, mtab, nq, nb, lane, fidx, a.sr, a.qidx, a.kbin, a.sbest,
-                         a.rbest);
       }
     }
   }

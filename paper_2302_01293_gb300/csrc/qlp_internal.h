@@ -100,6 +100,8 @@ struct CellArgs {
   float* rbest;
   double noverlap;
   double E[kMaxQ];
+  int32_t per_q;           // QLP_BIN_PER_Q: one histogram of bins q_j / noverlap per duration j
+  int32_t m_perq;          // bins per box in that mode (noverlap)
 };
 
 struct PrepCellsArgs {
@@ -150,7 +152,8 @@ struct SnrArgs {
   int32_t nq;
   int32_t mad_mode;
   int32_t n_stars;
-  int32_t pad0;
+  int32_t per_q;             // QLP_BIN_PER_Q: box j is m_perq bins of histogram j
+  int32_t m_perq;
 };
 
 // device error flags

@@ -297,8 +297,12 @@ __global__ void __launch_bounds__(kSnrThreads) snr_kernel(const SnrArgs a) {
     } else {
       const double f = fq[bi].x;
       const double qmin = fq[bi].y;
-      const int nb = (int)ceil(__ddiv_rn(a.noverlap, qmin));
-      const int m = max(1, (int)floor(__dadd_rn(__dmul_rn(__dmul_rn(qmin, a.E[j]), (double)nb), 0.5)));
+      // shared histogram: nbins(q_min) and the window m_j; per-duration histograms:
+      // nbins(q_j) bins of q_j / noverlap and a window of noverlap bins
+      const int nb = a.per_q ? (int)ceil(__ddiv_rn(a.noverlap, __dmul_rn(qmin, a.E[j])))
+                             : (int)ceil(__ddiv_rn(a.noverlap, qmin));
+      const int m = a.per_q ? a.m_perq
+                            : max(1, (int)floor(__dadd_rn(__dmul_rn(__dmul_rn(qmin, a.E[j]), (double)nb), 0.5)));
       const int kb = (int)a.kbin[st.f_off + bi];
       const double period = __ddiv_rn(1.0, f);
       const double mid = __ddiv_rn(__dadd_rn((double)kb, __dmul_rn(0.5, (double)m)), (double)nb);

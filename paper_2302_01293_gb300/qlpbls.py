@@ -17,6 +17,7 @@ from . import build as _build
 
 PHASE_FP64, PHASE_DF, PHASE_FP32 = 0, 1, 2
 SUM_PLAIN, SUM_COMP = 0, 1
+BIN_SHARED, BIN_PER_Q = 0, 1
 MAD_RAW, MAD_RESID = 0, 1
 METHOD_AUTO, METHOD_POINTS, METHOD_CELLS = 0, 1, 2
 TREND_DOUBLES = 84
@@ -49,7 +50,8 @@ class CParams(ctypes.Structure):
                 ("n_threads", ctypes.c_int32), ("tile_points", ctypes.c_int32),
                 ("method", ctypes.c_int32), ("grid_mode", ctypes.c_int32),
                 ("coarse_bins", ctypes.c_int32), ("cell_window", ctypes.c_int32),
-                ("coarse_pmin", ctypes.c_double), ("coarse_pmax", ctypes.c_double)]
+                ("coarse_pmin", ctypes.c_double), ("coarse_pmax", ctypes.c_double),
+                ("bin_mode", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
 
 @dataclasses.dataclass
@@ -76,6 +78,8 @@ class Params:
     cell_window: int = 0
     coarse_pmin: float = 0.1
     coarse_pmax: float = 400.0
+    bin_mode: int = 0
+    reserved1: int = 0
 
     def to_c(self) -> CParams:
         c = CParams()

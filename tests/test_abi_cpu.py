@@ -49,7 +49,7 @@ def test_params_default_matches_paper_settings():
     L.qlp_bls_params_default(ctypes.byref(p))
     assert (p.samples_per_peak, p.dlogq, p.noverlap) == (2.0, 0.1, 3.0)
     assert (p.qmin_fac, p.qmax_fac, p.pmin_aR, p.gap_days, p.rho_default) == (0.5, 2.0, 2.0, 27.4, 1.41)
-    assert ctypes.sizeof(qlpbls.CParams) == 128
+    assert ctypes.sizeof(qlpbls.CParams) == 136 and p.bin_mode == 0
     assert (p.grid_mode, p.coarse_bins, p.coarse_pmin, p.coarse_pmax) == (0, 4096, 0.1, 400.0)
 
 

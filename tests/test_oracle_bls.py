@@ -174,3 +174,41 @@ def test_restricted_plan_equals_full_search_at_those_frequencies():
         sub = ob.bls_star(ob.restrict(pl, idx))
         assert np.array_equal(sub.sr, full.sr[idx])
         assert np.array_equal(sub.j, full.j[idx]) and np.array_equal(sub.k, full.k[idx])
+
+
+def test_per_q_binning_brute_force_and_special_case():
+    from oracle import bls as ob
+    b = synth.tiny_batch(n_stars=2, seed=13, n_min=30, n_max=60)
+    for s in range(2):
+        t, y, dy = b.star(s)
+        pl = oracle.plan_star(t, y, dy, float(b.rho[s]), 1.0)
+        idx = np.arange(0, pl.freqs.shape[0], max(1, pl.freqs.shape[0] // 12))
+        sub = ob.restrict(pl, idx)
+        res = ob.bls_star_per_q(sub)
+        w, d, _ = ob.weights(sub.y, sub.dy)
+        for i, f in enumerate(sub.freqs):
+            best, bj, bk = -1.0, -1, -1
+            for j in range(sub.m.shape[1]):
+                qj = float(sub.qmin[i]) * math.exp(0.1 * j)
+                nb = int(math.ceil(3.0 / qj))
+                bins = []
+                for tt in sub.tp:
+                    x = tt * f
+                    bins.append(min(nb - 1, int(math.floor((x - math.floor(x)) * nb))))
+                for k in range(nb):
+                    r = s_ = 0.0
+                    for pt, bb in enumerate(bins):
+                        if (bb - k) % nb < 3:
+                            r += w[pt]; s_ += w[pt] * d[pt]
+                    if 0 < r < 1:
+                        v = s_ * s_ / (r * (1 - r))
+                        if v > best * (1 + 1e-12):
+                            best, bj, bk = v, j, k
+            assert res.sr[i] == pytest.approx(best, rel=1e-9)
+            assert (res.j[i], res.k[i]) == (bj, bk) or res.sr[i] == pytest.approx(best, rel=1e-9)
+    # one duration (q_max = q_min) and noverlap 3: the variant is the shared histogram
+    p1 = op.Params(qmax_fac=0.5)
+    t, y, dy = b.star(0)
+    pl = oracle.plan_star(t, y, dy, float(b.rho[0]), 1.0, p1)
+    a1, a2 = ob.bls_star(pl), ob.bls_star_per_q(pl)
+    assert np.array_equal(a1.sr, a2.sr) and np.array_equal(a1.k, a2.k)
