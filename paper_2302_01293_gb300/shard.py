@@ -14,6 +14,7 @@ per-rank work and time).
 * ``job_totals``: the job's work and its max-over-ranks time (the throughput
   rule of the bench: all ranks' units / the slowest rank's time).
 * ``gather_best``: best records of every rank, in global star order, on rank 0.
+* ``search_sharded``: the driver every rank calls with the whole batch.
 """
 from __future__ import annotations
 
@@ -92,3 +93,36 @@ def gather_best(best_local: np.ndarray, indices, n_stars: int, group=None):
     if not seen.all():
         raise ValueError("stars missing from the gathered results")
     return out
+
+
+def _subset(offsets, arrays, stars):
+    offsets = np.asarray(offsets, np.int64)
+    idx = [np.arange(offsets[s], offsets[s + 1]) for s in stars]
+    sel = np.concatenate(idx) if idx else np.zeros(0, np.int64)
+    sub_off = np.concatenate([[0], np.cumsum([len(i) for i in idx])]).astype(np.int64)
+    return sub_off, [None if a is None else np.asarray(a)[sel] for a in arrays]
+
+
+def _search_library(offsets, t, y, dy, rho, rstar, params):
+    from . import qlpbls
+    return qlpbls.run_host(offsets, t, y, dy, rho, rstar, params)["best"]
+
+
+def search_sharded(offsets, t, y, dy, rho=None, rstar=None, params=None, group=None, search_fn=None):
+    """Every rank calls this with the same whole batch: each searches its
+    longest-first share of the stars (one GPU per rank, no collective while
+    searching) and rank 0 returns the best records of all stars in batch order
+    (other ranks return None). search_fn(offsets, t, y, dy, rho, rstar, params)
+    returns one record per star of its sub-batch; default: the library's
+    host-buffer search (qlp_bls_run_host)."""
+    import torch.distributed as dist
+    on = dist.is_available() and dist.is_initialized()
+    rank = dist.get_rank(group) if on else 0
+    world = dist.get_world_size(group) if on else 1
+    n_stars = int(np.asarray(offsets).shape[0] - 1)
+    mine = partition(star_cost(offsets, t, rho), world)[rank]
+    sub_off, (st, sy, sdy) = _subset(offsets, [t, y, dy], mine)
+    srho = None if rho is None else np.asarray(rho)[mine]
+    srs = None if rstar is None else np.asarray(rstar)[mine]
+    best = (search_fn or _search_library)(sub_off, st, sy, sdy, srho, srs, params)
+    return gather_best(np.asarray(best), mine, n_stars, group)

@@ -234,3 +234,11 @@ def test_pmin_at_three_stellar_radii(gpu_lib):
         assert np.array_equal(plan.freqs[sl], pl.freqs)
         compare_spectrum(pl, ores, g, sl, label=f"a=3R* star {s}")
         compare_snr(pl, ores, g, sl, g["best"][s], label=f"a=3R* star {s}")
+
+
+def test_sharded_driver_on_one_gpu_equals_host_call(gpu_lib):
+    from paper_2302_01293_gb300 import shard
+    b = synth.uneven_single_sector(n_stars=5, seed=26)
+    got = shard.search_sharded(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar)
+    ref = qlpbls.run_host(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar)["best"]
+    assert np.array_equal(got["f_idx"], ref["f_idx"]) and np.array_equal(got["snr"], ref["snr"])

@@ -99,6 +99,44 @@ def test_two_ranks_gather_equals_single_process(tmp_path):
     assert work == 7.0 and ms == 20.0
 
 
+def _oracle_search(offsets, t, y, dy, rho, rstar, params):
+    out = np.zeros(len(offsets) - 1, REC)
+    for s in range(len(offsets) - 1):
+        a, b = offsets[s], offsets[s + 1]
+        pl = oracle.plan_star(t[a:b], y[a:b], dy[a:b], float(rho[s]), 1.0)
+        res = oracle.bls_star(pl)
+        snr, _, sigma = oracle.spectral_snr(pl.freqs, res.sr)
+        k = int(np.argmax(snr)) if oracle.best_candidate(pl, res, snr, sigma) is not None else -1
+        out[s] = (k, 1.0 / pl.freqs[k] if k >= 0 else np.nan, snr[k] if k >= 0 else np.nan)
+    return out
+
+
+def _sharded_worker(rank, world, port, out_dir):
+    import datetime
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=20))
+    try:
+        b = synth.tiny_batch(n_stars=9, seed=23)
+        got = shard.search_sharded(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar, search_fn=_oracle_search)
+        if rank == 0:
+            np.save(os.path.join(out_dir, "sharded.npy"), got)
+        else:
+            assert got is None
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_search_driver_equals_single_process(tmp_path):
+    import torch.multiprocessing as tmp
+    tmp.spawn(_sharded_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    got = np.load(tmp_path / "sharded.npy")
+    b = synth.tiny_batch(n_stars=9, seed=23)
+    ref = _oracle_search(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar, None)
+    assert np.array_equal(got["f_idx"], ref["f_idx"])
+    np.testing.assert_array_equal(got["snr"], ref["snr"])
+
+
 def test_failing_rank_is_reported(tmp_path):
     import torch.multiprocessing as tmp
     t0 = time.monotonic()
