@@ -317,7 +317,7 @@ int qlp_bls_top_peaks(const qlp_bls_plan_t* plan, void* stream, const float* snr
  * (at least two transits, S/N_pink > 9, S/N > 9).
  *  best  device qlp_bls_best[n_stars] from qlp_bls_snr / qlp_bls_snr_trend of this plan.
  *  out   device qlp_bls_cand_stats[n_stars].
- * The first call allocates an int32 scratch array of the plan's point count
+ * The first call allocates a scratch array of 32 bytes per point of the plan
  * (kept by the plan). Runs on `stream`; results are valid after it.
  */
 #define QLP_STATS_OK             0

@@ -102,7 +102,7 @@ struct qlp_bls_plan {
   int32_t* d_ctl = nullptr;       // [0] per-point queue head, [1] cell queue head, [2] error flags
   // search + S/N captured as one CUDA graph (qlp_bls_graph_capture)
   // slot parts-1: parts = 1 search, 2 S/N, 3 both
-  int32_t* d_widx = nullptr;      // candidate statistics scratch (allocated on first use)
+  double4* d_wrec = nullptr;      // candidate statistics scratch (allocated on first use)
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph[3] = {};
   cudaGraphExec_t gexec[3] = {};
@@ -129,7 +129,7 @@ static void free_plan(qlp_bls_plan_t* pl) {
   cudaFree(pl->d_loc);
   cudaFree(pl->d_base);
   cudaFree(pl->d_gidx);
-  cudaFree(pl->d_widx);
+  cudaFree(pl->d_wrec);
   cudaFree(pl->d_ctl);
   delete pl;
 }
@@ -769,8 +769,8 @@ int qlp_bls_candidate_stats(qlp_bls_plan_t* pl, void* stream, const qlp_bls_best
   if (!pl) return QLP_ERR_ARG;
   if (pl->n_stars > 0 && (!best || !out)) return QLP_ERR_ARG;
   if (pl->n_stars == 0) return QLP_OK;
-  if (!pl->d_widx) {
-    const int rc = dev_alloc(&pl->d_widx, (size_t)std::max<int64_t>(pl->n_points, 1));
+  if (!pl->d_wrec) {
+    const int rc = dev_alloc(&pl->d_wrec, (size_t)std::max<int64_t>(pl->n_points, 1));
     if (rc) return rc;
   }
   StatsArgs a{};
@@ -781,7 +781,7 @@ int qlp_bls_candidate_stats(qlp_bls_plan_t* pl, void* stream, const qlp_bls_best
   a.dy = pl->d_dy;
   a.best = best;
   a.out = out;
-  a.widx = pl->d_widx;
+  a.wrec = pl->d_wrec;
   const int e = launch_stats(a, stream);
   return e ? cuda_fail((cudaError_t)e, "stats launch") : QLP_OK;
 }

@@ -183,7 +183,7 @@ struct StatsArgs {
   const double* dy;
   const qlp_bls_best* best;
   qlp_bls_cand_stats* out;
-  int32_t* widx;  // scratch: window point indices, CSR by pt_off
+  double4* wrec;  // scratch: fit-window points (t', y, 1/dy, transit index), CSR by pt_off
 };
 int launch_peaks(const StarDev* stars, int n_stars, const double2* fq, const float* snr, int n_peaks, double sep,
                  int32_t* out, void* stream);

@@ -77,21 +77,23 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block sum of n values per thread (n <= kSums); thread 0 gets the totals.
+// Block sum of n values per thread (n <= kSums); every thread gets the totals
+// (warp sums, then one thread per value adds the warps' partials in order).
 __device__ __forceinline__ void block_sums(double* v, int n, double (*red)[kSums]) {
+  __shared__ double tot[kSums];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = 0; i < n; ++i) {
     const double w = warp_sum(v[i]);
     if (lane == 0) red[warp][i] = w;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < n; ++i) {
-      double t = 0.0;
-      for (int w = 0; w < kWarps; ++w) t += red[w][i];
-      v[i] = t;
-    }
+  if (threadIdx.x < n) {
+    double t = 0.0;
+    for (int w = 0; w < kWarps; ++w) t += red[w][threadIdx.x];
+    tot[threadIdx.x] = t;
   }
+  __syncthreads();
+  for (int i = 0; i < n; ++i) v[i] = tot[i];
   __syncthreads();
 }
 
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const StatsArgs a) {
   const double* tp = a.tp + st.pt_off;
   const double* yv = a.y + st.pt_off;
   const double* dyv = a.dy + st.pt_off;
-  int32_t* widx = a.widx + st.pt_off;
+  double4* wrec = a.wrec + st.pt_off;
   const double period = bb.period;
   const double t0p = __dsub_rn(bb.t0, st.t_ref);
   const double q0 = bb.q;
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const StatsArgs a) {
       const double u = __dsub_rn(tp[i], t0p);
       const double nn = floor(__dadd_rn(__ddiv_rn(u, period), 0.5));
       const double dt = fabs(__dsub_rn(u, __dmul_rn(period, nn)));
-      if (dt <= lim) widx[o++] = i;
+      if (dt <= lim) wrec[o++] = make_double4(tp[i], yv[i], __ddiv_rn(1.0, dyv[i]), nn);
     }
   }
   if (nwin < 6) {
@@ -223,30 +225,58 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const StatsArgs a) {
   // 2. Levenberg-Marquardt (thread 0 keeps the state; every pass is block-wide)
   const int wseg = (nwin + kThreads - 1) / kThreads;
   const int w0 = min(nwin, tid * wseg), w1 = min(nwin, w0 + wseg);
+  // The model at s_x and its derivatives. Only points on a ramp have nonzero
+  // derivatives in T0, q and q_in; flat-bottom points add to the (delta, z)
+  // block and outside points to z alone, so those skip the zero products.
   auto evaluate = [&](double* sums) {  // at s_x: chi^2, J^T r, J^T J
     double x[5];
     for (int i = 0; i < 5; ++i) x[i] = s_x[i];
+    const double d = __dmul_rn(x[2], period);
+    const double t_in = __dmul_rn(x[3], d);
+    const double half = __dmul_rn(0.5, d);
+    const double edge = __dsub_rn(half, t_in);
+    const double hp = __dmul_rn(0.5, period);
     for (int i = 0; i < kSums; ++i) sums[i] = 0.0;
     for (int wi = w0; wi < w1; ++wi) {
-      const int i = widx[wi];
-      const Model md = model_at(tp[i], x, period);
-      const double inv = __ddiv_rn(1.0, dyv[i]);
-      const double r = __dmul_rn(__dsub_rn(yv[i], md.m), inv);
-      double j[5];
-      const double d = __dmul_rn(x[2], period);
-      const double t_in = __dmul_rn(x[3], d);
-      const double sg = md.dt > 0.0 ? 1.0 : (md.dt < 0.0 ? -1.0 : 0.0);
-      j[0] = md.ramp ? -x[1] * sg / t_in : 0.0;
-      j[1] = -md.s;
-      j[2] = md.ramp ? -x[1] * md.a / (x[3] * x[2] * x[2] * period) : 0.0;
-      j[3] = md.ramp ? x[1] * md.s / x[3] : 0.0;
-      j[4] = 1.0;
-      for (int k = 0; k < 5; ++k) j[k] *= inv;
-      sums[0] += r * r;
-      for (int k = 0; k < 5; ++k) sums[1 + k] += j[k] * r;
-      int p = 6;
-      for (int k = 0; k < 5; ++k)
-        for (int l = k; l < 5; ++l) sums[p++] += j[k] * j[l];
+      const double4 pt = wrec[wi];  // t', y, 1/dy, transit index of the starting epoch
+      const double u = __dsub_rn(pt.x, x[0]);
+      double dt = __dsub_rn(u, __dmul_rn(period, pt.w));
+      if (fabs(dt) > hp) {  // the epoch moved by half a period: the nearest transit changed
+        const double nn = floor(__dadd_rn(__ddiv_rn(u, period), 0.5));
+        dt = __dsub_rn(u, __dmul_rn(period, nn));
+      }
+      const double aa = fabs(dt);
+      const double inv = pt.z;
+      if (aa <= edge) {  // flat bottom: s = 1, dm/ddelta = -1, dm/dz = 1
+        const double r = __dmul_rn(__dsub_rn(pt.y, __dsub_rn(x[4], x[1])), inv);
+        const double i2 = inv * inv;
+        sums[0] += r * r;
+        sums[2] -= inv * r;
+        sums[5] += inv * r;
+        sums[6 + 5] += i2;   // A11
+        sums[6 + 8] -= i2;   // A14
+        sums[6 + 14] += i2;  // A44
+      } else if (aa < half) {  // ramp
+        const double sv = __ddiv_rn(__dsub_rn(half, aa), t_in);
+        const double r = __dmul_rn(__dsub_rn(pt.y, __dsub_rn(x[4], __dmul_rn(x[1], sv))), inv);
+        const double sg = dt > 0.0 ? 1.0 : (dt < 0.0 ? -1.0 : 0.0);
+        double j[5];
+        j[0] = -x[1] * sg / t_in * inv;
+        j[1] = -sv * inv;
+        j[2] = -x[1] * aa / (x[3] * x[2] * x[2] * period) * inv;
+        j[3] = x[1] * sv / x[3] * inv;
+        j[4] = inv;
+        sums[0] += r * r;
+        for (int k = 0; k < 5; ++k) sums[1 + k] += j[k] * r;
+        int p = 6;
+        for (int k = 0; k < 5; ++k)
+          for (int l = k; l < 5; ++l) sums[p++] += j[k] * j[l];
+      } else {  // outside the transit: s = 0, dm/dz = 1
+        const double r = __dmul_rn(__dsub_rn(pt.y, x[4]), inv);
+        sums[0] += r * r;
+        sums[5] += inv * r;
+        sums[6 + 14] += inv * inv;
+      }
     }
     block_sums(sums, kSums, red);
   };
