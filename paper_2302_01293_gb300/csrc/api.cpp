@@ -102,7 +102,7 @@ struct qlp_bls_plan {
   int32_t* d_ctl = nullptr;       // [0] per-point queue head, [1] cell queue head, [2] error flags
   // search + S/N captured as one CUDA graph (qlp_bls_graph_capture)
   // slot parts-1: parts = 1 search, 2 S/N, 3 both
-  double4* d_wrec = nullptr;      // candidate statistics scratch (allocated on first use)
+  WinRec* d_wrec = nullptr;      // candidate statistics scratch (allocated on first use)
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph[3] = {};
   cudaGraphExec_t gexec[3] = {};

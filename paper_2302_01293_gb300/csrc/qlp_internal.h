@@ -175,6 +175,11 @@ int launch_prep_cells(const PrepCellsArgs& a, void* stream);
 int launch_cells(const CellArgs& a, int sum_mode, int warps, int blocks, size_t smem, void* stream);
 // bytes of shared memory before the histograms of the cell kernel for a star with
 // ncs cells (incl. sentinel) and nw warps
+// One point of a candidate's fit window: t', y, 1/dy and its transit index.
+struct __align__(16) WinRec {
+  double t, y, inv, n;
+};
+
 struct StatsArgs {
   const StarDev* stars;
   int32_t n_stars;
@@ -183,7 +188,7 @@ struct StatsArgs {
   const double* dy;
   const qlp_bls_best* best;
   qlp_bls_cand_stats* out;
-  double4* wrec;  // scratch: fit-window points (t', y, 1/dy, transit index), CSR by pt_off
+  WinRec* wrec;  // scratch: fit-window points, CSR by pt_off
 };
 int launch_peaks(const StarDev* stars, int n_stars, const double2* fq, const float* snr, int n_peaks, double sep,
                  int32_t* out, void* stream);

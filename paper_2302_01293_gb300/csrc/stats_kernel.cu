@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const StatsArgs a) {
   const double* tp = a.tp + st.pt_off;
   const double* yv = a.y + st.pt_off;
   const double* dyv = a.dy + st.pt_off;
-  double4* wrec = a.wrec + st.pt_off;
+  WinRec* wrec = a.wrec + st.pt_off;
   const double period = bb.period;
   const double t0p = __dsub_rn(bb.t0, st.t_ref);
   const double q0 = bb.q;
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const StatsArgs a) {
       const double u = __dsub_rn(tp[i], t0p);
       const double nn = floor(__dadd_rn(__ddiv_rn(u, period), 0.5));
       const double dt = fabs(__dsub_rn(u, __dmul_rn(period, nn)));
-      if (dt <= lim) wrec[o++] = make_double4(tp[i], yv[i], __ddiv_rn(1.0, dyv[i]), nn);
+      if (dt <= lim) wrec[o++] = WinRec{tp[i], yv[i], __ddiv_rn(1.0, dyv[i]), nn};
     }
   }
   if (nwin < 6) {
@@ -238,15 +238,15 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const StatsArgs a) {
     const double hp = __dmul_rn(0.5, period);
     for (int i = 0; i < kSums; ++i) sums[i] = 0.0;
     for (int wi = w0; wi < w1; ++wi) {
-      const double4 pt = wrec[wi];  // t', y, 1/dy, transit index of the starting epoch
-      const double u = __dsub_rn(pt.x, x[0]);
-      double dt = __dsub_rn(u, __dmul_rn(period, pt.w));
+      const WinRec pt = wrec[wi];  // t', y, 1/dy, transit index of the starting epoch
+      const double u = __dsub_rn(pt.t, x[0]);
+      double dt = __dsub_rn(u, __dmul_rn(period, pt.n));
       if (fabs(dt) > hp) {  // the epoch moved by half a period: the nearest transit changed
         const double nn = floor(__dadd_rn(__ddiv_rn(u, period), 0.5));
         dt = __dsub_rn(u, __dmul_rn(period, nn));
       }
       const double aa = fabs(dt);
-      const double inv = pt.z;
+      const double inv = pt.inv;
       if (aa <= edge) {  // flat bottom: s = 1, dm/ddelta = -1, dm/dz = 1
         const double r = __dmul_rn(__dsub_rn(pt.y, __dsub_rn(x[4], x[1])), inv);
         const double i2 = inv * inv;
