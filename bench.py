@@ -135,6 +135,12 @@ def _peaks():
 FP32_OPS_PER_EVAL = 16
 CELL_OPS_PER_EDGE = {0: 20, 1: 30}
 CELL_SMEM_BYTES_PER_EDGE = {0: 44, 1: 60}
+#  exact cell path (integer prefix sums), per bin edge: 14 lane operations
+#    (96-bit edge step 3, cell and position 3, comparison and band test 3, two
+#    64-bit accumulations of base + local 5) and 28 shared-memory bytes gathered
+#    (dt 4, local prefix 8, group base 16); no histogram traffic.
+EXACT_OPS_PER_EDGE = 14
+EXACT_SMEM_BYTES_PER_EDGE = 28
 FP32_LANES_PER_SM = 128
 SMEM_BYTES_PER_CLK_PER_SM = 128
 N_SMS = 152
@@ -336,6 +342,7 @@ def main():
     t_tune = time.perf_counter() - t0
     plan = qlpbls.Plan(batch.offsets, batch.t, batch.y, batch.dy, batch.rho, batch.rstar, params)
     out = plan.alloc_outputs()
+    plan.kernel_timing(True)  # events around the main search kernel, inside the graph
     # the step as two CUDA graphs: the search (prep + persistent kernels), the S/N
     plan.graph_capture(out, parts=1)
     plan.graph_capture(out, parts=2)
@@ -366,6 +373,15 @@ def main():
     clk = clocks.stop()
     ms = e_start.elapsed_time(e_end) / args.steps
     ms_search = float(np.mean([a.elapsed_time(b) for a, b in k_ev]))
+    # the main search kernel alone: the plan's events inside the search graph, one
+    # replay at a time (after the timed region)
+    k_times = []
+    for _ in range(args.steps):
+        plan.graph_launch(1)
+        torch.cuda.synchronize()
+        k_times.append(plan.kernel_time())
+    ms_kernel = float(np.mean([t for t, _ in k_times]))
+    kernel_id = k_times[0][1]
     flags = plan.device_status()
     if flags:
         raise RuntimeError(f"device flags {flags}")
@@ -411,7 +427,14 @@ def main():
     peak_ops = N_SMS * FP32_LANES_PER_SM * sm_clock / 1e12  # T lane ops / s
     peak_smem = N_SMS * SMEM_BYTES_PER_CLK_PER_SM * sm_clock / 1e9  # GB/s
     cells_dominant = plan.work_cells >= plan.work_points
-    if cells_dominant:
+    if kernel_id == 2:
+        ops = plan.exact_edges * EXACT_OPS_PER_EDGE
+        achieved = ops / (ms_kernel * 1e-3) / 1e12
+        smem_gbs = plan.exact_edges * EXACT_SMEM_BYTES_PER_EDGE / (ms_kernel * 1e-3) / 1e9
+        kernel = "cells_fixed_kernel (exact cell path; CUDA events around the launch inside the graph)"
+        unit_note = (f"{plan.exact_edges:.4e} bin edges x {EXACT_OPS_PER_EDGE} lane ops "
+                     f"({EXACT_SMEM_BYTES_PER_EDGE} shared bytes) per launch")
+    elif cells_dominant:
         ops = plan.edges * CELL_OPS_PER_EDGE[params.sum_mode]
         achieved = ops / (ms_search * 1e-3) / 1e12
         smem_gbs = plan.edges * CELL_SMEM_BYTES_PER_EDGE[params.sum_mode] / (ms_search * 1e-3) / 1e9
@@ -425,7 +448,7 @@ def main():
     # DRAM traffic of one cells_kernel launch: ncu capture of the same kernel on
     # 1,024 stars of this workload (423.0 MB), scaled by points to the default batch
     traffic = None
-    if cells_dominant and args.stars == 4096 and args.seed == 2 and params.sum_mode == 1:
+    if cells_dominant and kernel_id == 1 and args.stars == 4096 and args.seed == 2 and params.sum_mode == 1:
         traffic = 423.0e6 * plan.n_points / 10638874
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "TFLOP/s",
                 "frac": achieved / peak_ops, "traffic": traffic, "kernel": kernel,
@@ -445,7 +468,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32 sums, FP64 prefix sums, FP64 bin decisions", "data": "synthetic",
+                "dtype": ("int64 fixed-point sums, f32 box scores, FP64 bin decisions" if kernel_id == 2
+                          else "f32 sums, FP64 prefix sums, FP64 bin decisions"), "data": "synthetic",
                 "config": {"workload": "uneven_single_sector_200s", "stars_per_gpu": args.stars,
                            "points": plan.n_points, "trial_freqs": plan.n_freq_total,
                            "point_freq_per_gpu": plan.work, "bin_edges": plan.edges,
@@ -456,10 +480,11 @@ def main():
                                          "sample_stars": None if args.no_tune else args.tune_sample,
                                          "seconds": t_tune},
                            "launch": "CUDA graphs (search, S/N) per step",
-                           "sum_mode": "COMP" if params.sum_mode else "PLAIN",
+                           "sum_mode": ["PLAIN", "COMP", "FIXED"][params.sum_mode],
                            "l2": "inputs larger than L2 (light curves "
                            f"{plan.n_points * 24 / 1e6:.0f} MB FP64)", "parallelism": f"replicas x{world}"},
-                "ms_search": ms_search,
+                "ms_search": ms_search, "ms_kernel": ms_kernel,
+                "exact_path_stars": plan.n_exact_stars,
                 "gpu_launches": args.steps * (1 + 2 * (plan.work_points > 0) + 2 * (plan.work_cells > 0)),
                 "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "candidate_stats": cand_stats,

@@ -67,6 +67,13 @@ extern "C" {
 #define QLP_SUM_PLAIN   0  /* FP32 histogram sums */
 #define QLP_SUM_COMP    1  /* FP32 sums with the rounding error of every shared-memory add
                               captured exactly (TwoSum) and added back (compensated) */
+#define QLP_SUM_FIXED   2  /* exact sums (default): per star the weights w and w (y - ybar) are
+                              rounded once to integers, round(w 2^kw) and round(w d 2^ky) with
+                              per-star scales that keep 32 consecutive points below 2^30, and
+                              every bin and box sum is an exact 64-bit integer sum of those; the
+                              box sums reach FP32 as double-float (hi, lo) differences. Used on
+                              the cell path for stars whose whole table fits in shared memory;
+                              the per-point path and time-windowed stars use QLP_SUM_COMP. */
 
 #define QLP_MAD_RAW     0  /* sigma_SR = 1.4826 median|SR - median(SR)| (the paper's wording) */
 #define QLP_MAD_RESID   1  /* same on the detrended residual SR - trend */
@@ -82,7 +89,7 @@ typedef struct qlp_bls_params {
   double rho_default;       /* 1.41  (Sec. 2.1) solar density (g/cm^3) when rho is missing */
   int32_t nbins_cap;        /* largest phase-bin count a star may need (default 8192) */
   int32_t phase_mode;       /* QLP_PHASE_* (default QLP_PHASE_DF) */
-  int32_t sum_mode;         /* QLP_SUM_*   (default QLP_SUM_COMP) */
+  int32_t sum_mode;         /* QLP_SUM_*   (default QLP_SUM_FIXED) */
   int32_t mad_mode;         /* QLP_MAD_*   (default QLP_MAD_RAW) */
   int32_t chunk_freqs;      /* frequencies per work item, 0 = chosen by the planner */
   int32_t warps_per_block;  /* 0 = chosen by the planner; else 4, 8, 16 or 32 (32: cell path only,
@@ -181,6 +188,31 @@ int qlp_bls_plan_info(const qlp_bls_plan_t* plan, int64_t* n_freq_total, int64_t
  */
 int qlp_bls_plan_stats(const qlp_bls_plan_t* plan, double* work_points, double* work_cells,
                        double* edges, int32_t* n_cell_stars, int32_t* n_windowed);
+
+/*
+ * qlp_bls_plan_exact_stats -- the part of the cell path that runs with exact
+ * integer sums (QLP_SUM_FIXED, Sec. 2.1's binned BLS with the bins' weights summed
+ * exactly). Any output may be NULL.
+ *  n_exact_stars  stars searched by the exact cell kernel (counted in n_cell_stars too).
+ *  exact_edges    bin edges those stars evaluate (counted in edges too).
+ * Returns QLP_ERR_ARG for a NULL plan.
+ */
+int qlp_bls_plan_exact_stats(const qlp_bls_plan_t* plan, int32_t* n_exact_stars, double* exact_edges);
+
+/*
+ * qlp_bls_kernel_timing -- measurement aid (no counterpart in the paper): with
+ * enable != 0 the plan creates two CUDA events that every later qlp_bls_search on
+ * it records just before and after its main kernel (the exact cell kernel when the
+ * plan has exact-path stars, else the compensated cell kernel, else the per-point
+ * kernel), also inside a graph captured afterwards (as event nodes); enable = 0
+ * destroys them. Returns QLP_ERR_CUDA if an event cannot be created.
+ * qlp_bls_kernel_time -- waits for the end event and returns, in *ms, the time
+ * between the two events of the most recent search (or graph replay), and in
+ * *kernel (may be NULL) which kernel they bracket: 0 per-point, 1 compensated cell,
+ * 2 exact cell. QLP_ERR_ARG when timing is not enabled.
+ */
+int qlp_bls_kernel_timing(qlp_bls_plan_t* plan, int32_t enable);
+int qlp_bls_kernel_time(qlp_bls_plan_t* plan, float* ms, int32_t* kernel);
 
 /*
  * qlp_bls_search -- Sec. 2.1 / Eq. 1's SR: binned BLS residue at every trial frequency.

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqlpbls.so")
 ROOT = os.path.dirname(HERE)
 
-CU_SOURCES = ["bls_kernels.cu", "cells_kernels.cu", "snr_kernel.cu", "static_search.cu",
+CU_SOURCES = ["bls_kernels.cu", "cells_kernels.cu", "fixed_kernels.cu", "snr_kernel.cu", "static_search.cu",
               "cnn_kernels.cu", "stats_kernel.cu"]
 CPP_SOURCES = ["planner.cpp", "api.cpp", "cnn_api.cpp", "learned_api.cpp", "autotune.cpp", "multi_api.cpp"]
 HEADERS = ["qlp_internal.h", "planner.h", "bls_device.cuh", "tc_common.cuh"]

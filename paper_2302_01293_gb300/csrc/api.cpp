@@ -84,6 +84,12 @@ struct qlp_bls_plan {
   int32_t c_items = 0;
   int32_t n_cell_stars = 0;
   int32_t n_windowed = 0;
+  // exact cell path launch shape
+  int f_blocks = 0;
+  size_t f_smem = 0;
+  int32_t f_items = 0;
+  int32_t n_fixed_stars = 0;
+  double edges_fixed = 0.0;
   // device
   StarDev* d_stars = nullptr;
   double2* d_fq = nullptr;
@@ -99,11 +105,16 @@ struct qlp_bls_plan {
   float2* d_loc = nullptr;
   float4* d_base = nullptr;
   int32_t* d_gidx = nullptr;
-  int32_t* d_ctl = nullptr;       // [0] per-point queue head, [1] cell queue head, [2] error flags
+  int32_t* d_fixed_stars = nullptr;
+  FixedStar* d_fx = nullptr;
+  FreqRec* d_frec = nullptr;
+  int32_t* d_ctl = nullptr;       // [0] per-point queue head, [1] cell queue head, [2] error flags,
+                                  // [3] exact cell queue head
   // search + S/N captured as one CUDA graph (qlp_bls_graph_capture)
   // slot parts-1: parts = 1 search, 2 S/N, 3 both
   WinRec* d_wrec = nullptr;      // candidate statistics scratch (allocated on first use)
   cudaStream_t cap_stream = nullptr;
+  cudaEvent_t kev[2] = {};        // qlp_bls_kernel_timing: around the main search kernel
   cudaGraph_t graph[3] = {};
   cudaGraphExec_t gexec[3] = {};
 };
@@ -115,6 +126,8 @@ static void free_plan(qlp_bls_plan_t* pl) {
     if (pl->graph[i]) cudaGraphDestroy(pl->graph[i]);
   }
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+  if (pl->kev[0]) cudaEventDestroy(pl->kev[0]);
+  if (pl->kev[1]) cudaEventDestroy(pl->kev[1]);
   cudaFree(pl->d_stars);
   cudaFree(pl->d_fq);
   cudaFree(pl->d_items);
@@ -129,6 +142,9 @@ static void free_plan(qlp_bls_plan_t* pl) {
   cudaFree(pl->d_loc);
   cudaFree(pl->d_base);
   cudaFree(pl->d_gidx);
+  cudaFree(pl->d_fixed_stars);
+  cudaFree(pl->d_fx);
+  cudaFree(pl->d_frec);
   cudaFree(pl->d_wrec);
   cudaFree(pl->d_ctl);
   delete pl;
@@ -149,7 +165,7 @@ void qlp_bls_params_default(qlp_bls_params* p) {
   p->rho_default = 1.41;
   p->nbins_cap = 8192;
   p->phase_mode = QLP_PHASE_DF;
-  p->sum_mode = QLP_SUM_COMP;
+  p->sum_mode = QLP_SUM_FIXED;
   p->mad_mode = QLP_MAD_RAW;
   p->chunk_freqs = 0;
   p->warps_per_block = 0;
@@ -183,7 +199,7 @@ static int check_params(const qlp_bls_params& p) {
       !(p.qmax_fac >= p.qmin_fac) || !(p.pmin_aR > 0) || !(p.gap_days > 0) || !(p.rho_default > 0) ||
       p.nbins_cap < 2)
     return QLP_ERR_ARG;
-  if (p.phase_mode < 0 || p.phase_mode > 2 || p.sum_mode < 0 || p.sum_mode > 1 || p.mad_mode < 0 ||
+  if (p.phase_mode < 0 || p.phase_mode > 2 || p.sum_mode < 0 || p.sum_mode > 2 || p.mad_mode < 0 ||
       p.mad_mode > 1 || p.tile_points < 0 || p.chunk_freqs < 0 || p.method < 0 || p.method > 2 ||
       p.grid_mode < 0 || p.grid_mode > 1 || p.cell_window < 0 || p.bin_mode < 0 || p.bin_mode > 1 ||
       (p.bin_mode == QLP_BIN_PER_Q && (p.noverlap != std::floor(p.noverlap) || p.phase_mode == QLP_PHASE_FP32 ||
@@ -255,7 +271,9 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   pl->nq = n_q_of(p);
   for (int j = 0; j < pl->nq; ++j) pl->E[j] = std::exp(j * p.dlogq);
 
-  const int NA = (p.sum_mode == QLP_SUM_COMP) ? 4 : 2;
+  // the per-point and windowed cell kernels run compensated sums under QLP_SUM_FIXED
+  const int sum_old = p.sum_mode == QLP_SUM_PLAIN ? QLP_SUM_PLAIN : QLP_SUM_COMP;
+  const int NA = (sum_old == QLP_SUM_COMP) ? 4 : 2;
   const int smem_max = bls_max_smem_per_block();
   if (smem_max <= 0) { delete pl; return cuda_fail(cudaGetLastError(), "device query"); }
   const int budget = smem_max - 1024;
@@ -283,7 +301,8 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
     if (h.status != 0 || !h.cells_ok || p.method == 1 || p.phase_mode == QLP_PHASE_FP32) continue;
     CellWin& W = cwin[(size_t)s];
     const double ovl = std::ceil(h.bin_dmax / h.cell_h) + 4.0;
-    if (!(ovl < 1.0e6)) continue;
+    // the edge step D/h is a 2^-56 fixed-point number below 2^8
+    if (!(ovl < 1.0e6) || !(h.bin_dmax / h.cell_h < 255.0)) continue;
     W.ovl = (int32_t)ovl;
     const bool whole = p.cell_window > 0 ? p.cell_window >= h.n_cells
                                           : cell_smem(h.n_cells + 1, h.nbins_max) <= (size_t)budget;
@@ -300,8 +319,20 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
       W.cap = (int32_t)std::min<int64_t>(h.n_cells + 1, c + W.ovl + 33);
       W.n_win = (int32_t)((h.n_cells + c - 1) / c);
     }
-    if (cell_smem(W.cap, h.nbins_max) > (size_t)budget) continue;
+    const bool old_fits = cell_smem(W.cap, h.nbins_max) <= (size_t)budget;
     const double pp_work = (double)h.freqs.size() * (double)round32((int64_t)h.tp.size());
+    // exact path: the whole table and the warps' rings in shared memory, at least 32 bins,
+    // at most 2^14 cycles and 2^21 points (the integer prefix sums stay below 2^62)
+    const bool fixed_ok = p.sum_mode == QLP_SUM_FIXED && p.bin_mode == QLP_BIN_SHARED &&
+                          (p.cell_window == 0 || p.cell_window >= h.n_cells) &&
+                          (size_t)fixed_smem_bytes((int)h.n_cells + 1) <= (size_t)budget && h.nbins_min >= 32 &&
+                          h.baseline * h.freqs.back() <= 16384.0 && h.tp.size() <= ((size_t)1 << 21);
+    if (fixed_ok && (p.method == 2 || h.cells_work < 2.0 * pp_work)) {
+      method[(size_t)s] = kMethodFixed;
+      W = CellWin{1, (int32_t)h.n_cells, (int32_t)ovl, (int32_t)h.n_cells + 1};
+      continue;
+    }
+    if (!old_fits) continue;
     if (p.method == 2 || p.bin_mode == QLP_BIN_PER_Q || h.cells_work < pp_work) method[(size_t)s] = kMethodCells;
   }
   if (p.bin_mode == QLP_BIN_PER_Q)  // per-duration histograms exist on the cell path only
@@ -315,7 +346,8 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   int64_t npt = 0, npad = 0, nf = 0, ncell = 0, nbase = 0, ncpre = 0;
   int32_t max_npts = 0, nb_pp = 0, nb_c = 0;
   int64_t cells_cap = 0;
-  std::vector<int32_t> cell_stars;
+  std::vector<int32_t> cell_stars, fixed_stars;
+  int64_t fixed_ncs = 0;
   for (int32_t s = 0; s < n_stars; ++s) {
     const StarPlanHost& h = sp[(size_t)s];
     StarDev& d = stars[(size_t)s];
@@ -338,7 +370,7 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
     nf += d.n_f;
     pl->f_off[(size_t)s + 1] = nf;
     if (ok) pl->work += (double)d.n_pts * (double)d.n_f;
-    if (ok && d.method == kMethodCells) {
+    if (ok && (d.method == kMethodCells || d.method == kMethodFixed)) {
       pl->work_cells += (double)d.n_pts * (double)d.n_f;
       pl->edges += h.cells_work;
       d.h = h.cell_h;
@@ -354,9 +386,15 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
       ncell += h.n_cells + 1;
       nbase += (h.n_cells + 1 + 31) / 32;
       ncpre += d.n_pts + 1;
-      cells_cap = std::max<int64_t>(cells_cap, h.n_cells + 1);
-      nb_c = std::max(nb_c, h.nbins_max);
-      cell_stars.push_back(s);
+      if (d.method == kMethodFixed) {
+        fixed_stars.push_back(s);
+        fixed_ncs = std::max<int64_t>(fixed_ncs, h.n_cells + 1);
+        pl->edges_fixed += h.cells_work;
+      } else {
+        cells_cap = std::max<int64_t>(cells_cap, h.n_cells + 1);
+        nb_c = std::max(nb_c, h.nbins_max);
+        cell_stars.push_back(s);
+      }
     } else if (ok) {
       pl->work_points += (double)d.n_pts * (double)d.n_f;
       npad += ((int64_t)d.n_pts + 31) & ~(int64_t)31;
@@ -366,7 +404,8 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
     if (ok) pl->nbins_max = std::max(pl->nbins_max, h.nbins_max);
   }
   pl->n_points = npt;
-  pl->n_cell_stars = (int32_t)cell_stars.size();
+  pl->n_cell_stars = (int32_t)(cell_stars.size() + fixed_stars.size());
+  pl->n_fixed_stars = (int32_t)fixed_stars.size();
   // staging buffers without zero fill, filled star by star in parallel
   const size_t npt_alloc = (size_t)std::max<int64_t>(npt, 1), nf_alloc = (size_t)std::max<int64_t>(nf, 1);
   std::unique_ptr<double[]> tp_all(new (std::nothrow) double[npt_alloc]);
@@ -407,7 +446,7 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   pl->tile_pts = tile;
   pl->tile_off = (uint32_t)hb;
   pl->smem = hb + (size_t)tile * 16;
-  int per_sm = bls_blocks_per_sm(p.phase_mode, p.sum_mode, warps, pl->smem);
+  int per_sm = bls_blocks_per_sm(p.phase_mode, sum_old, warps, pl->smem);
   if (per_sm < 1) { delete pl; return QLP_ERR_UNSUPPORTED; }
   pl->blocks = sms * per_sm;
 
@@ -418,9 +457,15 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   if (!cell_stars.empty()) {
     pl->c_warps = cw;
     pl->c_smem = (size_t)budget;
-    const int cper = cells_blocks_per_sm(p.sum_mode, cw, pl->c_smem);
+    const int cper = cells_blocks_per_sm(sum_old, cw, pl->c_smem);
     if (cper < 1) { delete pl; return QLP_ERR_UNSUPPORTED; }
     pl->c_blocks = sms * cper;
+  }
+  if (!fixed_stars.empty()) {
+    pl->f_smem = fixed_smem_bytes((int)fixed_ncs);
+    const int fper = fixed_blocks_per_sm(pl->f_smem);
+    if (fper < 1) { delete pl; return QLP_ERR_UNSUPPORTED; }
+    pl->f_blocks = sms * fper;
   }
 
   // work items: (star, chunk of frequencies), longest first, one queue per path
@@ -456,8 +501,8 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
         items.push_back(wi);
         const int mid = b + wi.f_count / 2;
         const double nbm = (double)h.nbins[(size_t)mid];
-        const double per_f = meth == kMethodCells ? h.baseline * h.freqs[(size_t)mid] * nbm + 3.0 * nbm
-                                                  : (double)d.n_pts + 3.0 * nbm;
+        const double per_f = meth != kMethodPoints ? h.baseline * h.freqs[(size_t)mid] * nbm + 3.0 * nbm
+                                                   : (double)d.n_pts + 3.0 * nbm;
         cost.push_back((double)wi.f_count * per_f);
       }
     }
@@ -471,6 +516,7 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   std::vector<WorkItem> sorted;
   pl->n_items = make_items(kMethodPoints, warps, pl->blocks, &sorted);
   pl->c_items = make_items(kMethodCells, cw, pl->c_blocks, &sorted);
+  pl->f_items = make_items(kMethodFixed, kFixedWarps, pl->f_blocks, &sorted);
 
   // device buffers
   cudaStream_t st = (cudaStream_t)stream;
@@ -484,7 +530,10 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
       (rc = dev_alloc(&pl->d_dt, (size_t)std::max<int64_t>(ncell, 1))) ||
       (rc = dev_alloc(&pl->d_loc, (size_t)std::max<int64_t>(ncell, 1))) ||
       (rc = dev_alloc(&pl->d_gidx, (size_t)std::max<int64_t>(ncell, 1))) ||
-      (rc = dev_alloc(&pl->d_base, (size_t)std::max<int64_t>(nbase, 1))) || (rc = dev_alloc(&pl->d_ctl, 4))) {
+      (rc = dev_alloc(&pl->d_base, (size_t)std::max<int64_t>(nbase, 1))) ||
+      (rc = dev_alloc(&pl->d_fixed_stars, std::max<size_t>(fixed_stars.size(), 1))) ||
+      (rc = dev_alloc(&pl->d_fx, (size_t)std::max(n_stars, 1))) ||
+      (rc = dev_alloc(&pl->d_frec, fixed_stars.empty() ? (size_t)1 : nf_alloc)) || (rc = dev_alloc(&pl->d_ctl, 4))) {
     free_plan(pl);
     return rc;
   }
@@ -493,6 +542,7 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   if (e == cudaSuccess && nf > 0) e = cudaMemcpyAsync(pl->d_fq, fq.get(), sizeof(double2) * (size_t)nf, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !sorted.empty()) e = cudaMemcpyAsync(pl->d_items, sorted.data(), sizeof(WorkItem) * sorted.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !cell_stars.empty()) e = cudaMemcpyAsync(pl->d_cell_stars, cell_stars.data(), sizeof(int32_t) * cell_stars.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !fixed_stars.empty()) e = cudaMemcpyAsync(pl->d_fixed_stars, fixed_stars.data(), sizeof(int32_t) * fixed_stars.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(pl->d_tp, tp_all.get(), sizeof(double) * (size_t)npt, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(pl->d_y, y_all.get(), sizeof(double) * (size_t)npt, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(pl->d_dy, dy_all.get(), sizeof(double) * (size_t)npt, cudaMemcpyHostToDevice, st);
@@ -529,6 +579,50 @@ int qlp_bls_plan_stats(const qlp_bls_plan_t* pl, double* work_points, double* wo
   return QLP_OK;
 }
 
+// Records a timing event of the main search kernel; inside a stream capture the
+// record becomes an event node of the graph.
+static cudaError_t record_kev(qlp_bls_plan_t* pl, int i, cudaStream_t st) {
+  if (!pl->kev[i]) return cudaSuccess;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
+  return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(pl->kev[i], st, cudaEventRecordExternal)
+                                             : cudaEventRecord(pl->kev[i], st);
+}
+
+// The kernel the timing events bracket: the exact cell kernel when it has work,
+// else the compensated cell kernel, else the per-point kernel.
+static int timed_kernel(const qlp_bls_plan_t* pl) {
+  return pl->f_items > 0 ? kMethodFixed : pl->c_items > 0 ? kMethodCells : kMethodPoints;
+}
+
+int qlp_bls_kernel_timing(qlp_bls_plan_t* pl, int32_t enable) {
+  if (!pl) return QLP_ERR_ARG;
+  for (int i = 0; i < 2; ++i) {
+    if (enable && !pl->kev[i]) QLP_CK(cudaEventCreate(&pl->kev[i]));
+    if (!enable && pl->kev[i]) {
+      cudaEventDestroy(pl->kev[i]);
+      pl->kev[i] = nullptr;
+    }
+  }
+  return QLP_OK;
+}
+
+int qlp_bls_kernel_time(qlp_bls_plan_t* pl, float* ms, int32_t* kernel) {
+  if (!pl || !ms || !pl->kev[0]) return QLP_ERR_ARG;
+  QLP_CK(cudaEventSynchronize(pl->kev[1]));
+  QLP_CK(cudaEventElapsedTime(ms, pl->kev[0], pl->kev[1]));
+  if (kernel) *kernel = timed_kernel(pl);
+  return QLP_OK;
+}
+
+int qlp_bls_plan_exact_stats(const qlp_bls_plan_t* pl, int32_t* n_exact_stars, double* exact_edges) {
+  if (!pl) return QLP_ERR_ARG;
+  if (n_exact_stars) *n_exact_stars = pl->n_fixed_stars;
+  if (exact_edges) *exact_edges = pl->edges_fixed;
+  return QLP_OK;
+}
+
 int qlp_bls_search(qlp_bls_plan_t* pl, void* stream, float* sr, uint8_t* qidx, uint32_t* phase_bin,
                    float* s_best, float* r_best) {
   if (!pl) return QLP_ERR_ARG;
@@ -536,6 +630,7 @@ int qlp_bls_search(qlp_bls_plan_t* pl, void* stream, float* sr, uint8_t* qidx, u
   if (pl->n_stars == 0 || pl->f_off.back() == 0) return QLP_OK;
   cudaStream_t st = (cudaStream_t)stream;
   QLP_CK(cudaMemsetAsync(pl->d_ctl, 0, 2 * sizeof(int32_t), st));
+  QLP_CK(cudaMemsetAsync(pl->d_ctl + 3, 0, sizeof(int32_t), st));
   int e = 0;
   if (pl->n_items > 0) {
     PrepArgs pa{};
@@ -569,14 +664,17 @@ int qlp_bls_search(qlp_bls_plan_t* pl, void* stream, float* sr, uint8_t* qidx, u
     a.tile_pts = pl->tile_pts;
     a.hist_stride = pl->hist_stride;
     a.tile_off = pl->tile_off;
-    e = launch_bls(a, pl->p.phase_mode, pl->p.sum_mode, pl->warps, pl->blocks, pl->smem, stream);
+    if (timed_kernel(pl) == kMethodPoints) QLP_CK(record_kev(pl, 0, st));
+    e = launch_bls(a, pl->p.phase_mode, pl->p.sum_mode == QLP_SUM_PLAIN ? QLP_SUM_PLAIN : QLP_SUM_COMP, pl->warps,
+                   pl->blocks, pl->smem, stream);
     if (e) return cuda_fail((cudaError_t)e, "search launch");
+    if (timed_kernel(pl) == kMethodPoints) QLP_CK(record_kev(pl, 1, st));
   }
   if (pl->c_items > 0) {
     PrepCellsArgs pc{};
     pc.stars = pl->d_stars;
     pc.cell_stars = pl->d_cell_stars;
-    pc.n = pl->n_cell_stars;
+    pc.n = pl->n_cell_stars - pl->n_fixed_stars;  // the compensated kernel's stars (d_cell_stars)
     pc.tp = pl->d_tp;
     pc.y = pl->d_y;
     pc.dy = pl->d_dy;
@@ -609,8 +707,58 @@ int qlp_bls_search(qlp_bls_plan_t* pl, void* stream, float* sr, uint8_t* qidx, u
     c.per_q = pl->p.bin_mode == QLP_BIN_PER_Q ? 1 : 0;
     c.m_perq = (int32_t)pl->p.noverlap;
     for (int j = 0; j < kMaxQ; ++j) c.E[j] = pl->E[j];
-    e = launch_cells(c, pl->p.sum_mode, pl->c_warps, pl->c_blocks, pl->c_smem, stream);
+    if (timed_kernel(pl) == kMethodCells) QLP_CK(record_kev(pl, 0, st));
+    e = launch_cells(c, pl->p.sum_mode == QLP_SUM_PLAIN ? QLP_SUM_PLAIN : QLP_SUM_COMP, pl->c_warps, pl->c_blocks,
+                     pl->c_smem, stream);
     if (e) return cuda_fail((cudaError_t)e, "cell search launch");
+    if (timed_kernel(pl) == kMethodCells) QLP_CK(record_kev(pl, 1, st));
+  }
+  if (pl->f_items > 0) {
+    PrepFixedArgs pf{};
+    pf.stars = pl->d_stars;
+    pf.fixed_stars = pl->d_fixed_stars;
+    pf.n = pl->n_fixed_stars;
+    pf.nq = pl->nq;
+    pf.tp = pl->d_tp;
+    pf.y = pl->d_y;
+    pf.dy = pl->d_dy;
+    pf.fq = pl->d_fq;
+    pf.ipre = reinterpret_cast<longlong2*>(pl->d_cpre);
+    pf.dt = pl->d_dt;
+    pf.loc = reinterpret_cast<int2*>(pl->d_loc);
+    pf.base = reinterpret_cast<longlong2*>(pl->d_base);
+    pf.gidx = pl->d_gidx;
+    pf.fx = pl->d_fx;
+    pf.frec = pl->d_frec;
+    pf.noverlap = pl->p.noverlap;
+    for (int j = 0; j < kMaxQ; ++j) pf.E[j] = pl->E[j];
+    pf.nb_cap = pl->p.nbins_cap;
+    e = launch_prep_fixed(pf, stream);
+    if (e) return cuda_fail((cudaError_t)e, "exact cell prep launch");
+    FixedArgs fa{};
+    fa.stars = pl->d_stars;
+    fa.fx = pl->d_fx;
+    fa.fq = pl->d_fq;
+    fa.frec = pl->d_frec;
+    fa.items = pl->d_items + pl->n_items + pl->c_items;
+    fa.n_items = pl->f_items;
+    fa.nq = pl->nq;
+    fa.tp = pl->d_tp;
+    fa.dt = pl->d_dt;
+    fa.loc = reinterpret_cast<const int2*>(pl->d_loc);
+    fa.base = reinterpret_cast<const longlong2*>(pl->d_base);
+    fa.gidx = pl->d_gidx;
+    fa.cursor = pl->d_ctl + 3;
+    fa.err = pl->d_ctl + 2;
+    fa.sr = sr;
+    fa.qidx = qidx;
+    fa.kbin = phase_bin;
+    fa.sbest = s_best;
+    fa.rbest = r_best;
+    QLP_CK(record_kev(pl, 0, st));
+    e = launch_cells_fixed(fa, pl->f_blocks, pl->f_smem, stream);
+    if (e) return cuda_fail((cudaError_t)e, "exact cell search launch");
+    QLP_CK(record_kev(pl, 1, st));
   }
   return QLP_OK;
 }

@@ -27,6 +27,22 @@ static __device__ __noinline__ int exact_global_bin(const double* tptr, double f
   return c * nb + b;
 }
 
+// Cell path: cell of a point: u = floor(t'/h) adjusted so that t' - u h (in FP64) is in [0, h).
+__device__ __forceinline__ int cell_of(double t, double h) {
+  double q = floor(__ddiv_rn(t, h));
+  const double r = __dsub_rn(t, __dmul_rn(q, h));
+  if (r < 0.0) q -= 1.0;
+  else if (r >= h) q += 1.0;
+  return (int)q;
+}
+
+// Exact "point of cell u lies before edge G" from the FP64 fold of that point.
+static __device__ __noinline__ int exact_before(const double* tp, int i, double f, int nb, int G) {
+  int c;
+  const int b = fold_fp64(tp[i], f, nb, &c);
+  return (c * nb + b) < G ? 1 : 0;
+}
+
 constexpr int kU = 4;
 constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: adding it rounds |x| < 2^22 to an integer
 constexpr int kMagicBits = 0x4B400000;

@@ -34,15 +34,6 @@
 
 namespace qlp {
 
-// Cell of a point: u = floor(t'/h) adjusted so that t' - u h (in FP64) is in [0, h).
-__device__ __forceinline__ int cell_of(double t, double h) {
-  double q = floor(__ddiv_rn(t, h));
-  const double r = __dsub_rn(t, __dmul_rn(q, h));
-  if (r < 0.0) q -= 1.0;
-  else if (r >= h) q += 1.0;
-  return (int)q;
-}
-
 // ------------------------------------------------------------------ K1c
 
 __global__ void __launch_bounds__(256) prep_cells_kernel(const PrepCellsArgs a) {
@@ -144,13 +135,6 @@ int launch_prep_cells(const PrepCellsArgs& a, void* stream) {
 }
 
 // ------------------------------------------------------------------ K2c
-
-// Exact "point of cell u lies before edge G" from the FP64 fold of that point.
-static __device__ __noinline__ int exact_before(const double* tp, int i, double f, int nb, int G) {
-  int c;
-  const int b = fold_fp64(tp[i], f, nb, &c);
-  return (c * nb + b) < G ? 1 : 0;
-}
 
 // Shared-memory layout of one star's cell table followed by the per-warp
 // duration tables and histograms (the histogram stride is chosen per work item).

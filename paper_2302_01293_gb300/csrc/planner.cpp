@@ -115,6 +115,7 @@ void plan_one(const qlp_bls_params& p, const double* t, const double* y, const d
     const int nb = nbins_of(q, p);
     s.nbins.push_back(nb);
     s.nbins_max = std::max(s.nbins_max, nb);
+    s.nbins_min = s.nbins.size() == 1 ? nb : std::min(s.nbins_min, nb);
     s.ymax = std::max(s.ymax, s.baseline * f * (double)nb);
   };
   if (p.grid_mode == 1) {

@@ -47,6 +47,7 @@ struct StarDev {
 
 constexpr int32_t kMethodPoints = 0;
 constexpr int32_t kMethodCells = 1;
+constexpr int32_t kMethodFixed = 2;   // cell path with exact fixed-point prefix sums (fixed_kernels.cu)
 
 // (star, frequency chunk) unit of the device work queue.
 struct WorkItem {
@@ -102,6 +103,71 @@ struct CellArgs {
   double E[kMaxQ];
   int32_t per_q;           // QLP_BIN_PER_Q: one histogram of bins q_j / noverlap per duration j
   int32_t m_perq;          // bins per box in that mode (noverlap)
+};
+
+// Exact cell path (fixed_kernels.cu). Per star: the point weights and weighted
+// residuals as integers, w_int = round(w 2^kw) and y_int = round(w d 2^ky), with
+// kw, ky chosen so that any 32 consecutive points sum to less than 2^30 in
+// magnitude; the prefix sums of these integers are exact.
+struct FixedStar {
+  long long w_tot;   // sum of w_int over the star (the prefix sum at the sentinel cell)
+  long long y_tot;   // sum of y_int
+  int32_t kw, ky;
+};
+
+// Per trial frequency of an exact-path star, derived once from (f, q_min) in FP64
+// with the same operations as the other search kernels.
+struct __align__(16) FreqRec {
+  unsigned long long K;      // bin duration D = 1/(f nbins) in cells, 2^-56 fixed point
+  unsigned long long mpack;  // m_j (bins per duration j), 4 bits each, j < nq
+  int32_t nb;                // phase bins; 0 when unsupported (SR 0 and the nbins flag)
+  uint32_t band_q;           // guard band around each edge, 2^-32 of a cell
+  int32_t g_end;             // last edge: tau_{g_end} = g_end D > T
+  int32_t pad;
+};
+
+struct PrepFixedArgs {
+  const StarDev* stars;
+  const int32_t* fixed_stars;  // stars on the exact cell path
+  int32_t n;
+  int32_t nq;
+  const double* tp;
+  const double* y;
+  const double* dy;
+  const double2* fq;
+  longlong2* ipre;             // integer prefix sums before each point, N + 1 per star
+  uint32_t* dt;
+  int2* loc;                   // per cell: prefix sums minus the 32-cell group base (int32 each)
+  longlong2* base;             // per 32 cells: the group's prefix sums (int64 each)
+  int32_t* gidx;
+  FixedStar* fx;
+  FreqRec* frec;
+  double noverlap;
+  double E[kMaxQ];
+  int32_t nb_cap;
+  int32_t pad0;
+};
+
+struct FixedArgs {
+  const StarDev* stars;
+  const FixedStar* fx;
+  const double2* fq;
+  const FreqRec* frec;
+  const WorkItem* items;
+  int32_t n_items;
+  int32_t nq;
+  const double* tp;
+  const uint32_t* dt;
+  const int2* loc;
+  const longlong2* base;
+  const int32_t* gidx;
+  int32_t* cursor;
+  int32_t* err;
+  float* sr;
+  uint8_t* qidx;
+  uint32_t* kbin;
+  float* sbest;
+  float* rbest;
 };
 
 struct PrepCellsArgs {
@@ -173,6 +239,12 @@ int launch_coarse_tensor(const StarDev* stars, int n_stars, const float* snr, in
 int launch_topk(const float* logits, const void* x0, int batch, int len, int k, int32_t* out, void* stream);
 int launch_prep_cells(const PrepCellsArgs& a, void* stream);
 int launch_cells(const CellArgs& a, int sum_mode, int warps, int blocks, size_t smem, void* stream);
+int launch_prep_fixed(const PrepFixedArgs& a, void* stream);
+int launch_cells_fixed(const FixedArgs& a, int blocks, size_t smem, void* stream);
+// shared memory of the exact cell kernel for a table of ncs cells (incl. sentinel)
+uint32_t fixed_smem_bytes(int ncs);
+int fixed_blocks_per_sm(size_t smem);
+constexpr int kFixedWarps = 32;
 // bytes of shared memory before the histograms of the cell kernel for a star with
 // ncs cells (incl. sentinel) and nw warps
 // One point of a candidate's fit window: t', y, 1/dy and its transit index.

@@ -90,7 +90,9 @@ extern "C" int qlp_bls_search_static(const qlp_bls_params* pin, int32_t n, const
   if (!(baseline > 0.0) || !(p.noverlap >= 1.0) || !(p.dlogq > 0.0) || !(p.qmin_fac > 0.0) ||
       !(p.qmax_fac >= p.qmin_fac))
     return QLP_ERR_ARG;
-  if (p.phase_mode < 0 || p.phase_mode > 2 || p.sum_mode < 0 || p.sum_mode > 1) return QLP_ERR_ARG;
+  if (p.phase_mode < 0 || p.phase_mode > 2 || p.sum_mode < 0 || p.sum_mode > 2) return QLP_ERR_ARG;
+  // this entry point folds every point; it runs QLP_SUM_FIXED as compensated sums
+  const int sum_mode = p.sum_mode == QLP_SUM_PLAIN ? QLP_SUM_PLAIN : QLP_SUM_COMP;
   if (p.warps_per_block != 0 && p.warps_per_block != 4 && p.warps_per_block != 8 &&
       p.warps_per_block != 16)
     return QLP_ERR_ARG;
@@ -116,7 +118,7 @@ extern "C" int qlp_bls_search_static(const qlp_bls_params* pin, int32_t n, const
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QLP_ERR_CUDA;
 
   // launch shape, as the planned path chooses it
-  const int NA = (p.sum_mode == QLP_SUM_COMP) ? 4 : 2;
+  const int NA = (sum_mode == QLP_SUM_COMP) ? 4 : 2;
   const int hist_stride = ((nbins_max + qlp::kMPad + 31) / 32) * 32;
   const int smem_max = qlp::bls_max_smem_per_block();
   if (smem_max <= 0) return QLP_ERR_CUDA;
@@ -130,7 +132,7 @@ extern "C" int qlp_bls_search_static(const qlp_bls_params* pin, int32_t n, const
   tile = std::min<int64_t>(tile, npad);
   if (p.tile_points > 0) tile = std::min(tile, std::max(32, (p.tile_points / 32) * 32));
   const size_t smem = hb + (size_t)tile * 16;
-  const int per_sm = qlp::bls_blocks_per_sm(p.phase_mode, p.sum_mode, warps, smem);
+  const int per_sm = qlp::bls_blocks_per_sm(p.phase_mode, sum_mode, warps, smem);
   if (per_sm < 1) return QLP_ERR_UNSUPPORTED;
   const int blocks = sms * per_sm;
   int chunk = p.chunk_freqs;
@@ -204,6 +206,6 @@ extern "C" int qlp_bls_search_static(const qlp_bls_params* pin, int32_t n, const
   a.hist_stride = hist_stride;
   a.tile_off = (uint32_t)hb;
   const int phase = (ymax >= 4194304.0) ? QLP_PHASE_FP64 : p.phase_mode;
-  if (qlp::launch_bls(a, phase, p.sum_mode, warps, blocks, smem, stream)) return QLP_ERR_CUDA;
+  if (qlp::launch_bls(a, phase, sum_mode, warps, blocks, smem, stream)) return QLP_ERR_CUDA;
   return QLP_OK;
 }

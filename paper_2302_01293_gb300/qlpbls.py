@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 PHASE_FP64, PHASE_DF, PHASE_FP32 = 0, 1, 2
-SUM_PLAIN, SUM_COMP = 0, 1
+SUM_PLAIN, SUM_COMP, SUM_FIXED = 0, 1, 2
 BIN_SHARED, BIN_PER_Q = 0, 1
 MAD_RAW, MAD_RESID = 0, 1
 METHOD_AUTO, METHOD_POINTS, METHOD_CELLS = 0, 1, 2
@@ -66,7 +66,7 @@ class Params:
     rho_default: float = 1.41
     nbins_cap: int = 8192
     phase_mode: int = PHASE_DF
-    sum_mode: int = SUM_COMP
+    sum_mode: int = SUM_FIXED
     mad_mode: int = MAD_RAW
     chunk_freqs: int = 0
     warps_per_block: int = 0
@@ -119,6 +119,12 @@ def lib():
             L.qlp_bls_plan_info.restype = ctypes.c_int
             L.qlp_bls_plan_stats.argtypes = [_vp, _P(_d), _P(_d), _P(_d), _P(_i32), _P(_i32)]
             L.qlp_bls_plan_stats.restype = ctypes.c_int
+            L.qlp_bls_plan_exact_stats.argtypes = [_vp, _P(_i32), _P(_d)]
+            L.qlp_bls_plan_exact_stats.restype = ctypes.c_int
+            L.qlp_bls_kernel_timing.argtypes = [_vp, _i32]
+            L.qlp_bls_kernel_timing.restype = ctypes.c_int
+            L.qlp_bls_kernel_time.argtypes = [_vp, _P(ctypes.c_float), _P(_i32)]
+            L.qlp_bls_kernel_time.restype = ctypes.c_int
             L.qlp_bls_search.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp]
             L.qlp_bls_search.restype = ctypes.c_int
             L.qlp_bls_snr.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
@@ -282,6 +288,11 @@ class Plan:
         self.work_points, self.work_cells, self.edges = wp.value, wc.value, ed.value
         self.n_cell_stars = int(nc.value)
         self.n_windowed = int(nw.value)
+        ne, ee = _i32(), _d()
+        _check(L.qlp_bls_plan_exact_stats(self._h, ctypes.byref(ne), ctypes.byref(ee)),
+               "qlp_bls_plan_exact_stats")
+        self.n_exact_stars = int(ne.value)
+        self.exact_edges = ee.value
 
     def alloc_outputs(self):
         import torch
@@ -355,6 +366,18 @@ class Plan:
 
     def graph_launch(self, parts: int = 3, stream=None):
         _check(lib().qlp_bls_graph_launch(self._h, int(parts), _stream_ptr(stream)), "qlp_bls_graph_launch")
+
+    def kernel_timing(self, enable: bool = True):
+        """qlp_bls_kernel_timing: bracket the main search kernel of every later
+        search (and graph captured afterwards) with CUDA events."""
+        _check(lib().qlp_bls_kernel_timing(self._h, 1 if enable else 0), "qlp_bls_kernel_timing")
+
+    def kernel_time(self):
+        """qlp_bls_kernel_time: (milliseconds, kernel id) of the last search's main
+        kernel; kernel 0 per-point, 1 compensated cell, 2 exact cell."""
+        ms, k = ctypes.c_float(), _i32()
+        _check(lib().qlp_bls_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(k)), "qlp_bls_kernel_time")
+        return float(ms.value), int(k.value)
 
     def candidate_stats(self, out, stats=None, stream=None):
         """qlp_bls_candidate_stats on the best records in `out` (after snr); returns

@@ -35,7 +35,7 @@ def _check_batch(batch, params, stars=None, with_snr=True):
 
 
 @pytest.mark.parametrize("phase", [qlpbls.PHASE_FP64, qlpbls.PHASE_DF])
-@pytest.mark.parametrize("summ", [qlpbls.SUM_PLAIN, qlpbls.SUM_COMP])
+@pytest.mark.parametrize("summ", [qlpbls.SUM_PLAIN, qlpbls.SUM_COMP, qlpbls.SUM_FIXED])
 def test_single_star(gpu_lib, phase, summ):
     b = synth.single_star()
     g, stats = _check_batch(b, qlpbls.Params(phase_mode=phase, sum_mode=summ))
@@ -44,10 +44,33 @@ def test_single_star(gpu_lib, phase, summ):
 
 
 @pytest.mark.parametrize("method", [qlpbls.METHOD_POINTS, qlpbls.METHOD_CELLS])
-@pytest.mark.parametrize("summ", [qlpbls.SUM_PLAIN, qlpbls.SUM_COMP])
+@pytest.mark.parametrize("summ", [qlpbls.SUM_PLAIN, qlpbls.SUM_COMP, qlpbls.SUM_FIXED])
 def test_uneven_batch_both_paths(gpu_lib, method, summ):
     b = synth.uneven_single_sector(n_stars=5, seed=22)
-    _check_batch(b, qlpbls.Params(method=method, sum_mode=summ))
+    g, _ = _check_batch(b, qlpbls.Params(method=method, sum_mode=summ))
+    exact = method == qlpbls.METHOD_CELLS and summ == qlpbls.SUM_FIXED
+    assert g["plan"].n_exact_stars == (5 if exact else 0)
+
+
+def test_exact_cell_path_is_the_default(gpu_lib):
+    # exact integer sums on the cell path for every star whose table fits shared memory
+    b = synth.uneven_single_sector(n_stars=8, seed=27)
+    g, _ = _check_batch(b, qlpbls.Params())
+    assert g["plan"].n_exact_stars == 8 and g["plan"].exact_edges == g["plan"].edges
+
+
+def test_exact_path_falls_back_below_32_bins(gpu_lib):
+    # durations from 1.5 q_circ: 12 bins at Pmin, fewer than a warp's 32 lanes; those
+    # stars take the compensated cell kernel, with the same results
+    b = synth.uneven_single_sector(n_stars=3, seed=28)
+    p = qlpbls.Params(qmin_fac=1.5)
+    g = run_gpu(b, p)
+    assert g["flags"] == 0 and g["plan"].n_exact_stars == 0 and g["plan"].n_cell_stars == 3
+    for s in range(b.n_stars):
+        pl, ores = oracle_star(b, s, oracle.Params(qmin_fac=1.5))
+        sl = g["plan"].star_slice(s)
+        assert np.array_equal(g["plan"].freqs[sl], pl.freqs)
+        compare_spectrum(pl, ores, g, sl, label=f"qmin 1.5 star {s}")
 
 
 @pytest.mark.parametrize("warps", [4, 8, 16])
@@ -55,7 +78,7 @@ def test_cell_path_single_star_and_warps(gpu_lib, warps):
     # 30-min cadence: the cell path is forced (the planner would fold points here)
     b = synth.single_star()
     _check_batch(b, qlpbls.Params(method=qlpbls.METHOD_CELLS, warps_per_block=warps,
-                                  chunk_freqs=warps * 2))
+                                  chunk_freqs=warps * 2, sum_mode=qlpbls.SUM_COMP))
 
 
 @pytest.mark.parametrize("tile", [0, 256, 1024])
