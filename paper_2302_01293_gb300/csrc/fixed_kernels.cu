@@ -40,7 +40,7 @@
 
 namespace qlp {
 
-constexpr int kRing = 96;  // float4 per warp: blocks 2i and 2i+1, then a copy of block 2i
+constexpr int kRing = 96;  // float2 per warp: blocks 2i and 2i+1, then a copy of block 2i
 
 // Byte offsets of the table arrays in shared memory: dt (4 B per cell), loc (8 B
 // per cell), base (16 B per 32 cells), then the rings.
@@ -222,14 +222,6 @@ int launch_prep_fixed(const PrepFixedArgs& a, void* stream) {
 
 // ------------------------------------------------------------------ K2x
 
-// int64 -> (hi, lo) FP32 pair with hi + lo = v to ~2^-48 relative, scaled by
-// the power of two sc (exact).
-__device__ __forceinline__ float2 split_ll(long long v, float sc) {
-  const float hi = __ll2float_rn(v);
-  const float lo = __ll2float_rn(v - __float2ll_rn(hi));
-  return make_float2(__fmul_rn(hi, sc), __fmul_rn(lo, sc));
-}
-
 template <int NW>
 __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -255,7 +247,7 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
     const uint32_t* s_dt = reinterpret_cast<const uint32_t*>(smem);
     const int2* s_loc = reinterpret_cast<const int2*>(smem + fixed_loc_off(ncs));
     const longlong2* s_base = reinterpret_cast<const longlong2*>(smem + fixed_base_off(ncs));
-    float4* ring = reinterpret_cast<float4*>(smem + fixed_ring_off(ncs)) + warp * kRing;
+    float2* ring = reinterpret_cast<float2*>(smem + fixed_ring_off(ncs)) + warp * kRing;
     if (s_star != wi.star) {  // block-uniform: stage the star's table
       uint32_t* d_dt = reinterpret_cast<uint32_t*>(smem);
       int2* d_loc = reinterpret_cast<int2*>(smem + fixed_loc_off(ncs));
@@ -296,52 +288,52 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
       const double f = a.fq[fidx].x;  // for the exact decision near ties
       const int g_end = R.g_end;
       const uint32_t band_q = R.band_q;
-      // distinct widths in increasing order, each with its lowest duration index
-      unsigned long long dmw = 0ull, djw = 0ull;
-      int nd = 0, last = 0;
-      for (int j = 0; j < a.nq; ++j) {
+      // widths present (bit w-1 for a box of w bins) and the lowest duration index j
+      // of each width (4 bits per width); m_j is non-decreasing in j
+      uint32_t wmask = 0u;
+      unsigned long long jlow = 0ull;
+      int mmax = 1;
+      for (int j = a.nq - 1; j >= 0; --j) {
         const int m = (int)((R.mpack >> (4 * j)) & 15ull);
-        if (m != last) {
-          dmw |= (unsigned long long)m << (4 * nd);
-          djw |= (unsigned long long)j << (4 * nd);
-          ++nd;
-          last = m;
-        }
+        wmask |= 1u << (m - 1);
+        jlow = (jlow & ~(0xfull << (4 * (m - 1)))) | ((unsigned long long)j << (4 * (m - 1)));
+        mmax = max(mmax, m);
       }
       const int bstar = g_end % nb;
       const uint32_t k_lo = (uint32_t)R.K, k_hi = (uint32_t)(R.K >> 32);
-      // nb K as a 96-bit step [dh : dm : dl]
+      // nb K as a 96-bit step [stp_h : stp_m : stp_l]
       const unsigned long long p0 = (unsigned long long)(uint32_t)nb * k_lo;
       const unsigned long long p1 = (unsigned long long)(uint32_t)nb * k_hi + (p0 >> 32);
       const uint32_t stp_l = (uint32_t)p0, stp_m = (uint32_t)p1, stp_h = (uint32_t)(p1 >> 32);
       const int nblk = (nb + 31) >> 5;
 
       long long h0w = 0, h0y = 0;  // U of bins 0..31 (the wrap-around values)
+      long long pw = 0, py = 0;    // U of the previous block
       float bs2 = -1.f, bd = 1.f, bsv = 0.f, brv = 0.f;
-      int bj = 255, bk = -1;
-      for (int i = 0; i <= nblk; ++i) {
+      int bo = 255, bk = -1;       // best box: width - 1 and start bin
+      // block i: U of bins 32 i + lane; then the histogram of block i - 1 and the
+      // sweep of block i - 2 (boxes of up to 15 bins starting in it)
+      for (int i = 0; i <= nblk + 1; ++i) {
         const int x = (i << 5) + lane;
         long long uw = 0, uy = 0;
         if ((i << 5) < nb) {  // warp-uniform: lanes x < nb own bin x
-          const bool inb = x < nb;
-          // X = G K for G = x, in 96 bits [xh : xm : xl]
-          const unsigned long long q0 = (unsigned long long)(uint32_t)x * k_lo;
-          const unsigned long long q1 = (unsigned long long)(uint32_t)x * k_hi + (q0 >> 32);
+          // edges G = G0, G0 + nb, ... <= g_end; the edge at t' = 0 (G = 0) is skipped:
+          // no point lies before it, its prefix sum is exactly 0
+          const int G0 = x == 0 ? nb : x;
+          // X = G0 K in 96 bits [xh : xm : xl]
+          const unsigned long long q0 = (unsigned long long)(uint32_t)G0 * k_lo;
+          const unsigned long long q1 = (unsigned long long)(uint32_t)G0 * k_hi + (q0 >> 32);
           uint32_t xl = (uint32_t)q0, xm = (uint32_t)q1, xh = (uint32_t)(q1 >> 32);
-          int G = x;
           long long aw = 0, ay = 0;
-          const int cmax = (g_end - (i << 5)) / nb + 1;  // edges of the block's first bin
-          for (int c = 0; c < cmax; ++c) {
-            const bool valid = inb && G <= g_end;
+          bool near = false;  // some edge of this lane lies within the guard band of its cell's point
+          // all lanes take cnt edges; only in the last one may a lane be past g_end
+          const int cnt = (g_end - (i << 5)) / nb + 1;
+          auto edge = [&](bool valid) {
             const int u = min((int)__funnelshift_r(xm, xh, 24), nc);  // cell of tau_G
             const uint32_t fr = __funnelshift_r(xl, xm, 24);           // position in it, 2^-32
             const uint32_t dq = s_dt[u];
-            int sel = dq < fr ? 1 : 0;  // the cell's point lies before tau_G
-            const bool need = valid && (dq != 0xffffffffu) && (uint32_t)(dq - fr + band_q) <= 2u * band_q;
-            if (__any_sync(0xffffffffu, need)) {  // rare: decide by the exact FP64 fold
-              if (need) sel = exact_before(tp, gidx[u], f, nb, G);
-            }
-            const int v = u + sel;
+            near = near || (uint32_t)(dq - fr + band_q) <= 2u * band_q;
+            const int v = u + (dq < fr ? 1 : 0);  // past the cell's point if it lies before tau_G
             const int2 lc = s_loc[v];
             const longlong2 bs = s_base[v >> 5];
             if (valid) {
@@ -351,7 +343,38 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
             asm("add.cc.u32 %0, %0, %3;\n\taddc.cc.u32 %1, %1, %4;\n\taddc.u32 %2, %2, %5;"
                 : "+r"(xl), "+r"(xm), "+r"(xh)
                 : "r"(stp_l), "r"(stp_m), "r"(stp_h));
-            G += nb;
+          };
+          int c = 0;
+          for (; c + 2 < cnt; c += 2) {
+            edge(true);
+            edge(true);
+          }
+          if (c + 1 < cnt) edge(true);
+          edge(G0 + (cnt - 1) * nb <= g_end);
+          // lanes past the last bin accumulated nothing meaningful
+          if (x >= nb) {
+            aw = 0;
+            ay = 0;
+            near = false;
+          }
+          if (__any_sync(0xffffffffu, near)) {  // rare: redo the bin, near-ties by the exact FP64 fold
+            if (near) {
+              aw = 0;
+              ay = 0;
+              for (int g = G0; g <= g_end; g += nb) {
+                const unsigned long long r0 = (unsigned long long)(uint32_t)g * k_lo;
+                const unsigned long long r1 = (unsigned long long)(uint32_t)g * k_hi + (r0 >> 32);
+                const int u = min((int)(r1 >> 24), nc);
+                const uint32_t fr = ((uint32_t)r1 << 8) | ((uint32_t)r0 >> 24);
+                const uint32_t dq = s_dt[u];
+                int sel = dq < fr ? 1 : 0;
+                if (dq != 0xffffffffu && (uint32_t)(dq - fr + band_q) <= 2u * band_q)
+                  sel = exact_before(tp, gidx[u], f, nb, g);
+                const int v = u + sel;
+                aw += s_base[v >> 5].x + (long long)s_loc[v].x;
+                ay += s_base[v >> 5].y + (long long)s_loc[v].y;
+              }
+            }
           }
           if (bstar < x) {
             aw += fx.w_tot;
@@ -361,7 +384,7 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
           uy = ay;
         }
         if ((i << 5) + 31 >= nb) {  // warp-uniform: lanes x >= nb take U[x - nb] + total
-          const int src = (x - nb) & 31;  // x - nb < 32 for every value the sweep reads
+          const int src = (x - nb) & 31;  // x - nb < 32 for every value the sweep uses
           const long long ow = __shfl_sync(0xffffffffu, h0w, src);
           const long long oy = __shfl_sync(0xffffffffu, h0y, src);
           if (x >= nb) {
@@ -372,31 +395,42 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
         if (i == 0) {
           h0w = uw;
           h0y = uy;
+        } else {
+          // histogram of block i - 1: H[x] = U[x + 1] - U[x], exact, then FP32
+          long long nw = __shfl_down_sync(0xffffffffu, pw, 1);
+          long long ny = __shfl_down_sync(0xffffffffu, py, 1);
+          const long long fw = __shfl_sync(0xffffffffu, uw, 0);
+          const long long fy = __shfl_sync(0xffffffffu, uy, 0);
+          if (lane == 31) {
+            nw = fw;
+            ny = fy;
+          }
+          const float2 hv = make_float2(__fmul_rn(__ll2float_rn(nw - pw), scw), __fmul_rn(__ll2float_rn(ny - py), scy));
+          ring[(((i - 1) & 1) << 5) + lane] = hv;
+          if (!((i - 1) & 1)) ring[64 + lane] = hv;
         }
-        const float2 pw = split_ll(uw, scw), py = split_ll(uy, scy);
-        const float4 v = make_float4(pw.x, pw.y, py.x, py.y);
-        ring[((i & 1) << 5) + lane] = v;
-        if (!(i & 1)) ring[64 + lane] = v;
+        pw = uw;
+        py = uy;
         __syncwarp();
-        if (i >= 1) {  // sweep block i - 1: boxes starting at bins k = 32 (i-1) + lane
-          const int k = ((i - 1) << 5) + lane;
-          const float4* rb = ring + (((i - 1) & 1) << 5) + lane;
-          const float4 uk = rb[0];
-          if (k < nb) {
-            for (int d = 0; d < nd; ++d) {
-              const int m = (int)((dmw >> (4 * d)) & 15ull);
-              const int j = (int)((djw >> (4 * d)) & 15ull);
-              const float4 ve = rb[m];
-              const float r = __fadd_rn(__fsub_rn(ve.x, uk.x), __fsub_rn(ve.y, uk.y));
-              const float sv = __fadd_rn(__fsub_rn(ve.z, uk.z), __fsub_rn(ve.w, uk.w));
-              if (r > 0.f && r < 1.f) {
-                const float dd = __fmul_rn(r, __fsub_rn(1.f, r));
-                const float s2 = __fmul_rn(sv, sv);
+        if (i >= 2) {  // sweep block i - 2: running sums over its boxes' bins
+          const int k = ((i - 2) << 5) + lane;
+          const float2* rb = ring + (((i - 2) & 1) << 5) + lane;
+          const bool kin = k < nb;
+          float rw = 0.f, ry = 0.f;
+#pragma unroll
+          for (int o = 0; o < 15; ++o) {
+            if (o < mmax) {
+              const float2 hv = rb[o];
+              rw = __fadd_rn(rw, hv.x);
+              ry = __fadd_rn(ry, hv.y);
+              if (((wmask >> o) & 1u) && kin && rw > 0.f && rw < 1.f) {
+                const float dd = __fmul_rn(rw, __fsub_rn(1.f, rw));
+                const float s2 = __fmul_rn(ry, ry);
                 const float lhs = __fmul_rn(s2, bd), rhs = __fmul_rn(bs2, dd);
-                // a later box wins on a larger score, or on an equal one with a lower j
-                // (this lane visits k in increasing order, and j increasing per k)
-                if (lhs > rhs || (lhs == rhs && j < bj)) {
-                  bs2 = s2; bd = dd; bsv = sv; brv = r; bj = j; bk = k;
+                // larger score, or equal with a narrower box (= lower j); this lane visits
+                // k in increasing order and the widths increasing per k
+                if (lhs > rhs || (lhs == rhs && o < bo)) {
+                  bs2 = s2; bd = dd; bsv = ry; brv = rw; bo = o; bk = k;
                 }
               }
             }
@@ -404,6 +438,7 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
         }
         __syncwarp();
       }
+      int bj = bo < 16 ? (int)((jlow >> (4 * bo)) & 15ull) : 255;
       for (int off = 16; off > 0; off >>= 1) {
         const float o_s2 = __shfl_xor_sync(0xffffffffu, bs2, off);
         const float o_d = __shfl_xor_sync(0xffffffffu, bd, off);
@@ -423,7 +458,7 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
   if (!done && threadIdx.x == 0) atomicOr(a.err, kErrQueueBound);
 }
 
-uint32_t fixed_smem_bytes(int ncs) { return fixed_ring_off(ncs) + (uint32_t)kFixedWarps * kRing * 16u; }
+uint32_t fixed_smem_bytes(int ncs) { return fixed_ring_off(ncs) + (uint32_t)kFixedWarps * kRing * 8u; }
 
 int launch_cells_fixed(const FixedArgs& a, int blocks, size_t smem, void* stream) {
   auto kern = cells_fixed_kernel<kFixedWarps>;
