@@ -755,6 +755,7 @@ int qlp_bls_search(qlp_bls_plan_t* pl, void* stream, float* sr, uint8_t* qidx, u
     fa.kbin = phase_bin;
     fa.sbest = s_best;
     fa.rbest = r_best;
+    fa.stride4 = 4;
     QLP_CK(record_kev(pl, 0, st));
     e = launch_cells_fixed(fa, pl->f_blocks, pl->f_smem, stream);
     if (e) return cuda_fail((cudaError_t)e, "exact cell search launch");

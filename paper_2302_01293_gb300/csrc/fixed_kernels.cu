@@ -41,6 +41,9 @@
 namespace qlp {
 
 constexpr int kRing = 96;  // float2 per warp: blocks 2i and 2i+1, then a copy of block 2i
+// cells staged past the sentinel (copies of it): every edge G <= g_end lies before
+// T + 2 D, at most 2 x 255 + 1 cells past the table, so the loop needs no clamp
+constexpr int kPadCells = 544;
 
 // Byte offsets of the table arrays in shared memory: dt (4 B per cell), loc (8 B
 // per cell), base (16 B per 32 cells), then the rings.
@@ -184,30 +187,37 @@ __global__ void __launch_bounds__(256) prep_fixed_kernel(const PrepFixedArgs a) 
     const double2 fq = a.fq[fidx];
     FreqRec r;
     r.K = 0ull;
-    r.mpack = 0ull;
+    r.jlow = 0ull;
     r.nb = 0;
     r.band_q = 0u;
-    r.g_end = 0;
-    r.pad = 0;
+    r.gq_bstar = 0u;
+    r.wmask = 0u;
     const int nb = (int)ceil(__ddiv_rn(a.noverlap, fq.y));
-    if (nb >= 32 && nb <= a.nb_cap) {
+    if (nb >= 32 && nb <= min(a.nb_cap, 8192)) {
       const double F = __dmul_rn(fq.x, (double)nb);
       const double D = __ddiv_rn(1.0, F);  // bin duration (days)
       const double yT = __dmul_rn(st.baseline, F);
-      r.g_end = (int)floor(yT) + 2;  // edges 0 .. g_end; tau_{g_end} > T
-      r.K = __double2ull_rn(__dmul_rn(__ddiv_rn(D, h), 72057594037927936.0));
-      // guard band in 2^-32 cell units: the FP64 fold's and the fixed-point edge's
-      // errors (2^-20 + 2^-40 T F bins, converted) plus the table's quantisation
+      const int g_end = (int)floor(yT) + 2;  // edges 0 .. g_end; tau_{g_end} > T
+      r.gq_bstar = ((uint32_t)(g_end / nb) << 13) | (uint32_t)(g_end % nb);
+      r.K = __double2ull_rn(__dmul_rn(__ddiv_rn(D, h), 1099511627776.0));  // D/h < 2^8 in 2^-40 units
+      // guard band in 2^-32 cell units, twice the sum of the bounds on: the FP64 fold's
+      // error, (T F + nbins) 2^-53 bins = (T F + nbins) (D/h) 2^-21 units; the edge step's
+      // rounding, 2^-41 cells per edge (g_end 2^-9 units); the FP64 cell offsets of the
+      // points and of D/h, (T/h) 2^-20 units; and the two 32-bit truncations
       r.band_q = (uint32_t)fmin(
-          __dmul_rn(__ddiv_rn(__dmul_rn(9.5367431640625e-07 + 9.094947017729282e-13 * yT, D), h), 4294967296.0) +
-              64.0,
+          __dmul_rn(__dmul_rn(__dadd_rn(yT, (double)nb), __ddiv_rn(D, h)), 9.5367431640625e-07) +
+              (double)(g_end >> 8) + __dmul_rn(__ddiv_rn(st.baseline, h), 3.814697265625e-06) + 16.0,
           1073741824.0);
-      unsigned long long mp = 0ull;
-      for (int j = 0; j < a.nq; ++j) {
-        const int m = max(1, (int)floor(__dadd_rn(__dmul_rn(__dmul_rn(fq.y, a.E[j]), (double)nb), 0.5)));
-        mp |= (unsigned long long)min(m, 15) << (4 * j);
+      // box widths m_j and, per width, its lowest j (m_j is non-decreasing in j)
+      unsigned long long jl = 0ull;
+      uint32_t wm = 0u;
+      for (int j = a.nq - 1; j >= 0; --j) {
+        const int m = min(15, max(1, (int)floor(__dadd_rn(__dmul_rn(__dmul_rn(fq.y, a.E[j]), (double)nb), 0.5))));
+        wm |= 1u << (m - 1);
+        jl = (jl & ~(0xfull << (4 * (m - 1)))) | ((unsigned long long)j << (4 * (m - 1)));
       }
-      r.mpack = mp;
+      r.jlow = jl;
+      r.wmask = wm;
       r.nb = nb;
     }
     a.frec[fidx] = r;
@@ -222,6 +232,36 @@ int launch_prep_fixed(const PrepFixedArgs& a, void* stream) {
 
 // ------------------------------------------------------------------ K2x
 
+// Box sweep of one start bin k over the running sums of its next bins (rb[o] = H[k + o]):
+// every width w = o + 1 present is scored s^2 / (r (1 - r)) for 0 < r < 1 and compared
+// division-free with the lane's best (s, r) so far; ties go to the narrower box, then
+// the lower k (key = o << 16 | k). ALL: widths 3..11 (the paper's grid; no mask test).
+template <bool ALL>
+__device__ __forceinline__ void sweep_start(const float2* rb, bool kin, int k, int mmax, uint32_t wmask,
+                                            float& bsv, float& brv, int& bkey) {
+  float rw = kin ? 0.f : 2.f, ry = 0.f;  // a start past the last bin never scores (r >= 1)
+#pragma unroll
+  for (int o = 0; o < (ALL ? 11 : 15); ++o) {
+    if (ALL || o < mmax) {
+      const float2 hv = rb[o];
+      rw = __fadd_rn(rw, hv.x);
+      ry = __fadd_rn(ry, hv.y);
+      if (ALL ? o >= 2 : ((wmask >> o) & 1u) != 0u) {
+        const float dd = __fmaf_rn(-rw, rw, rw);  // r (1 - r)
+        const float s2 = __fmul_rn(ry, ry);
+        const float bd = __fmaf_rn(-brv, brv, brv);
+        const float bs2 = __fmul_rn(bsv, bsv);
+        const float lhs = __fmul_rn(s2, bd), rhs = __fmul_rn(bs2, dd);
+        const int key = (o << 16) | k;
+        const bool better = rw > 0.f && rw < 1.f && (lhs > rhs || (lhs == rhs && key < bkey));
+        bsv = better ? ry : bsv;
+        brv = better ? rw : brv;
+        bkey = better ? key : bkey;
+      }
+    }
+  }
+}
+
 template <int NW>
 __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -229,6 +269,9 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
   const int lane = threadIdx.x & 31;
   __shared__ int s_item, s_star, s_next;
   if (threadIdx.x == 0) s_star = -1;
+  // element strides as run-time values, so that the table addresses are formed by
+  // integer multiply-adds rather than by the (busier) integer logic pipe
+  const uint32_t st4 = a.stride4, st8 = 2u * a.stride4, st16 = 4u * a.stride4;
 
   bool done = false;
   for (int iter = 0; iter <= a.n_items; ++iter) {
@@ -242,25 +285,26 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
     if (it >= a.n_items) { done = true; break; }
     const WorkItem wi = a.items[it];
     const StarDev st = a.stars[wi.star];
+    const FixedStar fx = a.fx[wi.star];
     const int nc = st.n_cells;  // sentinel cell index
-    const int ncs = nc + 1;
-    const uint32_t* s_dt = reinterpret_cast<const uint32_t*>(smem);
-    const int2* s_loc = reinterpret_cast<const int2*>(smem + fixed_loc_off(ncs));
-    const longlong2* s_base = reinterpret_cast<const longlong2*>(smem + fixed_base_off(ncs));
-    float2* ring = reinterpret_cast<float2*>(smem + fixed_ring_off(ncs)) + warp * kRing;
-    if (s_star != wi.star) {  // block-uniform: stage the star's table
+    const int ncp = nc + 1 + kPadCells;
+    const uint32_t loc_off = fixed_loc_off(ncp), base_off = fixed_base_off(ncp);
+    float2* ring = reinterpret_cast<float2*>(smem + fixed_ring_off(ncp)) + warp * kRing;
+    if (s_star != wi.star) {  // block-uniform: stage the star's table and its padding
       uint32_t* d_dt = reinterpret_cast<uint32_t*>(smem);
-      int2* d_loc = reinterpret_cast<int2*>(smem + fixed_loc_off(ncs));
-      longlong2* d_base = reinterpret_cast<longlong2*>(smem + fixed_base_off(ncs));
-      for (int i = threadIdx.x; i < ncs; i += NW * 32) {
-        d_dt[i] = a.dt[st.cell_off + i];
-        d_loc[i] = a.loc[st.cell_off + i];
+      int2* d_loc = reinterpret_cast<int2*>(smem + loc_off);
+      longlong2* d_base = reinterpret_cast<longlong2*>(smem + base_off);
+      const int2 lnc = a.loc[st.cell_off + nc];
+      for (int i = threadIdx.x; i < ncp; i += NW * 32) {
+        const bool in = i <= nc;
+        d_dt[i] = in ? a.dt[st.cell_off + i] : 0xffffffffu;
+        d_loc[i] = in ? a.loc[st.cell_off + i] : ((i >> 5) == (nc >> 5) ? lnc : make_int2(0, 0));
       }
-      for (int i = threadIdx.x; i < (ncs + 31) / 32; i += NW * 32) d_base[i] = a.base[st.base_off + i];
+      for (int i = threadIdx.x; i < (ncp + 31) / 32; i += NW * 32)
+        d_base[i] = i <= (nc >> 5) ? a.base[st.base_off + i] : make_longlong2(fx.w_tot, fx.y_tot);
       __syncthreads();
       if (threadIdx.x == 0) s_star = wi.star;
     }
-    const FixedStar fx = a.fx[wi.star];
     const float scw = __int_as_float((127 - fx.kw) << 23);  // 2^-kw (|kw| <= 100)
     const float scy = __int_as_float((127 - fx.ky) << 23);
     const double* tp = a.tp + st.pt_off;
@@ -286,71 +330,82 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
         continue;
       }
       const double f = a.fq[fidx].x;  // for the exact decision near ties
-      const int g_end = R.g_end;
       const uint32_t band_q = R.band_q;
-      // widths present (bit w-1 for a box of w bins) and the lowest duration index j
-      // of each width (4 bits per width); m_j is non-decreasing in j
-      uint32_t wmask = 0u;
-      unsigned long long jlow = 0ull;
-      int mmax = 1;
-      for (int j = a.nq - 1; j >= 0; --j) {
-        const int m = (int)((R.mpack >> (4 * j)) & 15ull);
-        wmask |= 1u << (m - 1);
-        jlow = (jlow & ~(0xfull << (4 * (m - 1)))) | ((unsigned long long)j << (4 * (m - 1)));
-        mmax = max(mmax, m);
-      }
-      const int bstar = g_end % nb;
+      const uint32_t wmask = R.wmask;
+      const unsigned long long jlow = R.jlow;
+      const int mmax = 32 - __clz(wmask);
+      const bool all_widths = wmask == 0x7fcu;  // exactly 3 .. 11 bins
+      const int gq = (int)(R.gq_bstar >> 13), bstar = (int)(R.gq_bstar & 8191u);
+      const int g_end = gq * nb + bstar;
       const uint32_t k_lo = (uint32_t)R.K, k_hi = (uint32_t)(R.K >> 32);
-      // nb K as a 96-bit step [stp_h : stp_m : stp_l]
-      const unsigned long long p0 = (unsigned long long)(uint32_t)nb * k_lo;
-      const unsigned long long p1 = (unsigned long long)(uint32_t)nb * k_hi + (p0 >> 32);
-      const uint32_t stp_l = (uint32_t)p0, stp_m = (uint32_t)p1, stp_h = (uint32_t)(p1 >> 32);
       const int nblk = (nb + 31) >> 5;
 
       long long h0w = 0, h0y = 0;  // U of bins 0..31 (the wrap-around values)
       long long pw = 0, py = 0;    // U of the previous block
-      float bs2 = -1.f, bd = 1.f, bsv = 0.f, brv = 0.f;
-      int bo = 255, bk = -1;       // best box: width - 1 and start bin
+      float bsv = 0.f, brv = 0.f;  // best box of this lane: s, r and its key
+      int bkey = 0x7fffffff;
       // block i: U of bins 32 i + lane; then the histogram of block i - 1 and the
       // sweep of block i - 2 (boxes of up to 15 bins starting in it)
       for (int i = 0; i <= nblk + 1; ++i) {
         const int x = (i << 5) + lane;
         long long uw = 0, uy = 0;
         if ((i << 5) < nb) {  // warp-uniform: lanes x < nb own bin x
-          // edges G = G0, G0 + nb, ... <= g_end; the edge at t' = 0 (G = 0) is skipped:
-          // no point lies before it, its prefix sum is exactly 0
-          const int G0 = x == 0 ? nb : x;
-          // X = G0 K in 96 bits [xh : xm : xl]
-          const unsigned long long q0 = (unsigned long long)(uint32_t)G0 * k_lo;
-          const unsigned long long q1 = (unsigned long long)(uint32_t)G0 * k_hi + (q0 >> 32);
-          uint32_t xl = (uint32_t)q0, xm = (uint32_t)q1, xh = (uint32_t)(q1 >> 32);
+          // edges G = G0, G0 + nb, ... <= g_end (one per cycle). The edge at t' = 0
+          // (G = 0) is skipped: no point lies before it. A block of r <= 16 bins spreads
+          // each bin's cycles over P = 32 / r lanes (phase ph: cycles ph, ph + P, ...),
+          // summed by shuffles afterwards. Idle lanes walk a real bin's edges
+          // (discarded), so that every edge stays inside the staged table.
+          const int r = nb - (i << 5);
+          const bool split = r <= 16;
+          int P = 1, ph = 0, xb = x;
+          if (split) {
+            P = 32 / r;
+            ph = lane / r;
+            xb = (i << 5) + (lane - ph * r);
+          }
+          const bool idle = split ? ph >= P : x >= nb;
+          const int G0 = idle ? (i << 5) : (xb == 0 ? nb : xb + ph * nb);
+          const int gstep = P * nb;
           long long aw = 0, ay = 0;
-          bool near = false;  // some edge of this lane lies within the guard band of its cell's point
-          // all lanes take cnt edges; only in the last one may a lane be past g_end
-          const int cnt = (g_end - (i << 5)) / nb + 1;
-          auto edge = [&](bool valid) {
-            const int u = min((int)__funnelshift_r(xm, xh, 24), nc);  // cell of tau_G
-            const uint32_t fr = __funnelshift_r(xl, xm, 24);           // position in it, 2^-32
-            const uint32_t dq = s_dt[u];
+          bool near = false;  // an edge within the guard band of its cell's point
+          // every lane takes cnt edges; only in the last one may a lane be past g_end
+          const int cnt = (gq + ((i << 5) > bstar ? 0 : 1) + P - 1) / P;
+          auto edge = [&](int G, bool valid, bool clamp) {
+            // tau_G / h in 24.40 fixed point: cell u and position fr (2^-32 of a cell)
+            const unsigned long long X =
+                (unsigned long long)(uint32_t)G * k_lo + ((unsigned long long)((uint32_t)G * k_hi) << 32);
+            int u = (int)((uint32_t)(X >> 32) >> 8);
+            if (clamp) u = min(u, nc);
+            const uint32_t fr = (uint32_t)(X >> 8);
+            const uint32_t dq = *reinterpret_cast<const uint32_t*>(smem + (uint32_t)u * st4);
             near = near || (uint32_t)(dq - fr + band_q) <= 2u * band_q;
             const int v = u + (dq < fr ? 1 : 0);  // past the cell's point if it lies before tau_G
-            const int2 lc = s_loc[v];
-            const longlong2 bs = s_base[v >> 5];
+            const int2 lc = *reinterpret_cast<const int2*>(smem + loc_off + (uint32_t)v * st8);
+            const longlong2 bs = *reinterpret_cast<const longlong2*>(smem + base_off + (uint32_t)(v >> 5) * st16);
             if (valid) {
               aw += bs.x + (long long)lc.x;
               ay += bs.y + (long long)lc.y;
             }
-            asm("add.cc.u32 %0, %0, %3;\n\taddc.cc.u32 %1, %1, %4;\n\taddc.u32 %2, %2, %5;"
-                : "+r"(xl), "+r"(xm), "+r"(xh)
-                : "r"(stp_l), "r"(stp_m), "r"(stp_h));
           };
           int c = 0;
           for (; c + 2 < cnt; c += 2) {
-            edge(true);
-            edge(true);
+            edge(G0 + c * gstep, true, false);
+            edge(G0 + (c + 1) * gstep, true, false);
           }
-          if (c + 1 < cnt) edge(true);
-          edge(G0 + (cnt - 1) * nb <= g_end);
+          if (c + 1 < cnt) edge(G0 + c * gstep, true, false);
+          edge(G0 + (cnt - 1) * gstep, G0 + (cnt - 1) * gstep <= g_end, true);
+          if (split) {  // warp-uniform: add the other phases of each bin into lanes 0 .. r-1
+            for (int q = 1; q < P; ++q) {
+              const long long ow = __shfl_down_sync(0xffffffffu, aw, q * r);
+              const long long oy = __shfl_down_sync(0xffffffffu, ay, q * r);
+              const bool on = __shfl_down_sync(0xffffffffu, near ? 1 : 0, q * r) != 0;
+              if (lane < r) {
+                aw += ow;
+                ay += oy;
+                near = near || on;
+              }
+            }
+          }
           // lanes past the last bin accumulated nothing meaningful
           if (x >= nb) {
             aw = 0;
@@ -361,18 +416,20 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
             if (near) {
               aw = 0;
               ay = 0;
-              for (int g = G0; g <= g_end; g += nb) {
-                const unsigned long long r0 = (unsigned long long)(uint32_t)g * k_lo;
-                const unsigned long long r1 = (unsigned long long)(uint32_t)g * k_hi + (r0 >> 32);
-                const int u = min((int)(r1 >> 24), nc);
-                const uint32_t fr = ((uint32_t)r1 << 8) | ((uint32_t)r0 >> 24);
-                const uint32_t dq = s_dt[u];
+              for (int g = x == 0 ? nb : x; g <= g_end; g += nb) {
+                const unsigned long long X =
+                    (unsigned long long)(uint32_t)g * k_lo + ((unsigned long long)((uint32_t)g * k_hi) << 32);
+                const int u = min((int)((uint32_t)(X >> 32) >> 8), nc);
+                const uint32_t fr = (uint32_t)(X >> 8);
+                const uint32_t dq = reinterpret_cast<const uint32_t*>(smem)[u];
                 int sel = dq < fr ? 1 : 0;
                 if (dq != 0xffffffffu && (uint32_t)(dq - fr + band_q) <= 2u * band_q)
                   sel = exact_before(tp, gidx[u], f, nb, g);
                 const int v = u + sel;
-                aw += s_base[v >> 5].x + (long long)s_loc[v].x;
-                ay += s_base[v >> 5].y + (long long)s_loc[v].y;
+                const int2 lc = reinterpret_cast<const int2*>(smem + loc_off)[v];
+                const longlong2 bs = reinterpret_cast<const longlong2*>(smem + base_off)[v >> 5];
+                aw += bs.x + (long long)lc.x;
+                ay += bs.y + (long long)lc.y;
               }
             }
           }
@@ -412,33 +469,20 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
         pw = uw;
         py = uy;
         __syncwarp();
-        if (i >= 2) {  // sweep block i - 2: running sums over its boxes' bins
+        if (i >= 2) {  // sweep block i - 2: boxes starting at its bins
           const int k = ((i - 2) << 5) + lane;
           const float2* rb = ring + (((i - 2) & 1) << 5) + lane;
-          const bool kin = k < nb;
-          float rw = 0.f, ry = 0.f;
-#pragma unroll
-          for (int o = 0; o < 15; ++o) {
-            if (o < mmax) {
-              const float2 hv = rb[o];
-              rw = __fadd_rn(rw, hv.x);
-              ry = __fadd_rn(ry, hv.y);
-              if (((wmask >> o) & 1u) && kin && rw > 0.f && rw < 1.f) {
-                const float dd = __fmul_rn(rw, __fsub_rn(1.f, rw));
-                const float s2 = __fmul_rn(ry, ry);
-                const float lhs = __fmul_rn(s2, bd), rhs = __fmul_rn(bs2, dd);
-                // larger score, or equal with a narrower box (= lower j); this lane visits
-                // k in increasing order and the widths increasing per k
-                if (lhs > rhs || (lhs == rhs && o < bo)) {
-                  bs2 = s2; bd = dd; bsv = ry; brv = rw; bo = o; bk = k;
-                }
-              }
-            }
-          }
+          if (all_widths) sweep_start<true>(rb, k < nb, k, mmax, wmask, bsv, brv, bkey);
+          else sweep_start<false>(rb, k < nb, k, mmax, wmask, bsv, brv, bkey);
         }
         __syncwarp();
       }
-      int bj = bo < 16 ? (int)((jlow >> (4 * bo)) & 15ull) : 255;
+      const bool none = bkey == 0x7fffffff;
+      float bs2 = none ? -1.f : __fmul_rn(bsv, bsv);
+      float bd = none ? 1.f : __fmaf_rn(-brv, brv, brv);
+      const int bo = bkey >> 16;
+      int bj = none ? 255 : (int)((jlow >> (4 * bo)) & 15ull);
+      int bk = none ? -1 : (bkey & 0xffff);
       for (int off = 16; off > 0; off >>= 1) {
         const float o_s2 = __shfl_xor_sync(0xffffffffu, bs2, off);
         const float o_d = __shfl_xor_sync(0xffffffffu, bd, off);
@@ -458,7 +502,7 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
   if (!done && threadIdx.x == 0) atomicOr(a.err, kErrQueueBound);
 }
 
-uint32_t fixed_smem_bytes(int ncs) { return fixed_ring_off(ncs) + (uint32_t)kFixedWarps * kRing * 8u; }
+uint32_t fixed_smem_bytes(int ncs) { return fixed_ring_off(ncs + kPadCells) + (uint32_t)kFixedWarps * kRing * 8u; }
 
 int launch_cells_fixed(const FixedArgs& a, int blocks, size_t smem, void* stream) {
   auto kern = cells_fixed_kernel<kFixedWarps>;

@@ -118,12 +118,13 @@ struct FixedStar {
 // Per trial frequency of an exact-path star, derived once from (f, q_min) in FP64
 // with the same operations as the other search kernels.
 struct __align__(16) FreqRec {
-  unsigned long long K;      // bin duration D = 1/(f nbins) in cells, 2^-56 fixed point
-  unsigned long long mpack;  // m_j (bins per duration j), 4 bits each, j < nq
+  unsigned long long K;      // bin duration D = 1/(f nbins) in cells, 2^-40 fixed point
+  unsigned long long jlow;   // per box width w (bins): the lowest duration index j with m_j = w,
+                             // 4 bits at bit 4 (w - 1)
   int32_t nb;                // phase bins; 0 when unsupported (SR 0 and the nbins flag)
   uint32_t band_q;           // guard band around each edge, 2^-32 of a cell
-  int32_t g_end;             // last edge: tau_{g_end} = g_end D > T
-  int32_t pad;
+  uint32_t gq_bstar;         // last edge g_end = gq nbins + b*: gq << 13 | b* (b* < nbins <= 8192)
+  uint32_t wmask;            // box widths present: bit w - 1 for a width of w bins
 };
 
 struct PrepFixedArgs {
@@ -168,6 +169,8 @@ struct FixedArgs {
   uint32_t* kbin;
   float* sbest;
   float* rbest;
+  uint32_t stride4;            // 4 (bytes of a table entry; a run-time value on purpose)
+  int32_t pad0;
 };
 
 struct PrepCellsArgs {
