@@ -89,6 +89,7 @@ struct qlp_bls_plan {
   size_t f_smem = 0;
   int32_t f_items = 0;
   int32_t n_fixed_stars = 0;
+  int32_t fixed_max_pts = 0;
   double edges_fixed = 0.0;
   // device
   StarDev* d_stars = nullptr;
@@ -217,6 +218,31 @@ static int check_params(const qlp_bls_params& p) {
   return QLP_OK;
 }
 
+// Arguments of the exact cell path's preparation kernels.
+static PrepFixedArgs fixed_args(const qlp_bls_plan_t* pl) {
+  PrepFixedArgs pf{};
+  pf.stars = pl->d_stars;
+  pf.fixed_stars = pl->d_fixed_stars;
+  pf.n = pl->n_fixed_stars;
+  pf.nq = pl->nq;
+  pf.tp = pl->d_tp;
+  pf.y = pl->d_y;
+  pf.dy = pl->d_dy;
+  pf.fq = pl->d_fq;
+  pf.ipre = reinterpret_cast<longlong2*>(pl->d_cpre);
+  pf.dt = pl->d_dt;
+  pf.loc = reinterpret_cast<int2*>(pl->d_loc);
+  pf.base = reinterpret_cast<longlong2*>(pl->d_base);
+  pf.gidx = pl->d_gidx;
+  pf.fx = pl->d_fx;
+  pf.frec = pl->d_frec;
+  pf.noverlap = pl->p.noverlap;
+  for (int j = 0; j < kMaxQ; ++j) pf.E[j] = pl->E[j];
+  pf.nb_cap = pl->p.nbins_cap;
+  pf.max_pts = pl->fixed_max_pts;
+  return pf;
+}
+
 static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offsets, const double* t,
                      const double* y, const double* dy, const double* rho, const double* rstar,
                      const int64_t* win_off, const double* win_lo, const double* win_hi, void* stream,
@@ -326,7 +352,8 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
     const bool fixed_ok = p.sum_mode == QLP_SUM_FIXED && p.bin_mode == QLP_BIN_SHARED &&
                           (p.cell_window == 0 || p.cell_window >= h.n_cells) &&
                           (size_t)fixed_smem_bytes((int)h.n_cells + 1) <= (size_t)budget && h.nbins_min >= 32 &&
-                          h.baseline * h.freqs.back() <= 16384.0 && h.tp.size() <= ((size_t)1 << 21);
+                          h.baseline * h.freqs.back() <= 16384.0 && h.tp.size() <= ((size_t)1 << 21) &&
+                          (size_t)fixed_prep_smem_bytes((int)h.tp.size()) <= (size_t)budget;
     if (fixed_ok && (p.method == 2 || h.cells_work < 2.0 * pp_work)) {
       method[(size_t)s] = kMethodFixed;
       W = CellWin{1, (int32_t)h.n_cells, (int32_t)ovl, (int32_t)h.n_cells + 1};
@@ -388,6 +415,7 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
       ncpre += d.n_pts + 1;
       if (d.method == kMethodFixed) {
         fixed_stars.push_back(s);
+        pl->fixed_max_pts = std::max(pl->fixed_max_pts, d.n_pts);
         fixed_ncs = std::max<int64_t>(fixed_ncs, h.n_cells + 1);
         pl->edges_fixed += h.cells_work;
       } else {
@@ -547,6 +575,10 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(pl->d_y, y_all.get(), sizeof(double) * (size_t)npt, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(pl->d_dy, dy_all.get(), sizeof(double) * (size_t)npt, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_ctl, 0, 4 * sizeof(int32_t), st);
+  if (e == cudaSuccess && !fixed_stars.empty()) {  // per-frequency records of the exact path
+    const int le = launch_freq_recs(fixed_args(pl), stream);
+    if (le) e = (cudaError_t)le;
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // host staging vectors die at return
   if (e != cudaSuccess) {
     free_plan(pl);
@@ -714,25 +746,7 @@ int qlp_bls_search(qlp_bls_plan_t* pl, void* stream, float* sr, uint8_t* qidx, u
     if (timed_kernel(pl) == kMethodCells) QLP_CK(record_kev(pl, 1, st));
   }
   if (pl->f_items > 0) {
-    PrepFixedArgs pf{};
-    pf.stars = pl->d_stars;
-    pf.fixed_stars = pl->d_fixed_stars;
-    pf.n = pl->n_fixed_stars;
-    pf.nq = pl->nq;
-    pf.tp = pl->d_tp;
-    pf.y = pl->d_y;
-    pf.dy = pl->d_dy;
-    pf.fq = pl->d_fq;
-    pf.ipre = reinterpret_cast<longlong2*>(pl->d_cpre);
-    pf.dt = pl->d_dt;
-    pf.loc = reinterpret_cast<int2*>(pl->d_loc);
-    pf.base = reinterpret_cast<longlong2*>(pl->d_base);
-    pf.gidx = pl->d_gidx;
-    pf.fx = pl->d_fx;
-    pf.frec = pl->d_frec;
-    pf.noverlap = pl->p.noverlap;
-    for (int j = 0; j < kMaxQ; ++j) pf.E[j] = pl->E[j];
-    pf.nb_cap = pl->p.nbins_cap;
+    const PrepFixedArgs pf = fixed_args(pl);
     e = launch_prep_fixed(pf, stream);
     if (e) return cuda_fail((cudaError_t)e, "exact cell prep launch");
     FixedArgs fa{};

@@ -23,7 +23,7 @@
 // prefix sums, the per-cell tables (offset of the cell's point, prefix sums at
 // the cell start as a 64-bit group base plus a 32-bit local part), and one
 // FreqRec per trial frequency (bins, the edge step in 2^-56 cells, guard band,
-// last edge, the bins m_j of each duration).
+// last edge, the box widths present and the lowest duration index of each).
 // K2x cells_fixed_kernel: persistent; work queue of (star, frequency chunk); the
 // star's table in shared memory; warps take the item's frequencies one at a time.
 // Per frequency the bins are handled 32 at a time (lane = bin): the lanes'
@@ -57,7 +57,7 @@ __host__ __device__ __forceinline__ uint32_t fixed_ring_off(int ncs) {
 
 // ------------------------------------------------------------------ K1x
 
-__device__ __forceinline__ double block_sum256(double v, double* red) {
+__device__ __forceinline__ double block_sum(double v, double* red) {  // blockDim.x a multiple of 32, at most 512
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
@@ -67,7 +67,7 @@ __device__ __forceinline__ double block_sum256(double v, double* red) {
   return s;
 }
 
-__device__ __forceinline__ double block_max256(double v, double* red) {
+__device__ __forceinline__ double block_max(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
@@ -86,9 +86,14 @@ __device__ __forceinline__ int fixed_exponent(double vmax) {
   return max(-100, min(25 - e, 100));
 }
 
-__global__ void __launch_bounds__(256) prep_fixed_kernel(const PrepFixedArgs a) {
-  __shared__ double red[8];
-  __shared__ long long scan_w[256], scan_y[256];
+// Dynamic shared memory of prep_fixed_kernel for a star of n points: 1/dy^2 (FP64)
+// and the cell of every point.
+__host__ __device__ __forceinline__ uint32_t prep_fixed_smem(int n) { return (uint32_t)n * 12u; }
+
+__global__ void __launch_bounds__(512) prep_fixed_kernel(const PrepFixedArgs a) {
+  extern __shared__ __align__(16) unsigned char psm[];
+  __shared__ double red[16];
+  __shared__ long long scan_w[512], scan_y[512];
   const int s = a.fixed_stars[blockIdx.x];
   const StarDev st = a.stars[s];
   const int n = st.n_pts;
@@ -97,22 +102,32 @@ __global__ void __launch_bounds__(256) prep_fixed_kernel(const PrepFixedArgs a) 
   const double* y = a.y + st.pt_off;
   const double* dy = a.dy + st.pt_off;
   const int tid = threadIdx.x;
+  const int nc = st.n_cells;
+  const double h = st.h;
+  double* s_inv = reinterpret_cast<double*>(psm);
+  int* s_cell = reinterpret_cast<int*>(psm + 8u * (uint32_t)n);
 
-  // weights w = dy^-2 / sum dy^-2 and the weighted mean (FP64)
+  // weights w = dy^-2 / sum dy^-2 and the weighted mean (FP64); each point's
+  // inverse variance and cell once
   double acc = 0.0;
-  for (int i = tid; i < n; i += blockDim.x) acc += 1.0 / (dy[i] * dy[i]);
-  const double wsum = block_sum256(acc, red);
+  for (int i = tid; i < n; i += blockDim.x) {
+    const double inv = 1.0 / (dy[i] * dy[i]);
+    s_inv[i] = inv;
+    s_cell[i] = cell_of(tp[i], h);
+    acc += inv;
+  }
+  const double rws = 1.0 / block_sum(acc, red);
   acc = 0.0;
-  for (int i = tid; i < n; i += blockDim.x) acc += (1.0 / (dy[i] * dy[i])) / wsum * y[i];
-  const double ybar = block_sum256(acc, red);
+  for (int i = tid; i < n; i += blockDim.x) acc += s_inv[i] * rws * y[i];
+  const double ybar = block_sum(acc, red);
   double mw = 0.0, md = 0.0;
   for (int i = tid; i < n; i += blockDim.x) {
-    const double w = (1.0 / (dy[i] * dy[i])) / wsum;
+    const double w = s_inv[i] * rws;
     mw = fmax(mw, w);
     md = fmax(md, fabs(w * (y[i] - ybar)));
   }
-  mw = block_max256(mw, red);
-  md = block_max256(md, red);
+  mw = block_max(mw, red);
+  md = block_max(md, red);
   const int kw = fixed_exponent(mw), ky = fixed_exponent(md);
   const double pw = ldexp(1.0, kw), py = ldexp(1.0, ky);
 
@@ -122,53 +137,68 @@ __global__ void __launch_bounds__(256) prep_fixed_kernel(const PrepFixedArgs a) 
   const int i0 = min(n, tid * L), i1 = min(n, i0 + L);
   long long sw = 0, sy = 0;
   for (int i = i0; i < i1; ++i) {
-    const double w = (1.0 / (dy[i] * dy[i])) / wsum;
+    const double w = s_inv[i] * rws;
     sw += __double2ll_rn(w * pw);
     sy += __double2ll_rn(w * (y[i] - ybar) * py);
   }
   scan_w[tid] = sw;
   scan_y[tid] = sy;
   __syncthreads();
-  if (tid == 0) {
-    long long rw = 0, ry = 0;
-    for (int k = 0; k < (int)blockDim.x; ++k) {
-      const long long tw = scan_w[k], ty = scan_y[k];
-      scan_w[k] = rw;
-      scan_y[k] = ry;
+  if (tid < 32) {  // exclusive scan of the segment totals: 16 per lane, then the warp
+    const int per = (int)blockDim.x / 32;
+    long long lw = 0, ly = 0;
+    for (int k = 0; k < per; ++k) {
+      lw += scan_w[tid * per + k];
+      ly += scan_y[tid * per + k];
+    }
+    long long xw = lw, xy = ly;  // inclusive warp scan of the lane totals
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long tw = __shfl_up_sync(0xffffffffu, xw, o);
+      const long long ty = __shfl_up_sync(0xffffffffu, xy, o);
+      if (tid >= o) {
+        xw += tw;
+        xy += ty;
+      }
+    }
+    long long rw = xw - lw, ry = xy - ly;  // exclusive
+    for (int k = 0; k < per; ++k) {
+      const long long tw = scan_w[tid * per + k], ty = scan_y[tid * per + k];
+      scan_w[tid * per + k] = rw;
+      scan_y[tid * per + k] = ry;
       rw += tw;
       ry += ty;
     }
-    a.ipre[st.cpre_off + n] = make_longlong2(rw, ry);
-    FixedStar f;
-    f.w_tot = rw;
-    f.y_tot = ry;
-    f.kw = kw;
-    f.ky = ky;
-    a.fx[s] = f;
+    if (tid == 31) {
+      a.ipre[st.cpre_off + n] = make_longlong2(rw, ry);
+      FixedStar f;
+      f.w_tot = rw;
+      f.y_tot = ry;
+      f.kw = kw;
+      f.ky = ky;
+      a.fx[s] = f;
+    }
   }
   __syncthreads();
   long long cw = scan_w[tid], cy = scan_y[tid];
   for (int i = i0; i < i1; ++i) {
     a.ipre[st.cpre_off + i] = make_longlong2(cw, cy);
-    const double w = (1.0 / (dy[i] * dy[i])) / wsum;
+    const double w = s_inv[i] * rws;
     cw += __double2ll_rn(w * pw);
     cy += __double2ll_rn(w * (y[i] - ybar) * py);
   }
   __syncthreads();
 
   // first point at or after each cell start: point i fills cells (cell(i-1), cell(i)]
-  const int nc = st.n_cells;
-  const double h = st.h;
   int32_t* first = a.gidx + st.cell_off;
   for (int i = tid; i <= n; i += blockDim.x) {
-    const int up = (i == 0) ? -1 : cell_of(tp[i - 1], h);
-    const int ui = (i == n) ? nc : cell_of(tp[i], h);
+    const int up = (i == 0) ? -1 : s_cell[i - 1];
+    const int ui = (i == n) ? nc : s_cell[i];
     for (int c = up + 1; c <= ui && c <= nc; ++c) first[c] = i;
   }
   __syncthreads();
   for (int u = tid; u <= nc; u += blockDim.x) {
     const int f = first[u];
-    const bool in_cell = (u < nc) && (f < n) && (cell_of(tp[f], h) == u);
+    const bool in_cell = (u < nc) && (f < n) && (s_cell[f] == u);
     uint32_t q = 0xffffffffu;  // the cell's point as a 32-bit fraction of the cell, empty = all ones
     if (in_cell) {
       const double fr = __ddiv_rn(__dsub_rn(tp[f], __dmul_rn((double)u, h)), h);
@@ -180,7 +210,16 @@ __global__ void __launch_bounds__(256) prep_fixed_kernel(const PrepFixedArgs a) 
     a.loc[st.cell_off + u] = make_int2((int)(c.x - cb.x), (int)(c.y - cb.y));
     if ((u & 31) == 0) a.base[st.base_off + (u >> 5)] = cb;
   }
+}
 
+// K0x freq_rec_kernel (1 CTA per exact-path star, at plan time): one FreqRec per
+// trial frequency. It depends on the grid and the star's cell width only, not on
+// the fluxes, so a plan computes it once for all its searches.
+__global__ void __launch_bounds__(256) freq_rec_kernel(const PrepFixedArgs a) {
+  const int s = a.fixed_stars[blockIdx.x];
+  const StarDev st = a.stars[s];
+  const double h = st.h;
+  const int tid = threadIdx.x;
   // per trial frequency: the same FP64 operations as the other search kernels
   for (int k = tid; k < st.n_f; k += blockDim.x) {
     const int64_t fidx = st.f_off + k;
@@ -224,11 +263,22 @@ __global__ void __launch_bounds__(256) prep_fixed_kernel(const PrepFixedArgs a) 
   }
 }
 
-int launch_prep_fixed(const PrepFixedArgs& a, void* stream) {
+int launch_freq_recs(const PrepFixedArgs& a, void* stream) {
   if (a.n <= 0) return 0;
-  prep_fixed_kernel<<<a.n, 256, 0, (cudaStream_t)stream>>>(a);
+  freq_rec_kernel<<<a.n, 256, 0, (cudaStream_t)stream>>>(a);
   return (int)cudaGetLastError();
 }
+
+int launch_prep_fixed(const PrepFixedArgs& a, void* stream) {
+  if (a.n <= 0) return 0;
+  const int smem = (int)prep_fixed_smem(a.max_pts);
+  cudaError_t e = cudaFuncSetAttribute(prep_fixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return (int)e;
+  prep_fixed_kernel<<<a.n, 512, smem, (cudaStream_t)stream>>>(a);
+  return (int)cudaGetLastError();
+}
+
+uint32_t fixed_prep_smem_bytes(int n_pts) { return prep_fixed_smem(n_pts); }
 
 // ------------------------------------------------------------------ K2x
 

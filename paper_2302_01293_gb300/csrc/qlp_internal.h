@@ -146,7 +146,7 @@ struct PrepFixedArgs {
   double noverlap;
   double E[kMaxQ];
   int32_t nb_cap;
-  int32_t pad0;
+  int32_t max_pts;             // most points of a star in the list (shared memory of the prep)
 };
 
 struct FixedArgs {
@@ -243,9 +243,11 @@ int launch_topk(const float* logits, const void* x0, int batch, int len, int k, 
 int launch_prep_cells(const PrepCellsArgs& a, void* stream);
 int launch_cells(const CellArgs& a, int sum_mode, int warps, int blocks, size_t smem, void* stream);
 int launch_prep_fixed(const PrepFixedArgs& a, void* stream);
+int launch_freq_recs(const PrepFixedArgs& a, void* stream);
 int launch_cells_fixed(const FixedArgs& a, int blocks, size_t smem, void* stream);
 // shared memory of the exact cell kernel for a table of ncs cells (incl. sentinel)
 uint32_t fixed_smem_bytes(int ncs);
+uint32_t fixed_prep_smem_bytes(int n_pts);
 int fixed_blocks_per_sm(size_t smem);
 constexpr int kFixedWarps = 32;
 // bytes of shared memory before the histograms of the cell kernel for a star with
