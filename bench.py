@@ -136,11 +136,17 @@ FP32_OPS_PER_EVAL = 16
 CELL_OPS_PER_EDGE = {0: 20, 1: 30}
 CELL_SMEM_BYTES_PER_EDGE = {0: 44, 1: 60}
 #  exact cell path (integer prefix sums), per bin edge: 14 lane operations
-#    (96-bit edge step 3, cell and position 3, comparison and band test 3, two
-#    64-bit accumulations of base + local 5) and 28 shared-memory bytes gathered
-#    (dt 4, local prefix 8, group base 16); no histogram traffic.
+#    (edge position in 24.40 fixed point 3, cell and offset 2, comparison and
+#    guard-band test 3, next-cell select 1, two 64-bit accumulations of group
+#    base + local prefix 5) and 28 shared-memory bytes gathered (dt 4, local
+#    prefix 8, group base 16); per box start bin of the sweep: 76 lane operations
+#    (running sums over 11 bins 22, then per width of 3..11 bins the score and
+#    the division-free comparison 6) and 88 shared-memory bytes (11 histogram
+#    records of 8 bytes).
 EXACT_OPS_PER_EDGE = 14
 EXACT_SMEM_BYTES_PER_EDGE = 28
+EXACT_OPS_PER_BIN = 76
+EXACT_SMEM_BYTES_PER_BIN = 88
 FP32_LANES_PER_SM = 128
 SMEM_BYTES_PER_CLK_PER_SM = 128
 N_SMS = 152
@@ -428,12 +434,14 @@ def main():
     peak_smem = N_SMS * SMEM_BYTES_PER_CLK_PER_SM * sm_clock / 1e9  # GB/s
     cells_dominant = plan.work_cells >= plan.work_points
     if kernel_id == 2:
-        ops = plan.exact_edges * EXACT_OPS_PER_EDGE
+        ops = plan.exact_edges * EXACT_OPS_PER_EDGE + plan.exact_bins * EXACT_OPS_PER_BIN
         achieved = ops / (ms_kernel * 1e-3) / 1e12
-        smem_gbs = plan.exact_edges * EXACT_SMEM_BYTES_PER_EDGE / (ms_kernel * 1e-3) / 1e9
+        smem_gbs = (plan.exact_edges * EXACT_SMEM_BYTES_PER_EDGE
+                    + plan.exact_bins * EXACT_SMEM_BYTES_PER_BIN) / (ms_kernel * 1e-3) / 1e9
         kernel = "cells_fixed_kernel (exact cell path; CUDA events around the launch inside the graph)"
         unit_note = (f"{plan.exact_edges:.4e} bin edges x {EXACT_OPS_PER_EDGE} lane ops "
-                     f"({EXACT_SMEM_BYTES_PER_EDGE} shared bytes) per launch")
+                     f"({EXACT_SMEM_BYTES_PER_EDGE} shared bytes) + {plan.exact_bins:.4e} box start "
+                     f"bins x {EXACT_OPS_PER_BIN} ({EXACT_SMEM_BYTES_PER_BIN} bytes) per launch")
     elif cells_dominant:
         ops = plan.edges * CELL_OPS_PER_EDGE[params.sum_mode]
         achieved = ops / (ms_search * 1e-3) / 1e12
@@ -445,11 +453,15 @@ def main():
         smem_gbs = None
         kernel = "bls_kernel (search-call duration: includes prep)"
         unit_note = f"{plan.work:.4e} point-freq x {FP32_OPS_PER_EVAL} ops"
-    # DRAM traffic of one cells_kernel launch: ncu capture of the same kernel on
-    # 1,024 stars of this workload (423.0 MB), scaled by points to the default batch
+    # DRAM traffic of one launch of the timed kernel: ncu capture of the same kernel on
+    # 1,024 stars of this workload, scaled by points to the default batch
     traffic = None
     if cells_dominant and kernel_id == 1 and args.stars == 4096 and args.seed == 2 and params.sum_mode == 1:
         traffic = 423.0e6 * plan.n_points / 10638874
+    if kernel_id == 2 and args.stars == 4096 and args.seed == 2:
+        # cells_fixed_kernel: ncu capture on 1,024 stars of this workload (504.1 MB read +
+        # 83.0 MB written), scaled by points (tables, records and outputs grow with them)
+        traffic = 587.1e6 * plan.n_points / 10638874
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "TFLOP/s",
                 "frac": achieved / peak_ops, "traffic": traffic, "kernel": kernel,
                 "algorithmic": unit_note,

@@ -195,9 +195,22 @@ int qlp_bls_plan_stats(const qlp_bls_plan_t* plan, double* work_points, double* 
  * exactly). Any output may be NULL.
  *  n_exact_stars  stars searched by the exact cell kernel (counted in n_cell_stars too).
  *  exact_edges    bin edges those stars evaluate (counted in edges too).
+ *  exact_bins     sum of nbins over those stars' trial frequencies (box start positions
+ *                 the sweep scores).
  * Returns QLP_ERR_ARG for a NULL plan.
  */
-int qlp_bls_plan_exact_stats(const qlp_bls_plan_t* plan, int32_t* n_exact_stars, double* exact_edges);
+int qlp_bls_plan_exact_stats(const qlp_bls_plan_t* plan, int32_t* n_exact_stars, double* exact_edges,
+                             double* exact_bins);
+
+/*
+ * qlp_bls_plan_times -- measurement aid (no counterpart in the paper): wall-clock
+ * seconds the plan's construction spent in four phases, written to seconds4[0..3]:
+ * the host grid and per-star plans (Sec. 2.1 rules, all stars in parallel), the
+ * host staging of flat arrays and work items, device allocation, and the uploads
+ * with the plan-time kernels up to the final stream synchronisation.
+ * QLP_ERR_ARG for a NULL plan or array.
+ */
+int qlp_bls_plan_times(const qlp_bls_plan_t* plan, double* seconds4);
 
 /*
  * qlp_bls_kernel_timing -- measurement aid (no counterpart in the paper): with

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -91,6 +92,8 @@ struct qlp_bls_plan {
   int32_t n_fixed_stars = 0;
   int32_t fixed_max_pts = 0;
   double edges_fixed = 0.0;
+  double bins_fixed = 0.0;       // sum of nbins over the exact path's frequencies
+  double times[4] = {};          // seconds: host grid, host staging, device allocation, upload
   // device
   StarDev* d_stars = nullptr;
   double2* d_fq = nullptr;
@@ -287,11 +290,15 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
     if (offsets[n_stars] > 0 && (!t || !y || !dy)) return QLP_ERR_ARG;
   }
 
+  using clk = std::chrono::steady_clock;
+  const auto c0 = clk::now();
   std::vector<StarPlanHost> sp;
   plan_all(p, n_stars, offsets, t, y, dy, rho, &sp, win_off, win_lo, win_hi);
+  const auto c1 = clk::now();
 
   qlp_bls_plan_t* pl = new (std::nothrow) qlp_bls_plan_t();
   if (!pl) return QLP_ERR_NOMEM;
+  pl->times[0] = std::chrono::duration<double>(c1 - c0).count();
   pl->p = p;
   pl->n_stars = n_stars;
   pl->nq = n_q_of(p);
@@ -418,6 +425,7 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
         pl->fixed_max_pts = std::max(pl->fixed_max_pts, d.n_pts);
         fixed_ncs = std::max<int64_t>(fixed_ncs, h.n_cells + 1);
         pl->edges_fixed += h.cells_work;
+        for (const int32_t nbk : h.nbins) pl->bins_fixed += (double)nbk;
       } else {
         cells_cap = std::max<int64_t>(cells_cap, h.n_cells + 1);
         nb_c = std::max(nb_c, h.nbins_max);
@@ -547,6 +555,8 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   pl->f_items = make_items(kMethodFixed, kFixedWarps, pl->f_blocks, &sorted);
 
   // device buffers
+  const auto c2 = clk::now();
+  pl->times[1] = std::chrono::duration<double>(c2 - c1).count();
   cudaStream_t st = (cudaStream_t)stream;
   if ((rc = dev_alloc(&pl->d_stars, (size_t)n_stars)) || (rc = dev_alloc(&pl->d_fq, nf_alloc)) ||
       (rc = dev_alloc(&pl->d_items, sorted.size())) || (rc = dev_alloc(&pl->d_tp, npt_alloc)) ||
@@ -565,6 +575,8 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
     free_plan(pl);
     return rc;
   }
+  const auto c3 = clk::now();
+  pl->times[2] = std::chrono::duration<double>(c3 - c2).count();
   cudaError_t e = cudaSuccess;
   if (n_stars > 0) e = cudaMemcpyAsync(pl->d_stars, stars.data(), sizeof(StarDev) * (size_t)n_stars, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && nf > 0) e = cudaMemcpyAsync(pl->d_fq, fq.get(), sizeof(double2) * (size_t)nf, cudaMemcpyHostToDevice, st);
@@ -584,6 +596,7 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
     free_plan(pl);
     return cuda_fail(e, "plan upload");
   }
+  pl->times[3] = std::chrono::duration<double>(clk::now() - c3).count();
   *out_plan = pl;
   return QLP_OK;
 }
@@ -648,10 +661,18 @@ int qlp_bls_kernel_time(qlp_bls_plan_t* pl, float* ms, int32_t* kernel) {
   return QLP_OK;
 }
 
-int qlp_bls_plan_exact_stats(const qlp_bls_plan_t* pl, int32_t* n_exact_stars, double* exact_edges) {
+int qlp_bls_plan_times(const qlp_bls_plan_t* pl, double* seconds4) {
+  if (!pl || !seconds4) return QLP_ERR_ARG;
+  for (int i = 0; i < 4; ++i) seconds4[i] = pl->times[i];
+  return QLP_OK;
+}
+
+int qlp_bls_plan_exact_stats(const qlp_bls_plan_t* pl, int32_t* n_exact_stars, double* exact_edges,
+                             double* exact_bins) {
   if (!pl) return QLP_ERR_ARG;
   if (n_exact_stars) *n_exact_stars = pl->n_fixed_stars;
   if (exact_edges) *exact_edges = pl->edges_fixed;
+  if (exact_bins) *exact_bins = pl->bins_fixed;
   return QLP_OK;
 }
 
@@ -850,40 +871,92 @@ int qlp_bls_run_host(const qlp_bls_params* p, int32_t n_stars, const int64_t* of
                      float* sr_host, float* snr_host, int64_t sr_capacity, qlp_bls_best* best_host,
                      int64_t* n_freq_total_out) {
   if (!best_host && n_stars > 0) return QLP_ERR_ARG;
-  cudaStream_t st = nullptr;
-  QLP_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-  qlp_bls_plan_t* pl = nullptr;
-  int rc = qlp_bls_plan(p, n_stars, offsets, t, y, dy, rho, rstar, st, &pl);
-  if (rc) { cudaStreamDestroy(st); return rc; }
-  const int64_t nf = pl->f_off.back();
-  if (n_freq_total_out) *n_freq_total_out = nf;
-  float *d_sr = nullptr, *d_snr = nullptr, *d_s = nullptr, *d_r = nullptr;
-  uint8_t* d_q = nullptr;
-  uint32_t* d_k = nullptr;
-  qlp_bls_best* d_best = nullptr;
-  if ((rc = dev_alloc(&d_sr, (size_t)nf)) || (rc = dev_alloc(&d_snr, (size_t)nf)) ||
-      (rc = dev_alloc(&d_s, (size_t)nf)) || (rc = dev_alloc(&d_r, (size_t)nf)) ||
-      (rc = dev_alloc(&d_q, (size_t)nf)) || (rc = dev_alloc(&d_k, (size_t)nf)) ||
-      (rc = dev_alloc(&d_best, (size_t)std::max(n_stars, 1)))) {
-    // fall through to cleanup
-  } else if ((rc = qlp_bls_search(pl, st, d_sr, d_q, d_k, d_s, d_r)) == QLP_OK &&
-             (rc = qlp_bls_snr(pl, st, d_sr, d_q, d_k, d_s, d_r, d_snr, d_best)) == QLP_OK) {
-    cudaError_t e = cudaSuccess;
-    if (n_stars > 0) e = cudaMemcpyAsync(best_host, d_best, sizeof(qlp_bls_best) * (size_t)n_stars, cudaMemcpyDeviceToHost, st);
-    const bool fits = nf <= sr_capacity;
-    if (e == cudaSuccess && sr_host && fits && nf > 0) e = cudaMemcpyAsync(sr_host, d_sr, sizeof(float) * (size_t)nf, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && snr_host && fits && nf > 0) e = cudaMemcpyAsync(snr_host, d_snr, sizeof(float) * (size_t)nf, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) rc = cuda_fail(e, "result download");
-    else {
-      int32_t flags = 0;
-      rc = qlp_bls_device_status(pl, st, &flags);
-      if (rc == QLP_OK && (sr_host || snr_host) && !fits) rc = QLP_ERR_ARG;
-    }
+  if (n_stars < 0 || (n_stars > 0 && !offsets)) return QLP_ERR_ARG;
+  // The batch runs in chunks of whole stars with about equal numbers of points:
+  // the host plans chunk k + 1 (the grid and tables, on all cores) while the
+  // device searches chunk k. Uploads and the plan's own synchronisation use one
+  // stream, the searches another; results come back after the last launch.
+  const int64_t npts = n_stars > 0 ? offsets[n_stars] - offsets[0] : 0;
+  const int nch = std::max(1, std::min(8, n_stars / 512));
+  struct Chunk {
+    qlp_bls_plan_t* pl = nullptr;
+    int32_t s0 = 0, ns = 0;
+    int64_t nf = 0;
+    float *sr = nullptr, *snr = nullptr, *s = nullptr, *r = nullptr;
+    uint8_t* q = nullptr;
+    uint32_t* k = nullptr;
+    qlp_bls_best* best = nullptr;
+  };
+  std::vector<Chunk> ch;
+  cudaStream_t st_up = nullptr, st_run = nullptr;
+  QLP_CK(cudaStreamCreateWithFlags(&st_up, cudaStreamNonBlocking));
+  cudaError_t ce = cudaStreamCreateWithFlags(&st_run, cudaStreamNonBlocking);
+  if (ce != cudaSuccess) {
+    cudaStreamDestroy(st_up);
+    return cuda_fail(ce, "cudaStreamCreate");
   }
-  cudaFree(d_sr); cudaFree(d_snr); cudaFree(d_s); cudaFree(d_r); cudaFree(d_q); cudaFree(d_k); cudaFree(d_best);
-  qlp_bls_plan_destroy(pl);
-  cudaStreamDestroy(st);
+  int rc = QLP_OK;
+  int32_t s0 = 0;
+  for (int c = 0; c < nch && rc == QLP_OK && (s0 < n_stars || (c == 0 && n_stars == 0)); ++c) {
+    int32_t s1 = n_stars;
+    if (c < nch - 1) {
+      const int64_t goal = offsets[0] + npts * (c + 1) / nch;
+      s1 = s0;
+      while (s1 < n_stars && offsets[s1] < goal) ++s1;
+      s1 = std::max(s1, std::min(n_stars, s0 + 1));
+    }
+    Chunk k;
+    k.s0 = s0;
+    k.ns = s1 - s0;
+    std::vector<int64_t> off((size_t)k.ns + 1);
+    for (int32_t i = 0; i <= k.ns; ++i) off[(size_t)i] = n_stars > 0 ? offsets[s0 + i] - offsets[s0] : 0;
+    const int64_t o0 = n_stars > 0 ? offsets[s0] : 0;
+    rc = qlp_bls_plan(p, k.ns, off.data(), t ? t + o0 : nullptr, y ? y + o0 : nullptr, dy ? dy + o0 : nullptr,
+                      rho ? rho + s0 : nullptr, rstar ? rstar + s0 : nullptr, st_up, &k.pl);
+    if (rc) break;
+    k.nf = k.pl->f_off.back();
+    ch.push_back(k);
+    Chunk& b = ch.back();
+    if ((rc = dev_alloc(&b.sr, (size_t)b.nf)) || (rc = dev_alloc(&b.snr, (size_t)b.nf)) ||
+        (rc = dev_alloc(&b.s, (size_t)b.nf)) || (rc = dev_alloc(&b.r, (size_t)b.nf)) ||
+        (rc = dev_alloc(&b.q, (size_t)b.nf)) || (rc = dev_alloc(&b.k, (size_t)b.nf)) ||
+        (rc = dev_alloc(&b.best, (size_t)std::max(b.ns, 1))))
+      break;
+    if ((rc = qlp_bls_search(b.pl, st_run, b.sr, b.q, b.k, b.s, b.r)) != QLP_OK) break;
+    if ((rc = qlp_bls_snr(b.pl, st_run, b.sr, b.q, b.k, b.s, b.r, b.snr, b.best)) != QLP_OK) break;
+    s0 = s1;
+  }
+  int64_t nf_tot = 0;
+  for (const Chunk& k : ch) nf_tot += k.nf;
+  if (n_freq_total_out) *n_freq_total_out = nf_tot;
+  const bool fits = nf_tot <= sr_capacity;
+  if (rc == QLP_OK) {
+    cudaError_t e = cudaStreamSynchronize(st_run);
+    int64_t f0 = 0;
+    for (const Chunk& k : ch) {
+      if (e == cudaSuccess && k.ns > 0)
+        e = cudaMemcpy(best_host + k.s0, k.best, sizeof(qlp_bls_best) * (size_t)k.ns, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess && sr_host && fits && k.nf > 0)
+        e = cudaMemcpy(sr_host + f0, k.sr, sizeof(float) * (size_t)k.nf, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess && snr_host && fits && k.nf > 0)
+        e = cudaMemcpy(snr_host + f0, k.snr, sizeof(float) * (size_t)k.nf, cudaMemcpyDeviceToHost);
+      f0 += k.nf;
+    }
+    if (e != cudaSuccess) rc = cuda_fail(e, "result download");
+    for (const Chunk& k : ch) {
+      if (rc != QLP_OK) break;
+      int32_t flags = 0;
+      rc = qlp_bls_device_status(k.pl, st_run, &flags);
+    }
+    if (rc == QLP_OK && (sr_host || snr_host) && !fits) rc = QLP_ERR_ARG;
+  }
+  cudaStreamSynchronize(st_run);
+  for (Chunk& k : ch) {
+    cudaFree(k.sr); cudaFree(k.snr); cudaFree(k.s); cudaFree(k.r); cudaFree(k.q); cudaFree(k.k); cudaFree(k.best);
+    qlp_bls_plan_destroy(k.pl);
+  }
+  cudaStreamDestroy(st_up);
+  cudaStreamDestroy(st_run);
   return rc;
 }
 

@@ -108,7 +108,9 @@ void plan_one(const qlp_bls_params& p, const double* t, const double* y, const d
   s.pmin = pmin_of(s.rho_kg, p);
   s.pmax = pmax_of(s.tp.data(), m, p);
   if (!(s.baseline > 0.0) || !(s.pmin < s.pmax)) { s.status = QLP_STAR_EMPTY_GRID; return; }
-  auto add = [&](double f) {
+  // the bin edges across the baseline and the longest bin duration (cell path)
+  double edges = 0.0, dmax = 0.0;
+  auto add = [&](double f) {  // returns q_min(f)
     const double q = q_min_of(f, s.rho_kg, p);
     s.freqs.push_back(f);
     s.qmins.push_back(q);
@@ -116,7 +118,11 @@ void plan_one(const qlp_bls_params& p, const double* t, const double* y, const d
     s.nbins.push_back(nb);
     s.nbins_max = std::max(s.nbins_max, nb);
     s.nbins_min = s.nbins.size() == 1 ? nb : std::min(s.nbins_min, nb);
-    s.ymax = std::max(s.ymax, s.baseline * f * (double)nb);
+    const double y = s.baseline * f * (double)nb;
+    s.ymax = std::max(s.ymax, y);
+    edges += std::floor(y) + 3.0;
+    dmax = std::max(dmax, 1.0 / (f * (double)nb));
+    return q;
   };
   if (p.grid_mode == 1) {
     // coarse log-period grid, increasing frequency = decreasing bin index
@@ -146,19 +152,13 @@ void plan_one(const qlp_bls_params& p, const double* t, const double* y, const d
     for (const auto& iv : merged) {
       double f = std::max(iv.first, fmin);
       const double end = std::min(iv.second, fmax);
-      while (f <= end) {
-        add(f);
-        f = f + q_min_of(f, s.rho_kg, p) / denom;
-      }
+      while (f <= end) f = f + add(f) / denom;
     }
   } else {
     const double fmax = 1.0 / s.pmin;
     const double denom = p.samples_per_peak * s.baseline;
     double f = 1.0 / s.pmax;
-    while (f <= fmax) {
-      add(f);
-      f = f + q_min_of(f, s.rho_kg, p) / denom;
-    }
+    while (f <= fmax) f = f + add(f) / denom;
   }
   if (s.freqs.empty()) { s.status = QLP_STAR_EMPTY_GRID; return; }
   if (s.nbins_max > p.nbins_cap) {
@@ -186,13 +186,7 @@ void plan_one(const qlp_bls_params& p, const double* t, const double* y, const d
       s.cells_ok = true;
       s.cell_h = h;
       s.n_cells = prev + 1;
-      double work = 0.0, dmax = 0.0;
-      for (size_t k = 0; k < s.freqs.size(); ++k) {
-        const double nb = (double)s.nbins[k];
-        work += std::floor(s.baseline * s.freqs[k] * nb) + 3.0;
-        dmax = std::max(dmax, 1.0 / (s.freqs[k] * nb));
-      }
-      s.cells_work = work;
+      s.cells_work = edges;
       s.bin_dmax = dmax;
     }
   }

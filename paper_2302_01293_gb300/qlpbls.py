@@ -119,8 +119,10 @@ def lib():
             L.qlp_bls_plan_info.restype = ctypes.c_int
             L.qlp_bls_plan_stats.argtypes = [_vp, _P(_d), _P(_d), _P(_d), _P(_i32), _P(_i32)]
             L.qlp_bls_plan_stats.restype = ctypes.c_int
-            L.qlp_bls_plan_exact_stats.argtypes = [_vp, _P(_i32), _P(_d)]
+            L.qlp_bls_plan_exact_stats.argtypes = [_vp, _P(_i32), _P(_d), _P(_d)]
             L.qlp_bls_plan_exact_stats.restype = ctypes.c_int
+            L.qlp_bls_plan_times.argtypes = [_vp, _P(_d)]
+            L.qlp_bls_plan_times.restype = ctypes.c_int
             L.qlp_bls_kernel_timing.argtypes = [_vp, _i32]
             L.qlp_bls_kernel_timing.restype = ctypes.c_int
             L.qlp_bls_kernel_time.argtypes = [_vp, _P(ctypes.c_float), _P(_i32)]
@@ -288,11 +290,12 @@ class Plan:
         self.work_points, self.work_cells, self.edges = wp.value, wc.value, ed.value
         self.n_cell_stars = int(nc.value)
         self.n_windowed = int(nw.value)
-        ne, ee = _i32(), _d()
-        _check(L.qlp_bls_plan_exact_stats(self._h, ctypes.byref(ne), ctypes.byref(ee)),
+        ne, ee, eb = _i32(), _d(), _d()
+        _check(L.qlp_bls_plan_exact_stats(self._h, ctypes.byref(ne), ctypes.byref(ee), ctypes.byref(eb)),
                "qlp_bls_plan_exact_stats")
         self.n_exact_stars = int(ne.value)
         self.exact_edges = ee.value
+        self.exact_bins = eb.value
 
     def alloc_outputs(self):
         import torch
@@ -366,6 +369,13 @@ class Plan:
 
     def graph_launch(self, parts: int = 3, stream=None):
         _check(lib().qlp_bls_graph_launch(self._h, int(parts), _stream_ptr(stream)), "qlp_bls_graph_launch")
+
+    def plan_times(self):
+        """qlp_bls_plan_times: seconds of the plan's construction phases (host grid,
+        host staging, device allocation, upload and plan-time kernels)."""
+        v = (ctypes.c_double * 4)()
+        _check(lib().qlp_bls_plan_times(self._h, v), "qlp_bls_plan_times")
+        return dict(host_grid=v[0], host_staging=v[1], device_alloc=v[2], upload=v[3])
 
     def kernel_timing(self, enable: bool = True):
         """qlp_bls_kernel_timing: bracket the main search kernel of every later

@@ -164,6 +164,20 @@ def test_run_host_matches_device_path(gpu_lib):
     assert np.array_equal(h["best"]["f_idx"], g["best"]["f_idx"])
 
 
+def test_run_host_in_chunks_equals_one_plan(gpu_lib):
+    # 1,100 stars: the host-buffer call plans and searches them in two chunks
+    # (planning of the second overlaps the search of the first); the exact path is
+    # deterministic, so every spectrum value equals the single plan's bit for bit
+    b = synth.uneven_single_sector(n_stars=1100, seed=29)
+    g = run_gpu(b, qlpbls.Params())
+    n = g["plan"].n_freq_total
+    h = qlpbls.run_host(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar, qlpbls.Params(), sr_capacity=n)
+    assert h["n_freq_total"] == n and g["plan"].n_exact_stars == 1100
+    assert np.array_equal(h["sr"], g["sr"][:n])
+    assert np.array_equal(h["snr"], g["snr"][:n])
+    assert np.array_equal(h["best"], g["best"])
+
+
 def test_full_batch_sampled(gpu_lib):
     # the 4,096-star uneven single-sector batch in the default launch shape;
     # 12 sampled stars checked in full against the oracle
