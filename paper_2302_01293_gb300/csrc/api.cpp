@@ -91,6 +91,8 @@ struct qlp_bls_plan {
   int32_t f_items = 0;
   int32_t n_fixed_stars = 0;
   int32_t fixed_max_pts = 0;
+  bool fixed_windowed = false;    // some exact-path star is searched in time windows
+  longlong2* d_ws = nullptr;      // their bin-sum workspace, kFixedWsBlock entries per block
   double edges_fixed = 0.0;
   double bins_fixed = 0.0;       // sum of nbins over the exact path's frequencies
   double times[4] = {};          // seconds: host grid, host staging, device allocation, upload
@@ -149,6 +151,7 @@ static void free_plan(qlp_bls_plan_t* pl) {
   cudaFree(pl->d_fixed_stars);
   cudaFree(pl->d_fx);
   cudaFree(pl->d_frec);
+  cudaFree(pl->d_ws);
   cudaFree(pl->d_wrec);
   cudaFree(pl->d_ctl);
   delete pl;
@@ -354,17 +357,31 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
     }
     const bool old_fits = cell_smem(W.cap, h.nbins_max) <= (size_t)budget;
     const double pp_work = (double)h.freqs.size() * (double)round32((int64_t)h.tp.size());
-    // exact path: the whole table and the warps' rings in shared memory, at least 32 bins,
-    // at most 2^14 cycles and 2^21 points (the integer prefix sums stay below 2^62)
-    const bool fixed_ok = p.sum_mode == QLP_SUM_FIXED && p.bin_mode == QLP_BIN_SHARED &&
-                          (p.cell_window == 0 || p.cell_window >= h.n_cells) &&
-                          (size_t)fixed_smem_bytes((int)h.n_cells + 1) <= (size_t)budget && h.nbins_min >= 32 &&
+    // exact path: at least 32 bins, at most 2^14 cycles and 2^21 points (the integer
+    // prefix sums stay below 2^62); the whole table and the warps' rings in shared
+    // memory, or else windows of the table (bin sums through a global workspace)
+    const bool fixed_ok = p.sum_mode == QLP_SUM_FIXED && p.bin_mode == QLP_BIN_SHARED && h.nbins_min >= 32 &&
                           h.baseline * h.freqs.back() <= 16384.0 && h.tp.size() <= ((size_t)1 << 21) &&
-                          (size_t)fixed_prep_smem_bytes((int)h.tp.size()) <= (size_t)budget;
+                          (size_t)32 * 16 * ((h.nbins_max + 31) / 32) <= (size_t)kFixedWsBlock * 16;
     if (fixed_ok && (p.method == 2 || h.cells_work < 2.0 * pp_work)) {
-      method[(size_t)s] = kMethodFixed;
-      W = CellWin{1, (int32_t)h.n_cells, (int32_t)ovl, (int32_t)h.n_cells + 1};
-      continue;
+      const bool fwhole = p.cell_window > 0 ? p.cell_window >= h.n_cells
+                                            : (size_t)fixed_smem_bytes((int)h.n_cells + 1) <= (size_t)budget;
+      CellWin F{1, (int32_t)h.n_cells, (int32_t)ovl, (int32_t)h.n_cells + 1};
+      if (!fwhole) {
+        int64_t c = p.cell_window;
+        if (c <= 0) {  // the largest multiple of 32 whose staged window fits
+          c = 32;
+          while (fixed_smem_bytes((int)(c + 32 + F.ovl + 34)) <= (size_t)budget) c += 32;
+        }
+        F.cells = (int32_t)c;
+        F.cap = (int32_t)std::min<int64_t>(h.n_cells + 1, c + F.ovl + 33);
+        F.n_win = (int32_t)((h.n_cells + c - 1) / c);
+      }
+      if ((size_t)fixed_smem_bytes(F.cap + 1) <= (size_t)budget) {
+        method[(size_t)s] = kMethodFixed;
+        W = F;
+        continue;
+      }
     }
     if (!old_fits) continue;
     if (p.method == 2 || p.bin_mode == QLP_BIN_PER_Q || h.cells_work < pp_work) method[(size_t)s] = kMethodCells;
@@ -423,7 +440,8 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
       if (d.method == kMethodFixed) {
         fixed_stars.push_back(s);
         pl->fixed_max_pts = std::max(pl->fixed_max_pts, d.n_pts);
-        fixed_ncs = std::max<int64_t>(fixed_ncs, h.n_cells + 1);
+        fixed_ncs = std::max<int64_t>(fixed_ncs, d.n_win > 1 ? (int64_t)d.win_cap + 1 : h.n_cells + 1);
+        if (d.n_win > 1) pl->fixed_windowed = true;
         pl->edges_fixed += h.cells_work;
         for (const int32_t nbk : h.nbins) pl->bins_fixed += (double)nbk;
       } else {
@@ -521,11 +539,18 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
       const StarDev& d = stars[(size_t)s];
       if (d.method != meth) continue;
       const StarPlanHost& h = sp[(size_t)s];
-      for (int32_t b = 0; b < d.n_f; b += chunk) {
+      int ck = chunk;
+      int32_t ws_stride = 0;
+      if (meth == kMethodFixed && d.n_win > 1) {  // rows of round32(nbins) bins in the block's workspace
+        ws_stride = (int32_t)round32(h.nbins_max);
+        ck = std::max(1, std::min(ck, (int)(kFixedWsBlock / ws_stride)));
+      }
+      for (int32_t b = 0; b < d.n_f; b += ck) {
         WorkItem wi{};
         wi.star = s;
         wi.f_begin = b;
-        wi.f_count = std::min(chunk, d.n_f - b);
+        wi.f_count = std::min(ck, d.n_f - b);
+        if (meth == kMethodFixed) wi.pad0 = ws_stride;
         if (meth == kMethodCells) {
           int nbm = 1;
           for (int32_t k = b; k < b + wi.f_count; ++k) nbm = std::max(nbm, h.nbins[(size_t)k]);
@@ -571,7 +596,9 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
       (rc = dev_alloc(&pl->d_base, (size_t)std::max<int64_t>(nbase, 1))) ||
       (rc = dev_alloc(&pl->d_fixed_stars, std::max<size_t>(fixed_stars.size(), 1))) ||
       (rc = dev_alloc(&pl->d_fx, (size_t)std::max(n_stars, 1))) ||
-      (rc = dev_alloc(&pl->d_frec, fixed_stars.empty() ? (size_t)1 : nf_alloc)) || (rc = dev_alloc(&pl->d_ctl, 4))) {
+      (rc = dev_alloc(&pl->d_frec, fixed_stars.empty() ? (size_t)1 : nf_alloc)) ||
+      (rc = dev_alloc(&pl->d_ws, pl->fixed_windowed ? (size_t)pl->f_blocks * (size_t)kFixedWsBlock : (size_t)1)) ||
+      (rc = dev_alloc(&pl->d_ctl, 4))) {
     free_plan(pl);
     return rc;
   }
@@ -791,6 +818,8 @@ int qlp_bls_search(qlp_bls_plan_t* pl, void* stream, float* sr, uint8_t* qidx, u
     fa.sbest = s_best;
     fa.rbest = r_best;
     fa.stride4 = 4;
+    fa.ws = pl->d_ws;
+    fa.ws_block = kFixedWsBlock;
     QLP_CK(record_kev(pl, 0, st));
     e = launch_cells_fixed(fa, pl->f_blocks, pl->f_smem, stream);
     if (e) return cuda_fail((cudaError_t)e, "exact cell search launch");

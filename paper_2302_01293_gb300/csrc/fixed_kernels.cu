@@ -87,8 +87,9 @@ __device__ __forceinline__ int fixed_exponent(double vmax) {
 }
 
 // Dynamic shared memory of prep_fixed_kernel for a star of n points: 1/dy^2 (FP64)
-// and the cell of every point.
-__host__ __device__ __forceinline__ uint32_t prep_fixed_smem(int n) { return (uint32_t)n * 12u; }
+// and the cell of every point, cached for stars of at most kPrepCachePts points.
+constexpr int kPrepCachePts = 18000;
+__host__ __device__ __forceinline__ uint32_t prep_fixed_smem(int n) { return (uint32_t)min(n, kPrepCachePts) * 12u; }
 
 __global__ void __launch_bounds__(512) prep_fixed_kernel(const PrepFixedArgs a) {
   extern __shared__ __align__(16) unsigned char psm[];
@@ -104,25 +105,30 @@ __global__ void __launch_bounds__(512) prep_fixed_kernel(const PrepFixedArgs a) 
   const int tid = threadIdx.x;
   const int nc = st.n_cells;
   const double h = st.h;
+  const bool cache = n <= kPrepCachePts;  // block-uniform
   double* s_inv = reinterpret_cast<double*>(psm);
-  int* s_cell = reinterpret_cast<int*>(psm + 8u * (uint32_t)n);
+  int* s_cell = reinterpret_cast<int*>(psm + 8u * (uint32_t)(cache ? n : 0));
+  auto inv_of = [&](int i) { return cache ? s_inv[i] : 1.0 / (dy[i] * dy[i]); };
+  auto cell_at = [&](int i) { return cache ? s_cell[i] : cell_of(tp[i], h); };
 
   // weights w = dy^-2 / sum dy^-2 and the weighted mean (FP64); each point's
-  // inverse variance and cell once
+  // inverse variance and cell once (kept in shared memory when the star fits)
   double acc = 0.0;
   for (int i = tid; i < n; i += blockDim.x) {
     const double inv = 1.0 / (dy[i] * dy[i]);
-    s_inv[i] = inv;
-    s_cell[i] = cell_of(tp[i], h);
+    if (cache) {
+      s_inv[i] = inv;
+      s_cell[i] = cell_of(tp[i], h);
+    }
     acc += inv;
   }
   const double rws = 1.0 / block_sum(acc, red);
   acc = 0.0;
-  for (int i = tid; i < n; i += blockDim.x) acc += s_inv[i] * rws * y[i];
+  for (int i = tid; i < n; i += blockDim.x) acc += inv_of(i) * rws * y[i];
   const double ybar = block_sum(acc, red);
   double mw = 0.0, md = 0.0;
   for (int i = tid; i < n; i += blockDim.x) {
-    const double w = s_inv[i] * rws;
+    const double w = inv_of(i) * rws;
     mw = fmax(mw, w);
     md = fmax(md, fabs(w * (y[i] - ybar)));
   }
@@ -137,7 +143,7 @@ __global__ void __launch_bounds__(512) prep_fixed_kernel(const PrepFixedArgs a) 
   const int i0 = min(n, tid * L), i1 = min(n, i0 + L);
   long long sw = 0, sy = 0;
   for (int i = i0; i < i1; ++i) {
-    const double w = s_inv[i] * rws;
+    const double w = inv_of(i) * rws;
     sw += __double2ll_rn(w * pw);
     sy += __double2ll_rn(w * (y[i] - ybar) * py);
   }
@@ -182,7 +188,7 @@ __global__ void __launch_bounds__(512) prep_fixed_kernel(const PrepFixedArgs a) 
   long long cw = scan_w[tid], cy = scan_y[tid];
   for (int i = i0; i < i1; ++i) {
     a.ipre[st.cpre_off + i] = make_longlong2(cw, cy);
-    const double w = s_inv[i] * rws;
+    const double w = inv_of(i) * rws;
     cw += __double2ll_rn(w * pw);
     cy += __double2ll_rn(w * (y[i] - ybar) * py);
   }
@@ -191,14 +197,14 @@ __global__ void __launch_bounds__(512) prep_fixed_kernel(const PrepFixedArgs a) 
   // first point at or after each cell start: point i fills cells (cell(i-1), cell(i)]
   int32_t* first = a.gidx + st.cell_off;
   for (int i = tid; i <= n; i += blockDim.x) {
-    const int up = (i == 0) ? -1 : s_cell[i - 1];
-    const int ui = (i == n) ? nc : s_cell[i];
+    const int up = (i == 0) ? -1 : cell_at(i - 1);
+    const int ui = (i == n) ? nc : cell_at(i);
     for (int c = up + 1; c <= ui && c <= nc; ++c) first[c] = i;
   }
   __syncthreads();
   for (int u = tid; u <= nc; u += blockDim.x) {
     const int f = first[u];
-    const bool in_cell = (u < nc) && (f < n) && (s_cell[f] == u);
+    const bool in_cell = (u < nc) && (f < n) && (cell_at(f) == u);
     uint32_t q = 0xffffffffu;  // the cell's point as a 32-bit fraction of the cell, empty = all ones
     if (in_cell) {
       const double fr = __ddiv_rn(__dsub_rn(tp[f], __dmul_rn((double)u, h)), h);
@@ -312,6 +318,337 @@ __device__ __forceinline__ void sweep_start(const float2* rb, bool kin, int k, i
   }
 }
 
+// One trial frequency on a warp: the bin sums S (from the staged table's edges, or
+// from the window passes' workspace row when WS), then per block of 32 bins U, the
+// FP32 histogram records in the ring and the sweep, the warp argmax and the store.
+template <bool WS>
+__device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, const FreqRec& R,
+                                              const FixedStar& fx, const unsigned char* smem,
+                                              uint32_t loc_off, uint32_t base_off, int nc, float2* ring,
+                                              int lane, float scw, float scy, const double* tp,
+                                              const int32_t* gidx, uint32_t st4, uint32_t st8, uint32_t st16,
+                                              const longlong2* wsrow) {
+  const int nb = R.nb;
+  const double f = a.fq[fidx].x;  // for the exact decision near ties
+  const uint32_t band_q = R.band_q;
+  const uint32_t wmask = R.wmask;
+  const unsigned long long jlow = R.jlow;
+  const int mmax = 32 - __clz(wmask);
+  const bool all_widths = wmask == 0x7fcu;  // exactly 3 .. 11 bins
+  const int gq = (int)(R.gq_bstar >> 13), bstar = (int)(R.gq_bstar & 8191u);
+  const int g_end = gq * nb + bstar;
+  const uint32_t k_lo = (uint32_t)R.K, k_hi = (uint32_t)(R.K >> 32);
+  const int nblk = (nb + 31) >> 5;
+
+  long long h0w = 0, h0y = 0;  // U of bins 0..31 (the wrap-around values)
+  long long pw = 0, py = 0;    // U of the previous block
+  float bsv = 0.f, brv = 0.f;  // best box of this lane: s, r and its key
+  int bkey = 0x7fffffff;
+  // block i: U of bins 32 i + lane; then the histogram of block i - 1 and the
+  // sweep of block i - 2 (boxes of up to 15 bins starting in it)
+  for (int i = 0; i <= nblk + 1; ++i) {
+    const int x = (i << 5) + lane;
+    long long uw = 0, uy = 0;
+    if constexpr (WS) {  // bin sums from the window passes
+      if ((i << 5) < nb) {
+        if (x < nb) {
+          const longlong2 sv = wsrow[x];
+          uw = sv.x + (bstar < x ? fx.w_tot : 0);
+          uy = sv.y + (bstar < x ? fx.y_tot : 0);
+        }
+      }
+    } else {
+      if ((i << 5) < nb) {  // warp-uniform: lanes x < nb own bin x
+        // edges G = G0, G0 + nb, ... <= g_end (one per cycle). The edge at t' = 0
+        // (G = 0) is skipped: no point lies before it. A block of r <= 16 bins spreads
+        // each bin's cycles over P = 32 / r lanes (phase ph: cycles ph, ph + P, ...),
+        // summed by shuffles afterwards. Idle lanes walk a real bin's edges
+        // (discarded), so that every edge stays inside the staged table.
+        const int r = nb - (i << 5);
+        const bool split = r <= 16;
+        int P = 1, ph = 0, xb = x;
+        if (split) {
+          P = 32 / r;
+          ph = lane / r;
+          xb = (i << 5) + (lane - ph * r);
+        }
+        const bool idle = split ? ph >= P : x >= nb;
+        const int G0 = idle ? (i << 5) : (xb == 0 ? nb : xb + ph * nb);
+        const int gstep = P * nb;
+        long long aw = 0, ay = 0;
+        bool near = false;  // an edge within the guard band of its cell's point
+        // every lane takes cnt edges; only in the last one may a lane be past g_end
+        const int cnt = (gq + ((i << 5) > bstar ? 0 : 1) + P - 1) / P;
+        auto edge = [&](int G, bool valid, bool clamp) {
+          // tau_G / h in 24.40 fixed point: cell u and position fr (2^-32 of a cell)
+          const unsigned long long X =
+              (unsigned long long)(uint32_t)G * k_lo + ((unsigned long long)((uint32_t)G * k_hi) << 32);
+          int u = (int)((uint32_t)(X >> 32) >> 8);
+          if (clamp) u = min(u, nc);
+          const uint32_t fr = (uint32_t)(X >> 8);
+          const uint32_t dq = *reinterpret_cast<const uint32_t*>(smem + (uint32_t)u * st4);
+          near = near || (uint32_t)(dq - fr + band_q) <= 2u * band_q;
+          const int v = u + (dq < fr ? 1 : 0);  // past the cell's point if it lies before tau_G
+          const int2 lc = *reinterpret_cast<const int2*>(smem + loc_off + (uint32_t)v * st8);
+          const longlong2 bs = *reinterpret_cast<const longlong2*>(smem + base_off + (uint32_t)(v >> 5) * st16);
+          if (valid) {
+            aw += bs.x + (long long)lc.x;
+            ay += bs.y + (long long)lc.y;
+          }
+        };
+        int c = 0;
+        for (; c + 2 < cnt; c += 2) {
+          edge(G0 + c * gstep, true, false);
+          edge(G0 + (c + 1) * gstep, true, false);
+        }
+        if (c + 1 < cnt) edge(G0 + c * gstep, true, false);
+        edge(G0 + (cnt - 1) * gstep, G0 + (cnt - 1) * gstep <= g_end, true);
+        if (split) {  // warp-uniform: add the other phases of each bin into lanes 0 .. r-1
+          for (int q = 1; q < P; ++q) {
+            const long long ow = __shfl_down_sync(0xffffffffu, aw, q * r);
+            const long long oy = __shfl_down_sync(0xffffffffu, ay, q * r);
+            const bool on = __shfl_down_sync(0xffffffffu, near ? 1 : 0, q * r) != 0;
+            if (lane < r) {
+              aw += ow;
+              ay += oy;
+              near = near || on;
+            }
+          }
+        }
+        // lanes past the last bin accumulated nothing meaningful
+        if (x >= nb) {
+          aw = 0;
+          ay = 0;
+          near = false;
+        }
+        if (__any_sync(0xffffffffu, near)) {  // rare: redo the bin, near-ties by the exact FP64 fold
+          if (near) {
+            aw = 0;
+            ay = 0;
+            for (int g = x == 0 ? nb : x; g <= g_end; g += nb) {
+              const unsigned long long X =
+                  (unsigned long long)(uint32_t)g * k_lo + ((unsigned long long)((uint32_t)g * k_hi) << 32);
+              const int u = min((int)((uint32_t)(X >> 32) >> 8), nc);
+              const uint32_t fr = (uint32_t)(X >> 8);
+              const uint32_t dq = reinterpret_cast<const uint32_t*>(smem)[u];
+              int sel = dq < fr ? 1 : 0;
+              if (dq != 0xffffffffu && (uint32_t)(dq - fr + band_q) <= 2u * band_q)
+                sel = exact_before(tp, gidx[u], f, nb, g);
+              const int v = u + sel;
+              const int2 lc = reinterpret_cast<const int2*>(smem + loc_off)[v];
+              const longlong2 bs = reinterpret_cast<const longlong2*>(smem + base_off)[v >> 5];
+              aw += bs.x + (long long)lc.x;
+              ay += bs.y + (long long)lc.y;
+            }
+          }
+        }
+        if (bstar < x) {
+          aw += fx.w_tot;
+          ay += fx.y_tot;
+        }
+        uw = aw;
+        uy = ay;
+      }
+    }
+    if ((i << 5) + 31 >= nb) {  // warp-uniform: lanes x >= nb take U[x - nb] + total
+      const int src = (x - nb) & 31;  // x - nb < 32 for every value the sweep uses
+      const long long ow = __shfl_sync(0xffffffffu, h0w, src);
+      const long long oy = __shfl_sync(0xffffffffu, h0y, src);
+      if (x >= nb) {
+        uw = ow + fx.w_tot;
+        uy = oy + fx.y_tot;
+      }
+    }
+    if (i == 0) {
+      h0w = uw;
+      h0y = uy;
+    } else {
+      // histogram of block i - 1: H[x] = U[x + 1] - U[x], exact, then FP32
+      long long nw = __shfl_down_sync(0xffffffffu, pw, 1);
+      long long ny = __shfl_down_sync(0xffffffffu, py, 1);
+      const long long fw = __shfl_sync(0xffffffffu, uw, 0);
+      const long long fy = __shfl_sync(0xffffffffu, uy, 0);
+      if (lane == 31) {
+        nw = fw;
+        ny = fy;
+      }
+      const float2 hv = make_float2(__fmul_rn(__ll2float_rn(nw - pw), scw), __fmul_rn(__ll2float_rn(ny - py), scy));
+      ring[(((i - 1) & 1) << 5) + lane] = hv;
+      if (!((i - 1) & 1)) ring[64 + lane] = hv;
+    }
+    pw = uw;
+    py = uy;
+    __syncwarp();
+    if (i >= 2) {  // sweep block i - 2: boxes starting at its bins
+      const int k = ((i - 2) << 5) + lane;
+      const float2* rb = ring + (((i - 2) & 1) << 5) + lane;
+      if (all_widths) sweep_start<true>(rb, k < nb, k, mmax, wmask, bsv, brv, bkey);
+      else sweep_start<false>(rb, k < nb, k, mmax, wmask, bsv, brv, bkey);
+    }
+    __syncwarp();
+  }
+  const bool none = bkey == 0x7fffffff;
+  float bs2 = none ? -1.f : __fmul_rn(bsv, bsv);
+  float bd = none ? 1.f : __fmaf_rn(-brv, brv, brv);
+  const int bo = bkey >> 16;
+  int bj = none ? 255 : (int)((jlow >> (4 * bo)) & 15ull);
+  int bk = none ? -1 : (bkey & 0xffff);
+  for (int off = 16; off > 0; off >>= 1) {
+    const float o_s2 = __shfl_xor_sync(0xffffffffu, bs2, off);
+    const float o_d = __shfl_xor_sync(0xffffffffu, bd, off);
+    const float o_s = __shfl_xor_sync(0xffffffffu, bsv, off);
+    const float o_r = __shfl_xor_sync(0xffffffffu, brv, off);
+    const int o_j = __shfl_xor_sync(0xffffffffu, bj, off);
+    const int o_k = __shfl_xor_sync(0xffffffffu, bk, off);
+    if (beats(o_s2, o_d, o_j, o_k, bs2, bd, bj, bk)) {
+      bs2 = o_s2; bd = o_d; bsv = o_s; brv = o_r; bj = o_j; bk = o_k;
+    }
+  }
+  BoxBest bb;
+  bb.s2 = bs2; bb.d = bd; bb.s = bsv; bb.r = brv; bb.j = bj; bb.k = bk;
+  store_box(bb, lane, fidx, a.sr, a.qidx, a.kbin, a.sbest, a.rbest);
+}
+
+// One work item of a star whose table is longer than shared memory. Pass A, window
+// by window (the window's cells staged once for all the item's frequencies): every
+// warp adds, for each of its frequencies and bins, the prefix sums C(tau_G) of the
+// window's edges G (the edges of a window are those in [ceil(w C h F),
+// ceil((w+1) C h F)), the same FP64 expression on both sides of each boundary, so
+// the windows partition them) to the bin's row of this block's workspace. Pass B:
+// each frequency runs the block pipeline from its row.
+template <int NW>
+__device__ void windowed_item(const FixedArgs& a, const WorkItem& wi, const StarDev& st, const FixedStar& fx,
+                              unsigned char* smem, int warp, int lane, uint32_t st4, uint32_t st8, uint32_t st16) {
+  const int nc = st.n_cells;
+  const int cap = st.win_cap + 1;  // staged cells of a window, plus one past its end
+  const uint32_t loc_off = fixed_loc_off(cap), base_off = fixed_base_off(cap);
+  float2* ring = reinterpret_cast<float2*>(smem + fixed_ring_off(cap)) + warp * kRing;
+  const int stride = wi.pad0;      // workspace row length (bins)
+  longlong2* ws = a.ws + (size_t)blockIdx.x * (size_t)a.ws_block;
+  const double h = st.h;
+  const double* tp = a.tp + st.pt_off;
+  const int32_t* gidx = a.gidx + st.cell_off;
+  const uint32_t* s_dt = reinterpret_cast<const uint32_t*>(smem);
+  for (int w = 0; w < st.n_win; ++w) {
+    const int cstart = w * st.win_cells;
+    const int lo = (w == 0) ? 0 : ((cstart - 1) >> 5) << 5;
+    const int hi = (w == st.n_win - 1) ? nc : min(nc, (w + 1) * st.win_cells + st.win_ovl);
+    const int n_loc = hi - lo + 1;
+    __syncthreads();  // the previous window's passes are done
+    {
+      uint32_t* d_dt = reinterpret_cast<uint32_t*>(smem);
+      int2* d_loc = reinterpret_cast<int2*>(smem + loc_off);
+      longlong2* d_base = reinterpret_cast<longlong2*>(smem + base_off);
+      const int2 lnc = a.loc[st.cell_off + nc];
+      for (int i = threadIdx.x; i <= n_loc; i += NW * 32) {  // n_loc + 1 cells
+        const int c = lo + i;
+        d_dt[i] = c <= nc ? a.dt[st.cell_off + c] : 0xffffffffu;
+        d_loc[i] = c <= nc ? a.loc[st.cell_off + c] : ((c >> 5) == (nc >> 5) ? lnc : make_int2(0, 0));
+      }
+      for (int i = threadIdx.x; i < (n_loc + 32) / 32; i += NW * 32) {
+        const int g = (lo >> 5) + i;
+        d_base[i] = g <= (nc >> 5) ? a.base[st.base_off + g] : make_longlong2(fx.w_tot, fx.y_tot);
+      }
+    }
+    __syncthreads();
+    for (int fl = warp; fl < wi.f_count; fl += NW) {
+      const int64_t fidx = st.f_off + wi.f_begin + fl;
+      const FreqRec R = a.frec[fidx];
+      const int nb = R.nb;
+      if (nb == 0) continue;  // reported by pass B
+      const double f = a.fq[fidx].x;
+      const double Fq = __dmul_rn(f, (double)nb);
+      const int gq = (int)(R.gq_bstar >> 13), bstar = (int)(R.gq_bstar & 8191u);
+      const int g_end = gq * nb + bstar;
+      const int gs = (w == 0) ? 0 : (int)ceil(__dmul_rn(__dmul_rn((double)cstart, h), Fq));
+      const int ge = (w == st.n_win - 1) ? g_end + 1
+                                          : (int)ceil(__dmul_rn(__dmul_rn((double)((w + 1) * st.win_cells), h), Fq));
+      const uint32_t k_lo = (uint32_t)R.K, k_hi = (uint32_t)(R.K >> 32);
+      const uint32_t band_q = R.band_q;
+      longlong2* row = ws + (size_t)fl * (size_t)stride;
+      for (int i = 0; (i << 5) < nb; ++i) {
+        const int x = (i << 5) + lane;
+        const bool inb = x < nb;
+        // this bin's edges in [gs, ge): cycles c0 .. c1 (the edge at t' = 0 is skipped)
+        int c0 = gs > x ? (gs - x + nb - 1) / nb : 0;
+        if (x == 0 && c0 == 0) c0 = 1;
+        const int c1 = ge - 1 >= x ? (ge - 1 - x) / nb : -1;
+        const int cntl = inb ? max(0, c1 - c0 + 1) : 0;
+        const int cmax = __reduce_max_sync(0xffffffffu, (unsigned)cntl);
+        long long aw = 0, ay = 0;
+        bool near = false;
+        for (int k = 0; k < cmax; ++k) {
+          const bool valid = k < cntl;
+          const int G = x + (c0 + k) * nb;
+          const unsigned long long X =
+              (unsigned long long)(uint32_t)G * k_lo + ((unsigned long long)((uint32_t)G * k_hi) << 32);
+          const int ul = min(max((int)((uint32_t)(X >> 32) >> 8) - lo, 0), n_loc - 1);  // staged cell
+          const uint32_t fr = (uint32_t)(X >> 8);
+          const uint32_t dq = *reinterpret_cast<const uint32_t*>(smem + (uint32_t)ul * st4);
+          near = near || (valid && (uint32_t)(dq - fr + band_q) <= 2u * band_q);
+          const int v = ul + (dq < fr ? 1 : 0);
+          const int2 lc = *reinterpret_cast<const int2*>(smem + loc_off + (uint32_t)v * st8);
+          const longlong2 bs = *reinterpret_cast<const longlong2*>(smem + base_off + (uint32_t)(v >> 5) * st16);
+          if (valid) {
+            aw += bs.x + (long long)lc.x;
+            ay += bs.y + (long long)lc.y;
+          }
+        }
+        if (__any_sync(0xffffffffu, near)) {  // rare: redo, near-ties by the exact FP64 fold
+          if (near) {
+            aw = 0;
+            ay = 0;
+            for (int c = c0; c <= c1; ++c) {
+              const int G = x + c * nb;
+              const unsigned long long X =
+                  (unsigned long long)(uint32_t)G * k_lo + ((unsigned long long)((uint32_t)G * k_hi) << 32);
+              const int ul = min(max((int)((uint32_t)(X >> 32) >> 8) - lo, 0), n_loc - 1);
+              const uint32_t fr = (uint32_t)(X >> 8);
+              const uint32_t dq = s_dt[ul];
+              int sel = dq < fr ? 1 : 0;
+              if (dq != 0xffffffffu && (uint32_t)(dq - fr + band_q) <= 2u * band_q)
+                sel = exact_before(tp, gidx[lo + ul], f, nb, G);
+              const int v = ul + sel;
+              const int2 lc = reinterpret_cast<const int2*>(smem + loc_off)[v];
+              const longlong2 bs = reinterpret_cast<const longlong2*>(smem + base_off)[v >> 5];
+              aw += bs.x + (long long)lc.x;
+              ay += bs.y + (long long)lc.y;
+            }
+          }
+        }
+        if (inb) {
+          if (w == 0) {
+            row[x] = make_longlong2(aw, ay);
+          } else {
+            const longlong2 o = row[x];
+            row[x] = make_longlong2(o.x + aw, o.y + ay);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();  // every window's sums are in the workspace
+  const float scw = __int_as_float((127 - fx.kw) << 23);
+  const float scy = __int_as_float((127 - fx.ky) << 23);
+  for (int fl = warp; fl < wi.f_count; fl += NW) {
+    const int64_t fidx = st.f_off + wi.f_begin + fl;
+    const FreqRec R = a.frec[fidx];
+    if (R.nb == 0) {
+      if (lane == 0) {
+        atomicOr(a.err, kErrNbins);
+        a.sr[fidx] = 0.f;
+        if (a.qidx) a.qidx[fidx] = 255;
+        if (a.kbin) a.kbin[fidx] = 0xffffffffu;
+        if (a.sbest) a.sbest[fidx] = 0.f;
+        if (a.rbest) a.rbest[fidx] = 0.f;
+      }
+      continue;
+    }
+    run_frequency<true>(a, fidx, R, fx, smem, loc_off, base_off, nc, ring, lane, scw, scy, tp, gidx, st4, st8,
+                        st16, ws + (size_t)fl * (size_t)stride);
+  }
+}
+
 template <int NW>
 __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -336,6 +673,11 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
     const WorkItem wi = a.items[it];
     const StarDev st = a.stars[wi.star];
     const FixedStar fx = a.fx[wi.star];
+    if (st.n_win > 1) {  // block-uniform: a table longer than shared memory
+      windowed_item<NW>(a, wi, st, fx, smem, warp, lane, st4, st8, st16);
+      if (threadIdx.x == 0) s_star = -1;  // shared memory no longer holds a whole table
+      continue;
+    }
     const int nc = st.n_cells;  // sentinel cell index
     const int ncp = nc + 1 + kPadCells;
     const uint32_t loc_off = fixed_loc_off(ncp), base_off = fixed_base_off(ncp);
@@ -379,174 +721,8 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
         }
         continue;
       }
-      const double f = a.fq[fidx].x;  // for the exact decision near ties
-      const uint32_t band_q = R.band_q;
-      const uint32_t wmask = R.wmask;
-      const unsigned long long jlow = R.jlow;
-      const int mmax = 32 - __clz(wmask);
-      const bool all_widths = wmask == 0x7fcu;  // exactly 3 .. 11 bins
-      const int gq = (int)(R.gq_bstar >> 13), bstar = (int)(R.gq_bstar & 8191u);
-      const int g_end = gq * nb + bstar;
-      const uint32_t k_lo = (uint32_t)R.K, k_hi = (uint32_t)(R.K >> 32);
-      const int nblk = (nb + 31) >> 5;
-
-      long long h0w = 0, h0y = 0;  // U of bins 0..31 (the wrap-around values)
-      long long pw = 0, py = 0;    // U of the previous block
-      float bsv = 0.f, brv = 0.f;  // best box of this lane: s, r and its key
-      int bkey = 0x7fffffff;
-      // block i: U of bins 32 i + lane; then the histogram of block i - 1 and the
-      // sweep of block i - 2 (boxes of up to 15 bins starting in it)
-      for (int i = 0; i <= nblk + 1; ++i) {
-        const int x = (i << 5) + lane;
-        long long uw = 0, uy = 0;
-        if ((i << 5) < nb) {  // warp-uniform: lanes x < nb own bin x
-          // edges G = G0, G0 + nb, ... <= g_end (one per cycle). The edge at t' = 0
-          // (G = 0) is skipped: no point lies before it. A block of r <= 16 bins spreads
-          // each bin's cycles over P = 32 / r lanes (phase ph: cycles ph, ph + P, ...),
-          // summed by shuffles afterwards. Idle lanes walk a real bin's edges
-          // (discarded), so that every edge stays inside the staged table.
-          const int r = nb - (i << 5);
-          const bool split = r <= 16;
-          int P = 1, ph = 0, xb = x;
-          if (split) {
-            P = 32 / r;
-            ph = lane / r;
-            xb = (i << 5) + (lane - ph * r);
-          }
-          const bool idle = split ? ph >= P : x >= nb;
-          const int G0 = idle ? (i << 5) : (xb == 0 ? nb : xb + ph * nb);
-          const int gstep = P * nb;
-          long long aw = 0, ay = 0;
-          bool near = false;  // an edge within the guard band of its cell's point
-          // every lane takes cnt edges; only in the last one may a lane be past g_end
-          const int cnt = (gq + ((i << 5) > bstar ? 0 : 1) + P - 1) / P;
-          auto edge = [&](int G, bool valid, bool clamp) {
-            // tau_G / h in 24.40 fixed point: cell u and position fr (2^-32 of a cell)
-            const unsigned long long X =
-                (unsigned long long)(uint32_t)G * k_lo + ((unsigned long long)((uint32_t)G * k_hi) << 32);
-            int u = (int)((uint32_t)(X >> 32) >> 8);
-            if (clamp) u = min(u, nc);
-            const uint32_t fr = (uint32_t)(X >> 8);
-            const uint32_t dq = *reinterpret_cast<const uint32_t*>(smem + (uint32_t)u * st4);
-            near = near || (uint32_t)(dq - fr + band_q) <= 2u * band_q;
-            const int v = u + (dq < fr ? 1 : 0);  // past the cell's point if it lies before tau_G
-            const int2 lc = *reinterpret_cast<const int2*>(smem + loc_off + (uint32_t)v * st8);
-            const longlong2 bs = *reinterpret_cast<const longlong2*>(smem + base_off + (uint32_t)(v >> 5) * st16);
-            if (valid) {
-              aw += bs.x + (long long)lc.x;
-              ay += bs.y + (long long)lc.y;
-            }
-          };
-          int c = 0;
-          for (; c + 2 < cnt; c += 2) {
-            edge(G0 + c * gstep, true, false);
-            edge(G0 + (c + 1) * gstep, true, false);
-          }
-          if (c + 1 < cnt) edge(G0 + c * gstep, true, false);
-          edge(G0 + (cnt - 1) * gstep, G0 + (cnt - 1) * gstep <= g_end, true);
-          if (split) {  // warp-uniform: add the other phases of each bin into lanes 0 .. r-1
-            for (int q = 1; q < P; ++q) {
-              const long long ow = __shfl_down_sync(0xffffffffu, aw, q * r);
-              const long long oy = __shfl_down_sync(0xffffffffu, ay, q * r);
-              const bool on = __shfl_down_sync(0xffffffffu, near ? 1 : 0, q * r) != 0;
-              if (lane < r) {
-                aw += ow;
-                ay += oy;
-                near = near || on;
-              }
-            }
-          }
-          // lanes past the last bin accumulated nothing meaningful
-          if (x >= nb) {
-            aw = 0;
-            ay = 0;
-            near = false;
-          }
-          if (__any_sync(0xffffffffu, near)) {  // rare: redo the bin, near-ties by the exact FP64 fold
-            if (near) {
-              aw = 0;
-              ay = 0;
-              for (int g = x == 0 ? nb : x; g <= g_end; g += nb) {
-                const unsigned long long X =
-                    (unsigned long long)(uint32_t)g * k_lo + ((unsigned long long)((uint32_t)g * k_hi) << 32);
-                const int u = min((int)((uint32_t)(X >> 32) >> 8), nc);
-                const uint32_t fr = (uint32_t)(X >> 8);
-                const uint32_t dq = reinterpret_cast<const uint32_t*>(smem)[u];
-                int sel = dq < fr ? 1 : 0;
-                if (dq != 0xffffffffu && (uint32_t)(dq - fr + band_q) <= 2u * band_q)
-                  sel = exact_before(tp, gidx[u], f, nb, g);
-                const int v = u + sel;
-                const int2 lc = reinterpret_cast<const int2*>(smem + loc_off)[v];
-                const longlong2 bs = reinterpret_cast<const longlong2*>(smem + base_off)[v >> 5];
-                aw += bs.x + (long long)lc.x;
-                ay += bs.y + (long long)lc.y;
-              }
-            }
-          }
-          if (bstar < x) {
-            aw += fx.w_tot;
-            ay += fx.y_tot;
-          }
-          uw = aw;
-          uy = ay;
-        }
-        if ((i << 5) + 31 >= nb) {  // warp-uniform: lanes x >= nb take U[x - nb] + total
-          const int src = (x - nb) & 31;  // x - nb < 32 for every value the sweep uses
-          const long long ow = __shfl_sync(0xffffffffu, h0w, src);
-          const long long oy = __shfl_sync(0xffffffffu, h0y, src);
-          if (x >= nb) {
-            uw = ow + fx.w_tot;
-            uy = oy + fx.y_tot;
-          }
-        }
-        if (i == 0) {
-          h0w = uw;
-          h0y = uy;
-        } else {
-          // histogram of block i - 1: H[x] = U[x + 1] - U[x], exact, then FP32
-          long long nw = __shfl_down_sync(0xffffffffu, pw, 1);
-          long long ny = __shfl_down_sync(0xffffffffu, py, 1);
-          const long long fw = __shfl_sync(0xffffffffu, uw, 0);
-          const long long fy = __shfl_sync(0xffffffffu, uy, 0);
-          if (lane == 31) {
-            nw = fw;
-            ny = fy;
-          }
-          const float2 hv = make_float2(__fmul_rn(__ll2float_rn(nw - pw), scw), __fmul_rn(__ll2float_rn(ny - py), scy));
-          ring[(((i - 1) & 1) << 5) + lane] = hv;
-          if (!((i - 1) & 1)) ring[64 + lane] = hv;
-        }
-        pw = uw;
-        py = uy;
-        __syncwarp();
-        if (i >= 2) {  // sweep block i - 2: boxes starting at its bins
-          const int k = ((i - 2) << 5) + lane;
-          const float2* rb = ring + (((i - 2) & 1) << 5) + lane;
-          if (all_widths) sweep_start<true>(rb, k < nb, k, mmax, wmask, bsv, brv, bkey);
-          else sweep_start<false>(rb, k < nb, k, mmax, wmask, bsv, brv, bkey);
-        }
-        __syncwarp();
-      }
-      const bool none = bkey == 0x7fffffff;
-      float bs2 = none ? -1.f : __fmul_rn(bsv, bsv);
-      float bd = none ? 1.f : __fmaf_rn(-brv, brv, brv);
-      const int bo = bkey >> 16;
-      int bj = none ? 255 : (int)((jlow >> (4 * bo)) & 15ull);
-      int bk = none ? -1 : (bkey & 0xffff);
-      for (int off = 16; off > 0; off >>= 1) {
-        const float o_s2 = __shfl_xor_sync(0xffffffffu, bs2, off);
-        const float o_d = __shfl_xor_sync(0xffffffffu, bd, off);
-        const float o_s = __shfl_xor_sync(0xffffffffu, bsv, off);
-        const float o_r = __shfl_xor_sync(0xffffffffu, brv, off);
-        const int o_j = __shfl_xor_sync(0xffffffffu, bj, off);
-        const int o_k = __shfl_xor_sync(0xffffffffu, bk, off);
-        if (beats(o_s2, o_d, o_j, o_k, bs2, bd, bj, bk)) {
-          bs2 = o_s2; bd = o_d; bsv = o_s; brv = o_r; bj = o_j; bk = o_k;
-        }
-      }
-      BoxBest bb;
-      bb.s2 = bs2; bb.d = bd; bb.s = bsv; bb.r = brv; bb.j = bj; bb.k = bk;
-      store_box(bb, lane, fidx, a.sr, a.qidx, a.kbin, a.sbest, a.rbest);
+      run_frequency<false>(a, fidx, R, fx, smem, loc_off, base_off, nc, ring, lane, scw, scy, tp, gidx, st4, st8,
+                           st16, nullptr);
     }
   }
   if (!done && threadIdx.x == 0) atomicOr(a.err, kErrQueueBound);

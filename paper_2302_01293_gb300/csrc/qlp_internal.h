@@ -171,6 +171,8 @@ struct FixedArgs {
   float* rbest;
   uint32_t stride4;            // 4 (bytes of a table entry; a run-time value on purpose)
   int32_t pad0;
+  longlong2* ws;               // time-windowed stars: per block, bin-sum rows of ws_block entries
+  int64_t ws_block;
 };
 
 struct PrepCellsArgs {
@@ -250,6 +252,7 @@ uint32_t fixed_smem_bytes(int ncs);
 uint32_t fixed_prep_smem_bytes(int n_pts);
 int fixed_blocks_per_sm(size_t smem);
 constexpr int kFixedWarps = 32;
+constexpr int64_t kFixedWsBlock = 131072;  // workspace entries (16 B) per block for windowed stars
 // bytes of shared memory before the histograms of the cell kernel for a star with
 // ncs cells (incl. sentinel) and nw warps
 // One point of a candidate's fit window: t', y, 1/dy and its transit index.

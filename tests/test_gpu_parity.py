@@ -104,10 +104,17 @@ def test_multi_sector_cell_path_in_windows(gpu_lib):
     b = synth.multi_sector(n_stars=3, seed=4, max_sectors=4)
     g, _ = _check_batch(b, qlpbls.Params(method=qlpbls.METHOD_CELLS))
     assert g["plan"].n_cell_stars == 3 and g["plan"].n_windowed >= 2
+    assert g["plan"].n_exact_stars == 3  # exact sums through the windows' workspace
+
+
+def test_multi_sector_windows_compensated(gpu_lib):
+    b = synth.multi_sector(n_stars=3, seed=4, max_sectors=4)
+    g, _ = _check_batch(b, qlpbls.Params(method=qlpbls.METHOD_CELLS, sum_mode=qlpbls.SUM_COMP))
+    assert g["plan"].n_exact_stars == 0 and g["plan"].n_windowed >= 2
 
 
 @pytest.mark.parametrize("window", [64, 700, 4000])
-@pytest.mark.parametrize("summ", [qlpbls.SUM_PLAIN, qlpbls.SUM_COMP])
+@pytest.mark.parametrize("summ", [qlpbls.SUM_PLAIN, qlpbls.SUM_COMP, qlpbls.SUM_FIXED])
 def test_cell_windows_forced(gpu_lib, window, summ):
     # forced short windows: many window boundaries per frequency, windows shorter
     # than one bin (64 cells) and a ragged last window

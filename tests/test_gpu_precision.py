@@ -1,8 +1,9 @@
 """Precision study on multi-sector stars (up to 13 contiguous sectors, AR(1) red
 noise): the phase reduction x = t'f in FP64, in double-float (hi/lo FP32 with an
 FP64 re-fold near bin edges) and in plain FP32 on the point path, and the cell
-path's fixed-point edges, each against the FP64 oracle on sampled trial
-frequencies (evenly spaced, plus every mode's own SR maximum).
+path's fixed-point edges with exact integer and with compensated FP32 sums, each
+against the FP64 oracle on sampled trial frequencies (evenly spaced, plus every
+mode's own SR maximum).
 
 Reported per mode: the largest relative SR error and the agreement of the
 per-frequency box (duration index j, start bin k) and of the sampled maximum.
@@ -24,7 +25,8 @@ from parity import SR_RTOL, run_gpu
 pytestmark = pytest.mark.gpu
 
 MODES = {
-    "cell path (fixed-point edges, FP64 ties)": qlpbls.Params(method=qlpbls.METHOD_CELLS),
+    "cell path, exact integer sums (time windows for long tables)": qlpbls.Params(method=qlpbls.METHOD_CELLS),
+    "cell path, compensated FP32 sums": qlpbls.Params(method=qlpbls.METHOD_CELLS, sum_mode=qlpbls.SUM_COMP),
     "points, FP64 phase": qlpbls.Params(method=qlpbls.METHOD_POINTS, phase_mode=qlpbls.PHASE_FP64),
     "points, double-float phase": qlpbls.Params(method=qlpbls.METHOD_POINTS, phase_mode=qlpbls.PHASE_DF),
     "points, FP32 phase": qlpbls.Params(method=qlpbls.METHOD_POINTS, phase_mode=qlpbls.PHASE_FP32),
@@ -36,7 +38,7 @@ def test_multi_sector_precision(gpu_lib):
     b = synth.multi_sector(n_stars=8, seed=7, max_sectors=13)
     runs = {name: run_gpu(b, p, with_snr=False) for name, p in MODES.items()}
     stats = {name: {"max_sr_rel": 0.0, "box_agree": 0, "box_near_tie": 0, "sampled": 0,
-                    "best_agree": 0} for name in MODES}
+                    "best_agree": 0, "best_near_tie": 0} for name in MODES}
     max_cycles = 0.0
     for s in range(b.n_stars):
         t, y, dy = b.star(s)
@@ -65,7 +67,11 @@ def test_multi_sector_precision(gpu_lib):
                 v = ob.box_value(sub, int(i), int(q[i]), int(k[i]))
                 if v >= o.sr[i] * (1 - SR_RTOL):
                     st["box_near_tie"] += 1
-            st["best_agree"] += int(np.argmax(sr) == np.argmax(o.sr))
+            # the sampled maximum: the same frequency, or a near tie (the oracle's own
+            # value at the GPU's choice within the SR tolerance of its maximum)
+            gi, oi = int(np.argmax(sr)), int(np.argmax(o.sr))
+            st["best_agree"] += int(gi == oi or o.sr[gi] >= o.sr[oi] * (1 - SR_RTOL))
+            st["best_near_tie"] += int(gi != oi and o.sr[gi] >= o.sr[oi] * (1 - SR_RTOL))
     report = {"stars": b.n_stars, "points": int(b.offsets[-1]), "max_cycles_t_f": max_cycles,
               "modes": stats}
     print(json.dumps(report, indent=1))
