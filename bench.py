@@ -51,6 +51,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-stars", type=int, default=256)
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-multi", action="store_true", help="skip the multi-sector search line")
     ap.add_argument("--learned-train", type=int, default=8192)
     ap.add_argument("--learned-eval", type=int, default=2048)
     ap.add_argument("--tune-sample", type=int, default=512)
@@ -273,6 +274,38 @@ def cnn_throughput(net, x0, labels, peak_tflops):
             "peak_source": "bf16_tflops (burst) of MEASURED_PEAKS.json"}
 
 
+def multi_sector_line(steps: int):
+    """Search throughput on 256 multi-sector stars (1-13 contiguous 27.4-d sectors at
+    200 s, AR(1) red noise; up to ~150 k points per star): the exact cell path with
+    its tables in time windows, and the compensated FP32 cell kernel on the same
+    plan shape, each the mean of `steps` searches timed with CUDA events."""
+    import torch
+    import synth
+    from paper_2302_01293_gb300 import qlpbls
+    b = synth.multi_sector(n_stars=256, seed=3, max_sectors=13)
+    res = {"workload": "256 multi-sector stars, 1-13 sectors at 200 s (seed 3)", "points": int(b.offsets[-1])}
+    stream = torch.cuda.current_stream()
+    for name, p in (("exact", qlpbls.Params()), ("compensated", qlpbls.Params(sum_mode=qlpbls.SUM_COMP))):
+        plan = qlpbls.Plan(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar, p)
+        out = plan.alloc_outputs()
+        plan.search(out)  # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            plan.search(out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        if plan.device_status():
+            raise RuntimeError("device flags in the multi-sector search")
+        res[name] = {"value": plan.work / (ms * 1e-3), "unit": UNIT, "ms": ms,
+                     "point_freq": plan.work, "windowed_stars": plan.n_windowed,
+                     "exact_path_stars": plan.n_exact_stars}
+        del plan, out
+    return res
+
+
 def cpu_baseline(batch, n_sample: int):
     """Time the FP64 oracle (plan + BLS + S/N) on the first n_sample stars, all cores."""
     import multiprocessing as mp
@@ -475,6 +508,9 @@ def main():
         if not args.no_cpu_baseline and world == 1:
             cpu = cpu_baseline(batch, args.cpu_sample_stars)
         learned_line = None
+        multi_line = None
+        if not args.no_multi and world == 1:
+            multi_line = multi_sector_line(3)
         if not args.no_learned and world == 1:
             learned_line = learned_comparison(args)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -500,6 +536,7 @@ def main():
                 "gpu_launches": args.steps * (1 + 2 * (plan.work_points > 0) + 2 * (plan.work_cells > 0)),
                 "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "candidate_stats": cand_stats,
+                "multi_sector": multi_line,
                 "learned": learned_line}
         print(json.dumps(line), flush=True)
     if world > 1:
