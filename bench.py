@@ -54,6 +54,7 @@ def _args():
     ap.add_argument("--no-multi", action="store_true", help="skip the multi-sector search line")
     ap.add_argument("--learned-train", type=int, default=8192)
     ap.add_argument("--learned-eval", type=int, default=2048)
+    ap.add_argument("--sector-scale-stars", type=int, default=1024)
     ap.add_argument("--tune-sample", type=int, default=512)
     ap.add_argument("--no-tune", action="store_true", help="library defaults instead of the autotuner")
     ap.add_argument("--method", type=int, default=0, choices=[0, 1, 2],
@@ -207,6 +208,7 @@ def learned_comparison(args):
         at_k[str(k)] = {"network": float((rn & rf).sum() / max(rf.sum(), 1)),
                         "coarse_snr_without_network": float((rk & rf).sum() / max(rf.sum(), 1))}
     n = test.n_stars
+    sector_scale = sector_scale_line(net, args.sector_scale_stars) if args.sector_scale_stars > 0 else None
     return {"workload": f"{n} held-out stars, 1-4 sectors at 200 s, 50 % injected "
                         "(P log-U(0.5, 100) d, depth log-U(1e-4, 1e-2))",
             "train_stars": args.learned_train, "epochs": 4, "train_seconds": t_train,
@@ -217,7 +219,57 @@ def learned_comparison(args):
             "recall_at_k": at_k,
             "stars_per_hour_full": n / t_full * 3600.0,
             "stars_per_hour_learned": n / t_learned * 3600.0,
-            "speedup": t_full / t_learned, "cnn": cnn}
+            "speedup": t_full / t_learned, "cnn": cnn, "sector_scale": sector_scale}
+
+
+def sector_scale_line(net, n_stars: int):
+    """The sector-scale mix (geometric sector counts, mean 3, at most 40; mixed rho,
+    R*, noise; 1 % injected): the full-grid path through the public host-buffer call
+    and the learned path through its one-call C entry, each timed wall clock from host
+    arrays to best records (second of two runs), on one GPU; plus the device step
+    (search + S/N of a plan built once, CUDA events)."""
+    import torch
+    import synth
+    from paper_2302_01293_gb300 import learned, qlpbls
+    b = synth.sector_scale(n_stars=n_stars, seed=6)
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        full = qlpbls.run_host(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar)
+        t_full = time.perf_counter() - t0
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        best_l, _ = learned.search_learned(b, net, k=32)
+        torch.cuda.synchronize()
+        t_learned = time.perf_counter() - t0
+    plan = qlpbls.Plan(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar)
+    out = plan.alloc_outputs()
+    plan.search(out)
+    plan.snr(out)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    plan.search(out)
+    plan.snr(out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if plan.device_status():
+        raise RuntimeError("device flags in the sector-scale search")
+    rf = learned.recovered(full["best"], b)
+    rl = learned.recovered(best_l, b)
+    kmax = int(synth.sector_counts_geometric(n_stars, 6, 3.0, 40).max())
+    return {"workload": f"{n_stars} stars, geometric sector counts (mean 3, at most 40; {kmax} here), "
+                        "200 s, 1 % injected",
+            "points": int(b.offsets[-1]), "point_freq": plan.work, "trial_freqs": plan.n_freq_total,
+            "windowed_stars": plan.n_windowed, "exact_path_stars": plan.n_exact_stars,
+            "device_step_ms": ms, "device_point_freq_per_s": plan.work / (ms * 1e-3),
+            "full_grid_e2e_s": t_full, "stars_per_hour_full": n_stars / t_full * 3600.0,
+            "learned_e2e_s": t_learned, "stars_per_hour_learned": n_stars / t_learned * 3600.0,
+            "injected": int(b.inj.sum()), "full_recovered": int(rf.sum()),
+            "learned_recovered_of_full": int((rl & rf).sum())}
 
 
 # CNN FLOPs per input bin (kernel 9, 64 channels): conv 2->64, four 64->64, 64->1

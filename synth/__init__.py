@@ -219,6 +219,39 @@ def sector_counts_geometric(n_stars: int, seed: int, mean: float = 3.0, cap: int
     return np.minimum(rng.geometric(1.0 / mean, n_stars), cap)
 
 
+def sector_scale(n_stars: int = 1024, seed: int = 6, frac_injected: float = 0.01,
+                 mean_sectors: float = 3.0, cap: int = 40) -> Batch:
+    """Sector-scale mix: per star a geometric number of contiguous 27.4-d sectors
+    (mean 3, at most 40) at 200-s cadence with 1-d gaps, rho log-U(0.1, 10), R*
+    log-U(0.5, 3), white sigma log-U(2e-4, 1e-2) as in the uneven single-sector
+    batch, and 1 % injected boxes (P log-U(0.5, 13) d, depth log-U(3e-4, 1e-2),
+    circular-orbit duration)."""
+    nsec = sector_counts_geometric(n_stars, seed, mean_sectors, cap)
+    rng = np.random.default_rng(seed + 1)
+    rho = _loguniform(rng, 0.1, 10.0, n_stars)
+    rstar = _loguniform(rng, 0.5, 3.0, n_stars)
+    sig = _loguniform(rng, 2e-4, 1e-2, n_stars)
+    inj = rng.uniform(size=n_stars) < frac_injected
+    per = np.where(inj, _loguniform(rng, 0.5, 13.0, n_stars), np.nan)
+    dep = np.where(inj, _loguniform(rng, 3e-4, 1e-2, n_stars), np.nan)
+    dur = np.where(inj, circular_duration_days(np.nan_to_num(per, nan=1.0), rho, rstar), np.nan)
+    t0 = np.full(n_stars, np.nan)
+    grids = {}
+    ts, ys, dys = [], [], []
+    start = T_START + rng.uniform(0.0, 1.0, n_stars)
+    for s in range(n_stars):
+        k = int(nsec[s])
+        if k not in grids:
+            grids[k] = _sector_cadences(0.0, CADENCE_200S, k)
+        t = start[s] + grids[k]
+        y = 1.0 + rng.normal(0.0, sig[s], t.shape[0])
+        if inj[s]:
+            t0[s] = start[s] + rng.uniform(0.0, per[s])
+            y -= dep[s] * box_mask(t, per[s], t0[s], dur[s])
+        ts.append(t); ys.append(y); dys.append(np.full(t.shape[0], sig[s]))
+    return _assemble("sector_scale_200s", ts, ys, dys, rho, rstar, inj, per, t0, dep, dur)
+
+
 def proposal_set(n_stars: int, seed: int, min_sectors: int = 1, max_sectors: int = 4,
                  frac_injected: float = 0.5, depth_range=(1e-4, 1e-2), period_range=(0.5, 100.0),
                  sigma_range=(2e-4, 2e-3)) -> Batch:
