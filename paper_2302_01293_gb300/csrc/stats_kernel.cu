@@ -77,10 +77,9 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block sum of n values per thread (n <= kSums); every thread gets the totals
-// (warp sums, then one thread per value adds the warps' partials in order).
-__device__ __forceinline__ void block_sums(double* v, int n, double (*red)[kSums]) {
-  __shared__ double tot[kSums];
+// Block sum of n values per thread (n <= kSums) into tot[0 .. n-1] in shared
+// memory (warp sums, then one thread per value adds the warps' partials in order).
+__device__ __forceinline__ void block_sums(const double* v, int n, double (*red)[kSums], double* tot) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = 0; i < n; ++i) {
     const double w = warp_sum(v[i]);
@@ -93,8 +92,6 @@ __device__ __forceinline__ void block_sums(double* v, int n, double (*red)[kSums
     tot[threadIdx.x] = t;
   }
   __syncthreads();
-  for (int i = 0; i < n; ++i) v[i] = tot[i];
-  __syncthreads();
 }
 
 __device__ __forceinline__ void clip(double* x) {
@@ -103,7 +100,7 @@ __device__ __forceinline__ void clip(double* x) {
 }
 
 // Gaussian elimination with partial pivoting of the 5 x 5 system m h = b; false if singular.
-__device__ bool solve5(double m[5][6], double* h) {
+__device__ bool solve5(double (*m)[6], double* h) {
   for (int c = 0; c < 5; ++c) {
     int p = c;
     for (int r = c + 1; r < 5; ++r)
@@ -130,8 +127,11 @@ __device__ bool solve5(double m[5][6], double* h) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads) stats_kernel(const StatsArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) stats_kernel(const StatsArgs a) {
   __shared__ double red[kWarps][kSums];
+  __shared__ double s_tot[kSums];  // block totals of the last reduction
+  __shared__ double s_cur[kSums];  // chi^2, g, A at the accepted parameters (thread 0)
+  __shared__ double s_m[5][6];     // the damped normal equations (thread 0)
   __shared__ double s_x[5];
   __shared__ int s_go;
   __shared__ int s_cnt[kThreads];
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const StatsArgs a) {
 
   // 1. the fit window (ordered compaction) and the initial out-of-transit level
   int c = 0;
-  double v[kSums];
+  double v[4];
   for (int i = 0; i < 4; ++i) v[i] = 0.0;
   for (int i = i0; i < i1; ++i) {
     const double u = __dsub_rn(tp[i], t0p);
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const StatsArgs a) {
     }
   }
   s_cnt[tid] = c;
-  block_sums(v, 4, red);
+  block_sums(v, 4, red, s_tot);
   if (tid == 0) {  // exclusive scan of the per-thread counts
     int run = 0;
     for (int t = 0; t < kThreads; ++t) {
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const StatsArgs a) {
     s_x[1] = bb.depth;
     s_x[2] = q0;
     s_x[3] = kQinInit;
-    s_x[4] = v[3] > 0.0 ? v[2] / v[3] : v[0] / v[1];
+    s_x[4] = s_tot[3] > 0.0 ? s_tot[2] / s_tot[3] : s_tot[0] / s_tot[1];
     clip(s_x);
   }
   __syncthreads();
@@ -228,7 +228,8 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const StatsArgs a) {
   // The model at s_x and its derivatives. Only points on a ramp have nonzero
   // derivatives in T0, q and q_in; flat-bottom points add to the (delta, z)
   // block and outside points to z alone, so those skip the zero products.
-  auto evaluate = [&](double* sums) {  // at s_x: chi^2, J^T r, J^T J
+  auto evaluate = [&]() {  // at s_x: chi^2, J^T r, J^T J into s_tot
+    double sums[kSums];
     double x[5];
     for (int i = 0; i < 5; ++i) x[i] = s_x[i];
     const double d = __dmul_rn(x[2], period);
@@ -278,11 +279,12 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const StatsArgs a) {
         sums[6 + 14] += inv * inv;
       }
     }
-    block_sums(sums, kSums, red);
+    block_sums(sums, kSums, red, s_tot);
   };
-  double cur[kSums];  // thread 0: chi^2, g, A at the accepted x
   double xa[5];
-  evaluate(cur);
+  evaluate();
+  if (tid == 0)
+    for (int i = 0; i < kSums; ++i) s_cur[i] = s_tot[i];
   for (int i = 0; i < 5; ++i) xa[i] = s_x[i];
   double lam = kLam0;
   int it = 0;
@@ -290,20 +292,17 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const StatsArgs a) {
   while (it < kMaxIt) {  // block-uniform: s_go decides
     ++it;
     if (tid == 0) {
-      double A[5][5];
       int p = 6;
       for (int k = 0; k < 5; ++k)
-        for (int l = k; l < 5; ++l) A[k][l] = A[l][k] = cur[p++];
+        for (int l = k; l < 5; ++l) s_m[k][l] = s_m[l][k] = s_cur[p++];
       double dmax = 0.0;
-      for (int k = 0; k < 5; ++k) dmax = fmax(dmax, A[k][k]);
-      double m[5][6];
+      for (int k = 0; k < 5; ++k) dmax = fmax(dmax, s_m[k][k]);
       for (int k = 0; k < 5; ++k) {
-        for (int l = 0; l < 5; ++l) m[k][l] = A[k][l];
-        m[k][k] = __dadd_rn(A[k][k], __dmul_rn(lam, fmax(A[k][k], __dmul_rn(1e-12, dmax))));
-        m[k][5] = cur[1 + k];
+        s_m[k][k] = __dadd_rn(s_m[k][k], __dmul_rn(lam, fmax(s_m[k][k], __dmul_rn(1e-12, dmax))));
+        s_m[k][5] = s_cur[1 + k];
       }
       double h[5];
-      const bool ok = solve5(m, h);
+      const bool ok = solve5(s_m, h);
       if (ok) {
         for (int k = 0; k < 5; ++k) s_x[k] = __dadd_rn(xa[k], h[k]);
         clip(s_x);
@@ -311,14 +310,13 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const StatsArgs a) {
       s_go = ok ? 1 : 0;
     }
     __syncthreads();
-    double trial[kSums];
     const bool ok = s_go != 0;
-    if (ok) evaluate(trial);
+    if (ok) evaluate();
     if (tid == 0) {
       int act = 0;  // 0 continue, 1 stop
-      if (ok && trial[0] < cur[0]) {
-        const double rel = cur[0] > 0.0 ? (cur[0] - trial[0]) / cur[0] : 0.0;
-        for (int i = 0; i < kSums; ++i) cur[i] = trial[i];
+      if (ok && s_tot[0] < s_cur[0]) {
+        const double rel = s_cur[0] > 0.0 ? (s_cur[0] - s_tot[0]) / s_cur[0] : 0.0;
+        for (int i = 0; i < kSums; ++i) s_cur[i] = s_tot[i];
         for (int i = 0; i < 5; ++i) xa[i] = s_x[i];
         lam /= 10.0;
         if (rel < kRtol) { conv = true; act = 1; }
@@ -379,8 +377,8 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const StatsArgs a) {
   s_kf[tid] = kf;
   s_kl[tid] = kl;
   s_kd[tid] = kd;
-  double tot[4] = {r2, sb2, 0.0, 0.0};
-  block_sums(tot, 2, red);
+  const double part[2] = {r2, sb2};
+  block_sums(part, 2, red, s_tot);
   int cnt3[3] = {n_in, n_before, n_after};
   for (int i = 0; i < 3; ++i) {
     double vv = (double)cnt3[i];
@@ -393,7 +391,7 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const StatsArgs a) {
     for (int w = 0; w < kWarps; ++w)
       for (int i = 0; i < 3; ++i) cn[i] += red[w][2 + i];
     // merge the run partials in thread order
-    double sbm = tot[1];
+    double sbm = s_tot[1];
     long long nb_occ = 0;
     for (int t = 0; t < kThreads; ++t) nb_occ += s_runs[t];
     long long carry_bin = -1;
@@ -422,7 +420,7 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const StatsArgs a) {
       last = s_kl[t];
       have = true;
     }
-    const double sw = sqrt(tot[0] / n);
+    const double sw = sqrt(s_tot[0] / n);
     const double nb_mean = (double)n / (double)nb_occ;
     const double sb2m = sbm / (double)nb_occ;
     const double sr = sqrt(fmax(0.0, sb2m - sw * sw / nb_mean));
@@ -435,7 +433,7 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const StatsArgs a) {
     o.q = x[2];
     o.q_in = x[3];
     o.z = x[4];
-    o.chi2 = cur[0];
+    o.chi2 = s_cur[0];
     o.sigma_w = sw;
     o.sigma_r = sr;
     o.depth_mean = depth_mean;
