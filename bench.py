@@ -585,7 +585,10 @@ def main():
                            f"{plan.n_points * 24 / 1e6:.0f} MB FP64)", "parallelism": f"replicas x{world}"},
                 "ms_search": ms_search, "ms_kernel": ms_kernel,
                 "exact_path_stars": plan.n_exact_stars,
-                "gpu_launches": args.steps * (1 + 2 * (plan.work_points > 0) + 2 * (plan.work_cells > 0)),
+                # per step: S/N, and per search path in use its preparation and search kernels
+                "gpu_launches": args.steps * (1 + 2 * (plan.work_points > 0)
+                                              + 2 * (plan.n_cell_stars > plan.n_exact_stars)
+                                              + 2 * (plan.n_exact_stars > 0)),
                 "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "candidate_stats": cand_stats,
                 "multi_sector": multi_line,
