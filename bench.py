@@ -52,6 +52,9 @@ def _args():
     ap.add_argument("--cpu-sample-stars", type=int, default=256)
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-multi", action="store_true", help="skip the multi-sector search line")
+    ap.add_argument("--workload", default="uneven", choices=["uneven", "multi_sector"],
+                    help="the timed batch: uneven single-sector stars (default) or multi-sector stars "
+                         "(1-13 sectors, for profiling the time-windowed path)")
     ap.add_argument("--learned-train", type=int, default=8192)
     ap.add_argument("--learned-eval", type=int, default=2048)
     ap.add_argument("--sector-scale-stars", type=int, default=1024)
@@ -422,7 +425,10 @@ def main():
         if world > 1:
             dist.barrier()
 
-    batch = synth.uneven_single_sector(n_stars=args.stars, seed=args.seed + 1000 * rank)
+    if args.workload == "multi_sector":
+        batch = synth.multi_sector(n_stars=args.stars, seed=3 + 1000 * rank, max_sectors=13)
+    else:
+        batch = synth.uneven_single_sector(n_stars=args.stars, seed=args.seed + 1000 * rank)
     stream = torch.cuda.current_stream()
     # launch settings from the autotuner (timed on a sample of the batch; untimed here)
     t0 = time.perf_counter()
@@ -541,9 +547,10 @@ def main():
     # DRAM traffic of one launch of the timed kernel: ncu capture of the same kernel on
     # 1,024 stars of this workload, scaled by points to the default batch
     traffic = None
-    if cells_dominant and kernel_id == 1 and args.stars == 4096 and args.seed == 2 and params.sum_mode == 1:
+    default_batch = args.workload == "uneven" and args.stars == 4096 and args.seed == 2
+    if cells_dominant and kernel_id == 1 and default_batch and params.sum_mode == 1:
         traffic = 423.0e6 * plan.n_points / 10638874
-    if kernel_id == 2 and args.stars == 4096 and args.seed == 2:
+    if kernel_id == 2 and default_batch:
         # cells_fixed_kernel: ncu capture on 1,024 stars of this workload (504.1 MB read +
         # 83.0 MB written), scaled by points (tables, records and outputs grow with them)
         traffic = 587.1e6 * plan.n_points / 10638874
@@ -570,7 +577,8 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": ("int64 fixed-point sums, f32 box scores, FP64 bin decisions" if kernel_id == 2
                           else "f32 sums, FP64 prefix sums, FP64 bin decisions"), "data": "synthetic",
-                "config": {"workload": "uneven_single_sector_200s", "stars_per_gpu": args.stars,
+                "config": {"workload": ("uneven_single_sector_200s" if args.workload == "uneven"
+                                        else "multi_sector_200s_1to13"), "stars_per_gpu": args.stars,
                            "points": plan.n_points, "trial_freqs": plan.n_freq_total,
                            "point_freq_per_gpu": plan.work, "bin_edges": plan.edges,
                            "cell_path_stars": plan.n_cell_stars, "phase_mode": "DF",
