@@ -52,6 +52,8 @@ def _args():
     ap.add_argument("--cpu-sample-stars", type=int, default=256)
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-multi", action="store_true", help="skip the multi-sector search line")
+    ap.add_argument("--sum-mode", default="fixed", choices=["fixed", "comp", "plain"],
+                    help="cell-path sums: exact integers (default), compensated FP32, plain FP32")
     ap.add_argument("--workload", default="uneven", choices=["uneven", "multi_sector"],
                     help="the timed batch: uneven single-sector stars (default) or multi-sector stars "
                          "(1-13 sectors, for profiling the time-windowed path)")
@@ -432,7 +434,8 @@ def main():
     stream = torch.cuda.current_stream()
     # launch settings from the autotuner (timed on a sample of the batch; untimed here)
     t0 = time.perf_counter()
-    params = qlpbls.Params(method=args.method)
+    params = qlpbls.Params(method=args.method, sum_mode={"fixed": qlpbls.SUM_FIXED, "comp": qlpbls.SUM_COMP,
+                                                         "plain": qlpbls.SUM_PLAIN}[args.sum_mode])
     if not args.no_tune:
         params, _ = qlpbls.autotune(batch.offsets, batch.t, batch.y, batch.dy, batch.rho, batch.rstar,
                                     params, sample_stars=args.tune_sample)
