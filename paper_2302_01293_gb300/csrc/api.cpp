@@ -443,7 +443,7 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
         fixed_ncs = std::max<int64_t>(fixed_ncs, d.n_win > 1 ? (int64_t)d.win_cap + 1 : h.n_cells + 1);
         if (d.n_win > 1) pl->fixed_windowed = true;
         pl->edges_fixed += h.cells_work;
-        for (const int32_t nbk : h.nbins) pl->bins_fixed += (double)nbk;
+        pl->bins_fixed += h.nbins_sum;
       } else {
         cells_cap = std::max<int64_t>(cells_cap, h.n_cells + 1);
         nb_c = std::max(nb_c, h.nbins_max);

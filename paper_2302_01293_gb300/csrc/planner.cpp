@@ -118,6 +118,7 @@ void plan_one(const qlp_bls_params& p, const double* t, const double* y, const d
     s.nbins.push_back(nb);
     s.nbins_max = std::max(s.nbins_max, nb);
     s.nbins_min = s.nbins.size() == 1 ? nb : std::min(s.nbins_min, nb);
+    s.nbins_sum += (double)nb;
     const double y = s.baseline * f * (double)nb;
     s.ymax = std::max(s.ymax, y);
     edges += std::floor(y) + 3.0;

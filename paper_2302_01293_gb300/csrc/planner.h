@@ -23,6 +23,7 @@ struct StarPlanHost {
   std::vector<int32_t> nbins;      // nbins at each frequency
   int32_t nbins_max = 0;
   int32_t nbins_min = 0;
+  double nbins_sum = 0.0;          // sum of nbins over the grid
   double ymax = 0.0;               // max over f of T f nbins(f)
   int32_t sturges_nb = 0;
   // cell path: cells of width h (just below the smallest point spacing) hold at
