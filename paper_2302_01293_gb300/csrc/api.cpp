@@ -358,9 +358,13 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
     const bool old_fits = cell_smem(W.cap, h.nbins_max) <= (size_t)budget;
     const double pp_work = (double)h.freqs.size() * (double)round32((int64_t)h.tp.size());
     // exact path: at least 32 bins, at most 2^14 cycles and 2^21 points (the integer
-    // prefix sums stay below 2^62); the whole table and the warps' rings in shared
-    // memory, or else windows of the table (bin sums through a global workspace)
+    // prefix sums stay below 2^62), no weight or weighted residual above 256 times
+    // the star's mean (the integer scale follows the largest one: a single extreme
+    // point would coarsen every other point's weight); the whole table and the
+    // warps' rings in shared memory, or else windows of the table (bin sums through
+    // a global workspace)
     const bool fixed_ok = p.sum_mode == QLP_SUM_FIXED && p.bin_mode == QLP_BIN_SHARED && h.nbins_min >= 32 &&
+                          h.w_spread <= 256.0 && h.wd_spread <= 256.0 &&
                           h.baseline * h.freqs.back() <= 16384.0 && h.tp.size() <= ((size_t)1 << 21) &&
                           (size_t)32 * 16 * ((h.nbins_max + 31) / 32) <= (size_t)kFixedWsBlock * 16;
     if (fixed_ok && (p.method == 2 || h.cells_work < 2.0 * pp_work)) {

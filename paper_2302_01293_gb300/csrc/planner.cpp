@@ -171,6 +171,27 @@ void plan_one(const qlp_bls_params& p, const double* t, const double* y, const d
   }
   s.sturges_nb = sturges_of((int64_t)s.freqs.size());
 
+  // weight spreads (FP64; only a routing decision depends on them, so the sums
+  // are plain and the weights are not normalised)
+  {
+    double isum = 0.0, iysum = 0.0, imax = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+      const double inv = 1.0 / (s.dy[i] * s.dy[i]);
+      isum += inv;
+      iysum += inv * s.y[i];
+      imax = std::max(imax, inv);
+    }
+    const double ybar = iysum / isum;
+    double dsum = 0.0, dmax = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+      const double v = std::fabs((s.y[i] - ybar) / (s.dy[i] * s.dy[i]));
+      dsum += v;
+      dmax = std::max(dmax, v);
+    }
+    s.w_spread = imax / (isum / (double)m);
+    s.wd_spread = dsum > 0.0 ? dmax / (dsum / (double)m) : 0.0;
+  }
+
   // cell path: smallest spacing, cells just narrower, one point per cell
   double min_gap = INFINITY;
   for (int64_t i = 1; i < m; ++i) min_gap = std::min(min_gap, s.tp[i] - s.tp[i - 1]);

@@ -24,6 +24,10 @@ struct StarPlanHost {
   int32_t nbins_max = 0;
   int32_t nbins_min = 0;
   double nbins_sum = 0.0;          // sum of nbins over the grid
+  // spread of the normalised weights w = dy^-2 / sum dy^-2 and of w (y - ybar):
+  // the largest over the mean (the exact path's integer scale follows the largest)
+  double w_spread = 0.0;
+  double wd_spread = 0.0;
   double ymax = 0.0;               // max over f of T f nbins(f)
   int32_t sturges_nb = 0;
   // cell path: cells of width h (just below the smallest point spacing) hold at

@@ -59,6 +59,21 @@ def test_exact_cell_path_is_the_default(gpu_lib):
     assert g["plan"].n_exact_stars == 8 and g["plan"].exact_edges == g["plan"].edges
 
 
+def test_exact_path_falls_back_on_an_extreme_point(gpu_lib):
+    # one point with an error bar 20 times smaller than the rest (weight 400 times
+    # the others) and one flux outlier of 2,000 sigma: those stars take the
+    # compensated cell kernel, the untouched star the exact one; all three match the
+    # oracle
+    b = synth.uneven_single_sector(n_stars=3, seed=33)
+    dy = b.dy.copy()
+    y = b.y.copy()
+    dy[b.offsets[0] + 500] *= 0.05
+    y[b.offsets[1] + 700] += 2000.0 * dy[b.offsets[1] + 700]
+    b2 = synth.Batch(b.offsets, b.t, y, dy, b.rho, b.rstar, b.inj, b.period, b.t0, b.depth, b.duration, "extreme")
+    g, _ = _check_batch(b2, qlpbls.Params())
+    assert g["plan"].n_exact_stars == 1 and g["plan"].n_cell_stars == 3
+
+
 def test_exact_path_falls_back_below_32_bins(gpu_lib):
     # durations from 1.5 q_circ: 12 bins at Pmin, fewer than a warp's 32 lanes; those
     # stars take the compensated cell kernel, with the same results
