@@ -6,6 +6,7 @@
 // Every numeric stage is a kernel of this library; this file sequences the calls.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -62,6 +63,25 @@ int alloc_spectrum(DevBufs& b, int64_t nf, int32_t n_stars, Spectrum* o) {
 
 }  // namespace
 
+namespace {
+
+// One chunk of stars on the learned path: its coarse plan and spectrum, the
+// network's proposals, and its refine plan and spectrum.
+struct LearnedChunk {
+  int32_t s0 = 0, ns = 0;
+  PlanGuard cp, rp;
+  Spectrum c{}, r{};
+  double* trend = nullptr;
+  uint16_t* x0 = nullptr;
+  int32_t* bins = nullptr;
+  cudaEvent_t proposed = nullptr;  // the chunk's proposals are in `bins`
+  ~LearnedChunk() {
+    if (proposed) cudaEventDestroy(proposed);
+  }
+};
+
+}  // namespace
+
 extern "C" int qlp_bls_search_learned(const qlp_bls_params* p, int32_t n_stars, const int64_t* offsets,
                                       const double* t, const double* y, const double* dy,
                                       const double* rho, const double* rstar, qlp_cnn_t* net, int32_t k,
@@ -69,86 +89,167 @@ extern "C" int qlp_bls_search_learned(const qlp_bls_params* p, int32_t n_stars, 
                                       int32_t* bins_host) {
   if (!p || !net || !best_host || n_stars < 0 || k < 1 || !(half_width > 0.0)) return QLP_ERR_ARG;
   if (n_stars == 0) return QLP_OK;
+  if (!offsets) return QLP_ERR_ARG;
   int32_t max_batch = 0, len = 0;
   int rc = qlp_cnn_shape(net, &max_batch, &len);
   if (rc) return rc;
   if (len != p->coarse_bins || k > len) return QLP_ERR_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  DevBufs buf(st);
-
-  // coarse spectrum, its S/N and trend records, and the network input
-  qlp_bls_params pc = *p;
-  pc.grid_mode = 1;
-  PlanGuard cp;
-  if ((rc = qlp_bls_plan(&pc, n_stars, offsets, t, y, dy, rho, rstar, stream, &cp.p))) return rc;
-  int64_t nfc = 0;
-  if ((rc = qlp_bls_plan_info(cp.p, &nfc, nullptr, nullptr, nullptr, nullptr, nullptr))) return rc;
-  Spectrum c{};
-  double* trend = nullptr;
-  uint16_t* x0 = nullptr;  // BF16 [n_stars][len][2]
-  float* logits = nullptr;
-  int32_t* bins = nullptr;
-  if ((rc = alloc_spectrum(buf, nfc, n_stars, &c)) || (rc = buf.get(&trend, (size_t)n_stars * QLP_TREND_DOUBLES)) ||
-      (rc = buf.get(&x0, (size_t)n_stars * len * 2)) || (rc = buf.get(&logits, (size_t)max_batch * len)) ||
-      (rc = buf.get(&bins, (size_t)n_stars * k)))
-    return rc;
-  if ((rc = qlp_bls_search(cp.p, stream, c.sr, c.qidx, c.kbin, c.s, c.r))) return rc;
-  if ((rc = qlp_bls_snr_trend(cp.p, stream, c.sr, c.qidx, c.kbin, c.s, c.r, nullptr, trend, c.snr, c.best)))
-    return rc;
-  if ((rc = qlp_bls_coarse_tensor(cp.p, stream, c.snr, len, x0))) return rc;
-
-  // proposals: the network's top-k bins per star
-  for (int32_t a = 0; a < n_stars; a += max_batch) {
-    const int32_t nb = n_stars - a < max_batch ? n_stars - a : max_batch;
-    const uint16_t* xb = x0 + (size_t)a * len * 2;
-    if ((rc = qlp_cnn_forward(net, xb, nb, logits, stream))) return rc;
-    if ((rc = qlp_cnn_topk(logits, xb, nb, len, k, bins + (size_t)a * k, stream))) return rc;
+  // Chunks of whole stars with about equal points, in a two-stage pipeline: while
+  // the device searches chunk c's coarse spectrum and runs the network on it, the
+  // host plans chunk c + 1's coarse grid and then chunk c - 1's refine grid. Plans
+  // upload and synchronise on their own stream; coarse work and the network run on
+  // one stream, the refine searches on another.
+  const int64_t npts = offsets[n_stars] - offsets[0];
+  const int nch = n_stars >= 1024 ? std::min(8, n_stars / 256) : 1;
+  cudaStream_t st_in = (cudaStream_t)stream;
+  cudaStream_t st_up = nullptr, st_c = nullptr, st_r = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&st_up, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st_c, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st_r, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    if (st_up) cudaStreamDestroy(st_up);
+    if (st_c) cudaStreamDestroy(st_c);
+    return qlp::record_cuda_error(e, "cudaStreamCreate");
   }
-  std::vector<int32_t> hb((size_t)n_stars * k);
-  cudaError_t e = cudaMemcpyAsync(hb.data(), bins, sizeof(int32_t) * hb.size(), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return qlp::record_cuda_error(e, "proposal download");
-  if (bins_host)
-    for (size_t i = 0; i < hb.size(); ++i) bins_host[i] = hb[i];
+  // the caller's stream's earlier work (the network's weights) comes first
+  cudaEvent_t ev_in = nullptr;
+  e = cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev_in, st_in);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st_c, ev_in, 0);
+  if (ev_in) cudaEventDestroy(ev_in);
+  std::vector<LearnedChunk> ch((size_t)nch);
+  {
+    DevBufs buf_c(st_c), buf_r(st_r);
+    float* logits = nullptr;
+    qlp_bls_params pc = *p;
+    pc.grid_mode = 1;
+    qlp_bls_params pr = *p;
+    pr.grid_mode = 0;
+    const double ratio = p->coarse_pmax / p->coarse_pmin;
+    auto period = [&](double x) { return p->coarse_pmin * std::pow(ratio, x / (double)(len - 1)); };
+    if (e != cudaSuccess) rc = qlp::record_cuda_error(e, "stream order");
+    if (rc == QLP_OK) rc = buf_c.get(&logits, (size_t)max_batch * len);
 
-  // windows in frequency around each proposed bin: P(x) = pmin (pmax/pmin)^(x/(bins-1))
-  const double ratio = p->coarse_pmax / p->coarse_pmin;
-  auto period = [&](double x) { return p->coarse_pmin * std::pow(ratio, x / (double)(len - 1)); };
-  std::vector<int64_t> woff((size_t)n_stars + 1, 0);
-  std::vector<double> wlo, whi;
-  for (int32_t s = 0; s < n_stars; ++s) {
-    for (int32_t i = 0; i < k; ++i) {
-      const int32_t kb = hb[(size_t)s * k + i];
-      if (kb < 0) continue;
-      wlo.push_back(1.0 / period((double)kb + half_width));
-      whi.push_back(1.0 / period((double)kb - half_width));
+    // stage 1 of chunk c: coarse plan (host), spectrum, S/N, network input, proposals
+    auto coarse = [&](int c) -> int {
+      LearnedChunk& q = ch[(size_t)c];
+      const int64_t o0 = offsets[q.s0];
+      std::vector<int64_t> off((size_t)q.ns + 1);
+      for (int32_t i = 0; i <= q.ns; ++i) off[(size_t)i] = offsets[q.s0 + i] - o0;
+      int r2 = qlp_bls_plan(&pc, q.ns, off.data(), t + o0, y + o0, dy + o0, rho ? rho + q.s0 : nullptr,
+                            rstar ? rstar + q.s0 : nullptr, st_up, &q.cp.p);
+      if (r2) return r2;
+      int64_t nfc = 0;
+      if ((r2 = qlp_bls_plan_info(q.cp.p, &nfc, nullptr, nullptr, nullptr, nullptr, nullptr))) return r2;
+      if ((r2 = alloc_spectrum(buf_c, nfc, q.ns, &q.c)) || (r2 = buf_c.get(&q.trend, (size_t)q.ns * QLP_TREND_DOUBLES)) ||
+          (r2 = buf_c.get(&q.x0, (size_t)q.ns * len * 2)) || (r2 = buf_c.get(&q.bins, (size_t)q.ns * k)))
+        return r2;
+      if ((r2 = qlp_bls_search(q.cp.p, st_c, q.c.sr, q.c.qidx, q.c.kbin, q.c.s, q.c.r))) return r2;
+      if ((r2 = qlp_bls_snr_trend(q.cp.p, st_c, q.c.sr, q.c.qidx, q.c.kbin, q.c.s, q.c.r, nullptr, q.trend, q.c.snr,
+                                  q.c.best)))
+        return r2;
+      if ((r2 = qlp_bls_coarse_tensor(q.cp.p, st_c, q.c.snr, len, q.x0))) return r2;
+      for (int32_t a = 0; a < q.ns; a += max_batch) {
+        const int32_t nb = q.ns - a < max_batch ? q.ns - a : max_batch;
+        const uint16_t* xb = q.x0 + (size_t)a * len * 2;
+        if ((r2 = qlp_cnn_forward(net, xb, nb, logits, st_c))) return r2;
+        if ((r2 = qlp_cnn_topk(logits, xb, nb, len, k, q.bins + (size_t)a * k, st_c))) return r2;
+      }
+      cudaError_t e2 = cudaEventCreateWithFlags(&q.proposed, cudaEventDisableTiming);
+      if (e2 == cudaSuccess) e2 = cudaEventRecord(q.proposed, st_c);
+      return e2 == cudaSuccess ? QLP_OK : qlp::record_cuda_error(e2, "proposal event");
+    };
+    // stage 2 of chunk c: windows around the proposals, refine plan (host), search,
+    // S/N from the coarse trend
+    auto refine = [&](int c) -> int {
+      LearnedChunk& q = ch[(size_t)c];
+      cudaError_t e2 = cudaEventSynchronize(q.proposed);
+      std::vector<int32_t> hb((size_t)q.ns * k);
+      if (e2 == cudaSuccess)
+        e2 = cudaMemcpyAsync(hb.data(), q.bins, sizeof(int32_t) * hb.size(), cudaMemcpyDeviceToHost, st_up);
+      if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st_up);
+      if (e2 != cudaSuccess) return qlp::record_cuda_error(e2, "proposal download");
+      if (bins_host)
+        for (size_t i = 0; i < hb.size(); ++i) bins_host[(size_t)q.s0 * k + i] = hb[i];
+      // windows in frequency around each proposed bin: P(x) = pmin (pmax/pmin)^(x/(bins-1))
+      std::vector<int64_t> woff((size_t)q.ns + 1, 0);
+      std::vector<double> wlo, whi;
+      for (int32_t s = 0; s < q.ns; ++s) {
+        for (int32_t i = 0; i < k; ++i) {
+          const int32_t kb = hb[(size_t)s * k + i];
+          if (kb < 0) continue;
+          wlo.push_back(1.0 / period((double)kb + half_width));
+          whi.push_back(1.0 / period((double)kb - half_width));
+        }
+        woff[(size_t)s + 1] = (int64_t)wlo.size();
+      }
+      const int64_t o0 = offsets[q.s0];
+      std::vector<int64_t> off((size_t)q.ns + 1);
+      for (int32_t i = 0; i <= q.ns; ++i) off[(size_t)i] = offsets[q.s0 + i] - o0;
+      int r2 = qlp_bls_plan_windows(&pr, q.ns, off.data(), t + o0, y + o0, dy + o0, rho ? rho + q.s0 : nullptr,
+                                    rstar ? rstar + q.s0 : nullptr, woff.data(), wlo.data(), whi.data(), st_up,
+                                    &q.rp.p);
+      if (r2) return r2;
+      int64_t nfr = 0;
+      if ((r2 = qlp_bls_plan_info(q.rp.p, &nfr, nullptr, nullptr, nullptr, nullptr, nullptr))) return r2;
+      if ((r2 = alloc_spectrum(buf_r, nfr, q.ns, &q.r))) return r2;
+      if ((r2 = qlp_bls_search(q.rp.p, st_r, q.r.sr, q.r.qidx, q.r.kbin, q.r.s, q.r.r))) return r2;
+      return qlp_bls_snr_trend(q.rp.p, st_r, q.r.sr, q.r.qidx, q.r.kbin, q.r.s, q.r.r, q.trend, nullptr, q.r.snr,
+                               q.r.best);
+    };
+
+    int32_t s0 = 0;
+    for (int c = 0; c < nch; ++c) {  // chunk boundaries by points
+      int32_t s1 = n_stars;
+      if (c < nch - 1) {
+        const int64_t goal = offsets[0] + npts * (c + 1) / nch;
+        s1 = s0;
+        while (s1 < n_stars && offsets[s1] < goal) ++s1;
+        s1 = std::max(s1, std::min(n_stars, s0 + 1));
+      }
+      ch[(size_t)c].s0 = s0;
+      ch[(size_t)c].ns = s1 - s0;
+      s0 = s1;
     }
-    woff[(size_t)s + 1] = (int64_t)wlo.size();
+    for (int c = 0; c <= nch && rc == QLP_OK; ++c) {
+      if (c < nch && ch[(size_t)c].ns > 0) rc = coarse(c);
+      if (rc == QLP_OK && c >= 1 && ch[(size_t)(c - 1)].ns > 0) rc = refine(c - 1);
+    }
+    if (rc == QLP_OK) {
+      e = cudaStreamSynchronize(st_r);
+      for (const LearnedChunk& q : ch) {
+        if (e != cudaSuccess || q.ns == 0) continue;
+        e = cudaMemcpyAsync(best_host + q.s0, q.r.best, sizeof(qlp_bls_best) * (size_t)q.ns, cudaMemcpyDeviceToHost,
+                            st_up);
+      }
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st_up);
+      if (e != cudaSuccess) rc = qlp::record_cuda_error(e, "result download");
+    }
+    // device error flags of every plan and of the network's tensor-core waits
+    int32_t fl = 0;
+    for (const LearnedChunk& q : ch) {
+      if (rc != QLP_OK) break;
+      for (qlp_bls_plan_t* pp : {q.cp.p, q.rp.p}) {
+        if (!pp) continue;
+        int32_t f = 0;
+        const int x = qlp_bls_device_status(pp, st_r, &f);
+        if (x && x != QLP_ERR_DEVICE) rc = x;
+        fl |= f;
+      }
+    }
+    if (rc == QLP_OK) {
+      int32_t f3 = 0;
+      const int r3 = qlp_cnn_loss(net, nullptr, &f3, st_c);
+      if (r3 && r3 != QLP_ERR_DEVICE) rc = r3;
+      fl |= f3;
+      if (rc == QLP_OK && fl) rc = QLP_ERR_DEVICE;
+    }
+    cudaStreamSynchronize(st_c);
+    cudaStreamSynchronize(st_r);
+  }  // buffers freed (stream-ordered) before the streams go
+  for (cudaStream_t x : {st_up, st_c, st_r}) {
+    cudaStreamSynchronize(x);
+    cudaStreamDestroy(x);
   }
-
-  // full-resolution grid inside the windows, scored with the coarse trend
-  qlp_bls_params pr = *p;
-  pr.grid_mode = 0;
-  PlanGuard rp;
-  if ((rc = qlp_bls_plan_windows(&pr, n_stars, offsets, t, y, dy, rho, rstar, woff.data(), wlo.data(), whi.data(),
-                                 stream, &rp.p)))
-    return rc;
-  int64_t nfr = 0;
-  if ((rc = qlp_bls_plan_info(rp.p, &nfr, nullptr, nullptr, nullptr, nullptr, nullptr))) return rc;
-  Spectrum r{};
-  if ((rc = alloc_spectrum(buf, nfr, n_stars, &r))) return rc;
-  if ((rc = qlp_bls_search(rp.p, stream, r.sr, r.qidx, r.kbin, r.s, r.r))) return rc;
-  if ((rc = qlp_bls_snr_trend(rp.p, stream, r.sr, r.qidx, r.kbin, r.s, r.r, trend, nullptr, r.snr, r.best)))
-    return rc;
-  e = cudaMemcpyAsync(best_host, r.best, sizeof(qlp_bls_best) * (size_t)n_stars, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return qlp::record_cuda_error(e, "result download");
-  // device error flags of both plans and of the network's tensor-core waits
-  int32_t f1 = 0, f2 = 0, f3 = 0;
-  const int r1 = qlp_bls_device_status(cp.p, stream, &f1);
-  const int r2 = qlp_bls_device_status(rp.p, stream, &f2);
-  const int r3 = qlp_cnn_loss(net, nullptr, &f3, stream);
-  for (int x : {r1, r2, r3})
-    if (x && x != QLP_ERR_DEVICE) return x;
-  return (f1 | f2 | f3) ? QLP_ERR_DEVICE : QLP_OK;
+  return rc;
 }

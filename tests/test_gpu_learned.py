@@ -134,6 +134,22 @@ def test_learned_path_recall(gpu_lib):
     net.close()
 
 
+def test_learned_one_call_in_chunks_equals_whole_batch_stages(gpu_lib):
+    """1,100 stars take the one-call path in several chunks (planning of one
+    chunk overlaps the device work of its neighbours); every star's proposals
+    and best record equal those of the stages run over the whole batch at once."""
+    test = synth.proposal_set(1100, seed=778)
+    net = qlpbls.CNN(max_batch=64, length=4096, seed=3)
+    best_l, bins = learned.search_learned(test, net, k=8)
+    cs = learned.CoarseStage(test)
+    bins_py = learned.propose(net, cs.x0, 8).cpu().numpy()
+    assert np.array_equal(bins, bins_py)
+    best_py = learned.search_with_bins(test, cs, bins_py)
+    for key in ("f_idx", "snr", "sr", "period", "q", "t0"):
+        np.testing.assert_array_equal(best_py[key], best_l[key], err_msg=key)
+    net.close()
+
+
 def test_cnn_checkpoint_roundtrip(gpu_lib, tmp_path):
     import torch
     b = synth.proposal_set(64, seed=61)
