@@ -447,6 +447,24 @@ int qlp_bls_star_grid(const qlp_bls_params* p, int64_t n, const double* t, const
                       int64_t capacity, int64_t* n_f_out);
 
 /*
+ * qlp_bls_batch_grid -- host only, no device work: the Sec. 2.1 trial-frequency
+ * grids of a batch, built by the batch planner qlp_bls_plan uses (all host
+ * threads, the recurrences of several stars stepped together; every grid equals
+ * its one-star definition bit for bit).
+ *  n_stars, offsets, t, y, dy, rho   the batch, as for qlp_bls_plan.
+ *  star_status   host int32[n_stars] per-star status (may be NULL).
+ *  freq_offsets  host int64[n_stars + 1] (required): star s owns
+ *                freqs[freq_offsets[s] .. freq_offsets[s + 1]); stars with a
+ *                non-zero status own none.
+ *  freqs         host double[capacity] (may be NULL).
+ * Returns QLP_ERR_ARG when freqs is given and capacity < freq_offsets[n_stars]
+ * (freq_offsets and star_status are still written).
+ */
+int qlp_bls_batch_grid(const qlp_bls_params* p, int32_t n_stars, const int64_t* offsets, const double* t,
+                       const double* y, const double* dy, const double* rho, int32_t* star_status,
+                       int64_t* freq_offsets, double* freqs, int64_t capacity);
+
+/*
  * qlp_bls_search_static -- the paper has no counterpart of this entry point.
  * The BLS search of ONE star (qlp_bls_search's results for that star) without
  * allocating any device memory, for callers that may not call cudaMalloc: code

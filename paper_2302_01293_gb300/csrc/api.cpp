@@ -1024,6 +1024,33 @@ int qlp_bls_star_grid(const qlp_bls_params* pin, int64_t n, const double* t, con
   return QLP_OK;
 }
 
+int qlp_bls_batch_grid(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offsets, const double* t,
+                       const double* y, const double* dy, const double* rho, int32_t* star_status,
+                       int64_t* freq_offsets, double* freqs, int64_t capacity) {
+  if (n_stars < 0 || !freq_offsets || (n_stars > 0 && (!offsets || !t || !y || !dy))) return QLP_ERR_ARG;
+  for (int32_t s = 0; s < n_stars; ++s)
+    if (offsets[s + 1] < offsets[s]) return QLP_ERR_ARG;
+  qlp_bls_params p;
+  if (pin) p = *pin; else qlp_bls_params_default(&p);
+  const int rc = check_params(p);
+  if (rc) return rc;
+  std::vector<StarPlanHost> sp;
+  plan_all(p, n_stars, offsets, t, y, dy, rho, &sp);
+  freq_offsets[0] = 0;
+  for (int32_t s = 0; s < n_stars; ++s) {
+    const StarPlanHost& h = sp[(size_t)s];
+    if (star_status) star_status[s] = h.status;
+    freq_offsets[s + 1] = freq_offsets[s] + (h.status == 0 ? (int64_t)h.freqs.size() : 0);
+  }
+  if (!freqs) return QLP_OK;
+  if (capacity < freq_offsets[n_stars]) return QLP_ERR_ARG;
+  for (int32_t s = 0; s < n_stars; ++s) {
+    const int64_t k = freq_offsets[s + 1] - freq_offsets[s];
+    if (k) std::memcpy(freqs + freq_offsets[s], sp[(size_t)s].freqs.data(), sizeof(double) * (size_t)k);
+  }
+  return QLP_OK;
+}
+
 void qlp_bls_plan_destroy(qlp_bls_plan_t* pl) { free_plan(pl); }
 
 int qlp_bls_top_peaks(const qlp_bls_plan_t* pl, void* stream, const float* snr, int32_t n_peaks, double sep,

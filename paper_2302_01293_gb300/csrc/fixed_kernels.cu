@@ -18,19 +18,22 @@
 // memory, no atomics, no exchange between lanes, and the result does not depend
 // on the order of the additions.
 //
+// K0x freq_rec_kernel (plan time): one FreqRec per trial frequency (bins, the
+// edge step in 2^-40 cells, guard band, last edge, the box widths present and
+// the lowest duration index of each).
 // K1x prep_fixed_kernel (1 CTA per exact-path star): weights and the weighted
 // mean in FP64 as the other prep kernels, the integer weights, their exact
-// prefix sums, the per-cell tables (offset of the cell's point, prefix sums at
-// the cell start as a 64-bit group base plus a 32-bit local part), and one
-// FreqRec per trial frequency (bins, the edge step in 2^-56 cells, guard band,
-// last edge, the box widths present and the lowest duration index of each).
+// prefix sums and the per-cell tables (offset of the cell's point, prefix sums at
+// the cell start as a 64-bit group base plus a 32-bit local part).
 // K2x cells_fixed_kernel: persistent; work queue of (star, frequency chunk); the
 // star's table in shared memory; warps take the item's frequencies one at a time.
-// Per frequency the bins are handled 32 at a time (lane = bin): the lanes'
-// S values become U, converted to a double-float (hi, lo) pair per quantity and
-// written to a per-warp ring of two 32-bin blocks (plus a copy of the even block
-// behind the odd one, so that block i and i+1 are always contiguous); the sweep
-// of block i - 1 runs as soon as block i is in the ring.
+// Per frequency the bins are handled 32 at a time (lane = bin): the lanes' S
+// values become U, the exact differences H[x] = U[x + 1] - U[x] are scaled to FP32
+// (w, w d) pairs and written to a per-warp ring of two 32-bin blocks (plus a copy
+// of the even block behind the odd one, so that block i and i+1 are always
+// contiguous); the sweep of the boxes starting in block i - 2 runs once block
+// i - 1 is in the ring. Stars whose table does not fit in shared memory take
+// their edges window by window into a global workspace first (windowed_item).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -309,7 +312,9 @@ __device__ __forceinline__ void sweep_start(const float2* rb, bool kin, int k, i
         const float bs2 = __fmul_rn(bsv, bsv);
         const float lhs = __fmul_rn(s2, bd), rhs = __fmul_rn(bs2, dd);
         const int key = (o << 16) | k;
-        const bool better = rw > 0.f && rw < 1.f && (lhs > rhs || (lhs == rhs && key < bkey));
+        // 0 < r < 1 exactly when r - r^2 > 0: r is a sum of non-negative weights, and
+        // fma(-r, r, r) is r (1 - r) rounded once, positive for every float in (0, 1)
+        const bool better = dd > 0.f && (lhs > rhs || (lhs == rhs && key < bkey));
         bsv = better ? ry : bsv;
         brv = better ? rw : brv;
         bkey = better ? key : bkey;
@@ -330,14 +335,20 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
                                               const longlong2* wsrow) {
   const int nb = R.nb;
   const double f = a.fq[fidx].x;  // for the exact decision near ties
-  const uint32_t band_q = R.band_q;
   const uint32_t wmask = R.wmask;
   const unsigned long long jlow = R.jlow;
   const int mmax = 32 - __clz(wmask);
   const bool all_widths = wmask == 0x7fcu;  // exactly 3 .. 11 bins
   const int gq = (int)(R.gq_bstar >> 13), bstar = (int)(R.gq_bstar & 8191u);
   const int g_end = gq * nb + bstar;
-  const uint32_t k_lo = (uint32_t)R.K, k_hi = (uint32_t)(R.K >> 32);
+  // edge step in 32.32 fixed point, so that the cell and the position in it are the
+  // two halves of G K with no shift. Rounding the 24.40 step to it adds at most
+  // 2^-33 cells per step, G / 2 units of 2^-32 cells at edge G: the guard band
+  // grows by twice that at the last edge (g_end < 2^27: at most 16384 cycles of
+  // 8192 bins; so the band stays below 2^31)
+  const unsigned long long K32 = (R.K + 128ull) >> 8;
+  const uint32_t k_lo = (uint32_t)K32, k_hi = (uint32_t)(K32 >> 32);
+  const uint32_t band_q = R.band_q + (uint32_t)g_end;
   const int nblk = (nb + 31) >> 5;
 
   long long h0w = 0, h0y = 0;  // U of bins 0..31 (the wrap-around values)
@@ -378,14 +389,15 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
         long long aw = 0, ay = 0;
         bool near = false;  // an edge within the guard band of its cell's point
         // every lane takes cnt edges; only in the last one may a lane be past g_end
-        const int cnt = (gq + ((i << 5) > bstar ? 0 : 1) + P - 1) / P;
+        const int cnt0 = gq + ((i << 5) > bstar ? 0 : 1);
+        const int cnt = split ? (cnt0 + P - 1) / P : cnt0;  // no division in full blocks
         auto edge = [&](int G, bool valid, bool clamp) {
-          // tau_G / h in 24.40 fixed point: cell u and position fr (2^-32 of a cell)
+          // tau_G / h in 32.32 fixed point: cell u and position fr (2^-32 of a cell)
           const unsigned long long X =
               (unsigned long long)(uint32_t)G * k_lo + ((unsigned long long)((uint32_t)G * k_hi) << 32);
-          int u = (int)((uint32_t)(X >> 32) >> 8);
+          int u = (int)(uint32_t)(X >> 32);
           if (clamp) u = min(u, nc);
-          const uint32_t fr = (uint32_t)(X >> 8);
+          const uint32_t fr = (uint32_t)X;
           const uint32_t dq = *reinterpret_cast<const uint32_t*>(smem + (uint32_t)u * st4);
           near = near || (uint32_t)(dq - fr + band_q) <= 2u * band_q;
           const int v = u + (dq < fr ? 1 : 0);  // past the cell's point if it lies before tau_G
@@ -428,8 +440,8 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
             for (int g = x == 0 ? nb : x; g <= g_end; g += nb) {
               const unsigned long long X =
                   (unsigned long long)(uint32_t)g * k_lo + ((unsigned long long)((uint32_t)g * k_hi) << 32);
-              const int u = min((int)((uint32_t)(X >> 32) >> 8), nc);
-              const uint32_t fr = (uint32_t)(X >> 8);
+              const int u = min((int)(uint32_t)(X >> 32), nc);
+              const uint32_t fr = (uint32_t)X;
               const uint32_t dq = reinterpret_cast<const uint32_t*>(smem)[u];
               int sel = dq < fr ? 1 : 0;
               if (dq != 0xffffffffu && (uint32_t)(dq - fr + band_q) <= 2u * band_q)

@@ -78,51 +78,56 @@ int64_t cell_of(double tp, double h) {
 
 int sturges_of(int64_t n) { return (int)std::floor(1.0 + 3.322 * std::log10((double)n) + 0.5); }
 
-void plan_one(const qlp_bls_params& p, const double* t, const double* y, const double* dy, int64_t n,
-              double rho, StarPlanHost* out, const Windows* win) {
-  StarPlanHost& s = *out;
+namespace {
+
+// Validation, t' = t - t_min, Pmin and Pmax. False when the star gets no grid
+// (its status says why).
+bool plan_head(const qlp_bls_params& p, const double* t, const double* y, const double* dy, int64_t n,
+               double rho, StarPlanHost& s) {
   s = StarPlanHost();
   const double rho_gcc = (std::isfinite(rho) && rho > 0.0) ? rho : p.rho_default;
   s.rho_kg = rho_gcc * 1000.0;
-  s.tp.reserve((size_t)n);
-  s.y.reserve((size_t)n);
-  s.dy.reserve((size_t)n);
-  std::vector<double> tk;
-  tk.reserve((size_t)n);
-  for (int64_t i = 0; i < n; ++i) {
+  // valid points (finite, dy > 0), checked for non-decreasing t as they are kept
+  int64_t i0 = 0;
+  while (i0 < n && !(std::isfinite(t[i0]) && std::isfinite(y[i0]) && std::isfinite(dy[i0]) && dy[i0] > 0.0)) ++i0;
+  s.tp.resize((size_t)(n - i0));
+  s.y.resize((size_t)(n - i0));
+  s.dy.resize((size_t)(n - i0));
+  const double t_ref = i0 < n ? t[i0] : 0.0;
+  int64_t m = 0;
+  bool sorted = true;
+  double t_prev = t_ref;
+  for (int64_t i = i0; i < n; ++i) {
     if (std::isfinite(t[i]) && std::isfinite(y[i]) && std::isfinite(dy[i]) && dy[i] > 0.0) {
-      tk.push_back(t[i]);
-      s.y.push_back(y[i]);
-      s.dy.push_back(dy[i]);
+      sorted = sorted && !(t[i] < t_prev);
+      t_prev = t[i];
+      s.tp[(size_t)m] = t[i] - t_ref;
+      s.y[(size_t)m] = y[i];
+      s.dy[(size_t)m] = dy[i];
+      ++m;
     }
   }
-  const int64_t m = (int64_t)tk.size();
-  if (m < 2) { s.status = QLP_STAR_TOO_FEW; s.n_valid = m; return; }
-  for (int64_t i = 1; i < m; ++i)
-    if (tk[i] < tk[i - 1]) { s.status = QLP_STAR_UNSORTED; s.n_valid = m; return; }
-  s.n_valid = m;
-  s.t_ref = tk[0];
   s.tp.resize((size_t)m);
-  for (int64_t i = 0; i < m; ++i) s.tp[i] = tk[i] - s.t_ref;
+  s.y.resize((size_t)m);
+  s.dy.resize((size_t)m);
+  if (m < 2) { s.status = QLP_STAR_TOO_FEW; s.n_valid = m; return false; }
+  if (!sorted) { s.status = QLP_STAR_UNSORTED; s.n_valid = m; return false; }
+  s.n_valid = m;
+  s.t_ref = t_ref;
   s.baseline = s.tp[m - 1];
   s.pmin = pmin_of(s.rho_kg, p);
   s.pmax = pmax_of(s.tp.data(), m, p);
-  if (!(s.baseline > 0.0) || !(s.pmin < s.pmax)) { s.status = QLP_STAR_EMPTY_GRID; return; }
-  // the bin edges across the baseline and the longest bin duration (cell path)
-  double edges = 0.0, dmax = 0.0;
+  if (!(s.baseline > 0.0) || !(s.pmin < s.pmax)) { s.status = QLP_STAR_EMPTY_GRID; return false; }
+  return true;
+}
+
+// The frequencies and q_min of one star: the coarse log-period grid, the spacing
+// rule inside windows, or the spacing rule over [1/Pmax, 1/Pmin].
+void grid_one(const qlp_bls_params& p, StarPlanHost& s, const Windows* win) {
   auto add = [&](double f) {  // returns q_min(f)
     const double q = q_min_of(f, s.rho_kg, p);
     s.freqs.push_back(f);
     s.qmins.push_back(q);
-    const int nb = nbins_of(q, p);
-    s.nbins.push_back(nb);
-    s.nbins_max = std::max(s.nbins_max, nb);
-    s.nbins_min = s.nbins.size() == 1 ? nb : std::min(s.nbins_min, nb);
-    s.nbins_sum += (double)nb;
-    const double y = s.baseline * f * (double)nb;
-    s.ymax = std::max(s.ymax, y);
-    edges += std::floor(y) + 3.0;
-    dmax = std::max(dmax, 1.0 / (f * (double)nb));
     return q;
   };
   if (p.grid_mode == 1) {
@@ -161,6 +166,65 @@ void plan_one(const qlp_bls_params& p, const double* t, const double* y, const d
     double f = 1.0 / s.pmax;
     while (f <= fmax) f = f + add(f) / denom;
   }
+}
+
+// The plain grids of up to kChains stars at once. Each star's recurrence is a
+// chain of dependent steps (a cube root, an arcsine and four divisions each), so
+// one chain leaves the core mostly waiting; stepping several independent chains
+// in one loop lets it overlap them. Every chain performs exactly the operations
+// of the one-star loop above, so the grids are the same bit for bit.
+constexpr int kChains = 8;
+void grid_chains(const qlp_bls_params& p, StarPlanHost* const* st, int n) {
+  double f[kChains], fmax[kChains], denom[kChains];
+  bool on[kChains];
+  int left = 0;
+  for (int j = 0; j < kChains; ++j) {
+    on[j] = false;
+    if (j >= n) continue;
+    fmax[j] = 1.0 / st[j]->pmin;
+    denom[j] = p.samples_per_peak * st[j]->baseline;
+    f[j] = 1.0 / st[j]->pmax;
+    on[j] = f[j] <= fmax[j];
+    left += on[j] ? 1 : 0;
+  }
+  while (left > 0) {
+    for (int j = 0; j < kChains; ++j) {
+      if (!on[j]) continue;
+      StarPlanHost& s = *st[j];
+      const double q = q_min_of(f[j], s.rho_kg, p);
+      s.freqs.push_back(f[j]);
+      s.qmins.push_back(q);
+      f[j] = f[j] + q / denom[j];
+      if (!(f[j] <= fmax[j])) {
+        on[j] = false;
+        --left;
+      }
+    }
+  }
+}
+
+// Bins and the grid's sums, the nbins cap, Sturges' bin count, the weight
+// spreads and the cell table.
+void plan_tail(const qlp_bls_params& p, StarPlanHost& s) {
+  const int64_t m = s.n_valid;
+  // the bin edges across the baseline and the longest bin duration (cell path)
+  double edges = 0.0, dmax = 0.0, fnb_min = 0.0;
+  const size_t nf = s.freqs.size();
+  s.nbins.resize(nf);
+  for (size_t k = 0; k < nf; ++k) {
+    const double f = s.freqs[k];
+    const int nb = nbins_of(s.qmins[k], p);
+    s.nbins[k] = nb;
+    s.nbins_max = std::max(s.nbins_max, nb);
+    s.nbins_min = k == 0 ? nb : std::min(s.nbins_min, nb);
+    s.nbins_sum += (double)nb;
+    const double y = s.baseline * f * (double)nb;
+    s.ymax = std::max(s.ymax, y);
+    edges += std::floor(y) + 3.0;
+    fnb_min = k == 0 ? f * (double)nb : std::min(fnb_min, f * (double)nb);
+  }
+  // longest bin duration: max of 1 / (f nbins) = 1 / min(f nbins) (division is monotonic)
+  if (nf > 0) dmax = 1.0 / fnb_min;
   if (s.freqs.empty()) { s.status = QLP_STAR_EMPTY_GRID; return; }
   if (s.nbins_max > p.nbins_cap) {
     s.status = QLP_STAR_NBINS_CAP;
@@ -214,6 +278,16 @@ void plan_one(const qlp_bls_params& p, const double* t, const double* y, const d
   }
 }
 
+}  // namespace
+
+void plan_one(const qlp_bls_params& p, const double* t, const double* y, const double* dy, int64_t n,
+              double rho, StarPlanHost* out, const Windows* win) {
+  StarPlanHost& s = *out;
+  if (!plan_head(p, t, y, dy, n, rho, s)) return;
+  grid_one(p, s, win);
+  plan_tail(p, s);
+}
+
 void parallel_stars(const qlp_bls_params& p, int32_t n_stars, const std::function<void(int32_t)>& fn) {
   int nth = p.n_threads > 0 ? p.n_threads : (int)std::thread::hardware_concurrency();
   nth = std::max(1, std::min(nth, std::max(1, n_stars)));
@@ -234,16 +308,33 @@ void plan_all(const qlp_bls_params& p, int32_t n_stars, const int64_t* offsets, 
               const double* y, const double* dy, const double* rho, std::vector<StarPlanHost>* out,
               const int64_t* win_off, const double* win_lo, const double* win_hi) {
   out->assign((size_t)n_stars, StarPlanHost());
-  parallel_stars(p, n_stars, [&](int32_t s) {
-    const int64_t a = offsets[s], b = offsets[s + 1];
-    const double r = rho ? rho[s] : NAN;
-    Windows w;
-    if (win_off) {
-      w.lo = win_lo + win_off[s];
-      w.hi = win_hi + win_off[s];
-      w.n = win_off[s + 1] - win_off[s];
+  if (win_off || p.grid_mode == 1) {
+    parallel_stars(p, n_stars, [&](int32_t s) {
+      const int64_t a = offsets[s], b = offsets[s + 1];
+      const double r = rho ? rho[s] : NAN;
+      Windows w;
+      if (win_off) {
+        w.lo = win_lo + win_off[s];
+        w.hi = win_hi + win_off[s];
+        w.n = win_off[s + 1] - win_off[s];
+      }
+      plan_one(p, t + a, y + a, dy + a, b - a, r, &(*out)[(size_t)s], win_off ? &w : nullptr);
+    });
+    return;
+  }
+  // plain grids: groups of kChains consecutive stars, their recurrences interleaved
+  const int32_t n_groups = (n_stars + kChains - 1) / kChains;
+  parallel_stars(p, n_groups, [&](int32_t g) {
+    StarPlanHost* st[kChains];
+    int n = 0;
+    const int32_t s1 = std::min(n_stars, (g + 1) * kChains);
+    for (int32_t s = g * kChains; s < s1; ++s) {
+      const int64_t a = offsets[s], b = offsets[s + 1];
+      StarPlanHost& h = (*out)[(size_t)s];
+      if (plan_head(p, t + a, y + a, dy + a, b - a, rho ? rho[s] : NAN, h)) st[n++] = &h;
     }
-    plan_one(p, t + a, y + a, dy + a, b - a, r, &(*out)[(size_t)s], win_off ? &w : nullptr);
+    grid_chains(p, st, n);
+    for (int j = 0; j < n; ++j) plan_tail(p, *st[j]);
   });
 }
 

@@ -159,7 +159,7 @@ struct FixedArgs {
   int32_t nq;
   const double* tp;
   const uint32_t* dt;
-  const int2* loc;
+  const int2* loc;             // layout as in PrepFixedArgs: base + loc = prefix sum
   const longlong2* base;
   const int32_t* gidx;
   int32_t* cursor;

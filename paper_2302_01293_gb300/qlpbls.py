@@ -142,6 +142,9 @@ def lib():
                                             _P(_i32), _P(_d), _P(_d), _P(_d), _P(_d), _vp, _vp, _i64,
                                             _P(_i64)]
             L.qlp_bls_star_grid.restype = ctypes.c_int
+            L.qlp_bls_batch_grid.argtypes = [_P(CParams), _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                             _i64]
+            L.qlp_bls_batch_grid.restype = ctypes.c_int
             L.qlp_bls_search_static.argtypes = [_P(CParams), _i32, _vp, _vp, _vp, _d, _i32, _vp,
                                                 _vp, _vp, _vp, _vp, _vp, _vp, _vp]
             L.qlp_bls_search_static.restype = ctypes.c_int
@@ -488,6 +491,27 @@ def star_grid(t, y, dy, rho=float("nan"), params: Params | None = None, windows=
            "qlp_bls_star_grid")
     return dict(status=int(st.value), pmin=pmin.value, pmax=pmax.value, t_ref=tref.value,
                 baseline=base.value, freqs=freqs, qmins=qmins)
+
+
+def batch_grid(offsets, t, y, dy, rho=None, params: Params | None = None):
+    """qlp_bls_batch_grid: the trial-frequency grids of a batch from the batch
+    planner (host only); returns (star_status, freq_offsets, freqs)."""
+    L = lib()
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    n = offsets.shape[0] - 1
+    t = np.ascontiguousarray(t, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    dy = np.ascontiguousarray(dy, np.float64)
+    rho = None if rho is None else np.ascontiguousarray(rho, np.float64)
+    cp = (params or Params()).to_c()
+    status = np.zeros(n, np.int32)
+    foff = np.zeros(n + 1, np.int64)
+    args = [ctypes.byref(cp), n, _np_ptr(offsets), _np_ptr(t), _np_ptr(y), _np_ptr(dy), _np_ptr(rho),
+            _np_ptr(status), _np_ptr(foff)]
+    _check(L.qlp_bls_batch_grid(*args, None, 0), "qlp_bls_batch_grid")
+    freqs = np.zeros(int(foff[-1]), np.float64)
+    _check(L.qlp_bls_batch_grid(*args, _np_ptr(freqs), freqs.shape[0]), "qlp_bls_batch_grid")
+    return status, foff, freqs
 
 
 def search_static(tp, y, dy, baseline, freqs, qmins, out, params: Params | None = None, stream=None):

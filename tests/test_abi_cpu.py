@@ -84,6 +84,31 @@ def test_planner_grid_is_bit_identical_to_oracle(which):
         assert np.array_equal(g["qmins"], o.qmin)
 
 
+def test_batch_planner_equals_oracle_star_by_star():
+    """The batch planner (several stars' grid recurrences stepped together on each
+    host thread) gives every star the oracle's grid bit for bit, in a batch that
+    mixes valid stars with rejected ones (unsorted, one point, NaN-only) and whose
+    size is not a multiple of the interleaving width."""
+    b = synth.uneven_single_sector(n_stars=11, seed=31)
+    t = [b.star(s)[0] for s in range(b.n_stars)]
+    y = [b.star(s)[1] for s in range(b.n_stars)]
+    dy = [b.star(s)[2] for s in range(b.n_stars)]
+    rho = list(b.rho)
+    base = np.linspace(2000, 2010, 40)
+    for tt, yy in ((base[::-1], np.ones(40)), (base[:1], np.ones(1)), (base, np.full(40, np.nan))):
+        t.insert(3, tt); y.insert(3, yy); dy.insert(3, np.full(tt.shape[0], 1e-3)); rho.insert(3, float("nan"))
+    off = np.concatenate([[0], np.cumsum([x.shape[0] for x in t])])
+    status, foff, freqs = qlpbls.batch_grid(off, np.concatenate(t), np.concatenate(y), np.concatenate(dy),
+                                            np.array(rho))
+    assert sorted(status[3:6].tolist()) == sorted([qlpbls.STAR_UNSORTED, qlpbls.STAR_TOO_FEW,
+                                                   qlpbls.STAR_TOO_FEW])
+    for s in range(len(t)):
+        o = oracle.plan_star(t[s], y[s], dy[s], rho[s], 1.0)
+        assert status[s] == o.status
+        got = freqs[foff[s]:foff[s + 1]]
+        assert np.array_equal(got, o.freqs if o.status == 0 else np.zeros(0))
+
+
 def test_planner_status_flags_match_oracle():
     t = np.linspace(0, 10, 50) + 2000.0
     y = np.ones(50)
