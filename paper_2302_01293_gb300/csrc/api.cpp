@@ -64,7 +64,8 @@ struct qlp_bls_plan {
   std::vector<int32_t> status;
   std::vector<int64_t> f_off;     // n_stars + 1
   std::vector<double> freqs;      // all stars
-  int64_t n_points = 0;
+  int64_t n_points = 0;       // valid points of the batch
+  int64_t n_pts_alloc = 0;    // raw points: device point arrays (star s at its raw offset)
   double work = 0.0;              // sum N_s * n_f,s
   double work_points = 0.0;       // point-frequency pairs folded by the point path
   double work_cells = 0.0;        // point-frequency pairs served by the cell path
@@ -295,8 +296,20 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
 
   using clk = std::chrono::steady_clock;
   const auto c0 = clk::now();
+  // the valid points go straight into the upload arrays, each star at its raw
+  // offset (a star's entries past its valid count are zero and never read)
+  const int64_t npt_raw = n_stars > 0 ? offsets[n_stars] - offsets[0] : 0;
+  const size_t npt_alloc = (size_t)std::max<int64_t>(npt_raw, 1);
+  std::unique_ptr<double[]> tp_all(new (std::nothrow) double[npt_alloc]);
+  std::unique_ptr<double[]> y_all(new (std::nothrow) double[npt_alloc]);
+  std::unique_ptr<double[]> dy_all(new (std::nothrow) double[npt_alloc]);
+  if (!tp_all || !y_all || !dy_all) return QLP_ERR_NOMEM;
+  PointDst pdst;
+  pdst.tp = tp_all.get();
+  pdst.y = y_all.get();
+  pdst.dy = dy_all.get();
   std::vector<StarPlanHost> sp;
-  plan_all(p, n_stars, offsets, t, y, dy, rho, &sp, win_off, win_lo, win_hi);
+  plan_all(p, n_stars, offsets, t, y, dy, rho, &sp, win_off, win_lo, win_hi, &pdst);
   const auto c1 = clk::now();
 
   qlp_bls_plan_t* pl = new (std::nothrow) qlp_bls_plan_t();
@@ -304,6 +317,7 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   pl->times[0] = std::chrono::duration<double>(c1 - c0).count();
   pl->p = p;
   pl->n_stars = n_stars;
+  pl->n_pts_alloc = npt_raw;
   pl->nq = n_q_of(p);
   for (int j = 0; j < pl->nq; ++j) pl->E[j] = std::exp(j * p.dlogq);
 
@@ -356,7 +370,7 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
       W.n_win = (int32_t)((h.n_cells + c - 1) / c);
     }
     const bool old_fits = cell_smem(W.cap, h.nbins_max) <= (size_t)budget;
-    const double pp_work = (double)h.freqs.size() * (double)round32((int64_t)h.tp.size());
+    const double pp_work = (double)h.freqs.size() * (double)round32(h.n_valid);
     // exact path: at least 32 bins, at most 2^14 cycles and 2^21 points (the integer
     // prefix sums stay below 2^62), no weight or weighted residual above 256 times
     // the star's mean (the integer scale follows the largest one: a single extreme
@@ -365,7 +379,7 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
     // a global workspace)
     const bool fixed_ok = p.sum_mode == QLP_SUM_FIXED && p.bin_mode == QLP_BIN_SHARED && h.nbins_min >= 32 &&
                           h.w_spread <= 256.0 && h.wd_spread <= 256.0 &&
-                          h.baseline * h.freqs.back() <= 16384.0 && h.tp.size() <= ((size_t)1 << 21) &&
+                          h.baseline * h.freqs.back() <= 16384.0 && h.n_valid <= ((int64_t)1 << 21) &&
                           (size_t)32 * 16 * ((h.nbins_max + 31) / 32) <= (size_t)kFixedWsBlock * 16;
     if (fixed_ok && (p.method == 2 || h.cells_work < 2.0 * pp_work)) {
       const bool fwhole = p.cell_window > 0 ? p.cell_window >= h.n_cells
@@ -408,10 +422,10 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
     StarDev& d = stars[(size_t)s];
     std::memset(&d, 0, sizeof(d));
     const bool ok = h.status == 0;
-    d.pt_off = npt;
+    d.pt_off = offsets[s] - offsets[0];
     d.pad_off = npad;
     d.f_off = nf;
-    d.n_pts = ok ? (int32_t)h.tp.size() : 0;
+    d.n_pts = ok ? (int32_t)h.n_valid : 0;
     d.n_f = ok ? (int32_t)h.freqs.size() : 0;
     d.status = h.status;
     d.sturges_nb = h.sturges_nb;
@@ -464,22 +478,14 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   pl->n_points = npt;
   pl->n_cell_stars = (int32_t)(cell_stars.size() + fixed_stars.size());
   pl->n_fixed_stars = (int32_t)fixed_stars.size();
-  // staging buffers without zero fill, filled star by star in parallel
-  const size_t npt_alloc = (size_t)std::max<int64_t>(npt, 1), nf_alloc = (size_t)std::max<int64_t>(nf, 1);
-  std::unique_ptr<double[]> tp_all(new (std::nothrow) double[npt_alloc]);
-  std::unique_ptr<double[]> y_all(new (std::nothrow) double[npt_alloc]);
-  std::unique_ptr<double[]> dy_all(new (std::nothrow) double[npt_alloc]);
+  // frequency staging without zero fill, filled star by star in parallel
+  const size_t nf_alloc = (size_t)std::max<int64_t>(nf, 1);
   std::unique_ptr<double2[]> fq(new (std::nothrow) double2[nf_alloc]);
-  if (!tp_all || !y_all || !dy_all || !fq) { delete pl; return QLP_ERR_NOMEM; }
+  if (!fq) { delete pl; return QLP_ERR_NOMEM; }
   pl->freqs.resize((size_t)nf);
   parallel_stars(p, n_stars, [&](int32_t s) {
     const StarPlanHost& h = sp[(size_t)s];
     const StarDev& d = stars[(size_t)s];
-    if (d.n_pts > 0) {
-      std::memcpy(&tp_all[(size_t)d.pt_off], h.tp.data(), sizeof(double) * (size_t)d.n_pts);
-      std::memcpy(&y_all[(size_t)d.pt_off], h.y.data(), sizeof(double) * (size_t)d.n_pts);
-      std::memcpy(&dy_all[(size_t)d.pt_off], h.dy.data(), sizeof(double) * (size_t)d.n_pts);
-    }
     for (int32_t k = 0; k < d.n_f; ++k) {
       fq[(size_t)(d.f_off + k)] = make_double2(h.freqs[(size_t)k], h.qmins[(size_t)k]);
       pl->freqs[(size_t)(d.f_off + k)] = h.freqs[(size_t)k];
@@ -614,9 +620,9 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   if (e == cudaSuccess && !sorted.empty()) e = cudaMemcpyAsync(pl->d_items, sorted.data(), sizeof(WorkItem) * sorted.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !cell_stars.empty()) e = cudaMemcpyAsync(pl->d_cell_stars, cell_stars.data(), sizeof(int32_t) * cell_stars.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !fixed_stars.empty()) e = cudaMemcpyAsync(pl->d_fixed_stars, fixed_stars.data(), sizeof(int32_t) * fixed_stars.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(pl->d_tp, tp_all.get(), sizeof(double) * (size_t)npt, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(pl->d_y, y_all.get(), sizeof(double) * (size_t)npt, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(pl->d_dy, dy_all.get(), sizeof(double) * (size_t)npt, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && npt_raw > 0) e = cudaMemcpyAsync(pl->d_tp, tp_all.get(), sizeof(double) * (size_t)npt_raw, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && npt_raw > 0) e = cudaMemcpyAsync(pl->d_y, y_all.get(), sizeof(double) * (size_t)npt_raw, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && npt_raw > 0) e = cudaMemcpyAsync(pl->d_dy, dy_all.get(), sizeof(double) * (size_t)npt_raw, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_ctl, 0, 4 * sizeof(int32_t), st);
   if (e == cudaSuccess && !fixed_stars.empty()) {  // per-frequency records of the exact path
     const int le = launch_freq_recs(fixed_args(pl), stream);
@@ -1066,7 +1072,7 @@ int qlp_bls_candidate_stats(qlp_bls_plan_t* pl, void* stream, const qlp_bls_best
   if (pl->n_stars > 0 && (!best || !out)) return QLP_ERR_ARG;
   if (pl->n_stars == 0) return QLP_OK;
   if (!pl->d_wrec) {
-    const int rc = dev_alloc(&pl->d_wrec, (size_t)std::max<int64_t>(pl->n_points, 1));
+    const int rc = dev_alloc(&pl->d_wrec, (size_t)std::max<int64_t>(pl->n_pts_alloc, 1));
     if (rc) return rc;
   }
   StatsArgs a{};

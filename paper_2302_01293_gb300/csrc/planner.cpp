@@ -16,10 +16,14 @@
 //    T = t_max - t_min, while f <= 1/Pmin;
 //  * bins: nbins(f) = ceil(noverlap / q_min(f)).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
-#include <utility>
+#include <condition_variable>
 #include <cstdint>
+#include <mutex>
+#include <pthread.h>
 #include <thread>
+#include <utility>
 #include <vector>
 
 #include "planner.h"
@@ -83,16 +87,29 @@ namespace {
 // Validation, t' = t - t_min, Pmin and Pmax. False when the star gets no grid
 // (its status says why).
 bool plan_head(const qlp_bls_params& p, const double* t, const double* y, const double* dy, int64_t n,
-               double rho, StarPlanHost& s) {
+               double rho, StarPlanHost& s, const PointDst* dst) {
   s = StarPlanHost();
   const double rho_gcc = (std::isfinite(rho) && rho > 0.0) ? rho : p.rho_default;
   s.rho_kg = rho_gcc * 1000.0;
   // valid points (finite, dy > 0), checked for non-decreasing t as they are kept
   int64_t i0 = 0;
   while (i0 < n && !(std::isfinite(t[i0]) && std::isfinite(y[i0]) && std::isfinite(dy[i0]) && dy[i0] > 0.0)) ++i0;
-  s.tp.resize((size_t)(n - i0));
-  s.y.resize((size_t)(n - i0));
-  s.dy.resize((size_t)(n - i0));
+  double *otp, *oy, *ody;
+  if (dst) {
+    otp = dst->tp;
+    oy = dst->y;
+    ody = dst->dy;
+    s.ext_tp = otp;
+    s.ext_y = oy;
+    s.ext_dy = ody;
+  } else {
+    s.tp.resize((size_t)(n - i0));
+    s.y.resize((size_t)(n - i0));
+    s.dy.resize((size_t)(n - i0));
+    otp = s.tp.data();
+    oy = s.y.data();
+    ody = s.dy.data();
+  }
   const double t_ref = i0 < n ? t[i0] : 0.0;
   int64_t m = 0;
   bool sorted = true;
@@ -101,22 +118,26 @@ bool plan_head(const qlp_bls_params& p, const double* t, const double* y, const 
     if (std::isfinite(t[i]) && std::isfinite(y[i]) && std::isfinite(dy[i]) && dy[i] > 0.0) {
       sorted = sorted && !(t[i] < t_prev);
       t_prev = t[i];
-      s.tp[(size_t)m] = t[i] - t_ref;
-      s.y[(size_t)m] = y[i];
-      s.dy[(size_t)m] = dy[i];
+      otp[m] = t[i] - t_ref;
+      oy[m] = y[i];
+      ody[m] = dy[i];
       ++m;
     }
   }
-  s.tp.resize((size_t)m);
-  s.y.resize((size_t)m);
-  s.dy.resize((size_t)m);
+  if (dst) {
+    for (int64_t i = m; i < n; ++i) otp[i] = oy[i] = ody[i] = 0.0;
+  } else {
+    s.tp.resize((size_t)m);
+    s.y.resize((size_t)m);
+    s.dy.resize((size_t)m);
+  }
   if (m < 2) { s.status = QLP_STAR_TOO_FEW; s.n_valid = m; return false; }
   if (!sorted) { s.status = QLP_STAR_UNSORTED; s.n_valid = m; return false; }
   s.n_valid = m;
   s.t_ref = t_ref;
-  s.baseline = s.tp[m - 1];
+  s.baseline = otp[m - 1];
   s.pmin = pmin_of(s.rho_kg, p);
-  s.pmax = pmax_of(s.tp.data(), m, p);
+  s.pmax = pmax_of(otp, m, p);
   if (!(s.baseline > 0.0) || !(s.pmin < s.pmax)) { s.status = QLP_STAR_EMPTY_GRID; return false; }
   return true;
 }
@@ -207,6 +228,9 @@ void grid_chains(const qlp_bls_params& p, StarPlanHost* const* st, int n) {
 // spreads and the cell table.
 void plan_tail(const qlp_bls_params& p, StarPlanHost& s) {
   const int64_t m = s.n_valid;
+  const double* tp = s.tp_data();
+  const double* yv = s.y_data();
+  const double* dyv = s.dy_data();
   // the bin edges across the baseline and the longest bin duration (cell path)
   double edges = 0.0, dmax = 0.0, fnb_min = 0.0;
   const size_t nf = s.freqs.size();
@@ -240,15 +264,15 @@ void plan_tail(const qlp_bls_params& p, StarPlanHost& s) {
   {
     double isum = 0.0, iysum = 0.0, imax = 0.0;
     for (int64_t i = 0; i < m; ++i) {
-      const double inv = 1.0 / (s.dy[i] * s.dy[i]);
+      const double inv = 1.0 / (dyv[i] * dyv[i]);
       isum += inv;
-      iysum += inv * s.y[i];
+      iysum += inv * yv[i];
       imax = std::max(imax, inv);
     }
     const double ybar = iysum / isum;
     double dsum = 0.0, dmax = 0.0;
     for (int64_t i = 0; i < m; ++i) {
-      const double v = std::fabs((s.y[i] - ybar) / (s.dy[i] * s.dy[i]));
+      const double v = std::fabs((yv[i] - ybar) / (dyv[i] * dyv[i]));
       dsum += v;
       dmax = std::max(dmax, v);
     }
@@ -258,13 +282,13 @@ void plan_tail(const qlp_bls_params& p, StarPlanHost& s) {
 
   // cell path: smallest spacing, cells just narrower, one point per cell
   double min_gap = INFINITY;
-  for (int64_t i = 1; i < m; ++i) min_gap = std::min(min_gap, s.tp[i] - s.tp[i - 1]);
+  for (int64_t i = 1; i < m; ++i) min_gap = std::min(min_gap, tp[i] - tp[i - 1]);
   if (min_gap > 0.0 && std::isfinite(min_gap) && s.baseline / min_gap < 4.0e6) {
     const double h = min_gap * 0.999;
     bool ok = true;
     int64_t prev = -1;
     for (int64_t i = 0; i < m && ok; ++i) {
-      const int64_t u = cell_of(s.tp[i], h);
+      const int64_t u = cell_of(tp[i], h);
       ok = u > prev;
       prev = u;
     }
@@ -281,12 +305,102 @@ void plan_tail(const qlp_bls_params& p, StarPlanHost& s) {
 }  // namespace
 
 void plan_one(const qlp_bls_params& p, const double* t, const double* y, const double* dy, int64_t n,
-              double rho, StarPlanHost* out, const Windows* win) {
+              double rho, StarPlanHost* out, const Windows* win, const PointDst* dst) {
   StarPlanHost& s = *out;
-  if (!plan_head(p, t, y, dy, n, rho, s)) return;
+  if (!plan_head(p, t, y, dy, n, rho, s, dst)) return;
   grid_one(p, s, win);
   plan_tail(p, s);
 }
+
+namespace {
+
+// Process-wide pool of host worker threads for the planner: started on first
+// use, one fewer than the cores (the calling thread works too). A job is a range
+// of task indices taken one at a time from an atomic counter, so stars of very
+// different grid lengths balance across threads. One job runs at a time; a call
+// that finds the pool busy (another host thread planning) starts threads of its
+// own instead.
+class HostPool {
+ public:
+  static HostPool& get() {
+    // never destroyed (workers may outlive static teardown); a forked child, which
+    // has none of the parent's threads, starts a pool of its own
+    static std::once_flag once;
+    std::call_once(once, [] { pthread_atfork(nullptr, nullptr, [] { instance().store(nullptr); }); });
+    HostPool* p = instance().load();
+    if (!p) {
+      std::lock_guard<std::mutex> lk(create_mu());
+      p = instance().load();
+      if (!p) {
+        p = new HostPool();
+        instance().store(p);
+      }
+    }
+    return *p;
+  }
+  int workers() const { return (int)th_.size(); }
+  bool try_run(int32_t n_tasks, int helpers, const std::function<void(int32_t)>& fn) {
+    std::unique_lock<std::mutex> job(job_mu_, std::try_to_lock);
+    if (!job.owns_lock()) return false;
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      fn_ = &fn;
+      n_tasks_ = n_tasks;
+      next_.store(0);
+      helpers_ = std::min(helpers, workers());
+      active_ = helpers_;
+      ++gen_;
+    }
+    cv_.notify_all();
+    work();
+    std::unique_lock<std::mutex> lk(mu_);
+    done_cv_.wait(lk, [&] { return active_ == 0; });
+    fn_ = nullptr;
+    return true;
+  }
+
+ private:
+  HostPool() {
+    const int n = std::max(0, (int)std::thread::hardware_concurrency() - 1);
+    for (int i = 0; i < n; ++i) th_.emplace_back([this, i] { loop(i); });
+    for (auto& x : th_) x.detach();
+  }
+  void work() {
+    for (int32_t k = next_.fetch_add(1); k < n_tasks_; k = next_.fetch_add(1)) (*fn_)(k);
+  }
+  void loop(int idx) {
+    uint64_t seen = 0;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return gen_ != seen; });
+        seen = gen_;
+        if (idx >= helpers_) continue;  // this job asked for fewer threads
+      }
+      work();
+      std::lock_guard<std::mutex> lk(mu_);
+      if (--active_ == 0) done_cv_.notify_all();
+    }
+  }
+  static std::atomic<HostPool*>& instance() {
+    static std::atomic<HostPool*> p{nullptr};
+    return p;
+  }
+  static std::mutex& create_mu() {
+    static std::mutex m;
+    return m;
+  }
+  std::vector<std::thread> th_;
+  std::mutex job_mu_, mu_;
+  std::condition_variable cv_, done_cv_;
+  const std::function<void(int32_t)>* fn_ = nullptr;
+  int32_t n_tasks_ = 0;
+  std::atomic<int32_t> next_{0};
+  int helpers_ = 0, active_ = 0;
+  uint64_t gen_ = 0;
+};
+
+}  // namespace
 
 void parallel_stars(const qlp_bls_params& p, int32_t n_stars, const std::function<void(int32_t)>& fn) {
   int nth = p.n_threads > 0 ? p.n_threads : (int)std::thread::hardware_concurrency();
@@ -295,6 +409,7 @@ void parallel_stars(const qlp_bls_params& p, int32_t n_stars, const std::functio
     for (int32_t s = 0; s < n_stars; ++s) fn(s);
     return;
   }
+  if (HostPool::get().try_run(n_stars, nth - 1, fn)) return;
   std::vector<std::thread> th;
   th.reserve((size_t)nth);
   for (int i = 0; i < nth; ++i)
@@ -306,8 +421,17 @@ void parallel_stars(const qlp_bls_params& p, int32_t n_stars, const std::functio
 
 void plan_all(const qlp_bls_params& p, int32_t n_stars, const int64_t* offsets, const double* t,
               const double* y, const double* dy, const double* rho, std::vector<StarPlanHost>* out,
-              const int64_t* win_off, const double* win_lo, const double* win_hi) {
+              const int64_t* win_off, const double* win_lo, const double* win_hi, const PointDst* dst) {
   out->assign((size_t)n_stars, StarPlanHost());
+  // star s's points go to the caller's arrays at its raw offset, when given
+  auto dst_of = [&](int32_t s, PointDst* d) -> const PointDst* {
+    if (!dst) return nullptr;
+    const int64_t o = offsets[s] - offsets[0];
+    d->tp = dst->tp + o;
+    d->y = dst->y + o;
+    d->dy = dst->dy + o;
+    return d;
+  };
   if (win_off || p.grid_mode == 1) {
     parallel_stars(p, n_stars, [&](int32_t s) {
       const int64_t a = offsets[s], b = offsets[s + 1];
@@ -318,7 +442,8 @@ void plan_all(const qlp_bls_params& p, int32_t n_stars, const int64_t* offsets, 
         w.hi = win_hi + win_off[s];
         w.n = win_off[s + 1] - win_off[s];
       }
-      plan_one(p, t + a, y + a, dy + a, b - a, r, &(*out)[(size_t)s], win_off ? &w : nullptr);
+      PointDst d;
+      plan_one(p, t + a, y + a, dy + a, b - a, r, &(*out)[(size_t)s], win_off ? &w : nullptr, dst_of(s, &d));
     });
     return;
   }
@@ -331,7 +456,8 @@ void plan_all(const qlp_bls_params& p, int32_t n_stars, const int64_t* offsets, 
     for (int32_t s = g * kChains; s < s1; ++s) {
       const int64_t a = offsets[s], b = offsets[s + 1];
       StarPlanHost& h = (*out)[(size_t)s];
-      if (plan_head(p, t + a, y + a, dy + a, b - a, rho ? rho[s] : NAN, h)) st[n++] = &h;
+      PointDst d;
+      if (plan_head(p, t + a, y + a, dy + a, b - a, rho ? rho[s] : NAN, h, dst_of(s, &d))) st[n++] = &h;
     }
     grid_chains(p, st, n);
     for (int j = 0; j < n; ++j) plan_tail(p, *st[j]);

@@ -17,7 +17,14 @@ struct StarPlanHost {
   double pmin = 0.0;
   double pmax = 0.0;
   double rho_kg = 0.0;
-  std::vector<double> tp, y, dy;   // valid points, t' = t - t_ref
+  std::vector<double> tp, y, dy;   // valid points, t' = t - t_ref (unless ext_tp is set)
+  // the valid points in a caller's arrays instead (batch planner with staging arrays)
+  const double* ext_tp = nullptr;
+  const double* ext_y = nullptr;
+  const double* ext_dy = nullptr;
+  const double* tp_data() const { return ext_tp ? ext_tp : tp.data(); }
+  const double* y_data() const { return ext_tp ? ext_y : y.data(); }
+  const double* dy_data() const { return ext_tp ? ext_dy : dy.data(); }
   std::vector<double> freqs;       // trial frequencies (1/day)
   std::vector<double> qmins;       // q_min at each frequency
   std::vector<int32_t> nbins;      // nbins at each frequency
@@ -40,6 +47,14 @@ struct StarPlanHost {
   int32_t grid_k0 = -1;            // coarse grid: bin index of the first (lowest) frequency
 };
 
+// Arrays that receive a star's valid points (t', y, dy), at least as long as its
+// raw point count; entries past the valid count are set to zero.
+struct PointDst {
+  double* tp = nullptr;
+  double* y = nullptr;
+  double* dy = nullptr;
+};
+
 // Frequency windows [lo, hi] of one star (1/day) that restrict its grid.
 struct Windows {
   const double* lo = nullptr;
@@ -56,13 +71,13 @@ double pmin_of(double rho_kg, const qlp_bls_params& p);
 double pmax_of(const double* tp, int64_t n, const qlp_bls_params& p);
 int sturges_of(int64_t n);
 void plan_one(const qlp_bls_params& p, const double* t, const double* y, const double* dy, int64_t n,
-              double rho, StarPlanHost* out, const Windows* win = nullptr);
+              double rho, StarPlanHost* out, const Windows* win = nullptr, const PointDst* dst = nullptr);
 // Runs fn(s) for every star s on the planner's threads (p.n_threads, 0 = all cores).
 void parallel_stars(const qlp_bls_params& p, int32_t n_stars, const std::function<void(int32_t)>& fn);
 
 void plan_all(const qlp_bls_params& p, int32_t n_stars, const int64_t* offsets, const double* t,
               const double* y, const double* dy, const double* rho, std::vector<StarPlanHost>* out,
               const int64_t* win_off = nullptr, const double* win_lo = nullptr,
-              const double* win_hi = nullptr);
+              const double* win_hi = nullptr, const PointDst* dst = nullptr);
 
 }  // namespace qlp

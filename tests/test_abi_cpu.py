@@ -159,3 +159,35 @@ def test_window_grid_is_bit_identical_to_oracle():
         o = oracle.plan_star(t, y, dy, float(b.rho[s]), 1.0, windows=wins)
         assert g["status"] == o.status
         assert np.array_equal(g["freqs"], o.freqs) and np.array_equal(g["qmins"], o.qmin)
+
+
+@pytest.mark.filterwarnings("ignore:This process .* is multi-threaded:DeprecationWarning")
+def test_batch_planner_after_fork():
+    """The planner's host thread pool does not survive fork(); a child process
+    that plans after its parent did gets a pool of its own (no hang) and the
+    same grids."""
+    import os, time
+    b = synth.uneven_single_sector(n_stars=9, seed=32)
+    args = (b.offsets, b.t, b.y, b.dy, b.rho)
+    _, foff, freqs = qlpbls.batch_grid(*args)  # starts the pool in this process
+    pid = os.fork()
+    if pid == 0:  # child: plan again, exit 0 on equal grids
+        code = 1
+        try:
+            _, f2, q2 = qlpbls.batch_grid(*args)
+            code = 0 if (np.array_equal(f2, foff) and np.array_equal(q2, freqs)) else 1
+        finally:
+            os._exit(code)
+    deadline = time.time() + 120
+    status = None
+    while time.time() < deadline:
+        done, st = os.waitpid(pid, os.WNOHANG)
+        if done:
+            status = st
+            break
+        time.sleep(0.05)
+    if status is None:
+        os.kill(pid, 9)
+        os.waitpid(pid, 0)
+        pytest.fail("the child's planner did not finish")
+    assert os.WIFEXITED(status) and os.WEXITSTATUS(status) == 0
