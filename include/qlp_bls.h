@@ -155,7 +155,10 @@ void qlp_bls_params_default(qlp_bls_params* p);
  * Host-side work: validation, Pmin (a = pmin_aR R*), Pmax (longest continuous
  * stretch, or half of it when no gap exceeds gap_days), the frequency grid
  * f_{k+1} = f_k + q_min(f_k)/(spp T) from 1/Pmax to 1/Pmin in FP64, and the
- * device work list; multithreaded over stars.
+ * device work list; multithreaded over stars. Returns once the uploads are
+ * complete (the host arrays may then be reused); the plan's last device work
+ * (control words, per-frequency records) may still be queued on `stream`, and
+ * every later call on the plan orders itself after it on its own stream.
  */
 int qlp_bls_plan(const qlp_bls_params* p, int32_t n_stars, const int64_t* offsets,
                  const double* t, const double* y, const double* dy,
@@ -207,7 +210,7 @@ int qlp_bls_plan_exact_stats(const qlp_bls_plan_t* plan, int32_t* n_exact_stars,
  * seconds the plan's construction spent in four phases, written to seconds4[0..3]:
  * the host grid and per-star plans (Sec. 2.1 rules, all stars in parallel), the
  * host staging of flat arrays and work items, device allocation, and the uploads
- * with the plan-time kernels up to the final stream synchronisation.
+ * up to their completion (the plan-time kernels are queued after them).
  * QLP_ERR_ARG for a NULL plan or array.
  */
 int qlp_bls_plan_times(const qlp_bls_plan_t* plan, double* seconds4);
@@ -241,7 +244,11 @@ int qlp_bls_kernel_time(qlp_bls_plan_t* plan, float* ms, int32_t* kernel);
  *  phase_bin uint32: first bin k of that window; 0xFFFFFFFF when none. May be NULL.
  *  s_best, r_best  float: s and r of that window. May be NULL.
  * Runs one persistent kernel over a device work queue of (star, frequency-chunk)
- * items. Returns QLP_ERR_DEVICE if a device bound was hit.
+ * items, ordered on `stream` after the plan's own device work. Returns
+ * QLP_ERR_DEVICE if a device bound was hit. Inside a stream capture of the
+ * caller's own it returns QLP_ERR_CUDA unless the plan's own device work is
+ * known to be complete (after qlp_bls_device_status or qlp_bls_graph_capture on
+ * this plan); qlp_bls_graph_capture handles that itself.
  */
 int qlp_bls_search(qlp_bls_plan_t* plan, void* stream, float* sr, uint8_t* qidx,
                    uint32_t* phase_bin, float* s_best, float* r_best);
@@ -415,8 +422,9 @@ int qlp_bls_search_multi(const qlp_bls_params* p, int32_t n_stars, const int64_t
  * (device, as for qlp_bls_search / qlp_bls_snr), as a CUDA graph kept by the
  * plan: parts = 1 one qlp_bls_search, 2 one qlp_bls_snr, 3 the search followed by
  * the S/N (snr and best may be NULL for parts = 1). Each value of parts has its
- * own slot; capturing again replaces that slot's graph. Nothing runs on the GPU
- * during the capture, which uses a private stream of the plan.
+ * own slot; capturing again replaces that slot's graph. It first waits on the
+ * host for the plan's own device work; nothing runs on the GPU during the
+ * capture, which uses a private stream of the plan.
  * qlp_bls_graph_launch -- replay the graph of slot `parts` on `stream` (any
  * stream, including the legacy default one): the same work and results as the
  * recorded calls, from one launch call. QLP_ERR_ARG if that slot is empty.

@@ -53,6 +53,38 @@ int dev_alloc(T** p, size_t count) {
   return QLP_OK;
 }
 
+// One device allocation for a set of buffers (cheaper to make and to free than
+// one per buffer); every buffer starts on a 256-byte boundary.
+struct DevArena {
+  struct Req {
+    void** p;
+    size_t bytes;
+  };
+  std::vector<Req> reqs;
+  template <typename T>
+  DevArena& add(T** p, size_t count) {
+    reqs.push_back({reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T)});
+    return *this;
+  }
+  int commit(void** base) {
+    size_t total = 0;
+    for (const Req& r : reqs) total += (r.bytes + 255) & ~(size_t)255;
+    void* b = nullptr;
+    const cudaError_t e = cudaMalloc(&b, std::max<size_t>(total, 256));
+    if (e != cudaSuccess) {
+      cuda_fail(e, "cudaMalloc");
+      return QLP_ERR_NOMEM;
+    }
+    *base = b;
+    size_t off = 0;
+    for (const Req& r : reqs) {
+      *r.p = static_cast<char*>(b) + off;
+      off += (r.bytes + 255) & ~(size_t)255;
+    }
+    return QLP_OK;
+  }
+};
+
 }  // namespace
 
 struct qlp_bls_plan {
@@ -122,12 +154,22 @@ struct qlp_bls_plan {
   WinRec* d_wrec = nullptr;      // candidate statistics scratch (allocated on first use)
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t kev[2] = {};        // qlp_bls_kernel_timing: around the main search kernel
+  // recorded after the plan's last device work (control words, per-frequency
+  // records): searches wait for it on their own stream, so building a plan does
+  // not wait for kernels that occupy the GPU
+  cudaEvent_t ready = nullptr;
+  void* d_arena = nullptr;        // the one allocation holding the plan's buffers
+  bool ready_seen = false;        // the host has seen `ready` complete
   cudaGraph_t graph[3] = {};
   cudaGraphExec_t gexec[3] = {};
 };
 
 static void free_plan(qlp_bls_plan_t* pl) {
   if (!pl) return;
+  if (pl->ready) {
+    cudaEventSynchronize(pl->ready);
+    cudaEventDestroy(pl->ready);
+  }
   for (int i = 0; i < 3; ++i) {
     if (pl->gexec[i]) cudaGraphExecDestroy(pl->gexec[i]);
     if (pl->graph[i]) cudaGraphDestroy(pl->graph[i]);
@@ -135,26 +177,8 @@ static void free_plan(qlp_bls_plan_t* pl) {
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
   if (pl->kev[0]) cudaEventDestroy(pl->kev[0]);
   if (pl->kev[1]) cudaEventDestroy(pl->kev[1]);
-  cudaFree(pl->d_stars);
-  cudaFree(pl->d_fq);
-  cudaFree(pl->d_items);
-  cudaFree(pl->d_tp);
-  cudaFree(pl->d_y);
-  cudaFree(pl->d_dy);
-  cudaFree(pl->d_pts);
-  cudaFree(pl->d_tpd);
-  cudaFree(pl->d_cell_stars);
-  cudaFree(pl->d_cpre);
-  cudaFree(pl->d_dt);
-  cudaFree(pl->d_loc);
-  cudaFree(pl->d_base);
-  cudaFree(pl->d_gidx);
-  cudaFree(pl->d_fixed_stars);
-  cudaFree(pl->d_fx);
-  cudaFree(pl->d_frec);
-  cudaFree(pl->d_ws);
+  cudaFree(pl->d_arena);  // every buffer below but d_wrec lives in it
   cudaFree(pl->d_wrec);
-  cudaFree(pl->d_ctl);
   delete pl;
 }
 
@@ -593,22 +617,27 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   const auto c2 = clk::now();
   pl->times[1] = std::chrono::duration<double>(c2 - c1).count();
   cudaStream_t st = (cudaStream_t)stream;
-  if ((rc = dev_alloc(&pl->d_stars, (size_t)n_stars)) || (rc = dev_alloc(&pl->d_fq, nf_alloc)) ||
-      (rc = dev_alloc(&pl->d_items, sorted.size())) || (rc = dev_alloc(&pl->d_tp, npt_alloc)) ||
-      (rc = dev_alloc(&pl->d_y, npt_alloc)) || (rc = dev_alloc(&pl->d_dy, npt_alloc)) ||
-      (rc = dev_alloc(&pl->d_pts, (size_t)std::max<int64_t>(npad, 1))) ||
-      (rc = dev_alloc(&pl->d_tpd, (size_t)std::max<int64_t>(npad, 1))) ||
-      (rc = dev_alloc(&pl->d_cell_stars, std::max<size_t>(cell_stars.size(), 1))) ||
-      (rc = dev_alloc(&pl->d_cpre, (size_t)std::max<int64_t>(ncpre, 1))) ||
-      (rc = dev_alloc(&pl->d_dt, (size_t)std::max<int64_t>(ncell, 1))) ||
-      (rc = dev_alloc(&pl->d_loc, (size_t)std::max<int64_t>(ncell, 1))) ||
-      (rc = dev_alloc(&pl->d_gidx, (size_t)std::max<int64_t>(ncell, 1))) ||
-      (rc = dev_alloc(&pl->d_base, (size_t)std::max<int64_t>(nbase, 1))) ||
-      (rc = dev_alloc(&pl->d_fixed_stars, std::max<size_t>(fixed_stars.size(), 1))) ||
-      (rc = dev_alloc(&pl->d_fx, (size_t)std::max(n_stars, 1))) ||
-      (rc = dev_alloc(&pl->d_frec, fixed_stars.empty() ? (size_t)1 : nf_alloc)) ||
-      (rc = dev_alloc(&pl->d_ws, pl->fixed_windowed ? (size_t)pl->f_blocks * (size_t)kFixedWsBlock : (size_t)1)) ||
-      (rc = dev_alloc(&pl->d_ctl, 4))) {
+  DevArena arena;
+  arena.add(&pl->d_stars, (size_t)n_stars)
+      .add(&pl->d_fq, nf_alloc)
+      .add(&pl->d_items, sorted.size())
+      .add(&pl->d_tp, npt_alloc)
+      .add(&pl->d_y, npt_alloc)
+      .add(&pl->d_dy, npt_alloc)
+      .add(&pl->d_pts, (size_t)npad)
+      .add(&pl->d_tpd, (size_t)npad)
+      .add(&pl->d_cell_stars, cell_stars.size())
+      .add(&pl->d_cpre, (size_t)ncpre)
+      .add(&pl->d_dt, (size_t)ncell)
+      .add(&pl->d_loc, (size_t)ncell)
+      .add(&pl->d_gidx, (size_t)ncell)
+      .add(&pl->d_base, (size_t)nbase)
+      .add(&pl->d_fixed_stars, fixed_stars.size())
+      .add(&pl->d_fx, (size_t)n_stars)
+      .add(&pl->d_frec, fixed_stars.empty() ? (size_t)1 : nf_alloc)
+      .add(&pl->d_ws, pl->fixed_windowed ? (size_t)pl->f_blocks * (size_t)kFixedWsBlock : (size_t)1)
+      .add(&pl->d_ctl, 4);
+  if ((rc = arena.commit(&pl->d_arena))) {
     free_plan(pl);
     return rc;
   }
@@ -623,12 +652,15 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   if (e == cudaSuccess && npt_raw > 0) e = cudaMemcpyAsync(pl->d_tp, tp_all.get(), sizeof(double) * (size_t)npt_raw, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && npt_raw > 0) e = cudaMemcpyAsync(pl->d_y, y_all.get(), sizeof(double) * (size_t)npt_raw, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && npt_raw > 0) e = cudaMemcpyAsync(pl->d_dy, dy_all.get(), sizeof(double) * (size_t)npt_raw, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // host staging arrays die at return
+  // the rest runs on the device after the uploads without the host waiting for it
   if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_ctl, 0, 4 * sizeof(int32_t), st);
   if (e == cudaSuccess && !fixed_stars.empty()) {  // per-frequency records of the exact path
     const int le = launch_freq_recs(fixed_args(pl), stream);
     if (le) e = (cudaError_t)le;
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // host staging vectors die at return
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ready, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(pl->ready, st);
   if (e != cudaSuccess) {
     free_plan(pl);
     return cuda_fail(e, "plan upload");
@@ -713,12 +745,34 @@ int qlp_bls_plan_exact_stats(const qlp_bls_plan_t* pl, int32_t* n_exact_stars, d
   return QLP_OK;
 }
 
+// Orders `stream` after the plan's own device work (see `ready`). A stream capture
+// may not wait on work outside it: qlp_bls_graph_capture and qlp_bls_device_status
+// wait on the host first; a capture of the caller's own that starts before either
+// (or before a stream synchronisation seen here) is refused.
+static cudaError_t wait_plan_ready(qlp_bls_plan_t* pl, cudaStream_t st) {
+  if (!pl->ready || pl->ready_seen) return cudaSuccess;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusNone) return cudaErrorStreamCaptureUnsupported;
+  return cudaStreamWaitEvent(st, pl->ready, 0);
+}
+
+// Host wait for the plan's own device work.
+static cudaError_t sync_plan_ready(qlp_bls_plan_t* pl) {
+  if (!pl->ready || pl->ready_seen) return cudaSuccess;
+  const cudaError_t e = cudaEventSynchronize(pl->ready);
+  if (e == cudaSuccess) pl->ready_seen = true;
+  return e;
+}
+
 int qlp_bls_search(qlp_bls_plan_t* pl, void* stream, float* sr, uint8_t* qidx, uint32_t* phase_bin,
                    float* s_best, float* r_best) {
   if (!pl) return QLP_ERR_ARG;
   if (pl->f_off.back() > 0 && !sr) return QLP_ERR_ARG;
   if (pl->n_stars == 0 || pl->f_off.back() == 0) return QLP_OK;
   cudaStream_t st = (cudaStream_t)stream;
+  QLP_CK(wait_plan_ready(pl, st));
   QLP_CK(cudaMemsetAsync(pl->d_ctl, 0, 2 * sizeof(int32_t), st));
   QLP_CK(cudaMemsetAsync(pl->d_ctl + 3, 0, sizeof(int32_t), st));
   int e = 0;
@@ -869,6 +923,7 @@ int qlp_bls_snr_trend(qlp_bls_plan_t* pl, void* stream, const float* sr, const u
   if (pl->n_stars > 0 && !best) return QLP_ERR_ARG;
   if (pl->f_off.back() > 0 && (!sr || !qidx || !phase_bin || !s_best || !r_best || !snr)) return QLP_ERR_ARG;
   if (pl->n_stars == 0) return QLP_OK;
+  QLP_CK(wait_plan_ready(pl, (cudaStream_t)stream));
   SnrArgs a{};
   a.stars = pl->d_stars;
   a.fq = pl->d_fq;
@@ -898,6 +953,7 @@ int qlp_bls_device_status(qlp_bls_plan_t* pl, void* stream, int32_t* flags) {
   if (!pl || !flags) return QLP_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   QLP_CK(cudaStreamSynchronize(st));
+  QLP_CK(sync_plan_ready(pl));
   int32_t v = 0;
   QLP_CK(cudaMemcpy(&v, pl->d_ctl + 2, sizeof(int32_t), cudaMemcpyDeviceToHost));
   *flags = v;
@@ -911,12 +967,13 @@ int qlp_bls_run_host(const qlp_bls_params* p, int32_t n_stars, const int64_t* of
                      int64_t* n_freq_total_out) {
   if (!best_host && n_stars > 0) return QLP_ERR_ARG;
   if (n_stars < 0 || (n_stars > 0 && !offsets)) return QLP_ERR_ARG;
-  // The batch runs in chunks of whole stars with about equal numbers of points:
-  // the host plans chunk k + 1 (the grid and tables, on all cores) while the
-  // device searches chunk k. Uploads and the plan's own synchronisation use one
+  // The batch runs in chunks of whole stars: the host plans chunk k + 1 (the grid
+  // and tables, on all cores) while the device searches chunk k. The first and
+  // the last chunk hold half the points of the others, so that the device starts
+  // early and the last search after the host's work is short. Uploads use one
   // stream, the searches another; results come back after the last launch.
   const int64_t npts = n_stars > 0 ? offsets[n_stars] - offsets[0] : 0;
-  const int nch = std::max(1, std::min(8, n_stars / 512));
+  const int nch = n_stars >= 1024 ? 9 : 1;
   struct Chunk {
     qlp_bls_plan_t* pl = nullptr;
     int32_t s0 = 0, ns = 0;
@@ -925,6 +982,7 @@ int qlp_bls_run_host(const qlp_bls_params* p, int32_t n_stars, const int64_t* of
     uint8_t* q = nullptr;
     uint32_t* k = nullptr;
     qlp_bls_best* best = nullptr;
+    void* mem = nullptr;  // one allocation holding the outputs above
   };
   std::vector<Chunk> ch;
   cudaStream_t st_up = nullptr, st_run = nullptr;
@@ -938,8 +996,8 @@ int qlp_bls_run_host(const qlp_bls_params* p, int32_t n_stars, const int64_t* of
   int32_t s0 = 0;
   for (int c = 0; c < nch && rc == QLP_OK && (s0 < n_stars || (c == 0 && n_stars == 0)); ++c) {
     int32_t s1 = n_stars;
-    if (c < nch - 1) {
-      const int64_t goal = offsets[0] + npts * (c + 1) / nch;
+    if (c < nch - 1) {  // end of chunk c at (c + 1/2) of nch - 1 equal shares of the points
+      const int64_t goal = offsets[0] + npts * (2 * c + 1) / (2 * (nch - 1));
       s1 = s0;
       while (s1 < n_stars && offsets[s1] < goal) ++s1;
       s1 = std::max(s1, std::min(n_stars, s0 + 1));
@@ -956,11 +1014,15 @@ int qlp_bls_run_host(const qlp_bls_params* p, int32_t n_stars, const int64_t* of
     k.nf = k.pl->f_off.back();
     ch.push_back(k);
     Chunk& b = ch.back();
-    if ((rc = dev_alloc(&b.sr, (size_t)b.nf)) || (rc = dev_alloc(&b.snr, (size_t)b.nf)) ||
-        (rc = dev_alloc(&b.s, (size_t)b.nf)) || (rc = dev_alloc(&b.r, (size_t)b.nf)) ||
-        (rc = dev_alloc(&b.q, (size_t)b.nf)) || (rc = dev_alloc(&b.k, (size_t)b.nf)) ||
-        (rc = dev_alloc(&b.best, (size_t)std::max(b.ns, 1))))
-      break;
+    DevArena outs;
+    outs.add(&b.sr, (size_t)b.nf)
+        .add(&b.snr, (size_t)b.nf)
+        .add(&b.s, (size_t)b.nf)
+        .add(&b.r, (size_t)b.nf)
+        .add(&b.q, (size_t)b.nf)
+        .add(&b.k, (size_t)b.nf)
+        .add(&b.best, (size_t)b.ns);
+    if ((rc = outs.commit(&b.mem))) break;
     if ((rc = qlp_bls_search(b.pl, st_run, b.sr, b.q, b.k, b.s, b.r)) != QLP_OK) break;
     if ((rc = qlp_bls_snr(b.pl, st_run, b.sr, b.q, b.k, b.s, b.r, b.snr, b.best)) != QLP_OK) break;
     s0 = s1;
@@ -991,7 +1053,7 @@ int qlp_bls_run_host(const qlp_bls_params* p, int32_t n_stars, const int64_t* of
   }
   cudaStreamSynchronize(st_run);
   for (Chunk& k : ch) {
-    cudaFree(k.sr); cudaFree(k.snr); cudaFree(k.s); cudaFree(k.r); cudaFree(k.q); cudaFree(k.k); cudaFree(k.best);
+    cudaFree(k.mem);
     qlp_bls_plan_destroy(k.pl);
   }
   cudaStreamDestroy(st_up);
@@ -1094,6 +1156,7 @@ int qlp_bls_graph_capture(qlp_bls_plan_t* pl, int32_t parts, float* sr, uint8_t*
   if (pl->f_off.back() > 0 && (!sr || !qidx || !phase_bin || !s_best || !r_best)) return QLP_ERR_ARG;
   if ((parts & 2) && ((pl->f_off.back() > 0 && !snr) || (pl->n_stars > 0 && !best))) return QLP_ERR_ARG;
   if (!pl->cap_stream) QLP_CK(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
+  QLP_CK(sync_plan_ready(pl));
   const int slot = parts - 1;
   if (pl->gexec[slot]) { cudaGraphExecDestroy(pl->gexec[slot]); pl->gexec[slot] = nullptr; }
   if (pl->graph[slot]) { cudaGraphDestroy(pl->graph[slot]); pl->graph[slot] = nullptr; }
