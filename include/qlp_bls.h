@@ -307,7 +307,10 @@ int qlp_cnn_topk(const float* logits, const void* x0, int32_t batch, int32_t len
  * are host arrays: sr_host and snr_host float[n_freq_total] (may be NULL; the
  * caller sizes them from a previous plan of the same input or passes NULL),
  * best_host qlp_bls_best[n_stars] (required). Device memory is allocated and
- * freed inside the call. *n_freq_total_out (may be NULL) receives the size.
+ * freed inside the call. A batch of 1,024 stars or more runs in chunks of whole
+ * stars (9, the first and the last with half the points of the others): the
+ * host plans the next chunk while the device searches the previous ones.
+ * *n_freq_total_out (may be NULL) receives the size.
  * If sr_host/snr_host are given they must hold sr_capacity floats; a larger
  * spectrum returns QLP_ERR_ARG after best_host is written.
  */
