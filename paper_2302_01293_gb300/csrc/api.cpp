@@ -40,6 +40,19 @@ int qlp::record_cuda_error(cudaError_t e, const char* what) { return cuda_fail(e
 
 namespace {
 
+// Host exceptions (allocation failures in the planner's containers) end at the C
+// boundary as error codes.
+template <typename F>
+int guarded(F&& f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    return QLP_ERR_NOMEM;
+  } catch (...) {
+    return QLP_ERR_ARG;
+  }
+}
+
 template <typename T>
 int dev_alloc(T** p, size_t count) {
   *p = nullptr;
@@ -282,7 +295,10 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
 int qlp_bls_plan(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offsets, const double* t,
                  const double* y, const double* dy, const double* rho, const double* rstar,
                  void* stream, qlp_bls_plan_t** out_plan) {
-  return plan_impl(pin, n_stars, offsets, t, y, dy, rho, rstar, nullptr, nullptr, nullptr, stream, out_plan);
+  if (out_plan) *out_plan = nullptr;
+  return guarded([&] {
+    return plan_impl(pin, n_stars, offsets, t, y, dy, rho, rstar, nullptr, nullptr, nullptr, stream, out_plan);
+  });
 }
 
 int qlp_bls_plan_windows(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offsets,
@@ -296,7 +312,10 @@ int qlp_bls_plan_windows(const qlp_bls_params* pin, int32_t n_stars, const int64
   qlp_bls_params p;
   if (pin) p = *pin; else qlp_bls_params_default(&p);
   if (p.grid_mode != 0) return QLP_ERR_ARG;
-  return plan_impl(&p, n_stars, offsets, t, y, dy, rho, rstar, win_offsets, win_flo, win_fhi, stream, out_plan);
+  if (out_plan) *out_plan = nullptr;
+  return guarded([&] {
+    return plan_impl(&p, n_stars, offsets, t, y, dy, rho, rstar, win_offsets, win_flo, win_fhi, stream, out_plan);
+  });
 }
 
 static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offsets, const double* t,
@@ -375,7 +394,8 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
     if (h.status != 0 || !h.cells_ok || p.method == 1 || p.phase_mode == QLP_PHASE_FP32) continue;
     CellWin& W = cwin[(size_t)s];
     const double ovl = std::ceil(h.bin_dmax / h.cell_h) + 4.0;
-    // the edge step D/h is a 2^-56 fixed-point number below 2^8
+    // the edge step D/h must stay below 2^8 cells: the compensated kernel holds it
+    // in 8.56 fixed point, the exact one in 24.40 (32.32 for whole tables)
     if (!(ovl < 1.0e6) || !(h.bin_dmax / h.cell_h < 255.0)) continue;
     W.ovl = (int32_t)ovl;
     const bool whole = p.cell_window > 0 ? p.cell_window >= h.n_cells
@@ -961,10 +981,10 @@ int qlp_bls_device_status(qlp_bls_plan_t* pl, void* stream, int32_t* flags) {
   return v ? QLP_ERR_DEVICE : QLP_OK;
 }
 
-int qlp_bls_run_host(const qlp_bls_params* p, int32_t n_stars, const int64_t* offsets, const double* t,
-                     const double* y, const double* dy, const double* rho, const double* rstar,
-                     float* sr_host, float* snr_host, int64_t sr_capacity, qlp_bls_best* best_host,
-                     int64_t* n_freq_total_out) {
+static int bls_run_host_impl(const qlp_bls_params* p, int32_t n_stars, const int64_t* offsets, const double* t,
+                             const double* y, const double* dy, const double* rho, const double* rstar,
+                             float* sr_host, float* snr_host, int64_t sr_capacity, qlp_bls_best* best_host,
+                             int64_t* n_freq_total_out) {
   if (!best_host && n_stars > 0) return QLP_ERR_ARG;
   if (n_stars < 0 || (n_stars > 0 && !offsets)) return QLP_ERR_ARG;
   // The batch runs in chunks of whole stars: the host plans chunk k + 1 (the grid
@@ -1061,11 +1081,21 @@ int qlp_bls_run_host(const qlp_bls_params* p, int32_t n_stars, const int64_t* of
   return rc;
 }
 
-int qlp_bls_star_grid(const qlp_bls_params* pin, int64_t n, const double* t, const double* y,
-                      const double* dy, double rho, int64_t n_win, const double* win_flo,
-                      const double* win_fhi, int32_t* status, double* pmin, double* pmax,
-                      double* t_ref, double* baseline, double* freqs, double* qmins,
-                      int64_t capacity, int64_t* n_f_out) {
+int qlp_bls_run_host(const qlp_bls_params* p, int32_t n_stars, const int64_t* offsets, const double* t,
+                     const double* y, const double* dy, const double* rho, const double* rstar,
+                     float* sr_host, float* snr_host, int64_t sr_capacity, qlp_bls_best* best_host,
+                     int64_t* n_freq_total_out) {
+  return guarded([&] {
+    return bls_run_host_impl(p, n_stars, offsets, t, y, dy, rho, rstar, sr_host, snr_host, sr_capacity, best_host,
+                             n_freq_total_out);
+  });
+}
+
+static int bls_star_grid_impl(const qlp_bls_params* pin, int64_t n, const double* t, const double* y,
+                              const double* dy, double rho, int64_t n_win, const double* win_flo,
+                              const double* win_fhi, int32_t* status, double* pmin, double* pmax,
+                              double* t_ref, double* baseline, double* freqs, double* qmins,
+                              int64_t capacity, int64_t* n_f_out) {
   if (!n_f_out || n < 0 || (n > 0 && (!t || !y || !dy))) return QLP_ERR_ARG;
   if (win_flo && (n_win < 0 || (n_win > 0 && !win_fhi))) return QLP_ERR_ARG;
   qlp_bls_params p;
@@ -1092,9 +1122,20 @@ int qlp_bls_star_grid(const qlp_bls_params* pin, int64_t n, const double* t, con
   return QLP_OK;
 }
 
-int qlp_bls_batch_grid(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offsets, const double* t,
-                       const double* y, const double* dy, const double* rho, int32_t* star_status,
-                       int64_t* freq_offsets, double* freqs, int64_t capacity) {
+int qlp_bls_star_grid(const qlp_bls_params* pin, int64_t n, const double* t, const double* y,
+                      const double* dy, double rho, int64_t n_win, const double* win_flo,
+                      const double* win_fhi, int32_t* status, double* pmin, double* pmax,
+                      double* t_ref, double* baseline, double* freqs, double* qmins,
+                      int64_t capacity, int64_t* n_f_out) {
+  return guarded([&] {
+    return bls_star_grid_impl(pin, n, t, y, dy, rho, n_win, win_flo, win_fhi, status, pmin, pmax, t_ref, baseline,
+                              freqs, qmins, capacity, n_f_out);
+  });
+}
+
+static int bls_batch_grid_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offsets, const double* t,
+                               const double* y, const double* dy, const double* rho, int32_t* star_status,
+                               int64_t* freq_offsets, double* freqs, int64_t capacity) {
   if (n_stars < 0 || !freq_offsets || (n_stars > 0 && (!offsets || !t || !y || !dy))) return QLP_ERR_ARG;
   for (int32_t s = 0; s < n_stars; ++s)
     if (offsets[s + 1] < offsets[s]) return QLP_ERR_ARG;
@@ -1117,6 +1158,14 @@ int qlp_bls_batch_grid(const qlp_bls_params* pin, int32_t n_stars, const int64_t
     if (k) std::memcpy(freqs + freq_offsets[s], sp[(size_t)s].freqs.data(), sizeof(double) * (size_t)k);
   }
   return QLP_OK;
+}
+
+int qlp_bls_batch_grid(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offsets, const double* t,
+                       const double* y, const double* dy, const double* rho, int32_t* star_status,
+                       int64_t* freq_offsets, double* freqs, int64_t capacity) {
+  return guarded([&] {
+    return bls_batch_grid_impl(pin, n_stars, offsets, t, y, dy, rho, star_status, freq_offsets, freqs, capacity);
+  });
 }
 
 void qlp_bls_plan_destroy(qlp_bls_plan_t* pl) { free_plan(pl); }

@@ -20,6 +20,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <cstdint>
+#include <exception>
 #include <mutex>
 #include <pthread.h>
 #include <thread>
@@ -339,6 +340,8 @@ class HostPool {
     return *p;
   }
   int workers() const { return (int)th_.size(); }
+  // Runs the job; an exception thrown by fn (on any thread) ends the job early and
+  // is rethrown here once every thread has left it.
   bool try_run(int32_t n_tasks, int helpers, const std::function<void(int32_t)>& fn) {
     std::unique_lock<std::mutex> job(job_mu_, std::try_to_lock);
     if (!job.owns_lock()) return false;
@@ -347,15 +350,22 @@ class HostPool {
       fn_ = &fn;
       n_tasks_ = n_tasks;
       next_.store(0);
+      err_ = nullptr;
       helpers_ = std::min(helpers, workers());
       active_ = helpers_;
       ++gen_;
     }
     cv_.notify_all();
     work();
-    std::unique_lock<std::mutex> lk(mu_);
-    done_cv_.wait(lk, [&] { return active_ == 0; });
-    fn_ = nullptr;
+    std::exception_ptr err;
+    {
+      std::unique_lock<std::mutex> lk(mu_);
+      done_cv_.wait(lk, [&] { return active_ == 0; });
+      fn_ = nullptr;
+      err = err_;
+      err_ = nullptr;
+    }
+    if (err) std::rethrow_exception(err);
     return true;
   }
 
@@ -366,7 +376,13 @@ class HostPool {
     for (auto& x : th_) x.detach();
   }
   void work() {
-    for (int32_t k = next_.fetch_add(1); k < n_tasks_; k = next_.fetch_add(1)) (*fn_)(k);
+    try {
+      for (int32_t k = next_.fetch_add(1); k < n_tasks_; k = next_.fetch_add(1)) (*fn_)(k);
+    } catch (...) {
+      std::lock_guard<std::mutex> lk(mu_);
+      if (!err_) err_ = std::current_exception();
+      next_.store(n_tasks_);  // the other threads take no further task
+    }
   }
   void loop(int idx) {
     uint64_t seen = 0;
@@ -398,6 +414,7 @@ class HostPool {
   std::atomic<int32_t> next_{0};
   int helpers_ = 0, active_ = 0;
   uint64_t gen_ = 0;
+  std::exception_ptr err_;
 };
 
 }  // namespace
@@ -410,13 +427,21 @@ void parallel_stars(const qlp_bls_params& p, int32_t n_stars, const std::functio
     return;
   }
   if (HostPool::get().try_run(n_stars, nth - 1, fn)) return;
+  // the pool is busy with another caller's job: threads of this call's own
   std::vector<std::thread> th;
+  std::vector<std::exception_ptr> err((size_t)nth);
   th.reserve((size_t)nth);
   for (int i = 0; i < nth; ++i)
     th.emplace_back([&, i]() {
-      for (int32_t s = i; s < n_stars; s += nth) fn(s);
+      try {
+        for (int32_t s = i; s < n_stars; s += nth) fn(s);
+      } catch (...) {
+        err[(size_t)i] = std::current_exception();
+      }
     });
   for (auto& x : th) x.join();
+  for (auto& e : err)
+    if (e) std::rethrow_exception(e);
 }
 
 void plan_all(const qlp_bls_params& p, int32_t n_stars, const int64_t* offsets, const double* t,

@@ -161,6 +161,17 @@ def test_window_grid_is_bit_identical_to_oracle():
         assert np.array_equal(g["freqs"], o.freqs) and np.array_equal(g["qmins"], o.qmin)
 
 
+@pytest.mark.parametrize("n_threads", [1, 2, 3, 0])
+def test_batch_planner_thread_counts(n_threads):
+    """The batch planner gives the same grids whatever the number of host threads
+    (1 = the calling thread alone; 0 = every core, from the process-wide pool)."""
+    b = synth.uneven_single_sector(n_stars=21, seed=33)
+    ref = qlpbls.batch_grid(b.offsets, b.t, b.y, b.dy, b.rho, qlpbls.Params(n_threads=1))
+    got = qlpbls.batch_grid(b.offsets, b.t, b.y, b.dy, b.rho, qlpbls.Params(n_threads=n_threads))
+    for r, g in zip(ref, got):
+        assert np.array_equal(r, g)
+
+
 @pytest.mark.filterwarnings("ignore:This process .* is multi-threaded:DeprecationWarning")
 def test_batch_planner_after_fork():
     """The planner's host thread pool does not survive fork(); a child process
