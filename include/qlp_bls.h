@@ -42,6 +42,11 @@ extern "C" {
 #define QLP_ERR_DEVICE      -4  /* a device-side bound was hit (iteration limit, capacity) */
 #define QLP_ERR_UNSUPPORTED -5  /* option combination not built into this library */
 
+/* Device error bits, as qlp_bls_device_status and qlp_bls_search_static report them. */
+#define QLP_DEVERR_QUEUE     1  /* a persistent work loop hit its iteration bound */
+#define QLP_DEVERR_NBINS     2  /* a frequency needed more bins than the histogram holds */
+#define QLP_DEVERR_SNR_BINS  4  /* more S/N (Sturges) bins than supported */
+
 /* ---- per-star status flags (qlp_bls_plan_info star_status, qlp_bls_best.status) ---- */
 #define QLP_STAR_UNSORTED    1  /* t decreases somewhere (after dropping invalid points) */
 #define QLP_STAR_TOO_FEW     2  /* fewer than 2 valid points */
@@ -110,7 +115,12 @@ typedef struct qlp_bls_params {
   double coarse_pmin;       /* 0.1 d */
   double coarse_pmax;       /* 400 d */
   int32_t bin_mode;         /* QLP_BIN_* (default QLP_BIN_SHARED) */
-  int32_t reserved1;
+  int32_t work_loop_bound;  /* 0 = each persistent search kernel's work loop may run as many
+                               iterations as there are work items (default); n > 0 = a block
+                               stops after n + 1 queue pops and raises QLP_DEVERR_QUEUE
+                               (watchdog and failure-injection setting; results of items not
+                               taken are left unwritten, and qlp_bls_search returns
+                               QLP_ERR_DEVICE through qlp_bls_device_status) */
 } qlp_bls_params;
 
 /* Best candidate of one star: the frequency of maximum S/N and its BLS box. */
@@ -322,14 +332,27 @@ int qlp_bls_run_host(const qlp_bls_params* p, int32_t n_stars, const int64_t* of
 
 /*
  * qlp_bls_device_status -- synchronise `stream`, return the device error flags
- * accumulated by this plan's kernels since the last call in *flags (bit 1: the
- * work loop hit its iteration bound, 2: a frequency needed more bins than the
- * shared histogram holds, 4: more S/N bins than supported) and clear them.
+ * accumulated by this plan's kernels since the last call in *flags (QLP_DEVERR_*:
+ * 1 the work loop hit its iteration bound, 2 a frequency needed more bins than the
+ * shared histogram holds, 4 more S/N bins than supported) and clear them.
  * Returns QLP_ERR_DEVICE when any flag was set, else QLP_OK.
  */
 int qlp_bls_device_status(qlp_bls_plan_t* plan, void* stream, int32_t* flags);
 
 void qlp_bls_plan_destroy(qlp_bls_plan_t* plan);
+
+/*
+ * qlp_set_device_budget -- a cap on the device bytes the library's plans and
+ * networks may hold at once (0 = none, the default; negative = QLP_ERR_ARG). A
+ * qlp_bls_plan / qlp_cnn_create / qlp_bls_candidate_stats allocation that would
+ * pass it fails before any device memory is taken and returns QLP_ERR_NOMEM,
+ * exactly as an out-of-memory cudaMalloc would; everything the failing call
+ * took before is released. It serves capacity control and host-side failure
+ * injection (the allocation failure path is tested this way, with no GPU fault).
+ * qlp_device_bytes_held -- the bytes those objects hold now.
+ */
+int qlp_set_device_budget(int64_t bytes);
+int64_t qlp_device_bytes_held(void);
 
 /*
  * qlp_bls_autotune -- choose the search's launch settings for a batch (an
@@ -502,14 +525,23 @@ int qlp_bls_batch_grid(const qlp_bls_params* p, int32_t n_stars, const int64_t* 
  *               q_min, e.g. from qlp_bls_star_grid.
  *  stream       cudaStream_t (NULL = default stream).
  *  sr, qidx, phase_bin, s_best, r_best  device outputs of n_f entries, as for
- *               qlp_bls_search (qidx, phase_bin, s_best, r_best may be NULL).
- * Asynchronous on `stream`; results are valid after it is synchronised.
+ *               qlp_bls_search (qidx, phase_bin, s_best, r_best may be NULL). A
+ *               frequency the kernel could not search (its bin count beyond the
+ *               histogram it sized) keeps sr = 0, qidx = 255, phase_bin =
+ *               0xFFFFFFFF and raises QLP_DEVERR_NBINS in flags.
+ *  flags        device int32 (may be NULL): receives, on `stream`, this call's
+ *               device error bits (0 = clean; QLP_DEVERR_NBINS, QLP_DEVERR_QUEUE),
+ *               the same bits qlp_bls_device_status reports for a plan.
+ * Only the shared histogram of Sec. 2.1 (bin_mode QLP_BIN_SHARED): any other
+ * bin_mode returns QLP_ERR_UNSUPPORTED. warps_per_block 32 runs as 16, as the
+ * point path of qlp_bls_plan does.
+ * Asynchronous on `stream`; results and flags are valid after it is synchronised.
  */
 #define QLP_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
 int qlp_bls_search_static(const qlp_bls_params* p, int32_t n, const double* tp, const double* y,
                           const double* dy, double baseline, int32_t n_f, const double* freqs,
                           const double* qmins, void* stream, float* sr, uint8_t* qidx,
-                          uint32_t* phase_bin, float* s_best, float* r_best);
+                          uint32_t* phase_bin, float* s_best, float* r_best, int32_t* flags);
 
 /* ---------------------------------------------------------------- learned path
  * Not in the paper: a small 1-D CNN proposes period windows from a coarse BLS
@@ -578,6 +610,15 @@ int qlp_cnn_loss(qlp_cnn_t* net, float* loss_host, int32_t* err_host, void* stre
 const char* qlp_cnn_last_error(void);
 
 /*
+ * qlp_cnn_get_tensor  host copy of a tensor the last forward / backward kept, for
+ *                checks of each layer on its own inputs: which = QLP_CNN_ACT (BF16
+ *                [batch][len][64] output of layer 1..5 after its ReLU),
+ *                QLP_CNN_GACT (BF16 [batch][len][64] loss gradient of the
+ *                pre-activation of layer 1..5), QLP_CNN_LOGIT (FP32 [batch][len]
+ *                logits; layer ignored) or QLP_CNN_DLOGIT (FP32 [batch][len] loss
+ *                gradient of the logits). batch <= max_batch rows are copied into
+ *                host (bytes >= the tensor's size, else QLP_ERR_ARG); synchronises
+ *                `stream`.
  * qlp_cnn_shape  the max_batch and len the network was created with.
  * qlp_cnn_save   checkpoint to a file: the parameters, Adam's two moment vectors
  *                and its step count (FP32 little-endian after a short header);
@@ -587,6 +628,12 @@ const char* qlp_cnn_last_error(void);
  *                training resumes where it stopped. QLP_ERR_ARG for a missing file
  *                or one of another layout; the network is unchanged then.
  */
+#define QLP_CNN_ACT 0
+#define QLP_CNN_GACT 1
+#define QLP_CNN_LOGIT 2
+#define QLP_CNN_DLOGIT 3
+int qlp_cnn_get_tensor(const qlp_cnn_t* net, int32_t which, int32_t layer, int32_t batch, void* host,
+                       int64_t bytes, void* stream);
 int qlp_cnn_shape(const qlp_cnn_t* net, int32_t* max_batch, int32_t* len);
 int qlp_cnn_save(const qlp_cnn_t* net, const char* path, void* stream);
 int qlp_cnn_load(qlp_cnn_t* net, const char* path, void* stream);

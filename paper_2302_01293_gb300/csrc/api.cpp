@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -38,6 +39,27 @@ int cuda_fail(cudaError_t e, const char* what) {
 // Records a CUDA failure for qlp_last_cuda_error (other translation units).
 int qlp::record_cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
 
+namespace qlp {
+
+// Device-memory budget of the library's own allocations (plans and networks): a cap
+// on the bytes they hold at once, 0 = none. An allocation that would pass it fails
+// before cudaMalloc is called, as an out-of-memory cudaMalloc would.
+static std::atomic<int64_t> g_budget{0};
+static std::atomic<int64_t> g_held{0};
+
+bool budget_take(size_t bytes) {
+  const int64_t cap = g_budget.load();
+  int64_t cur = g_held.load();
+  for (;;) {
+    if (cap > 0 && cur + (int64_t)bytes > cap) return false;
+    if (g_held.compare_exchange_weak(cur, cur + (int64_t)bytes)) return true;
+  }
+}
+
+void budget_give(size_t bytes) { g_held.fetch_sub((int64_t)bytes); }
+
+}  // namespace qlp
+
 namespace {
 
 // Host exceptions (allocation failures in the planner's containers) end at the C
@@ -54,15 +76,18 @@ int guarded(F&& f) {
 }
 
 template <typename T>
-int dev_alloc(T** p, size_t count) {
+int dev_alloc(T** p, size_t count, size_t* held) {
   *p = nullptr;
   if (count == 0) count = 1;
+  if (!budget_take(count * sizeof(T))) return QLP_ERR_NOMEM;
   cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
   if (e != cudaSuccess) {
     *p = nullptr;
+    budget_give(count * sizeof(T));
     cuda_fail(e, "cudaMalloc");
     return QLP_ERR_NOMEM;
   }
+  *held = count * sizeof(T);
   return QLP_OK;
 }
 
@@ -79,16 +104,20 @@ struct DevArena {
     reqs.push_back({reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T)});
     return *this;
   }
-  int commit(void** base) {
+  int commit(void** base, size_t* held) {
     size_t total = 0;
     for (const Req& r : reqs) total += (r.bytes + 255) & ~(size_t)255;
+    total = std::max<size_t>(total, 256);
+    if (!budget_take(total)) return QLP_ERR_NOMEM;
     void* b = nullptr;
-    const cudaError_t e = cudaMalloc(&b, std::max<size_t>(total, 256));
+    const cudaError_t e = cudaMalloc(&b, total);
     if (e != cudaSuccess) {
+      budget_give(total);
       cuda_fail(e, "cudaMalloc");
       return QLP_ERR_NOMEM;
     }
     *base = b;
+    *held = total;
     size_t off = 0;
     for (const Req& r : reqs) {
       *r.p = static_cast<char*>(b) + off;
@@ -138,7 +167,10 @@ struct qlp_bls_plan {
   int32_t n_fixed_stars = 0;
   int32_t fixed_max_pts = 0;
   bool fixed_windowed = false;    // some exact-path star is searched in time windows
-  longlong2* d_ws = nullptr;      // their bin-sum workspace, kFixedWsBlock entries per block
+  longlong2* d_ws = nullptr;      // exact-path bin-sum workspace, ws_block entries per block:
+  int64_t ws_block = 1;           // kFixedWsBlock with windowed stars, else a row of the largest
+                                  // bin count per warp (the exact rescoring of each best box)
+  int32_t fixed_nb_max = 0;       // largest bin count of an exact-path star
   double edges_fixed = 0.0;
   double bins_fixed = 0.0;       // sum of nbins over the exact path's frequencies
   double times[4] = {};          // seconds: host grid, host staging, device allocation, upload
@@ -172,6 +204,7 @@ struct qlp_bls_plan {
   // not wait for kernels that occupy the GPU
   cudaEvent_t ready = nullptr;
   void* d_arena = nullptr;        // the one allocation holding the plan's buffers
+  size_t arena_bytes = 0, wrec_bytes = 0;  // device bytes held against the budget
   bool ready_seen = false;        // the host has seen `ready` complete
   cudaGraph_t graph[3] = {};
   cudaGraphExec_t gexec[3] = {};
@@ -192,6 +225,7 @@ static void free_plan(qlp_bls_plan_t* pl) {
   if (pl->kev[1]) cudaEventDestroy(pl->kev[1]);
   cudaFree(pl->d_arena);  // every buffer below but d_wrec lives in it
   cudaFree(pl->d_wrec);
+  budget_give(pl->arena_bytes + pl->wrec_bytes);
   delete pl;
 }
 
@@ -222,7 +256,7 @@ void qlp_bls_params_default(qlp_bls_params* p) {
   p->coarse_pmin = 0.1;
   p->coarse_pmax = 400.0;
   p->bin_mode = QLP_BIN_SHARED;
-  p->reserved1 = 0;
+  p->work_loop_bound = 0;
 }
 
 const char* qlp_strerror(int code) {
@@ -247,6 +281,7 @@ static int check_params(const qlp_bls_params& p) {
   if (p.phase_mode < 0 || p.phase_mode > 2 || p.sum_mode < 0 || p.sum_mode > 2 || p.mad_mode < 0 ||
       p.mad_mode > 1 || p.tile_points < 0 || p.chunk_freqs < 0 || p.method < 0 || p.method > 2 ||
       p.grid_mode < 0 || p.grid_mode > 1 || p.cell_window < 0 || p.bin_mode < 0 || p.bin_mode > 1 ||
+      p.work_loop_bound < 0 ||
       (p.bin_mode == QLP_BIN_PER_Q && (p.noverlap != std::floor(p.noverlap) || p.phase_mode == QLP_PHASE_FP32 ||
                                        p.method == 1)) ||
       (p.grid_mode == 1 && (p.coarse_bins < 2 || !(p.coarse_pmin > 0) || !(p.coarse_pmax > p.coarse_pmin))))
@@ -504,6 +539,7 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
         pl->fixed_max_pts = std::max(pl->fixed_max_pts, d.n_pts);
         fixed_ncs = std::max<int64_t>(fixed_ncs, d.n_win > 1 ? (int64_t)d.win_cap + 1 : h.n_cells + 1);
         if (d.n_win > 1) pl->fixed_windowed = true;
+        pl->fixed_nb_max = std::max(pl->fixed_nb_max, h.nbins_max);
         pl->edges_fixed += h.cells_work;
         pl->bins_fixed += h.nbins_sum;
       } else {
@@ -575,6 +611,12 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
     if (fper < 1) { delete pl; return QLP_ERR_UNSUPPORTED; }
     pl->f_blocks = sms * fper;
   }
+
+  // exact-path workspace per block: the windowed stars' rows (each item's bins per
+  // frequency), which also hold one row of 4,096 >= nbins per warp; else one row of
+  // the largest bin count per warp
+  if (!fixed_stars.empty())
+    pl->ws_block = pl->fixed_windowed ? kFixedWsBlock : (int64_t)kFixedWarps * round32(pl->fixed_nb_max);
 
   // work items: (star, chunk of frequencies), longest first, one queue per path
   auto make_items = [&](int32_t meth, int w, int blocks, std::vector<WorkItem>* outv) {
@@ -655,9 +697,9 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
       .add(&pl->d_fixed_stars, fixed_stars.size())
       .add(&pl->d_fx, (size_t)n_stars)
       .add(&pl->d_frec, fixed_stars.empty() ? (size_t)1 : nf_alloc)
-      .add(&pl->d_ws, pl->fixed_windowed ? (size_t)pl->f_blocks * (size_t)kFixedWsBlock : (size_t)1)
+      .add(&pl->d_ws, fixed_stars.empty() ? (size_t)1 : (size_t)pl->f_blocks * (size_t)pl->ws_block)
       .add(&pl->d_ctl, 4);
-  if ((rc = arena.commit(&pl->d_arena))) {
+  if ((rc = arena.commit(&pl->d_arena, &pl->arena_bytes))) {
     free_plan(pl);
     return rc;
   }
@@ -813,6 +855,7 @@ int qlp_bls_search(qlp_bls_plan_t* pl, void* stream, float* sr, uint8_t* qidx, u
     a.fq = pl->d_fq;
     a.items = pl->d_items;
     a.n_items = pl->n_items;
+    a.loop_bound = pl->p.work_loop_bound;
     a.nq = pl->nq;
     a.pts = pl->d_pts;
     a.tpd = pl->d_tpd;
@@ -854,6 +897,7 @@ int qlp_bls_search(qlp_bls_plan_t* pl, void* stream, float* sr, uint8_t* qidx, u
     c.fq = pl->d_fq;
     c.items = pl->d_items + pl->n_items;
     c.n_items = pl->c_items;
+    c.loop_bound = pl->p.work_loop_bound;
     c.nq = pl->nq;
     c.tp = pl->d_tp;
     c.dt = pl->d_dt;
@@ -888,6 +932,7 @@ int qlp_bls_search(qlp_bls_plan_t* pl, void* stream, float* sr, uint8_t* qidx, u
     fa.frec = pl->d_frec;
     fa.items = pl->d_items + pl->n_items + pl->c_items;
     fa.n_items = pl->f_items;
+    fa.loop_bound = pl->p.work_loop_bound;
     fa.nq = pl->nq;
     fa.tp = pl->d_tp;
     fa.dt = pl->d_dt;
@@ -903,7 +948,7 @@ int qlp_bls_search(qlp_bls_plan_t* pl, void* stream, float* sr, uint8_t* qidx, u
     fa.rbest = r_best;
     fa.stride4 = 4;
     fa.ws = pl->d_ws;
-    fa.ws_block = kFixedWsBlock;
+    fa.ws_block = pl->ws_block;
     QLP_CK(record_kev(pl, 0, st));
     e = launch_cells_fixed(fa, pl->f_blocks, pl->f_smem, stream);
     if (e) return cuda_fail((cudaError_t)e, "exact cell search launch");
@@ -1003,6 +1048,7 @@ static int bls_run_host_impl(const qlp_bls_params* p, int32_t n_stars, const int
     uint32_t* k = nullptr;
     qlp_bls_best* best = nullptr;
     void* mem = nullptr;  // one allocation holding the outputs above
+    size_t mem_bytes = 0;
   };
   std::vector<Chunk> ch;
   cudaStream_t st_up = nullptr, st_run = nullptr;
@@ -1042,7 +1088,7 @@ static int bls_run_host_impl(const qlp_bls_params* p, int32_t n_stars, const int
         .add(&b.q, (size_t)b.nf)
         .add(&b.k, (size_t)b.nf)
         .add(&b.best, (size_t)b.ns);
-    if ((rc = outs.commit(&b.mem))) break;
+    if ((rc = outs.commit(&b.mem, &b.mem_bytes))) break;
     if ((rc = qlp_bls_search(b.pl, st_run, b.sr, b.q, b.k, b.s, b.r)) != QLP_OK) break;
     if ((rc = qlp_bls_snr(b.pl, st_run, b.sr, b.q, b.k, b.s, b.r, b.snr, b.best)) != QLP_OK) break;
     s0 = s1;
@@ -1074,6 +1120,7 @@ static int bls_run_host_impl(const qlp_bls_params* p, int32_t n_stars, const int
   cudaStreamSynchronize(st_run);
   for (Chunk& k : ch) {
     cudaFree(k.mem);
+    budget_give(k.mem_bytes);
     qlp_bls_plan_destroy(k.pl);
   }
   cudaStreamDestroy(st_up);
@@ -1170,6 +1217,14 @@ int qlp_bls_batch_grid(const qlp_bls_params* pin, int32_t n_stars, const int64_t
 
 void qlp_bls_plan_destroy(qlp_bls_plan_t* pl) { free_plan(pl); }
 
+int qlp_set_device_budget(int64_t bytes) {
+  if (bytes < 0) return QLP_ERR_ARG;
+  g_budget.store(bytes);
+  return QLP_OK;
+}
+
+int64_t qlp_device_bytes_held(void) { return g_held.load(); }
+
 int qlp_bls_top_peaks(const qlp_bls_plan_t* pl, void* stream, const float* snr, int32_t n_peaks, double sep,
                       int32_t* out) {
   if (!pl || n_peaks < 1 || n_peaks > 64 || !(sep >= 0.0)) return QLP_ERR_ARG;
@@ -1183,7 +1238,7 @@ int qlp_bls_candidate_stats(qlp_bls_plan_t* pl, void* stream, const qlp_bls_best
   if (pl->n_stars > 0 && (!best || !out)) return QLP_ERR_ARG;
   if (pl->n_stars == 0) return QLP_OK;
   if (!pl->d_wrec) {
-    const int rc = dev_alloc(&pl->d_wrec, (size_t)std::max<int64_t>(pl->n_pts_alloc, 1));
+    const int rc = dev_alloc(&pl->d_wrec, (size_t)std::max<int64_t>(pl->n_pts_alloc, 1), &pl->wrec_bytes);
     if (rc) return rc;
   }
   StatsArgs a{};

@@ -104,10 +104,105 @@ __device__ __forceinline__ void flush_run(float* hw, float* hy, float* hwc, floa
   }
 }
 
+// Double-float numbers (hi + lo, |lo| <= ulp(hi) / 2) on the FP32 pipes: the
+// error-free sum and product (Knuth's TwoSum, Dekker's product through one FMA)
+// and the pair arithmetic built on them carry about 44 bits, so that a value
+// computed from exact sums rounds to FP32 within half an ulp and a hair, without
+// the FP64 units (1/64 of the FP32 rate here).
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {  // |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return DF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const DF s = df_two_sum(a.hi, b.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);  // exact: p + e = a.hi b.hi
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+
+// x / y rounded to FP32: the quotient of the leading parts, corrected once by the
+// remainder x - q y (the product q y.hi split exactly by one FMA).
+__device__ __forceinline__ float df_div_to_float(DF x, DF y) {
+  const float q = __fdiv_rn(x.hi, y.hi);
+  const float p = __fmul_rn(q, y.hi);
+  const float pe = __fmaf_rn(q, y.hi, -p);
+  const float rem = __fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(x.hi, p), pe), x.lo), __fmul_rn(q, y.lo));
+  return __fadd_rn(q, __fdiv_rn(rem, y.hi));
+}
+
+// An integer of magnitude below 2^48 as an exact pair, times 2^-k (k in [-100, 100]).
+__device__ __forceinline__ DF df_from_ll_scaled(long long v, int k) {
+  const float hi = __ll2float_rn(v);
+  const float lo = __ll2float_rn(v - (long long)hi);  // |v - hi| < 2^24: exact
+  const float sc = __int_as_float((127 - (k >> 1)) << 23), sc2 = __int_as_float((127 - (k - (k >> 1))) << 23);
+  return DF{__fmul_rn(__fmul_rn(hi, sc), sc2), __fmul_rn(__fmul_rn(lo, sc), sc2)};
+}
+
+// A frequency's best box: the FP32 score terms the sweep compared, and, on lane 0,
+// s, r and 1 - r of that box again as double-float numbers (from the exact integer
+// sums, or from the histogram's bins with their compensation terms); xv = false
+// when they were not taken.
 struct BoxBest {
   float s2, d, s, r;
   int j, k;
+  DF xs, xr, xq;
+  bool xv;
 };
+
+// s, r and 1 - r of the box [k, k + m) summed as double-float numbers over a
+// histogram's bins (wrap-padded, so k + m - 1 < nb + kMPad), compensation terms
+// included.
+template <typename F>
+__device__ __forceinline__ void box_sums_df(F bin, int k, int m, BoxBest& b) {
+  DF sw{0.f, 0.f}, sy{0.f, 0.f};
+  for (int o = 0; o < m; ++o) {
+    const float4 v = bin(k + o);  // (w, w-compensation, w d, w d-compensation)
+    sw = df_add(sw, df_two_sum(v.x, v.y));
+    sy = df_add(sy, df_two_sum(v.z, v.w));
+  }
+  b.xs = sy;
+  b.xr = sw;
+  b.xq = df_add(DF{1.f, 0.f}, DF{-sw.hi, -sw.lo});
+  b.xv = true;
+}
+
+// Lane 0 stores a frequency's best box: j, k, and SR = s^2 / (r (1 - r)), s, r of
+// that box from its FP64 sums, each rounded once to FP32 (the FP32 sweep's own
+// values when the FP64 sums are absent or give no positive r (1 - r)); SR 0, j 255,
+// k 0xFFFFFFFF when no window was valid.
+__device__ __forceinline__ void store_box(const BoxBest& b, int lane, int64_t fidx, float* sr, uint8_t* qidx,
+                                          uint32_t* kbin, float* sbest, float* rbest) {
+  if (lane != 0) return;
+  const bool none = b.s2 < 0.f;
+  float v = none ? 0.f : __fdiv_rn(b.s2, b.d), sv = b.s, rv = b.r;
+  if (!none && b.xv && b.xr.hi > 0.f && b.xq.hi > 0.f) {  // 0 < r < 1
+    v = df_div_to_float(df_mul(b.xs, b.xs), df_mul(b.xr, b.xq));
+    sv = __fadd_rn(b.xs.hi, b.xs.lo);
+    rv = __fadd_rn(b.xr.hi, b.xr.lo);
+  }
+  sr[fidx] = v;
+  if (qidx) qidx[fidx] = none ? (uint8_t)255 : (uint8_t)b.j;
+  if (kbin) kbin[fidx] = none ? 0xffffffffu : (uint32_t)b.k;
+  if (sbest) sbest[fidx] = none ? 0.f : sv;
+  if (rbest) rbest[fidx] = none ? 0.f : rv;
+}
 
 // Strict "a beats b": larger s^2/d, then lower j, then lower k; s2 < 0 = no box.
 __device__ __forceinline__ bool beats(float s2a, float da, int ja, int ka, float s2b, float db,
@@ -185,14 +280,14 @@ __device__ __forceinline__ void sweep_store(float* hw, float* hy, float* hwc, fl
       bs2 = o_s2; bd = o_d; bsv = o_s; brv = o_r; bj = o_j; bk = o_k;
     }
   }
-  if (lane == 0) {
-    const bool none = bs2 < 0.f;
-    sr[fidx] = none ? 0.f : __fdiv_rn(bs2, bd);
-    if (qidx) qidx[fidx] = none ? (uint8_t)255 : (uint8_t)bj;
-    if (kbin) kbin[fidx] = none ? 0xffffffffu : (uint32_t)bk;
-    if (sbest) sbest[fidx] = none ? 0.f : bsv;
-    if (rbest) rbest[fidx] = none ? 0.f : brv;
-  }
+  BoxBest b;
+  b.s2 = bs2; b.d = bd; b.s = bsv; b.r = brv; b.j = bj; b.k = bk;
+  b.xv = false;
+  if (lane == 0 && bk >= 0)
+    box_sums_df([&](int i) {
+      return make_float4(hw[i], SUM == QLP_SUM_COMP ? hwc[i] : 0.f, hy[i], SUM == QLP_SUM_COMP ? hyc[i] : 0.f);
+    }, bk, mtab[bj], b);
+  store_box(b, lane, fidx, sr, qidx, kbin, sbest, rbest);
 }
 
 // Histogram of the cell path: one record per bin, (w, w-compensation, w d,
@@ -271,20 +366,14 @@ __device__ __forceinline__ BoxBest sweep_best_packed(typename PackedBin<SUM>::T*
   }
   BoxBest o;
   o.s2 = bs2; o.d = bd; o.s = bsv; o.r = brv; o.j = bj; o.k = bk;
+  o.xv = false;
+  if (lane == 0 && bk >= 0)
+    box_sums_df([&](int i) {
+      const typename PB::T v = h[i];
+      return make_float4(PB::w(v), PB::wc(v), PB::y(v), PB::yc(v));
+    }, bk, mtab[bj], o);
   return o;
 }
 
-// Lane 0 stores a frequency's best box: SR = s^2/d, j, k, s, r (SR 0, j 255,
-// k 0xFFFFFFFF when no window was valid).
-__device__ __forceinline__ void store_box(const BoxBest& b, int lane, int64_t fidx, float* sr, uint8_t* qidx,
-                                          uint32_t* kbin, float* sbest, float* rbest) {
-  if (lane != 0) return;
-  const bool none = b.s2 < 0.f;
-  sr[fidx] = none ? 0.f : __fdiv_rn(b.s2, b.d);
-  if (qidx) qidx[fidx] = none ? (uint8_t)255 : (uint8_t)b.j;
-  if (kbin) kbin[fidx] = none ? 0xffffffffu : (uint32_t)b.k;
-  if (sbest) sbest[fidx] = none ? 0.f : b.s;
-  if (rbest) rbest[fidx] = none ? 0.f : b.r;
-}
 
 }  // namespace qlp

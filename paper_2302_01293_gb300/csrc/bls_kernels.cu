@@ -116,7 +116,8 @@ __global__ void __launch_bounds__(NW * 32) bls_kernel(const BlsArgs a) {
   if (threadIdx.x == 0) { s_star = -1; s_tile = -1; }
 
   bool done = false;
-  for (int iter = 0; iter <= a.n_items; ++iter) {
+  const int iter_lim = a.loop_bound > 0 ? min(a.loop_bound, a.n_items) : a.n_items;
+  for (int iter = 0; iter <= iter_lim; ++iter) {
     __syncthreads();
     if (threadIdx.x == 0) s_item = atomicAdd(a.cursor, 1);
     __syncthreads();

@@ -236,7 +236,8 @@ __global__ void __launch_bounds__(NW * 32) cells_kernel(const CellArgs a) {
   if (threadIdx.x == 0) { s_star = -1; s_win = -1; }
 
   bool done = false;
-  for (int iter = 0; iter <= a.n_items; ++iter) {
+  const int iter_lim = a.loop_bound > 0 ? min(a.loop_bound, a.n_items) : a.n_items;
+  for (int iter = 0; iter <= iter_lim; ++iter) {
     __syncthreads();
     if (threadIdx.x == 0) s_item = atomicAdd(a.cursor, 1);
     __syncthreads();
@@ -267,6 +268,7 @@ __global__ void __launch_bounds__(NW * 32) cells_kernel(const CellArgs a) {
       const int n_pass = a.per_q ? nq : 1;
       BoxBest acc;
       acc.s2 = -1.f; acc.d = 1.f; acc.s = 0.f; acc.r = 0.f; acc.j = 255; acc.k = -1;
+      acc.xv = false;
       bool failed = false;
       for (int pass = 0; pass < n_pass; ++pass) {
         double f = 0.0, F = 1.0;

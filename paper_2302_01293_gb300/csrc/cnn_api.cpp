@@ -25,8 +25,8 @@ int launch_wgrad64(const void* dy, const void* x, float* partial, float* out, in
                    void* s);
 int launch_dw_small(const void* dy, int dy_is_f32, const void* x, float* partial, float* out, int batch,
                     int len, int n_co, int n_ci, void* s);
-int launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps,
-                float c1, float c2, void* s);
+int launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float omb1,
+                float omb2, float eps, float c1, float c2, void* s);
 int wgrad64_parts(int batch, int len);
 int dw_small_parts(int batch, int len);
 }  // namespace qlp
@@ -95,6 +95,7 @@ struct qlp_cnn {
   float* loss = nullptr;
   int32_t* err = nullptr;
   float* partial = nullptr;
+  size_t held = 0;  // device bytes held against the library's budget
 };
 typedef struct qlp_cnn qlp_cnn_t;
 
@@ -104,6 +105,7 @@ static void cnn_free(qlp_cnn_t* n) {
   for (int i = 0; i < 4; ++i) { cudaFree(n->pack_f[i]); cudaFree(n->pack_b[i]); }
   for (int i = 0; i < 6; ++i) { cudaFree(n->act[i]); cudaFree(n->gact[i]); }
   cudaFree(n->logit); cudaFree(n->dlogit); cudaFree(n->loss); cudaFree(n->err); cudaFree(n->partial);
+  budget_give(n->held);
   delete n;
 }
 
@@ -131,6 +133,13 @@ int qlp_cnn_create(int32_t max_batch, int32_t len, uint64_t seed, qlp_cnn_t** ou
   const size_t pos = (size_t)max_batch * len;
   const size_t parts = std::max((size_t)wgrad64_parts(max_batch, len) * (kW64 + kCh),
                                 (size_t)dw_small_parts(max_batch, len) * (kW1 + kCh));
+  const size_t total = sizeof(float) * (4 * (size_t)kNParams + 2 * pos + parts + 1) + sizeof(int32_t) +
+                       8 * kPackBytes + 10 * pos * kCh * 2;
+  if (!budget_take(total)) {
+    delete n;
+    return QLP_ERR_NOMEM;
+  }
+  n->held = total;
   bool ok = cudaMalloc(&n->params, sizeof(float) * kNParams) == cudaSuccess &&
             cudaMalloc(&n->grads, sizeof(float) * kNParams) == cudaSuccess &&
             cudaMalloc(&n->m, sizeof(float) * kNParams) == cudaSuccess &&
@@ -180,6 +189,28 @@ int qlp_cnn_set_params(qlp_cnn_t* n, const float* host, void* stream) {
   n->step = 0;
   const int rc = repack(n, stream);
   if (rc) return rc;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return QLP_OK;
+}
+
+int qlp_cnn_get_tensor(const qlp_cnn_t* n, int32_t which, int32_t layer, int32_t batch, void* host,
+                       int64_t bytes, void* stream) {
+  if (!n || !host || batch <= 0 || batch > n->max_batch) return QLP_ERR_ARG;
+  const size_t pos = (size_t)batch * (size_t)n->len;
+  const void* src = nullptr;
+  size_t need = 0;
+  if (which == QLP_CNN_ACT || which == QLP_CNN_GACT) {
+    if (layer < 1 || layer > 5) return QLP_ERR_ARG;
+    src = which == QLP_CNN_ACT ? n->act[layer] : n->gact[layer];
+    need = pos * kCh * 2;
+  } else if (which == QLP_CNN_LOGIT || which == QLP_CNN_DLOGIT) {
+    src = which == QLP_CNN_LOGIT ? n->logit : n->dlogit;
+    need = pos * sizeof(float);
+  } else {
+    return QLP_ERR_ARG;
+  }
+  if (bytes < (int64_t)need) return QLP_ERR_ARG;
+  CK(cudaMemcpyAsync(host, src, need, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   return QLP_OK;
 }
@@ -287,9 +318,12 @@ int qlp_cnn_backward(qlp_cnn_t* n, const void* x0, const float* labels, int32_t 
 int qlp_cnn_adam_step(qlp_cnn_t* n, float lr, void* stream) {
   if (!n) return QLP_ERR_ARG;
   n->step += 1;
-  const float b1 = 0.9f, b2 = 0.999f;
-  const float c1 = 1.f - std::pow(b1, (float)n->step), c2 = 1.f - std::pow(b2, (float)n->step);
-  CKL(launch_adam(n->params, n->grads, n->m, n->v, kNParams, lr, b1, b2, 1e-8f, c1, c2, stream));
+  // beta1 = 0.9, beta2 = 0.999: the complements and the bias corrections in FP64,
+  // each rounded once to FP32
+  const double b1 = 0.9, b2 = 0.999;
+  const double c1 = 1.0 - std::pow(b1, (double)n->step), c2 = 1.0 - std::pow(b2, (double)n->step);
+  CKL(launch_adam(n->params, n->grads, n->m, n->v, kNParams, lr, (float)b1, (float)b2, (float)(1.0 - b1),
+                  (float)(1.0 - b2), 1e-8f, (float)c1, (float)c2, stream));
   return repack(n, stream);
 }
 

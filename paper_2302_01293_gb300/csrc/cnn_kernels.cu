@@ -562,13 +562,16 @@ __global__ void reduce_partials_kernel(const float* partial, int n_parts, int n_
   out[i] = s;
 }
 
+// Adam with the decay rates and their complements given separately (each the
+// FP32 rounding of its exact decimal value: 1 - 0.999f is 1.3e-5 away from 0.001)
+// and the bias corrections c1 = 1 - b1^t, c2 = 1 - b2^t computed in FP64 by the host.
 __global__ void adam_kernel(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2,
-                            float eps, float c1, float c2) {
+                            float omb1, float omb2, float eps, float c1, float c2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float gi = g[i];
-  const float mi = b1 * m[i] + (1.f - b1) * gi;
-  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  const float mi = b1 * m[i] + omb1 * gi;
+  const float vi = b2 * v[i] + omb2 * gi * gi;
   m[i] = mi;
   v[i] = vi;
   p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
@@ -653,9 +656,9 @@ int launch_dw_small(const void* dy, int dy_is_f32, const void* x, float* partial
   return (int)cudaGetLastError();
 }
 
-int launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps,
-                float c1, float c2, void* s) {
-  adam_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)s>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+int launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float omb1,
+                float omb2, float eps, float c1, float c2, void* s) {
+  adam_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)s>>>(p, g, m, v, n, lr, b1, b2, omb1, omb2, eps, c1, c2);
   return (int)cudaGetLastError();
 }
 

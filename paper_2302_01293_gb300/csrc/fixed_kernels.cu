@@ -326,13 +326,23 @@ __device__ __forceinline__ void sweep_start(const float2* rb, bool kin, int k, i
 // One trial frequency on a warp: the bin sums S (from the staged table's edges, or
 // from the window passes' workspace row when WS), then per block of 32 bins U, the
 // FP32 histogram records in the ring and the sweep, the warp argmax and the store.
+// This warp's row of exact bin sums in the block's workspace: ws_block / kFixedWarps
+// entries, at least the bins of every whole-table star of the plan.
+__device__ __forceinline__ longlong2* warp_row(const FixedArgs& a) {
+  return a.ws + (size_t)blockIdx.x * (size_t)a.ws_block +
+         (size_t)(threadIdx.x >> 5) * (size_t)(a.ws_block / kFixedWarps);
+}
+
+// The row srow holds the exact bin sums S of the frequency (the window passes'
+// workspace row when WS, else this warp's row (warp_row), written here block by block), so that
+// the box the FP32 sweep chose is scored once more from its exact integer sums.
 template <bool WS>
 __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, const FreqRec& R,
                                               const FixedStar& fx, const unsigned char* smem,
                                               uint32_t loc_off, uint32_t base_off, int nc, float2* ring,
                                               int lane, float scw, float scy, const double* tp,
                                               const int32_t* gidx, uint32_t st4, uint32_t st8, uint32_t st16,
-                                              const longlong2* wsrow) {
+                                              longlong2* srow) {
   const int nb = R.nb;
   const double f = a.fq[fidx].x;  // for the exact decision near ties
   const uint32_t wmask = R.wmask;
@@ -363,7 +373,7 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
     if constexpr (WS) {  // bin sums from the window passes
       if ((i << 5) < nb) {
         if (x < nb) {
-          const longlong2 sv = wsrow[x];
+          const longlong2 sv = srow[x];
           uw = sv.x + (bstar < x ? fx.w_tot : 0);
           uy = sv.y + (bstar < x ? fx.y_tot : 0);
         }
@@ -454,6 +464,7 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
             }
           }
         }
+        if (x < nb) warp_row(a)[x] = make_longlong2(aw, ay);  // S of bin x, for the rescoring below
         if (bstar < x) {
           aw += fx.w_tot;
           ay += fx.y_tot;
@@ -505,6 +516,7 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
   const int bo = bkey >> 16;
   int bj = none ? 255 : (int)((jlow >> (4 * bo)) & 15ull);
   int bk = none ? -1 : (bkey & 0xffff);
+  int bm = none ? 0 : bo + 1;  // bins of the box
   for (int off = 16; off > 0; off >>= 1) {
     const float o_s2 = __shfl_xor_sync(0xffffffffu, bs2, off);
     const float o_d = __shfl_xor_sync(0xffffffffu, bd, off);
@@ -512,12 +524,32 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
     const float o_r = __shfl_xor_sync(0xffffffffu, brv, off);
     const int o_j = __shfl_xor_sync(0xffffffffu, bj, off);
     const int o_k = __shfl_xor_sync(0xffffffffu, bk, off);
+    const int o_m = __shfl_xor_sync(0xffffffffu, bm, off);
     if (beats(o_s2, o_d, o_j, o_k, bs2, bd, bj, bk)) {
-      bs2 = o_s2; bd = o_d; bsv = o_s; brv = o_r; bj = o_j; bk = o_k;
+      bs2 = o_s2; bd = o_d; bsv = o_s; brv = o_r; bj = o_j; bk = o_k; bm = o_m;
     }
   }
   BoxBest bb;
   bb.s2 = bs2; bb.d = bd; bb.s = bsv; bb.r = brv; bb.j = bj; bb.k = bk;
+  bb.xv = false;
+  if (lane == 0 && bk >= 0) {
+    // the chosen box [bk, bk + bm) from the exact integer sums: U[bk + bm] - U[bk],
+    // U[x] = S[x mod nb] + ([b* < x mod nb] + floor(x / nb)) C_end; the difference is
+    // a box sum (below 2^46), so it and 2^kw - it split into exact float pairs
+    const int k2 = bk + bm;
+    const int k2m = k2 >= nb ? k2 - nb : k2;
+    const longlong2* row = WS ? srow : warp_row(a);
+    const longlong2 a0 = row[bk], a1 = row[k2m];
+    const long long nwrap = (bstar < k2m ? 1 : 0) + (k2 >= nb ? 1 : 0) - (bstar < bk ? 1 : 0);
+    const long long dw = a1.x - a0.x + nwrap * fx.w_tot;
+    const long long dy = a1.y - a0.y + nwrap * fx.y_tot;
+    if (fx.kw >= 0 && fx.kw <= 60) {
+      bb.xr = df_from_ll_scaled(dw, fx.kw);
+      bb.xq = df_from_ll_scaled((1ll << fx.kw) - dw, fx.kw);  // 1 - r
+      bb.xs = df_from_ll_scaled(dy, fx.ky);
+      bb.xv = true;
+    }
+  }
   store_box(bb, lane, fidx, a.sr, a.qidx, a.kbin, a.sbest, a.rbest);
 }
 
@@ -673,7 +705,8 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
   const uint32_t st4 = a.stride4, st8 = 2u * a.stride4, st16 = 4u * a.stride4;
 
   bool done = false;
-  for (int iter = 0; iter <= a.n_items; ++iter) {
+  const int iter_lim = a.loop_bound > 0 ? min(a.loop_bound, a.n_items) : a.n_items;
+  for (int iter = 0; iter <= iter_lim; ++iter) {
     __syncthreads();
     if (threadIdx.x == 0) {
       s_item = atomicAdd(a.cursor, 1);

@@ -62,6 +62,7 @@ struct BlsArgs {
   const double2* fq;       // per frequency: (f, q_min)
   const WorkItem* items;
   int32_t n_items;
+  int32_t loop_bound;  // 0 = n_items; else each block's work loop stops after loop_bound + 1 pops
   int32_t nq;
   const float4* pts;       // prepared points: (t'_hi, t'_lo, w d, w)
   const double* tpd;       // prepared points: t' in FP64 (same slots)
@@ -86,6 +87,7 @@ struct CellArgs {
   const double2* fq;
   const WorkItem* items;
   int32_t n_items;
+  int32_t loop_bound;  // 0 = n_items; else each block's work loop stops after loop_bound + 1 pops
   int32_t nq;
   const double* tp;        // raw t' (CSR by pt_off), for the exact decision near ties
   const uint32_t* dt;      // per cell: its point's offset, 2^-32 of the cell; 0xFFFFFFFF if empty
@@ -156,6 +158,7 @@ struct FixedArgs {
   const FreqRec* frec;
   const WorkItem* items;
   int32_t n_items;
+  int32_t loop_bound;  // 0 = n_items; else each block's work loop stops after loop_bound + 1 pops
   int32_t nq;
   const double* tp;
   const uint32_t* dt;
@@ -230,6 +233,7 @@ struct SnrArgs {
 // device error flags
 constexpr int32_t kErrQueueBound = 1;   // work loop exceeded its iteration bound
 constexpr int32_t kErrNbins = 2;        // a frequency needed more bins than the histogram holds
+static_assert(kErrQueueBound == QLP_DEVERR_QUEUE && kErrNbins == QLP_DEVERR_NBINS, "device error bits");
 constexpr int32_t kErrSturges = 4;      // more S/N bins than the kernel supports
 constexpr int32_t kErrSelect = 8;       // median selection failed to converge
 constexpr int32_t kErrMmaWait = 16;     // a tensor-core completion wait hit its bound
@@ -274,6 +278,10 @@ int launch_peaks(const StarDev* stars, int n_stars, const double2* fq, const flo
                  int32_t* out, void* stream);
 int launch_stats(const StatsArgs& a, void* stream);
 int record_cuda_error(cudaError_t e, const char* what);
+// the library's device-memory budget (qlp_set_device_budget): take before a
+// cudaMalloc of a plan or network buffer (false = over the budget), give back on free
+bool budget_take(size_t bytes);
+void budget_give(size_t bytes);
 uint32_t cells_hist_offset(int ncs, int nw);
 int cells_blocks_per_sm(int sum_mode, int warps, size_t smem);
 int bls_max_smem_per_block();

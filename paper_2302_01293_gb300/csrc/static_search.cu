@@ -83,7 +83,7 @@ extern "C" int qlp_bls_search_static(const qlp_bls_params* pin, int32_t n, const
                                      const double* y, const double* dy, double baseline,
                                      int32_t n_f, const double* freqs, const double* qmins,
                                      void* stream, float* sr, uint8_t* qidx, uint32_t* phase_bin,
-                                     float* s_best, float* r_best) {
+                                     float* s_best, float* r_best, int32_t* flags) {
   qlp_bls_params p;
   if (pin) p = *pin; else qlp_bls_params_default(&p);
   if (n < 2 || n_f < 1 || !tp || !y || !dy || !freqs || !qmins || !sr) return QLP_ERR_ARG;
@@ -91,10 +91,12 @@ extern "C" int qlp_bls_search_static(const qlp_bls_params* pin, int32_t n, const
       !(p.qmax_fac >= p.qmin_fac))
     return QLP_ERR_ARG;
   if (p.phase_mode < 0 || p.phase_mode > 2 || p.sum_mode < 0 || p.sum_mode > 2) return QLP_ERR_ARG;
+  // one shared histogram per frequency only: the per-duration variant needs the cell path
+  if (p.bin_mode != QLP_BIN_SHARED) return QLP_ERR_UNSUPPORTED;
   // this entry point folds every point; it runs QLP_SUM_FIXED as compensated sums
   const int sum_mode = p.sum_mode == QLP_SUM_PLAIN ? QLP_SUM_PLAIN : QLP_SUM_COMP;
   if (p.warps_per_block != 0 && p.warps_per_block != 4 && p.warps_per_block != 8 &&
-      p.warps_per_block != 16)
+      p.warps_per_block != 16 && p.warps_per_block != 32)
     return QLP_ERR_ARG;
   const int nq = qlp::n_q_of(p);
   if (nq < 1 || nq > qlp::kMaxQ) return QLP_ERR_UNSUPPORTED;
@@ -123,7 +125,7 @@ extern "C" int qlp_bls_search_static(const qlp_bls_params* pin, int32_t n, const
   const int smem_max = qlp::bls_max_smem_per_block();
   if (smem_max <= 0) return QLP_ERR_CUDA;
   const int budget = smem_max - 1024;
-  int warps = p.warps_per_block ? p.warps_per_block : 8;
+  int warps = p.warps_per_block ? std::min(p.warps_per_block, 16) : 8;  // as qlp_bls_plan: 32 is for cells
   auto hist_bytes = [&](int w) { return (size_t)w * NA * hist_stride * 4 + (size_t)w * qlp::kMaxQ * 4; };
   while (warps > 4 && hist_bytes(warps) > (size_t)budget / 2) warps /= 2;
   const size_t hb = (hist_bytes(warps) + 15) & ~(size_t)15;
@@ -207,5 +209,8 @@ extern "C" int qlp_bls_search_static(const qlp_bls_params* pin, int32_t n, const
   a.tile_off = (uint32_t)hb;
   const int phase = (ymax >= 4194304.0) ? QLP_PHASE_FP64 : p.phase_mode;
   if (qlp::launch_bls(a, phase, sum_mode, warps, blocks, smem, stream)) return QLP_ERR_CUDA;
+  // the kernel's error bits (histogram guard, work-queue bound) for the caller
+  if (flags && cudaMemcpyAsync(flags, ctl + 1, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return QLP_ERR_CUDA;
   return QLP_OK;
 }

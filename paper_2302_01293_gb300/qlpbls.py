@@ -21,6 +21,7 @@ BIN_SHARED, BIN_PER_Q = 0, 1
 MAD_RAW, MAD_RESID = 0, 1
 METHOD_AUTO, METHOD_POINTS, METHOD_CELLS = 0, 1, 2
 TREND_DOUBLES = 84
+CNN_ACT, CNN_GACT, CNN_LOGIT, CNN_DLOGIT = 0, 1, 2, 3
 
 STAR_UNSORTED, STAR_TOO_FEW, STAR_EMPTY_GRID, STAR_NBINS_CAP, STAR_ZERO_MAD = 1, 2, 4, 8, 16
 
@@ -51,7 +52,7 @@ class CParams(ctypes.Structure):
                 ("method", ctypes.c_int32), ("grid_mode", ctypes.c_int32),
                 ("coarse_bins", ctypes.c_int32), ("cell_window", ctypes.c_int32),
                 ("coarse_pmin", ctypes.c_double), ("coarse_pmax", ctypes.c_double),
-                ("bin_mode", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+                ("bin_mode", ctypes.c_int32), ("work_loop_bound", ctypes.c_int32)]
 
 
 @dataclasses.dataclass
@@ -79,7 +80,7 @@ class Params:
     coarse_pmin: float = 0.1
     coarse_pmax: float = 400.0
     bin_mode: int = 0
-    reserved1: int = 0
+    work_loop_bound: int = 0
 
     def to_c(self) -> CParams:
         c = CParams()
@@ -92,8 +93,16 @@ class Params:
         return cls(**{f.name: getattr(c, f.name) for f in dataclasses.fields(cls)})
 
 
+ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_DEVICE, ERR_UNSUPPORTED = -1, -2, -3, -4, -5
+DEVERR_QUEUE, DEVERR_NBINS, DEVERR_SNR_BINS = 1, 2, 4
+
+
 class QlpError(RuntimeError):
-    pass
+    """A library call returned a non-zero status; .code holds it (ERR_*)."""
+
+    def __init__(self, msg: str, code: int = 0):
+        super().__init__(msg)
+        self.code = code
 
 
 _lib = None
@@ -146,7 +155,7 @@ def lib():
                                              _i64]
             L.qlp_bls_batch_grid.restype = ctypes.c_int
             L.qlp_bls_search_static.argtypes = [_P(CParams), _i32, _vp, _vp, _vp, _d, _i32, _vp,
-                                                _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+                                                _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
             L.qlp_bls_search_static.restype = ctypes.c_int
             L.qlp_cnn_pack_w64.argtypes = [_vp, _vp, _i32, _vp]
             L.qlp_cnn_pack_w64.restype = ctypes.c_int
@@ -189,6 +198,12 @@ def lib():
             L.qlp_cnn_topk.restype = ctypes.c_int
             L.qlp_cnn_shape.argtypes = [_vp, _P(_i32), _P(_i32)]
             L.qlp_cnn_shape.restype = ctypes.c_int
+            L.qlp_cnn_get_tensor.argtypes = [_vp, _i32, _i32, _i32, _vp, _i64, _vp]
+            L.qlp_cnn_get_tensor.restype = ctypes.c_int
+            L.qlp_set_device_budget.argtypes = [_i64]
+            L.qlp_set_device_budget.restype = ctypes.c_int
+            L.qlp_device_bytes_held.argtypes = []
+            L.qlp_device_bytes_held.restype = _i64
             L.qlp_cnn_save.argtypes = [_vp, ctypes.c_char_p, _vp]
             L.qlp_cnn_save.restype = ctypes.c_int
             L.qlp_cnn_load.argtypes = [_vp, ctypes.c_char_p, _vp]
@@ -223,7 +238,7 @@ def _check(rc: int, what: str):
         L = lib()
         msg = L.qlp_strerror(rc).decode()
         cu = L.qlp_last_cuda_error().decode()
-        raise QlpError(f"{what}: {msg} ({rc}){' / ' + cu if cu else ''}")
+        raise QlpError(f"{what}: {msg} ({rc}){' / ' + cu if cu else ''}", rc)
 
 
 def _np_ptr(a):
@@ -514,11 +529,24 @@ def batch_grid(offsets, t, y, dy, rho=None, params: Params | None = None):
     return status, foff, freqs
 
 
-def search_static(tp, y, dy, baseline, freqs, qmins, out, params: Params | None = None, stream=None):
+def set_device_budget(nbytes: int):
+    """qlp_set_device_budget: cap the device bytes the library's plans and networks
+    hold at once (0 = no cap)."""
+    _check(lib().qlp_set_device_budget(int(nbytes)), "qlp_set_device_budget")
+
+
+def device_bytes_held() -> int:
+    """qlp_device_bytes_held: device bytes the library's plans and networks hold."""
+    return int(lib().qlp_device_bytes_held())
+
+
+def search_static(tp, y, dy, baseline, freqs, qmins, out, params: Params | None = None, stream=None,
+                  flags=None):
     """qlp_bls_search_static: one star's search with no device allocation inside
     the call. tp, y, dy: device float64 tensors (t - t_min sorted, flux, error);
     freqs, qmins: host float64 arrays; out: dict of device tensors sr, qidx, kbin,
-    s, r with at least len(freqs) entries (as from Plan.alloc_outputs)."""
+    s, r with at least len(freqs) entries (as from Plan.alloc_outputs); flags: an
+    optional device int32 tensor that receives the call's device error bits."""
     L = lib()
     freqs = np.ascontiguousarray(freqs, np.float64)
     qmins = np.ascontiguousarray(qmins, np.float64)
@@ -527,7 +555,8 @@ def search_static(tp, y, dy, baseline, freqs, qmins, out, params: Params | None 
                                  dy.data_ptr(), float(baseline), int(freqs.shape[0]),
                                  _np_ptr(freqs), _np_ptr(qmins), _stream_ptr(stream),
                                  out["sr"].data_ptr(), out["qidx"].data_ptr(), out["kbin"].data_ptr(),
-                                 out["s"].data_ptr(), out["r"].data_ptr())
+                                 out["s"].data_ptr(), out["r"].data_ptr(),
+                                 flags.data_ptr() if flags is not None else None)
     _check(rc, "qlp_bls_search_static")
     return out
 
@@ -573,6 +602,9 @@ class CNN:
         self._chk(lib().qlp_cnn_backward(self._h, x0.data_ptr(), labels.data_ptr(), int(x0.shape[0]),
                                          float(pos_weight), _stream_ptr(stream)), "qlp_cnn_backward")
 
+    def adam_step(self, lr: float, stream=None):
+        self._chk(lib().qlp_cnn_adam_step(self._h, float(lr), _stream_ptr(stream)), "qlp_cnn_adam_step")
+
     def train_step(self, x0, labels, pos_weight: float, lr: float, stream=None):
         self._chk(lib().qlp_cnn_train_step(self._h, x0.data_ptr(), labels.data_ptr(), int(x0.shape[0]),
                                            float(pos_weight), float(lr), _stream_ptr(stream)),
@@ -584,6 +616,20 @@ class CNN:
         rc = lib().qlp_cnn_loss(self._h, ctypes.byref(v), ctypes.byref(e), _stream_ptr(stream))
         self._chk(rc, "qlp_cnn_loss")
         return float(v.value)
+
+    def tensor(self, which: int, layer: int, batch: int, stream=None) -> np.ndarray:
+        """qlp_cnn_get_tensor: a kept tensor of the last forward / backward as a host
+        array: ACT / GACT layer 1..5 as float32 [batch][len][64] (from BF16),
+        LOGIT / DLOGIT as float32 [batch][len]."""
+        if which in (CNN_ACT, CNN_GACT):
+            raw = np.zeros((batch, self.length, 64), np.uint16)
+        else:
+            raw = np.zeros((batch, self.length), np.float32)
+        self._chk(lib().qlp_cnn_get_tensor(self._h, int(which), int(layer), int(batch), _np_ptr(raw),
+                                           raw.nbytes, _stream_ptr(stream)), "qlp_cnn_get_tensor")
+        if raw.dtype == np.uint16:
+            return (raw.astype(np.uint32) << 16).view(np.float32)
+        return raw
 
     def save(self, path: str, stream=None):
         self._chk(lib().qlp_cnn_save(self._h, os.fsencode(path), _stream_ptr(stream)), "qlp_cnn_save")

@@ -162,13 +162,13 @@ def uneven_single_sector(n_stars: int = 4096, seed: int = 2, frac_injected: floa
 
 
 def multi_sector(n_stars: int = 1024, seed: int = 3, max_sectors: int = 13,
-                 frac_injected: float = 0.5, rho_value: float = 1.41) -> Batch:
-    """1..max_sectors contiguous sectors at 200-s cadence with 1-d inter-sector gaps,
-    AR(1) red noise (phi = 0.9, stationary sigma 1e-3) plus white noise 1e-3,
-    injected P log-U(0.5, 100) d, depth log-U(3e-4, 1e-2)."""
+                 frac_injected: float = 0.5, rho_value: float = 1.41, min_sectors: int = 1) -> Batch:
+    """min_sectors..max_sectors contiguous sectors at 200-s cadence with 1-d
+    inter-sector gaps, AR(1) red noise (phi = 0.9, stationary sigma 1e-3) plus
+    white noise 1e-3, injected P log-U(0.5, 100) d, depth log-U(3e-4, 1e-2)."""
     rng = np.random.default_rng(seed)
     ts, ys, dys = [], [], []
-    nsec = rng.integers(1, max_sectors + 1, n_stars)
+    nsec = rng.integers(min_sectors, max_sectors + 1, n_stars)
     rho = np.full(n_stars, rho_value)
     rstar = np.ones(n_stars)
     inj = rng.uniform(size=n_stars) < frac_injected

@@ -2,17 +2,39 @@
 FP64 oracle on the same seeded inputs.
 
 Tolerances (stated once, used by every GPU parity test):
-  * SR: relative 1e-5 (the FP32 residue of an FP64-binned histogram);
+  * SR: relative 1e-5 (the benchmark spec's bound) on every frequency. The library
+    scores the chosen box once more in FP64 (from the exact integer sums of the
+    default path, or from the compensated histograms) and rounds that once to
+    FP32. Where every star of a plan took the exact path or the point path, the
+    frequencies at which the GPU and the oracle chose the same box are held to
+    relative 5e-7: half an FP32 ulp (6e-8) plus the integer weights'
+    quantisation (w d rounded to 2^-25 of the star's largest |w d|, a random walk
+    over the box's points that weighs most where s itself cancels; measured up
+    to 3.6e-7). The compensated cell path keeps FP32 local prefix sums (about
+    1e-6 relative on a bin) and is held to the 1e-5 bound only;
   * duration index j and start bin k of each frequency's maximum: equal, unless
     the oracle's own residue at the GPU's (j, k) is within relative 1e-5 of its
-    maximum (a near tie, where either answer is correct);
-  * S/N: absolute 1e-4 where |S/N| <= 100; above that relative 1e-6 (one FP32
-    ulp of SR already moves S/N by ~6e-8 of its value);
+    maximum (a near tie, where either answer is correct). At a near tie the
+    GPU's SR is compared with the oracle's residue of the GPU's box (to the same
+    bound as the same-box frequencies), and its S/N with the S/N that residue has on the oracle's trend
+    and sigma; every near tie is counted in the parity report;
+  * S/N (FP64-rescored modes): absolute 1e-4 where |S/N| <= 1000; above that
+    relative 1e-7. S/N is stored in FP32 (ulp 6.1e-5 at 1,000) and comes from
+    the FP32 SR, whose half-ulp rounding (6e-8 relative) moves S/N by
+    6e-8 (|S/N| + |trend| / sigma) and sigma's median selections by as much
+    again; at |S/N| = 1000 these sum to about 1e-4, beyond it to ~1e-7 of S/N;
+  * S/N (PLAIN sums, a study mode whose FP32 bins carry ~1e-6 relative
+    rounding): absolute 1e-4 where |S/N| <= 100, relative 1e-6 above;
   * best frequency index: equal, unless the oracle's S/N at the GPU's index is
     within the S/N tolerance of the oracle's maximum; P, q exact given the index,
     T0 absolute 1e-9 d, depth relative 1e-5.
+
+Every comparison adds its counts and error maxima to REPORT, which the test
+session writes out as JSON (see conftest.py).
 """
 from __future__ import annotations
+
+import os
 
 import numpy as np
 
@@ -20,13 +42,39 @@ import oracle
 from oracle import bls as ob
 
 SR_RTOL = 1e-5
+SR_RTOL_TIGHT = 5e-7
 SNR_ATOL = 1e-4
-SNR_RTOL_HIGH = 1e-6
+SNR_LIMIT_ABS = 1000.0        # FP64-rescored modes: absolute 1e-4 up to here
+SNR_RTOL_BEYOND = 1e-7
+SNR_LIMIT_ABS_PLAIN = 100.0
+SNR_RTOL_PLAIN = 1e-6
+
+# test name -> accumulated parity figures
+REPORT: dict = {}
 
 
-def snr_tol(v):
+def _entry():
+    name = os.environ.get("PYTEST_CURRENT_TEST", "unknown").split(" ")[0]
+    e = REPORT.get(name)
+    if e is None:
+        e = REPORT[name] = dict(stars=0, freqs=0, near_ties=0, sr_rel_max=0.0, sr_rel_max_same_box=0.0,
+                                snr_abs_max_le100=0.0, snr_abs_max_le1000=0.0, snr_rel_max_gt1000=0.0,
+                                snr_abs_max_seen=0.0, best_ties=0, bests=0)
+    return e
+
+
+def rescored(params) -> bool:
+    """True when the library scores each chosen box again in FP64 (every sum mode
+    but PLAIN)."""
+    from paper_2302_01293_gb300 import qlpbls
+    return params is None or params.sum_mode != qlpbls.SUM_PLAIN
+
+
+def snr_tol(v, exact: bool = True):
     v = np.abs(np.asarray(v, np.float64))
-    return np.where(v <= 100.0, SNR_ATOL, SNR_RTOL_HIGH * v)
+    if exact:
+        return np.where(v <= SNR_LIMIT_ABS, SNR_ATOL, SNR_RTOL_BEYOND * v)
+    return np.where(v <= SNR_LIMIT_ABS_PLAIN, SNR_ATOL, SNR_RTOL_PLAIN * v)
 
 
 def run_gpu(batch, params, with_snr=True):
@@ -42,6 +90,9 @@ def run_gpu(batch, params, with_snr=True):
     res["best"] = plan.best_host(out) if with_snr else None
     res["flags"] = flags
     res["plan"] = plan
+    res["exact"] = rescored(params)
+    # the tight SR bound holds when no star took the compensated cell path
+    res["sr_tight"] = res["exact"] and plan.n_cell_stars == plan.n_exact_stars
     return res
 
 
@@ -53,8 +104,14 @@ def oracle_star(batch, s, params=None):
     return pl, res
 
 
-def compare_spectrum(pl, ores, g, sl, label=""):
-    """Compare one star's SR / argmax boxes; returns a dict of stats."""
+def compare_spectrum(pl, ores, g, sl, label="", tight=None, box_value=None):
+    """Compare one star's SR / argmax boxes; returns a dict of stats, with
+    'alt_sr' = {frequency index: the oracle's residue of the GPU's box} at near
+    ties. box_value(i, j, k) evaluates a box (default: the shared-histogram
+    oracle); tight: hold same-box frequencies to SR_RTOL_TIGHT (default: as
+    run_gpu found the plan's paths, else True)."""
+    tight = g.get("sr_tight", True) if tight is None else tight
+    box_value = box_value or (lambda i, j, k: ob.box_value(pl, i, j, k))
     sr_g = g["sr"][sl].astype(np.float64)
     q_g = g["qidx"][sl].astype(np.int64)
     k_g = g["kbin"][sl].view(np.uint32).astype(np.int64)
@@ -70,34 +127,74 @@ def compare_spectrum(pl, ores, g, sl, label=""):
     rel = np.where(ok, np.abs(sr_g - ores.sr) / denom, 0.0)
     assert rel.max(initial=0.0) <= SR_RTOL, f"{label} SR rel {rel.max()} at {int(np.argmax(rel))}"
     mism = np.nonzero(ok & ((q_g != ores.j) | (k_g != ores.k)))[0]
+    alt = {}
+    tol = SR_RTOL_TIGHT if tight else SR_RTOL
     for i in mism:
-        v = ob.box_value(pl, int(i), int(q_g[i]), int(k_g[i]))
+        v = box_value(int(i), int(q_g[i]), int(k_g[i]))
         assert v >= ores.sr[i] * (1 - SR_RTOL), (
             f"{label} f#{i}: GPU box (j={q_g[i]}, k={k_g[i]}) oracle value {v} vs max {ores.sr[i]} "
             f"at (j={ores.j[i]}, k={ores.k[i]})")
+        assert abs(sr_g[i] - v) <= tol * abs(v), f"{label} f#{i}: near-tie SR {sr_g[i]} vs its box {v}"
+        alt[int(i)] = v
     same = ok & (q_g == ores.j) & (k_g == ores.k)
+    rel_same = np.where(same, rel, 0.0).max(initial=0.0)
+    assert rel_same <= tol, f"{label} same-box SR rel {rel_same} at {int(np.argmax(np.where(same, rel, 0)))}"
     if same.any():
         np.testing.assert_allclose(r_g[same], ores.r[same], rtol=2e-6, atol=1e-12, err_msg=label)
         np.testing.assert_allclose(s_g[same], ores.s[same], rtol=1e-5, atol=1e-6 * np.abs(ores.s).max(),
                                    err_msg=label)
-    return dict(n=n, sr_rel_max=float(rel.max(initial=0.0)), near_ties=int(mism.shape[0]))
+    e = _entry()
+    e["stars"] += 1
+    e["freqs"] += int(n)
+    e["near_ties"] += int(mism.shape[0])
+    e["sr_rel_max"] = max(e["sr_rel_max"], float(rel.max(initial=0.0)))
+    e["sr_rel_max_same_box"] = max(e["sr_rel_max_same_box"], float(rel_same))
+    return dict(n=n, sr_rel_max=float(rel.max(initial=0.0)), sr_rel_max_same_box=float(rel_same),
+                near_ties=int(mism.shape[0]), alt_sr=alt)
 
 
-def compare_snr(pl, ores, g, sl, best_g, label=""):
-    snr_o, _, sigma = oracle.spectral_snr(pl.freqs, ores.sr)
+def expected_snr(pl, ores, alt=None, mad_mode="raw"):
+    """The oracle's S/N, and at near ties the S/N of the residue of the GPU's box
+    on the oracle's own trend and sigma."""
+    snr_o, trend, sigma = oracle.spectral_snr(pl.freqs, ores.sr, mad_mode)
+    exp = snr_o.copy()
+    if alt and sigma > 0.0:
+        for i, v in alt.items():
+            exp[i] = (v - trend[i]) / sigma
+    return snr_o, exp, sigma
+
+
+def compare_snr(pl, ores, g, sl, best_g, label="", alt=None, exact=None, per_q=None):
+    exact = g.get("exact", True) if exact is None else exact
+    snr_o, exp, sigma = expected_snr(pl, ores, alt)
     snr_g = g["snr"][sl].astype(np.float64)
-    d = np.abs(snr_g - snr_o)
-    tol = snr_tol(snr_o)
-    assert np.all(d <= tol), f"{label} S/N worst {float((d - tol).max())} at {int(np.argmax(d - tol))}"
-    bo = oracle.best_candidate(pl, ores, snr_o, sigma)
+    d = np.abs(snr_g - exp)
+    tol = snr_tol(exp, exact)
+    assert np.all(d <= tol), (f"{label} S/N worst excess {float((d - tol).max())} at "
+                              f"{int(np.argmax(d - tol))} (S/N {exp[int(np.argmax(d - tol))]})")
+    a = np.abs(exp)
+    e = _entry()
+    lo = a <= 100.0
+    mid = (a > 100.0) & (a <= 1000.0)
+    hi = a > 1000.0
+    e["snr_abs_max_le100"] = max(e["snr_abs_max_le100"], float(d[lo].max(initial=0.0)))
+    e["snr_abs_max_le1000"] = max(e["snr_abs_max_le1000"], float(d[mid].max(initial=0.0)))
+    e["snr_rel_max_gt1000"] = max(e["snr_rel_max_gt1000"], float((d[hi] / a[hi]).max(initial=0.0)))
+    e["snr_abs_max_seen"] = max(e["snr_abs_max_seen"], float(a.max(initial=0.0)))
+    e["bests"] += 1
+    bo = oracle.best_candidate(pl, ores, snr_o, sigma, per_q=per_q)
     if bo is None:
         assert best_g["f_idx"] == -1, label
         return dict(snr_abs_max=float(d.max(initial=0.0)))
     fi = int(best_g["f_idx"])
     if fi != bo["f_idx"]:
-        assert snr_o[fi] >= bo["snr"] - snr_tol(bo["snr"]), f"{label} best index {fi} vs {bo['f_idx']}"
+        assert exp[fi] >= bo["snr"] - snr_tol(bo["snr"], exact), f"{label} best index {fi} vs {bo['f_idx']}"
+        e["best_ties"] += 1
         return dict(snr_abs_max=float(d.max()), best_tie=True)
     assert best_g["period"] == bo["period"], label
+    if fi in (alt or {}):  # a near tie at the best frequency: the GPU's own box
+        e["best_ties"] += 1
+        return dict(snr_abs_max=float(d.max()), best_tie=True)
     assert best_g["q"] == bo["q"] and best_g["j"] == bo["j"], label
     assert best_g["k"] == bo["k"] and best_g["m"] == bo["m"] and best_g["nbins"] == bo["nbins"], label
     assert abs(best_g["t0"] - bo["t0"]) <= 1e-9, label

@@ -202,3 +202,24 @@ def test_batch_planner_after_fork():
         os.waitpid(pid, 0)
         pytest.fail("the child's planner did not finish")
     assert os.WIFEXITED(status) and os.WEXITSTATUS(status) == 0
+
+
+def test_device_budget_setting_needs_no_gpu():
+    # the budget is host bookkeeping: set, read back, reject a negative cap
+    from paper_2302_01293_gb300 import qlpbls
+    L = qlpbls.lib()
+    assert L.qlp_set_device_budget(-1) == qlpbls.ERR_ARG
+    assert L.qlp_set_device_budget(1 << 30) == 0
+    assert qlpbls.device_bytes_held() == 0
+    assert L.qlp_set_device_budget(0) == 0
+
+
+def test_work_loop_bound_is_validated():
+    from paper_2302_01293_gb300 import qlpbls
+    import synth
+    b = synth.tiny_batch(n_stars=2, seed=3)
+    st, foff, freqs = qlpbls.batch_grid(b.offsets, b.t, b.y, b.dy, b.rho,
+                                        qlpbls.Params(work_loop_bound=3))
+    assert foff[-1] > 0
+    with pytest.raises(qlpbls.QlpError):
+        qlpbls.batch_grid(b.offsets, b.t, b.y, b.dy, b.rho, qlpbls.Params(work_loop_bound=-1))

@@ -10,7 +10,7 @@ import synth
 from oracle import plan as op
 from oracle import snr as osn
 from paper_2302_01293_gb300 import learned, qlpbls
-from parity import SR_RTOL, compare_spectrum, snr_tol
+from parity import SR_RTOL, compare_spectrum, expected_snr, snr_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -34,10 +34,11 @@ def test_coarse_stage_matches_oracle(gpu_lib):
         pl, ores = _oracle_star(b, s, p)
         sl = cs.plan.star_slice(s)
         assert np.array_equal(cs.plan.freqs[sl], pl.freqs)
-        compare_spectrum(pl, ores, g, sl, label=f"coarse star {s}")
-        snr_o, tr_o, sigma = osn.spectral_snr(pl.freqs, ores.sr)
-        d = np.abs(g["snr"][sl] - snr_o)
-        assert np.all(d <= snr_tol(snr_o))
+        st = compare_spectrum(pl, ores, g, sl, label=f"coarse star {s}",
+                              tight=cs.plan.n_cell_stars == cs.plan.n_exact_stars)
+        snr_o, exp, sigma = expected_snr(pl, ores, st["alt_sr"])
+        d = np.abs(g["snr"][sl] - exp)
+        assert np.all(d <= snr_tol(exp)), float((d - snr_tol(exp)).max())
         _, xs, ys = osn.trend_curve(pl.freqs, ores.sr)
         nx = int(trend[s, 0])
         assert nx == len(xs)
@@ -90,13 +91,19 @@ def test_windowed_refine_matches_oracle(gpu_lib):
         ores = oracle.bls_star(pl)
         sl = plan.star_slice(s)
         assert np.array_equal(plan.freqs[sl], pl.freqs) and pl.freqs.shape[0] > 0
-        compare_spectrum(pl, ores, g, sl, label=f"refine star {s}")
-        # S/N against the oracle's own coarse trend and sigma
+        st = compare_spectrum(pl, ores, g, sl, label=f"refine star {s}",
+                              tight=plan.n_cell_stars == plan.n_exact_stars)
+        # S/N against the oracle's own coarse trend and sigma (near ties: the
+        # oracle's residue of the GPU's box)
         plc, oc = _oracle_star(b, s, pco)
         _, xs, ys = osn.trend_curve(plc.freqs, oc.sr)
         _, _, sig = osn.spectral_snr(plc.freqs, oc.sr)
-        snr_o = osn.snr_from_trend(pl.freqs, ores.sr, xs, ys, sig)
-        assert np.all(np.abs(g["snr"][sl] - snr_o) <= snr_tol(snr_o) + 1e-5 * np.abs(snr_o))
+        sr_e = ores.sr.copy()
+        for i, v in st["alt_sr"].items():
+            sr_e[i] = v
+        snr_o = osn.snr_from_trend(pl.freqs, sr_e, xs, ys, sig)
+        d = np.abs(g["snr"][sl] - snr_o)
+        assert np.all(d <= snr_tol(snr_o)), float((d - snr_tol(snr_o)).max())
         assert best[s]["f_idx"] == int(np.argmax(g["snr"][sl]))
         assert abs(best[s]["period"] / b.period[s] - 1) < 0.01
 

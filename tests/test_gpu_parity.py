@@ -29,7 +29,7 @@ def _check_batch(batch, params, stars=None, with_snr=True):
         assert np.array_equal(plan.freqs[sl], pl.freqs)
         st = compare_spectrum(pl, ores, g, sl, label=f"star {s}")
         if with_snr:
-            st.update(compare_snr(pl, ores, g, sl, g["best"][s], label=f"star {s}"))
+            st.update(compare_snr(pl, ores, g, sl, g["best"][s], label=f"star {s}", alt=st["alt_sr"]))
         stats.append(st)
     return g, stats
 
@@ -229,8 +229,9 @@ def test_graph_replay_matches_oracle(gpu_lib):
         for s in range(b.n_stars):
             pl, ores = oracle_star(b, s)
             sl = plan.star_slice(s)
-            compare_spectrum(pl, ores, g, sl, label=f"graph star {s}")
-            compare_snr(pl, ores, g, sl, best[s], label=f"graph star {s}")
+            st = compare_spectrum(pl, ores, g, sl, label=f"graph star {s}",
+                                  tight=plan.n_cell_stars == plan.n_exact_stars)
+            compare_snr(pl, ores, g, sl, best[s], label=f"graph star {s}", alt=st["alt_sr"])
     assert plan.device_status() == 0
 
 
@@ -246,12 +247,15 @@ def test_autotune_choice_is_cached_and_exact(gpu_lib):
 
 @pytest.mark.parametrize("summ", [qlpbls.SUM_PLAIN, qlpbls.SUM_COMP])
 def test_per_duration_binning_variant(gpu_lib, summ):
-    # bin_mode PER_Q: one histogram of q_j / noverlap bins per duration, boxes of noverlap bins
+    # bin_mode PER_Q: one histogram of q_j / noverlap bins per duration, boxes of
+    # noverlap bins; the spectrum, the S/N and the best record against the oracle's
+    # per-duration BLS (near ties judged on the oracle's histogram j of the GPU's box)
+    import dataclasses
     import math
     from oracle import bls as ob
-    from oracle import snr as osn
     b = synth.uneven_single_sector(n_stars=3, seed=24)
-    g = run_gpu(b, qlpbls.Params(bin_mode=qlpbls.BIN_PER_Q, sum_mode=summ))
+    p = qlpbls.Params(bin_mode=qlpbls.BIN_PER_Q, sum_mode=summ)
+    g = run_gpu(b, p)
     assert g["flags"] == 0
     plan = g["plan"]
     for s in range(b.n_stars):
@@ -259,25 +263,16 @@ def test_per_duration_binning_variant(gpu_lib, summ):
         pl = oracle.plan_star(t, y, dy, float(b.rho[s]), float(b.rstar[s]))
         ores = ob.bls_star_per_q(pl)
         sl = plan.star_slice(s)
-        sr = g["sr"][sl].astype(np.float64)
-        q = g["qidx"][sl].astype(np.int64)
-        k = g["kbin"][sl].view(np.uint32).astype(np.int64)
-        rel = np.abs(sr - ores.sr) / np.maximum(ores.sr, 1e-300)
-        assert rel.max() <= 1e-5, rel.max()
-        for i in np.nonzero((q != ores.j) | (k != ores.k))[0]:   # near ties only
-            j = int(q[i])
+
+        def box(i, j, k, pl=pl):
             nb = int(math.ceil(3.0 / (float(pl.qmin[i]) * math.exp(0.1 * j))))
-            import dataclasses
             sub = dataclasses.replace(ob.restrict(pl, [i]), nbins=np.array([nb], np.int32),
                                       m=np.array([[3]], np.int32))
-            v = ob.box_value(sub, 0, 0, int(k[i]))
-            assert v >= ores.sr[i] * (1 - 1e-5)
-        snr, _, sigma = osn.spectral_snr(pl.freqs, ores.sr)
-        ob_best = osn.best_candidate(pl, ores, snr, sigma, per_q=(3.0, 0.1))
-        gb = g["best"][s]
-        if gb["f_idx"] == ob_best["f_idx"] and gb["j"] == ob_best["j"] and gb["k"] == ob_best["k"]:
-            assert (gb["m"], gb["nbins"]) == (ob_best["m"], ob_best["nbins"])
-            assert gb["q"] == ob_best["q"] and abs(gb["t0"] - ob_best["t0"]) < 1e-9
+            return ob.box_value(sub, 0, 0, k)
+
+        st = compare_spectrum(pl, ores, g, sl, label=f"per-q star {s}", box_value=box)
+        compare_snr(pl, ores, g, sl, g["best"][s], label=f"per-q star {s}", alt=st["alt_sr"],
+                    per_q=(3.0, 0.1))
 
 
 def test_pmin_at_three_stellar_radii(gpu_lib):
@@ -291,8 +286,8 @@ def test_pmin_at_three_stellar_radii(gpu_lib):
         pl, ores = oracle_star(b, s, oracle.Params(pmin_aR=3.0))
         sl = plan.star_slice(s)
         assert np.array_equal(plan.freqs[sl], pl.freqs)
-        compare_spectrum(pl, ores, g, sl, label=f"a=3R* star {s}")
-        compare_snr(pl, ores, g, sl, g["best"][s], label=f"a=3R* star {s}")
+        st = compare_spectrum(pl, ores, g, sl, label=f"a=3R* star {s}")
+        compare_snr(pl, ores, g, sl, g["best"][s], label=f"a=3R* star {s}", alt=st["alt_sr"])
 
 
 def test_sharded_driver_on_one_gpu_equals_host_call(gpu_lib):
