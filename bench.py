@@ -57,9 +57,10 @@ def _args():
     ap.add_argument("--workload", default="uneven", choices=["uneven", "multi_sector"],
                     help="the timed batch: uneven single-sector stars (default) or multi-sector stars "
                          "(1-13 sectors, for profiling the time-windowed path)")
-    ap.add_argument("--learned-train", type=int, default=8192)
-    ap.add_argument("--learned-eval", type=int, default=2048)
-    ap.add_argument("--sector-scale-stars", type=int, default=1024)
+    ap.add_argument("--learned-train", type=int, default=200000)
+    ap.add_argument("--learned-epochs", type=int, default=2)
+    ap.add_argument("--learned-eval", type=int, default=4096)
+    ap.add_argument("--sector-scale-stars", type=int, default=32768)
     ap.add_argument("--tune-sample", type=int, default=512)
     ap.add_argument("--no-tune", action="store_true", help="library defaults instead of the autotuner")
     ap.add_argument("--method", type=int, default=0, choices=[0, 1, 2],
@@ -159,132 +160,161 @@ SMEM_BYTES_PER_CLK_PER_SM = 128
 N_SMS = 152
 
 
-def learned_comparison(args):
-    """Stars per hour of the learned proposal vs the full-grid search on the same
-    held-out multi-sector stars, with the recall of the full grid's recoveries.
+def _training_batches(n_train: int, workers: int):
+    """The proposal set's seeded stars in chunks of 2,048 (seeds 100, 101, ...),
+    generated on a thread pool while the GPU turns each finished chunk into its
+    coarse spectrum (network input) and labels; returns [(x0, labels)] on the GPU."""
+    from concurrent.futures import ThreadPoolExecutor
+    import synth
+    from paper_2302_01293_gb300 import learned
+    sizes = [min(2048, n_train - a) for a in range(0, n_train, 2048)]
+    out = []
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        futs = {}
+        for c in range(min(len(sizes), 2 * workers)):
+            futs[c] = ex.submit(synth.proposal_set, sizes[c], 100 + c)
+        for c in range(len(sizes)):
+            tb = futs.pop(c).result()
+            nxt = c + 2 * workers
+            if nxt < len(sizes):
+                futs[nxt] = ex.submit(synth.proposal_set, sizes[nxt], 100 + nxt)
+            cs = learned.CoarseStage(tb)
+            out.append((cs.x0.clone(), learned.labels(tb, cs.params, "cuda")))
+            del cs, tb
+    return out
 
-    The network is trained here from scratch on seeded coarse spectra (no stored
-    weights). Both paths are timed wall-clock from host arrays to best records
-    (planning, uploads, searches, S/N, network), on one GPU."""
+
+def _smallest_k(curve, target=0.99):
+    for k in sorted(curve, key=int):
+        if curve[k] >= target:
+            return int(k)
+    return None
+
+
+def learned_comparison(args):
+    """The learned proposal against the same path without the network, and both
+    against the full-grid search, on held-out multi-sector stars.
+
+    The network is trained here from scratch on the proposal set's seeded stars
+    (no stored weights). Recall is counted among the injections the full grid
+    recovers. For K = 1, 2, 4, ..., 32 proposals per star, the network's top-K
+    coarse bins and the coarse S/N's own top-K are refined; the smallest K at which
+    each ranking reaches 99 % of the full grid's recoveries is then timed through
+    the library's one-call path (qlp_bls_search_learned, with and without the
+    network), wall clock from host arrays to best records, as is the full grid
+    through the host-buffer call."""
     import torch
     import synth
     from paper_2302_01293_gb300 import learned, qlpbls
+    workers = min(16, os.cpu_count() or 1)
     t0 = time.perf_counter()
-    batches = []
-    for c in range(0, args.learned_train, 2048):
-        tb = synth.proposal_set(min(2048, args.learned_train - c), seed=100 + c)
-        cs = learned.CoarseStage(tb)
-        batches.append((cs.x0.clone(), learned.labels(tb, cs.params, "cuda")))
-        del cs
+    batches = _training_batches(args.learned_train, workers)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
     net = qlpbls.CNN(max_batch=128, length=4096, seed=0)
-    losses = learned.train(net, batches, epochs=4, lr=3e-4, pos_weight=16.0)
+    t0 = time.perf_counter()
+    losses = learned.train(net, batches, epochs=args.learned_epochs, lr=3e-4, pos_weight=16.0)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     peaks, _ = _peaks()
     cnn = cnn_throughput(net, batches[0][0], batches[0][1], peaks.get("bf16_tflops", 1900.0))
-    test = synth.proposal_set(args.learned_eval, seed=999)
-    # both through their public one-call entries (the full grid: the host-buffer call,
-    # which overlaps host planning with device search); a warm-up, then the fastest
-    # of three runs of each
-    t_full = t_learned = float("inf")
-    for rep in range(4):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        best_full = qlpbls.run_host(test.offsets, test.t, test.y, test.dy, test.rho, test.rstar)["best"]
-        dt = time.perf_counter() - t0
-        if rep:
-            t_full = min(t_full, dt)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        best_l, _ = learned.search_learned(test, net, k=32)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if rep:
-            t_learned = min(t_learned, dt)
-    rf = learned.recovered(best_full, test)
-    rl = learned.recovered(best_l, test)
+    del batches
+    test = synth.in_chunks(lambda n, s: synth.proposal_set(n, s), args.learned_eval, 512, 999, workers)
+
+    def timed(fn, reps=3):  # a warm-up, then the fastest of `reps` runs
+        best_t, res = float("inf"), None
+        for rep in range(reps + 1):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            res = fn()
+            torch.cuda.synchronize()
+            if rep:
+                best_t = min(best_t, time.perf_counter() - t1)
+        return best_t, res
+
+    t_full, full = timed(lambda: qlpbls.run_host(test.offsets, test.t, test.y, test.dy, test.rho, test.rstar))
+    rf = learned.recovered(full["best"], test)
+    n_rf = max(int(rf.sum()), 1)
     coarse = learned.CoarseStage(test)
-    bins_a = learned.propose_without_network(coarse, 32).cpu().numpy()
-    best_a = learned.search_with_bins(test, coarse, bins_a)
-    ra = learned.recovered(best_a, test)
-    # recall with fewer proposals: the network's ranking against the coarse S/N's own
     bins_n = learned.propose(net, coarse.x0, 32).cpu().numpy()
-    at_k = {}
-    for k in (1, 4):
-        rn = learned.recovered(learned.search_with_bins(test, coarse, bins_n[:, :k]), test)
-        rk = learned.recovered(learned.search_with_bins(test, coarse, bins_a[:, :k]), test)
-        at_k[str(k)] = {"network": float((rn & rf).sum() / max(rf.sum(), 1)),
-                        "coarse_snr_without_network": float((rk & rf).sum() / max(rf.sum(), 1))}
+    bins_a = learned.propose_without_network(coarse, 32).cpu().numpy()
+    curve = {"network": {}, "coarse_snr_without_network": {}}
+    for k in (1, 2, 4, 8, 16, 32):
+        for name, bins in (("network", bins_n), ("coarse_snr_without_network", bins_a)):
+            r = learned.recovered(learned.search_with_bins(test, coarse, bins[:, :k]), test)
+            curve[name][str(k)] = float((r & rf).sum() / n_rf)
+    del coarse
+    k99 = {name: _smallest_k(c) for name, c in curve.items()}
     n = test.n_stars
-    sector_scale = sector_scale_line(net, args.sector_scale_stars) if args.sector_scale_stars > 0 else None
+    per_hour = {"full_grid": n / t_full * 3600.0}
+    for name, use_net in (("network", True), ("coarse_snr_without_network", False)):
+        for k in sorted({32, k99[name] or 32}):
+            t_l, (best_l, _) = timed(lambda: learned.search_learned(test, net if use_net else None, k=k))
+            rl = learned.recovered(best_l, test)
+            per_hour[f"{name}_k{k}"] = {"stars_per_hour": n / t_l * 3600.0, "seconds": t_l,
+                                        "recall": float((rl & rf).sum() / n_rf),
+                                        "speedup_vs_full": t_full / t_l}
+    gain = None
+    if k99["network"] is not None and k99["coarse_snr_without_network"] is not None:
+        a = per_hour[f"network_k{k99['network']}"]["stars_per_hour"]
+        b = per_hour[f"coarse_snr_without_network_k{k99['coarse_snr_without_network']}"]["stars_per_hour"]
+        gain = {"k99_network": k99["network"], "k99_without_network": k99["coarse_snr_without_network"],
+                "stars_per_hour_ratio": a / b}
+    sector_scale = sector_scale_line(net, args.sector_scale_stars, workers) if args.sector_scale_stars > 0 else None
     return {"workload": f"{n} held-out stars, 1-4 sectors at 200 s, 50 % injected "
                         "(P log-U(0.5, 100) d, depth log-U(1e-4, 1e-2))",
-            "train_stars": args.learned_train, "epochs": 4, "train_seconds": t_train,
-            "final_loss": losses[-1], "K": 32,
+            "train_stars": args.learned_train, "epochs": args.learned_epochs,
+            "train_data_seconds": t_data, "train_seconds": t_train, "final_loss": losses[-1],
             "full_recovered": int(rf.sum()), "injected": int(test.inj.sum()),
-            "recall": float((rl & rf).sum() / max(rf.sum(), 1)),
-            "recall_coarse_snr_topk_without_network": float((ra & rf).sum() / max(rf.sum(), 1)),
-            "recall_at_k": at_k,
-            "stars_per_hour_full": n / t_full * 3600.0,
-            "stars_per_hour_learned": n / t_learned * 3600.0,
-            "speedup": t_full / t_learned, "cnn": cnn, "sector_scale": sector_scale}
+            "recall_at_k": curve, "k_for_99pct_recall": k99, "stars_per_hour": per_hour,
+            "network_gain_at_99pct": gain, "cnn": cnn, "sector_scale": sector_scale}
 
 
-def sector_scale_line(net, n_stars: int):
-    """The sector-scale mix (geometric sector counts, mean 3, at most 40; mixed rho,
-    R*, noise; 1 % injected): the full-grid path through the public host-buffer call
-    and the learned path through its one-call C entry, each timed wall clock from host
-    arrays to best records (the faster of two runs after a warm-up), on one GPU; plus
-    the device step
-    (search + S/N of a plan built once, CUDA events)."""
+def sector_scale_line(net, n_stars: int, workers: int):
+    """The sector-scale mix (geometric sector counts, mean 3, at most 40, plus 16
+    stars of 40 sectors; mixed rho, R*, noise; 1 % injected), generated in
+    independently seeded chunks: the full-grid path through the public host-buffer
+    call and the learned path through its one-call C entry (K = 32), each timed wall
+    clock from host arrays to best records on one GPU (the full grid once, the
+    learned path the faster of two runs after a warm-up)."""
     import torch
     import synth
     from paper_2302_01293_gb300 import learned, qlpbls
-    b = synth.sector_scale(n_stars=n_stars, seed=6)
-    t_full = t_learned = float("inf")
-    for rep in range(3):  # a warm-up, then the faster of two runs of each
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        full = qlpbls.run_host(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar)
-        if rep:
-            t_full = min(t_full, time.perf_counter() - t0)
+    mix = synth.in_chunks(lambda n, s: synth.sector_scale(n, seed=s), n_stars, 2048, 6000, workers)
+    deep = synth.sector_scale(16, seed=5999, sectors=40)
+    b = synth.concat([mix, deep], "sector_scale_200s")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    full = qlpbls.run_host(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar)
+    t_full = time.perf_counter() - t0
+    t_learned = float("inf")
+    best_l = None
+    for rep in range(3):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         best_l, _ = learned.search_learned(b, net, k=32)
         torch.cuda.synchronize()
         if rep:
             t_learned = min(t_learned, time.perf_counter() - t0)
-    plan = qlpbls.Plan(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar)
-    out = plan.alloc_outputs()
-    plan.search(out)
-    plan.snr(out)
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    plan.search(out)
-    plan.snr(out)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    if plan.device_status():
-        raise RuntimeError("device flags in the sector-scale search")
     rf = learned.recovered(full["best"], b)
     rl = learned.recovered(best_l, b)
-    kmax = int(synth.sector_counts_geometric(n_stars, 6, 3.0, 40).max())
-    return {"workload": f"{n_stars} stars, geometric sector counts (mean 3, at most 40; {kmax} here), "
-                        "200 s, 1 % injected",
-            "points": int(b.offsets[-1]), "point_freq": plan.work, "trial_freqs": plan.n_freq_total,
-            "windowed_stars": plan.n_windowed, "exact_path_stars": plan.n_exact_stars,
-            "device_step_ms": ms, "device_point_freq_per_s": plan.work / (ms * 1e-3),
-            "full_grid_e2e_s": t_full, "stars_per_hour_full": n_stars / t_full * 3600.0,
-            "learned_e2e_s": t_learned, "stars_per_hour_learned": n_stars / t_learned * 3600.0,
+    # sectors per star from its span: k sectors of 27.4 d with 1-d gaps span 28.4 k - 1 d
+    nsec = np.rint((b.t[b.offsets[1:] - 1] - b.t[b.offsets[:-1]] + 1.0) / 28.4).astype(int)
+    ok = full["best"]["f_idx"] >= 0
+    return {"workload": f"{b.n_stars} stars: geometric sector counts (mean 3, at most 40) and 16 of "
+                        "40 sectors, 200 s, 1 % injected",
+            "points": int(b.offsets[-1]), "max_sectors": int(nsec.max()),
+            "searched_stars": int(ok.sum()),
+            "full_grid_e2e_s": t_full, "stars_per_hour_full": b.n_stars / t_full * 3600.0,
+            "learned_e2e_s": t_learned, "stars_per_hour_learned": b.n_stars / t_learned * 3600.0,
+            "speedup": t_full / t_learned,
             "injected": int(b.inj.sum()), "full_recovered": int(rf.sum()),
-            "learned_recovered_of_full": int((rl & rf).sum())}
+            "learned_recovered_of_full": int((rl & rf).sum()),
+            "recall": float((rl & rf).sum() / max(int(rf.sum()), 1))}
 
 
-# CNN FLOPs per input bin (kernel 9, 64 channels): conv 2->64, four 64->64, 64->1
-CNN_FWD_FLOP_PER_BIN = 2 * 9 * (2 * 64 + 4 * 64 * 64 + 64)
+# CNN FLOPs per input bin (kernel 9, 64 channels): conv 6->64, four 64->64, 64->1
+CNN_FWD_FLOP_PER_BIN = 2 * 9 * (6 * 64 + 4 * 64 * 64 + 64)
 CONV64_FLOP_PER_BIN = 2 * 9 * 64 * 64
 # training step: forward, input gradients of layers 6..2 (not of layer 1), all
 # weight gradients (as many FLOPs as the forward)
@@ -559,10 +589,7 @@ def main():
     default_batch = args.workload == "uneven" and args.stars == 4096 and args.seed == 2
     if cells_dominant and kernel_id == 1 and default_batch and params.sum_mode == 1:
         traffic = 423.0e6 * plan.n_points / 10638874
-    if kernel_id == 2 and default_batch:
-        # cells_fixed_kernel: ncu capture on 1,024 stars of this workload (513.1 MB read +
-        # 83.2 MB written), scaled by points (tables, records and outputs grow with them)
-        traffic = 596.3e6 * plan.n_points / 10638874
+
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "TFLOP/s",
                 "frac": achieved / peak_ops, "traffic": traffic, "kernel": kernel,
                 "algorithmic": unit_note,

@@ -51,7 +51,8 @@ extern "C" {
 #define QLP_STAR_UNSORTED    1  /* t decreases somewhere (after dropping invalid points) */
 #define QLP_STAR_TOO_FEW     2  /* fewer than 2 valid points */
 #define QLP_STAR_EMPTY_GRID  4  /* Pmin >= Pmax or zero baseline: nothing to search */
-#define QLP_STAR_NBINS_CAP   8  /* some frequency needs more phase bins than nbins_cap */
+#define QLP_STAR_NBINS_CAP   8  /* some frequency needs more phase bins than nbins_cap, or than the
+                                   shared-memory histograms of the star's search path hold */
 #define QLP_STAR_ZERO_MAD   16  /* sigma_SR = 0: S/N undefined, no candidate */
 #define QLP_STAR_UNSUPPORTED 32 /* the star cannot be searched with these options (bin_mode
                                    QLP_BIN_PER_Q needs the cell path: one point per cell) */
@@ -292,13 +293,20 @@ int qlp_bls_snr(qlp_bls_plan_t* plan, void* stream, const float* sr, const uint8
  *   from that trend and sigma instead of the spectrum's own (device arrays,
  *   n_stars records, same star order).
  * qlp_bls_coarse_tensor -- for a grid_mode 1 plan: the network input, device BF16
- *   [n_stars][n_bins][2] = (asinh(S/N / 4), 1) on the star's searched coarse bins,
- *   (0, 0) elsewhere; n_bins must equal coarse_bins.
+ *   [n_stars][n_bins][QLP_CNN_IN_CH]; on the star's searched coarse bin k channel 0
+ *   is a(k) = asinh(S/N(k) / 4) and channel 1 is 1; channels 2-5 are a() at the
+ *   bins of the periods 2P, P/2, 3P and P/3, k + d2, k - d2, k + d3, k - d3 with
+ *   d_h = round((coarse_bins - 1) ln h / ln(coarse_pmax / coarse_pmin)) (0 where
+ *   that bin is off the grid or not searched); every channel is 0 on bins not
+ *   searched. n_bins must equal coarse_bins. snr_rows (device FP32
+ *   [n_stars][n_bins], may be NULL) receives the S/N itself on the searched bins
+ *   and 0 elsewhere (the ranking of the search without the network).
  * qlp_cnn_topk -- indices (device int32 [batch][k]) of the k largest logits of each
- *   row among bins whose x0 channel 1 is positive, largest first; -1 past the last
- *   valid bin.
+ *   row among bins whose x0 (BF16 [batch][len][QLP_CNN_IN_CH]) channel 1 is
+ *   positive, largest first (ties: the lower bin); -1 past the last valid bin.
  */
 #define QLP_TREND_DOUBLES 84
+#define QLP_CNN_IN_CH 6   /* channels of the network input (qlp_bls_coarse_tensor) */
 int qlp_bls_plan_windows(const qlp_bls_params* p, int32_t n_stars, const int64_t* offsets,
                          const double* t, const double* y, const double* dy, const double* rho,
                          const double* rstar, const int64_t* win_offsets, const double* win_flo,
@@ -307,7 +315,24 @@ int qlp_bls_snr_trend(qlp_bls_plan_t* plan, void* stream, const float* sr, const
                       const uint32_t* phase_bin, const float* s_best, const float* r_best,
                       const double* trend_in, double* trend_out, float* snr, qlp_bls_best* best);
 int qlp_bls_coarse_tensor(qlp_bls_plan_t* plan, void* stream, const float* snr, int32_t n_bins,
-                          void* out);
+                          void* out, float* snr_rows);
+/*
+ * Coarse-grid arithmetic of the learned path, on the host (the same functions
+ * qlp_bls_search_learned uses), for callers that sequence its stages themselves:
+ * qlp_bls_coarse_periods -- periods[i] = coarse_pmin (coarse_pmax / coarse_pmin)^
+ *   (x[i] / (coarse_bins - 1)) for (fractional) coarse bin positions x.
+ * qlp_bls_coarse_bins -- the nearest coarse bin of each period (rounded half to
+ *   even), -1 outside [0, coarse_bins) or for a period <= 0.
+ * qlp_bls_proposal_windows -- frequency windows [1/P(k + half_width), 1/P(k -
+ *   half_width)] around every valid (>= 0) bin k of bins (int32 [n_stars][k]),
+ *   star by star: win_offsets (int64 [n_stars + 1]) always; win_lo / win_hi
+ *   (double [capacity]) when given, QLP_ERR_ARG if capacity < win_offsets[n_stars].
+ */
+int qlp_bls_coarse_periods(const qlp_bls_params* p, int32_t n, const double* x, double* periods);
+int qlp_bls_coarse_bins(const qlp_bls_params* p, int32_t n, const double* periods, int32_t* bins);
+int qlp_bls_proposal_windows(const qlp_bls_params* p, int32_t n_stars, const int32_t* bins, int32_t k,
+                             double half_width, int64_t* win_offsets, double* win_lo, double* win_hi,
+                             int64_t capacity);
 int qlp_cnn_topk(const float* logits, const void* x0, int32_t batch, int32_t len, int32_t k,
                  int32_t* out, void* stream);
 
@@ -573,11 +598,12 @@ int qlp_cnn_conv64(const void* x, const void* wpack, const float* bias, const vo
                    int32_t batch, int32_t len, int32_t relu, int32_t* err, void* stream);
 
 /*
- * The network: input x0 BF16 [batch][len][2] (channel 0 the coarse S/N, channel 1
- * the valid-bin mask), conv(2->64)+ReLU, 4 x [conv(64->64)+ReLU], conv(64->1): one
- * logit per bin, kernel 9, zero padding, len a multiple of 128.
+ * The network: input x0 BF16 [batch][len][QLP_CNN_IN_CH] (as qlp_bls_coarse_tensor
+ * writes it: the coarse S/N, the valid-bin mask, the S/N at the bins of 2P, P/2, 3P
+ * and P/3), conv(6->64)+ReLU, 4 x [conv(64->64)+ReLU], conv(64->1): one logit per
+ * bin, kernel 9, zero padding, len a multiple of 128.
  * Parameters (FP32, qlp_cnn_n_params() of them) in the order
- *   W1 [9][64][2], b1 [64], (W_k [9][64][64], b_k [64]) for k = 2..5, W6 [9][64], b6,
+ *   W1 [9][64][6], b1 [64], (W_k [9][64][64], b_k [64]) for k = 2..5, W6 [9][64], b6,
  * with W[tap][out channel][in channel]. Weights are the FP32 masters of Adam; the
  * 64->64 layers compute with BF16 copies on the tensor cores, activations are
  * BF16, accumulation FP32.
@@ -649,7 +675,9 @@ int qlp_cnn_load(qlp_cnn_t* net, const char* path, void* stream);
  *      proposed bin k_b, P(x) = coarse_pmin (coarse_pmax/coarse_pmin)^(x/(coarse_bins-1));
  *   4. the paper's grid (grid_mode 0) restricted to those windows, searched, and
  *      scored with the coarse trend and sigma_SR.
- * net must have len == coarse_bins. best_host (n_stars records, required) gets the
+ * net must have len == coarse_bins; net = NULL ranks the coarse bins by their S/N
+ * itself instead (the same path without the network, its ablation). best_host
+ * (n_stars records, required) gets the
  * best candidate of step 4 (f_idx indexes the windowed grid; a star with no grid
  * frequency in its windows gets f_idx -1 and QLP_STAR_EMPTY_GRID). bins_host
  * (int32 [n_stars][k], optional) gets the proposed bins, -1 past a star's last

@@ -2,12 +2,14 @@
 
 The learned proposal is not in the paper; its network is defined here in the
 plainest form so that the GPU training kernels can be checked against it:
-  x0 [B, L, 2]  ->  conv(2 -> 64) + ReLU  ->  4 x [conv(64 -> 64) + ReLU]
+  x0 [B, L, 6]  ->  conv(6 -> 64) + ReLU  ->  4 x [conv(64 -> 64) + ReLU]
                 ->  conv(64 -> 1)  ->  logits [B, L]
+(the six input channels: the coarse S/N, the valid-bin mask and the S/N at the
+bins of the periods 2P, P/2, 3P and P/3; the network takes them as given)
 every conv with kernel 9 and zero padding: y[l, co] = b[co] + sum_k sum_ci
 W[k, co, ci] x[l + k - 4, ci]. Loss: BCE with logits, positives weighted by
 pos_weight, mean over B L. Update: Adam (beta 0.9, 0.999, eps 1e-8, bias-corrected).
-Parameters flatten in the order W1 [9,64,2], b1, (W_k [9,64,64], b_k) k = 2..5,
+Parameters flatten in the order W1 [9,64,6], b1, (W_k [9,64,64], b_k) k = 2..5,
 W6 [9,64] (the one output channel), b6.
 """
 from __future__ import annotations
@@ -16,7 +18,8 @@ import numpy as np
 
 K = 9
 C = 64
-SHAPES = [("W1", (K, C, 2)), ("b1", (C,))]
+IN_CH = 6
+SHAPES = [("W1", (K, C, IN_CH)), ("b1", (C,))]
 for _k in range(2, 6):
     SHAPES += [(f"W{_k}", (K, C, C)), (f"b{_k}", (C,))]
 SHAPES += [("W6", (K, 1, C)), ("b6", (1,))]

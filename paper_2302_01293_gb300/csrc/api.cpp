@@ -483,6 +483,16 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
     if (!old_fits) continue;
     if (p.method == 2 || p.bin_mode == QLP_BIN_PER_Q || h.cells_work < pp_work) method[(size_t)s] = kMethodCells;
   }
+  // the per-point kernel holds NA histogram arrays of round32(nbins + kMPad) floats per
+  // warp in shared memory, at least 4 warps and one 32-point tile beside them: a star
+  // left on that path with more bins than they hold is flagged, not searched
+  {
+    const int64_t rows = ((int64_t)budget - 32 * 16 - 4 * kMaxQ * 4) / (4LL * NA * 4);
+    const int32_t pp_nb_cap = (int32_t)(rows / 32 * 32) - kMPad;
+    for (int32_t s = 0; s < n_stars; ++s)
+      if (sp[(size_t)s].status == 0 && method[(size_t)s] == kMethodPoints && sp[(size_t)s].nbins_max > pp_nb_cap)
+        sp[(size_t)s].status |= QLP_STAR_NBINS_CAP;
+  }
   if (p.bin_mode == QLP_BIN_PER_Q)  // per-duration histograms exist on the cell path only
     for (int32_t s = 0; s < n_stars; ++s)
       if (sp[(size_t)s].status == 0 && method[(size_t)s] != kMethodCells) sp[(size_t)s].status = QLP_STAR_UNSUPPORTED;
@@ -967,10 +977,14 @@ int qlp_bls_snr(qlp_bls_plan_t* pl, void* stream, const float* sr, const uint8_t
   return qlp_bls_snr_trend(pl, stream, sr, qidx, phase_bin, s_best, r_best, nullptr, nullptr, snr, best);
 }
 
-int qlp_bls_coarse_tensor(qlp_bls_plan_t* pl, void* stream, const float* snr, int32_t n_bins, void* out) {
+int qlp_bls_coarse_tensor(qlp_bls_plan_t* pl, void* stream, const float* snr, int32_t n_bins, void* out,
+                          float* snr_rows) {
   if (!pl || !out || n_bins <= 0 || (pl->f_off.back() > 0 && !snr)) return QLP_ERR_ARG;
   if (pl->p.grid_mode != 1 || n_bins != pl->p.coarse_bins) return QLP_ERR_ARG;
-  const int e = launch_coarse_tensor(pl->d_stars, pl->n_stars, snr, n_bins, out, stream);
+  // harmonic offsets on the log-period grid: the bins of 2P and 3P lie d2 and d3 above
+  const double per_bin = std::log(pl->p.coarse_pmax / pl->p.coarse_pmin) / (double)(n_bins - 1);
+  const int d2 = (int)std::nearbyint(std::log(2.0) / per_bin), d3 = (int)std::nearbyint(std::log(3.0) / per_bin);
+  const int e = launch_coarse_tensor(pl->d_stars, pl->n_stars, snr, n_bins, out, snr_rows, d2, d3, stream);
   return e ? cuda_fail((cudaError_t)e, "coarse tensor launch") : QLP_OK;
 }
 

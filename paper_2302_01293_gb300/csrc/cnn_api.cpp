@@ -1,6 +1,7 @@
 // C-ABI of the learned period proposal's network (declared in include/qlp_bls.h):
-// a 6-layer 1-D CNN over a 2-channel coarse spectrum (S/N, valid mask):
-//   conv(2->64)+ReLU, 4 x [conv(64->64)+ReLU], conv(64->1) -> one logit per bin,
+// a 6-layer 1-D CNN over the coarse spectrum's QLP_CNN_IN_CH channels (S/N, valid
+// mask, S/N at the bins of 2P, P/2, 3P and P/3):
+//   conv(6->64)+ReLU, 4 x [conv(64->64)+ReLU], conv(64->1) -> one logit per bin,
 // kernel 9, same padding. Parameters are FP32 masters (Adam); the 64->64 layers
 // run on the tensor cores from BF16 copies repacked after every update.
 #include <cuda_runtime.h>
@@ -35,8 +36,8 @@ using namespace qlp;
 
 namespace {
 
-constexpr int kCh = 64, kK = 9;
-constexpr int kW1 = kK * kCh * 2, kW64 = kK * kCh * kCh, kW6 = kK * kCh;
+constexpr int kCh = 64, kK = 9, kIn = QLP_CNN_IN_CH;
+constexpr int kW1 = kK * kCh * kIn, kW64 = kK * kCh * kCh, kW6 = kK * kCh;
 // parameter offsets: [W1 | b1 | (W_k | b_k) k = 2..5 | W6 | b6]
 constexpr int kOffW1 = 0, kOffB1 = kW1;
 constexpr int off_w(int k) { return kW1 + kCh + (k - 2) * (kW64 + kCh); }  // k = 2..5
@@ -161,7 +162,7 @@ int qlp_cnn_create(int32_t max_batch, int32_t len, uint64_t seed, qlp_cnn_t** ou
   // starts at -4 (a prior of ~2 % positives)
   std::vector<float> h(kNParams, 0.f);
   uint64_t st = seed * 0x9e3779b97f4a7c15ull + 12345;
-  for (int i = 0; i < kW1; ++i) h[kOffW1 + i] = (float)(normal(st) * std::sqrt(2.0 / (kK * 2)));
+  for (int i = 0; i < kW1; ++i) h[kOffW1 + i] = (float)(normal(st) * std::sqrt(2.0 / (kK * kIn)));
   for (int k = 2; k <= 5; ++k)
     for (int i = 0; i < kW64; ++i) h[off_w(k) + i] = (float)(normal(st) * std::sqrt(2.0 / (kK * kCh)));
   for (int i = 0; i < kW6; ++i) h[kOffW6 + i] = (float)(normal(st) * std::sqrt(1.0 / (kK * kCh)));
@@ -311,7 +312,7 @@ int qlp_cnn_backward(qlp_cnn_t* n, const void* x0, const float* labels, int32_t 
     CKL(launch_conv64(n->gact[k], n->pack_b[k - 2], nullptr, n->act[k - 1], n->gact[k - 1], n->err, batch, L, 0,
                       stream));
   }
-  CKL(launch_dw_small(n->gact[1], 0, x0, n->partial, n->grads + kOffW1, batch, L, kCh, 2, stream));
+  CKL(launch_dw_small(n->gact[1], 0, x0, n->partial, n->grads + kOffW1, batch, L, kCh, kIn, stream));
   return QLP_OK;
 }
 

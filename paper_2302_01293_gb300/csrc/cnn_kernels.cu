@@ -243,33 +243,34 @@ int launch_pack_w64(const float* w, void* out, int transpose, void* stream) {
 
 
 // ------------------------------------------------------------------ other layers
-// First layer 2 -> 64 channels and last layer 64 -> 1 channel (kernel 9, same
+// First layer QLP_CNN_IN_CH -> 64 channels and last layer 64 -> 1 channel (kernel 9, same
 // padding) on the CUDA cores; their weight gradients and the bias gradients as
 // two-stage reductions (per-CTA partial sums, then a sum over CTAs); BCE with
 // logits; Adam with FP32 master weights.
 
-// x0 [B][L][2] BF16 -> a1 [B][L][64] BF16 = relu(b1 + conv(x0, W1)), W1 [9][64][2]
+// x0 [B][L][CI] BF16 -> a1 [B][L][64] BF16 = relu(b1 + conv(x0, W1)), W1 [9][64][CI]
 __global__ void __launch_bounds__(128) conv_in_kernel(const __nv_bfloat16* x0, const float* w1,
                                                       const float* b1, __nv_bfloat16* a1, int batch,
                                                       int len) {
-  __shared__ float sw[kTaps * kC * 2];
+  constexpr int CI = QLP_CNN_IN_CH;
+  __shared__ float sw[kTaps * kC * CI];
   __shared__ float sb[kC];
-  for (int i = threadIdx.x; i < kTaps * kC * 2; i += blockDim.x) sw[i] = w1[i];
+  for (int i = threadIdx.x; i < kTaps * kC * CI; i += blockDim.x) sw[i] = w1[i];
   for (int i = threadIdx.x; i < kC; i += blockDim.x) sb[i] = b1[i];
   __syncthreads();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= batch * len) return;
   const int b = p / len, l = p - b * len;
-  float xv[kTaps][2];
+  float xv[kTaps][CI];
 #pragma unroll
   for (int kk = 0; kk < kTaps; ++kk) {
     const int ll = l + kk - kTaps / 2;
     const bool in = ll >= 0 && ll < len;
-    xv[kk][0] = in ? __bfloat162float(x0[((size_t)b * len + ll) * 2 + 0]) : 0.f;
-    xv[kk][1] = in ? __bfloat162float(x0[((size_t)b * len + ll) * 2 + 1]) : 0.f;
+#pragma unroll
+    for (int ci = 0; ci < CI; ++ci)
+      xv[kk][ci] = in ? __bfloat162float(x0[((size_t)b * len + ll) * CI + ci]) : 0.f;
   }
   __nv_bfloat16* out = a1 + (size_t)p * kC;
-#pragma unroll
   for (int c0 = 0; c0 < kC; c0 += 8) {
     __align__(16) __nv_bfloat16 o[8];
 #pragma unroll
@@ -278,7 +279,8 @@ __global__ void __launch_bounds__(128) conv_in_kernel(const __nv_bfloat16* x0, c
       float z = sb[co];
 #pragma unroll
       for (int kk = 0; kk < kTaps; ++kk)
-        z += sw[(kk * kC + co) * 2 + 0] * xv[kk][0] + sw[(kk * kC + co) * 2 + 1] * xv[kk][1];
+#pragma unroll
+        for (int ci = 0; ci < CI; ++ci) z += sw[(kk * kC + co) * CI + ci] * xv[kk][ci];
       o[e] = __float2bfloat16_rn(fmaxf(z, 0.f));
     }
     *reinterpret_cast<uint4*>(out + c0) = *reinterpret_cast<const uint4*>(o);
@@ -525,7 +527,7 @@ __global__ void __launch_bounds__(128) wgrad64_tc_kernel(const __nv_bfloat16* dy
   if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
-// Partial gradients of a small layer: n_co x n_ci channels (first layer 64 x 2 with
+// Partial gradients of a small layer: n_co x n_ci channels (first layer 64 x QLP_CNN_IN_CH with
 // dY BF16, last layer 1 x 64 with dY FP32). One thread per (kk, co, ci) output
 // plus n_co bias outputs; each CTA covers a range of positions.
 template <typename TY>
@@ -636,7 +638,7 @@ int launch_wgrad64(const void* dy, const void* x, float* partial, float* out, in
   return (int)cudaGetLastError();
 }
 
-// dW and db of the first (dy BF16 [B][L][64], x BF16 [B][L][2]) or last (dy FP32
+// dW and db of the first (dy BF16 [B][L][64], x BF16 [B][L][QLP_CNN_IN_CH]) or last (dy FP32
 // [B][L], x BF16 [B][L][64]) layer into out[9 co ci + co]
 int launch_dw_small(const void* dy, int dy_is_f32, const void* x, float* partial, float* out, int batch,
                     int len, int n_co, int n_ci, void* s) {

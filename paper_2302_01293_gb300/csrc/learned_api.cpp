@@ -61,7 +61,71 @@ int alloc_spectrum(DevBufs& b, int64_t nf, int32_t n_stars, Spectrum* o) {
   return QLP_OK;
 }
 
+// P(x) = coarse_pmin (coarse_pmax / coarse_pmin)^(x / (coarse_bins - 1)): the period
+// of (fractional) coarse bin x.
+double coarse_period(const qlp_bls_params& p, double x) {
+  return p.coarse_pmin * std::pow(p.coarse_pmax / p.coarse_pmin, x / (double)(p.coarse_bins - 1));
+}
+
+bool coarse_ok(const qlp_bls_params* p) {
+  return p && p->coarse_bins >= 2 && p->coarse_pmin > 0.0 && p->coarse_pmax > p->coarse_pmin;
+}
+
+// Frequency windows [1/P(k + w), 1/P(k - w)] around every valid (k >= 0) proposed bin,
+// star by star; offsets[s] .. offsets[s + 1] - 1 are star s's windows.
+void proposal_windows(const qlp_bls_params& p, int32_t n_stars, const int32_t* bins, int32_t k, double w,
+                      std::vector<int64_t>* off, std::vector<double>* lo, std::vector<double>* hi) {
+  off->assign((size_t)n_stars + 1, 0);
+  lo->clear();
+  hi->clear();
+  for (int32_t s = 0; s < n_stars; ++s) {
+    for (int32_t i = 0; i < k; ++i) {
+      const int32_t kb = bins[(size_t)s * k + i];
+      if (kb < 0) continue;
+      lo->push_back(1.0 / coarse_period(p, (double)kb + w));
+      hi->push_back(1.0 / coarse_period(p, (double)kb - w));
+    }
+    (*off)[(size_t)s + 1] = (int64_t)lo->size();
+  }
+}
+
 }  // namespace
+
+extern "C" int qlp_bls_coarse_periods(const qlp_bls_params* p, int32_t n, const double* x, double* periods) {
+  if (!coarse_ok(p) || n < 0 || (n > 0 && (!x || !periods))) return QLP_ERR_ARG;
+  for (int32_t i = 0; i < n; ++i) periods[i] = coarse_period(*p, x[i]);
+  return QLP_OK;
+}
+
+extern "C" int qlp_bls_coarse_bins(const qlp_bls_params* p, int32_t n, const double* periods, int32_t* bins) {
+  if (!coarse_ok(p) || n < 0 || (n > 0 && (!periods || !bins))) return QLP_ERR_ARG;
+  const double scale = (double)(p->coarse_bins - 1) / std::log(p->coarse_pmax / p->coarse_pmin);
+  for (int32_t i = 0; i < n; ++i) {
+    if (!(periods[i] > 0.0)) {
+      bins[i] = -1;
+      continue;
+    }
+    const double xb = std::nearbyint(scale * std::log(periods[i] / p->coarse_pmin));
+    bins[i] = (xb >= 0.0 && xb <= (double)(p->coarse_bins - 1)) ? (int32_t)xb : -1;
+  }
+  return QLP_OK;
+}
+
+extern "C" int qlp_bls_proposal_windows(const qlp_bls_params* p, int32_t n_stars, const int32_t* bins, int32_t k,
+                                        double half_width, int64_t* win_offsets, double* win_lo, double* win_hi,
+                                        int64_t capacity) {
+  if (!coarse_ok(p) || n_stars < 0 || k < 1 || !(half_width > 0.0) || (n_stars > 0 && !bins) || !win_offsets)
+    return QLP_ERR_ARG;
+  std::vector<int64_t> off;
+  std::vector<double> lo, hi;
+  proposal_windows(*p, n_stars, bins, k, half_width, &off, &lo, &hi);
+  std::copy(off.begin(), off.end(), win_offsets);
+  if (!win_lo && !win_hi) return QLP_OK;
+  if (!win_lo || !win_hi || capacity < (int64_t)lo.size()) return QLP_ERR_ARG;
+  std::copy(lo.begin(), lo.end(), win_lo);
+  std::copy(hi.begin(), hi.end(), win_hi);
+  return QLP_OK;
+}
 
 namespace {
 
@@ -87,11 +151,11 @@ extern "C" int qlp_bls_search_learned(const qlp_bls_params* p, int32_t n_stars, 
                                       const double* rho, const double* rstar, qlp_cnn_t* net, int32_t k,
                                       double half_width, void* stream, qlp_bls_best* best_host,
                                       int32_t* bins_host) {
-  if (!p || !net || !best_host || n_stars < 0 || k < 1 || !(half_width > 0.0)) return QLP_ERR_ARG;
+  if (!p || !best_host || n_stars < 0 || k < 1 || !(half_width > 0.0) || !coarse_ok(p)) return QLP_ERR_ARG;
   if (n_stars == 0) return QLP_OK;
   if (!offsets) return QLP_ERR_ARG;
-  int32_t max_batch = 0, len = 0;
-  int rc = qlp_cnn_shape(net, &max_batch, &len);
+  int32_t max_batch = 0, len = p->coarse_bins;
+  int rc = net ? qlp_cnn_shape(net, &max_batch, &len) : QLP_OK;
   if (rc) return rc;
   if (len != p->coarse_bins || k > len) return QLP_ERR_ARG;
   // Chunks of whole stars with about equal points, in a two-stage pipeline: while
@@ -125,10 +189,8 @@ extern "C" int qlp_bls_search_learned(const qlp_bls_params* p, int32_t n_stars, 
     pc.grid_mode = 1;
     qlp_bls_params pr = *p;
     pr.grid_mode = 0;
-    const double ratio = p->coarse_pmax / p->coarse_pmin;
-    auto period = [&](double x) { return p->coarse_pmin * std::pow(ratio, x / (double)(len - 1)); };
     if (e != cudaSuccess) rc = qlp::record_cuda_error(e, "stream order");
-    if (rc == QLP_OK) rc = buf_c.get(&logits, (size_t)max_batch * len);
+    if (rc == QLP_OK && net) rc = buf_c.get(&logits, (size_t)max_batch * len);
 
     // stage 1 of chunk c: coarse plan (host), spectrum, S/N, network input, proposals
     auto coarse = [&](int c) -> int {
@@ -142,18 +204,25 @@ extern "C" int qlp_bls_search_learned(const qlp_bls_params* p, int32_t n_stars, 
       int64_t nfc = 0;
       if ((r2 = qlp_bls_plan_info(q.cp.p, &nfc, nullptr, nullptr, nullptr, nullptr, nullptr))) return r2;
       if ((r2 = alloc_spectrum(buf_c, nfc, q.ns, &q.c)) || (r2 = buf_c.get(&q.trend, (size_t)q.ns * QLP_TREND_DOUBLES)) ||
-          (r2 = buf_c.get(&q.x0, (size_t)q.ns * len * 2)) || (r2 = buf_c.get(&q.bins, (size_t)q.ns * k)))
+          (r2 = buf_c.get(&q.x0, (size_t)q.ns * len * QLP_CNN_IN_CH)) || (r2 = buf_c.get(&q.bins, (size_t)q.ns * k)))
         return r2;
       if ((r2 = qlp_bls_search(q.cp.p, st_c, q.c.sr, q.c.qidx, q.c.kbin, q.c.s, q.c.r))) return r2;
       if ((r2 = qlp_bls_snr_trend(q.cp.p, st_c, q.c.sr, q.c.qidx, q.c.kbin, q.c.s, q.c.r, nullptr, q.trend, q.c.snr,
                                   q.c.best)))
         return r2;
-      if ((r2 = qlp_bls_coarse_tensor(q.cp.p, st_c, q.c.snr, len, q.x0))) return r2;
-      for (int32_t a = 0; a < q.ns; a += max_batch) {
-        const int32_t nb = q.ns - a < max_batch ? q.ns - a : max_batch;
-        const uint16_t* xb = q.x0 + (size_t)a * len * 2;
-        if ((r2 = qlp_cnn_forward(net, xb, nb, logits, st_c))) return r2;
-        if ((r2 = qlp_cnn_topk(logits, xb, nb, len, k, q.bins + (size_t)a * k, st_c))) return r2;
+      if (net) {
+        if ((r2 = qlp_bls_coarse_tensor(q.cp.p, st_c, q.c.snr, len, q.x0, nullptr))) return r2;
+        for (int32_t a = 0; a < q.ns; a += max_batch) {
+          const int32_t nb = q.ns - a < max_batch ? q.ns - a : max_batch;
+          const uint16_t* xb = q.x0 + (size_t)a * len * QLP_CNN_IN_CH;
+          if ((r2 = qlp_cnn_forward(net, xb, nb, logits, st_c))) return r2;
+          if ((r2 = qlp_cnn_topk(logits, xb, nb, len, k, q.bins + (size_t)a * k, st_c))) return r2;
+        }
+      } else {  // without the network: the top-k coarse bins by S/N
+        float* rows = nullptr;
+        if ((r2 = buf_c.get(&rows, (size_t)q.ns * len))) return r2;
+        if ((r2 = qlp_bls_coarse_tensor(q.cp.p, st_c, q.c.snr, len, q.x0, rows))) return r2;
+        if ((r2 = qlp_cnn_topk(rows, q.x0, q.ns, len, k, q.bins, st_c))) return r2;
       }
       cudaError_t e2 = cudaEventCreateWithFlags(&q.proposed, cudaEventDisableTiming);
       if (e2 == cudaSuccess) e2 = cudaEventRecord(q.proposed, st_c);
@@ -171,18 +240,10 @@ extern "C" int qlp_bls_search_learned(const qlp_bls_params* p, int32_t n_stars, 
       if (e2 != cudaSuccess) return qlp::record_cuda_error(e2, "proposal download");
       if (bins_host)
         for (size_t i = 0; i < hb.size(); ++i) bins_host[(size_t)q.s0 * k + i] = hb[i];
-      // windows in frequency around each proposed bin: P(x) = pmin (pmax/pmin)^(x/(bins-1))
-      std::vector<int64_t> woff((size_t)q.ns + 1, 0);
+      // windows in frequency around each proposed bin
+      std::vector<int64_t> woff;
       std::vector<double> wlo, whi;
-      for (int32_t s = 0; s < q.ns; ++s) {
-        for (int32_t i = 0; i < k; ++i) {
-          const int32_t kb = hb[(size_t)s * k + i];
-          if (kb < 0) continue;
-          wlo.push_back(1.0 / period((double)kb + half_width));
-          whi.push_back(1.0 / period((double)kb - half_width));
-        }
-        woff[(size_t)s + 1] = (int64_t)wlo.size();
-      }
+      proposal_windows(*p, q.ns, hb.data(), k, half_width, &woff, &wlo, &whi);
       const int64_t o0 = offsets[q.s0];
       std::vector<int64_t> off((size_t)q.ns + 1);
       for (int32_t i = 0; i <= q.ns; ++i) off[(size_t)i] = offsets[q.s0 + i] - o0;
@@ -239,7 +300,7 @@ extern "C" int qlp_bls_search_learned(const qlp_bls_params* p, int32_t n_stars, 
     }
     if (rc == QLP_OK) {
       int32_t f3 = 0;
-      const int r3 = qlp_cnn_loss(net, nullptr, &f3, st_c);
+      const int r3 = net ? qlp_cnn_loss(net, nullptr, &f3, st_c) : QLP_OK;
       if (r3 && r3 != QLP_ERR_DEVICE) rc = r3;
       fl |= f3;
       if (rc == QLP_OK && fl) rc = QLP_ERR_DEVICE;

@@ -244,7 +244,7 @@ int launch_bls(const BlsArgs& a, int phase_mode, int sum_mode, int warps, int bl
                size_t smem_bytes, void* stream);
 int launch_snr(const SnrArgs& a, void* stream);
 int launch_coarse_tensor(const StarDev* stars, int n_stars, const float* snr, int n_bins, void* out,
-                         void* stream);
+                         float* snr_rows, int d2, int d3, void* stream);
 int launch_topk(const float* logits, const void* x0, int batch, int len, int k, int32_t* out, void* stream);
 int launch_prep_cells(const PrepCellsArgs& a, void* stream);
 int launch_cells(const CellArgs& a, int sum_mode, int warps, int blocks, size_t smem, void* stream);

@@ -329,33 +329,59 @@ __global__ void __launch_bounds__(kSnrThreads) snr_kernel(const SnrArgs a) {
 // spectrum is bin grid_k0 - i), (0, 0) elsewhere; BF16 [n_stars][n_bins][2]. The
 // monotone asinh compression keeps the ordering of the S/N while bounding the
 // range the network sees (S/N from -5 to 10^4 maps to about -1.1 to 8.5).
-__global__ void coarse_tensor_kernel(const StarDev* stars, const float* snr, int n_bins, __nv_bfloat16* out) {
+// The network input per coarse bin k: a(k) = asinh(S/N / 4) and 1 on searched bins,
+// then a() at the harmonic bins k + d2, k - d2, k + d3, k - d3 (periods 2P, P/2, 3P,
+// P/3), 0 off the grid or on bins not searched; with snr_rows, also the FP32 S/N
+// itself per bin (0 elsewhere) in [star][bin] rows. Pass 1 writes channels 0 and 1;
+// after the block barrier pass 2 copies channel 0 of the harmonic bins (the same
+// BF16 values).
+__global__ void coarse_tensor_kernel(const StarDev* stars, const float* snr, int n_bins, __nv_bfloat16* out,
+                                     float* snr_rows, int d2, int d3) {
+  constexpr int C = QLP_CNN_IN_CH;
   const int s = blockIdx.x;
   const StarDev st = stars[s];
-  __nv_bfloat16* row = out + (size_t)s * n_bins * 2;
+  __nv_bfloat16* row = out + (size_t)s * n_bins * C;
+  float* srow = snr_rows ? snr_rows + (size_t)s * n_bins : nullptr;
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
   for (int k = threadIdx.x; k < n_bins; k += blockDim.x) {
-    row[2 * k] = __float2bfloat16_rn(0.f);
-    row[2 * k + 1] = __float2bfloat16_rn(0.f);
+    row[C * k] = zero;
+    row[C * k + 1] = zero;
+    if (srow) srow[k] = 0.f;
   }
   __syncthreads();
-  if (st.status != 0) return;
-  for (int i = threadIdx.x; i < st.n_f; i += blockDim.x) {
-    const int k = st.grid_k0 - i;
-    if (k < 0 || k >= n_bins) continue;
-    row[2 * k] = __float2bfloat16_rn(asinhf(0.25f * snr[st.f_off + i]));
-    row[2 * k + 1] = __float2bfloat16_rn(1.f);
+  if (st.status == 0) {
+    for (int i = threadIdx.x; i < st.n_f; i += blockDim.x) {
+      const int k = st.grid_k0 - i;
+      if (k < 0 || k >= n_bins) continue;
+      const float v = snr[st.f_off + i];
+      row[C * k] = __float2bfloat16_rn(asinhf(0.25f * v));
+      row[C * k + 1] = __float2bfloat16_rn(1.f);
+      if (srow) srow[k] = v;
+    }
+  }
+  __syncthreads();
+  const int dk[4] = {d2, -d2, d3, -d3};
+  for (int k = threadIdx.x; k < n_bins; k += blockDim.x) {
+    const bool here = __bfloat162float(row[C * k + 1]) > 0.f;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int kh = k + dk[h];
+      row[C * k + 2 + h] = (here && kh >= 0 && kh < n_bins) ? row[C * kh] : zero;
+    }
   }
 }
 
 int launch_coarse_tensor(const StarDev* stars, int n_stars, const float* snr, int n_bins, void* out,
-                         void* stream) {
+                         float* snr_rows, int d2, int d3, void* stream) {
   if (n_stars <= 0) return 0;
   coarse_tensor_kernel<<<n_stars, 256, 0, (cudaStream_t)stream>>>(stars, snr, n_bins,
-                                                                   static_cast<__nv_bfloat16*>(out));
+                                                                   static_cast<__nv_bfloat16*>(out), snr_rows,
+                                                                   d2, d3);
   return (int)cudaGetLastError();
 }
 
-// The k largest logits of each row among valid bins (x0 channel 1 > 0), largest
+// The k largest logits of each row among valid bins (x0 channel 1 > 0, rows of
+// QLP_CNN_IN_CH channels), largest
 // first, ties to the lower bin; -1 when fewer than k bins are valid.
 __global__ void __launch_bounds__(256) topk_kernel(const float* logits, const __nv_bfloat16* x0, int len,
                                                    int k, int32_t* out) {
@@ -364,8 +390,9 @@ __global__ void __launch_bounds__(256) topk_kernel(const float* logits, const __
   __shared__ int bi[8];
   const int s = blockIdx.x;
   const float* z = logits + (size_t)s * len;
-  const __nv_bfloat16* m = x0 + (size_t)s * len * 2;
-  for (int i = threadIdx.x; i < len; i += blockDim.x) taken[i] = __bfloat162float(m[2 * i + 1]) > 0.f ? 0 : 1;
+  const __nv_bfloat16* m = x0 + (size_t)s * len * QLP_CNN_IN_CH;
+  for (int i = threadIdx.x; i < len; i += blockDim.x)
+    taken[i] = __bfloat162float(m[QLP_CNN_IN_CH * i + 1]) > 0.f ? 0 : 1;
   __syncthreads();
   for (int r = 0; r < k; ++r) {
     float v = -3.0e38f;

@@ -5,14 +5,13 @@ frequencies inside those windows are searched at full resolution, scored
 against the coarse spectrum's trend and sigma_SR.
 
 Every numeric step runs in the CUDA library (coarse plan, search, S/N, input
-tensor, CNN, top-K, windowed plan, search, S/N); this module only sequences the
-calls and turns bin indices into frequency windows; the same sequence runs
-inside the library behind qlp_bls_search_learned.
+tensor, CNN, top-K, windowed plan, search, S/N) and the coarse-grid arithmetic
+(bin periods, nearest bins, windows) in its host code; this module only
+sequences the calls, as the library does behind qlp_bls_search_learned.
 """
 from __future__ import annotations
 
 import dataclasses
-import math
 
 import numpy as np
 
@@ -26,20 +25,20 @@ def coarse_params(base: qlpbls.Params | None = None) -> qlpbls.Params:
 
 
 def bin_period(k, p: qlpbls.Params):
-    """Period (days) of coarse bin k."""
-    return p.coarse_pmin * (p.coarse_pmax / p.coarse_pmin) ** (np.asarray(k, np.float64) / (p.coarse_bins - 1))
+    """Period (days) of coarse bin k (qlp_bls_coarse_periods)."""
+    k = np.asarray(k, np.float64)
+    return qlpbls.coarse_periods(k.reshape(-1), p).reshape(k.shape)
 
 
 def period_bin(period, p: qlpbls.Params):
-    """Nearest coarse bin of a period."""
-    x = (p.coarse_bins - 1) * np.log(np.asarray(period, np.float64) / p.coarse_pmin) / \
-        math.log(p.coarse_pmax / p.coarse_pmin)
-    return np.rint(x).astype(np.int64)
+    """Nearest coarse bin of a period (qlp_bls_coarse_bins; -1 off the grid)."""
+    per = np.asarray(period, np.float64)
+    return qlpbls.coarse_bins(per.reshape(-1), p).reshape(per.shape).astype(np.int64)
 
 
 class CoarseStage:
     """Coarse plan, search and S/N of a batch, its trend records and the
-    network input tensor [n_stars, bins, 2]."""
+    network input tensor [n_stars, bins, CNN_IN_CH]."""
 
     def __init__(self, batch, base: qlpbls.Params | None = None, stream=None):
         self.params = coarse_params(base)
@@ -56,23 +55,16 @@ def labels(batch, p: qlpbls.Params, device, half_width: int = 1):
     import torch
     lab = torch.zeros(batch.n_stars, p.coarse_bins, dtype=torch.float32)
     k = period_bin(np.where(batch.inj, batch.period, 1.0), p)
-    for s in np.nonzero(batch.inj)[0]:
+    for s in np.nonzero(batch.inj & (k >= 0))[0]:
         a, b = max(0, int(k[s]) - half_width), min(p.coarse_bins, int(k[s]) + half_width + 1)
         lab[s, a:b] = 1.0
     return lab.to(device)
 
 
 def windows_from_bins(bins, p: qlpbls.Params, half_width: float = 1.0):
-    """Frequency windows [1/P(k + w), 1/P(k - w)] for every valid proposed bin k."""
-    bins = np.asarray(bins)
-    offs = [0]
-    lo, hi = [], []
-    for row in bins:
-        ks = row[row >= 0]
-        lo.extend((1.0 / bin_period(ks + half_width, p)).tolist())
-        hi.extend((1.0 / bin_period(ks - half_width, p)).tolist())
-        offs.append(len(lo))
-    return np.asarray(offs, np.int64), np.asarray(lo, np.float64), np.asarray(hi, np.float64)
+    """Frequency windows [1/P(k + w), 1/P(k - w)] for every valid proposed bin k
+    (qlp_bls_proposal_windows, the windows the one-call path uses)."""
+    return qlpbls.proposal_windows(bins, p, half_width)
 
 
 def refine(batch, windows, trend, base: qlpbls.Params | None = None, stream=None):
@@ -98,10 +90,10 @@ def propose(net, x0, k: int, stream=None):
 
 
 def propose_without_network(coarse: CoarseStage, k: int, stream=None):
-    """Ablation: the top-k coarse bins by coarse S/N itself (no network)."""
-    x0 = coarse.x0
-    snr = x0[..., 0].float().contiguous()
-    return qlpbls.topk(snr, x0, k, stream=stream)
+    """Ablation: the top-k coarse bins by the coarse S/N itself (FP32; no network),
+    as qlp_bls_search_learned ranks them without a network."""
+    _, rows = coarse.plan.coarse_tensor(coarse.out, stream=stream, snr_rows=True)
+    return qlpbls.topk(rows.contiguous(), coarse.x0, k, stream=stream)
 
 
 def search_learned(batch, net, k: int = 32, base: qlpbls.Params | None = None, stream=None,

@@ -22,6 +22,7 @@ MAD_RAW, MAD_RESID = 0, 1
 METHOD_AUTO, METHOD_POINTS, METHOD_CELLS = 0, 1, 2
 TREND_DOUBLES = 84
 CNN_ACT, CNN_GACT, CNN_LOGIT, CNN_DLOGIT = 0, 1, 2, 3
+CNN_IN_CH = 6  # network input channels: S/N, mask, S/N at the bins of 2P, P/2, 3P, P/3
 
 STAR_UNSORTED, STAR_TOO_FEW, STAR_EMPTY_GRID, STAR_NBINS_CAP, STAR_ZERO_MAD = 1, 2, 4, 8, 16
 
@@ -192,7 +193,13 @@ def lib():
             L.qlp_bls_plan_windows.restype = ctypes.c_int
             L.qlp_bls_snr_trend.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
             L.qlp_bls_snr_trend.restype = ctypes.c_int
-            L.qlp_bls_coarse_tensor.argtypes = [_vp, _vp, _vp, _i32, _vp]
+            L.qlp_bls_coarse_tensor.argtypes = [_vp, _vp, _vp, _i32, _vp, _vp]
+            L.qlp_bls_coarse_periods.argtypes = [_P(CParams), _i32, _vp, _vp]
+            L.qlp_bls_coarse_periods.restype = ctypes.c_int
+            L.qlp_bls_coarse_bins.argtypes = [_P(CParams), _i32, _vp, _vp]
+            L.qlp_bls_coarse_bins.restype = ctypes.c_int
+            L.qlp_bls_proposal_windows.argtypes = [_P(CParams), _i32, _vp, _i32, _d, _vp, _vp, _vp, _i64]
+            L.qlp_bls_proposal_windows.restype = ctypes.c_int
             L.qlp_bls_coarse_tensor.restype = ctypes.c_int
             L.qlp_cnn_topk.argtypes = [_vp, _vp, _i32, _i32, _i32, _vp, _vp]
             L.qlp_cnn_topk.restype = ctypes.c_int
@@ -359,14 +366,18 @@ class Plan:
         import torch
         return torch.zeros(max(self.n_stars, 1) * TREND_DOUBLES, dtype=torch.float64, device=self.device)
 
-    def coarse_tensor(self, out, stream=None):
-        """qlp_bls_coarse_tensor: BF16 [n_stars, coarse_bins, 2] network input."""
+    def coarse_tensor(self, out, stream=None, snr_rows: bool = False):
+        """qlp_bls_coarse_tensor: BF16 [n_stars, coarse_bins, CNN_IN_CH] network input; with
+        snr_rows also the FP32 S/N per coarse bin [n_stars, coarse_bins]."""
         import torch
         nb = self.params.coarse_bins
-        x0 = torch.empty(max(self.n_stars, 1), nb, 2, dtype=torch.bfloat16, device=self.device)
+        x0 = torch.empty(max(self.n_stars, 1), nb, CNN_IN_CH, dtype=torch.bfloat16, device=self.device)
+        rows = torch.empty(max(self.n_stars, 1), nb, dtype=torch.float32, device=self.device) if snr_rows else None
         rc = lib().qlp_bls_coarse_tensor(self._h, _stream_ptr(stream), out["snr"].data_ptr(), nb,
-                                         x0.data_ptr())
+                                         x0.data_ptr(), rows.data_ptr() if rows is not None else None)
         _check(rc, "qlp_bls_coarse_tensor")
+        if snr_rows:
+            return x0[: self.n_stars], rows[: self.n_stars]
         return x0[: self.n_stars]
 
     def device_status(self, stream=None) -> int:
@@ -562,7 +573,7 @@ def search_static(tp, y, dy, baseline, freqs, qmins, out, params: Params | None 
 
 
 class CNN:
-    """The proposal network (qlp_cnn_*): BF16 inputs [B][L][2] and FP32 labels
+    """The proposal network (qlp_cnn_*): BF16 inputs [B][L][CNN_IN_CH] and FP32 labels
     [B][L] as device tensors; parameters as a host float32 array."""
 
     def __init__(self, max_batch: int, length: int = 4096, seed: int = 0):
@@ -696,10 +707,48 @@ def topk(logits, x0, k: int, stream=None):
     return out
 
 
-def search_learned(offsets, t, y, dy, rho, rstar, net: CNN, k: int = 32, half_width: float = 1.0,
+def coarse_periods(x, params: Params | None = None) -> np.ndarray:
+    """qlp_bls_coarse_periods: the period of (fractional) coarse bin positions x."""
+    x = np.ascontiguousarray(np.atleast_1d(x), np.float64)
+    out = np.zeros(x.shape[0], np.float64)
+    cp = (params or Params()).to_c()
+    _check(lib().qlp_bls_coarse_periods(ctypes.byref(cp), int(x.shape[0]), _np_ptr(x), _np_ptr(out)),
+           "qlp_bls_coarse_periods")
+    return out
+
+
+def coarse_bins(periods, params: Params | None = None) -> np.ndarray:
+    """qlp_bls_coarse_bins: the nearest coarse bin of each period (-1 outside the grid)."""
+    per = np.ascontiguousarray(np.atleast_1d(periods), np.float64)
+    out = np.zeros(per.shape[0], np.int32)
+    cp = (params or Params()).to_c()
+    _check(lib().qlp_bls_coarse_bins(ctypes.byref(cp), int(per.shape[0]), _np_ptr(per), _np_ptr(out)),
+           "qlp_bls_coarse_bins")
+    return out
+
+
+def proposal_windows(bins, params: Params | None = None, half_width: float = 1.0):
+    """qlp_bls_proposal_windows: (win_offsets, f_lo, f_hi) around each star's valid
+    proposed coarse bins (int [n_stars, k])."""
+    b = np.ascontiguousarray(np.atleast_2d(bins), np.int32)
+    n, k = int(b.shape[0]), int(b.shape[1])
+    cp = (params or Params()).to_c()
+    off = np.zeros(n + 1, np.int64)
+    L = lib()
+    _check(L.qlp_bls_proposal_windows(ctypes.byref(cp), n, _np_ptr(b), k, float(half_width), _np_ptr(off),
+                                      None, None, 0), "qlp_bls_proposal_windows")
+    lo = np.zeros(max(int(off[-1]), 1), np.float64)
+    hi = np.zeros_like(lo)
+    _check(L.qlp_bls_proposal_windows(ctypes.byref(cp), n, _np_ptr(b), k, float(half_width), _np_ptr(off),
+                                      _np_ptr(lo), _np_ptr(hi), lo.shape[0]), "qlp_bls_proposal_windows")
+    return off, lo[: off[-1]], hi[: off[-1]]
+
+
+def search_learned(offsets, t, y, dy, rho, rstar, net: CNN | None, k: int = 32, half_width: float = 1.0,
                    params: Params | None = None, stream=None):
     """qlp_bls_search_learned: host light curves in, the learned path's best
-    candidate per star and the proposed coarse bins [n_stars, k] out."""
+    candidate per star and the proposed coarse bins [n_stars, k] out. net=None
+    ranks the coarse bins by S/N instead (the path without the network)."""
     L = lib()
     offsets, t, y, dy, rho, rstar = _host_inputs(offsets, t, y, dy, rho, rstar)
     n_stars = int(offsets.shape[0] - 1)
@@ -707,7 +756,8 @@ def search_learned(offsets, t, y, dy, rho, rstar, net: CNN, k: int = 32, half_wi
     best = np.zeros(max(n_stars, 1), BEST_DTYPE)
     bins = np.zeros((max(n_stars, 1), int(k)), np.int32)
     rc = L.qlp_bls_search_learned(ctypes.byref(cp), n_stars, _np_ptr(offsets), _np_ptr(t), _np_ptr(y),
-                                  _np_ptr(dy), _np_ptr(rho), _np_ptr(rstar), net._h, int(k),
+                                  _np_ptr(dy), _np_ptr(rho), _np_ptr(rstar),
+                                  net._h if net is not None else None, int(k),
                                   float(half_width), _stream_ptr(stream), _np_ptr(best), _np_ptr(bins))
     _check(rc, "qlp_bls_search_learned")
     return best[:n_stars], bins[:n_stars]

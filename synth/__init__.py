@@ -109,6 +109,31 @@ def _assemble(name, ts, ys, dys, rho, rstar, inj, per, t0, dep, dur) -> Batch:
                  np.asarray(dep, np.float64), np.asarray(dur, np.float64), name)
 
 
+def concat(batches, name: str = "") -> Batch:
+    """One batch of the stars of several, in order (for batches generated in
+    independently seeded chunks)."""
+    offs = [np.zeros(1, np.int64)]
+    base = 0
+    for b in batches:
+        offs.append(b.offsets[1:] + base)
+        base += int(b.offsets[-1])
+    cat = lambda f: np.concatenate([getattr(b, f) for b in batches])
+    return Batch(np.concatenate(offs), cat("t"), cat("y"), cat("dy"), cat("rho"), cat("rstar"), cat("inj"),
+                 cat("period"), cat("t0"), cat("depth"), cat("duration"),
+                 name or (batches[0].name if batches else ""))
+
+
+def in_chunks(make, n_stars: int, chunk: int, seed: int, workers: int = 8) -> Batch:
+    """make(n, seed) for ceil(n_stars / chunk) chunks with seeds seed, seed + 1, ...,
+    run on a thread pool (NumPy releases the interpreter lock in its array work),
+    joined in chunk order: the same batch for any number of workers."""
+    from concurrent.futures import ThreadPoolExecutor
+    sizes = [min(chunk, n_stars - a) for a in range(0, n_stars, chunk)]
+    with ThreadPoolExecutor(max_workers=max(1, workers)) as ex:
+        parts = list(ex.map(lambda c: make(sizes[c], seed + c), range(len(sizes))))
+    return concat(parts)
+
+
 def single_star(seed: int = 1) -> Batch:
     """One 27.4-d sector at 30-min cadence, 1-d gap at mid-sector, white noise 1e-3,
     box transit P = 3.7 d, depth 2e-3, circular duration for rho = 1.41, R* = 1."""
@@ -220,13 +245,15 @@ def sector_counts_geometric(n_stars: int, seed: int, mean: float = 3.0, cap: int
 
 
 def sector_scale(n_stars: int = 1024, seed: int = 6, frac_injected: float = 0.01,
-                 mean_sectors: float = 3.0, cap: int = 40) -> Batch:
+                 mean_sectors: float = 3.0, cap: int = 40, sectors: int | None = None) -> Batch:
     """Sector-scale mix: per star a geometric number of contiguous 27.4-d sectors
-    (mean 3, at most 40) at 200-s cadence with 1-d gaps, rho log-U(0.1, 10), R*
-    log-U(0.5, 3), white sigma log-U(2e-4, 1e-2) as in the uneven single-sector
-    batch, and 1 % injected boxes (P log-U(0.5, 13) d, depth log-U(3e-4, 1e-2),
-    circular-orbit duration)."""
+    (mean 3, at most 40; every star `sectors` of them when given) at 200-s cadence
+    with 1-d gaps, rho log-U(0.1, 10), R* log-U(0.5, 3), white sigma log-U(2e-4,
+    1e-2) as in the uneven single-sector batch, and 1 % injected boxes (P log-U(0.5,
+    13) d, depth log-U(3e-4, 1e-2), circular-orbit duration)."""
     nsec = sector_counts_geometric(n_stars, seed, mean_sectors, cap)
+    if sectors is not None:
+        nsec = np.full(n_stars, int(sectors))
     rng = np.random.default_rng(seed + 1)
     rho = _loguniform(rng, 0.1, 10.0, n_stars)
     rstar = _loguniform(rng, 0.5, 3.0, n_stars)

@@ -223,3 +223,28 @@ def test_work_loop_bound_is_validated():
     assert foff[-1] > 0
     with pytest.raises(qlpbls.QlpError):
         qlpbls.batch_grid(b.offsets, b.t, b.y, b.dy, b.rho, qlpbls.Params(work_loop_bound=-1))
+
+
+def test_coarse_periods_and_bins_match_oracle_grid():
+    # the library's coarse-bin periods are the oracle's log-period grid bit for bit,
+    # and every grid period maps back to its own bin
+    from oracle import plan as op
+    p = op.Params(grid_mode=1)
+    ratio = p.coarse_pmax / p.coarse_pmin
+    ks = np.arange(p.coarse_bins)
+    ref = np.array([p.coarse_pmin * (ratio ** (k / (p.coarse_bins - 1))) for k in ks])
+    qp = qlpbls.Params(grid_mode=1)
+    assert np.array_equal(qlpbls.coarse_periods(ks.astype(np.float64), qp), ref)
+    assert np.array_equal(qlpbls.coarse_bins(ref, qp), ks.astype(np.int32))
+    assert list(qlpbls.coarse_bins(np.array([0.05, -1.0, 500.0]), qp)) == [-1, -1, -1]
+
+
+def test_proposal_windows_bracket_their_bins():
+    qp = qlpbls.Params(grid_mode=1)
+    bins = np.array([[10, 4095, -1], [-1, -1, -1], [2000, 2001, 0]], np.int32)
+    off, lo, hi = qlpbls.proposal_windows(bins, qp, 1.0)
+    assert list(off) == [0, 2, 2, 5]
+    kk = np.array([10, 4095, 2000, 2001, 0], np.float64)
+    np.testing.assert_array_equal(lo, 1.0 / qlpbls.coarse_periods(kk + 1.0, qp))
+    np.testing.assert_array_equal(hi, 1.0 / qlpbls.coarse_periods(kk - 1.0, qp))
+    assert np.all(lo < hi)

@@ -157,7 +157,8 @@ def _net_case(gpu_lib, B=2, L=256, seed=4, pos_weight=30.0):
     rng = np.random.default_rng(seed)
     snr = rng.normal(size=(B, L)).astype(np.float32) * 2.0
     mask = (rng.uniform(size=(B, L)) > 0.1).astype(np.float32)
-    x0 = torch.tensor(np.stack([snr * mask, mask], axis=-1)).to(torch.bfloat16)
+    harm = [np.roll(snr * mask, d, axis=1) * mask for d in (37, -37, 59, -59)]  # stand-ins for 2P .. P/3
+    x0 = torch.tensor(np.stack([snr * mask, mask] + harm, axis=-1)).to(torch.bfloat16)
     labels = np.zeros((B, L), np.float32)
     labels[0, 40:43] = 1.0
     labels[1 % B, 200:203] = 1.0
@@ -289,7 +290,8 @@ def test_training_reduces_loss(gpu_lib):
         k = int(rng.integers(20, L - 20))
         snr[b, k - 1:k + 2] += 8.0
         labels[b, k - 1:k + 2] = 1.0
-    x0 = torch.tensor(np.stack([snr, np.ones_like(snr)], -1)).to(torch.bfloat16).cuda()
+    zero = np.zeros_like(snr)
+    x0 = torch.tensor(np.stack([snr, np.ones_like(snr), zero, zero, zero, zero], -1)).to(torch.bfloat16).cuda()
     lab = torch.tensor(labels).cuda()
     net = gpu_lib.CNN(max_batch=B, length=L, seed=2)
     net.backward(x0, lab, 20.0)

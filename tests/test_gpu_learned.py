@@ -45,12 +45,25 @@ def test_coarse_stage_matches_oracle(gpu_lib):
         np.testing.assert_allclose(trend[s, 4:4 + nx], xs, rtol=1e-13)
         np.testing.assert_allclose(trend[s, 44:44 + nx], ys, rtol=1e-5)
         assert trend[s, 1] == pytest.approx(sigma, rel=1e-5)
-        # network input: (asinh(S/N / 4), 1) on bins k0 - i, zeros elsewhere
+        # network input: (asinh(S/N / 4), 1) on bins k0 - i, zeros elsewhere; channels
+        # 2-5 the first channel at the bins of 2P, P/2, 3P, P/3 (log-period offsets)
         ks = pl.grid_k0 - np.arange(pl.freqs.shape[0])
         assert np.all(x0[s, ks, 1] == 1.0)
         assert np.sum(x0[s, :, 1]) == pl.freqs.shape[0]
         bf = torch.asinh(torch.tensor(g["snr"][sl]) * 0.25).to(torch.bfloat16).float().numpy()
         np.testing.assert_allclose(x0[s, ks, 0], bf, rtol=1e-2, atol=1e-2)
+        L = x0.shape[1]
+        a = np.zeros(L)
+        a[ks] = np.arcsinh(snr_o * 0.25)
+        on = x0[s, :, 1] > 0
+        for c, h in ((2, 2.0), (3, 0.5), (4, 3.0), (5, 1.0 / 3.0)):
+            d = int(round((L - 1) * np.log(h) / np.log(p.coarse_pmax / p.coarse_pmin)))
+            src = np.arange(L) + d
+            ok = on & (src >= 0) & (src < L)
+            want = np.where(ok, a[np.clip(src, 0, L - 1)], 0.0)
+            np.testing.assert_allclose(x0[s, :, c], want, rtol=1e-2, atol=1e-2)
+            # bit-identical copies of channel 0 where the harmonic bin exists
+            assert np.array_equal(x0[s, ok, c], x0[s, src[ok], 0])
 
 
 def test_topk_matches_torch(gpu_lib):
@@ -60,7 +73,8 @@ def test_topk_matches_torch(gpu_lib):
     logits = torch.randn(B, L, generator=g).cuda()
     mask = (torch.rand(B, L, generator=g) > 0.3).float()
     mask[4, 40:] = 0.0                      # fewer valid bins than K in the last row
-    x0 = torch.stack([torch.zeros(B, L), mask], -1).to(torch.bfloat16).cuda()
+    z = torch.zeros(B, L)
+    x0 = torch.stack([z, mask, z, z, z, z], -1).to(torch.bfloat16).cuda()
     idx = qlpbls.topk(logits, x0, K).cpu().numpy()
     masked = torch.where(mask.cuda() > 0, logits, torch.full_like(logits, -float("inf")))
     ref = torch.topk(masked, K, dim=1).indices.cpu().numpy()
@@ -109,35 +123,48 @@ def test_windowed_refine_matches_oracle(gpu_lib):
 
 
 def test_learned_path_recall(gpu_lib):
-    """Train the network briefly on seeded coarse spectra, then compare the
-    learned path (top-32 windows) with the full-grid search on held-out stars:
-    the learned path must recover at least 97 % of the injections the full grid
-    recovers (S/N > 9, period within 1 %)."""
+    """Train the network on 8,192 seeded coarse spectra, then compare, on 1,024
+    held-out stars, the learned path and the same path without the network
+    (proposals ranked by the coarse S/N itself) with the full-grid search: recall
+    among the injections the full grid recovers (S/N > 9, period within 1 %) for K
+    = 1 .. 32 proposals per star (written to the parity report); at K = 32 both
+    reach 99 %. The library's one-call path, with and without the network, equals
+    the same stages sequenced from Python."""
     import torch
+    from parity import REPORT
     batches = []
-    for c in range(2):
-        tb = synth.proposal_set(1024, seed=500 + c)
+    for c in range(4):
+        tb = synth.proposal_set(2048, seed=500 + c)
         cs = learned.CoarseStage(tb)
         batches.append((cs.x0.clone(), learned.labels(tb, cs.params, "cuda")))
-    net = qlpbls.CNN(max_batch=64, length=4096, seed=0)
-    losses = learned.train(net, batches, epochs=2, lr=2e-3)
-    assert losses[-1] < 0.2
-    test = synth.proposal_set(256, seed=777)
+        del cs
+    net = qlpbls.CNN(max_batch=128, length=4096, seed=0)
+    losses = learned.train(net, batches, epochs=3, lr=3e-4, pos_weight=16.0)
+    assert losses[-1] < 0.1
+    test = synth.proposal_set(1024, seed=777)
     plan = qlpbls.Plan(test.offsets, test.t, test.y, test.dy, test.rho, test.rstar)
     out = plan.search()
     plan.snr(out)
     rf = learned.recovered(plan.best_host(out), test)
-    best_l, bins = learned.search_learned(test, net, k=32)
-    rl = learned.recovered(best_l, test)
-    assert rf.sum() >= 40
-    assert (rl & rf).sum() >= 0.97 * rf.sum()
-    # the library's one-call path equals the same stages sequenced from Python
+    assert rf.sum() >= 200
     cs = learned.CoarseStage(test)
-    bins_py = learned.propose(net, cs.x0, 32).cpu().numpy()
-    assert np.array_equal(bins, bins_py)
-    best_py = learned.search_with_bins(test, cs, bins_py)
-    assert np.array_equal(best_py["f_idx"], best_l["f_idx"])
-    np.testing.assert_array_equal(best_py["snr"], best_l["snr"])
+    bins_n = learned.propose(net, cs.x0, 32).cpu().numpy()
+    bins_a = learned.propose_without_network(cs, 32).cpu().numpy()
+    curve = {"network": {}, "coarse_snr": {}}
+    for k in (1, 2, 4, 8, 16, 32):
+        for name, bins in (("network", bins_n), ("coarse_snr", bins_a)):
+            r = learned.recovered(learned.search_with_bins(test, cs, bins[:, :k]), test)
+            curve[name][k] = float((r & rf).sum() / rf.sum())
+    REPORT["learned: recall of the full grid's recoveries at K proposals"] = dict(
+        curve, full_recovered=int(rf.sum()), stars=test.n_stars)
+    assert curve["network"][32] >= 0.99 and curve["coarse_snr"][32] >= 0.99, curve
+    # the library's one-call path equals the same stages sequenced from Python
+    for use_net, bins_py in ((True, bins_n), (False, bins_a)):
+        best_l, bins = learned.search_learned(test, net if use_net else None, k=32)
+        assert np.array_equal(bins, bins_py)
+        best_py = learned.search_with_bins(test, cs, bins_py)
+        assert np.array_equal(best_py["f_idx"], best_l["f_idx"])
+        np.testing.assert_array_equal(best_py["snr"], best_l["snr"])
     net.close()
 
 

@@ -10,8 +10,9 @@ Three workloads:
   * 2 stars of 40 contiguous sectors at rho = 10 g/cm^3 (Pmin 0.123 d, baseline
     1,135 d, t'f up to 9.2e3 cycles), every mode, on 40 narrow frequency windows
     spread over the upper frequency range up to 1/Pmin (the windows' grids; their
-    bin counts stay within the exact path's 4,096, while the star's full grid needs
-    more than the 8,192-bin cap near Pmax);
+    bin counts stay below 3,000, while the star's full grid needs
+    more than the 8,192-bin cap near Pmax, and the point path's histograms hold
+    about 3,500 in compensated mode);
   * 1,024 stars of 1-13 sectors on the default path over the full grid, sampled at
     8 evenly spaced frequencies per star plus its SR maximum, and a 64-star subset
     through the point path in double-float and FP32 phase.
@@ -106,12 +107,12 @@ def test_multi_sector_precision(gpu_lib):
 
 def _upper_windows(t, rho, n_win=40, half=2e-5):
     """n_win narrow windows, log-spaced in frequency from where the bin count drops to
-    4,096 up to 1/Pmin (the last window ends there)."""
+    3,000 (within every mode's histograms) up to 1/Pmin (the last window ends there)."""
     p = op.Params()
     rho_kg = rho * 1000.0
     fmax = 1.0 / op.pmin_days(rho_kg, p)
     f_lo = fmax
-    while op.nbins_of(op.q_min(f_lo * 0.98, rho_kg, p), p) <= 4000:
+    while op.nbins_of(op.q_min(f_lo * 0.98, rho_kg, p), p) <= 3000:
         f_lo *= 0.98
     centres = np.geomspace(f_lo, fmax, n_win)
     lo = centres * (1 - half)

@@ -8,7 +8,9 @@ from oracle import cnn as oc
 
 def _data(B, L, seed):
     rng = np.random.default_rng(seed)
-    x0 = np.stack([rng.normal(size=(B, L)), (rng.uniform(size=(B, L)) > 0.2)], axis=-1).astype(np.float64)
+    snr = rng.normal(size=(B, L))
+    harm = [rng.normal(size=(B, L)) for _ in range(oc.IN_CH - 2)]
+    x0 = np.stack([snr, (rng.uniform(size=(B, L)) > 0.2)] + harm, axis=-1).astype(np.float64)
     labels = np.zeros((B, L))
     labels[:, L // 3] = 1.0
     return x0, labels
