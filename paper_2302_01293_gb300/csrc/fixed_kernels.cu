@@ -293,11 +293,12 @@ uint32_t fixed_prep_smem_bytes(int n_pts) { return prep_fixed_smem(n_pts); }
 
 // Box sweep of one start bin k over the running sums of its next bins (rb[o] = H[k + o]):
 // every width w = o + 1 present is scored s^2 / (r (1 - r)) for 0 < r < 1 and compared
-// division-free with the lane's best (s, r) so far; ties go to the narrower box, then
-// the lower k (key = o << 16 | k). ALL: widths 3..11 (the paper's grid; no mask test).
+// division-free with the lane's best (bs2 = s^2, bd = r (1 - r)) so far; ties go to the
+// narrower box, then the lower k (key = o << 16 | k). ALL: widths 3..11 (the paper's
+// grid; no mask test). The chosen box's s and r come from its exact sums afterwards.
 template <bool ALL>
 __device__ __forceinline__ void sweep_start(const float2* rb, bool kin, int k, int mmax, uint32_t wmask,
-                                            float& bsv, float& brv, int& bkey) {
+                                            float& bs2, float& bd, int& bkey) {
   float rw = kin ? 0.f : 2.f, ry = 0.f;  // a start past the last bin never scores (r >= 1)
 #pragma unroll
   for (int o = 0; o < (ALL ? 11 : 15); ++o) {
@@ -308,15 +309,13 @@ __device__ __forceinline__ void sweep_start(const float2* rb, bool kin, int k, i
       if (ALL ? o >= 2 : ((wmask >> o) & 1u) != 0u) {
         const float dd = __fmaf_rn(-rw, rw, rw);  // r (1 - r)
         const float s2 = __fmul_rn(ry, ry);
-        const float bd = __fmaf_rn(-brv, brv, brv);
-        const float bs2 = __fmul_rn(bsv, bsv);
         const float lhs = __fmul_rn(s2, bd), rhs = __fmul_rn(bs2, dd);
         const int key = (o << 16) | k;
         // 0 < r < 1 exactly when r - r^2 > 0: r is a sum of non-negative weights, and
         // fma(-r, r, r) is r (1 - r) rounded once, positive for every float in (0, 1)
         const bool better = dd > 0.f && (lhs > rhs || (lhs == rhs && key < bkey));
-        bsv = better ? ry : bsv;
-        brv = better ? rw : brv;
+        bs2 = better ? s2 : bs2;
+        bd = better ? dd : bd;
         bkey = better ? key : bkey;
       }
     }
@@ -346,7 +345,6 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
   const int nb = R.nb;
   const double f = a.fq[fidx].x;  // for the exact decision near ties
   const uint32_t wmask = R.wmask;
-  const unsigned long long jlow = R.jlow;
   const int mmax = 32 - __clz(wmask);
   const bool all_widths = wmask == 0x7fcu;  // exactly 3 .. 11 bins
   const int gq = (int)(R.gq_bstar >> 13), bstar = (int)(R.gq_bstar & 8191u);
@@ -363,7 +361,7 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
 
   long long h0w = 0, h0y = 0;  // U of bins 0..31 (the wrap-around values)
   long long pw = 0, py = 0;    // U of the previous block
-  float bsv = 0.f, brv = 0.f;  // best box of this lane: s, r and its key
+  float bs2 = 0.f, bd = 1.f;   // best box of this lane: s^2, r (1 - r) and its key
   int bkey = 0x7fffffff;
   // block i: U of bins 32 i + lane; then the histogram of block i - 1 and the
   // sweep of block i - 2 (boxes of up to 15 bins starting in it)
@@ -397,19 +395,26 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
         const int G0 = idle ? (i << 5) : (xb == 0 ? nb : xb + ph * nb);
         const int gstep = P * nb;
         long long aw = 0, ay = 0;
-        bool near = false;  // an edge within the guard band of its cell's point
+        // the smallest (dq - fr + band) mod 2^32 over the lane's edges: some edge lies
+        // within the guard band of its cell's point exactly when it is <= 2 band
+        uint32_t nmin = 0xffffffffu;
         // every lane takes cnt edges; only in the last one may a lane be past g_end
         const int cnt0 = gq + ((i << 5) > bstar ? 0 : 1);
         const int cnt = split ? (cnt0 + P - 1) / P : cnt0;  // no division in full blocks
-        auto edge = [&](int G, bool valid, bool clamp) {
-          // tau_G / h in 32.32 fixed point: cell u and position fr (2^-32 of a cell)
-          const unsigned long long X =
-              (unsigned long long)(uint32_t)G * k_lo + ((unsigned long long)((uint32_t)G * k_hi) << 32);
+        // tau_G / h in 32.32 fixed point, X = G K (below 2^54: the cell index u < 2^22),
+        // stepped by gstep K from edge to edge (the same bits as the product)
+        auto xpos = [&](int G) {
+          return (unsigned long long)(uint32_t)G * k_lo + ((unsigned long long)((uint32_t)G * k_hi) << 32);
+        };
+        const unsigned long long XS = xpos(gstep);
+        unsigned long long X = xpos(G0);
+        auto edge = [&](unsigned long long X, bool valid, bool clamp) {
+          // cell u and position fr (2^-32 of a cell)
           int u = (int)(uint32_t)(X >> 32);
           if (clamp) u = min(u, nc);
           const uint32_t fr = (uint32_t)X;
           const uint32_t dq = *reinterpret_cast<const uint32_t*>(smem + (uint32_t)u * st4);
-          near = near || (uint32_t)(dq - fr + band_q) <= 2u * band_q;
+          nmin = min(nmin, dq - fr + band_q);
           const int v = u + (dq < fr ? 1 : 0);  // past the cell's point if it lies before tau_G
           const int2 lc = *reinterpret_cast<const int2*>(smem + loc_off + (uint32_t)v * st8);
           const longlong2 bs = *reinterpret_cast<const longlong2*>(smem + base_off + (uint32_t)(v >> 5) * st16);
@@ -420,11 +425,16 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
         };
         int c = 0;
         for (; c + 2 < cnt; c += 2) {
-          edge(G0 + c * gstep, true, false);
-          edge(G0 + (c + 1) * gstep, true, false);
+          edge(X, true, false);
+          edge(X + XS, true, false);
+          X += 2ull * XS;
         }
-        if (c + 1 < cnt) edge(G0 + c * gstep, true, false);
-        edge(G0 + (cnt - 1) * gstep, G0 + (cnt - 1) * gstep <= g_end, true);
+        if (c + 1 < cnt) {
+          edge(X, true, false);
+          X += XS;
+        }
+        edge(X, G0 + (cnt - 1) * gstep <= g_end, true);
+        bool near = nmin <= 2u * band_q;  // an edge within the guard band of its cell's point
         if (split) {  // warp-uniform: add the other phases of each bin into lanes 0 .. r-1
           for (int q = 1; q < P; ++q) {
             const long long ow = __shfl_down_sync(0xffffffffu, aw, q * r);
@@ -505,32 +515,31 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
     if (i >= 2) {  // sweep block i - 2: boxes starting at its bins
       const int k = ((i - 2) << 5) + lane;
       const float2* rb = ring + (((i - 2) & 1) << 5) + lane;
-      if (all_widths) sweep_start<true>(rb, k < nb, k, mmax, wmask, bsv, brv, bkey);
-      else sweep_start<false>(rb, k < nb, k, mmax, wmask, bsv, brv, bkey);
+      if (all_widths) sweep_start<true>(rb, k < nb, k, mmax, wmask, bs2, bd, bkey);
+      else sweep_start<false>(rb, k < nb, k, mmax, wmask, bs2, bd, bkey);
     }
     __syncwarp();
   }
   const bool none = bkey == 0x7fffffff;
-  float bs2 = none ? -1.f : __fmul_rn(bsv, bsv);
-  float bd = none ? 1.f : __fmaf_rn(-brv, brv, brv);
+  bs2 = none ? -1.f : bs2;
   const int bo = bkey >> 16;
+  // the lowest duration index of each width, read again here rather than kept live
+  const unsigned long long jlow = a.frec[fidx].jlow;
   int bj = none ? 255 : (int)((jlow >> (4 * bo)) & 15ull);
   int bk = none ? -1 : (bkey & 0xffff);
   int bm = none ? 0 : bo + 1;  // bins of the box
   for (int off = 16; off > 0; off >>= 1) {
     const float o_s2 = __shfl_xor_sync(0xffffffffu, bs2, off);
     const float o_d = __shfl_xor_sync(0xffffffffu, bd, off);
-    const float o_s = __shfl_xor_sync(0xffffffffu, bsv, off);
-    const float o_r = __shfl_xor_sync(0xffffffffu, brv, off);
     const int o_j = __shfl_xor_sync(0xffffffffu, bj, off);
     const int o_k = __shfl_xor_sync(0xffffffffu, bk, off);
     const int o_m = __shfl_xor_sync(0xffffffffu, bm, off);
     if (beats(o_s2, o_d, o_j, o_k, bs2, bd, bj, bk)) {
-      bs2 = o_s2; bd = o_d; bsv = o_s; brv = o_r; bj = o_j; bk = o_k; bm = o_m;
+      bs2 = o_s2; bd = o_d; bj = o_j; bk = o_k; bm = o_m;
     }
   }
   BoxBest bb;
-  bb.s2 = bs2; bb.d = bd; bb.s = bsv; bb.r = brv; bb.j = bj; bb.k = bk;
+  bb.s2 = bs2; bb.d = bd; bb.s = 0.f; bb.r = 0.f; bb.j = bj; bb.k = bk;
   bb.xv = false;
   if (lane == 0 && bk >= 0) {
     // the chosen box [bk, bk + bm) from the exact integer sums: U[bk + bm] - U[bk],
@@ -543,12 +552,13 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
     const long long nwrap = (bstar < k2m ? 1 : 0) + (k2 >= nb ? 1 : 0) - (bstar < bk ? 1 : 0);
     const long long dw = a1.x - a0.x + nwrap * fx.w_tot;
     const long long dy = a1.y - a0.y + nwrap * fx.y_tot;
-    if (fx.kw >= 0 && fx.kw <= 60) {
-      bb.xr = df_from_ll_scaled(dw, fx.kw);
-      bb.xq = df_from_ll_scaled((1ll << fx.kw) - dw, fx.kw);  // 1 - r
-      bb.xs = df_from_ll_scaled(dy, fx.ky);
-      bb.xv = true;
-    }
+    // kw lies in [24, 46] on this path: the largest weight is at most 1 and at least
+    // 1/N with N <= 2^21 points, and w_max 2^kw lies in [2^24, 2^25)
+    const int kw = min(max(fx.kw, 0), 62);
+    bb.xr = df_from_ll_scaled(dw, kw);
+    bb.xq = df_from_ll_scaled((1ll << kw) - dw, kw);  // 1 - r
+    bb.xs = df_from_ll_scaled(dy, fx.ky);
+    bb.xv = true;
   }
   store_box(bb, lane, fidx, a.sr, a.qidx, a.kbin, a.sbest, a.rbest);
 }
