@@ -556,6 +556,54 @@ __global__ void __launch_bounds__(256) dw_small_kernel(const TY* dy, const __nv_
   }
 }
 
+// Partial gradients of the first layer (64 x QLP_CNN_IN_CH channels, dY BF16): each
+// CTA takes whole 128-position tiles (len is a multiple of 128, so a tile lies in one
+// star's row) and stages dY [128][64] and X [128 + 8][CI] in shared memory; thread t
+// owns output channel t mod 64 and every fourth (tap, input channel) pair, so that a
+// warp reads 32 consecutive dY channels and one broadcast X value per step.
+__global__ void __launch_bounds__(256) dw_in_kernel(const __nv_bfloat16* dy, const __nv_bfloat16* x,
+                                                    float* partial, int batch, int len, int per_cta) {
+  constexpr int CI = QLP_CNN_IN_CH, TP = 128, NP = kTaps * CI, NPT = (NP + 3) / 4;
+  __shared__ float s_dy[TP][kC];
+  __shared__ float s_x[TP + kTaps - 1][CI];
+  const int tid = threadIdx.x, co = tid & (kC - 1), g = tid >> 6;
+  const int total = batch * len;
+  const int p_begin = blockIdx.x * per_cta;
+  const int p_end = min(total, p_begin + per_cta);
+  float acc[NPT];
+#pragma unroll
+  for (int i = 0; i < NPT; ++i) acc[i] = 0.f;
+  float acc_b = 0.f;
+  for (int p0 = p_begin; p0 < p_end; p0 += TP) {
+    const int b = p0 / len, l0 = p0 - b * len;
+    __syncthreads();
+    for (int i = tid; i < TP * kC; i += blockDim.x)
+      s_dy[i / kC][i % kC] = __bfloat162float(dy[(size_t)p0 * kC + i]);
+    for (int i = tid; i < (TP + kTaps - 1) * CI; i += blockDim.x) {
+      const int r = i / CI, ci = i % CI;
+      const int ll = l0 + r - kTaps / 2;  // zero padding outside the star's row
+      s_x[r][ci] = (ll >= 0 && ll < len) ? __bfloat162float(x[((size_t)b * len + ll) * CI + ci]) : 0.f;
+    }
+    __syncthreads();
+    for (int q = 0; q < TP; ++q) {
+      const float a = s_dy[q][co];
+      acc_b += a;
+#pragma unroll
+      for (int i = 0; i < NPT; ++i) {
+        const int pr = g + 4 * i;
+        if (pr < NP) acc[i] = fmaf(a, s_x[q + pr / CI][pr % CI], acc[i]);
+      }
+    }
+  }
+  float* out = partial + (size_t)blockIdx.x * (kTaps * kC * CI + kC);
+#pragma unroll
+  for (int i = 0; i < NPT; ++i) {
+    const int pr = g + 4 * i;
+    if (pr < NP) out[((pr / CI) * kC + co) * CI + pr % CI] = acc[i];
+  }
+  if (g == 0) out[kTaps * kC * CI + co] = acc_b;
+}
+
 __global__ void reduce_partials_kernel(const float* partial, int n_parts, int n_out, float* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_out) return;
@@ -643,10 +691,16 @@ int launch_wgrad64(const void* dy, const void* x, float* partial, float* out, in
 int launch_dw_small(const void* dy, int dy_is_f32, const void* x, float* partial, float* out, int batch,
                     int len, int n_co, int n_ci, void* s) {
   const int total = batch * len;
-  const int parts = dw_small_parts(batch, len);
-  const int per = (total + parts - 1) / parts;
+  int parts = dw_small_parts(batch, len);
+  int per = (total + parts - 1) / parts;
   const int n_out = kTaps * n_co * n_ci + n_co;
-  if (dy_is_f32)
+  if (!dy_is_f32 && n_co == kC && n_ci == QLP_CNN_IN_CH && len % 128 == 0) {  // the first layer
+    per = (per + 127) / 128 * 128;  // whole tiles; no more CTAs than the partial buffer holds
+    parts = (total + per - 1) / per;
+    dw_in_kernel<<<parts, 256, 0, (cudaStream_t)s>>>(static_cast<const __nv_bfloat16*>(dy),
+                                                      static_cast<const __nv_bfloat16*>(x), partial, batch, len,
+                                                      per);
+  } else if (dy_is_f32)
     dw_small_kernel<float><<<parts, 256, 0, (cudaStream_t)s>>>(static_cast<const float*>(dy),
                                                                 static_cast<const __nv_bfloat16*>(x), partial,
                                                                 batch, len, n_co, n_ci, per);
