@@ -3,18 +3,28 @@
 // tensor cores, BF16 operands, FP32 accumulation in tensor memory.
 //
 // Layouts. Activations are channels-last BF16 [B][L][64] (one 128-byte row per
-// position). A CTA computes a tile of 128 positions x 64 output channels:
+// position). A tile is 128 positions x 64 output channels:
 //   Y[l, co] = sum_{kk=0..8} sum_{ci} W[kk][co][ci] X[l + kk - 4, ci]
-// The 136 input rows l0-4 .. l0+131 are staged once per tile in shared memory in
-// the no-swizzle K-major canonical layout, one "plane" per 8 input channels
-// (rows at a 16-byte stride), so tap kk is the same tile shifted by kk rows: its
-// A descriptor starts kk * 16 bytes later. The weights (9 taps x 64 x 64) stay
-// resident in the same layout. One thread issues 9 taps x 4 K-steps of
-// tcgen05.mma (M = 128, N = 64, K = 16); the accumulator (128 lanes x 64 FP32
-// columns of TMEM) is read back with tcgen05.ld for the epilogue (bias, ReLU or
-// the backward ReLU mask, BF16 store). Tiles are double-buffered: the next
-// tile's rows are copied (cp.async, zero-filled outside [0, L)) while the MMAs
-// of the current one run.
+// Its 136 input rows l0-4 .. l0+131 sit in shared memory in the no-swizzle
+// K-major canonical layout, one "plane" per 8 input channels (rows at a 16-byte
+// stride), so tap kk is the same tile shifted by kk rows: its A descriptor starts
+// kk * 16 bytes later. The weights (9 taps x 64 x 64) stay resident in the same
+// layout. Each tile takes 9 taps x 4 K-steps of tcgen05.mma (M = 128, N = 64,
+// K = 16) into a TMEM accumulator of 64 FP32 columns.
+//
+// Pipeline (one persistent CTA per SM, warp roles): warp 0 loads tiles with TMA
+// into a ring of kStages buffers (8 plane copies per tile, each a box of 8
+// channels x 136 rows of a 3-D tensor map over [B][L][64], so rows outside
+// [0, L) of the tile's own sample come back as zeros); warp 1 issues the MMAs of
+// each tile into one of kAcc accumulators and commits them to the buffer's
+// "empty" barrier and the accumulator's "full" barrier; warps 2-9 (two per TMEM
+// lane quarter, 32 output channels each) read an accumulator back (one tcgen05.ld
+// of 32 columns), apply bias and ReLU or the backward ReLU mask, store BF16 and
+// release the accumulator. Every barrier wait
+// is bounded; a wait that runs out raises QLP error bit 16, and the CTA still
+// waits (bounded) for its copies and MMAs in flight before it frees TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -30,13 +40,16 @@ constexpr int kTaps = 9;           // kernel size
 constexpr int kTileM = 128;        // positions per tile
 constexpr int kRows = kTileM + kTaps - 1;  // staged rows per tile
 constexpr int kPlanes = kC / 8;    // 8 channels (16 bytes) per plane
-constexpr int kPlaneBytes = kRows * 16;    // 2,176
+constexpr int kPlaneBytes = kRows * 16;    // 2,176 (a multiple of 128: TMA destinations stay aligned)
 constexpr int kABytes = kPlanes * kPlaneBytes;  // 17,408
 constexpr int kWBytes = kTaps * kPlanes * kC * 16;  // 73,728
+constexpr int kStages = 6;         // tile buffers in flight
+constexpr int kAcc = 4;            // TMEM accumulators (64 columns each)
+constexpr int kEpiWarps = 8;       // two per TMEM lane quarter, 32 columns each
+constexpr int kConvThreads = 64 + 32 * kEpiWarps;  // producer, MMA, epilogue warps
 constexpr uint32_t kWaitLimit = 1u << 26;
 
 struct ConvTcArgs {
-  const __nv_bfloat16* x;      // [B][L][64]
   const uint4* wpack;          // packed weights, kWBytes
   const float* bias;           // [64] or null
   const __nv_bfloat16* mask;   // [B][L][64]: multiply by (mask > 0) (backward), or null
@@ -47,43 +60,44 @@ struct ConvTcArgs {
   int32_t relu;
 };
 
-__device__ __forceinline__ void stage_tile(unsigned char* abuf, const __nv_bfloat16* x, int b, int l0,
-                                           int len) {
-  // plane j, row r  <-  x[b][l0 - 4 + r][8j .. 8j+7]
-  for (int i = threadIdx.x; i < kPlanes * kRows; i += blockDim.x) {
-    const int j = i / kRows, r = i - j * kRows;
-    const int l = l0 - (kTaps / 2) + r;
-    const bool in = l >= 0 && l < len;
-    const __nv_bfloat16* src = x + ((size_t)b * len + (in ? l : 0)) * kC + 8 * j;
-    cp_async16(abuf + j * kPlaneBytes + r * 16, src, in ? 16u : 0u);
-  }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// One TMA box of the 3-D map (channel x, row y, sample z) into shared memory,
+// completing `bytes` on the barrier. x must be a multiple of 8 (16 bytes).
+__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
 }
 
-// Epilogue of one tile from TMEM accumulator columns [col, col + 64): row =
-// 32 warp + lane; bias, ReLU or the backward mask, BF16 store.
+// Epilogue of one tile: accumulator columns [col + c0, col + c0 + 32) (output
+// channels c0 .. c0+31) for the lane quarter q of this warp, row = 32 q + lane;
+// one TMEM load and wait, then bias, ReLU or the backward mask, BF16 store.
 __device__ __forceinline__ void conv_epilogue(const ConvTcArgs& a, const float* s_bias, uint32_t tmem,
-                                              uint32_t col, int t, int tiles_per_sample) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+                                              uint32_t col, int c0, int q, int t, int tiles_per_sample) {
+  const int lane = threadIdx.x & 31;
   const int b = t / tiles_per_sample;
-  const int l = (t % tiles_per_sample) * kTileM + 32 * warp + lane;
-  const size_t off = ((size_t)b * a.len + l) * kC;
+  const int l = (t % tiles_per_sample) * kTileM + 32 * q + lane;
+  const size_t off = ((size_t)b * a.len + l) * kC + c0;
   __nv_bfloat16* yrow = a.y + off;
   const __nv_bfloat16* mrow = a.mask ? a.mask + off : nullptr;
+  float v[32];
+  tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + col + (uint32_t)c0, v);
 #pragma unroll
-  for (int c0 = 0; c0 < kC; c0 += 16) {
-    float v[16];
-    tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + col + (uint32_t)c0, v);
-    uint32_t mw[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-    if (mrow) {
-      const uint4 m0 = reinterpret_cast<const uint4*>(mrow + c0)[0];
-      const uint4 m1 = reinterpret_cast<const uint4*>(mrow + c0)[1];
-      mw[0] = m0.x; mw[1] = m0.y; mw[2] = m0.z; mw[3] = m0.w;
-      mw[4] = m1.x; mw[5] = m1.y; mw[6] = m1.z; mw[7] = m1.w;
-    }
-    uint32_t ow[8];
+  for (int h = 0; h < 32; h += 8) {
+    uint4 m = make_uint4(0u, 0u, 0u, 0u);
+    if (mrow) m = reinterpret_cast<const uint4*>(mrow + h)[0];
+    const uint32_t mw[4] = {m.x, m.y, m.z, m.w};
+    uint32_t ow[4];
 #pragma unroll
-    for (int i = 0; i < 16; i += 2) {
-      float z0 = v[i] + s_bias[c0 + i], z1 = v[i + 1] + s_bias[c0 + i + 1];
+    for (int i = 0; i < 8; i += 2) {
+      float z0 = v[h + i] + s_bias[c0 + h + i], z1 = v[h + i + 1] + s_bias[c0 + h + i + 1];
       if (a.relu) { z0 = fmaxf(z0, 0.f); z1 = fmaxf(z1, 0.f); }
       if (mrow) {  // keep where the forward activation (BF16) is positive
         if (!(__uint_as_float(mw[i >> 1] << 16) > 0.f)) z0 = 0.f;
@@ -92,106 +106,120 @@ __device__ __forceinline__ void conv_epilogue(const ConvTcArgs& a, const float* 
       ow[i >> 1] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(z0)) |
                    ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(z1)) << 16);
     }
-    uint4* dst = reinterpret_cast<uint4*>(yrow + c0);
-    dst[0] = make_uint4(ow[0], ow[1], ow[2], ow[3]);
-    dst[1] = make_uint4(ow[4], ow[5], ow[6], ow[7]);
+    reinterpret_cast<uint4*>(yrow + h)[0] = make_uint4(ow[0], ow[1], ow[2], ow[3]);
   }
 }
 
-// Pipeline per CTA over its tiles t_0, t_1, ... (stride gridDim.x): while the
-// tensor core runs the MMAs of tile t_i into accumulator i % 2, the CTA copies
-// tile t_{i+1} into the other row buffer and writes out tile t_{i-1} from the
-// other accumulator.
-__global__ void __launch_bounds__(128) conv64_tc_kernel(const ConvTcArgs a) {
-  extern __shared__ __align__(128) unsigned char smem[];
+// Tile i of this CTA is tile blockIdx.x + i gridDim.x (all roles walk the same list).
+__global__ void __launch_bounds__(kConvThreads, 1)
+    conv64_tc_kernel(const __grid_constant__ CUtensorMap xmap, const ConvTcArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];  // TMA destinations need 128-byte alignment
   unsigned char* wsm = smem;
-  unsigned char* abuf0 = smem + kWBytes;
-  __shared__ __align__(8) uint64_t mbar[2];
+  unsigned char* ring = smem + kWBytes;  // kStages tile buffers of kABytes
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], accf[kAcc], acce[kAcc], fin;
   __shared__ uint32_t tmem_base;
   __shared__ float s_bias[kC];
+  __shared__ int s_fail;
 
   const int tid = threadIdx.x;
-  const int warp = tid >> 5;
+  const int warp = tid >> 5, lane = tid & 31;
   const int tiles_per_sample = a.len / kTileM;
   const int n_tiles = a.batch * tiles_per_sample;
+  const int n_my = (int)blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
-  // resident weights and bias
+  // resident weights and bias; barriers; TMEM
   const uint4* wsrc = a.wpack;
   uint4* wdst = reinterpret_cast<uint4*>(wsm);
   for (int i = tid; i < kWBytes / 16; i += blockDim.x) wdst[i] = wsrc[i];
   if (tid < kC) s_bias[tid] = a.bias ? a.bias[tid] : 0.f;
   if (tid == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    for (int k = 0; k < kStages; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], 1);
+    }
+    for (int k = 0; k < kAcc; ++k) {
+      mbar_init(&accf[k], 1);
+      mbar_init(&acce[k], kEpiWarps);  // one arrival per epilogue warp
+    }
+    mbar_init(&fin, 1);
+    s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(&tmem_base, 2 * kC);
-  int t = blockIdx.x;
-  if (t < n_tiles) stage_tile(abuf0, a.x, t / tiles_per_sample, (t % tiles_per_sample) * kTileM, a.len);
-  asm volatile("cp.async.commit_group;" ::: "memory");
+  if (warp == 1) tmem_alloc(&tmem_base, kAcc * kC);
+  fence_proxy_async_smem();  // the weights become visible to the tensor core
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = idesc_bf16_f32(kTileM, kC);
-  uint32_t parity = 0u;  // bit c: the phase parity accumulator c waits for next
-  int t_prev = -1;
-  int i = 0;
   bool ok = true;
 
-  for (; t < n_tiles; t += gridDim.x, ++i) {
-    const int cur = i & 1;
-    unsigned char* acur = abuf0 + cur * kABytes;
-    cp_async_wait_all();
-    fence_proxy_async_smem();  // the copies become visible to the tensor core
-    __syncthreads();
-    if (tid == 0) {
+  if (warp == 0 && lane == 0) {  // TMA producer
+    int issued = 0;
+    for (int i = 0; i < n_my && ok; ++i) {
+      const int s = i % kStages;
+      if (i >= kStages) ok = mbar_wait(&empty[s], (uint32_t)((i / kStages - 1) & 1), kWaitLimit);
+      if (!ok) break;
+      const int t = (int)blockIdx.x + i * (int)gridDim.x;
+      const int b = t / tiles_per_sample, l0 = (t % tiles_per_sample) * kTileM;
+      unsigned char* buf = ring + s * kABytes;
+      mbar_arrive_expect_tx(&full[s], (uint32_t)kABytes);
+#pragma unroll
+      for (int j = 0; j < kPlanes; ++j) tma_load3(buf + j * kPlaneBytes, &xmap, 8 * j, l0 - kTaps / 2, b, &full[s]);
+      issued = i + 1;
+    }
+    // every copy issued has landed before the CTA goes on (bounded)
+    for (int i = issued > kStages ? issued - kStages : 0; i < issued; ++i)
+      if (!mbar_wait(&full[i % kStages], (uint32_t)((i / kStages) & 1), kWaitLimit)) ok = false;
+  } else if (warp == 1 && lane == 0) {  // MMA issuer
+    const uint32_t idesc = idesc_bf16_f32(kTileM, kC);
+    // descriptors as a base plus a compile-time offset: every offset is a multiple of
+    // 16 bytes and every address stays below 2^18, so (addr + off) >> 4 = (addr >> 4)
+    // + (off >> 4) within the 14-bit start-address field
+    const uint64_t bdesc0 = smem_desc(smem_u32(wsm), kC * 16, 128);
+    for (int i = 0; i < n_my && ok; ++i) {
+      const int s = i % kStages, ac = i % kAcc;
+      ok = mbar_wait(&full[s], (uint32_t)((i / kStages) & 1), kWaitLimit);
+      if (ok && i >= kAcc) ok = mbar_wait(&acce[ac], (uint32_t)((i / kAcc - 1) & 1), kWaitLimit);
+      if (!ok) break;
       tc_fence_after();
-      const uint32_t abase = smem_u32(acur), wbase = smem_u32(wsm);
-      bool acc = false;
-#pragma unroll 1
+      const uint64_t adesc0 = smem_desc(smem_u32(ring + s * kABytes), kPlaneBytes, 128);
+      const uint32_t dst = tmem + (uint32_t)(ac * kC);
+#pragma unroll
       for (int kk = 0; kk < kTaps; ++kk) {
 #pragma unroll
         for (int ks = 0; ks < kPlanes / 2; ++ks) {
-          const uint64_t ad = smem_desc(abase + 2 * ks * kPlaneBytes + kk * 16, kPlaneBytes, 128);
-          const uint64_t bd = smem_desc(wbase + (kk * kPlanes + 2 * ks) * (kC * 16), kC * 16, 128);
-          mma_bf16(tmem + (uint32_t)(cur * kC), ad, bd, idesc, acc);
-          acc = true;
+          const uint64_t ad = adesc0 + (uint64_t)((2 * ks * kPlaneBytes + kk * 16) >> 4);
+          const uint64_t bd = bdesc0 + (uint64_t)(((kk * kPlanes + 2 * ks) * (kC * 16)) >> 4);
+          mma_bf16(dst, ad, bd, idesc, kk > 0 || ks > 0);
         }
       }
-      mma_commit(&mbar[cur]);
+      mma_commit(&empty[s]);  // the buffer is free once these MMAs have read it
+      mma_commit(&accf[ac]);  // the accumulator is ready
     }
-    if (t_prev >= 0) {  // the previous tile's MMAs: its buffer and accumulator become free
-      ok = mbar_wait(&mbar[cur ^ 1], (parity >> (cur ^ 1)) & 1u, kWaitLimit);
-      parity ^= 1u << (cur ^ 1);
-      ok = __syncthreads_and(ok) != 0;
+    // every MMA issued has completed before TMEM is freed (bounded)
+    mma_commit(&fin);
+    if (!mbar_wait(&fin, 0u, kWaitLimit)) ok = false;
+  } else if (warp >= 2) {  // epilogue: TMEM lane quarter warp % 4, channels c0 .. c0+31
+    const int q = warp & 3, c0 = 32 * ((warp - 2) / 4);
+    for (int i = 0; i < n_my && ok; ++i) {
+      const int ac = i % kAcc;
+      ok = mbar_wait(&accf[ac], (uint32_t)((i / kAcc) & 1), kWaitLimit);
+      ok = __all_sync(0xffffffffu, ok) != 0;
       if (!ok) break;
       tc_fence_after();
-    }
-    const int tn = t + gridDim.x;
-    if (tn < n_tiles)
-      stage_tile(abuf0 + (cur ^ 1) * kABytes, a.x, tn / tiles_per_sample, (tn % tiles_per_sample) * kTileM,
-                 a.len);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    if (t_prev >= 0) conv_epilogue(a, s_bias, tmem, (uint32_t)((cur ^ 1) * kC), t_prev, tiles_per_sample);
-    tc_fence_before();
-    t_prev = t;
-  }
-  if (ok && t_prev >= 0) {  // the last tile
-    const int last = (i - 1) & 1;
-    ok = mbar_wait(&mbar[last], (parity >> last) & 1u, kWaitLimit);
-    ok = __syncthreads_and(ok) != 0;
-    if (ok) {
-      tc_fence_after();
-      conv_epilogue(a, s_bias, tmem, (uint32_t)(last * kC), t_prev, tiles_per_sample);
+      conv_epilogue(a, s_bias, tmem, (uint32_t)(ac * kC), c0, q, (int)blockIdx.x + i * (int)gridDim.x,
+                    tiles_per_sample);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[ac]);
     }
   }
-  if (!ok && tid == 0) atomicOr(a.err, kErrMmaWait);
-  cp_async_wait_all();
+  if (!ok) atomicExch(&s_fail, 1);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, 2 * kC);
+  if (tid == 0 && s_fail) atomicOr(a.err, kErrMmaWait);
+  if (warp == 1) tmem_dealloc(tmem, kAcc * kC);
 }
 
 // W[kk][co][ci] (FP32) -> BF16 planes for the tensor-core kernel. transpose=1
@@ -213,15 +241,43 @@ __global__ void pack_w64_kernel(const float* w, uint4* out, int transpose) {
 }
 
 // Shared memory of the conv kernel: resident weights and two row tiles.
-int conv64_smem_bytes() { return kWBytes + 2 * kABytes; }
+int conv64_smem_bytes() { return kWBytes + kStages * kABytes; }
+
+// cuTensorMapEncodeTiled from the driver, found once through the runtime
+static PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
 
 int launch_conv64(const void* xv, const void* wv, const float* bias, const void* mv, void* yv,
                   int32_t* err, int batch, int len, int relu, void* stream) {
-  const __nv_bfloat16* x = static_cast<const __nv_bfloat16*>(xv);
   const uint4* wpack = static_cast<const uint4*>(wv);
   const __nv_bfloat16* mask = static_cast<const __nv_bfloat16*>(mv);
   __nv_bfloat16* y = static_cast<__nv_bfloat16*>(yv);
   if (batch <= 0) return 0;
+  // the input as a 3-D tensor (channel, position, sample), boxes of 8 channels x 136
+  // rows x 1 sample: one plane of a tile, zeros outside the sample's [0, len)
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
+  if (!enc) return (int)cudaErrorNotSupported;
+  alignas(64) CUtensorMap map;
+  const cuuint64_t dims[3] = {(cuuint64_t)kC, (cuuint64_t)len, (cuuint64_t)batch};
+  const cuuint64_t strides[2] = {(cuuint64_t)kC * 2, (cuuint64_t)len * kC * 2};
+  const cuuint32_t box[3] = {8, (cuuint32_t)kRows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(xv), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return (int)cudaErrorInvalidValue;
   const int smem = conv64_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(conv64_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return (int)e;
@@ -229,9 +285,9 @@ int launch_conv64(const void* xv, const void* wv, const float* bias, const void*
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int tiles = batch * (len / kTileM);
-  const int grid = tiles < 2 * sms ? tiles : 2 * sms;
-  ConvTcArgs a{x, wpack, bias, mask, y, err, batch, len, relu};
-  conv64_tc_kernel<<<grid, 128, smem, (cudaStream_t)stream>>>(a);
+  const int grid = tiles < sms ? tiles : sms;
+  ConvTcArgs a{wpack, bias, mask, y, err, batch, len, relu};
+  conv64_tc_kernel<<<grid, kConvThreads, smem, (cudaStream_t)stream>>>(map, a);
   return (int)cudaGetLastError();
 }
 

@@ -259,9 +259,10 @@ constexpr int kFixedWarps = 32;
 constexpr int64_t kFixedWsBlock = 131072;  // workspace entries (16 B) per block for windowed stars
 // bytes of shared memory before the histograms of the cell kernel for a star with
 // ncs cells (incl. sentinel) and nw warps
-// One point of a candidate's fit window: t', y, 1/dy and its transit index.
+// One point of a candidate's fit window: t', y, 1/dy, and P n for its transit
+// index n at the starting epoch (the product the model's dt = (t' - T0) - P n uses).
 struct __align__(16) WinRec {
-  double t, y, inv, n;
+  double t, y, inv, pn;
 };
 
 struct StatsArgs {

@@ -34,8 +34,9 @@ namespace qlp {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 128;
 constexpr int kWarps = kThreads / 32;
+constexpr int kRampBuf = 64;  // queued ramp points per warp (a batch of 32 is taken at 32)
 constexpr int kSums = 21;  // chi^2, g[5], A upper triangle [15]
 constexpr double kQinMin = 1e-3, kQMin = 1e-6, kQinInit = 0.1;
 constexpr double kLam0 = 1e-3, kRtol = 1e-10, kLamMax = 1e10;
@@ -127,8 +128,11 @@ __device__ bool solve5(double (*m)[6], double* h) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads, 2) stats_kernel(const StatsArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) stats_kernel(const StatsArgs a) {
   __shared__ double red[kWarps][kSums];
+  __shared__ double s_part[kThreads][kSums + 1];  // per-thread normal-equation sums
+  __shared__ double s_q[kThreads / 32][kSums];
+  __shared__ int s_ramp[kWarps][kRampBuf];
   __shared__ double s_tot[kSums];  // block totals of the last reduction
   __shared__ double s_cur[kSums];  // chi^2, g, A at the accepted parameters (thread 0)
   __shared__ double s_m[5][6];     // the damped normal equations (thread 0)
@@ -209,7 +213,7 @@ __global__ void __launch_bounds__(kThreads, 2) stats_kernel(const StatsArgs a) {
       const double u = __dsub_rn(tp[i], t0p);
       const double nn = floor(__dadd_rn(__ddiv_rn(u, period), 0.5));
       const double dt = fabs(__dsub_rn(u, __dmul_rn(period, nn)));
-      if (dt <= lim) wrec[o++] = WinRec{tp[i], yv[i], __ddiv_rn(1.0, dyv[i]), nn};
+      if (dt <= lim) wrec[o++] = WinRec{tp[i], yv[i], __ddiv_rn(1.0, dyv[i]), __dmul_rn(period, nn)};
     }
   }
   if (nwin < 6) {
@@ -226,8 +230,14 @@ __global__ void __launch_bounds__(kThreads, 2) stats_kernel(const StatsArgs a) {
   const int wseg = (nwin + kThreads - 1) / kThreads;
   const int w0 = min(nwin, tid * wseg), w1 = min(nwin, w0 + wseg);
   // The model at s_x and its derivatives. Only points on a ramp have nonzero
-  // derivatives in T0, q and q_in; flat-bottom points add to the (delta, z)
-  // block and outside points to z alone, so those skip the zero products.
+  // derivatives in T0, q and q_in; flat-bottom points add to the (delta, z) block
+  // and outside points to z alone, in place. Ramp points are queued per warp and
+  // taken 32 at a time by all lanes, so that the long ramp branch runs once per 32
+  // ramp points instead of whenever one lane meets one; its divisions are
+  // multiplications by reciprocals taken once per evaluation. The region
+  // decisions keep the FP64 expressions of the model's definition.
+  const int lane = tid & 31, warp_id = tid >> 5;
+  int* rl = s_ramp[warp_id];
   auto evaluate = [&]() {  // at s_x: chi^2, J^T r, J^T J into s_tot
     double sums[kSums];
     double x[5];
@@ -237,49 +247,103 @@ __global__ void __launch_bounds__(kThreads, 2) stats_kernel(const StatsArgs a) {
     const double half = __dmul_rn(0.5, d);
     const double edge = __dsub_rn(half, t_in);
     const double hp = __dmul_rn(0.5, period);
+    const double r_tin = 1.0 / t_in;
+    const double m_flat = __dsub_rn(x[4], x[1]);  // the model on the flat bottom
+    const double r_q = -x[1] / (x[3] * x[2] * x[2] * period);  // d(-delta s)/dq per unit a
+    const double r_qin = x[1] / x[3];
     for (int i = 0; i < kSums; ++i) sums[i] = 0.0;
-    for (int wi = w0; wi < w1; ++wi) {
-      const WinRec pt = wrec[wi];  // t', y, 1/dy, transit index of the starting epoch
+    // |v| of a double as its bit pattern: for non-negative doubles the order of the
+    // patterns (as integers) is the order of the values, so the region tests below
+    // take the integer pipe instead of the FP64 one
+    auto mag = [](double v) { return __double_as_longlong(v) & 0x7fffffffffffffffll; };
+    const long long hp_b = mag(hp), edge_b = mag(edge), half_b = mag(half);
+    auto dt_of = [&](const WinRec& pt) {
       const double u = __dsub_rn(pt.t, x[0]);
-      double dt = __dsub_rn(u, __dmul_rn(period, pt.n));
-      if (fabs(dt) > hp) {  // the epoch moved by half a period: the nearest transit changed
+      double dt = __dsub_rn(u, pt.pn);
+      if (mag(dt) > hp_b) {  // the epoch moved by half a period: the nearest transit changed
         const double nn = floor(__dadd_rn(__ddiv_rn(u, period), 0.5));
         dt = __dsub_rn(u, __dmul_rn(period, nn));
       }
-      const double aa = fabs(dt);
-      const double inv = pt.inv;
-      if (aa <= edge) {  // flat bottom: s = 1, dm/ddelta = -1, dm/dz = 1
-        const double r = __dmul_rn(__dsub_rn(pt.y, __dsub_rn(x[4], x[1])), inv);
-        const double i2 = inv * inv;
-        sums[0] += r * r;
-        sums[2] -= inv * r;
-        sums[5] += inv * r;
-        sums[6 + 5] += i2;   // A11
-        sums[6 + 8] -= i2;   // A14
-        sums[6 + 14] += i2;  // A44
-      } else if (aa < half) {  // ramp
-        const double sv = __ddiv_rn(__dsub_rn(half, aa), t_in);
+      return dt;
+    };
+    auto ramp_batch = [&](int cnt) {  // lanes < cnt take the queued ramp points rl[lane]
+      if (lane < cnt) {
+        const WinRec pt = wrec[rl[lane]];
+        const double dt = dt_of(pt);
+        const double aa = fabs(dt);
+        const double inv = pt.inv;
+        const double sv = __dmul_rn(__dsub_rn(half, aa), r_tin);
         const double r = __dmul_rn(__dsub_rn(pt.y, __dsub_rn(x[4], __dmul_rn(x[1], sv))), inv);
         const double sg = dt > 0.0 ? 1.0 : (dt < 0.0 ? -1.0 : 0.0);
         double j[5];
-        j[0] = -x[1] * sg / t_in * inv;
+        j[0] = -x[1] * sg * r_tin * inv;
         j[1] = -sv * inv;
-        j[2] = -x[1] * aa / (x[3] * x[2] * x[2] * period) * inv;
-        j[3] = x[1] * sv / x[3] * inv;
+        j[2] = r_q * aa * inv;
+        j[3] = r_qin * sv * inv;
         j[4] = inv;
         sums[0] += r * r;
         for (int k = 0; k < 5; ++k) sums[1 + k] += j[k] * r;
         int p = 6;
         for (int k = 0; k < 5; ++k)
           for (int l = k; l < 5; ++l) sums[p++] += j[k] * j[l];
-      } else {  // outside the transit: s = 0, dm/dz = 1
-        const double r = __dmul_rn(__dsub_rn(pt.y, x[4]), inv);
-        sums[0] += r * r;
-        sums[5] += inv * r;
-        sums[6 + 14] += inv * inv;
+      }
+    };
+    int nr = 0;  // queued ramp points of this warp (warp-uniform)
+    for (int k = 0; k < wseg; ++k) {  // the same trip count on every lane
+      const int wi = w0 + k;
+      bool on_ramp = false;
+      if (wi < w1) {
+        const WinRec pt = wrec[wi];  // t', y, 1/dy, P n of the starting epoch
+        const long long ab = mag(dt_of(pt));
+        const double inv = pt.inv;
+        on_ramp = ab > edge_b && ab < half_b;
+        if (!on_ramp) {  // flat bottom (s = 1) or outside (s = 0): one path, no divergence
+          const bool flat = ab <= edge_b;  // dm/ddelta = -s, dm/dz = 1
+          const double r = __dmul_rn(__dsub_rn(pt.y, flat ? m_flat : x[4]), inv);
+          const double fs = flat ? 1.0 : 0.0;
+          const double ir = inv * r, i2 = inv * inv;
+          sums[0] += r * r;
+          sums[2] -= fs * ir;
+          sums[5] += ir;
+          sums[6 + 5] += fs * i2;   // A11
+          sums[6 + 8] -= fs * i2;   // A14
+          sums[6 + 14] += i2;       // A44
+        }
+      }
+      const unsigned mk = __ballot_sync(0xffffffffu, on_ramp);
+      if (on_ramp) rl[nr + __popc(mk & ((1u << lane) - 1u))] = wi;
+      nr += __popc(mk);
+      if (nr >= 32) {
+        __syncwarp();
+        ramp_batch(32);
+        const int rest = nr - 32;
+        const int moved = lane < rest ? rl[32 + lane] : 0;
+        __syncwarp();
+        if (lane < rest) rl[lane] = moved;
+        __syncwarp();
+        nr = rest;
       }
     }
-    block_sums(sums, kSums, red, s_tot);
+    __syncwarp();
+    if (nr > 0) ramp_batch(nr);
+    __syncwarp();
+    // block sums through shared memory: each thread of the first kSums x 4 sums one
+    // value over 32 threads, then kSums threads add the 4 quarters in order
+    for (int i = 0; i < kSums; ++i) s_part[tid][i] = sums[i];
+    __syncthreads();
+    if (tid < kSums * (kThreads / 32)) {
+      const int v = tid % kSums, qq = tid / kSums;
+      double acc = 0.0;
+      for (int r = 0; r < 32; ++r) acc += s_part[32 * qq + r][v];
+      s_q[qq][v] = acc;
+    }
+    __syncthreads();
+    if (tid < kSums) {
+      double acc = 0.0;
+      for (int qq = 0; qq < kThreads / 32; ++qq) acc += s_q[qq][tid];
+      s_tot[tid] = acc;
+    }
+    __syncthreads();
   };
   double xa[5];
   evaluate();
