@@ -197,6 +197,7 @@ struct qlp_bls_plan {
   // search + S/N captured as one CUDA graph (qlp_bls_graph_capture)
   // slot parts-1: parts = 1 search, 2 S/N, 3 both
   WinRec* d_wrec = nullptr;      // candidate statistics scratch (allocated on first use)
+  int32_t* d_sorder = nullptr;   // and the statistics' launch order
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t kev[2] = {};        // qlp_bls_kernel_timing: around the main search kernel
   // recorded after the plan's last device work (control words, per-frequency
@@ -204,7 +205,7 @@ struct qlp_bls_plan {
   // not wait for kernels that occupy the GPU
   cudaEvent_t ready = nullptr;
   void* d_arena = nullptr;        // the one allocation holding the plan's buffers
-  size_t arena_bytes = 0, wrec_bytes = 0;  // device bytes held against the budget
+  size_t arena_bytes = 0, wrec_bytes = 0, sorder_bytes = 0;  // device bytes held against the budget
   bool ready_seen = false;        // the host has seen `ready` complete
   cudaGraph_t graph[3] = {};
   cudaGraphExec_t gexec[3] = {};
@@ -225,7 +226,8 @@ static void free_plan(qlp_bls_plan_t* pl) {
   if (pl->kev[1]) cudaEventDestroy(pl->kev[1]);
   cudaFree(pl->d_arena);  // every buffer below but d_wrec lives in it
   cudaFree(pl->d_wrec);
-  budget_give(pl->arena_bytes + pl->wrec_bytes);
+  cudaFree(pl->d_sorder);
+  budget_give(pl->arena_bytes + pl->wrec_bytes + pl->sorder_bytes);
   delete pl;
 }
 
@@ -1255,6 +1257,10 @@ int qlp_bls_candidate_stats(qlp_bls_plan_t* pl, void* stream, const qlp_bls_best
     const int rc = dev_alloc(&pl->d_wrec, (size_t)std::max<int64_t>(pl->n_pts_alloc, 1), &pl->wrec_bytes);
     if (rc) return rc;
   }
+  if (!pl->d_sorder) {
+    const int rc = dev_alloc(&pl->d_sorder, (size_t)pl->n_stars, &pl->sorder_bytes);
+    if (rc) return rc;
+  }
   StatsArgs a{};
   a.stars = pl->d_stars;
   a.n_stars = pl->n_stars;
@@ -1264,6 +1270,7 @@ int qlp_bls_candidate_stats(qlp_bls_plan_t* pl, void* stream, const qlp_bls_best
   a.best = best;
   a.out = out;
   a.wrec = pl->d_wrec;
+  a.order = pl->d_sorder;
   const int e = launch_stats(a, stream);
   return e ? cuda_fail((cudaError_t)e, "stats launch") : QLP_OK;
 }

@@ -47,13 +47,14 @@ constexpr int kStages = 6;         // tile buffers in flight
 constexpr int kAcc = 4;            // TMEM accumulators (64 columns each)
 constexpr int kEpiWarps = 8;       // two per TMEM lane quarter, 32 columns each
 constexpr int kConvThreads = 64 + 32 * kEpiWarps;  // producer, MMA, epilogue warps
+constexpr int kOutBytes = kTileM * kC * 2;  // one BF16 output tile (16 KB), staged for a TMA store
+constexpr int kOutBufs = 2;
 constexpr uint32_t kWaitLimit = 1u << 26;
 
 struct ConvTcArgs {
   const uint4* wpack;          // packed weights, kWBytes
   const float* bias;           // [64] or null
   const __nv_bfloat16* mask;   // [B][L][64]: multiply by (mask > 0) (backward), or null
-  __nv_bfloat16* y;            // [B][L][64]
   int32_t* err;
   int32_t batch;
   int32_t len;                 // multiple of 128
@@ -76,19 +77,49 @@ __device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int
       : "memory");
 }
 
+// A shared-memory box to the 3-D map (channel x, row y, sample z) as one bulk group
+// of this thread. x = 0 and y >= 0: the store starts at a 16-byte boundary.
+__device__ __forceinline__ void tma_store3(const CUtensorMap* map, const void* src, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];\n\t"
+      "cp.async.bulk.commit_group;" ::"l"(reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
+      : "memory");
+}
+// This thread's bulk groups have finished reading shared memory / have completed.
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Barrier of the epilogue warps (id 1) that also ANDs a predicate over them.
+__device__ __forceinline__ bool epi_barrier_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+      "barrier.cta.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(32 * kEpiWarps)
+      : "memory");
+  return r != 0;
+}
+
 // Epilogue of one tile: accumulator columns [col + c0, col + c0 + 32) (output
-// channels c0 .. c0+31) for the lane quarter q of this warp, row = 32 q + lane;
-// one TMEM load and wait, then bias, ReLU or the backward mask, BF16 store.
+// channels c0 .. c0+31) for the lane quarter q of this warp, row r = 32 q + lane;
+// one TMEM load and wait, the accumulator released, then bias, ReLU or the backward
+// mask, BF16, into the staging tile `out` (128 rows of 128 bytes, 1024-byte aligned)
+// with the 128-byte swizzle of the store's tensor map: 16-byte chunk j of row r at
+// chunk j ^ (r & 7), so that eight lanes fill the 32 banks once.
 __device__ __forceinline__ void conv_epilogue(const ConvTcArgs& a, const float* s_bias, uint32_t tmem,
-                                              uint32_t col, int c0, int q, int t, int tiles_per_sample) {
+                                              uint32_t col, int c0, int q, int t, int tiles_per_sample,
+                                              uint64_t* acc_empty, unsigned char* out) {
   const int lane = threadIdx.x & 31;
+  const int r = 32 * q + lane;
   const int b = t / tiles_per_sample;
-  const int l = (t % tiles_per_sample) * kTileM + 32 * q + lane;
-  const size_t off = ((size_t)b * a.len + l) * kC + c0;
-  __nv_bfloat16* yrow = a.y + off;
-  const __nv_bfloat16* mrow = a.mask ? a.mask + off : nullptr;
+  const int l = (t % tiles_per_sample) * kTileM + r;
+  const __nv_bfloat16* mrow = a.mask ? a.mask + ((size_t)b * a.len + l) * kC + c0 : nullptr;
   float v[32];
   tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + col + (uint32_t)c0, v);
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(acc_empty);  // the values are in registers: the MMA may reuse the columns
 #pragma unroll
   for (int h = 0; h < 32; h += 8) {
     uint4 m = make_uint4(0u, 0u, 0u, 0u);
@@ -106,16 +137,21 @@ __device__ __forceinline__ void conv_epilogue(const ConvTcArgs& a, const float* 
       ow[i >> 1] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(z0)) |
                    ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(z1)) << 16);
     }
-    reinterpret_cast<uint4*>(yrow + h)[0] = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+    const int j = (c0 + h) >> 3;  // the 16-byte chunk of the 128-byte row
+    *reinterpret_cast<uint4*>(out + r * 128 + ((j ^ (r & 7)) << 4)) = make_uint4(ow[0], ow[1], ow[2], ow[3]);
   }
 }
 
 // Tile i of this CTA is tile blockIdx.x + i gridDim.x (all roles walk the same list).
 __global__ void __launch_bounds__(kConvThreads, 1)
-    conv64_tc_kernel(const __grid_constant__ CUtensorMap xmap, const ConvTcArgs a) {
+    conv64_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap ymap,
+                     const ConvTcArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];  // TMA destinations need 128-byte alignment
   unsigned char* wsm = smem;
   unsigned char* ring = smem + kWBytes;  // kStages tile buffers of kABytes
+  // kOutBufs output staging tiles at the next 1024-byte boundary (the 128-byte swizzle's period)
+  unsigned char* obuf = ring + kStages * kABytes;
+  obuf += (1024u - (smem_u32(obuf) & 1023u)) & 1023u;
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], accf[kAcc], acce[kAcc], fin;
   __shared__ uint32_t tmem_base;
   __shared__ float s_bias[kC];
@@ -201,18 +237,25 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     if (!mbar_wait(&fin, 0u, kWaitLimit)) ok = false;
   } else if (warp >= 2) {  // epilogue: TMEM lane quarter warp % 4, channels c0 .. c0+31
     const int q = warp & 3, c0 = 32 * ((warp - 2) / 4);
-    for (int i = 0; i < n_my && ok; ++i) {
+    const bool issuer = warp == 2 && lane == 0;  // issues the tile's TMA store
+    for (int i = 0; i < n_my; ++i) {
       const int ac = i % kAcc;
-      ok = mbar_wait(&accf[ac], (uint32_t)((i / kAcc) & 1), kWaitLimit);
-      ok = __all_sync(0xffffffffu, ok) != 0;
+      const int t = (int)blockIdx.x + i * (int)gridDim.x;
+      // staging tile i % 2: its store (tile i - 2) finished reading before the last barrier
+      unsigned char* out = obuf + (i % kOutBufs) * kOutBytes;
+      bool mine = mbar_wait(&accf[ac], (uint32_t)((i / kAcc) & 1), kWaitLimit);
+      mine = __all_sync(0xffffffffu, mine) != 0;
+      if (mine) {
+        tc_fence_after();
+        conv_epilogue(a, s_bias, tmem, (uint32_t)(ac * kC), c0, q, t, tiles_per_sample, &acce[ac], out);
+        fence_proxy_async_smem();  // the staged tile becomes visible to the TMA store
+      }
+      if (issuer) bulk_wait_read_all();  // tile i - 1's store has read the other staging tile
+      ok = epi_barrier_and(mine);  // every epilogue warp takes the same branch
       if (!ok) break;
-      tc_fence_after();
-      conv_epilogue(a, s_bias, tmem, (uint32_t)(ac * kC), c0, q, (int)blockIdx.x + i * (int)gridDim.x,
-                    tiles_per_sample);
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acce[ac]);
+      if (issuer) tma_store3(&ymap, out, 0, (t % tiles_per_sample) * kTileM, t / tiles_per_sample);
     }
+    if (issuer) bulk_wait_all();  // the stores are complete before the CTA ends
   }
   if (!ok) atomicExch(&s_fail, 1);
   tc_fence_before();
@@ -240,8 +283,9 @@ __global__ void pack_w64_kernel(const float* w, uint4* out, int transpose) {
   out[i] = *reinterpret_cast<const uint4*>(v);
 }
 
-// Shared memory of the conv kernel: resident weights and two row tiles.
-int conv64_smem_bytes() { return kWBytes + kStages * kABytes; }
+// Shared memory of the conv kernel: resident weights, the row tiles and the output
+// staging tiles (with up to 1 KB to align them).
+int conv64_smem_bytes() { return kWBytes + kStages * kABytes + 1024 + kOutBufs * kOutBytes; }
 
 // cuTensorMapEncodeTiled from the driver, found once through the runtime
 static PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
@@ -263,7 +307,6 @@ int launch_conv64(const void* xv, const void* wv, const float* bias, const void*
                   int32_t* err, int batch, int len, int relu, void* stream) {
   const uint4* wpack = static_cast<const uint4*>(wv);
   const __nv_bfloat16* mask = static_cast<const __nv_bfloat16*>(mv);
-  __nv_bfloat16* y = static_cast<__nv_bfloat16*>(yv);
   if (batch <= 0) return 0;
   // the input as a 3-D tensor (channel, position, sample), boxes of 8 channels x 136
   // rows x 1 sample: one plane of a tile, zeros outside the sample's [0, len)
@@ -278,6 +321,14 @@ int launch_conv64(const void* xv, const void* wv, const float* bias, const void*
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return (int)cudaErrorInvalidValue;
+  // the output as the same 3-D tensor, boxes of a whole tile (64 channels x 128 rows),
+  // 128-byte swizzle (one row of a tile is 128 bytes)
+  alignas(64) CUtensorMap ymap;
+  const cuuint32_t obox[3] = {(cuuint32_t)kC, (cuuint32_t)kTileM, 1};
+  if (enc(&ymap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, yv, dims, strides, obox, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return (int)cudaErrorInvalidValue;
   const int smem = conv64_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(conv64_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return (int)e;
@@ -286,8 +337,8 @@ int launch_conv64(const void* xv, const void* wv, const float* bias, const void*
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int tiles = batch * (len / kTileM);
   const int grid = tiles < sms ? tiles : sms;
-  ConvTcArgs a{wpack, bias, mask, y, err, batch, len, relu};
-  conv64_tc_kernel<<<grid, kConvThreads, smem, (cudaStream_t)stream>>>(map, a);
+  ConvTcArgs a{wpack, bias, mask, err, batch, len, relu};
+  conv64_tc_kernel<<<grid, kConvThreads, smem, (cudaStream_t)stream>>>(map, ymap, a);
   return (int)cudaGetLastError();
 }
 

@@ -259,10 +259,11 @@ constexpr int kFixedWarps = 32;
 constexpr int64_t kFixedWsBlock = 131072;  // workspace entries (16 B) per block for windowed stars
 // bytes of shared memory before the histograms of the cell kernel for a star with
 // ncs cells (incl. sentinel) and nw warps
-// One point of a candidate's fit window: t', y, 1/dy, and P n for its transit
-// index n at the starting epoch (the product the model's dt = (t' - T0) - P n uses).
+// One point of a candidate's fit window: t', P n for its transit index n at the
+// starting epoch (the product the model's dt = (t' - T0) - P n uses), y, 1/dy and
+// its square (the point's weight).
 struct __align__(16) WinRec {
-  double t, y, inv, pn;
+  double t, pn, y, inv, w, pad;
 };
 
 struct StatsArgs {
@@ -274,6 +275,7 @@ struct StatsArgs {
   const qlp_bls_best* best;
   qlp_bls_cand_stats* out;
   WinRec* wrec;  // scratch: fit-window points, CSR by pt_off
+  int32_t* order;  // scratch [n_stars]: the CTAs' stars, the longest fits first (or null: star = CTA)
 };
 int launch_peaks(const StarDev* stars, int n_stars, const double2* fq, const float* snr, int n_peaks, double sep,
                  int32_t* out, void* stream);

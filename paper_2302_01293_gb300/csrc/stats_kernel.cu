@@ -21,9 +21,17 @@
 //    (-2D <= dt < -D/2) and after (D/2 < dt <= 2D) transit;
 //  * detected = N_t >= 2 and S/N_pink > 9 and S/N > 9.
 // The model's region decisions use explicitly rounded FP64 operations (no
-// contraction), in the order the definition states them. Point sums are taken
-// per thread over contiguous index ranges and combined in a fixed order, so the
-// results do not depend on scheduling.
+// contraction), in the order the definition states them; the quotients they
+// round down (the nearest transit index, the residual time bin) come from a
+// reciprocal and fall back to the exact division wherever the two could round
+// differently. Point sums are taken per thread over contiguous index ranges and
+// combined in a fixed order, so the results do not depend on scheduling.
+//
+// GB300 executes FP64 at 1/64 of the FP32 rate, so the cost of this kernel is its
+// count of FP64 operations per point: the fit's pass over a flat-bottom or
+// outside point takes eight (the point's phase, residual and five sums; the
+// weight 1/dy^2 and the (z, z) curvature, the sum of all weights, are taken once),
+// and region tests compare FP64 bit patterns on the integer pipe.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -42,35 +50,24 @@ constexpr double kQinMin = 1e-3, kQMin = 1e-6, kQinInit = 0.1;
 constexpr double kLam0 = 1e-3, kRtol = 1e-10, kLamMax = 1e10;
 constexpr int kMaxIt = 100;
 
-struct Model {
-  double dt, a, s, m;
-  long long k;
-  bool ramp;
-};
+// |v| of a double as its bit pattern: for non-negative doubles the order of the
+// patterns (as integers) is the order of the values
+__device__ __forceinline__ long long mag(double v) { return __double_as_longlong(v) & 0x7fffffffffffffffll; }
 
-__device__ __forceinline__ Model model_at(double t, const double* x, double period) {
-  Model o;
-  const double u = __dsub_rn(t, x[0]);
-  const double n = floor(__dadd_rn(__ddiv_rn(u, period), 0.5));
-  o.k = (long long)n;
-  o.dt = __dsub_rn(u, __dmul_rn(period, n));
-  o.a = fabs(o.dt);
-  const double d = __dmul_rn(x[2], period);
-  const double t_in = __dmul_rn(x[3], d);
-  const double half = __dmul_rn(0.5, d);
-  const double edge = __dsub_rn(half, t_in);
-  if (o.a <= edge) {
-    o.s = 1.0;
-    o.ramp = false;
-  } else if (o.a < half) {
-    o.s = __ddiv_rn(__dsub_rn(half, o.a), t_in);
-    o.ramp = true;
-  } else {
-    o.s = 0.0;
-    o.ramp = false;
-  }
-  o.m = __dsub_rn(x[4], __dmul_rn(x[1], o.s));
-  return o;
+// floor(fl(fl(num / den) + add)), add = 0.5 (HALF) or 0, from rden = fl(1 / den).
+// fl(num rden) lies within 3 2^-53 |num / den| of fl(num / den); below 2^20 in
+// magnitude that is under 2^-31, and with the rounding of the sum the two floors
+// agree unless the sum lies within 2^-30 of an integer. There, and for larger
+// quotients, the quotient is taken exactly.
+template <bool HALF>
+__device__ __forceinline__ double floor_quot(double num, double den, double rden) {
+  const double q = __dmul_rn(num, rden);
+  const double b = HALF ? __dadd_rn(q, 0.5) : q;
+  const double nn = floor(b);
+  const double fr = __dsub_rn(b, nn);  // in [0, 1), accurate to 2^-53
+  if (fr > 0x1p-30 && fr < 1.0 - 0x1p-30 && fabs(b) < 0x1p20) return nn;
+  const double qe = __ddiv_rn(num, den);
+  return floor(HALF ? __dadd_rn(qe, 0.5) : qe);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -100,51 +97,99 @@ __device__ __forceinline__ void clip(double* x) {
   x[3] = fmin(fmax(x[3], kQinMin), 0.5);
 }
 
-// Gaussian elimination with partial pivoting of the 5 x 5 system m h = b; false if singular.
-__device__ bool solve5(double (*m)[6], double* h) {
+__device__ __forceinline__ double shfl_d(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+// Gaussian elimination with partial pivoting of the 5 x 5 system m h = b by one warp;
+// false if singular. Lane 6 r + j holds entry (r, j) of the augmented matrix [m | b]
+// (lanes 30 and 31 repeat lanes 24 and 25). Every entry goes through the same
+// operations in the same order as in the serial elimination (pivot: the first row of
+// the largest |m[r][c]|; m[r][j] -= (m[r][c] / m[c][c]) m[c][j]), and the back
+// substitution runs in that order on every lane, so h is the serial result. The
+// warp issues each step once for all entries: on GB300 a single thread's FP64
+// instruction takes the pipe as long as a full warp's.
+__device__ bool solve5_warp(double v, int r, int j, double* h) {
   for (int c = 0; c < 5; ++c) {
     int p = c;
-    for (int r = c + 1; r < 5; ++r)
-      if (fabs(m[r][c]) > fabs(m[p][c])) p = r;
-    if (m[p][c] == 0.0) return false;
-    if (p != c)
-      for (int j = 0; j < 6; ++j) {
-        const double t = m[c][j];
-        m[c][j] = m[p][j];
-        m[p][j] = t;
+    double best = shfl_d(v, 6 * c + c);
+    for (int rr = c + 1; rr < 5; ++rr) {
+      const double o = shfl_d(v, 6 * rr + c);
+      if (fabs(o) > fabs(best)) {
+        best = o;
+        p = rr;
       }
-    for (int r = c + 1; r < 5; ++r) {
-      const double f = __ddiv_rn(m[r][c], m[c][c]);
-      for (int j = c; j < 6; ++j) m[r][j] = __dsub_rn(m[r][j], __dmul_rn(f, m[c][j]));
     }
+    if (best == 0.0) return false;
+    const double vc = shfl_d(v, 6 * c + j), vp = shfl_d(v, 6 * p + j);
+    if (r == c) v = vp;
+    else if (r == p) v = vc;
+    const double piv = shfl_d(v, 6 * c + c);
+    const double rc = shfl_d(v, 6 * r + c);
+    const double cj = shfl_d(v, 6 * c + j);
+    if (r > c && j >= c) v = __dsub_rn(v, __dmul_rn(__ddiv_rn(rc, piv), cj));
   }
+  double u[5][6];
+#pragma unroll
+  for (int rr = 0; rr < 5; ++rr)
+#pragma unroll
+    for (int jj = rr; jj < 6; ++jj) u[rr][jj] = shfl_d(v, 6 * rr + jj);
+#pragma unroll
   for (int c = 4; c >= 0; --c) {
-    double acc = m[c][5];
-    for (int j = c + 1; j < 5; ++j) acc = __dsub_rn(acc, __dmul_rn(m[c][j], h[j]));
-    h[c] = __ddiv_rn(acc, m[c][c]);
+    double acc = u[c][5];
+#pragma unroll
+    for (int jj = c + 1; jj < 5; ++jj) acc = __dsub_rn(acc, __dmul_rn(u[c][jj], h[jj]));
+    h[c] = __ddiv_rn(acc, u[c][c]);
   }
   return true;
 }
 
 }  // namespace
 
+// Launch order of the statistics CTAs: stars by decreasing estimated fit cost (its
+// window holds about 4 q n points), so that the longest fits start first rather
+// than trail the launch. Half-octave buckets of q n; the order inside a bucket is
+// free (each star's results do not depend on it). One CTA.
+constexpr int kOrderBuckets = 64;
+__global__ void __launch_bounds__(1024) stats_order_kernel(const StatsArgs a) {
+  __shared__ int cnt[kOrderBuckets], pos[kOrderBuckets];
+  if (threadIdx.x < kOrderBuckets) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  auto bucket = [&](int s) {
+    const double key = a.best[s].f_idx >= 0 ? a.best[s].q * (double)a.stars[s].n_pts : 0.0;
+    const int e = key > 1.0 ? min((int)(2.0 * log2(key)), kOrderBuckets - 1) : 0;
+    return kOrderBuckets - 1 - e;  // the largest first
+  };
+  for (int s = threadIdx.x; s < a.n_stars; s += blockDim.x) atomicAdd(&cnt[bucket(s)], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int k = 0; k < kOrderBuckets; ++k) {
+      pos[k] = run;
+      run += cnt[k];
+    }
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < a.n_stars; s += blockDim.x) a.order[atomicAdd(&pos[bucket(s)], 1)] = s;
+}
+
 __global__ void __launch_bounds__(kThreads, 3) stats_kernel(const StatsArgs a) {
   __shared__ double red[kWarps][kSums];
-  __shared__ double s_part[kThreads][kSums + 1];  // per-thread normal-equation sums
+  __shared__ double s_part[kThreads][kSums + 1];  // per-thread sums of the fit's pass
   __shared__ double s_q[kThreads / 32][kSums];
   __shared__ int s_ramp[kWarps][kRampBuf];
   __shared__ double s_tot[kSums];  // block totals of the last reduction
   __shared__ double s_cur[kSums];  // chi^2, g, A at the accepted parameters (thread 0)
-  __shared__ double s_m[5][6];     // the damped normal equations (thread 0)
   __shared__ double s_x[5];
+  __shared__ double s_lam;         // the damping (thread 0 updates it, warp 0 reads it)
+  __shared__ double s_wsum;        // sum of the window points' weights 1/dy^2
   __shared__ int s_go;
   __shared__ int s_cnt[kThreads];
-  // run partials for the binned residuals and the transit count
+  // run partials for the binned residuals and the transit count (bins as the bit
+  // patterns of their non-negative FP64 indices)
   __shared__ long long s_hbin[kThreads], s_tbin[kThreads], s_kf[kThreads], s_kl[kThreads];
   __shared__ double s_hsum[kThreads], s_tsum[kThreads];
   __shared__ int s_hcnt[kThreads], s_tcnt[kThreads], s_runs[kThreads], s_kd[kThreads];
 
-  const int s = blockIdx.x;
+  const int s = a.order ? a.order[blockIdx.x] : (int)blockIdx.x;
   const int tid = threadIdx.x;
   const StarDev st = a.stars[s];
   const qlp_bls_best bb = a.best[s];
@@ -162,27 +207,33 @@ __global__ void __launch_bounds__(kThreads, 3) stats_kernel(const StatsArgs a) {
   const double* dyv = a.dy + st.pt_off;
   WinRec* wrec = a.wrec + st.pt_off;
   const double period = bb.period;
+  const double r_period = 1.0 / period;
   const double t0p = __dsub_rn(bb.t0, st.t_ref);
   const double q0 = bb.q;
-  const double lim = __dmul_rn(2.0, __dmul_rn(q0, period));
-  const double half0 = __dmul_rn(0.5, __dmul_rn(q0, period));
+  const long long lim_b = mag(__dmul_rn(2.0, __dmul_rn(q0, period)));
+  const long long half0_b = mag(__dmul_rn(0.5, __dmul_rn(q0, period)));
   const int seg = (n + kThreads - 1) / kThreads;
   const int i0 = min(n, tid * seg), i1 = min(n, i0 + seg);
+  // |dt| of point i from the candidate's epoch (t', y, dy in time order; t' >= 0)
+  auto dt0_of = [&](int i, double& pn) {
+    const double u = __dsub_rn(tp[i], t0p);
+    pn = __dmul_rn(period, floor_quot<true>(u, period, r_period));
+    return mag(__dsub_rn(u, pn));
+  };
 
   // 1. the fit window (ordered compaction) and the initial out-of-transit level
   int c = 0;
   double v[4];
   for (int i = 0; i < 4; ++i) v[i] = 0.0;
   for (int i = i0; i < i1; ++i) {
-    const double u = __dsub_rn(tp[i], t0p);
-    const double nn = floor(__dadd_rn(__ddiv_rn(u, period), 0.5));
-    const double dt = fabs(__dsub_rn(u, __dmul_rn(period, nn)));
-    if (dt <= lim) {
+    double pn;
+    const long long db = dt0_of(i, pn);
+    if (db <= lim_b) {
       ++c;
       const double w = __ddiv_rn(1.0, __dmul_rn(dyv[i], dyv[i]));
       v[0] += w * yv[i];
       v[1] += w;
-      if (dt > half0) {
+      if (db > half0_b) {
         v[2] += w * yv[i];
         v[3] += w;
       }
@@ -209,12 +260,17 @@ __global__ void __launch_bounds__(kThreads, 3) stats_kernel(const StatsArgs a) {
   const int nwin = s_go;
   {
     int o = s_cnt[tid];
+    double ws = 0.0;
     for (int i = i0; i < i1; ++i) {
-      const double u = __dsub_rn(tp[i], t0p);
-      const double nn = floor(__dadd_rn(__ddiv_rn(u, period), 0.5));
-      const double dt = fabs(__dsub_rn(u, __dmul_rn(period, nn)));
-      if (dt <= lim) wrec[o++] = WinRec{tp[i], yv[i], __ddiv_rn(1.0, dyv[i]), __dmul_rn(period, nn)};
+      double pn;
+      if (dt0_of(i, pn) <= lim_b) {
+        const double inv = __ddiv_rn(1.0, dyv[i]);
+        const double w = __dmul_rn(inv, inv);  // the (z, z) term of J^T J, as its product
+        wrec[o++] = WinRec{tp[i], pn, yv[i], inv, w, 0.0};
+        ws += w;
+      }
     }
+    block_sums(&ws, 1, red, &s_wsum);
   }
   if (nwin < 6) {
     if (tid == 0) {
@@ -236,10 +292,17 @@ __global__ void __launch_bounds__(kThreads, 3) stats_kernel(const StatsArgs a) {
   // ramp points instead of whenever one lane meets one; its divisions are
   // multiplications by reciprocals taken once per evaluation. The region
   // decisions keep the FP64 expressions of the model's definition.
+  //
+  // On a ramp every derivative is 1/dy times a factor: phi = (c0 sg, -s, r_q a,
+  // r_qin s, 1) with sg = sign(dt), c0 = -delta / t_in, r_q = -delta / (q_in q^2 P)
+  // and r_qin = delta / q_in, so J^T J and J^T r over the ramp points follow from
+  // nine weighted sums of 1, sg, s, a and their products and three of r / dy times
+  // sg, s, a; the factors c0, r_q, r_qin multiply the block totals once.
+  enum { kChi, kG4, kWeF, kWF, kGsg, kGs, kGa, kRw, kRsg, kRsgs, kRsga, kRss, kRsa, kRs, kRaa, kRa, kAcc };
   const int lane = tid & 31, warp_id = tid >> 5;
   int* rl = s_ramp[warp_id];
   auto evaluate = [&]() {  // at s_x: chi^2, J^T r, J^T J into s_tot
-    double sums[kSums];
+    double acc[kAcc];
     double x[5];
     for (int i = 0; i < 5; ++i) x[i] = s_x[i];
     const double d = __dmul_rn(x[2], period);
@@ -249,13 +312,7 @@ __global__ void __launch_bounds__(kThreads, 3) stats_kernel(const StatsArgs a) {
     const double hp = __dmul_rn(0.5, period);
     const double r_tin = 1.0 / t_in;
     const double m_flat = __dsub_rn(x[4], x[1]);  // the model on the flat bottom
-    const double r_q = -x[1] / (x[3] * x[2] * x[2] * period);  // d(-delta s)/dq per unit a
-    const double r_qin = x[1] / x[3];
-    for (int i = 0; i < kSums; ++i) sums[i] = 0.0;
-    // |v| of a double as its bit pattern: for non-negative doubles the order of the
-    // patterns (as integers) is the order of the values, so the region tests below
-    // take the integer pipe instead of the FP64 one
-    auto mag = [](double v) { return __double_as_longlong(v) & 0x7fffffffffffffffll; };
+    for (int i = 0; i < kAcc; ++i) acc[i] = 0.0;
     const long long hp_b = mag(hp), edge_b = mag(edge), half_b = mag(half);
     auto dt_of = [&](const WinRec& pt) {
       const double u = __dsub_rn(pt.t, x[0]);
@@ -270,22 +327,26 @@ __global__ void __launch_bounds__(kThreads, 3) stats_kernel(const StatsArgs a) {
       if (lane < cnt) {
         const WinRec pt = wrec[rl[lane]];
         const double dt = dt_of(pt);
+        const bool neg = __double_as_longlong(dt) < 0;  // sg = -1 (a ramp point has dt != 0)
         const double aa = fabs(dt);
-        const double inv = pt.inv;
         const double sv = __dmul_rn(__dsub_rn(half, aa), r_tin);
-        const double r = __dmul_rn(__dsub_rn(pt.y, __dsub_rn(x[4], __dmul_rn(x[1], sv))), inv);
-        const double sg = dt > 0.0 ? 1.0 : (dt < 0.0 ? -1.0 : 0.0);
-        double j[5];
-        j[0] = -x[1] * sg * r_tin * inv;
-        j[1] = -sv * inv;
-        j[2] = r_q * aa * inv;
-        j[3] = r_qin * sv * inv;
-        j[4] = inv;
-        sums[0] += r * r;
-        for (int k = 0; k < 5; ++k) sums[1 + k] += j[k] * r;
-        int p = 6;
-        for (int k = 0; k < 5; ++k)
-          for (int l = k; l < 5; ++l) sums[p++] += j[k] * j[l];
+        const double e = __dsub_rn(pt.y, __dsub_rn(x[4], __dmul_rn(x[1], sv)));
+        const double ir = pt.w * e;  // r / dy
+        acc[kChi] += ir * e;
+        acc[kG4] += ir;
+        acc[kGsg] += neg ? -ir : ir;
+        acc[kGs] += sv * ir;
+        acc[kGa] += aa * ir;
+        const double ws = pt.w * sv, wa = pt.w * aa;
+        acc[kRw] += pt.w;
+        acc[kRsg] += neg ? -pt.w : pt.w;
+        acc[kRsgs] += neg ? -ws : ws;
+        acc[kRsga] += neg ? -wa : wa;
+        acc[kRss] += ws * sv;
+        acc[kRsa] += ws * aa;
+        acc[kRs] += ws;
+        acc[kRaa] += wa * aa;
+        acc[kRa] += wa;
       }
     };
     int nr = 0;  // queued ramp points of this warp (warp-uniform)
@@ -293,21 +354,17 @@ __global__ void __launch_bounds__(kThreads, 3) stats_kernel(const StatsArgs a) {
       const int wi = w0 + k;
       bool on_ramp = false;
       if (wi < w1) {
-        const WinRec pt = wrec[wi];  // t', y, 1/dy, P n of the starting epoch
+        const WinRec pt = wrec[wi];
         const long long ab = mag(dt_of(pt));
-        const double inv = pt.inv;
         on_ramp = ab > edge_b && ab < half_b;
         if (!on_ramp) {  // flat bottom (s = 1) or outside (s = 0): one path, no divergence
           const bool flat = ab <= edge_b;  // dm/ddelta = -s, dm/dz = 1
-          const double r = __dmul_rn(__dsub_rn(pt.y, flat ? m_flat : x[4]), inv);
-          const double fs = flat ? 1.0 : 0.0;
-          const double ir = inv * r, i2 = inv * inv;
-          sums[0] += r * r;
-          sums[2] -= fs * ir;
-          sums[5] += ir;
-          sums[6 + 5] += fs * i2;   // A11
-          sums[6 + 8] -= fs * i2;   // A14
-          sums[6 + 14] += i2;       // A44
+          const double e = __dsub_rn(pt.y, flat ? m_flat : x[4]);
+          const double we = __dmul_rn(pt.w, e);  // r / dy with r = e / dy
+          acc[kChi] += we * e;                   // r^2
+          acc[kG4] += we;                        // g4 = sum r / dy
+          acc[kWeF] += flat ? we : 0.0;          // -g1 over the flat bottom
+          acc[kWF] += flat ? pt.w : 0.0;         // A11 and -A14 over the flat bottom
         }
       }
       const unsigned mk = __ballot_sync(0xffffffffu, on_ramp);
@@ -327,51 +384,85 @@ __global__ void __launch_bounds__(kThreads, 3) stats_kernel(const StatsArgs a) {
     __syncwarp();
     if (nr > 0) ramp_batch(nr);
     __syncwarp();
-    // block sums through shared memory: each thread of the first kSums x 4 sums one
-    // value over 32 threads, then kSums threads add the 4 quarters in order
-    for (int i = 0; i < kSums; ++i) s_part[tid][i] = sums[i];
+    // block sums through shared memory: each thread of the first kAcc x 4 sums one
+    // value over 32 threads; then every entry of chi^2, g and A adds the 4 quarters
+    // of the sums it takes, in order, and applies the factors
+    for (int i = 0; i < kAcc; ++i) s_part[tid][i] = acc[i];
     __syncthreads();
-    if (tid < kSums * (kThreads / 32)) {
-      const int v = tid % kSums, qq = tid / kSums;
-      double acc = 0.0;
-      for (int r = 0; r < 32; ++r) acc += s_part[32 * qq + r][v];
-      s_q[qq][v] = acc;
+    if (tid < kAcc * (kThreads / 32)) {
+      const int v = tid % kAcc, qq = tid / kAcc;
+      double sum = 0.0;
+      for (int r = 0; r < 32; ++r) sum += s_part[32 * qq + r][v];
+      s_q[qq][v] = sum;
     }
     __syncthreads();
     if (tid < kSums) {
-      double acc = 0.0;
-      for (int qq = 0; qq < kThreads / 32; ++qq) acc += s_q[qq][tid];
-      s_tot[tid] = acc;
+      auto T = [&](int v) {
+        double sum = 0.0;
+        for (int qq = 0; qq < kThreads / 32; ++qq) sum += s_q[qq][v];
+        return sum;
+      };
+      const double c0 = -x[1] * r_tin;
+      const double r_q = -x[1] / (x[3] * x[2] * x[2] * period);  // d(-delta s)/dq per unit a
+      const double r_qin = x[1] / x[3];
+      double v = 0.0;
+      switch (tid) {
+        case 0: v = T(kChi); break;
+        case 1: v = c0 * T(kGsg); break;                 // g0
+        case 2: v = -(T(kWeF) + T(kGs)); break;          // g1
+        case 3: v = r_q * T(kGa); break;                 // g2
+        case 4: v = r_qin * T(kGs); break;               // g3
+        case 5: v = T(kG4); break;                       // g4
+        case 6: v = c0 * c0 * T(kRw); break;             // A00
+        case 7: v = -c0 * T(kRsgs); break;               // A01
+        case 8: v = c0 * r_q * T(kRsga); break;          // A02
+        case 9: v = c0 * r_qin * T(kRsgs); break;        // A03
+        case 10: v = c0 * T(kRsg); break;                // A04
+        case 11: v = T(kRss) + T(kWF); break;            // A11
+        case 12: v = -r_q * T(kRsa); break;              // A12
+        case 13: v = -r_qin * T(kRss); break;            // A13
+        case 14: v = -(T(kRs) + T(kWF)); break;          // A14
+        case 15: v = r_q * r_q * T(kRaa); break;         // A22
+        case 16: v = r_q * r_qin * T(kRsa); break;       // A23
+        case 17: v = r_q * T(kRa); break;                // A24
+        case 18: v = r_qin * r_qin * T(kRss); break;     // A33
+        case 19: v = r_qin * T(kRs); break;              // A34
+        default: v = s_wsum; break;                      // A44: every window point's weight
+      }
+      s_tot[tid] = v;
     }
     __syncthreads();
   };
   double xa[5];
   evaluate();
-  if (tid == 0)
+  if (tid == 0) {
     for (int i = 0; i < kSums; ++i) s_cur[i] = s_tot[i];
+    s_lam = kLam0;
+  }
   for (int i = 0; i < 5; ++i) xa[i] = s_x[i];
-  double lam = kLam0;
+  __syncthreads();  // warp 0 reads s_cur and s_lam
   int it = 0;
   bool conv = false;
   while (it < kMaxIt) {  // block-uniform: s_go decides
     ++it;
-    if (tid == 0) {
-      int p = 6;
-      for (int k = 0; k < 5; ++k)
-        for (int l = k; l < 5; ++l) s_m[k][l] = s_m[l][k] = s_cur[p++];
+    if (tid < 32) {  // warp 0: the damped normal equations and their solution
+      // entry (r, j) of [A + lam diag(max(A_kk, 1e-12 max A_jj)) | g] on lane 6 r + j;
+      // A's upper triangle is stored row by row after chi^2 and g
+      const int r = min(lane / 6, 4), j = lane % 6;
+      const int k = min(r, j), l = max(r, j);
+      double v = j == 5 ? s_cur[1 + r] : s_cur[6 + 5 * k - k * (k - 1) / 2 + (l - k)];
       double dmax = 0.0;
-      for (int k = 0; k < 5; ++k) dmax = fmax(dmax, s_m[k][k]);
-      for (int k = 0; k < 5; ++k) {
-        s_m[k][k] = __dadd_rn(s_m[k][k], __dmul_rn(lam, fmax(s_m[k][k], __dmul_rn(1e-12, dmax))));
-        s_m[k][5] = s_cur[1 + k];
-      }
+      for (int kk = 0; kk < 5; ++kk) dmax = fmax(dmax, s_cur[6 + 5 * kk - kk * (kk - 1) / 2]);
+      if (r == j) v = __dadd_rn(v, __dmul_rn(s_lam, fmax(v, __dmul_rn(1e-12, dmax))));
       double h[5];
-      const bool ok = solve5(s_m, h);
-      if (ok) {
-        for (int k = 0; k < 5; ++k) s_x[k] = __dadd_rn(xa[k], h[k]);
-        clip(s_x);
+      const bool ok = solve5_warp(v, r, j, h);
+      if (tid == 0) {
+        if (ok) {
+          for (int kk = 0; kk < 5; ++kk) s_x[kk] = __dadd_rn(xa[kk], h[kk]);
+          clip(s_x);
+        }
+        s_go = ok ? 1 : 0;
       }
-      s_go = ok ? 1 : 0;
     }
     __syncthreads();
     const bool ok = s_go != 0;
@@ -382,11 +473,11 @@ __global__ void __launch_bounds__(kThreads, 3) stats_kernel(const StatsArgs a) {
         const double rel = s_cur[0] > 0.0 ? (s_cur[0] - s_tot[0]) / s_cur[0] : 0.0;
         for (int i = 0; i < kSums; ++i) s_cur[i] = s_tot[i];
         for (int i = 0; i < 5; ++i) xa[i] = s_x[i];
-        lam /= 10.0;
+        s_lam /= 10.0;
         if (rel < kRtol) { conv = true; act = 1; }
       } else {
-        lam *= 10.0;
-        if (lam > kLamMax) { conv = true; act = 1; }
+        s_lam *= 10.0;
+        if (s_lam > kLamMax) { conv = true; act = 1; }
       }
       for (int i = 0; i < 5; ++i) s_x[i] = xa[i];
       s_go = act;
@@ -399,7 +490,12 @@ __global__ void __launch_bounds__(kThreads, 3) stats_kernel(const StatsArgs a) {
   double x[5];
   for (int i = 0; i < 5; ++i) x[i] = s_x[i];
   const double D = __dmul_rn(x[2], period);
+  const double r_D = 1.0 / D;
   const double hD = __dmul_rn(0.5, D), tD = __dmul_rn(2.0, D);
+  const double t_in = __dmul_rn(x[3], D);
+  const double edge = __dsub_rn(hD, t_in);
+  const double m_flat = __dsub_rn(x[4], x[1]);
+  const long long hD_b = mag(hD), tD_b = mag(tD), edge_b = mag(edge);
   double r2 = 0.0, sb2 = 0.0;
   int n_in = 0, n_before = 0, n_after = 0, runs = 0;
   long long cbin = -1, hbin = -1;
@@ -409,18 +505,31 @@ __global__ void __launch_bounds__(kThreads, 3) stats_kernel(const StatsArgs a) {
   long long kf = 0, kl = 0;  // first and last transit index seen (valid when kd > 0)
   int kd = 0;
   for (int i = i0; i < i1; ++i) {
-    const Model md = model_at(tp[i], x, period);
-    const double r = __dsub_rn(yv[i], md.m);
+    // the model (Sec. 2.2 item 2) at t'_i: nearest transit, distance, trapezoid
+    const double u = __dsub_rn(tp[i], x[0]);
+    const double nn = floor_quot<true>(u, period, r_period);
+    const double dt = __dsub_rn(u, __dmul_rn(period, nn));
+    const long long ab = mag(dt);
+    const bool neg = __double_as_longlong(dt) < 0;  // sign bit (ab > hD_b excludes -0)
+    double m;
+    if (ab <= edge_b) m = m_flat;
+    else if (ab < hD_b) m = __dsub_rn(x[4], __dmul_rn(x[1], __ddiv_rn(__dsub_rn(hD, fabs(dt)), t_in)));
+    else m = x[4];
+    const double r = __dsub_rn(yv[i], m);
     r2 += r * r;
-    n_in += md.a < hD;
-    n_before += (md.dt >= -tD) && (md.dt < -hD);
-    n_after += (md.dt > hD) && (md.dt <= tD);
-    if (md.a <= hD && (kd == 0 || kl != md.k)) {  // indices do not decrease along t
-      if (kd == 0) kf = md.k;
-      kl = md.k;
-      ++kd;
+    n_in += ab < hD_b;
+    n_before += neg && ab > hD_b && ab <= tD_b;
+    n_after += !neg && ab > hD_b && ab <= tD_b;
+    if (ab <= hD_b) {
+      const long long k = (long long)nn;
+      if (kd == 0 || kl != k) {  // indices do not decrease along t
+        if (kd == 0) kf = k;
+        kl = k;
+        ++kd;
+      }
     }
-    const long long b = (long long)floor(__ddiv_rn(tp[i], D));
+    // the residual's time bin floor(t' / D) (t' >= 0: the bit pattern orders and identifies it)
+    const long long b = __double_as_longlong(floor_quot<false>(tp[i], D, r_D));
     if (ccnt > 0 && b != cbin) {  // close the current run
       if (!have_head) { have_head = true; hbin = cbin; hsum = csum; hcnt = ccnt; }
       else { const double mu = csum / ccnt; sb2 += mu * mu; ++runs; }
@@ -516,6 +625,7 @@ __global__ void __launch_bounds__(kThreads, 3) stats_kernel(const StatsArgs a) {
 
 int launch_stats(const StatsArgs& a, void* stream) {
   if (a.n_stars <= 0) return 0;
+  if (a.order) stats_order_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(a);
   stats_kernel<<<a.n_stars, kThreads, 0, (cudaStream_t)stream>>>(a);
   return (int)cudaGetLastError();
 }
