@@ -24,7 +24,9 @@
 // K1x prep_fixed_kernel (1 CTA per exact-path star): weights and the weighted
 // mean in FP64 as the other prep kernels, the integer weights, their exact
 // prefix sums and the per-cell tables (offset of the cell's point, prefix sums at
-// the cell start as a 64-bit group base plus a 32-bit local part).
+// the cell start as a 64-bit group base plus a 32-bit local part; the local part
+// of w d carries a bias of 2^30, so that both local parts are non-negative and
+// widen to 64 bits with a zero high word; the sums take the bias off once).
 // K2x cells_fixed_kernel: persistent; work queue of (star, frequency chunk); the
 // star's table in shared memory; warps take the item's frequencies one at a time.
 // Per frequency the bins are handled 32 at a time (lane = bin): the lanes' S
@@ -44,6 +46,13 @@
 namespace qlp {
 
 constexpr int kRing = 96;  // float2 per warp: blocks 2i and 2i+1, then a copy of block 2i
+constexpr long long kLocBias = 1ll << 30;  // added to the w d local parts of the cell table
+// prefix sums at a cell: the group base plus the local parts, widened from 32 bits with
+// a zero high word (the w d part still carries kLocBias, taken off per sum of edges)
+__device__ __forceinline__ void add_cell(long long& aw, long long& ay, const longlong2& bs, const int2& lc) {
+  aw += bs.x + (long long)(uint32_t)lc.x;
+  ay += bs.y + (long long)(uint32_t)lc.y;
+}
 // cells staged past the sentinel (copies of it): every edge G <= g_end lies before
 // T + 2 D, at most 2 x 255 + 1 cells past the table, so the loop needs no clamp
 constexpr int kPadCells = 544;
@@ -216,7 +225,9 @@ __global__ void __launch_bounds__(512) prep_fixed_kernel(const PrepFixedArgs a) 
     a.dt[st.cell_off + u] = q;
     const longlong2 c = a.ipre[st.cpre_off + f];
     const longlong2 cb = a.ipre[st.cpre_off + first[u & ~31]];
-    a.loc[st.cell_off + u] = make_int2((int)(c.x - cb.x), (int)(c.y - cb.y));
+    // at most 31 points of weights below 2^25 lie between the group start and the
+    // cell: both local parts are below 2^30 in magnitude
+    a.loc[st.cell_off + u] = make_int2((int)(c.x - cb.x), (int)(c.y - cb.y + kLocBias));
     if ((u & 31) == 0) a.base[st.base_off + (u >> 5)] = cb;
   }
 }
@@ -418,22 +429,24 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
           const int v = u + (dq < fr ? 1 : 0);  // past the cell's point if it lies before tau_G
           const int2 lc = *reinterpret_cast<const int2*>(smem + loc_off + (uint32_t)v * st8);
           const longlong2 bs = *reinterpret_cast<const longlong2*>(smem + base_off + (uint32_t)(v >> 5) * st16);
-          if (valid) {
-            aw += bs.x + (long long)lc.x;
-            ay += bs.y + (long long)lc.y;
-          }
+          if (valid) add_cell(aw, ay, bs, lc);
         };
         int c = 0;
-        for (; c + 2 < cnt; c += 2) {
+        for (; c + 4 < cnt; c += 4) {
+          const unsigned long long X1 = X + XS, X2 = X1 + XS, X3 = X2 + XS;
           edge(X, true, false);
-          edge(X + XS, true, false);
-          X += 2ull * XS;
+          edge(X1, true, false);
+          edge(X2, true, false);
+          edge(X3, true, false);
+          X = X3 + XS;
         }
-        if (c + 1 < cnt) {
+        for (; c + 1 < cnt; ++c) {
           edge(X, true, false);
           X += XS;
         }
-        edge(X, G0 + (cnt - 1) * gstep <= g_end, true);
+        const bool last = G0 + (cnt - 1) * gstep <= g_end;
+        edge(X, last, true);
+        ay -= (long long)(cnt - (last ? 0 : 1)) * kLocBias;  // the bias of the edges taken
         bool near = nmin <= 2u * band_q;  // an edge within the guard band of its cell's point
         if (split) {  // warp-uniform: add the other phases of each bin into lanes 0 .. r-1
           for (int q = 1; q < P; ++q) {
@@ -469,8 +482,8 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
               const int v = u + sel;
               const int2 lc = reinterpret_cast<const int2*>(smem + loc_off)[v];
               const longlong2 bs = reinterpret_cast<const longlong2*>(smem + base_off)[v >> 5];
-              aw += bs.x + (long long)lc.x;
-              ay += bs.y + (long long)lc.y;
+              add_cell(aw, ay, bs, lc);
+              ay -= kLocBias;
             }
           }
         }
@@ -597,7 +610,7 @@ __device__ void windowed_item(const FixedArgs& a, const WorkItem& wi, const Star
       for (int i = threadIdx.x; i <= n_loc; i += NW * 32) {  // n_loc + 1 cells
         const int c = lo + i;
         d_dt[i] = c <= nc ? a.dt[st.cell_off + c] : 0xffffffffu;
-        d_loc[i] = c <= nc ? a.loc[st.cell_off + c] : ((c >> 5) == (nc >> 5) ? lnc : make_int2(0, 0));
+        d_loc[i] = c <= nc ? a.loc[st.cell_off + c] : ((c >> 5) == (nc >> 5) ? lnc : make_int2(0, (int)kLocBias));
       }
       for (int i = threadIdx.x; i < (n_loc + 32) / 32; i += NW * 32) {
         const int g = (lo >> 5) + i;
@@ -643,11 +656,9 @@ __device__ void windowed_item(const FixedArgs& a, const WorkItem& wi, const Star
           const int v = ul + (dq < fr ? 1 : 0);
           const int2 lc = *reinterpret_cast<const int2*>(smem + loc_off + (uint32_t)v * st8);
           const longlong2 bs = *reinterpret_cast<const longlong2*>(smem + base_off + (uint32_t)(v >> 5) * st16);
-          if (valid) {
-            aw += bs.x + (long long)lc.x;
-            ay += bs.y + (long long)lc.y;
-          }
+          if (valid) add_cell(aw, ay, bs, lc);
         }
+        ay -= (long long)cntl * kLocBias;
         if (__any_sync(0xffffffffu, near)) {  // rare: redo, near-ties by the exact FP64 fold
           if (near) {
             aw = 0;
@@ -665,8 +676,8 @@ __device__ void windowed_item(const FixedArgs& a, const WorkItem& wi, const Star
               const int v = ul + sel;
               const int2 lc = reinterpret_cast<const int2*>(smem + loc_off)[v];
               const longlong2 bs = reinterpret_cast<const longlong2*>(smem + base_off)[v >> 5];
-              aw += bs.x + (long long)lc.x;
-              ay += bs.y + (long long)lc.y;
+              add_cell(aw, ay, bs, lc);
+              ay -= kLocBias;
             }
           }
         }
@@ -745,7 +756,7 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
       for (int i = threadIdx.x; i < ncp; i += NW * 32) {
         const bool in = i <= nc;
         d_dt[i] = in ? a.dt[st.cell_off + i] : 0xffffffffu;
-        d_loc[i] = in ? a.loc[st.cell_off + i] : ((i >> 5) == (nc >> 5) ? lnc : make_int2(0, 0));
+        d_loc[i] = in ? a.loc[st.cell_off + i] : ((i >> 5) == (nc >> 5) ? lnc : make_int2(0, (int)kLocBias));
       }
       for (int i = threadIdx.x; i < (ncp + 31) / 32; i += NW * 32)
         d_base[i] = i <= (nc >> 5) ? a.base[st.base_off + i] : make_longlong2(fx.w_tot, fx.y_tot);
