@@ -367,34 +367,86 @@ def cnn_throughput(net, x0, labels, peak_tflops):
             "peak_source": "bf16_tflops (burst) of MEASURED_PEAKS.json"}
 
 
-def multi_sector_line(steps: int):
-    """Search throughput on 256 multi-sector stars (1-13 contiguous 27.4-d sectors at
-    200 s, AR(1) red noise; up to ~150 k points per star): the exact cell path with
-    its tables in time windows, and the compensated FP32 cell kernel on the same
-    plan shape, each the mean of `steps` searches timed with CUDA events."""
+def _timed_searches(plan, out, steps, stream):
+    """Mean device time (ms) of `steps` searches after one warm-up (CUDA events)."""
+    import torch
+    plan.search(out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        plan.search(out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if plan.device_status():
+        raise RuntimeError("device flags in a bench search")
+    return e0.elapsed_time(e1) / steps
+
+
+def single_star_line(steps: int):
+    """The single-star case (one 27.4-d sector at 30 min, ~1,250 points, injected 3.7-d
+    box): search and S/N on the device, through the default exact cell path and the
+    per-point path with the FP64 phase, and the public host-buffer call end to end.
+    One star fills a few SMs at most: this line reports latency, not throughput."""
     import torch
     import synth
     from paper_2302_01293_gb300 import qlpbls
-    b = synth.multi_sector(n_stars=256, seed=3, max_sectors=13)
-    res = {"workload": "256 multi-sector stars, 1-13 sectors at 200 s (seed 3)", "points": int(b.offsets[-1])}
+    b = synth.single_star()
+    stream = torch.cuda.current_stream()
+    res = {"workload": "single star, 27.4-d sector at 30 min (synth.single_star)", "points": int(b.offsets[-1])}
+    for name, p in (("exact", qlpbls.Params()),
+                    ("points_fp64_phase", qlpbls.Params(method=qlpbls.METHOD_POINTS,
+                                                        phase_mode=qlpbls.PHASE_FP64))):
+        plan = qlpbls.Plan(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar, p)
+        out = plan.alloc_outputs()
+        ms = _timed_searches(plan, out, steps, stream)
+        res[name] = {"value": plan.work / (ms * 1e-3), "unit": UNIT, "ms": ms, "point_freq": plan.work,
+                     "trial_freqs": plan.n_freq_total}
+        del plan, out
+    times = []
+    for _ in range(max(3, steps)):
+        t0 = time.perf_counter()
+        r = qlpbls.run_host(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar, qlpbls.Params())
+        times.append(time.perf_counter() - t0)
+    res["e2e"] = {"seconds": min(times), "period_found": float(r["best"]["period"][0]),
+                  "period_injected": float(b.period[0]),
+                  "includes": "host plan (grid) + H2D + search + S/N + D2H of best"}
+    return res
+
+
+def multi_sector_line(steps: int, n_stars: int = 1024, n_phase: int = 64):
+    """Search throughput on the multi-sector precision workload: 1,024 stars of 1-13
+    contiguous 27.4-d sectors at 200 s, AR(1) red noise (up to ~150 k points per
+    star), through the exact cell path (tables in time windows where a star's table
+    exceeds shared memory) and the compensated FP32 cell kernel, each the mean of
+    `steps` searches (CUDA events); and the per-point path with each phase reduction
+    (FP64, double-float, FP32) on the first n_phase stars, one search each. The
+    agreement of each mode with the FP64 oracle is the precision tests' part."""
+    import torch
+    import synth
+    from paper_2302_01293_gb300 import qlpbls
+    b = synth.multi_sector(n_stars=n_stars, seed=3, max_sectors=13)
+    res = {"workload": f"{n_stars} multi-sector stars, 1-13 sectors at 200 s (seed 3)",
+           "points": int(b.offsets[-1])}
     stream = torch.cuda.current_stream()
     for name, p in (("exact", qlpbls.Params()), ("compensated", qlpbls.Params(sum_mode=qlpbls.SUM_COMP))):
         plan = qlpbls.Plan(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar, p)
         out = plan.alloc_outputs()
-        plan.search(out)  # warm-up
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(steps):
-            plan.search(out)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
-        if plan.device_status():
-            raise RuntimeError("device flags in the multi-sector search")
+        ms = _timed_searches(plan, out, steps, stream)
         res[name] = {"value": plan.work / (ms * 1e-3), "unit": UNIT, "ms": ms,
                      "point_freq": plan.work, "windowed_stars": plan.n_windowed,
                      "exact_path_stars": plan.n_exact_stars}
+        del plan, out
+    sub = b.subset(range(min(n_phase, n_stars)))
+    res["points_phase_modes"] = {"stars": sub.n_stars, "points": int(sub.offsets[-1])}
+    for name, mode in (("fp64", qlpbls.PHASE_FP64), ("double_float", qlpbls.PHASE_DF),
+                       ("fp32", qlpbls.PHASE_FP32)):
+        plan = qlpbls.Plan(sub.offsets, sub.t, sub.y, sub.dy, sub.rho, sub.rstar,
+                           qlpbls.Params(method=qlpbls.METHOD_POINTS, phase_mode=mode))
+        out = plan.alloc_outputs()
+        ms = _timed_searches(plan, out, 1, stream)
+        res["points_phase_modes"][name] = {"value": plan.work / (ms * 1e-3), "unit": UNIT, "ms": ms,
+                                           "point_freq": plan.work}
         del plan, out
     return res
 
@@ -608,8 +660,10 @@ def main():
             cpu = cpu_baseline(batch, args.cpu_sample_stars)
         learned_line = None
         multi_line = None
+        single_line = None
         if not args.no_multi and world == 1:
-            multi_line = multi_sector_line(3)
+            single_line = single_star_line(10)
+            multi_line = multi_sector_line(2)
         if not args.no_learned and world == 1:
             learned_line = learned_comparison(args)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -639,6 +693,7 @@ def main():
                                               + 2 * (plan.n_exact_stars > 0)),
                 "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "candidate_stats": cand_stats,
+                "single_star": single_line,
                 "multi_sector": multi_line,
                 "learned": learned_line}
         print(json.dumps(line), flush=True)
