@@ -63,6 +63,8 @@ def _args():
     ap.add_argument("--sector-scale-stars", type=int, default=32768)
     ap.add_argument("--tune-sample", type=int, default=512)
     ap.add_argument("--no-tune", action="store_true", help="library defaults instead of the autotuner")
+    ap.add_argument("--case", default=None, choices=["fixed", "stats", "conv"],
+                    help="run one small case of a kernel (for a profiler capture) and exit")
     ap.add_argument("--method", type=int, default=0, choices=[0, 1, 2],
                     help="0 per star the cheaper path, 1 fold every point, 2 cell path where possible")
     return ap.parse_args()
@@ -451,6 +453,40 @@ def multi_sector_line(steps: int, n_stars: int = 1024, n_phase: int = 64):
     return res
 
 
+def profile_case(which: str):
+    """One small launch of a kernel for a profiler capture, checked for device flags:
+    fixed: the exact search (and S/N) of 1,024 uneven single-sector stars; stats: the
+    candidate statistics of 512 such stars after their search; conv: the tensor-core
+    convolution (64 -> 64 channels, kernel 9) on 128 x 4,096 x 64 BF16 activations."""
+    import torch
+    import synth
+    from paper_2302_01293_gb300 import qlpbls
+    torch.cuda.set_device(0)
+    if which in ("fixed", "stats"):
+        b = synth.uneven_single_sector(n_stars=1024 if which == "fixed" else 512, seed=2)
+        plan = qlpbls.Plan(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar)
+        out = plan.search()
+        plan.snr(out)
+        if which == "stats":
+            plan.candidate_stats(out)
+        torch.cuda.synchronize()
+        if plan.device_status():
+            raise RuntimeError("device flags")
+    else:
+        g = torch.Generator(device="cpu").manual_seed(5)
+        x = torch.randn(128, 4096, 64, generator=g).to(torch.bfloat16).cuda()
+        w = (torch.randn(9, 64, 64, generator=g) * 0.05).cuda()
+        bias = torch.zeros(64).cuda()
+        err = torch.zeros(1, dtype=torch.int32, device="cuda")
+        wp = qlpbls.pack_w64(w)
+        y = qlpbls.conv64(x, wp, bias, err=err)
+        qlpbls.conv64(x, wp, bias, out=y, err=err)
+        torch.cuda.synchronize()
+        if int(err.item()):
+            raise RuntimeError("device flags")
+    print("ok", which)
+
+
 def cpu_baseline(batch, n_sample: int):
     """Time the FP64 oracle (plan + BLS + S/N) on the first n_sample stars, all cores."""
     import multiprocessing as mp
@@ -500,6 +536,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.case:
+        profile_case(args.case)
         return
 
     import torch

@@ -543,7 +543,7 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
       d.cell_off = ncell;
       d.base_off = nbase;
       d.cpre_off = ncpre;
-      ncell += h.n_cells + 1;
+      ncell += (h.n_cells + 1 + 3) & ~3;  // every star's table starts at a 16-byte boundary
       nbase += (h.n_cells + 1 + 31) / 32;
       ncpre += d.n_pts + 1;
       if (d.method == kMethodFixed) {

@@ -28,7 +28,8 @@
 // of w d carries a bias of 2^30, so that both local parts are non-negative and
 // widen to 64 bits with a zero high word; the sums take the bias off once).
 // K2x cells_fixed_kernel: persistent; work queue of (star, frequency chunk); the
-// star's table in shared memory; warps take the item's frequencies one at a time.
+// star's table in shared memory (three contiguous arrays, staged by bulk
+// asynchronous copies on an mbarrier); warps take the item's frequencies one at a time.
 // Per frequency the bins are handled 32 at a time (lane = bin): the lanes' S
 // values become U, the exact differences H[x] = U[x + 1] - U[x] are scaled to FP32
 // (w, w d) pairs and written to a per-warp ring of two 32-bin blocks (plus a copy
@@ -714,13 +715,31 @@ __device__ void windowed_item(const FixedArgs& a, const WorkItem& wi, const Star
   }
 }
 
+// Bulk asynchronous copy global -> shared of `bytes` (a multiple of 16; both addresses
+// 16-byte aligned), completing on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          (uint32_t)__cvta_generic_to_shared(dst)),
+      "l"(src), "r"(bytes), "r"((uint32_t)__cvta_generic_to_shared(bar))
+      : "memory");
+}
+constexpr uint32_t kCopyWaitLimit = 1u << 24;  // polls of a table copy (each ends after ~1 us at most)
+
 template <int NW>
 __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   __shared__ int s_item, s_star, s_next;
-  if (threadIdx.x == 0) s_star = -1;
+  __shared__ __align__(8) uint64_t s_tbar;  // completion of a table's bulk copies
+  uint32_t tphase = 0;                       // its phase (thread 0)
+  if (threadIdx.x == 0) {
+    s_star = -1;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&s_tbar))
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   // element strides as run-time values, so that the table addresses are formed by
   // integer multiply-adds rather than by the (busier) integer logic pipe
   const uint32_t st4 = a.stride4, st8 = 2u * a.stride4, st16 = 4u * a.stride4;
@@ -752,16 +771,47 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
       uint32_t* d_dt = reinterpret_cast<uint32_t*>(smem);
       int2* d_loc = reinterpret_cast<int2*>(smem + loc_off);
       longlong2* d_base = reinterpret_cast<longlong2*>(smem + base_off);
+      // cells [0, nb4) and groups [0, ng) by bulk copies (the table starts at a 16-byte
+      // boundary: cell_off is a multiple of 4), the rest of the table and the padding by
+      // the threads; the two parts do not overlap
+      const int nb4 = (nc + 1) & ~3, ng = (nc >> 5) + 1;
+      if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the last item's reads
+        const uint32_t bytes = (uint32_t)nb4 * 12u + (uint32_t)ng * 16u;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(&s_tbar)), "r"(bytes)
+                     : "memory");
+        if (nb4 > 0) {
+          bulk_g2s(d_dt, a.dt + st.cell_off, (uint32_t)nb4 * 4u, &s_tbar);
+          bulk_g2s(d_loc, a.loc + st.cell_off, (uint32_t)nb4 * 8u, &s_tbar);
+        }
+        bulk_g2s(d_base, a.base + st.base_off, (uint32_t)ng * 16u, &s_tbar);
+      }
       const int2 lnc = a.loc[st.cell_off + nc];
-      for (int i = threadIdx.x; i < ncp; i += NW * 32) {
+      for (int i = nb4 + (int)threadIdx.x; i < ncp; i += NW * 32) {
         const bool in = i <= nc;
         d_dt[i] = in ? a.dt[st.cell_off + i] : 0xffffffffu;
         d_loc[i] = in ? a.loc[st.cell_off + i] : ((i >> 5) == (nc >> 5) ? lnc : make_int2(0, (int)kLocBias));
       }
-      for (int i = threadIdx.x; i < (ncp + 31) / 32; i += NW * 32)
-        d_base[i] = i <= (nc >> 5) ? a.base[st.base_off + i] : make_longlong2(fx.w_tot, fx.y_tot);
+      for (int i = ng + (int)threadIdx.x; i < (ncp + 31) / 32; i += NW * 32)
+        d_base[i] = make_longlong2(fx.w_tot, fx.y_tot);
+      if (threadIdx.x == 0) {  // bounded wait for the copies
+        bool ok = false;
+        for (uint32_t k = 0; k < kCopyWaitLimit && !ok; ++k) {
+          uint32_t done;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+              "selp.u32 %0, 1, 0, p;\n\t}"
+              : "=r"(done)
+              : "r"((uint32_t)__cvta_generic_to_shared(&s_tbar)), "r"(tphase)
+              : "memory");
+          ok = done != 0;
+        }
+        if (!ok) atomicOr(a.err, kErrCopyWait);
+        tphase ^= 1u;
+        s_star = ok ? wi.star : -1;
+      }
       __syncthreads();
-      if (threadIdx.x == 0) s_star = wi.star;
     }
     const float scw = __int_as_float((127 - fx.kw) << 23);  // 2^-kw (|kw| <= 100)
     const float scy = __int_as_float((127 - fx.ky) << 23);

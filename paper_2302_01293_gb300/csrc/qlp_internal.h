@@ -237,6 +237,8 @@ static_assert(kErrQueueBound == QLP_DEVERR_QUEUE && kErrNbins == QLP_DEVERR_NBIN
 constexpr int32_t kErrSturges = 4;      // more S/N bins than the kernel supports
 constexpr int32_t kErrSelect = 8;       // median selection failed to converge
 constexpr int32_t kErrMmaWait = 16;     // a tensor-core completion wait hit its bound
+constexpr int32_t kErrCopyWait = 32;    // a bulk copy into shared memory did not complete in its bound
+static_assert(kErrCopyWait == QLP_DEVERR_COPY, "device error bits");
 
 // launchers (bls_kernels.cu / snr_kernel.cu); return cudaError_t as int
 int launch_prep(const PrepArgs& a, void* stream);
