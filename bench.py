@@ -682,9 +682,9 @@ def main():
         traffic = 423.0e6 * plan.n_points / 10638874
 
     if kernel_id == 2 and default_batch:
-        # cells_fixed_kernel: ncu capture on 1,024 stars of this workload (704.6 MB read +
-        # 222.2 MB written), scaled by points (tables, records and outputs grow with them)
-        traffic = 926.9e6 * plan.n_points / 10638874
+        # cells_fixed_kernel: ncu capture on 1,024 stars of this workload (703.1 MB read +
+        # 220.6 MB written), scaled by points (tables, records and outputs grow with them)
+        traffic = 923.7e6 * plan.n_points / 10638874
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "TFLOP/s",
                 "frac": achieved / peak_ops, "traffic": traffic, "kernel": kernel,
                 "algorithmic": unit_note,
