@@ -63,7 +63,7 @@ def _args():
     ap.add_argument("--sector-scale-stars", type=int, default=32768)
     ap.add_argument("--tune-sample", type=int, default=512)
     ap.add_argument("--no-tune", action="store_true", help="library defaults instead of the autotuner")
-    ap.add_argument("--case", default=None, choices=["fixed", "stats", "conv"],
+    ap.add_argument("--case", default=None, choices=["fixed", "stats", "conv", "train"],
                     help="run one small case of a kernel (for a profiler capture) and exit")
     ap.add_argument("--method", type=int, default=0, choices=[0, 1, 2],
                     help="0 per star the cheaper path, 1 fold every point, 2 cell path where possible")
@@ -457,7 +457,8 @@ def profile_case(which: str):
     """One small launch of a kernel for a profiler capture, checked for device flags:
     fixed: the exact search (and S/N) of 1,024 uneven single-sector stars; stats: the
     candidate statistics of 512 such stars after their search; conv: the tensor-core
-    convolution (64 -> 64 channels, kernel 9) on 128 x 4,096 x 64 BF16 activations."""
+    convolution (64 -> 64 channels, kernel 9) on 128 x 4,096 x 64 BF16 activations;
+    train: three training steps of the proposal network on a batch of 128 x 4,096 bins."""
     import torch
     import synth
     from paper_2302_01293_gb300 import qlpbls
@@ -472,6 +473,19 @@ def profile_case(which: str):
         torch.cuda.synchronize()
         if plan.device_status():
             raise RuntimeError("device flags")
+    elif which == "train":
+        net = qlpbls.CNN(max_batch=128, length=4096, seed=0)
+        g = torch.Generator(device="cpu").manual_seed(5)
+        x0 = torch.zeros(128, 4096, qlpbls.CNN_IN_CH, dtype=torch.bfloat16, device="cuda")
+        x0[..., 0] = torch.randn(128, 4096, generator=g).to(torch.bfloat16).cuda()
+        x0[..., 1] = 1
+        lab = torch.zeros(128, 4096, device="cuda")
+        lab[:, 2000:2003] = 1.0
+        for _ in range(3):
+            net.train_step(x0, lab, 16.0, 1e-4)
+        torch.cuda.synchronize()
+        if not np.isfinite(net.loss()):
+            raise RuntimeError("non-finite loss")
     else:
         g = torch.Generator(device="cpu").manual_seed(5)
         x = torch.randn(128, 4096, 64, generator=g).to(torch.bfloat16).cuda()
