@@ -355,42 +355,63 @@ int launch_pack_w64(const float* w, void* out, int transpose, void* stream) {
 // two-stage reductions (per-CTA partial sums, then a sum over CTAs); BCE with
 // logits; Adam with FP32 master weights.
 
-// x0 [B][L][CI] BF16 -> a1 [B][L][64] BF16 = relu(b1 + conv(x0, W1)), W1 [9][64][CI]
-__global__ void __launch_bounds__(128) conv_in_kernel(const __nv_bfloat16* x0, const float* w1,
-                                                      const float* b1, __nv_bfloat16* a1, int batch,
-                                                      int len) {
+// The small layers work on tiles of 128 positions of one sample (len is a multiple
+// of 128): a CTA stages the tile's rows with the 4 halo rows on each side (zeros
+// outside [0, len)) in shared memory and walks its tiles; 4 groups of 64 threads
+// each take 32 consecutive positions, thread = channel, so that a position's 64
+// channels are one coalesced 128-byte row and every row value a thread needs is
+// read once into a sliding window of 9 rows held in registers (the loop over the
+// group's 32 positions is unrolled, so the window's slots are fixed registers).
+constexpr int kSmTile = 128;                      // positions per tile
+constexpr int kSmRows = kSmTile + kTaps - 1;      // staged rows per tile
+constexpr int kSmGroupPos = 32;                   // positions per thread group
+constexpr int kSmThreads = 256;                   // 4 groups x 64 channels
+
+// Tiles of the small-layer kernels and the CTAs that walk them.
+__host__ __device__ __forceinline__ int small_tiles(int batch, int len) { return batch * (len / kSmTile); }
+
+// x0 [B][L][CI] BF16 -> a1 [B][L][64] BF16 = relu(b1 + conv(x0, W1)), W1 [9][64][CI]:
+// thread = output channel co, its 9 x CI weights in registers.
+__global__ void __launch_bounds__(kSmThreads) conv_in_kernel(const __nv_bfloat16* x0, const float* w1,
+                                                             const float* b1, __nv_bfloat16* a1, int batch,
+                                                             int len) {
   constexpr int CI = QLP_CNN_IN_CH;
-  __shared__ float sw[kTaps * kC * CI];
-  __shared__ float sb[kC];
-  for (int i = threadIdx.x; i < kTaps * kC * CI; i += blockDim.x) sw[i] = w1[i];
-  for (int i = threadIdx.x; i < kC; i += blockDim.x) sb[i] = b1[i];
-  __syncthreads();
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= batch * len) return;
-  const int b = p / len, l = p - b * len;
-  float xv[kTaps][CI];
+  __shared__ float s_x[kSmRows][CI];
+  const int co = threadIdx.x & (kC - 1), g = threadIdx.x >> 6;
+  float w[kTaps][CI];
 #pragma unroll
-  for (int kk = 0; kk < kTaps; ++kk) {
-    const int ll = l + kk - kTaps / 2;
-    const bool in = ll >= 0 && ll < len;
+  for (int kk = 0; kk < kTaps; ++kk)
 #pragma unroll
-    for (int ci = 0; ci < CI; ++ci)
-      xv[kk][ci] = in ? __bfloat162float(x0[((size_t)b * len + ll) * CI + ci]) : 0.f;
-  }
-  __nv_bfloat16* out = a1 + (size_t)p * kC;
-  for (int c0 = 0; c0 < kC; c0 += 8) {
-    __align__(16) __nv_bfloat16 o[8];
+    for (int ci = 0; ci < CI; ++ci) w[kk][ci] = w1[(kk * kC + co) * CI + ci];
+  const float bias = b1[co];
+  const int tps = len / kSmTile, n_tiles = batch * tps;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int b = t / tps, l0 = (t - b * tps) * kSmTile;
+    __syncthreads();  // the previous tile's rows are no longer read
+    for (int i = threadIdx.x; i < kSmRows * CI; i += blockDim.x) {
+      const int r = i / CI, ci = i - r * CI;
+      const int l = l0 - kTaps / 2 + r;
+      s_x[r][ci] = (l >= 0 && l < len) ? __bfloat162float(x0[((size_t)b * len + l) * CI + ci]) : 0.f;
+    }
+    __syncthreads();
+    const int q0 = g * kSmGroupPos;
+    float win[kTaps][CI];  // win[(q + kk) % 9] = staged row q0 + q + kk
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int co = c0 + e;
-      float z = sb[co];
+    for (int r = 0; r < kTaps - 1; ++r)
+#pragma unroll
+      for (int ci = 0; ci < CI; ++ci) win[r][ci] = s_x[q0 + r][ci];
+    __nv_bfloat16* out = a1 + ((size_t)b * len + l0 + q0) * kC + co;
+#pragma unroll
+    for (int q = 0; q < kSmGroupPos; ++q) {
+#pragma unroll
+      for (int ci = 0; ci < CI; ++ci) win[(q + kTaps - 1) % kTaps][ci] = s_x[q0 + q + kTaps - 1][ci];
+      float z = bias;
 #pragma unroll
       for (int kk = 0; kk < kTaps; ++kk)
 #pragma unroll
-        for (int ci = 0; ci < CI; ++ci) z += sw[(kk * kC + co) * CI + ci] * xv[kk][ci];
-      o[e] = __float2bfloat16_rn(fmaxf(z, 0.f));
+        for (int ci = 0; ci < CI; ++ci) z = fmaf(w[kk][ci], win[(q + kk) % kTaps][ci], z);
+      out[(size_t)q * kC] = __float2bfloat16_rn(fmaxf(z, 0.f));
     }
-    *reinterpret_cast<uint4*>(out + c0) = *reinterpret_cast<const uint4*>(o);
   }
 }
 
@@ -400,30 +421,60 @@ __device__ __forceinline__ void bf16x8_to_f32(uint4 u, float* f) {
   for (int e = 0; e < 8; ++e) f[e] = __bfloat162float(h[e]);
 }
 
-// a5 [B][L][64] BF16 -> logit [B][L] FP32 = b6 + conv(a5, W6), W6 [9][64]
-__global__ void __launch_bounds__(128) conv_out_kernel(const __nv_bfloat16* a5, const float* w6,
+// a5 [B][L][64] BF16 -> logit [B][L] FP32 = b6 + conv(a5, W6), W6 [9][64]. Per staged
+// row r and tap kk the CTA forms P[r][kk] = sum_ci W6[kk][ci] a5[r][ci] (thread = row,
+// the row read once, the weights broadcast from shared memory), then logit[q] =
+// b6 + sum_kk P[q + kk][kk]. Rows are 144 bytes apart in shared memory, so that a
+// warp's 16-byte row reads fall in distinct bank groups.
+constexpr int kOutRowB = 144;
+__global__ void __launch_bounds__(160) conv_out_kernel(const __nv_bfloat16* a5, const float* w6,
                                                        const float* b6, float* logit, int batch, int len) {
-  __shared__ float sw[kTaps * kC];
-  for (int i = threadIdx.x; i < kTaps * kC; i += blockDim.x) sw[i] = w6[i];
-  __syncthreads();
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= batch * len) return;
-  const int b = p / len, l = p - b * len;
-  float z = b6[0];
-#pragma unroll 1
-  for (int kk = 0; kk < kTaps; ++kk) {
-    const int ll = l + kk - kTaps / 2;
-    if (ll < 0 || ll >= len) continue;
-    const uint4* row = reinterpret_cast<const uint4*>(a5 + ((size_t)b * len + ll) * kC);
+  __shared__ __align__(16) unsigned char s_a[kSmRows * kOutRowB];
+  __shared__ __align__(16) float s_w[kTaps * kC];
+  __shared__ float s_p[kSmRows][kTaps + 1];
+  for (int i = threadIdx.x; i < kTaps * kC; i += blockDim.x) s_w[i] = w6[i];
+  const float bias = b6[0];
+  const int tps = len / kSmTile, n_tiles = batch * tps;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int b = t / tps, l0 = (t - b * tps) * kSmTile;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSmRows * (kC / 8); i += blockDim.x) {
+      const int r = i >> 3, c = i & 7;
+      const int l = l0 - kTaps / 2 + r;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (l >= 0 && l < len) v = reinterpret_cast<const uint4*>(a5 + ((size_t)b * len + l) * kC)[c];
+      *reinterpret_cast<uint4*>(s_a + r * kOutRowB + c * 16) = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kSmRows) {
+      const int r = threadIdx.x;
+      float acc[kTaps];
 #pragma unroll
-    for (int q = 0; q < kC / 8; ++q) {
-      float f[8];
-      bf16x8_to_f32(row[q], f);
+      for (int kk = 0; kk < kTaps; ++kk) acc[kk] = 0.f;
 #pragma unroll
-      for (int e = 0; e < 8; ++e) z += sw[kk * kC + 8 * q + e] * f[e];
+      for (int c = 0; c < kC / 8; ++c) {
+        float f[8];
+        bf16x8_to_f32(*reinterpret_cast<const uint4*>(s_a + r * kOutRowB + c * 16), f);
+#pragma unroll
+        for (int kk = 0; kk < kTaps; ++kk) {
+          const float4 wa = *reinterpret_cast<const float4*>(s_w + kk * kC + 8 * c);
+          const float4 wb = *reinterpret_cast<const float4*>(s_w + kk * kC + 8 * c + 4);
+          acc[kk] = fmaf(wa.x, f[0], fmaf(wa.y, f[1], fmaf(wa.z, f[2], fmaf(wa.w, f[3], acc[kk]))));
+          acc[kk] = fmaf(wb.x, f[4], fmaf(wb.y, f[5], fmaf(wb.z, f[6], fmaf(wb.w, f[7], acc[kk]))));
+        }
+      }
+#pragma unroll
+      for (int kk = 0; kk < kTaps; ++kk) s_p[r][kk] = acc[kk];
+    }
+    __syncthreads();
+    if (threadIdx.x < kSmTile) {
+      const int q = threadIdx.x;
+      float z = bias;
+#pragma unroll
+      for (int kk = 0; kk < kTaps; ++kk) z += s_p[q + kk][kk];
+      logit[(size_t)b * len + l0 + q] = z;
     }
   }
-  logit[p] = z;
 }
 
 // Weighted BCE with logits, mean over B L: loss_i = pw y softplus(-z) + (1-y) softplus(z);
@@ -451,37 +502,48 @@ __global__ void __launch_bounds__(256) bce_kernel(const float* logit, const floa
   }
 }
 
-// da5[b][l][ci] = (a5 > 0) * sum_kk W6[kk][ci] dlogit[b][l - kk + 4]
-__global__ void __launch_bounds__(128) conv_out_bwd_kernel(const float* dlogit, const float* w6,
+// da5[b][l][ci] = (a5 > 0) * sum_kk W6[kk][ci] dlogit[b][l - kk + 4]: thread = (8-channel
+// chunk, run of 8 consecutive positions of one sample), its 9 x 8 weights and the 16
+// logit gradients around the run in registers; 8 threads cover a position's row.
+constexpr int kBwdRun = 8;
+__global__ void __launch_bounds__(256) conv_out_bwd_kernel(const float* dlogit, const float* w6,
                                                            const __nv_bfloat16* a5, __nv_bfloat16* da5,
                                                            int batch, int len) {
-  __shared__ float sw[kTaps * kC];
-  for (int i = threadIdx.x; i < kTaps * kC; i += blockDim.x) sw[i] = w6[i];
-  __syncthreads();
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= batch * len) return;
-  const int b = p / len, l = p - b * len;
-  float g[kTaps];
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)batch * len / kBwdRun * (kC / 8)) return;
+  const int c = (int)(i & 7);
+  const size_t p0 = (i >> 3) * kBwdRun;  // len is a multiple of kBwdRun: a run stays in one sample
+  const int b = (int)(p0 / len), l0 = (int)(p0 - (size_t)b * len);
+  float w[kTaps][8];
 #pragma unroll
   for (int kk = 0; kk < kTaps; ++kk) {
-    const int ll = l - kk + kTaps / 2;
-    g[kk] = (ll >= 0 && ll < len) ? dlogit[(size_t)b * len + ll] : 0.f;
+    const float4 wa = *reinterpret_cast<const float4*>(w6 + kk * kC + 8 * c);
+    const float4 wb = *reinterpret_cast<const float4*>(w6 + kk * kC + 8 * c + 4);
+    w[kk][0] = wa.x; w[kk][1] = wa.y; w[kk][2] = wa.z; w[kk][3] = wa.w;
+    w[kk][4] = wb.x; w[kk][5] = wb.y; w[kk][6] = wb.z; w[kk][7] = wb.w;
   }
-  const uint4* arow = reinterpret_cast<const uint4*>(a5 + (size_t)p * kC);
-  uint4* drow = reinterpret_cast<uint4*>(da5 + (size_t)p * kC);
+  float d[kBwdRun + kTaps - 1];  // d[j] = dlogit[l0 - 4 + j], zero outside the sample
 #pragma unroll
-  for (int q = 0; q < kC / 8; ++q) {
+  for (int j = 0; j < kBwdRun + kTaps - 1; ++j) {
+    const int ll = l0 - kTaps / 2 + j;
+    d[j] = (ll >= 0 && ll < len) ? dlogit[(size_t)b * len + ll] : 0.f;
+  }
+#pragma unroll
+  for (int j = 0; j < kBwdRun; ++j) {
+    float s[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) s[e] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < kTaps; ++kk)  // dlogit[l - kk + 4] with l = l0 + j
+#pragma unroll
+      for (int e = 0; e < 8; ++e) s[e] = fmaf(w[kk][e], d[j + kTaps - 1 - kk], s[e]);
+    const size_t p = p0 + j;
     float av[8];
-    bf16x8_to_f32(arow[q], av);
+    bf16x8_to_f32(reinterpret_cast<const uint4*>(a5 + p * kC)[c], av);
     __align__(16) __nv_bfloat16 o[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      float s = 0.f;
-#pragma unroll
-      for (int kk = 0; kk < kTaps; ++kk) s += sw[kk * kC + 8 * q + e] * g[kk];
-      o[e] = __float2bfloat16_rn(av[e] > 0.f ? s : 0.f);
-    }
-    drow[q] = *reinterpret_cast<const uint4*>(o);
+    for (int e = 0; e < 8; ++e) o[e] = __float2bfloat16_rn(av[e] > 0.f ? s[e] : 0.f);
+    reinterpret_cast<uint4*>(da5 + p * kC)[c] = *reinterpret_cast<const uint4*>(o);
   }
 }
 
@@ -501,109 +563,117 @@ constexpr int kDwOut = kTaps * kC * kC + kC;
 // single descriptor (planes 8..15 = planes 0..7 moved by one row). Pairs (0,1),
 // (2,3), (4,5), (6,7), (8,-): 5 x 64 TMEM columns; the unused half of the last
 // pair reads staged rows and is discarded.
+// Warp roles: warp 0 loads each tile with TMA (24 boxes of 8 channels x 136 rows:
+// dY from the tile's row - 4 and - 5, X from its row; zeros outside the sample)
+// into a ring of 4 buffers; one thread of warp 1 issues the tile's 40 MMAs and
+// commits them to the buffer's empty barrier; warps 2-3 add the tile's own dY
+// rows into the bias gradient (thread = output channel) and arrive on the same
+// barrier. After the last tile all four warps read the accumulators (lane
+// quarter = warp) into the CTA's partial sums.
 constexpr int kWgTile = 128;                     // positions per tile (K)
-constexpr int kWgRowsA = kWgTile + kTaps - 1;    // 136 staged dY rows per plane
-constexpr int kWgPlaneA = kWgRowsA * 16;         // 2,176 B
-constexpr int kWgABytes = 2 * kPlanes * kWgPlaneA;  // 16 planes: 34,816 B
-constexpr int kWgPlaneB = kWgTile * 16;          // 2,048 B
-constexpr int kWgBBytes = kPlanes * kWgPlaneB;   // 16,384 B
-constexpr int kWgStage = kWgABytes + kWgBBytes;  // 51,200 B per stage
+constexpr int kWgRows = kWgTile + kTaps - 1;     // 136 staged rows per plane (dY and X)
+constexpr int kWgPlane = kWgRows * 16;           // 2,176 B
+constexpr int kWgABytes = 2 * kPlanes * kWgPlane;  // 16 dY planes: 34,816 B
+constexpr int kWgBBytes = kPlanes * kWgPlane;    // 8 X planes: 17,408 B
+constexpr int kWgStage = kWgABytes + kWgBBytes;  // 52,224 B per stage
+constexpr int kWgStages = 4;
 constexpr int kWgPairs = 5;
-constexpr int kWgSmem = 120 * 1024;              // two stages; > half an SM: one CTA per SM (512 TMEM columns)
+constexpr int kWgThreads = 128;
+constexpr int kWgSmem = kWgStages * kWgStage;    // 208,896 B: one CTA per SM (512 TMEM columns)
 
-__device__ __forceinline__ void stage_wgrad(unsigned char* buf, const __nv_bfloat16* dy, const __nv_bfloat16* x,
-                                            int b, int q0, int len) {
-  // dY planes j < 8: row r <- dY[q0 - 4 + r]; planes 8..15: row r <- dY[q0 - 5 + r]; X planes: row r <- X[q0 + r]
-  for (int i = threadIdx.x; i < 2 * kPlanes * kWgRowsA; i += blockDim.x) {
-    const int j = i / kWgRowsA, r = i - j * kWgRowsA;
-    const int l = q0 - (kTaps / 2) - (j >= kPlanes ? 1 : 0) + r;
-    const bool in = l >= 0 && l < len;
-    const __nv_bfloat16* src = dy + ((size_t)b * len + (in ? l : 0)) * kC + 8 * (j & (kPlanes - 1));
-    cp_async16(buf + j * kWgPlaneA + r * 16, src, in ? 16u : 0u);
-  }
-  unsigned char* bb = buf + kWgABytes;
-  for (int i = threadIdx.x; i < kPlanes * kWgTile; i += blockDim.x) {
-    const int j = i / kWgTile, r = i - j * kWgTile;
-    cp_async16(bb + j * kWgPlaneB + r * 16, x + ((size_t)b * len + q0 + r) * kC + 8 * j, 16u);
-  }
-}
-
-__global__ void __launch_bounds__(128) wgrad64_tc_kernel(const __nv_bfloat16* dy, const __nv_bfloat16* x,
-                                                         float* partial, int32_t* err, int batch, int len) {
+__global__ void __launch_bounds__(kWgThreads, 1)
+    wgrad64_tc_kernel(const __grid_constant__ CUtensorMap dymap, const __grid_constant__ CUtensorMap xmap,
+                      float* partial, int32_t* err, int batch, int len) {
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t full[kWgStages], empty[kWgStages], fin;
   __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int tiles_per_sample = len / kWgTile;
   const int n_tiles = batch * tiles_per_sample;
+  const int n_my = (int)blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
   if (tid == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    for (int k = 0; k < kWgStages; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], 3);  // the MMAs' commit and the two bias warps
+    }
+    mbar_init(&fin, 1);
+    s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(&tmem_base, 512);
-  int t = blockIdx.x;
-  if (t < n_tiles) stage_wgrad(smem, dy, x, t / tiles_per_sample, (t % tiles_per_sample) * kWgTile, len);
-  asm volatile("cp.async.commit_group;" ::: "memory");
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
-  // M = 128, N = 64, A and B MN-major
-  const uint32_t idesc = idesc_bf16_f32(128, kC) | (1u << 15) | (1u << 16);
-  uint32_t parity = 0u;
-  float db = 0.f;
-  int i = 0;
   bool ok = true;
-  for (; t < n_tiles; t += gridDim.x, ++i) {
-    const int cur = i & 1;
-    unsigned char* buf = smem + cur * kWgStage;
-    cp_async_wait_all();
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (tid == 0) {
+  float db = 0.f;
+
+  if (warp == 0 && lane == 0) {  // TMA producer
+    int issued = 0;
+    for (int i = 0; i < n_my && ok; ++i) {
+      const int s = i % kWgStages;
+      if (i >= kWgStages) ok = mbar_wait(&empty[s], (uint32_t)((i / kWgStages - 1) & 1), kWaitLimit);
+      if (!ok) break;
+      const int t = (int)blockIdx.x + i * (int)gridDim.x;
+      const int b = t / tiles_per_sample, q0 = (t % tiles_per_sample) * kWgTile;
+      unsigned char* buf = smem + s * kWgStage;
+      mbar_arrive_expect_tx(&full[s], (uint32_t)kWgStage);
+#pragma unroll
+      for (int j = 0; j < kPlanes; ++j) {
+        tma_load3(buf + j * kWgPlane, &dymap, 8 * j, q0 - kTaps / 2, b, &full[s]);
+        tma_load3(buf + (kPlanes + j) * kWgPlane, &dymap, 8 * j, q0 - kTaps / 2 - 1, b, &full[s]);
+        tma_load3(buf + kWgABytes + j * kWgPlane, &xmap, 8 * j, q0, b, &full[s]);
+      }
+      issued = i + 1;
+    }
+    for (int i = issued > kWgStages ? issued - kWgStages : 0; i < issued; ++i)  // every copy has landed
+      if (!mbar_wait(&full[i % kWgStages], (uint32_t)((i / kWgStages) & 1), kWaitLimit)) ok = false;
+  } else if (warp == 1 && lane == 0) {  // MMA issuer: M = 128, N = 64, A and B MN-major
+    const uint32_t idesc = idesc_bf16_f32(128, kC) | (1u << 15) | (1u << 16);
+    for (int i = 0; i < n_my && ok; ++i) {
+      const int s = i % kWgStages;
+      ok = mbar_wait(&full[s], (uint32_t)((i / kWgStages) & 1), kWaitLimit);
+      if (!ok) break;
       tc_fence_after();
-      const uint32_t abase = smem_u32(buf), bbase = smem_u32(buf + kWgABytes);
+      const uint32_t abase = smem_u32(smem + s * kWgStage), bbase = abase + kWgABytes;
 #pragma unroll 1
       for (int g = 0; g < kWgPairs; ++g) {
         const int kk = 2 * g;
 #pragma unroll
         for (int ks = 0; ks < kWgTile / 16; ++ks) {
-          const uint64_t ad = smem_desc(abase + (uint32_t)((kTaps - 1 - kk) * 16 + ks * 256), 128, kWgPlaneA);
-          const uint64_t bd = smem_desc(bbase + (uint32_t)(ks * 256), 128, kWgPlaneB);
+          const uint64_t ad = smem_desc(abase + (uint32_t)((kTaps - 1 - kk) * 16 + ks * 256), 128, kWgPlane);
+          const uint64_t bd = smem_desc(bbase + (uint32_t)(ks * 256), 128, kWgPlane);
           mma_bf16(tmem + (uint32_t)(g * kC), ad, bd, idesc, i > 0 || ks > 0);
         }
       }
-      mma_commit(&mbar[cur]);
+      mma_commit(&empty[s]);  // the buffer is free once these MMAs have read it
     }
-    if (tid < kC) {  // bias gradient: the tile's own dY rows (staged rows 4 .. 131 of plane co / 8)
-      const unsigned char* col = buf + (tid >> 3) * kWgPlaneA + (tid & 7) * 2;
+    mma_commit(&fin);  // every MMA issued has completed before TMEM is read or freed (bounded)
+    if (!mbar_wait(&fin, 0u, kWaitLimit)) ok = false;
+  } else if (warp >= 2) {  // bias gradient: the tile's own dY rows (staged rows 4 .. 131 of plane co / 8)
+    const int co = tid - 64;
+    for (int i = 0; i < n_my && ok; ++i) {
+      const int s = i % kWgStages;
+      ok = mbar_wait(&full[s], (uint32_t)((i / kWgStages) & 1), kWaitLimit);
+      ok = __all_sync(0xffffffffu, ok) != 0;
+      if (!ok) break;
+      const unsigned char* col = smem + s * kWgStage + (co >> 3) * kWgPlane + (co & 7) * 2;
 #pragma unroll 8
       for (int r = kTaps / 2; r < kTaps / 2 + kWgTile; ++r)
         db += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(col + r * 16));
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
     }
-    if (i > 0) {  // the previous tile's MMAs are done: its buffer is free
-      ok = mbar_wait(&mbar[cur ^ 1], (parity >> (cur ^ 1)) & 1u, kWaitLimit);
-      parity ^= 1u << (cur ^ 1);
-      ok = __syncthreads_and(ok) != 0;
-      if (!ok) break;
-    }
-    const int tn = t + gridDim.x;
-    if (tn < n_tiles)
-      stage_wgrad(smem + (cur ^ 1) * kWgStage, dy, x, tn / tiles_per_sample, (tn % tiles_per_sample) * kWgTile,
-                  len);
-    asm volatile("cp.async.commit_group;" ::: "memory");
   }
-  if (ok && i > 0) {  // the last tile's MMAs (and with them all earlier ones)
-    const int last = (i - 1) & 1;
-    ok = mbar_wait(&mbar[last], (parity >> last) & 1u, kWaitLimit);
-    ok = __syncthreads_and(ok) != 0;
-  }
+  if (!ok) atomicExch(&s_fail, 1);
+  tc_fence_before();
+  __syncthreads();
   tc_fence_after();
   float* out = partial + (size_t)blockIdx.x * kDwOut;
-  if (ok) {
+  if (!s_fail && n_my > 0) {
     // TMEM lane m = 32 warp + lane: tap 2g + (m >= 64), output channel m % 64; column = input channel
     const int m = 32 * warp + lane;
     const int co = m & (kC - 1);
@@ -623,11 +693,12 @@ __global__ void __launch_bounds__(128) wgrad64_tc_kernel(const __nv_bfloat16* dy
         }
       }
     }
-    if (tid < kC) out[kTaps * kC * kC + tid] = db;
+    if (warp >= 2) out[kTaps * kC * kC + (tid - 64)] = db;
+  } else if (!s_fail) {  // no tiles: zero partial sums
+    for (int i = tid; i < kDwOut; i += kWgThreads) out[i] = 0.f;
   } else if (tid == 0) {
     atomicOr(err, kErrMmaWait);
   }
-  cp_async_wait_all();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -663,52 +734,130 @@ __global__ void __launch_bounds__(256) dw_small_kernel(const TY* dy, const __nv_
   }
 }
 
-// Partial gradients of the first layer (64 x QLP_CNN_IN_CH channels, dY BF16): each
-// CTA takes whole 128-position tiles (len is a multiple of 128, so a tile lies in one
-// star's row) and stages dY [128][64] and X [128 + 8][CI] in shared memory; thread t
-// owns output channel t mod 64 and every fourth (tap, input channel) pair, so that a
-// warp reads 32 consecutive dY channels and one broadcast X value per step.
-__global__ void __launch_bounds__(256) dw_in_kernel(const __nv_bfloat16* dy, const __nv_bfloat16* x,
-                                                    float* partial, int batch, int len, int per_cta) {
-  constexpr int CI = QLP_CNN_IN_CH, TP = 128, NP = kTaps * CI, NPT = (NP + 3) / 4;
-  __shared__ float s_dy[TP][kC];
-  __shared__ float s_x[TP + kTaps - 1][CI];
-  const int tid = threadIdx.x, co = tid & (kC - 1), g = tid >> 6;
-  const int total = batch * len;
-  const int p_begin = blockIdx.x * per_cta;
-  const int p_end = min(total, p_begin + per_cta);
-  float acc[NPT];
+// Per-CTA partial gradients of the first layer (64 x QLP_CNN_IN_CH channels, dY BF16):
+// dW1[kk][co][ci] = sum_q dY[q][co] X[q + kk - 4][ci], db1[co] = sum_q dY[q][co]. Thread
+// = output channel co of one group; the 9 x CI input values around q in a sliding
+// window of registers, 9 x CI accumulators. The groups' sums are added in shared
+// memory in group order, then written as the CTA's partial.
+__global__ void __launch_bounds__(kSmThreads) dw_in_kernel(const __nv_bfloat16* dy, const __nv_bfloat16* x,
+                                                           float* partial, int batch, int len) {
+  constexpr int CI = QLP_CNN_IN_CH, NW = kTaps * CI;
+  __shared__ float s_x[kSmRows][CI];
+  __shared__ float s_red[kSmThreads / kC - 1][kC][NW + 1];  // the sums of groups 1..3
+  const int co = threadIdx.x & (kC - 1), g = threadIdx.x >> 6;
+  float acc[kTaps][CI];
 #pragma unroll
-  for (int i = 0; i < NPT; ++i) acc[i] = 0.f;
+  for (int kk = 0; kk < kTaps; ++kk)
+#pragma unroll
+    for (int ci = 0; ci < CI; ++ci) acc[kk][ci] = 0.f;
   float acc_b = 0.f;
-  for (int p0 = p_begin; p0 < p_end; p0 += TP) {
-    const int b = p0 / len, l0 = p0 - b * len;
+  const int tps = len / kSmTile, n_tiles = batch * tps;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int b = t / tps, l0 = (t - b * tps) * kSmTile;
     __syncthreads();
-    for (int i = tid; i < TP * kC; i += blockDim.x)
-      s_dy[i / kC][i % kC] = __bfloat162float(dy[(size_t)p0 * kC + i]);
-    for (int i = tid; i < (TP + kTaps - 1) * CI; i += blockDim.x) {
-      const int r = i / CI, ci = i % CI;
-      const int ll = l0 + r - kTaps / 2;  // zero padding outside the star's row
-      s_x[r][ci] = (ll >= 0 && ll < len) ? __bfloat162float(x[((size_t)b * len + ll) * CI + ci]) : 0.f;
+    for (int i = threadIdx.x; i < kSmRows * CI; i += blockDim.x) {
+      const int r = i / CI, ci = i - r * CI;
+      const int l = l0 - kTaps / 2 + r;
+      s_x[r][ci] = (l >= 0 && l < len) ? __bfloat162float(x[((size_t)b * len + l) * CI + ci]) : 0.f;
     }
     __syncthreads();
-    for (int q = 0; q < TP; ++q) {
-      const float a = s_dy[q][co];
+    const int q0 = g * kSmGroupPos;
+    float win[kTaps][CI];
+#pragma unroll
+    for (int r = 0; r < kTaps - 1; ++r)
+#pragma unroll
+      for (int ci = 0; ci < CI; ++ci) win[r][ci] = s_x[q0 + r][ci];
+    const __nv_bfloat16* drow = dy + ((size_t)b * len + l0 + q0) * kC + co;
+#pragma unroll
+    for (int q = 0; q < kSmGroupPos; ++q) {
+#pragma unroll
+      for (int ci = 0; ci < CI; ++ci) win[(q + kTaps - 1) % kTaps][ci] = s_x[q0 + q + kTaps - 1][ci];
+      const float a = __bfloat162float(drow[(size_t)q * kC]);
       acc_b += a;
 #pragma unroll
-      for (int i = 0; i < NPT; ++i) {
-        const int pr = g + 4 * i;
-        if (pr < NP) acc[i] = fmaf(a, s_x[q + pr / CI][pr % CI], acc[i]);
-      }
+      for (int kk = 0; kk < kTaps; ++kk)
+#pragma unroll
+        for (int ci = 0; ci < CI; ++ci) acc[kk][ci] = fmaf(a, win[(q + kk) % kTaps][ci], acc[kk][ci]);
     }
   }
-  float* out = partial + (size_t)blockIdx.x * (kTaps * kC * CI + kC);
+  if (g > 0) {
 #pragma unroll
-  for (int i = 0; i < NPT; ++i) {
-    const int pr = g + 4 * i;
-    if (pr < NP) out[((pr / CI) * kC + co) * CI + pr % CI] = acc[i];
+    for (int kk = 0; kk < kTaps; ++kk)
+#pragma unroll
+      for (int ci = 0; ci < CI; ++ci) s_red[g - 1][co][kk * CI + ci] = acc[kk][ci];
+    s_red[g - 1][co][NW] = acc_b;
   }
-  if (g == 0) out[kTaps * kC * CI + co] = acc_b;
+  __syncthreads();
+  if (g == 0) {  // group 0 adds the others' sums to its own, in group order
+    float* out = partial + (size_t)blockIdx.x * (kTaps * kC * CI + kC);
+#pragma unroll
+    for (int kk = 0; kk < kTaps; ++kk)
+#pragma unroll
+      for (int ci = 0; ci < CI; ++ci) {
+        float v = acc[kk][ci];
+        for (int gg = 0; gg < kSmThreads / kC - 1; ++gg) v += s_red[gg][co][kk * CI + ci];
+        out[(kk * kC + co) * CI + ci] = v;
+      }
+    float v = acc_b;
+    for (int gg = 0; gg < kSmThreads / kC - 1; ++gg) v += s_red[gg][co][NW];
+    out[kTaps * kC * CI + co] = v;
+  }
+}
+
+// Per-CTA partial gradients of the last layer (64 -> 1, dY FP32):
+// dW6[kk][ci] = sum_q dY[q] A5[q + kk - 4][ci], db6 = sum_q dY[q]. Thread = input channel ci
+// of one group; the 9 values of its channel around q in a sliding window, 9 accumulators.
+__global__ void __launch_bounds__(kSmThreads) dw_out_kernel(const float* dy, const __nv_bfloat16* x,
+                                                            float* partial, int batch, int len) {
+  __shared__ float s_dy[kSmTile];
+  __shared__ __align__(16) __nv_bfloat16 s_a[kSmRows][kC];
+  __shared__ float s_red[kSmThreads / kC][kC][kTaps + 1];
+  const int ci = threadIdx.x & (kC - 1), g = threadIdx.x >> 6;
+  float acc[kTaps];
+#pragma unroll
+  for (int kk = 0; kk < kTaps; ++kk) acc[kk] = 0.f;
+  float acc_b = 0.f;
+  const int tps = len / kSmTile, n_tiles = batch * tps;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int b = t / tps, l0 = (t - b * tps) * kSmTile;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSmTile; i += blockDim.x) s_dy[i] = dy[(size_t)b * len + l0 + i];
+    for (int i = threadIdx.x; i < kSmRows * (kC / 8); i += blockDim.x) {
+      const int r = i >> 3, c = i & 7;
+      const int l = l0 - kTaps / 2 + r;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (l >= 0 && l < len) v = reinterpret_cast<const uint4*>(x + ((size_t)b * len + l) * kC)[c];
+      *reinterpret_cast<uint4*>(&s_a[r][8 * c]) = v;
+    }
+    __syncthreads();
+    const int q0 = g * kSmGroupPos;
+    float win[kTaps];
+#pragma unroll
+    for (int r = 0; r < kTaps - 1; ++r) win[r] = __bfloat162float(s_a[q0 + r][ci]);
+#pragma unroll
+    for (int q = 0; q < kSmGroupPos; ++q) {
+      win[(q + kTaps - 1) % kTaps] = __bfloat162float(s_a[q0 + q + kTaps - 1][ci]);
+      const float d = s_dy[q0 + q];
+      if (ci == 0) acc_b += d;
+#pragma unroll
+      for (int kk = 0; kk < kTaps; ++kk) acc[kk] = fmaf(d, win[(q + kk) % kTaps], acc[kk]);
+    }
+  }
+#pragma unroll
+  for (int kk = 0; kk < kTaps; ++kk) s_red[g][ci][kk] = acc[kk];
+  s_red[g][ci][kTaps] = acc_b;
+  __syncthreads();
+  float* out = partial + (size_t)blockIdx.x * (kTaps * kC + 1);
+  for (int i = threadIdx.x; i < kTaps * kC + 1; i += blockDim.x) {
+    float v = 0.f;
+    if (i < kTaps * kC) {
+      const int kk = i / kC, c = i - kk * kC;
+      for (int gg = 0; gg < kSmThreads / kC; ++gg) v += s_red[gg][c][kk];
+    } else {
+      for (int gg = 0; gg < kSmThreads / kC; ++gg) v += s_red[gg][0][kTaps];
+    }
+    out[i] = v;
+  }
 }
 
 __global__ void reduce_partials_kernel(const float* partial, int n_parts, int n_out, float* out) {
@@ -736,17 +885,26 @@ __global__ void adam_kernel(float* p, const float* g, float* m, float* v, int n,
 
 // ------------------------------------------------------------------ launchers
 
+// CTAs of a small-layer kernel: a few per SM, each walking its share of the tiles
+static int small_grid(int batch, int len, int per_sm) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = small_tiles(batch, len);
+  return tiles < per_sm * sms ? tiles : per_sm * sms;
+}
+
 int launch_conv_in(const void* x0, const float* w1, const float* b1, void* a1, int batch, int len, void* s) {
-  const int n = batch * len;
-  conv_in_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)s>>>(
+  if (batch <= 0 || len % kSmTile != 0) return batch <= 0 ? 0 : (int)cudaErrorInvalidValue;
+  conv_in_kernel<<<small_grid(batch, len, 2), kSmThreads, 0, (cudaStream_t)s>>>(
       static_cast<const __nv_bfloat16*>(x0), w1, b1, static_cast<__nv_bfloat16*>(a1), batch, len);
   return (int)cudaGetLastError();
 }
 
 int launch_conv_out(const void* a5, const float* w6, const float* b6, float* logit, int batch, int len, void* s) {
-  const int n = batch * len;
-  conv_out_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)s>>>(static_cast<const __nv_bfloat16*>(a5), w6, b6,
-                                                                  logit, batch, len);
+  if (batch <= 0 || len % kSmTile != 0) return batch <= 0 ? 0 : (int)cudaErrorInvalidValue;
+  conv_out_kernel<<<small_grid(batch, len, 8), 160, 0, (cudaStream_t)s>>>(static_cast<const __nv_bfloat16*>(a5),
+                                                                          w6, b6, logit, batch, len);
   return (int)cudaGetLastError();
 }
 
@@ -758,8 +916,10 @@ int launch_bce(const float* logit, const float* label, float* dlogit, float* los
 
 int launch_conv_out_bwd(const float* dlogit, const float* w6, const void* a5, void* da5, int batch, int len,
                         void* s) {
-  const int n = batch * len;
-  conv_out_bwd_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)s>>>(
+  if (len % kBwdRun != 0) return (int)cudaErrorInvalidValue;
+  const size_t n = (size_t)batch * len / kBwdRun * (kC / 8);
+  if (n == 0) return 0;
+  conv_out_bwd_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)s>>>(
       dlogit, w6, static_cast<const __nv_bfloat16*>(a5), static_cast<__nv_bfloat16*>(da5), batch, len);
   return (int)cudaGetLastError();
 }
@@ -784,11 +944,24 @@ int launch_wgrad64(const void* dy, const void* x, float* partial, float* out, in
                    void* s) {
   if (batch <= 0) return 0;
   const int parts = wgrad64_parts(batch, len);
+  // dY and X as 3-D tensors (channel, position, sample), boxes of 8 channels x 136 rows
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
+  if (!enc) return (int)cudaErrorNotSupported;
+  alignas(64) CUtensorMap dymap, xmap;
+  const cuuint64_t dims[3] = {(cuuint64_t)kC, (cuuint64_t)len, (cuuint64_t)batch};
+  const cuuint64_t strides[2] = {(cuuint64_t)kC * 2, (cuuint64_t)len * kC * 2};
+  const cuuint32_t box[3] = {8, (cuuint32_t)kWgRows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  if (enc(&dymap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(dy), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+      enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(x), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return (int)cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(wgrad64_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
   if (e != cudaSuccess) return (int)e;
-  wgrad64_tc_kernel<<<parts, 128, kWgSmem, (cudaStream_t)s>>>(static_cast<const __nv_bfloat16*>(dy),
-                                                              static_cast<const __nv_bfloat16*>(x), partial, err,
-                                                              batch, len);
+  wgrad64_tc_kernel<<<parts, kWgThreads, kWgSmem, (cudaStream_t)s>>>(dymap, xmap, partial, err, batch, len);
   reduce_partials_kernel<<<(kDwOut + 255) / 256, 256, 0, (cudaStream_t)s>>>(partial, parts, kDwOut, out);
   return (int)cudaGetLastError();
 }
@@ -801,12 +974,19 @@ int launch_dw_small(const void* dy, int dy_is_f32, const void* x, float* partial
   int parts = dw_small_parts(batch, len);
   int per = (total + parts - 1) / parts;
   const int n_out = kTaps * n_co * n_ci + n_co;
-  if (!dy_is_f32 && n_co == kC && n_ci == QLP_CNN_IN_CH && len % 128 == 0) {  // the first layer
-    per = (per + 127) / 128 * 128;  // whole tiles; no more CTAs than the partial buffer holds
-    parts = (total + per - 1) / per;
-    dw_in_kernel<<<parts, 256, 0, (cudaStream_t)s>>>(static_cast<const __nv_bfloat16*>(dy),
-                                                      static_cast<const __nv_bfloat16*>(x), partial, batch, len,
-                                                      per);
+  const bool tiled = len % kSmTile == 0;
+  if (tiled) {  // no more CTAs than the partial buffer holds
+    const int g = small_grid(batch, len, 2);
+    parts = g < parts ? g : parts;
+  }
+  if (tiled && !dy_is_f32 && n_co == kC && n_ci == QLP_CNN_IN_CH) {  // the first layer
+    dw_in_kernel<<<parts, kSmThreads, 0, (cudaStream_t)s>>>(static_cast<const __nv_bfloat16*>(dy),
+                                                             static_cast<const __nv_bfloat16*>(x), partial, batch,
+                                                             len);
+  } else if (tiled && dy_is_f32 && n_co == 1 && n_ci == kC) {  // the last layer
+    dw_out_kernel<<<parts, kSmThreads, 0, (cudaStream_t)s>>>(static_cast<const float*>(dy),
+                                                              static_cast<const __nv_bfloat16*>(x), partial, batch,
+                                                              len);
   } else if (dy_is_f32)
     dw_small_kernel<float><<<parts, 256, 0, (cudaStream_t)s>>>(static_cast<const float*>(dy),
                                                                 static_cast<const __nv_bfloat16*>(x), partial,
