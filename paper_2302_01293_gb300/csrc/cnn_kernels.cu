@@ -106,15 +106,14 @@ __device__ __forceinline__ bool epi_barrier_and(bool v) {
 // one TMEM load and wait, the accumulator released, then bias, ReLU or the backward
 // mask, BF16, into the staging tile `out` (128 rows of 128 bytes, 1024-byte aligned)
 // with the 128-byte swizzle of the store's tensor map: 16-byte chunk j of row r at
-// chunk j ^ (r & 7), so that eight lanes fill the 32 banks once.
+// chunk j ^ (r & 7), so that eight lanes fill the 32 banks once. The backward mask
+// (the row's 32 channels, 4 chunks) was read by the caller before the accumulator wait.
 __device__ __forceinline__ void conv_epilogue(const ConvTcArgs& a, const float* s_bias, uint32_t tmem,
-                                              uint32_t col, int c0, int q, int t, int tiles_per_sample,
-                                              uint64_t* acc_empty, unsigned char* out) {
+                                              uint32_t col, int c0, int q, uint64_t* acc_empty,
+                                              unsigned char* out, const uint4* mk) {
   const int lane = threadIdx.x & 31;
   const int r = 32 * q + lane;
-  const int b = t / tiles_per_sample;
-  const int l = (t % tiles_per_sample) * kTileM + r;
-  const __nv_bfloat16* mrow = a.mask ? a.mask + ((size_t)b * a.len + l) * kC + c0 : nullptr;
+  const bool mrow = a.mask != nullptr;
   float v[32];
   tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + col + (uint32_t)c0, v);
   tc_fence_before();
@@ -122,8 +121,9 @@ __device__ __forceinline__ void conv_epilogue(const ConvTcArgs& a, const float* 
   if (lane == 0) mbar_arrive(acc_empty);  // the values are in registers: the MMA may reuse the columns
 #pragma unroll
   for (int h = 0; h < 32; h += 8) {
-    uint4 m = make_uint4(0u, 0u, 0u, 0u);
-    if (mrow) m = reinterpret_cast<const uint4*>(mrow + h)[0];
+    const int j = (c0 + h) >> 3;  // the 16-byte chunk of the 128-byte row
+    uint4* chunk = reinterpret_cast<uint4*>(out + r * 128 + ((j ^ (r & 7)) << 4));
+    const uint4 m = mk[h >> 3];
     const uint32_t mw[4] = {m.x, m.y, m.z, m.w};
     uint32_t ow[4];
 #pragma unroll
@@ -137,8 +137,7 @@ __device__ __forceinline__ void conv_epilogue(const ConvTcArgs& a, const float* 
       ow[i >> 1] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(z0)) |
                    ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(z1)) << 16);
     }
-    const int j = (c0 + h) >> 3;  // the 16-byte chunk of the 128-byte row
-    *reinterpret_cast<uint4*>(out + r * 128 + ((j ^ (r & 7)) << 4)) = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+    *chunk = make_uint4(ow[0], ow[1], ow[2], ow[3]);
   }
 }
 
@@ -243,11 +242,21 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       const int t = (int)blockIdx.x + i * (int)gridDim.x;
       // staging tile i % 2: its store (tile i - 2) finished reading before the last barrier
       unsigned char* out = obuf + (i % kOutBufs) * kOutBytes;
+      // the backward mask of this thread's row and channels, read before the wait so
+      // that its latency overlaps the tile's MMAs
+      uint4 mk[4] = {};
+      if (a.mask) {
+        const int l = (t % tiles_per_sample) * kTileM + 32 * q + lane;
+        const uint4* mrow = reinterpret_cast<const uint4*>(
+            a.mask + ((size_t)(t / tiles_per_sample) * a.len + l) * kC + c0);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) mk[h] = __ldg(mrow + h);
+      }
       bool mine = mbar_wait(&accf[ac], (uint32_t)((i / kAcc) & 1), kWaitLimit);
       mine = __all_sync(0xffffffffu, mine) != 0;
       if (mine) {
         tc_fence_after();
-        conv_epilogue(a, s_bias, tmem, (uint32_t)(ac * kC), c0, q, t, tiles_per_sample, &acce[ac], out);
+        conv_epilogue(a, s_bias, tmem, (uint32_t)(ac * kC), c0, q, &acce[ac], out, mk);
         fence_proxy_async_smem();  // the staged tile becomes visible to the TMA store
       }
       if (issuer) bulk_wait_read_all();  // tile i - 1's store has read the other staging tile
