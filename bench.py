@@ -699,8 +699,17 @@ def main():
         # cells_fixed_kernel: ncu capture on 1,024 stars of this workload (703.1 MB read +
         # 220.6 MB written), scaled by points (tables, records and outputs grow with them)
         traffic = 923.7e6 * plan.n_points / 10638874
+    # the same launch in the method's own unit: point-frequency pairs per second against
+    # the FP32-issue roof of a per-point search (14 lane operations per pair: double-float
+    # phase, bin index and the run sums), the unit in which the edge formulation's lower
+    # work count shows
+    pf_rate = plan.work / (ms_kernel * 1e-3)
+    pf_roof = peak_ops * 1e12 / 14.0
+    roofline_pf = {"achieved": pf_rate, "roof": pf_roof, "unit": "point-freq/s", "frac": pf_rate / pf_roof,
+                   "roof_source": "issue peak / 14 lane operations per point-frequency pair"}
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "TFLOP/s",
                 "frac": achieved / peak_ops, "traffic": traffic, "kernel": kernel,
+                "per_point_freq": roofline_pf,
                 "algorithmic": unit_note,
                 "peak_source": f"152 SMs x 128 FP32 lanes x {sm_clock/1e6:.0f} MHz ({src} max clock)",
                 "smem": None if smem_gbs is None else

@@ -869,12 +869,28 @@ __global__ void __launch_bounds__(kSmThreads) dw_out_kernel(const float* dy, con
   }
 }
 
-__global__ void reduce_partials_kernel(const float* partial, int n_parts, int n_out, float* out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_out) return;
+// out[o] = sum over the CTA partials g of partial[g][o]: a CTA takes 32 outputs, its 8
+// warps the partials g = w, w + 8, ... (in that order), then warp 0 adds the 8 sums in
+// warp order (a fixed order: deterministic).
+constexpr int kRedSlices = 8;
+__global__ void __launch_bounds__(32 * kRedSlices) reduce_partials_kernel(const float* partial, int n_parts,
+                                                                         int n_out, float* out) {
+  __shared__ float red[kRedSlices][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int o = blockIdx.x * 32 + lane;
   float s = 0.f;
-  for (int g = 0; g < n_parts; ++g) s += partial[(size_t)g * n_out + i];
-  out[i] = s;
+  if (o < n_out)
+    for (int g = w; g < n_parts; g += kRedSlices) s += partial[(size_t)g * n_out + o];
+  red[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && o < n_out) {
+    float t = 0.f;
+    for (int k = 0; k < kRedSlices; ++k) t += red[k][lane];
+    out[o] = t;
+  }
+}
+static void launch_reduce_partials(const float* partial, int n_parts, int n_out, float* out, cudaStream_t s) {
+  reduce_partials_kernel<<<(n_out + 31) / 32, 32 * kRedSlices, 0, s>>>(partial, n_parts, n_out, out);
 }
 
 // Adam with the decay rates and their complements given separately (each the
@@ -971,7 +987,7 @@ int launch_wgrad64(const void* dy, const void* x, float* partial, float* out, in
   cudaError_t e = cudaFuncSetAttribute(wgrad64_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
   if (e != cudaSuccess) return (int)e;
   wgrad64_tc_kernel<<<parts, kWgThreads, kWgSmem, (cudaStream_t)s>>>(dymap, xmap, partial, err, batch, len);
-  reduce_partials_kernel<<<(kDwOut + 255) / 256, 256, 0, (cudaStream_t)s>>>(partial, parts, kDwOut, out);
+  launch_reduce_partials(partial, parts, kDwOut, out, (cudaStream_t)s);
   return (int)cudaGetLastError();
 }
 
@@ -1004,7 +1020,7 @@ int launch_dw_small(const void* dy, int dy_is_f32, const void* x, float* partial
     dw_small_kernel<__nv_bfloat16><<<parts, 256, 0, (cudaStream_t)s>>>(
         static_cast<const __nv_bfloat16*>(dy), static_cast<const __nv_bfloat16*>(x), partial, batch, len, n_co,
         n_ci, per);
-  reduce_partials_kernel<<<(n_out + 255) / 256, 256, 0, (cudaStream_t)s>>>(partial, parts, n_out, out);
+  launch_reduce_partials(partial, parts, n_out, out, (cudaStream_t)s);
   return (int)cudaGetLastError();
 }
 
