@@ -42,7 +42,7 @@ namespace qlp {
 
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 64;
 constexpr int kWarps = kThreads / 32;
 constexpr int kRampBuf = 64;  // queued ramp points per warp (a batch of 32 is taken at 32)
 constexpr int kSums = 21;  // chi^2, g[5], A upper triangle [15]
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(1024) stats_order_kernel(const StatsArgs a) {
   for (int s = threadIdx.x; s < a.n_stars; s += blockDim.x) a.order[atomicAdd(&pos[bucket(s)], 1)] = s;
 }
 
-__global__ void __launch_bounds__(kThreads, 3) stats_kernel(const StatsArgs a) {
+__global__ void __launch_bounds__(kThreads, 6) stats_kernel(const StatsArgs a) {
   __shared__ double red[kWarps][kSums];
   __shared__ double s_part[kThreads][kSums + 1];  // per-thread sums of the fit's pass
   __shared__ double s_q[kThreads / 32][kSums];
