@@ -456,7 +456,7 @@ def multi_sector_line(steps: int, n_stars: int = 1024, n_phase: int = 64):
 def profile_case(which: str):
     """One small launch of a kernel for a profiler capture, checked for device flags:
     fixed: the exact search (and S/N) of 1,024 uneven single-sector stars; stats: the
-    candidate statistics of 512 such stars after their search; conv: the tensor-core
+    candidate statistics of 2,048 such stars after their search; conv: the tensor-core
     convolution (64 -> 64 channels, kernel 9) on 128 x 4,096 x 64 BF16 activations;
     train: three training steps of the proposal network on a batch of 128 x 4,096 bins."""
     import torch
@@ -464,7 +464,7 @@ def profile_case(which: str):
     from paper_2302_01293_gb300 import qlpbls
     torch.cuda.set_device(0)
     if which in ("fixed", "stats"):
-        b = synth.uneven_single_sector(n_stars=1024 if which == "fixed" else 512, seed=2)
+        b = synth.uneven_single_sector(n_stars=1024 if which == "fixed" else 2048, seed=2)
         plan = qlpbls.Plan(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar)
         out = plan.search()
         plan.snr(out)

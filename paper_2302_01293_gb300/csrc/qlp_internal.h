@@ -262,10 +262,11 @@ constexpr int64_t kFixedWsBlock = 131072;  // workspace entries (16 B) per block
 // bytes of shared memory before the histograms of the cell kernel for a star with
 // ncs cells (incl. sentinel) and nw warps
 // One point of a candidate's fit window: t', P n for its transit index n at the
-// starting epoch (the product the model's dt = (t' - T0) - P n uses), y, 1/dy and
-// its square (the point's weight).
+// starting epoch (the product the model's dt = (t' - T0) - P n uses), y and the
+// point's weight (1/dy)^2. 32 bytes: the windows of the stars in flight stay in L2
+// across the fit's iterations.
 struct __align__(16) WinRec {
-  double t, pn, y, inv, w, pad;
+  double t, pn, y, w;
 };
 
 struct StatsArgs {

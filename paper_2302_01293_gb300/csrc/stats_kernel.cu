@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 6) stats_kernel(const StatsArgs a) {
       if (dt0_of(i, pn) <= lim_b) {
         const double inv = __ddiv_rn(1.0, dyv[i]);
         const double w = __dmul_rn(inv, inv);  // the (z, z) term of J^T J, as its product
-        wrec[o++] = WinRec{tp[i], pn, yv[i], inv, w, 0.0};
+        wrec[o++] = WinRec{tp[i], pn, yv[i], w};
         ws += w;
       }
     }
