@@ -156,6 +156,15 @@ def test_tiny_ragged_and_rejected_stars(gpu_lib):
     assert np.all(g["best"]["f_idx"][5:] == -1)
 
 
+def test_tiny_stars_on_the_exact_path(gpu_lib):
+    # short, irregular stars (33-97 points) forced onto the cell path: small tables
+    # whose length is not a multiple of the bulk copies' 4-cell granularity, staged one
+    # after another by the same blocks
+    b = synth.tiny_batch(n_stars=12, seed=16, n_min=33, n_max=97)
+    g, _ = _check_batch(b, qlpbls.Params(method=qlpbls.METHOD_CELLS))
+    assert g["plan"].n_exact_stars > 0
+
+
 def test_empty_batch(gpu_lib):
     z = np.zeros(0)
     plan = qlpbls.Plan(np.zeros(1, np.int64), z, z, z, z, z)
