@@ -157,8 +157,12 @@ __global__ void __launch_bounds__(512) prep_fixed_kernel(const PrepFixedArgs a) 
   long long sw = 0, sy = 0;
   for (int i = i0; i < i1; ++i) {
     const double w = inv_of(i) * rws;
-    sw += __double2ll_rn(w * pw);
-    sy += __double2ll_rn(w * (y[i] - ybar) * py);
+    const long long wi = __double2ll_rn(w * pw), yi = __double2ll_rn(w * (y[i] - ybar) * py);
+    sw += wi;
+    sy += yi;
+    // both below 2^25 in magnitude: kept in the point's cache slot (its 1/dy^2 is no
+    // longer needed) for the prefix pass below
+    if (cache) reinterpret_cast<int2*>(s_inv)[i] = make_int2((int)wi, (int)yi);
   }
   scan_w[tid] = sw;
   scan_y[tid] = sy;
@@ -201,9 +205,15 @@ __global__ void __launch_bounds__(512) prep_fixed_kernel(const PrepFixedArgs a) 
   long long cw = scan_w[tid], cy = scan_y[tid];
   for (int i = i0; i < i1; ++i) {
     a.ipre[st.cpre_off + i] = make_longlong2(cw, cy);
-    const double w = inv_of(i) * rws;
-    cw += __double2ll_rn(w * pw);
-    cy += __double2ll_rn(w * (y[i] - ybar) * py);
+    if (cache) {
+      const int2 v = reinterpret_cast<const int2*>(s_inv)[i];
+      cw += v.x;
+      cy += v.y;
+    } else {
+      const double w = inv_of(i) * rws;
+      cw += __double2ll_rn(w * pw);
+      cy += __double2ll_rn(w * (y[i] - ybar) * py);
+    }
   }
   __syncthreads();
 
@@ -215,12 +225,16 @@ __global__ void __launch_bounds__(512) prep_fixed_kernel(const PrepFixedArgs a) 
     for (int c = up + 1; c <= ui && c <= nc; ++c) first[c] = i;
   }
   __syncthreads();
+  // 1/h: the point's offset in its cell, (t' - u h) / h, by a multiplication; with the
+  // product's rounding it stays within (T/h + 3) 2^-53 cells of the exact offset, inside
+  // the guard band's allowance of 2 (T/h) 2^-53 cells for the cell offsets
+  const double rh = 1.0 / h;
   for (int u = tid; u <= nc; u += blockDim.x) {
     const int f = first[u];
     const bool in_cell = (u < nc) && (f < n) && (cell_at(f) == u);
     uint32_t q = 0xffffffffu;  // the cell's point as a 32-bit fraction of the cell, empty = all ones
     if (in_cell) {
-      const double fr = __ddiv_rn(__dsub_rn(tp[f], __dmul_rn((double)u, h)), h);
+      const double fr = __dmul_rn(__dsub_rn(tp[f], __dmul_rn((double)u, h)), rh);
       q = (uint32_t)fmin(floor(__dmul_rn(fr, 4294967296.0)), 4294967294.0);
     }
     a.dt[st.cell_off + u] = q;
