@@ -289,6 +289,14 @@ int qlp_bls_snr(qlp_bls_plan_t* plan, void* stream, const float* sr, const uint8
  *   clipped to [1/Pmax, 1/Pmin], the Sec. 2.1 spacing f <- f + q_min(f)/(spp T)
  *   is walked from the window's low edge while f stays inside it. A star with no
  *   frequency inside its windows gets QLP_STAR_EMPTY_GRID.
+ * qlp_bls_plan_windows_from -- the same windowed plan for the stars of an existing
+ *   plan `base` (any grid mode), without their points: it takes base's validation,
+ *   t_ref, Pmin, Pmax, weight spreads and cell widths, and searches base's device
+ *   copy of the points (the grids, bins, paths and results are those of
+ *   qlp_bls_plan_windows on the same arrays). p must be grid_mode 0 and have
+ *   base's rho_default, pmin_aR and gap_days, else QLP_ERR_ARG. The new plan keeps
+ *   base's device memory alive until both are destroyed (either may go first);
+ *   base must not be destroyed while the call runs.
  * qlp_bls_snr_trend -- qlp_bls_snr with an optional per-star trend record
  *   (QLP_TREND_DOUBLES doubles: node count, sigma_SR, median, bin centres, bin
  *   medians) written to trend_out, or, when trend_in is given, the S/N computed
@@ -313,6 +321,9 @@ int qlp_bls_plan_windows(const qlp_bls_params* p, int32_t n_stars, const int64_t
                          const double* t, const double* y, const double* dy, const double* rho,
                          const double* rstar, const int64_t* win_offsets, const double* win_flo,
                          const double* win_fhi, void* stream, qlp_bls_plan_t** out_plan);
+int qlp_bls_plan_windows_from(const qlp_bls_plan_t* base, const qlp_bls_params* p,
+                              const int64_t* win_offsets, const double* win_flo, const double* win_fhi,
+                              void* stream, qlp_bls_plan_t** out_plan);
 int qlp_bls_snr_trend(qlp_bls_plan_t* plan, void* stream, const float* sr, const uint8_t* qidx,
                       const uint32_t* phase_bin, const float* s_best, const float* r_best,
                       const double* trend_in, double* trend_out, float* snr, qlp_bls_best* best);

@@ -206,6 +206,12 @@ struct qlp_bls_plan {
   cudaEvent_t ready = nullptr;
   void* d_arena = nullptr;        // the one allocation holding the plan's buffers
   size_t arena_bytes = 0, wrec_bytes = 0, sorder_bytes = 0;  // device bytes held against the budget
+  // owners of device memory: this plan's arena (freed, and its bytes given back, when
+  // the last holder lets go) and, for a plan made from another one, that plan's
+  // arena, which holds the points d_tp, d_y, d_dy this plan reads
+  std::shared_ptr<void> arena_ref, points_ref;
+  std::vector<StarPoints> pinfo;  // each star's point analysis (for plans made from this one)
+  std::vector<int64_t> pt_off0;   // offsets of the stars' points, from 0
   bool ready_seen = false;        // the host has seen `ready` complete
   cudaGraph_t graph[3] = {};
   cudaGraphExec_t gexec[3] = {};
@@ -224,10 +230,11 @@ static void free_plan(qlp_bls_plan_t* pl) {
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
   if (pl->kev[0]) cudaEventDestroy(pl->kev[0]);
   if (pl->kev[1]) cudaEventDestroy(pl->kev[1]);
-  cudaFree(pl->d_arena);  // every buffer below but d_wrec lives in it
+  pl->arena_ref.reset();  // every buffer below but d_wrec and d_sorder lives in it
+  pl->points_ref.reset();
   cudaFree(pl->d_wrec);
   cudaFree(pl->d_sorder);
-  budget_give(pl->arena_bytes + pl->wrec_bytes + pl->sorder_bytes);
+  budget_give(pl->wrec_bytes + pl->sorder_bytes);
   delete pl;
 }
 
@@ -327,7 +334,7 @@ static PrepFixedArgs fixed_args(const qlp_bls_plan_t* pl) {
 static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offsets, const double* t,
                      const double* y, const double* dy, const double* rho, const double* rstar,
                      const int64_t* win_off, const double* win_lo, const double* win_hi, void* stream,
-                     qlp_bls_plan_t** out_plan);
+                     qlp_bls_plan_t** out_plan, const qlp_bls_plan_t* from = nullptr);
 
 int qlp_bls_plan(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offsets, const double* t,
                  const double* y, const double* dy, const double* rho, const double* rstar,
@@ -355,10 +362,32 @@ int qlp_bls_plan_windows(const qlp_bls_params* pin, int32_t n_stars, const int64
   });
 }
 
+int qlp_bls_plan_windows_from(const qlp_bls_plan_t* base, const qlp_bls_params* pin,
+                              const int64_t* win_offsets, const double* win_flo, const double* win_fhi,
+                              void* stream, qlp_bls_plan_t** out_plan) {
+  if (out_plan) *out_plan = nullptr;
+  if (!base || !win_offsets) return QLP_ERR_ARG;
+  const int32_t n_stars = base->n_stars;
+  if (n_stars > 0 && win_offsets[n_stars] > 0 && (!win_flo || !win_fhi)) return QLP_ERR_ARG;
+  for (int32_t s = 0; s < n_stars; ++s)
+    if (win_offsets[s + 1] < win_offsets[s]) return QLP_ERR_ARG;
+  qlp_bls_params p;
+  if (pin) p = *pin; else qlp_bls_params_default(&p);
+  if (p.grid_mode != 0) return QLP_ERR_ARG;
+  // the point analysis depends on these: they must be the base plan's
+  if (!(p.rho_default == base->p.rho_default) || !(p.pmin_aR == base->p.pmin_aR) ||
+      !(p.gap_days == base->p.gap_days))
+    return QLP_ERR_ARG;
+  return guarded([&] {
+    return plan_impl(&p, n_stars, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, win_offsets, win_flo,
+                     win_fhi, stream, out_plan, base);
+  });
+}
+
 static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* offsets, const double* t,
                      const double* y, const double* dy, const double* rho, const double* rstar,
                      const int64_t* win_off, const double* win_lo, const double* win_hi, void* stream,
-                     qlp_bls_plan_t** out_plan) {
+                     qlp_bls_plan_t** out_plan, const qlp_bls_plan_t* from) {
   (void)rstar;
   if (!out_plan) return QLP_ERR_ARG;
   *out_plan = nullptr;
@@ -366,8 +395,12 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   if (pin) p = *pin; else qlp_bls_params_default(&p);
   int rc = check_params(p);
   if (rc) return rc;
+  if (from) {  // the stars and points of `from`: its offsets and point analysis
+    if (n_stars != from->n_stars) return QLP_ERR_ARG;
+    offsets = from->pt_off0.data();
+  }
   if (n_stars < 0 || (n_stars > 0 && !offsets)) return QLP_ERR_ARG;
-  if (n_stars > 0) {
+  if (n_stars > 0 && !from) {
     if (offsets[0] != 0) return QLP_ERR_ARG;
     for (int32_t s = 0; s < n_stars; ++s)
       if (offsets[s + 1] < offsets[s]) return QLP_ERR_ARG;
@@ -380,20 +413,32 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   // offset (a star's entries past its valid count are zero and never read)
   const int64_t npt_raw = n_stars > 0 ? offsets[n_stars] - offsets[0] : 0;
   const size_t npt_alloc = (size_t)std::max<int64_t>(npt_raw, 1);
-  std::unique_ptr<double[]> tp_all(new (std::nothrow) double[npt_alloc]);
-  std::unique_ptr<double[]> y_all(new (std::nothrow) double[npt_alloc]);
-  std::unique_ptr<double[]> dy_all(new (std::nothrow) double[npt_alloc]);
-  if (!tp_all || !y_all || !dy_all) return QLP_ERR_NOMEM;
-  PointDst pdst;
-  pdst.tp = tp_all.get();
-  pdst.y = y_all.get();
-  pdst.dy = dy_all.get();
+  std::unique_ptr<double[]> tp_all, y_all, dy_all;
   std::vector<StarPlanHost> sp;
-  plan_all(p, n_stars, offsets, t, y, dy, rho, &sp, win_off, win_lo, win_hi, &pdst);
+  std::vector<StarPoints> pinfo;
+  if (from) {  // the grids only: the points were validated, analysed and uploaded by `from`
+    plan_all_from(p, n_stars, from->pinfo.data(), &sp, win_off, win_lo, win_hi);
+    pinfo = from->pinfo;
+  } else {
+    tp_all.reset(new (std::nothrow) double[npt_alloc]);
+    y_all.reset(new (std::nothrow) double[npt_alloc]);
+    dy_all.reset(new (std::nothrow) double[npt_alloc]);
+    if (!tp_all || !y_all || !dy_all) return QLP_ERR_NOMEM;
+    PointDst pdst;
+    pdst.tp = tp_all.get();
+    pdst.y = y_all.get();
+    pdst.dy = dy_all.get();
+    plan_all(p, n_stars, offsets, t, y, dy, rho, &sp, win_off, win_lo, win_hi, &pdst);
+    pinfo.resize((size_t)n_stars);
+    parallel_stars(p, n_stars, [&](int32_t s) { pinfo[(size_t)s] = points_of(sp[(size_t)s]); });
+  }
   const auto c1 = clk::now();
 
   qlp_bls_plan_t* pl = new (std::nothrow) qlp_bls_plan_t();
   if (!pl) return QLP_ERR_NOMEM;
+  pl->pinfo = std::move(pinfo);
+  pl->pt_off0.resize((size_t)n_stars + 1, 0);
+  for (int32_t s = 0; s <= n_stars; ++s) pl->pt_off0[(size_t)s] = n_stars > 0 ? offsets[s] - offsets[0] : 0;
   pl->times[0] = std::chrono::duration<double>(c1 - c0).count();
   pl->p = p;
   pl->n_stars = n_stars;
@@ -695,9 +740,9 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   arena.add(&pl->d_stars, (size_t)n_stars)
       .add(&pl->d_fq, nf_alloc)
       .add(&pl->d_items, sorted.size())
-      .add(&pl->d_tp, npt_alloc)
-      .add(&pl->d_y, npt_alloc)
-      .add(&pl->d_dy, npt_alloc)
+      .add(&pl->d_tp, from ? (size_t)1 : npt_alloc)
+      .add(&pl->d_y, from ? (size_t)1 : npt_alloc)
+      .add(&pl->d_dy, from ? (size_t)1 : npt_alloc)
       .add(&pl->d_pts, (size_t)npad)
       .add(&pl->d_tpd, (size_t)npad)
       .add(&pl->d_cell_stars, cell_stars.size())
@@ -715,6 +760,19 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
     free_plan(pl);
     return rc;
   }
+  {
+    const size_t ab = pl->arena_bytes;
+    pl->arena_ref = std::shared_ptr<void>(pl->d_arena, [ab](void* b) {
+      cudaFree(b);
+      budget_give(ab);
+    });
+  }
+  if (from) {  // the points stay in `from`'s arena, held as long as this plan lives
+    pl->d_tp = from->d_tp;
+    pl->d_y = from->d_y;
+    pl->d_dy = from->d_dy;
+    pl->points_ref = from->points_ref ? from->points_ref : from->arena_ref;
+  }
   const auto c3 = clk::now();
   pl->times[2] = std::chrono::duration<double>(c3 - c2).count();
   cudaError_t e = cudaSuccess;
@@ -723,9 +781,9 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   if (e == cudaSuccess && !sorted.empty()) e = cudaMemcpyAsync(pl->d_items, sorted.data(), sizeof(WorkItem) * sorted.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !cell_stars.empty()) e = cudaMemcpyAsync(pl->d_cell_stars, cell_stars.data(), sizeof(int32_t) * cell_stars.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !fixed_stars.empty()) e = cudaMemcpyAsync(pl->d_fixed_stars, fixed_stars.data(), sizeof(int32_t) * fixed_stars.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && npt_raw > 0) e = cudaMemcpyAsync(pl->d_tp, tp_all.get(), sizeof(double) * (size_t)npt_raw, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && npt_raw > 0) e = cudaMemcpyAsync(pl->d_y, y_all.get(), sizeof(double) * (size_t)npt_raw, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && npt_raw > 0) e = cudaMemcpyAsync(pl->d_dy, dy_all.get(), sizeof(double) * (size_t)npt_raw, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && npt_raw > 0 && !from) e = cudaMemcpyAsync(pl->d_tp, tp_all.get(), sizeof(double) * (size_t)npt_raw, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && npt_raw > 0 && !from) e = cudaMemcpyAsync(pl->d_y, y_all.get(), sizeof(double) * (size_t)npt_raw, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && npt_raw > 0 && !from) e = cudaMemcpyAsync(pl->d_dy, dy_all.get(), sizeof(double) * (size_t)npt_raw, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // host staging arrays die at return
   // the rest runs on the device after the uploads without the host waiting for it
   if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_ctl, 0, 4 * sizeof(int32_t), st);

@@ -244,12 +244,8 @@ extern "C" int qlp_bls_search_learned(const qlp_bls_params* p, int32_t n_stars, 
       std::vector<int64_t> woff;
       std::vector<double> wlo, whi;
       proposal_windows(*p, q.ns, hb.data(), k, half_width, &woff, &wlo, &whi);
-      const int64_t o0 = offsets[q.s0];
-      std::vector<int64_t> off((size_t)q.ns + 1);
-      for (int32_t i = 0; i <= q.ns; ++i) off[(size_t)i] = offsets[q.s0 + i] - o0;
-      int r2 = qlp_bls_plan_windows(&pr, q.ns, off.data(), t + o0, y + o0, dy + o0, rho ? rho + q.s0 : nullptr,
-                                    rstar ? rstar + q.s0 : nullptr, woff.data(), wlo.data(), whi.data(), st_up,
-                                    &q.rp.p);
+      // the refine plan from the coarse plan: its stars' point analysis and device points
+      int r2 = qlp_bls_plan_windows_from(q.cp.p, &pr, woff.data(), wlo.data(), whi.data(), st_up, &q.rp.p);
       if (r2) return r2;
       int64_t nfr = 0;
       if ((r2 = qlp_bls_plan_info(q.rp.p, &nfr, nullptr, nullptr, nullptr, nullptr, nullptr))) return r2;

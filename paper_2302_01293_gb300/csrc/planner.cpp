@@ -140,6 +140,7 @@ bool plan_head(const qlp_bls_params& p, const double* t, const double* y, const 
   s.pmin = pmin_of(s.rho_kg, p);
   s.pmax = pmax_of(otp, m, p);
   if (!(s.baseline > 0.0) || !(s.pmin < s.pmax)) { s.status = QLP_STAR_EMPTY_GRID; return false; }
+  s.head_ok = true;
   return true;
 }
 
@@ -225,14 +226,10 @@ void grid_chains(const qlp_bls_params& p, StarPlanHost* const* st, int n) {
   }
 }
 
-// Bins and the grid's sums, the nbins cap, Sturges' bin count, the weight
-// spreads and the cell table.
-void plan_tail(const qlp_bls_params& p, StarPlanHost& s) {
-  const int64_t m = s.n_valid;
-  const double* tp = s.tp_data();
-  const double* yv = s.y_data();
-  const double* dyv = s.dy_data();
-  // the bin edges across the baseline and the longest bin duration (cell path)
+// Bins and the grid's sums, the nbins cap and Sturges' bin count; the bin edges
+// across the baseline and the longest bin duration into *edges_out, *dmax_out.
+// False when the grid is empty or over the cap (the status says which).
+bool tail_grid(const qlp_bls_params& p, StarPlanHost& s, double* edges_out, double* dmax_out) {
   double edges = 0.0, dmax = 0.0, fnb_min = 0.0;
   const size_t nf = s.freqs.size();
   s.nbins.resize(nf);
@@ -250,16 +247,26 @@ void plan_tail(const qlp_bls_params& p, StarPlanHost& s) {
   }
   // longest bin duration: max of 1 / (f nbins) = 1 / min(f nbins) (division is monotonic)
   if (nf > 0) dmax = 1.0 / fnb_min;
-  if (s.freqs.empty()) { s.status = QLP_STAR_EMPTY_GRID; return; }
+  if (s.freqs.empty()) { s.status = QLP_STAR_EMPTY_GRID; return false; }
   if (s.nbins_max > p.nbins_cap) {
     s.status = QLP_STAR_NBINS_CAP;
     s.freqs.clear();
     s.qmins.clear();
     s.nbins.clear();
-    return;
+    return false;
   }
   s.sturges_nb = sturges_of((int64_t)s.freqs.size());
+  *edges_out = edges;
+  *dmax_out = dmax;
+  return true;
+}
 
+// The weight spreads and the cell width of a star (its points only).
+void tail_points(StarPlanHost& s) {
+  const int64_t m = s.n_valid;
+  const double* tp = s.tp_data();
+  const double* yv = s.y_data();
+  const double* dyv = s.dy_data();
   // weight spreads (FP64; only a routing decision depends on them, so the sums
   // are plain and the weights are not normalised)
   {
@@ -297,9 +304,20 @@ void plan_tail(const qlp_bls_params& p, StarPlanHost& s) {
       s.cells_ok = true;
       s.cell_h = h;
       s.n_cells = prev + 1;
-      s.cells_work = edges;
-      s.bin_dmax = dmax;
     }
+  }
+  s.points_done = true;
+}
+
+// Bins and the grid's sums, the nbins cap, Sturges' bin count, the weight
+// spreads and the cell table.
+void plan_tail(const qlp_bls_params& p, StarPlanHost& s) {
+  double edges = 0.0, dmax = 0.0;
+  if (!tail_grid(p, s, &edges, &dmax)) return;
+  tail_points(s);
+  if (s.cells_ok) {
+    s.cells_work = edges;
+    s.bin_dmax = dmax;
   }
 }
 
@@ -486,6 +504,72 @@ void plan_all(const qlp_bls_params& p, int32_t n_stars, const int64_t* offsets, 
     }
     grid_chains(p, st, n);
     for (int j = 0; j < n; ++j) plan_tail(p, *st[j]);
+  });
+}
+
+StarPoints points_of(StarPlanHost& s) {
+  StarPoints o;
+  o.head_ok = s.head_ok;
+  o.status = s.head_ok ? 0 : s.status;
+  o.n_valid = s.n_valid;
+  o.t_ref = s.t_ref;
+  o.baseline = s.baseline;
+  o.pmin = s.pmin;
+  o.pmax = s.pmax;
+  o.rho_kg = s.rho_kg;
+  if (!s.head_ok) return o;
+  if (!s.points_done) tail_points(s);  // the grid was empty or over the cap
+  o.w_spread = s.w_spread;
+  o.wd_spread = s.wd_spread;
+  o.cells_ok = s.cells_ok;
+  o.cell_h = s.cell_h;
+  o.n_cells = s.n_cells;
+  return o;
+}
+
+void plan_all_from(const qlp_bls_params& p, int32_t n_stars, const StarPoints* pts,
+                   std::vector<StarPlanHost>* out, const int64_t* win_off, const double* win_lo,
+                   const double* win_hi) {
+  out->assign((size_t)n_stars, StarPlanHost());
+  parallel_stars(p, n_stars, [&](int32_t st) {
+    const StarPoints& q = pts[st];
+    StarPlanHost& s = (*out)[(size_t)st];
+    s.n_valid = q.n_valid;
+    s.rho_kg = q.rho_kg;
+    if (!q.head_ok) {  // the head's outcome: no grid (status as the head set it)
+      s.status = q.status;
+      if (q.status == QLP_STAR_EMPTY_GRID) {
+        s.t_ref = q.t_ref;
+        s.baseline = q.baseline;
+        s.pmin = q.pmin;
+        s.pmax = q.pmax;
+      }
+      return;
+    }
+    s.t_ref = q.t_ref;
+    s.baseline = q.baseline;
+    s.pmin = q.pmin;
+    s.pmax = q.pmax;
+    s.head_ok = true;
+    Windows w;
+    if (win_off) {
+      w.lo = win_lo + win_off[st];
+      w.hi = win_hi + win_off[st];
+      w.n = win_off[st + 1] - win_off[st];
+    }
+    grid_one(p, s, win_off ? &w : nullptr);
+    double edges = 0.0, dmax = 0.0;
+    if (!tail_grid(p, s, &edges, &dmax)) return;
+    s.w_spread = q.w_spread;
+    s.wd_spread = q.wd_spread;
+    s.points_done = true;
+    if (q.cells_ok) {
+      s.cells_ok = true;
+      s.cell_h = q.cell_h;
+      s.n_cells = q.n_cells;
+      s.cells_work = edges;
+      s.bin_dmax = dmax;
+    }
   });
 }
 

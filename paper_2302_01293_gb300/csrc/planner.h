@@ -45,6 +45,22 @@ struct StarPlanHost {
   double cells_work = 0.0;         // sum over f of the bin edges across the baseline
   double bin_dmax = 0.0;           // longest bin duration 1/(f nbins) over the grid (days)
   int32_t grid_k0 = -1;            // coarse grid: bin index of the first (lowest) frequency
+  bool head_ok = false;            // valid, sorted points and Pmin < Pmax: the star gets a grid
+  bool points_done = false;        // the point analysis (weight spreads, cells) has run
+};
+
+// The part of a star's plan that depends on its points only (validity, t_ref,
+// baseline, Pmin and Pmax, weight spreads, cells), kept by a plan so that a plan of
+// the same stars on other frequencies need not scan the points again.
+struct StarPoints {
+  int32_t status = 0;              // the head's status when head_ok is false
+  bool head_ok = false;
+  int64_t n_valid = 0;
+  double t_ref = 0.0, baseline = 0.0, pmin = 0.0, pmax = 0.0, rho_kg = 0.0;
+  double w_spread = 0.0, wd_spread = 0.0;
+  bool cells_ok = false;
+  double cell_h = 0.0;
+  int64_t n_cells = 0;
 };
 
 // Arrays that receive a star's valid points (t', y, dy), at least as long as its
@@ -74,6 +90,15 @@ void plan_one(const qlp_bls_params& p, const double* t, const double* y, const d
               double rho, StarPlanHost* out, const Windows* win = nullptr, const PointDst* dst = nullptr);
 // Runs fn(s) for every star s on the planner's threads (p.n_threads, 0 = all cores).
 void parallel_stars(const qlp_bls_params& p, int32_t n_stars, const std::function<void(int32_t)>& fn);
+
+// The point analysis of a planned star (running it first if its grid came out
+// empty or over the cap, which skips it); the star's point arrays must still exist.
+StarPoints points_of(StarPlanHost& s);
+// The plans of stars whose point analysis is known, on the grids of p (windows as
+// in plan_all); the same grids and bins as plan_all on the stars' points.
+void plan_all_from(const qlp_bls_params& p, int32_t n_stars, const StarPoints* pts,
+                   std::vector<StarPlanHost>* out, const int64_t* win_off = nullptr,
+                   const double* win_lo = nullptr, const double* win_hi = nullptr);
 
 void plan_all(const qlp_bls_params& p, int32_t n_stars, const int64_t* offsets, const double* t,
               const double* y, const double* dy, const double* rho, std::vector<StarPlanHost>* out,

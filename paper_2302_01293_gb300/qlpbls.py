@@ -191,6 +191,8 @@ def lib():
             L.qlp_bls_plan_windows.argtypes = [_P(CParams), _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                                _vp, _vp, _vp, _P(_vp)]
             L.qlp_bls_plan_windows.restype = ctypes.c_int
+            L.qlp_bls_plan_windows_from.argtypes = [_vp, _P(CParams), _vp, _vp, _vp, _vp, _P(_vp)]
+            L.qlp_bls_plan_windows_from.restype = ctypes.c_int
             L.qlp_bls_snr_trend.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
             L.qlp_bls_snr_trend.restype = ctypes.c_int
             L.qlp_bls_coarse_tensor.argtypes = [_vp, _vp, _vp, _i32, _vp, _vp]
@@ -296,6 +298,29 @@ class Plan:
                                         _np_ptr(y), _np_ptr(dy), _np_ptr(rho), _np_ptr(rstar), _np_ptr(wo),
                                         _np_ptr(wl), _np_ptr(wh), _stream_ptr(stream), ctypes.byref(self._h))
             _check(rc, "qlp_bls_plan_windows")
+        self._load_info()
+
+    @classmethod
+    def windows_from(cls, base: "Plan", windows, params: "Params | None" = None, stream=None) -> "Plan":
+        """qlp_bls_plan_windows_from: the windowed plan of base's stars (windows as in the
+        constructor) made from base's point analysis and device copy of the points."""
+        self = cls.__new__(cls)
+        self._h = ctypes.c_void_p()
+        self.n_stars = base.n_stars
+        self.params = params or Params()
+        self.device = base.device
+        cp = self.params.to_c()
+        wo = np.ascontiguousarray(windows[0], np.int64)
+        wl = np.ascontiguousarray(windows[1], np.float64)
+        wh = np.ascontiguousarray(windows[2], np.float64)
+        rc = lib().qlp_bls_plan_windows_from(base._h, ctypes.byref(cp), _np_ptr(wo), _np_ptr(wl), _np_ptr(wh),
+                                             _stream_ptr(stream), ctypes.byref(self._h))
+        _check(rc, "qlp_bls_plan_windows_from")
+        self._load_info()
+        return self
+
+    def _load_info(self):
+        L = lib()
         nft = _i64()
         npts = _i64()
         work = _d()

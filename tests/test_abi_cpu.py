@@ -214,6 +214,19 @@ def test_device_budget_setting_needs_no_gpu():
     assert L.qlp_set_device_budget(0) == 0
 
 
+def test_plan_from_plan_rejects_missing_arguments():
+    # checked before any device work: no base plan, no window offsets
+    import ctypes
+    import numpy as np
+    from paper_2302_01293_gb300 import qlpbls
+    L = qlpbls.lib()
+    out = ctypes.c_void_p()
+    wo = np.zeros(2, np.int64)
+    assert L.qlp_bls_plan_windows_from(None, None, wo.ctypes.data, None, None, None,
+                                       ctypes.byref(out)) == qlpbls.ERR_ARG
+    assert out.value is None
+
+
 def test_work_loop_bound_is_validated():
     from paper_2302_01293_gb300 import qlpbls
     import synth

@@ -168,6 +168,51 @@ def test_learned_path_recall(gpu_lib):
     net.close()
 
 
+def test_refine_plan_from_the_coarse_plan_equals_a_fresh_plan(gpu_lib):
+    """qlp_bls_plan_windows_from: the refine plan made from the coarse plan (its
+    point analysis and device points, no second scan or upload) has the fresh
+    windowed plan's grids, paths and results bit for bit, also after the coarse
+    plan is destroyed; parameters its point analysis depends on must match."""
+    import dataclasses
+    import torch
+    b = synth.proposal_set(40, seed=45, max_sectors=3)
+    cs = learned.CoarseStage(b)
+    bins = learned.propose_without_network(cs, 4).cpu().numpy()
+    win = learned.windows_from_bins(bins, cs.params)
+    p = qlpbls.Params()
+    fresh = qlpbls.Plan(b.offsets, b.t, b.y, b.dy, b.rho, b.rstar, p, windows=win)
+    derived = qlpbls.Plan.windows_from(cs.plan, win, p)
+    for key in ("freq_offsets", "freqs", "star_status"):
+        assert np.array_equal(getattr(fresh, key), getattr(derived, key)), key
+    for key in ("n_points", "work", "n_cell_stars", "n_exact_stars", "n_windowed", "edges"):
+        assert getattr(fresh, key) == getattr(derived, key), key
+
+    def run(plan):
+        out = plan.search()
+        plan.snr(out, trend_in=cs.trend)
+        torch.cuda.synchronize()
+        assert plan.device_status() == 0
+        g = {k: v.cpu().numpy() for k, v in out.items() if k != "best"}
+        return g, plan.best_host(out)
+
+    gf, bf = run(fresh)
+    gd, bd = run(derived)
+    cs.plan.close()  # the derived plan keeps the coarse plan's device points alive
+    gd2, bd2 = run(derived)
+    for g, bb in ((gd, bd), (gd2, bd2)):
+        for key in ("sr", "qidx", "kbin", "snr"):
+            np.testing.assert_array_equal(gf[key], g[key], err_msg=key)
+        for key in ("f_idx", "snr", "sr", "period", "q", "t0", "depth"):
+            np.testing.assert_array_equal(bf[key], bb[key], err_msg=key)
+    with pytest.raises(qlpbls.QlpError):
+        qlpbls.Plan.windows_from(derived, win, dataclasses.replace(p, gap_days=p.gap_days * 2))
+    again = qlpbls.Plan.windows_from(derived, win, p)  # a plan made from a derived plan
+    ga, ba = run(again)
+    np.testing.assert_array_equal(gf["sr"], ga["sr"])
+    for pl in (fresh, derived, again):
+        pl.close()
+
+
 def test_learned_one_call_in_chunks_equals_whole_batch_stages(gpu_lib):
     """1,100 stars take the one-call path in several chunks (planning of one
     chunk overlaps the device work of its neighbours); every star's proposals
