@@ -144,9 +144,20 @@ bool plan_head(const qlp_bls_params& p, const double* t, const double* y, const 
   return true;
 }
 
-// The frequencies and q_min of one star: the coarse log-period grid, the spacing
-// rule inside windows, or the spacing rule over [1/Pmax, 1/Pmin].
-void grid_one(const qlp_bls_params& p, StarPlanHost& s, const Windows* win) {
+// The coarse grid's periods, coarse_pmin (coarse_pmax / coarse_pmin)^(k / (bins - 1))
+// for k = 0 .. bins - 1: the same for every star, so a batch computes them once.
+std::vector<double> coarse_period_table(const qlp_bls_params& p) {
+  std::vector<double> per((size_t)std::max(p.coarse_bins, 0));
+  const double ratio = p.coarse_pmax / p.coarse_pmin;
+  for (int k = 0; k < p.coarse_bins; ++k)
+    per[(size_t)k] = p.coarse_pmin * std::pow(ratio, (double)k / (double)(p.coarse_bins - 1));
+  return per;
+}
+
+// The frequencies and q_min of one star: the coarse log-period grid (its periods
+// from coarse_per when given), the spacing rule inside windows, or the spacing rule
+// over [1/Pmax, 1/Pmin].
+void grid_one(const qlp_bls_params& p, StarPlanHost& s, const Windows* win, const double* coarse_per = nullptr) {
   auto add = [&](double f) {  // returns q_min(f)
     const double q = q_min_of(f, s.rho_kg, p);
     s.freqs.push_back(f);
@@ -157,7 +168,8 @@ void grid_one(const qlp_bls_params& p, StarPlanHost& s, const Windows* win) {
     // coarse log-period grid, increasing frequency = decreasing bin index
     const double ratio = p.coarse_pmax / p.coarse_pmin;
     for (int k = p.coarse_bins - 1; k >= 0; --k) {
-      const double per = p.coarse_pmin * std::pow(ratio, (double)k / (double)(p.coarse_bins - 1));
+      const double per = coarse_per ? coarse_per[k]
+                                    : p.coarse_pmin * std::pow(ratio, (double)k / (double)(p.coarse_bins - 1));
       if (per < s.pmin || per > s.pmax) continue;
       if (s.grid_k0 < 0) s.grid_k0 = k;
       add(1.0 / per);
@@ -476,6 +488,7 @@ void plan_all(const qlp_bls_params& p, int32_t n_stars, const int64_t* offsets, 
     return d;
   };
   if (win_off || p.grid_mode == 1) {
+    const std::vector<double> cper = p.grid_mode == 1 ? coarse_period_table(p) : std::vector<double>();
     parallel_stars(p, n_stars, [&](int32_t s) {
       const int64_t a = offsets[s], b = offsets[s + 1];
       const double r = rho ? rho[s] : NAN;
@@ -486,7 +499,10 @@ void plan_all(const qlp_bls_params& p, int32_t n_stars, const int64_t* offsets, 
         w.n = win_off[s + 1] - win_off[s];
       }
       PointDst d;
-      plan_one(p, t + a, y + a, dy + a, b - a, r, &(*out)[(size_t)s], win_off ? &w : nullptr, dst_of(s, &d));
+      StarPlanHost& h = (*out)[(size_t)s];
+      if (!plan_head(p, t + a, y + a, dy + a, b - a, r, h, dst_of(s, &d))) return;
+      grid_one(p, h, win_off ? &w : nullptr, cper.empty() ? nullptr : cper.data());
+      plan_tail(p, h);
     });
     return;
   }
@@ -531,6 +547,7 @@ void plan_all_from(const qlp_bls_params& p, int32_t n_stars, const StarPoints* p
                    std::vector<StarPlanHost>* out, const int64_t* win_off, const double* win_lo,
                    const double* win_hi) {
   out->assign((size_t)n_stars, StarPlanHost());
+  const std::vector<double> cper = p.grid_mode == 1 ? coarse_period_table(p) : std::vector<double>();
   parallel_stars(p, n_stars, [&](int32_t st) {
     const StarPoints& q = pts[st];
     StarPlanHost& s = (*out)[(size_t)st];
@@ -557,7 +574,7 @@ void plan_all_from(const qlp_bls_params& p, int32_t n_stars, const StarPoints* p
       w.hi = win_hi + win_off[st];
       w.n = win_off[st + 1] - win_off[st];
     }
-    grid_one(p, s, win_off ? &w : nullptr);
+    grid_one(p, s, win_off ? &w : nullptr, cper.empty() ? nullptr : cper.data());
     double edges = 0.0, dmax = 0.0;
     if (!tail_grid(p, s, &edges, &dmax)) return;
     s.w_spread = q.w_spread;
