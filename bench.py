@@ -52,7 +52,7 @@ def _args():
     ap.add_argument("--cpu-sample-stars", type=int, default=256)
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-multi", action="store_true", help="skip the multi-sector search line")
-    ap.add_argument("--sum-mode", default="fixed", choices=["fixed", "comp", "plain"],
+    ap.add_argument("--sum-mode", default="fixed", choices=["fixed", "fixed64", "comp", "plain"],
                     help="cell-path sums: exact integers (default), compensated FP32, plain FP32")
     ap.add_argument("--workload", default="uneven", choices=["uneven", "multi_sector"],
                     help="the timed batch: uneven single-sector stars (default) or multi-sector stars "
@@ -149,14 +149,18 @@ CELL_SMEM_BYTES_PER_EDGE = {0: 44, 1: 60}
 #    (edge position in 24.40 fixed point 3, cell and offset 2, comparison and
 #    guard-band test 3, next-cell select 1, two 64-bit accumulations of group
 #    base + local prefix 5) and 28 shared-memory bytes gathered (dt 4, local
-#    prefix 8, group base 16); per box start bin of the sweep: 76 lane operations
-#    (running sums over 11 bins 22, then per width of 3..11 bins the score and
-#    the division-free comparison 6) and 88 shared-memory bytes (11 histogram
-#    records of 8 bytes).
+#    prefix 8, group base 16) on the 64-bit table; on the 32-bit table 13 lane
+#    operations (two 64-bit accumulations of the prefix pair 4) and 12 bytes (dt 4,
+#    prefix pair 8); per box start bin of the sweep: 76 lane operations (running
+#    sums over 11 bins 22, then per width of 3..11 bins the score and the
+#    division-free comparison 6) and 48 shared-memory bytes (two adjacent starts
+#    read the 12 histogram records of 8 bytes they need between them).
 EXACT_OPS_PER_EDGE = 14
 EXACT_SMEM_BYTES_PER_EDGE = 28
+EXACT32_OPS_PER_EDGE = 13
+EXACT32_SMEM_BYTES_PER_EDGE = 12
 EXACT_OPS_PER_BIN = 76
-EXACT_SMEM_BYTES_PER_BIN = 88
+EXACT_SMEM_BYTES_PER_BIN = 48
 FP32_LANES_PER_SM = 128
 SMEM_BYTES_PER_CLK_PER_SM = 128
 N_SMS = 152
@@ -575,7 +579,7 @@ def main():
     stream = torch.cuda.current_stream()
     # launch settings from the autotuner (timed on a sample of the batch; untimed here)
     t0 = time.perf_counter()
-    params = qlpbls.Params(method=args.method, sum_mode={"fixed": qlpbls.SUM_FIXED, "comp": qlpbls.SUM_COMP,
+    params = qlpbls.Params(method=args.method, sum_mode={"fixed": qlpbls.SUM_FIXED, "fixed64": qlpbls.SUM_FIXED64, "comp": qlpbls.SUM_COMP,
                                                          "plain": qlpbls.SUM_PLAIN}[args.sum_mode])
     if not args.no_tune:
         params, _ = qlpbls.autotune(batch.offsets, batch.t, batch.y, batch.dy, batch.rho, batch.rstar,
@@ -669,14 +673,17 @@ def main():
     peak_smem = N_SMS * SMEM_BYTES_PER_CLK_PER_SM * sm_clock / 1e9  # GB/s
     cells_dominant = plan.work_cells >= plan.work_points
     if kernel_id == 2:
-        ops = plan.exact_edges * EXACT_OPS_PER_EDGE + plan.exact_bins * EXACT_OPS_PER_BIN
+        e64 = plan.exact_edges - plan.narrow_edges
+        ops = (e64 * EXACT_OPS_PER_EDGE + plan.narrow_edges * EXACT32_OPS_PER_EDGE
+               + plan.exact_bins * EXACT_OPS_PER_BIN)
         achieved = ops / (ms_kernel * 1e-3) / 1e12
-        smem_gbs = (plan.exact_edges * EXACT_SMEM_BYTES_PER_EDGE
+        smem_gbs = (e64 * EXACT_SMEM_BYTES_PER_EDGE + plan.narrow_edges * EXACT32_SMEM_BYTES_PER_EDGE
                     + plan.exact_bins * EXACT_SMEM_BYTES_PER_BIN) / (ms_kernel * 1e-3) / 1e9
         kernel = "cells_fixed_kernel (exact cell path; CUDA events around the launch inside the graph)"
-        unit_note = (f"{plan.exact_edges:.4e} bin edges x {EXACT_OPS_PER_EDGE} lane ops "
-                     f"({EXACT_SMEM_BYTES_PER_EDGE} shared bytes) + {plan.exact_bins:.4e} box start "
-                     f"bins x {EXACT_OPS_PER_BIN} ({EXACT_SMEM_BYTES_PER_BIN} bytes) per launch")
+        unit_note = (f"{plan.narrow_edges:.4e} bin edges on 32-bit tables x {EXACT32_OPS_PER_EDGE} lane ops "
+                     f"({EXACT32_SMEM_BYTES_PER_EDGE} shared bytes) + {e64:.4e} on 64-bit tables x "
+                     f"{EXACT_OPS_PER_EDGE} ({EXACT_SMEM_BYTES_PER_EDGE} bytes) + {plan.exact_bins:.4e} box "
+                     f"start bins x {EXACT_OPS_PER_BIN} ({EXACT_SMEM_BYTES_PER_BIN} bytes) per launch")
     elif cells_dominant:
         ops = plan.edges * CELL_OPS_PER_EDGE[params.sum_mode]
         achieved = ops / (ms_search * 1e-3) / 1e12
@@ -744,11 +751,12 @@ def main():
                                          "sample_stars": None if args.no_tune else args.tune_sample,
                                          "seconds": t_tune},
                            "launch": "CUDA graphs (search, S/N) per step",
-                           "sum_mode": ["PLAIN", "COMP", "FIXED"][params.sum_mode],
+                           "sum_mode": ["PLAIN", "COMP", "FIXED", "FIXED64"][params.sum_mode],
                            "l2": "inputs larger than L2 (light curves "
                            f"{plan.n_points * 24 / 1e6:.0f} MB FP64)", "parallelism": f"replicas x{world}"},
                 "ms_search": ms_search, "ms_kernel": ms_kernel,
                 "exact_path_stars": plan.n_exact_stars,
+                "exact_path_32bit_table_stars": plan.n_narrow_stars,
                 # per step: S/N, and per search path in use its preparation and search kernels
                 "gpu_launches": args.steps * (1 + 2 * (plan.work_points > 0)
                                               + 2 * (plan.n_cell_stars > plan.n_exact_stars)

@@ -76,12 +76,19 @@ extern "C" {
 #define QLP_SUM_COMP    1  /* FP32 sums with the rounding error of every shared-memory add
                               captured exactly (TwoSum) and added back (compensated) */
 #define QLP_SUM_FIXED   2  /* exact sums (default): per star the weights w and w (y - ybar) are
-                              rounded once to integers, round(w 2^kw) and round(w d 2^ky) with
-                              per-star scales that keep 32 consecutive points below 2^30, and
-                              every bin and box sum is an exact 64-bit integer sum of those; the
-                              box sums reach FP32 as double-float (hi, lo) differences. Used on
-                              the cell path for stars whose whole table fits in shared memory;
-                              the per-point path and time-windowed stars use QLP_SUM_COMP. */
+                              rounded once to integers and every bin and box sum is an exact
+                              integer sum of those; the chosen box's s, r and 1 - r reach FP32
+                              as double-float (hi, lo) numbers. Two table widths: a star whose
+                              whole table fits in shared memory, with at most 65,536 points and
+                              a running sum of w d that stays within 64 times its largest
+                              single |w d|, takes 32-bit prefix sums of round(w F), F = 2^32 -
+                              2^17 (r = the ratio of two integer sums), and of round(w d 2^ky),
+                              ky the largest with every prefix below 2^30; the other stars
+                              take round(w 2^kw) and round(w d 2^ky) with per-star scales that
+                              keep 32 consecutive points below 2^30, summed in 64 bits. Used on
+                              the cell path (whole tables or time windows); the per-point path
+                              uses QLP_SUM_COMP. */
+#define QLP_SUM_FIXED64 3  /* as QLP_SUM_FIXED with the 64-bit tables for every star */
 
 #define QLP_MAD_RAW     0  /* sigma_SR = 1.4826 median|SR - median(SR)| (the paper's wording) */
 #define QLP_MAD_RESID   1  /* same on the detrended residual SR - trend */
@@ -217,6 +224,17 @@ int qlp_bls_plan_stats(const qlp_bls_plan_t* plan, double* work_points, double* 
  */
 int qlp_bls_plan_exact_stats(const qlp_bls_plan_t* plan, int32_t* n_exact_stars, double* exact_edges,
                              double* exact_bins);
+
+/*
+ * qlp_bls_plan_narrow_stats -- of the exact path's stars, those whose table holds
+ * 32-bit prefix sums (QLP_SUM_FIXED; see there for which stars). Any output may be NULL.
+ *  n_narrow_stars  stars on the 32-bit table (counted in n_exact_stars too).
+ *  narrow_edges    bin edges those stars evaluate (counted in exact_edges too).
+ *  narrow_bins     sum of nbins over their trial frequencies (counted in exact_bins too).
+ * Returns QLP_ERR_ARG for a NULL plan.
+ */
+int qlp_bls_plan_narrow_stats(const qlp_bls_plan_t* plan, int32_t* n_narrow_stars, double* narrow_edges,
+                              double* narrow_bins);
 
 /*
  * qlp_bls_plan_times -- measurement aid (no counterpart in the paper): wall-clock

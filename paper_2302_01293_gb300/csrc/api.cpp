@@ -173,6 +173,8 @@ struct qlp_bls_plan {
   int32_t fixed_nb_max = 0;       // largest bin count of an exact-path star
   double edges_fixed = 0.0;
   double bins_fixed = 0.0;       // sum of nbins over the exact path's frequencies
+  int32_t n_narrow_stars = 0;    // of the exact path's stars, those on the 32-bit table
+  double edges_narrow = 0.0, bins_narrow = 0.0;
   double times[4] = {};          // seconds: host grid, host staging, device allocation, upload
   // device
   StarDev* d_stars = nullptr;
@@ -287,7 +289,7 @@ static int check_params(const qlp_bls_params& p) {
       !(p.qmax_fac >= p.qmin_fac) || !(p.pmin_aR > 0) || !(p.gap_days > 0) || !(p.rho_default > 0) ||
       p.nbins_cap < 2)
     return QLP_ERR_ARG;
-  if (p.phase_mode < 0 || p.phase_mode > 2 || p.sum_mode < 0 || p.sum_mode > 2 || p.mad_mode < 0 ||
+  if (p.phase_mode < 0 || p.phase_mode > 2 || p.sum_mode < 0 || p.sum_mode > 3 || p.mad_mode < 0 ||
       p.mad_mode > 1 || p.tile_points < 0 || p.chunk_freqs < 0 || p.method < 0 || p.method > 2 ||
       p.grid_mode < 0 || p.grid_mode > 1 || p.cell_window < 0 || p.bin_mode < 0 || p.bin_mode > 1 ||
       p.work_loop_bound < 0 ||
@@ -503,7 +505,8 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
     // point would coarsen every other point's weight); the whole table and the
     // warps' rings in shared memory, or else windows of the table (bin sums through
     // a global workspace)
-    const bool fixed_ok = p.sum_mode == QLP_SUM_FIXED && p.bin_mode == QLP_BIN_SHARED && h.nbins_min >= 32 &&
+    const bool fixed_ok = (p.sum_mode == QLP_SUM_FIXED || p.sum_mode == QLP_SUM_FIXED64) &&
+                          p.bin_mode == QLP_BIN_SHARED && h.nbins_min >= 32 &&
                           h.w_spread <= 256.0 && h.wd_spread <= 256.0 &&
                           h.baseline * h.freqs.back() <= 16384.0 && h.n_valid <= ((int64_t)1 << 21) &&
                           (size_t)32 * 16 * ((h.nbins_max + 31) / 32) <= (size_t)kFixedWsBlock * 16;
@@ -584,6 +587,16 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
       d.win_cells = cwin[(size_t)s].cells;
       d.win_ovl = cwin[(size_t)s].ovl;
       d.win_cap = cwin[(size_t)s].cap;
+      // the 32-bit exact table: whole table, at most 2^16 points (the w scale F leaves
+      // 2^17 for the roundings), the running sum of w d within 64 times the largest
+      // |w d|, so that its y scale (2^-30 of the running sum's range) is at most 4 times
+      // coarser than the 64-bit table's (2^-25 of the largest |w d|); a white-noise star
+      // of N points reaches about sqrt(N) / 4 of it
+      d.narrow = (d.method == kMethodFixed && d.n_win <= 1 && p.sum_mode == QLP_SUM_FIXED &&
+                  h.n_valid <= 65536 && h.y_exc > 0.0 && h.y_exc <= 64.0 * h.wd_max)
+                     ? 1
+                     : 0;
+      d.y_exc = h.y_exc;
       if (d.n_win > 1) pl->n_windowed++;
       d.cell_off = ncell;
       d.base_off = nbase;
@@ -599,6 +612,11 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
         pl->fixed_nb_max = std::max(pl->fixed_nb_max, h.nbins_max);
         pl->edges_fixed += h.cells_work;
         pl->bins_fixed += h.nbins_sum;
+        if (d.narrow) {
+          pl->n_narrow_stars++;
+          pl->edges_narrow += h.cells_work;
+          pl->bins_narrow += h.nbins_sum;
+        }
       } else {
         cells_cap = std::max<int64_t>(cells_cap, h.n_cells + 1);
         nb_c = std::max(nb_c, h.nbins_max);
@@ -874,6 +892,15 @@ int qlp_bls_plan_exact_stats(const qlp_bls_plan_t* pl, int32_t* n_exact_stars, d
   if (n_exact_stars) *n_exact_stars = pl->n_fixed_stars;
   if (exact_edges) *exact_edges = pl->edges_fixed;
   if (exact_bins) *exact_bins = pl->bins_fixed;
+  return QLP_OK;
+}
+
+int qlp_bls_plan_narrow_stats(const qlp_bls_plan_t* pl, int32_t* n_narrow_stars, double* narrow_edges,
+                              double* narrow_bins) {
+  if (!pl) return QLP_ERR_ARG;
+  if (n_narrow_stars) *n_narrow_stars = pl->n_narrow_stars;
+  if (narrow_edges) *narrow_edges = pl->edges_narrow;
+  if (narrow_bins) *narrow_bins = pl->bins_narrow;
   return QLP_OK;
 }
 

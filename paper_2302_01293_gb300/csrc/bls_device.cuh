@@ -147,6 +147,16 @@ __device__ __forceinline__ float df_div_to_float(DF x, DF y) {
   return __fadd_rn(q, __fdiv_rn(rem, y.hi));
 }
 
+// x / y as a double-float number: the same quotient and one correction, kept as the
+// pair's low part.
+__device__ __forceinline__ DF df_div(DF x, DF y) {
+  const float q = __fdiv_rn(x.hi, y.hi);
+  const float p = __fmul_rn(q, y.hi);
+  const float pe = __fmaf_rn(q, y.hi, -p);
+  const float rem = __fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(x.hi, p), pe), x.lo), __fmul_rn(q, y.lo));
+  return df_fast_two_sum(q, __fdiv_rn(rem, y.hi));
+}
+
 // An integer of magnitude below 2^48 as an exact pair, times 2^-k (k in [-100, 100]).
 __device__ __forceinline__ DF df_from_ll_scaled(long long v, int k) {
   const float hi = __ll2float_rn(v);

@@ -32,10 +32,9 @@
 // asynchronous copies on an mbarrier); warps take the item's frequencies one at a time.
 // Per frequency the bins are handled 32 at a time (lane = bin): the lanes' S
 // values become U, the exact differences H[x] = U[x + 1] - U[x] are scaled to FP32
-// (w, w d) pairs and written to a per-warp ring of two 32-bin blocks (plus a copy
-// of the even block behind the odd one, so that block i and i+1 are always
-// contiguous); the sweep of the boxes starting in block i - 2 runs once block
-// i - 1 is in the ring. Stars whose table does not fit in shared memory take
+// (w, w d) pairs and written to a per-warp ring of four 32-bin blocks (bin x at
+// x mod 128); the sweep of the boxes starting in blocks 2j and 2j + 1 (two start
+// bins per lane) runs once block 2j + 2 is in the ring. Stars whose table does not fit in shared memory take
 // their edges window by window into a global workspace first (windowed_item).
 #include <cuda_runtime.h>
 
@@ -46,8 +45,10 @@
 
 namespace qlp {
 
-constexpr int kRing = 96;  // float2 per warp: blocks 2i and 2i+1, then a copy of block 2i
+constexpr int kRing = 128;  // float2 per warp: H of the last four blocks of 32 bins, at (bin mod 128)
 constexpr long long kLocBias = 1ll << 30;  // added to the w d local parts of the cell table
+constexpr long long kNarrowBias = 1ll << 31;  // added to the w d prefix sums of the 32-bit table
+constexpr double kNarrowF = 4294836224.0;     // 2^32 - 2^17: the w scale of the 32-bit table
 // prefix sums at a cell: the group base plus the local parts, widened from 32 bits with
 // a zero high word (the w d part still carries kLocBias, taken off per sum of edges)
 __device__ __forceinline__ void add_cell(long long& aw, long long& ay, const longlong2& bs, const int2& lc) {
@@ -147,8 +148,22 @@ __global__ void __launch_bounds__(512) prep_fixed_kernel(const PrepFixedArgs a) 
   }
   mw = block_max(mw, red);
   md = block_max(md, red);
-  const int kw = fixed_exponent(mw), ky = fixed_exponent(md);
-  const double pw = ldexp(1.0, kw), py = ldexp(1.0, ky);
+  // 64-bit table: scales that keep 32 consecutive points below 2^30. 32-bit table:
+  // w_int = round(w F) with F = 2^32 - 2^17, so that the N <= 2^16 roundings leave the
+  // total below 2^32 (r is then the ratio of two integer sums), and the largest y scale
+  // that keeps every point's |y_int| (this kernel's largest |w d|) and every prefix sum
+  // of y_int (the planner's largest running sum; this kernel's lies within 2^-9 of it,
+  // and the roundings add at most 2^15) below 2^30
+  const bool narrow = st.narrow != 0;
+  int kw = fixed_exponent(mw), ky = fixed_exponent(md);
+  if (narrow) {
+    int e1 = 0, e2 = 0;
+    frexp(st.y_exc * 1.00390625, &e1);  // y_exc (1 + 2^-8) < 2^e1
+    frexp(md * 1.00390625, &e2);
+    kw = 0;
+    ky = max(-100, min(30 - max(e1, e2), 100));
+  }
+  const double pw = narrow ? kNarrowF : ldexp(1.0, kw), py = ldexp(1.0, ky);
 
   // exact prefix sums of the integer weights: contiguous segment per thread,
   // exclusive scan of the segment totals
@@ -162,7 +177,7 @@ __global__ void __launch_bounds__(512) prep_fixed_kernel(const PrepFixedArgs a) 
     sy += yi;
     // both below 2^25 in magnitude: kept in the point's cache slot (its 1/dy^2 is no
     // longer needed) for the prefix pass below
-    if (cache) reinterpret_cast<int2*>(s_inv)[i] = make_int2((int)wi, (int)yi);
+    if (cache) reinterpret_cast<int2*>(s_inv)[i] = make_int2((int)(uint32_t)wi, (int)yi);
   }
   scan_w[tid] = sw;
   scan_y[tid] = sy;
@@ -198,6 +213,8 @@ __global__ void __launch_bounds__(512) prep_fixed_kernel(const PrepFixedArgs a) 
       f.y_tot = ry;
       f.kw = kw;
       f.ky = ky;
+      f.scw = narrow ? (float)(1.0 / (double)rw) : __int_as_float((127 - kw) << 23);  // 1 / w_tot or 2^-kw
+      f.narrow = narrow ? 1 : 0;
       a.fx[s] = f;
     }
   }
@@ -207,7 +224,7 @@ __global__ void __launch_bounds__(512) prep_fixed_kernel(const PrepFixedArgs a) 
     a.ipre[st.cpre_off + i] = make_longlong2(cw, cy);
     if (cache) {
       const int2 v = reinterpret_cast<const int2*>(s_inv)[i];
-      cw += v.x;
+      cw += (long long)(uint32_t)v.x;
       cy += v.y;
     } else {
       const double w = inv_of(i) * rws;
@@ -239,6 +256,10 @@ __global__ void __launch_bounds__(512) prep_fixed_kernel(const PrepFixedArgs a) 
     }
     a.dt[st.cell_off + u] = q;
     const longlong2 c = a.ipre[st.cpre_off + f];
+    if (narrow) {  // the prefix sums themselves: w below 2^32, |y| below 2^30 + 2^15, biased by 2^31
+      a.loc[st.cell_off + u] = make_int2((int)(uint32_t)c.x, (int)(uint32_t)(c.y + kNarrowBias));
+      continue;
+    }
     const longlong2 cb = a.ipre[st.cpre_off + first[u & ~31]];
     // at most 31 points of weights below 2^25 lie between the group start and the
     // cell: both local parts are below 2^30 in magnitude
@@ -317,32 +338,46 @@ uint32_t fixed_prep_smem_bytes(int n_pts) { return prep_fixed_smem(n_pts); }
 
 // ------------------------------------------------------------------ K2x
 
-// Box sweep of one start bin k over the running sums of its next bins (rb[o] = H[k + o]):
-// every width w = o + 1 present is scored s^2 / (r (1 - r)) for 0 < r < 1 and compared
-// division-free with the lane's best (bs2 = s^2, bd = r (1 - r)) so far; ties go to the
-// narrower box, then the lower k (key = o << 16 | k). ALL: widths 3..11 (the paper's
-// grid; no mask test). The chosen box's s and r come from its exact sums afterwards.
+// Box sweep of the two start bins ka (even) and ka + 1 over the ring (H[x] at ring[x mod
+// 128]): the lane's running sums of both starts are (w, w d) pairs, added as packed FP32
+// pairs; a start at or past the last bin begins at r = 4, so that it never scores (every
+// window of the ring sums to more than -2 in w). Every width w = o + 1 present is scored
+// s^2 / (r (1 - r)) for 0 < r < 1 and compared division-free with the lane's best so far.
+// An exact FP32 tie keeps the lane's earlier candidate: within a pair of blocks the
+// narrower width, then the lower start; across the lane's pairs (disjoint boxes, tied
+// only by a coincidence of their FP32 sums) the earlier pair. Ties between lanes go to
+// the lower duration index, then the lower start (the warp argmax).
 template <bool ALL>
-__device__ __forceinline__ void sweep_start(const float2* rb, bool kin, int k, int mmax, uint32_t wmask,
-                                            float& bs2, float& bd, int& bkey) {
-  float rw = kin ? 0.f : 2.f, ry = 0.f;  // a start past the last bin never scores (r >= 1)
+__device__ __forceinline__ void sweep_pair(const float2* ring, int ka, bool ain, bool bin, int mmax, uint32_t wmask,
+                                           float& bs2, float& bd, int& bkey) {
+  constexpr int NO = ALL ? 11 : 15;
+  auto ld = [&](int t) { return *reinterpret_cast<const float4*>(ring + ((ka + 2 * t) & 127)); };
+  auto score = [&](const float2 acc, int key) {
+    const float dd = __fmaf_rn(-acc.x, acc.x, acc.x);  // r (1 - r)
+    const float s2 = __fmul_rn(acc.y, acc.y);
+    const float lhs = __fmul_rn(s2, bd), rhs = __fmul_rn(bs2, dd);
+    const bool better = dd > 0.f && lhs > rhs;
+    bs2 = better ? s2 : bs2;
+    bd = better ? dd : bd;
+    bkey = better ? key : bkey;
+  };
+  float2 A = make_float2(ain ? 0.f : 4.f, 0.f), B = make_float2(bin ? 0.f : 4.f, 0.f);
+  float4 cur = ld(0);
 #pragma unroll
-  for (int o = 0; o < (ALL ? 11 : 15); ++o) {
+  for (int o = 0; o < NO; ++o) {
     if (ALL || o < mmax) {
-      const float2 hv = rb[o];
-      rw = __fadd_rn(rw, hv.x);
-      ry = __fadd_rn(ry, hv.y);
+      if ((o & 1) == 0) {  // A += H[ka + o], B += H[ka + o + 1]
+        A = __fadd2_rn(A, make_float2(cur.x, cur.y));
+        B = __fadd2_rn(B, make_float2(cur.z, cur.w));
+      } else {
+        const float4 nxt = ld((o + 1) >> 1);
+        A = __fadd2_rn(A, make_float2(cur.z, cur.w));
+        B = __fadd2_rn(B, make_float2(nxt.x, nxt.y));
+        cur = nxt;
+      }
       if (ALL ? o >= 2 : ((wmask >> o) & 1u) != 0u) {
-        const float dd = __fmaf_rn(-rw, rw, rw);  // r (1 - r)
-        const float s2 = __fmul_rn(ry, ry);
-        const float lhs = __fmul_rn(s2, bd), rhs = __fmul_rn(bs2, dd);
-        const int key = (o << 16) | k;
-        // 0 < r < 1 exactly when r - r^2 > 0: r is a sum of non-negative weights, and
-        // fma(-r, r, r) is r (1 - r) rounded once, positive for every float in (0, 1)
-        const bool better = dd > 0.f && (lhs > rhs || (lhs == rhs && key < bkey));
-        bs2 = better ? s2 : bs2;
-        bd = better ? dd : bd;
-        bkey = better ? key : bkey;
+        score(A, (o << 16) | ka);
+        score(B, (o << 16) | (ka + 1));
       }
     }
   }
@@ -361,7 +396,7 @@ __device__ __forceinline__ longlong2* warp_row(const FixedArgs& a) {
 // The row srow holds the exact bin sums S of the frequency (the window passes'
 // workspace row when WS, else this warp's row (warp_row), written here block by block), so that
 // the box the FP32 sweep chose is scored once more from its exact integer sums.
-template <bool WS>
+template <bool WS, bool NARROW>
 __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, const FreqRec& R,
                                               const FixedStar& fx, const unsigned char* smem,
                                               uint32_t loc_off, uint32_t base_off, int nc, float2* ring,
@@ -389,9 +424,10 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
   long long pw = 0, py = 0;    // U of the previous block
   float bs2 = 0.f, bd = 1.f;   // best box of this lane: s^2, r (1 - r) and its key
   int bkey = 0x7fffffff;
-  // block i: U of bins 32 i + lane; then the histogram of block i - 1 and the
-  // sweep of block i - 2 (boxes of up to 15 bins starting in it)
-  for (int i = 0; i <= nblk + 1; ++i) {
+  // block i: U of bins 32 i + lane; then the histogram of block i - 1 and, for odd
+  // i >= 3, the sweep of blocks i - 3 and i - 2 (boxes of up to 15 bins starting in them)
+  const int i_last = (((nblk + 1) >> 1) << 1) + 1;  // the sweep of the last pair of blocks
+  for (int i = 0; i <= i_last; ++i) {
     const int x = (i << 5) + lane;
     long long uw = 0, uy = 0;
     if constexpr (WS) {  // bin sums from the window passes
@@ -443,8 +479,15 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
           nmin = min(nmin, dq - fr + band_q);
           const int v = u + (dq < fr ? 1 : 0);  // past the cell's point if it lies before tau_G
           const int2 lc = *reinterpret_cast<const int2*>(smem + loc_off + (uint32_t)v * st8);
-          const longlong2 bs = *reinterpret_cast<const longlong2*>(smem + base_off + (uint32_t)(v >> 5) * st16);
-          if (valid) add_cell(aw, ay, bs, lc);
+          if constexpr (NARROW) {  // the 32-bit prefix sums themselves
+            if (valid) {
+              aw += (long long)(uint32_t)lc.x;
+              ay += (long long)(uint32_t)lc.y;
+            }
+          } else {
+            const longlong2 bs = *reinterpret_cast<const longlong2*>(smem + base_off + (uint32_t)(v >> 5) * st16);
+            if (valid) add_cell(aw, ay, bs, lc);
+          }
         };
         int c = 0;
         for (; c + 4 < cnt; c += 4) {
@@ -461,7 +504,7 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
         }
         const bool last = G0 + (cnt - 1) * gstep <= g_end;
         edge(X, last, true);
-        ay -= (long long)(cnt - (last ? 0 : 1)) * kLocBias;  // the bias of the edges taken
+        ay -= (long long)(cnt - (last ? 0 : 1)) * (NARROW ? kNarrowBias : kLocBias);  // the bias of the edges taken
         bool near = nmin <= 2u * band_q;  // an edge within the guard band of its cell's point
         if (split) {  // warp-uniform: add the other phases of each bin into lanes 0 .. r-1
           for (int q = 1; q < P; ++q) {
@@ -496,9 +539,14 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
                 sel = exact_before(tp, gidx[u], f, nb, g);
               const int v = u + sel;
               const int2 lc = reinterpret_cast<const int2*>(smem + loc_off)[v];
-              const longlong2 bs = reinterpret_cast<const longlong2*>(smem + base_off)[v >> 5];
-              add_cell(aw, ay, bs, lc);
-              ay -= kLocBias;
+              if constexpr (NARROW) {
+                aw += (long long)(uint32_t)lc.x;
+                ay += (long long)(uint32_t)lc.y - kNarrowBias;
+              } else {
+                const longlong2 bs = reinterpret_cast<const longlong2*>(smem + base_off)[v >> 5];
+                add_cell(aw, ay, bs, lc);
+                ay -= kLocBias;
+              }
             }
           }
         }
@@ -524,27 +572,21 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
       h0w = uw;
       h0y = uy;
     } else {
-      // histogram of block i - 1: H[x] = U[x + 1] - U[x], exact, then FP32
-      long long nw = __shfl_down_sync(0xffffffffu, pw, 1);
-      long long ny = __shfl_down_sync(0xffffffffu, py, 1);
-      const long long fw = __shfl_sync(0xffffffffu, uw, 0);
-      const long long fy = __shfl_sync(0xffffffffu, uy, 0);
-      if (lane == 31) {
-        nw = fw;
-        ny = fy;
-      }
+      // histogram of block i - 1: H[x] = U[x + 1] - U[x], exact, then FP32. Lane x takes
+      // U[x + 1] from lane x + 1's previous block, lane 31 from lane 0's current one.
+      const int src = (lane + 1) & 31;
+      const long long nw = __shfl_sync(0xffffffffu, lane == 0 ? uw : pw, src);
+      const long long ny = __shfl_sync(0xffffffffu, lane == 0 ? uy : py, src);
       const float2 hv = make_float2(__fmul_rn(__ll2float_rn(nw - pw), scw), __fmul_rn(__ll2float_rn(ny - py), scy));
-      ring[(((i - 1) & 1) << 5) + lane] = hv;
-      if (!((i - 1) & 1)) ring[64 + lane] = hv;
+      ring[(((i - 1) & 3) << 5) + lane] = hv;
     }
     pw = uw;
     py = uy;
     __syncwarp();
-    if (i >= 2) {  // sweep block i - 2: boxes starting at its bins
-      const int k = ((i - 2) << 5) + lane;
-      const float2* rb = ring + (((i - 2) & 1) << 5) + lane;
-      if (all_widths) sweep_start<true>(rb, k < nb, k, mmax, wmask, bs2, bd, bkey);
-      else sweep_start<false>(rb, k < nb, k, mmax, wmask, bs2, bd, bkey);
+    if (i >= 3 && ((i - 3) & 1) == 0) {  // sweep blocks i - 3 and i - 2: boxes starting at their bins
+      const int ka = ((i - 3) << 5) + 2 * lane;
+      if (all_widths) sweep_pair<true>(ring, ka, ka < nb, ka + 1 < nb, mmax, wmask, bs2, bd, bkey);
+      else sweep_pair<false>(ring, ka, ka < nb, ka + 1 < nb, mmax, wmask, bs2, bd, bkey);
     }
     __syncwarp();
   }
@@ -580,11 +622,17 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
     const long long nwrap = (bstar < k2m ? 1 : 0) + (k2 >= nb ? 1 : 0) - (bstar < bk ? 1 : 0);
     const long long dw = a1.x - a0.x + nwrap * fx.w_tot;
     const long long dy = a1.y - a0.y + nwrap * fx.y_tot;
-    // kw lies in [24, 46] on this path: the largest weight is at most 1 and at least
-    // 1/N with N <= 2^21 points, and w_max 2^kw lies in [2^24, 2^25)
-    const int kw = min(max(fx.kw, 0), 62);
-    bb.xr = df_from_ll_scaled(dw, kw);
-    bb.xq = df_from_ll_scaled((1ll << kw) - dw, kw);  // 1 - r
+    if (NARROW) {  // r = dw / w_tot and 1 - r = (w_tot - dw) / w_tot, both sums below 2^32
+      const DF wt = df_from_ll_scaled(fx.w_tot, 0);
+      bb.xr = df_div(df_from_ll_scaled(dw, 0), wt);
+      bb.xq = df_div(df_from_ll_scaled(fx.w_tot - dw, 0), wt);
+    } else {
+      // kw lies in [24, 46] on this path: the largest weight is at most 1 and at least
+      // 1/N with N <= 2^21 points, and w_max 2^kw lies in [2^24, 2^25)
+      const int kw = min(max(fx.kw, 0), 62);
+      bb.xr = df_from_ll_scaled(dw, kw);
+      bb.xq = df_from_ll_scaled((1ll << kw) - dw, kw);  // 1 - r
+    }
     bb.xs = df_from_ll_scaled(dy, fx.ky);
     bb.xv = true;
   }
@@ -708,7 +756,7 @@ __device__ void windowed_item(const FixedArgs& a, const WorkItem& wi, const Star
     }
   }
   __syncthreads();  // every window's sums are in the workspace
-  const float scw = __int_as_float((127 - fx.kw) << 23);
+  const float scw = fx.scw;
   const float scy = __int_as_float((127 - fx.ky) << 23);
   for (int fl = warp; fl < wi.f_count; fl += NW) {
     const int64_t fidx = st.f_off + wi.f_begin + fl;
@@ -724,7 +772,7 @@ __device__ void windowed_item(const FixedArgs& a, const WorkItem& wi, const Star
       }
       continue;
     }
-    run_frequency<true>(a, fidx, R, fx, smem, loc_off, base_off, nc, ring, lane, scw, scy, tp, gidx, st4, st8,
+    run_frequency<true, false>(a, fidx, R, fx, smem, loc_off, base_off, nc, ring, lane, scw, scy, tp, gidx, st4, st8,
                         st16, ws + (size_t)fl * (size_t)stride);
   }
 }
@@ -788,7 +836,9 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
       // cells [0, nb4) and groups [0, ng) by bulk copies (the table starts at a 16-byte
       // boundary: cell_off is a multiple of 4), the rest of the table and the padding by
       // the threads; the two parts do not overlap
-      const int nb4 = (nc + 1) & ~3, ng = (nc >> 5) + 1;
+      // (the 32-bit table has no group bases: its padding cells repeat the sentinel's sums)
+      const bool narrow = fx.narrow != 0;
+      const int nb4 = (nc + 1) & ~3, ng = narrow ? 0 : (nc >> 5) + 1;
       if (threadIdx.x == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the last item's reads
         const uint32_t bytes = (uint32_t)nb4 * 12u + (uint32_t)ng * 16u;
@@ -799,16 +849,18 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
           bulk_g2s(d_dt, a.dt + st.cell_off, (uint32_t)nb4 * 4u, &s_tbar);
           bulk_g2s(d_loc, a.loc + st.cell_off, (uint32_t)nb4 * 8u, &s_tbar);
         }
-        bulk_g2s(d_base, a.base + st.base_off, (uint32_t)ng * 16u, &s_tbar);
+        if (ng > 0) bulk_g2s(d_base, a.base + st.base_off, (uint32_t)ng * 16u, &s_tbar);
       }
       const int2 lnc = a.loc[st.cell_off + nc];
       for (int i = nb4 + (int)threadIdx.x; i < ncp; i += NW * 32) {
         const bool in = i <= nc;
         d_dt[i] = in ? a.dt[st.cell_off + i] : 0xffffffffu;
-        d_loc[i] = in ? a.loc[st.cell_off + i] : ((i >> 5) == (nc >> 5) ? lnc : make_int2(0, (int)kLocBias));
+        d_loc[i] = in ? a.loc[st.cell_off + i]
+                      : ((narrow || (i >> 5) == (nc >> 5)) ? lnc : make_int2(0, (int)kLocBias));
       }
-      for (int i = ng + (int)threadIdx.x; i < (ncp + 31) / 32; i += NW * 32)
-        d_base[i] = make_longlong2(fx.w_tot, fx.y_tot);
+      if (!narrow)
+        for (int i = ng + (int)threadIdx.x; i < (ncp + 31) / 32; i += NW * 32)
+          d_base[i] = make_longlong2(fx.w_tot, fx.y_tot);
       if (threadIdx.x == 0) {  // bounded wait for the copies
         bool ok = false;
         for (uint32_t k = 0; k < kCopyWaitLimit && !ok; ++k) {
@@ -827,8 +879,8 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
       }
       __syncthreads();
     }
-    const float scw = __int_as_float((127 - fx.kw) << 23);  // 2^-kw (|kw| <= 100)
-    const float scy = __int_as_float((127 - fx.ky) << 23);
+    const float scw = fx.scw;  // 2^-kw, or 1 / w_tot on the 32-bit table
+    const float scy = __int_as_float((127 - fx.ky) << 23);  // 2^-ky (|ky| <= 100)
     const double* tp = a.tp + st.pt_off;
     const int32_t* gidx = a.gidx + st.cell_off;
 
@@ -851,8 +903,12 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
         }
         continue;
       }
-      run_frequency<false>(a, fidx, R, fx, smem, loc_off, base_off, nc, ring, lane, scw, scy, tp, gidx, st4, st8,
-                           st16, nullptr);
+      if (fx.narrow)  // block-uniform
+        run_frequency<false, true>(a, fidx, R, fx, smem, loc_off, base_off, nc, ring, lane, scw, scy, tp, gidx, st4,
+                                   st8, st16, nullptr);
+      else
+        run_frequency<false, false>(a, fidx, R, fx, smem, loc_off, base_off, nc, ring, lane, scw, scy, tp, gidx, st4,
+                                    st8, st16, nullptr);
     }
   }
   if (!done && threadIdx.x == 0) atomicOr(a.err, kErrQueueBound);

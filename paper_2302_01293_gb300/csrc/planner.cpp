@@ -298,6 +298,18 @@ void tail_points(StarPlanHost& s) {
     }
     s.w_spread = imax / (isum / (double)m);
     s.wd_spread = dsum > 0.0 ? dmax / (dsum / (double)m) : 0.0;
+    // the running sum of w (y - ybar) and its largest magnitude (it ends near zero).
+    // The device's weighted mean differs from this one by the FP64 sums' rounding,
+    // below 2^-37 max|y| for 2^16 points, which moves every running sum by as much:
+    // an excursion below 2^-28 max|y| is reported as 0 (no 32-bit table)
+    double run = 0.0, exc = 0.0, yabs = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+      run += (yv[i] - ybar) / (dyv[i] * dyv[i]);
+      exc = std::max(exc, std::fabs(run));
+      yabs = std::max(yabs, std::fabs(yv[i]));
+    }
+    s.wd_max = dmax / isum;
+    s.y_exc = (exc / isum >= std::ldexp(yabs, -28)) ? exc / isum : 0.0;
   }
 
   // cell path: smallest spacing, cells just narrower, one point per cell
@@ -537,6 +549,8 @@ StarPoints points_of(StarPlanHost& s) {
   if (!s.points_done) tail_points(s);  // the grid was empty or over the cap
   o.w_spread = s.w_spread;
   o.wd_spread = s.wd_spread;
+  o.wd_max = s.wd_max;
+  o.y_exc = s.y_exc;
   o.cells_ok = s.cells_ok;
   o.cell_h = s.cell_h;
   o.n_cells = s.n_cells;
@@ -579,6 +593,8 @@ void plan_all_from(const qlp_bls_params& p, int32_t n_stars, const StarPoints* p
     if (!tail_grid(p, s, &edges, &dmax)) return;
     s.w_spread = q.w_spread;
     s.wd_spread = q.wd_spread;
+    s.wd_max = q.wd_max;
+    s.y_exc = q.y_exc;
     s.points_done = true;
     if (q.cells_ok) {
       s.cells_ok = true;

@@ -35,6 +35,11 @@ struct StarPlanHost {
   // the largest over the mean (the exact path's integer scale follows the largest)
   double w_spread = 0.0;
   double wd_spread = 0.0;
+  // largest |w (y - ybar)| of a point and largest |sum over the points before t of
+  // w (y - ybar)| over t (normalised weights): the 32-bit exact tables need the
+  // second to stay within a small multiple of the first
+  double wd_max = 0.0;
+  double y_exc = 0.0;
   double ymax = 0.0;               // max over f of T f nbins(f)
   int32_t sturges_nb = 0;
   // cell path: cells of width h (just below the smallest point spacing) hold at
@@ -57,7 +62,7 @@ struct StarPoints {
   bool head_ok = false;
   int64_t n_valid = 0;
   double t_ref = 0.0, baseline = 0.0, pmin = 0.0, pmax = 0.0, rho_kg = 0.0;
-  double w_spread = 0.0, wd_spread = 0.0;
+  double w_spread = 0.0, wd_spread = 0.0, wd_max = 0.0, y_exc = 0.0;
   bool cells_ok = false;
   double cell_h = 0.0;
   int64_t n_cells = 0;

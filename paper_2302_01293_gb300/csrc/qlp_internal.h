@@ -43,6 +43,11 @@ struct StarDev {
   int32_t win_cells;
   int32_t win_ovl;
   int32_t win_cap;     // cells the shared table holds (one window, or the whole table)
+  // exact path, whole table: 1 = the 32-bit table (prefix sums of round(w F) and
+  // round(w d 2^ky) as 32-bit words, no group bases), with y_exc the planner's largest
+  // |prefix of w d| from which the y scale follows; 0 = the 64-bit table
+  int32_t narrow;
+  double y_exc;
 };
 
 constexpr int32_t kMethodPoints = 0;
@@ -114,7 +119,9 @@ struct CellArgs {
 struct FixedStar {
   long long w_tot;   // sum of w_int over the star (the prefix sum at the sentinel cell)
   long long y_tot;   // sum of y_int
-  int32_t kw, ky;
+  int32_t kw, ky;    // w_int = round(w 2^kw) (64-bit table), y_int = round(w d 2^ky)
+  float scw;         // FP32 scale of the w sums: 2^-kw, or 1 / w_tot on the 32-bit table
+  int32_t narrow;    // 1: the star's table is the 32-bit one (w_int = round(w F))
 };
 
 // Per trial frequency of an exact-path star, derived once from (f, q_min) in FP64

@@ -90,7 +90,7 @@ extern "C" int qlp_bls_search_static(const qlp_bls_params* pin, int32_t n, const
   if (!(baseline > 0.0) || !(p.noverlap >= 1.0) || !(p.dlogq > 0.0) || !(p.qmin_fac > 0.0) ||
       !(p.qmax_fac >= p.qmin_fac))
     return QLP_ERR_ARG;
-  if (p.phase_mode < 0 || p.phase_mode > 2 || p.sum_mode < 0 || p.sum_mode > 2) return QLP_ERR_ARG;
+  if (p.phase_mode < 0 || p.phase_mode > 2 || p.sum_mode < 0 || p.sum_mode > 3) return QLP_ERR_ARG;
   // one shared histogram per frequency only: the per-duration variant needs the cell path
   if (p.bin_mode != QLP_BIN_SHARED) return QLP_ERR_UNSUPPORTED;
   // this entry point folds every point; it runs QLP_SUM_FIXED as compensated sums

@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 PHASE_FP64, PHASE_DF, PHASE_FP32 = 0, 1, 2
-SUM_PLAIN, SUM_COMP, SUM_FIXED = 0, 1, 2
+SUM_PLAIN, SUM_COMP, SUM_FIXED, SUM_FIXED64 = 0, 1, 2, 3
 BIN_SHARED, BIN_PER_Q = 0, 1
 MAD_RAW, MAD_RESID = 0, 1
 METHOD_AUTO, METHOD_POINTS, METHOD_CELLS = 0, 1, 2
@@ -131,6 +131,8 @@ def lib():
             L.qlp_bls_plan_stats.restype = ctypes.c_int
             L.qlp_bls_plan_exact_stats.argtypes = [_vp, _P(_i32), _P(_d), _P(_d)]
             L.qlp_bls_plan_exact_stats.restype = ctypes.c_int
+            L.qlp_bls_plan_narrow_stats.argtypes = [_vp, _P(_i32), _P(_d), _P(_d)]
+            L.qlp_bls_plan_narrow_stats.restype = ctypes.c_int
             L.qlp_bls_plan_times.argtypes = [_vp, _P(_d)]
             L.qlp_bls_plan_times.restype = ctypes.c_int
             L.qlp_bls_kernel_timing.argtypes = [_vp, _i32]
@@ -346,6 +348,11 @@ class Plan:
         self.n_exact_stars = int(ne.value)
         self.exact_edges = ee.value
         self.exact_bins = eb.value
+        _check(L.qlp_bls_plan_narrow_stats(self._h, ctypes.byref(ne), ctypes.byref(ee), ctypes.byref(eb)),
+               "qlp_bls_plan_narrow_stats")
+        self.n_narrow_stars = int(ne.value)
+        self.narrow_edges = ee.value
+        self.narrow_bins = eb.value
 
     def alloc_outputs(self):
         import torch

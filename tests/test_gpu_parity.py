@@ -17,6 +17,21 @@ from parity import compare_snr, compare_spectrum, oracle_star, run_gpu
 pytestmark = pytest.mark.gpu
 
 
+def _narrow_expected(batch):
+    """Stars the 32-bit exact table takes (whole-table single-sector stars): the
+    running sum of w (y - ybar) within 64 times the largest |w (y - ybar)| and not
+    below 2^-28 max|y|, at most 65,536 points."""
+    n = 0
+    for s in range(batch.n_stars):
+        t, y, dy = batch.star(s)
+        inv = 1.0 / (dy * dy)
+        ybar = np.sum(inv * y) / np.sum(inv)
+        wd = inv * (y - ybar) / np.sum(inv)
+        exc = np.max(np.abs(np.cumsum(wd)))
+        n += int(len(t) <= 65536 and exc <= 64.0 * np.max(np.abs(wd)) and exc >= 2.0 ** -28 * np.max(np.abs(y)))
+    return n
+
+
 def _check_batch(batch, params, stars=None, with_snr=True):
     g = run_gpu(batch, params, with_snr=with_snr)
     assert g["flags"] == 0
@@ -35,7 +50,7 @@ def _check_batch(batch, params, stars=None, with_snr=True):
 
 
 @pytest.mark.parametrize("phase", [qlpbls.PHASE_FP64, qlpbls.PHASE_DF])
-@pytest.mark.parametrize("summ", [qlpbls.SUM_PLAIN, qlpbls.SUM_COMP, qlpbls.SUM_FIXED])
+@pytest.mark.parametrize("summ", [qlpbls.SUM_PLAIN, qlpbls.SUM_COMP, qlpbls.SUM_FIXED, qlpbls.SUM_FIXED64])
 def test_single_star(gpu_lib, phase, summ):
     b = synth.single_star()
     g, stats = _check_batch(b, qlpbls.Params(phase_mode=phase, sum_mode=summ))
@@ -44,19 +59,42 @@ def test_single_star(gpu_lib, phase, summ):
 
 
 @pytest.mark.parametrize("method", [qlpbls.METHOD_POINTS, qlpbls.METHOD_CELLS])
-@pytest.mark.parametrize("summ", [qlpbls.SUM_PLAIN, qlpbls.SUM_COMP, qlpbls.SUM_FIXED])
+@pytest.mark.parametrize("summ", [qlpbls.SUM_PLAIN, qlpbls.SUM_COMP, qlpbls.SUM_FIXED, qlpbls.SUM_FIXED64])
 def test_uneven_batch_both_paths(gpu_lib, method, summ):
     b = synth.uneven_single_sector(n_stars=5, seed=22)
     g, _ = _check_batch(b, qlpbls.Params(method=method, sum_mode=summ))
-    exact = method == qlpbls.METHOD_CELLS and summ == qlpbls.SUM_FIXED
+    exact = method == qlpbls.METHOD_CELLS and summ in (qlpbls.SUM_FIXED, qlpbls.SUM_FIXED64)
     assert g["plan"].n_exact_stars == (5 if exact else 0)
+    assert g["plan"].n_narrow_stars == (_narrow_expected(b) if exact and summ == qlpbls.SUM_FIXED else 0)
 
 
 def test_exact_cell_path_is_the_default(gpu_lib):
-    # exact integer sums on the cell path for every star whose table fits shared memory
+    # exact integer sums on the cell path for every star whose table fits shared memory,
+    # most of them (white noise, shallow or short transits) on the 32-bit table
     b = synth.uneven_single_sector(n_stars=8, seed=27)
     g, _ = _check_batch(b, qlpbls.Params())
     assert g["plan"].n_exact_stars == 8 and g["plan"].exact_edges == g["plan"].edges
+    assert g["plan"].n_narrow_stars == _narrow_expected(b) >= 6
+
+
+def test_slow_trend_takes_the_64_bit_table(gpu_lib):
+    # a linear flux trend of 10 sigma across the sector makes the running sum of
+    # w (y - ybar) reach about N / 8 times its largest single term, beyond the 32-bit
+    # table's 64: that star keeps the 64-bit table, the others take the 32-bit one,
+    # and all three match the oracle; the same batch with every star on the 64-bit
+    # table gives the same boxes
+    b = synth.uneven_single_sector(n_stars=3, seed=34)
+    y = b.y.copy()
+    a, e = int(b.offsets[1]), int(b.offsets[2])
+    t = b.t[a:e]
+    y[a:e] += 10.0 * b.dy[a:e] * (t - t.mean()) / (t.max() - t.min())
+    b2 = synth.Batch(b.offsets, b.t, y, b.dy, b.rho, b.rstar, b.inj, b.period, b.t0, b.depth, b.duration, "trend")
+    g, _ = _check_batch(b2, qlpbls.Params())
+    assert g["plan"].n_exact_stars == 3 and g["plan"].n_narrow_stars == _narrow_expected(b2) == _narrow_expected(b) - 1
+    g64, _ = _check_batch(b2, qlpbls.Params(sum_mode=qlpbls.SUM_FIXED64))
+    assert g64["plan"].n_exact_stars == 3 and g64["plan"].n_narrow_stars == 0
+    for k in ("qidx", "kbin"):
+        assert np.mean(g[k] == g64[k]) > 0.999
 
 
 def test_exact_path_falls_back_on_an_extreme_point(gpu_lib):
