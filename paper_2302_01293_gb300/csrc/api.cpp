@@ -518,13 +518,13 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
         int64_t c = p.cell_window;
         if (c <= 0) {  // the largest multiple of 32 whose staged window fits
           c = 32;
-          while (fixed_smem_bytes((int)(c + 32 + F.ovl + 34)) <= (size_t)budget) c += 32;
+          while (fixed_window_smem_bytes((int)(c + 32 + F.ovl + 34)) <= (size_t)budget) c += 32;
         }
         F.cells = (int32_t)c;
         F.cap = (int32_t)std::min<int64_t>(h.n_cells + 1, c + F.ovl + 33);
         F.n_win = (int32_t)((h.n_cells + c - 1) / c);
       }
-      if ((size_t)fixed_smem_bytes(F.cap + 1) <= (size_t)budget) {
+      if ((size_t)(F.n_win > 1 ? fixed_window_smem_bytes(F.cap + 1) : fixed_smem_bytes(F.cap + 1)) <= (size_t)budget) {
         method[(size_t)s] = kMethodFixed;
         W = F;
         continue;
@@ -555,7 +555,8 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   int32_t max_npts = 0, nb_pp = 0, nb_c = 0;
   int64_t cells_cap = 0;
   std::vector<int32_t> cell_stars, fixed_stars;
-  int64_t fixed_ncs = 0;
+  int64_t fixed_ncs = 0;   // cells (with the sentinel) of the largest whole table
+  size_t fixed_wsmem = 0;  // shared memory of the largest time window
   for (int32_t s = 0; s < n_stars; ++s) {
     const StarPlanHost& h = sp[(size_t)s];
     StarDev& d = stars[(size_t)s];
@@ -607,7 +608,10 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
       if (d.method == kMethodFixed) {
         fixed_stars.push_back(s);
         pl->fixed_max_pts = std::max(pl->fixed_max_pts, d.n_pts);
-        fixed_ncs = std::max<int64_t>(fixed_ncs, d.n_win > 1 ? (int64_t)d.win_cap + 1 : h.n_cells + 1);
+        if (d.n_win > 1)
+          fixed_wsmem = std::max<size_t>(fixed_wsmem, fixed_window_smem_bytes(d.win_cap + 1));
+        else
+          fixed_ncs = std::max<int64_t>(fixed_ncs, h.n_cells + 1);
         if (d.n_win > 1) pl->fixed_windowed = true;
         pl->fixed_nb_max = std::max(pl->fixed_nb_max, h.nbins_max);
         pl->edges_fixed += h.cells_work;
@@ -681,7 +685,7 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
     pl->c_blocks = sms * cper;
   }
   if (!fixed_stars.empty()) {
-    pl->f_smem = fixed_smem_bytes((int)fixed_ncs);
+    pl->f_smem = std::max<size_t>(fixed_ncs > 0 ? fixed_smem_bytes((int)fixed_ncs) : 0, fixed_wsmem);
     const int fper = fixed_blocks_per_sm(pl->f_smem);
     if (fper < 1) { delete pl; return QLP_ERR_UNSUPPORTED; }
     pl->f_blocks = sms * fper;

@@ -652,7 +652,8 @@ __device__ void windowed_item(const FixedArgs& a, const WorkItem& wi, const Star
   const int nc = st.n_cells;
   const int cap = st.win_cap + 1;  // staged cells of a window, plus one past its end
   const uint32_t loc_off = fixed_loc_off(cap), base_off = fixed_base_off(cap);
-  float2* ring = reinterpret_cast<float2*>(smem + fixed_ring_off(cap)) + warp * kRing;
+  // pass B reads the workspace rows only: its rings overlay the window's table
+  float2* ring = reinterpret_cast<float2*>(smem) + warp * kRing;
   const int stride = wi.pad0;      // workspace row length (bins)
   longlong2* ws = a.ws + (size_t)blockIdx.x * (size_t)a.ws_block;
   const double h = st.h;
@@ -915,6 +916,9 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
 }
 
 uint32_t fixed_smem_bytes(int ncs) { return fixed_ring_off(ncs + kPadCells) + (uint32_t)kFixedWarps * kRing * 8u; }
+uint32_t fixed_window_smem_bytes(int ncs) {
+  return fixed_ring_off(ncs) > (uint32_t)kFixedWarps * kRing * 8u ? fixed_ring_off(ncs) : (uint32_t)kFixedWarps * kRing * 8u;
+}
 
 int launch_cells_fixed(const FixedArgs& a, int blocks, size_t smem, void* stream) {
   auto kern = cells_fixed_kernel<kFixedWarps>;

@@ -262,6 +262,8 @@ int launch_freq_recs(const PrepFixedArgs& a, void* stream);
 int launch_cells_fixed(const FixedArgs& a, int blocks, size_t smem, void* stream);
 // shared memory of the exact cell kernel for a table of ncs cells (incl. sentinel)
 uint32_t fixed_smem_bytes(int ncs);
+// shared memory of a time window of ncs cells (its table; pass B's rings overlay it)
+uint32_t fixed_window_smem_bytes(int ncs);
 uint32_t fixed_prep_smem_bytes(int n_pts);
 int fixed_blocks_per_sm(size_t smem);
 constexpr int kFixedWarps = 32;
