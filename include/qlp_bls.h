@@ -606,13 +606,15 @@ int qlp_bls_search_static(const qlp_bls_params* p, int32_t n, const double* tp, 
  * caller-owned, asynchronous on `stream`).
  *
  * qlp_cnn_pack_w64 -- w: FP32 [9][64][64] weights (tap, out channel, in channel);
- *   wpack: 73,728-byte device buffer receiving them as BF16 in the tensor-core
- *   layout; transpose = 1 packs the input-gradient form W'[k][ci][co] = W[8-k][co][ci].
+ *   wpack: 73,728-byte device buffer at a 16-byte boundary receiving them as BF16 in
+ *   the tensor-core layout (per tap 64 rows of 128 bytes, 128-byte swizzle);
+ *   transpose = 1 packs the input-gradient form W'[k][ci][co] = W[8-k][co][ci].
  * qlp_cnn_conv64 -- y[b][l][co] = epi(sum_k sum_ci W[k][co][ci] x[b][l+k-4][ci]) for
  *   BF16 channels-last x, y [batch][len][64], len a multiple of 128, zero padding;
  *   epi adds bias (FP32 [64], or NULL), applies ReLU when relu != 0, and zeroes
  *   entries where mask (BF16 [batch][len][64], or NULL) is not positive. err: a
  *   device int32 that receives QLP error bits (16 = a tensor-core wait hit its bound).
+ *   x, wpack and y start at 16-byte boundaries (else QLP_ERR_ARG).
  */
 int qlp_cnn_pack_w64(const float* w, void* wpack, int32_t transpose, void* stream);
 /*

@@ -358,14 +358,17 @@ int qlp_cnn_conv64_wgrad(const void* dy, const void* x, float* workspace, float*
 }
 
 int qlp_cnn_pack_w64(const float* w, void* wpack, int32_t transpose, void* stream) {
-  if (!w || !wpack) return QLP_ERR_ARG;
+  if (!w || !wpack || (reinterpret_cast<uintptr_t>(wpack) & 15u) != 0) return QLP_ERR_ARG;
   CKL(launch_pack_w64(w, wpack, transpose, stream));
   return QLP_OK;
 }
 
 int qlp_cnn_conv64(const void* x, const void* wpack, const float* bias, const void* mask, void* y,
                    int32_t batch, int32_t len, int32_t relu, int32_t* err, void* stream) {
-  if (!x || !wpack || !y || !err || batch < 0 || len <= 0 || len % 128 != 0) return QLP_ERR_ARG;
+  // the weights arrive by one bulk copy and the activations by TMA: 16-byte boundaries
+  if (!x || !wpack || !y || !err || batch < 0 || len <= 0 || len % 128 != 0 ||
+      ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(wpack) | reinterpret_cast<uintptr_t>(y)) & 15u) != 0)
+    return QLP_ERR_ARG;
   CKL(launch_conv64(x, wpack, bias, mask, y, err, batch, len, relu, stream));
   return QLP_OK;
 }

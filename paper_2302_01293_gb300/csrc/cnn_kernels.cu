@@ -5,16 +5,19 @@
 // Layouts. Activations are channels-last BF16 [B][L][64] (one 128-byte row per
 // position). A tile is 128 positions x 64 output channels:
 //   Y[l, co] = sum_{kk=0..8} sum_{ci} W[kk][co][ci] X[l + kk - 4, ci]
-// Its 136 input rows l0-4 .. l0+131 sit in shared memory in the no-swizzle
-// K-major canonical layout, one "plane" per 8 input channels (rows at a 16-byte
-// stride), so tap kk is the same tile shifted by kk rows: its A descriptor starts
-// kk * 16 bytes later. The weights (9 taps x 64 x 64) stay resident in the same
-// layout. Each tile takes 9 taps x 4 K-steps of tcgen05.mma (M = 128, N = 64,
-// K = 16) into a TMEM accumulator of 64 FP32 columns.
+// Its 136 input rows l0-4 .. l0+131 sit in shared memory as they are in memory,
+// one 128-byte row per position, in the 128-byte-swizzled K-major layout (chunk c
+// of row r at chunk c ^ (r & 7)), so tap kk is the same tile shifted by kk rows:
+// its A descriptor starts kk * 128 bytes later (the swizzle follows the address
+// bits, so a shifted start reads the shifted rows). The weights (9 taps x 64 x 64)
+// stay resident in the same layout, 64 rows of 128 bytes per tap. Each tile takes
+// 9 taps x 4 K-steps of tcgen05.mma (M = 128, N = 64, K = 16, the K step 32 bytes
+// along the row) into a TMEM accumulator of 64 FP32 columns.
 //
-// Pipeline (one persistent CTA per SM, warp roles): warp 0 loads tiles with TMA
-// into a ring of kStages buffers (8 plane copies per tile, each a box of 8
-// channels x 136 rows of a 3-D tensor map over [B][L][64], so rows outside
+// Pipeline (one persistent CTA per SM, warp roles): warp 0 copies the weights in
+// one bulk asynchronous copy (on their own barrier, which the MMA issuer waits for)
+// and loads tiles with TMA into a ring of kStages buffers (one box of 64 channels x 136 rows per tile, of a
+// 3-D tensor map over [B][L][64] with the 128-byte swizzle, so rows outside
 // [0, L) of the tile's own sample come back as zeros); warp 1 issues the MMAs of
 // each tile into one of kAcc accumulators and commits them to the buffer's
 // "empty" barrier and the accumulator's "full" barrier; warps 2-9 (two per TMEM
@@ -39,10 +42,9 @@ constexpr int kC = 64;             // channels of the middle layers
 constexpr int kTaps = 9;           // kernel size
 constexpr int kTileM = 128;        // positions per tile
 constexpr int kRows = kTileM + kTaps - 1;  // staged rows per tile
-constexpr int kPlanes = kC / 8;    // 8 channels (16 bytes) per plane
-constexpr int kPlaneBytes = kRows * 16;    // 2,176 (a multiple of 128: TMA destinations stay aligned)
-constexpr int kABytes = kPlanes * kPlaneBytes;  // 17,408
-constexpr int kWBytes = kTaps * kPlanes * kC * 16;  // 73,728
+constexpr int kPlanes = kC / 8;    // 8 channels (16 bytes) per plane (the weight-gradient kernel's layout)
+constexpr int kABytes = kRows * kC * 2;     // 17,408 = 17 swizzle atoms of 1,024 bytes
+constexpr int kWBytes = kTaps * kC * kC * 2;  // 73,728 = 72 atoms
 constexpr int kStages = 6;         // tile buffers in flight
 constexpr int kAcc = 4;            // TMEM accumulators (64 columns each)
 constexpr int kEpiWarps = 8;       // two per TMEM lane quarter, 32 columns each
@@ -145,12 +147,13 @@ __device__ __forceinline__ void conv_epilogue(const ConvTcArgs& a, const float* 
 __global__ void __launch_bounds__(kConvThreads, 1)
     conv64_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap ymap,
                      const ConvTcArgs a) {
-  extern __shared__ __align__(128) unsigned char smem[];  // TMA destinations need 128-byte alignment
-  unsigned char* wsm = smem;
-  unsigned char* ring = smem + kWBytes;  // kStages tile buffers of kABytes
-  // kOutBufs output staging tiles at the next 1024-byte boundary (the 128-byte swizzle's period)
+  extern __shared__ __align__(128) unsigned char smem[];
+  // everything from the next 1024-byte boundary (the 128-byte swizzle's period): the
+  // weights, kStages tile buffers of kABytes and kOutBufs output staging tiles, each a
+  // whole number of 1,024-byte atoms
+  unsigned char* wsm = smem + ((1024u - (smem_u32(smem) & 1023u)) & 1023u);
+  unsigned char* ring = wsm + kWBytes;
   unsigned char* obuf = ring + kStages * kABytes;
-  obuf += (1024u - (smem_u32(obuf) & 1023u)) & 1023u;
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], accf[kAcc], acce[kAcc], fin;
   __shared__ uint32_t tmem_base;
   __shared__ float s_bias[kC];
@@ -162,10 +165,9 @@ __global__ void __launch_bounds__(kConvThreads, 1)
   const int n_tiles = a.batch * tiles_per_sample;
   const int n_my = (int)blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
-  // resident weights and bias; barriers; TMEM
-  const uint4* wsrc = a.wpack;
-  uint4* wdst = reinterpret_cast<uint4*>(wsm);
-  for (int i = tid; i < kWBytes / 16; i += blockDim.x) wdst[i] = wsrc[i];
+  // resident weights (one bulk asynchronous copy, issued below with the first tiles) and
+  // bias; barriers; TMEM
+  __shared__ __align__(8) uint64_t wbar;
   if (tid < kC) s_bias[tid] = a.bias ? a.bias[tid] : 0.f;
   if (tid == 0) {
     for (int k = 0; k < kStages; ++k) {
@@ -177,11 +179,11 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       mbar_init(&acce[k], kEpiWarps);  // one arrival per epilogue warp
     }
     mbar_init(&fin, 1);
+    mbar_init(&wbar, 1);
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) tmem_alloc(&tmem_base, kAcc * kC);
-  fence_proxy_async_smem();  // the weights become visible to the tensor core
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -189,6 +191,11 @@ __global__ void __launch_bounds__(kConvThreads, 1)
   bool ok = true;
 
   if (warp == 0 && lane == 0) {  // TMA producer
+    mbar_arrive_expect_tx(&wbar, (uint32_t)kWBytes);
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(wsm)),
+                 "l"(a.wpack), "r"((uint32_t)kWBytes), "r"(smem_u32(&wbar))
+                 : "memory");
     int issued = 0;
     for (int i = 0; i < n_my && ok; ++i) {
       const int s = i % kStages;
@@ -198,33 +205,34 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       const int b = t / tiles_per_sample, l0 = (t % tiles_per_sample) * kTileM;
       unsigned char* buf = ring + s * kABytes;
       mbar_arrive_expect_tx(&full[s], (uint32_t)kABytes);
-#pragma unroll
-      for (int j = 0; j < kPlanes; ++j) tma_load3(buf + j * kPlaneBytes, &xmap, 8 * j, l0 - kTaps / 2, b, &full[s]);
+      tma_load3(buf, &xmap, 0, l0 - kTaps / 2, b, &full[s]);
       issued = i + 1;
     }
     // every copy issued has landed before the CTA goes on (bounded)
     for (int i = issued > kStages ? issued - kStages : 0; i < issued; ++i)
       if (!mbar_wait(&full[i % kStages], (uint32_t)((i / kStages) & 1), kWaitLimit)) ok = false;
+    if (!mbar_wait(&wbar, 0u, kWaitLimit)) ok = false;
   } else if (warp == 1 && lane == 0) {  // MMA issuer
     const uint32_t idesc = idesc_bf16_f32(kTileM, kC);
     // descriptors as a base plus a compile-time offset: every offset is a multiple of
     // 16 bytes and every address stays below 2^18, so (addr + off) >> 4 = (addr >> 4)
     // + (off >> 4) within the 14-bit start-address field
-    const uint64_t bdesc0 = smem_desc(smem_u32(wsm), kC * 16, 128);
+    const uint64_t bdesc0 = smem_desc_sw128(smem_u32(wsm));
+    if (n_my > 0) ok = mbar_wait(&wbar, 0u, kWaitLimit);  // the weights have landed
     for (int i = 0; i < n_my && ok; ++i) {
       const int s = i % kStages, ac = i % kAcc;
       ok = mbar_wait(&full[s], (uint32_t)((i / kStages) & 1), kWaitLimit);
       if (ok && i >= kAcc) ok = mbar_wait(&acce[ac], (uint32_t)((i / kAcc - 1) & 1), kWaitLimit);
       if (!ok) break;
       tc_fence_after();
-      const uint64_t adesc0 = smem_desc(smem_u32(ring + s * kABytes), kPlaneBytes, 128);
+      const uint64_t adesc0 = smem_desc_sw128(smem_u32(ring + s * kABytes));
       const uint32_t dst = tmem + (uint32_t)(ac * kC);
 #pragma unroll
       for (int kk = 0; kk < kTaps; ++kk) {
 #pragma unroll
-        for (int ks = 0; ks < kPlanes / 2; ++ks) {
-          const uint64_t ad = adesc0 + (uint64_t)((2 * ks * kPlaneBytes + kk * 16) >> 4);
-          const uint64_t bd = bdesc0 + (uint64_t)(((kk * kPlanes + 2 * ks) * (kC * 16)) >> 4);
+        for (int ks = 0; ks < kC / 16; ++ks) {  // tap kk: kk rows on; K step ks: 32 bytes along the row
+          const uint64_t ad = adesc0 + (uint64_t)((kk * 128 + ks * 32) >> 4);
+          const uint64_t bd = bdesc0 + (uint64_t)((kk * kC * 128 + ks * 32) >> 4);
           mma_bf16(dst, ad, bd, idesc, kk > 0 || ks > 0);
         }
       }
@@ -276,12 +284,14 @@ __global__ void __launch_bounds__(kConvThreads, 1)
 
 // W[kk][co][ci] (FP32) -> BF16 planes for the tensor-core kernel. transpose=1
 // packs the weights of the input-gradient convolution: W'[kk][ci][co] = W[8-kk][co][ci].
+// Per tap kk, 64 rows n (the output channel) of 128 bytes (the 64 reduction channels),
+// 16-byte chunk j of row n at chunk j ^ (n & 7): the MMA's 128-byte-swizzled layout.
 __global__ void pack_w64_kernel(const float* w, uint4* out, int transpose) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // (kk, plane j, row n)
-  if (i >= kTaps * kPlanes * kC) return;
-  const int kk = i / (kPlanes * kC);
-  const int j = (i / kC) % kPlanes;
-  const int n = i % kC;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // (kk, row n, chunk j)
+  if (i >= kTaps * kC * 8) return;
+  const int kk = i / (kC * 8);
+  const int n = (i / 8) % kC;
+  const int j = i % 8;
   __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
@@ -289,7 +299,7 @@ __global__ void pack_w64_kernel(const float* w, uint4* out, int transpose) {
     const float x = transpose ? w[((kTaps - 1 - kk) * kC + k) * kC + n] : w[(kk * kC + n) * kC + k];
     v[e] = __float2bfloat16_rn(x);
   }
-  out[i] = *reinterpret_cast<const uint4*>(v);
+  out[(kk * kC + n) * 8 + (j ^ (n & 7))] = *reinterpret_cast<const uint4*>(v);
 }
 
 // Shared memory of the conv kernel: resident weights, the row tiles and the output
@@ -317,17 +327,17 @@ int launch_conv64(const void* xv, const void* wv, const float* bias, const void*
   const uint4* wpack = static_cast<const uint4*>(wv);
   const __nv_bfloat16* mask = static_cast<const __nv_bfloat16*>(mv);
   if (batch <= 0) return 0;
-  // the input as a 3-D tensor (channel, position, sample), boxes of 8 channels x 136
-  // rows x 1 sample: one plane of a tile, zeros outside the sample's [0, len)
+  // the input as a 3-D tensor (channel, position, sample), boxes of 64 channels x 136
+  // rows x 1 sample (a whole tile, 128-byte swizzle), zeros outside the sample's [0, len)
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
   if (!enc) return (int)cudaErrorNotSupported;
   alignas(64) CUtensorMap map;
   const cuuint64_t dims[3] = {(cuuint64_t)kC, (cuuint64_t)len, (cuuint64_t)batch};
   const cuuint64_t strides[2] = {(cuuint64_t)kC * 2, (cuuint64_t)len * kC * 2};
-  const cuuint32_t box[3] = {8, (cuuint32_t)kRows, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)kC, (cuuint32_t)kRows, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(xv), dims, strides, box, estr,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return (int)cudaErrorInvalidValue;
   // the output as the same 3-D tensor, boxes of a whole tile (64 channels x 128 rows),
@@ -352,7 +362,7 @@ int launch_conv64(const void* xv, const void* wv, const float* bias, const void*
 }
 
 int launch_pack_w64(const float* w, void* out, int transpose, void* stream) {
-  const int n = kTaps * kPlanes * kC;
+  const int n = kTaps * kC * 8;
   pack_w64_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(w, static_cast<uint4*>(out), transpose);
   return (int)cudaGetLastError();
 }

@@ -23,6 +23,16 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+// Shared-memory matrix descriptor, 128-byte swizzle, K-major: rows of 128 bytes (64
+// BF16 of K), 8-row atoms 1024 bytes apart (the stride field), 16-byte chunk c of
+// row r stored at chunk c ^ (r & 7) of the row, the XOR taken on the address bits
+// themselves: a start address 128 bytes (one row) or 32 bytes (one K step of 16)
+// past a 1024-byte-aligned atom needs no base offset. Layout field 2 (128B).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)(1024u >> 4) << 32) | (1ull << 46) |
+         (2ull << 61);
+}
+
 // Instruction descriptor of tcgen05.mma kind::f16: BF16 A and B (both K-major),
 // FP32 accumulator, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int m, int n) {

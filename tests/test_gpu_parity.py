@@ -77,6 +77,21 @@ def test_exact_cell_path_is_the_default(gpu_lib):
     assert g["plan"].n_narrow_stars == _narrow_expected(b) >= 6
 
 
+def test_32_bit_table_with_unequal_weights(gpu_lib):
+    # per-point errors scattered by up to 20 % (weights up to 2.25 times apart): on the
+    # 32-bit table r is then the ratio of integer sums of round(w F) that are no longer
+    # equal, each point's weight rounded to 2^-33 of the total; the spectra, S/N and best
+    # records still meet the parity tolerances (same-box SR within 5e-7)
+    b = synth.uneven_single_sector(n_stars=4, seed=35)
+    rng = np.random.default_rng(35)
+    dy = b.dy * rng.uniform(0.8, 1.2, b.dy.shape)
+    b2 = synth.Batch(b.offsets, b.t, b.y, dy, b.rho, b.rstar, b.inj, b.period, b.t0, b.depth, b.duration,
+                     "unequal weights")
+    g, _ = _check_batch(b2, qlpbls.Params())
+    assert g["sr_tight"] and g["plan"].n_exact_stars == 4
+    assert g["plan"].n_narrow_stars == _narrow_expected(b2) >= 3
+
+
 def test_slow_trend_takes_the_64_bit_table(gpu_lib):
     # a linear flux trend of 10 sigma across the sector makes the running sum of
     # w (y - ybar) reach about N / 8 times its largest single term, beyond the 32-bit
