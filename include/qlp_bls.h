@@ -48,6 +48,9 @@ extern "C" {
 #define QLP_DEVERR_SNR_BINS  4  /* more S/N (Sturges) bins than supported */
 #define QLP_DEVERR_COPY     32  /* an asynchronous copy into shared memory did not complete
                                    within its bound (the frequencies it fed are not valid) */
+#define QLP_DEVERR_RANGE    64  /* a star's 32-bit exact table got a prefix sum of w d outside
+                                   its 32-bit range (the planner's bound did not hold; that
+                                   star's results are not valid) */
 
 /* ---- per-star status flags (qlp_bls_plan_info star_status, qlp_bls_best.status) ---- */
 #define QLP_STAR_UNSORTED    1  /* t decreases somewhere (after dropping invalid points) */
@@ -391,7 +394,8 @@ int qlp_bls_run_host(const qlp_bls_params* p, int32_t n_stars, const int64_t* of
  * accumulated by this plan's kernels since the last call in *flags (QLP_DEVERR_*:
  * 1 the work loop hit its iteration bound, 2 a frequency needed more bins than the
  * shared histogram holds, 4 more S/N bins than supported, 32 a bulk copy of a star's
- * cell table into shared memory did not complete within its bound) and clear them.
+ * cell table into shared memory did not complete within its bound, 64 a 32-bit exact
+ * table's prefix sum left its range) and clear them.
  * Returns QLP_ERR_DEVICE when any flag was set, else QLP_OK.
  */
 int qlp_bls_device_status(qlp_bls_plan_t* plan, void* stream, int32_t* flags);

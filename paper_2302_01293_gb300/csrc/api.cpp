@@ -168,8 +168,8 @@ struct qlp_bls_plan {
   int32_t fixed_max_pts = 0;
   bool fixed_windowed = false;    // some exact-path star is searched in time windows
   longlong2* d_ws = nullptr;      // exact-path bin-sum workspace, ws_block entries per block:
-  int64_t ws_block = 1;           // kFixedWsBlock with windowed stars, else a row of the largest
-                                  // bin count per warp (the exact rescoring of each best box)
+  int64_t ws_block = 1;           // a row of the largest bin count per warp (the exact rescoring of
+                                  // each best box), or a windowed item's rows if larger
   int32_t fixed_nb_max = 0;       // largest bin count of an exact-path star
   double edges_fixed = 0.0;
   double bins_fixed = 0.0;       // sum of nbins over the exact path's frequencies
@@ -330,6 +330,7 @@ static PrepFixedArgs fixed_args(const qlp_bls_plan_t* pl) {
   for (int j = 0; j < kMaxQ; ++j) pf.E[j] = pl->E[j];
   pf.nb_cap = pl->p.nbins_cap;
   pf.max_pts = pl->fixed_max_pts;
+  pf.err = pl->d_ctl + 2;
   return pf;
 }
 
@@ -691,11 +692,10 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
     pl->f_blocks = sms * fper;
   }
 
-  // exact-path workspace per block: the windowed stars' rows (each item's bins per
-  // frequency), which also hold one row of 4,096 >= nbins per warp; else one row of
-  // the largest bin count per warp
-  if (!fixed_stars.empty())
-    pl->ws_block = pl->fixed_windowed ? kFixedWsBlock : (int64_t)kFixedWarps * round32(pl->fixed_nb_max);
+  // exact-path workspace per block: one row of the largest bin count per warp (the
+  // whole-table stars' bin sums), or the largest rows of a windowed item (its bins per
+  // frequency), whichever is larger (set below, once the items are cut)
+  int64_t win_rows_max = 0;
 
   // work items: (star, chunk of frequencies), longest first, one queue per path
   auto make_items = [&](int32_t meth, int w, int blocks, std::vector<WorkItem>* outv) {
@@ -717,8 +717,11 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
       int ck = chunk;
       int32_t ws_stride = 0;
       if (meth == kMethodFixed && d.n_win > 1) {  // rows of round32(nbins) bins in the block's workspace
+        // long items: every item stages all of its star's windows once, so the fewer
+        // items the less staging; at most kFixedWinRows entries per block
         ws_stride = (int32_t)round32(h.nbins_max);
-        ck = std::max(1, std::min(ck, (int)(kFixedWsBlock / ws_stride)));
+        ck = std::max(1, std::min(ck, (int)(kFixedWinRows / ws_stride)));
+        win_rows_max = std::max<int64_t>(win_rows_max, (int64_t)std::min(ck, d.n_f) * ws_stride);
       }
       for (int32_t b = 0; b < d.n_f; b += ck) {
         WorkItem wi{};
@@ -753,6 +756,8 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   pl->n_items = make_items(kMethodPoints, warps, pl->blocks, &sorted);
   pl->c_items = make_items(kMethodCells, cw, pl->c_blocks, &sorted);
   pl->f_items = make_items(kMethodFixed, kFixedWarps, pl->f_blocks, &sorted);
+  if (!fixed_stars.empty())
+    pl->ws_block = std::max<int64_t>((int64_t)kFixedWarps * round32(pl->fixed_nb_max), win_rows_max);
 
   // device buffers
   const auto c2 = clk::now();

@@ -220,6 +220,11 @@ __global__ void __launch_bounds__(512) prep_fixed_kernel(const PrepFixedArgs a) 
   }
   __syncthreads();
   long long cw = scan_w[tid], cy = scan_y[tid];
+  // the 32-bit table keeps every prefix of w_int below 2^32 and of y_int below 2^30 in
+  // magnitude by its scales; a sum past its word's range would wrap: raise the error bit
+  // (the star's results are then void)
+  auto wraps = [&](long long w, long long y) { return w >= (1ll << 32) || y >= kNarrowBias || y <= -kNarrowBias; };
+  bool out_of_range = narrow && wraps(cw, cy);
   for (int i = i0; i < i1; ++i) {
     a.ipre[st.cpre_off + i] = make_longlong2(cw, cy);
     if (cache) {
@@ -231,7 +236,9 @@ __global__ void __launch_bounds__(512) prep_fixed_kernel(const PrepFixedArgs a) 
       cw += __double2ll_rn(w * pw);
       cy += __double2ll_rn(w * (y[i] - ybar) * py);
     }
+    out_of_range = out_of_range || (narrow && wraps(cw, cy));
   }
+  if (out_of_range) atomicOr(a.err, kErrRange);
   __syncthreads();
 
   // first point at or after each cell start: point i fills cells (cell(i-1), cell(i)]

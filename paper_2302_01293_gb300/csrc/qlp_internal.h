@@ -156,6 +156,7 @@ struct PrepFixedArgs {
   double E[kMaxQ];
   int32_t nb_cap;
   int32_t max_pts;             // most points of a star in the list (shared memory of the prep)
+  int32_t* err;                // device error bits (kErrRange)
 };
 
 struct FixedArgs {
@@ -246,6 +247,8 @@ constexpr int32_t kErrSelect = 8;       // median selection failed to converge
 constexpr int32_t kErrMmaWait = 16;     // a tensor-core completion wait hit its bound
 constexpr int32_t kErrCopyWait = 32;    // a bulk copy into shared memory did not complete in its bound
 static_assert(kErrCopyWait == QLP_DEVERR_COPY, "device error bits");
+constexpr int32_t kErrRange = 64;       // a 32-bit exact table's w d prefix sum left its range
+static_assert(kErrRange == QLP_DEVERR_RANGE, "device error bits");
 
 // launchers (bls_kernels.cu / snr_kernel.cu); return cudaError_t as int
 int launch_prep(const PrepArgs& a, void* stream);
@@ -267,7 +270,8 @@ uint32_t fixed_window_smem_bytes(int ncs);
 uint32_t fixed_prep_smem_bytes(int n_pts);
 int fixed_blocks_per_sm(size_t smem);
 constexpr int kFixedWarps = 32;
-constexpr int64_t kFixedWsBlock = 131072;  // workspace entries (16 B) per block for windowed stars
+constexpr int64_t kFixedWsBlock = 131072;  // bound on a block's whole-table rows: 32 warps x round32(nbins)
+constexpr int64_t kFixedWinRows = 524288;  // workspace entries (16 B) a windowed item may take per block
 // bytes of shared memory before the histograms of the cell kernel for a star with
 // ncs cells (incl. sentinel) and nw warps
 // One point of a candidate's fit window: t', P n for its transit index n at the

@@ -95,7 +95,7 @@ class Params:
 
 
 ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_DEVICE, ERR_UNSUPPORTED = -1, -2, -3, -4, -5
-DEVERR_QUEUE, DEVERR_NBINS, DEVERR_SNR_BINS = 1, 2, 4
+DEVERR_QUEUE, DEVERR_NBINS, DEVERR_SNR_BINS, DEVERR_COPY, DEVERR_RANGE = 1, 2, 4, 32, 64
 
 
 class QlpError(RuntimeError):
