@@ -221,6 +221,18 @@ void grid_chains(const qlp_bls_params& p, StarPlanHost* const* st, int n) {
     f[j] = 1.0 / st[j]->pmax;
     on[j] = f[j] <= fmax[j];
     left += on[j] ? 1 : 0;
+    if (on[j]) {
+      // room for the grid at once: with q_min about proportional to f^(2/3) the steps
+      // number denom (3 / q(f0)) f0^(2/3) (fmax^(1/3) - f0^(1/3)); the arcsine makes
+      // q_min grow faster near Pmin, so this overestimates a little (only the vectors'
+      // capacity depends on it)
+      const double q0 = q_min_of(f[j], st[j]->rho_kg, p);
+      const double est = denom[j] * 3.0 / q0 * std::cbrt(f[j] * f[j]) * (std::cbrt(fmax[j]) - std::cbrt(f[j]));
+      if (est > 0.0 && est < 1.0e8) {
+        st[j]->freqs.reserve((size_t)(est * 1.02) + 64);
+        st[j]->qmins.reserve((size_t)(est * 1.02) + 64);
+      }
+    }
   }
   while (left > 0) {
     for (int j = 0; j < kChains; ++j) {
@@ -279,35 +291,37 @@ void tail_points(StarPlanHost& s) {
   const double* tp = s.tp_data();
   const double* yv = s.y_data();
   const double* dyv = s.dy_data();
-  // weight spreads (FP64; only a routing decision depends on them, so the sums
-  // are plain and the weights are not normalised)
+  // weight spreads and the running sum of w (y - ybar) (FP64; only routing decisions
+  // depend on them, so the sums are plain and the weights are not normalised): each
+  // point's 1 / dy^2 once, kept in this thread's scratch for the second pass
   {
+    thread_local std::vector<double> inv_s;
+    if (inv_s.size() < (size_t)m) inv_s.resize((size_t)m);
+    double* inv = inv_s.data();
     double isum = 0.0, iysum = 0.0, imax = 0.0;
     for (int64_t i = 0; i < m; ++i) {
-      const double inv = 1.0 / (dyv[i] * dyv[i]);
-      isum += inv;
-      iysum += inv * yv[i];
-      imax = std::max(imax, inv);
+      const double v = 1.0 / (dyv[i] * dyv[i]);
+      inv[i] = v;
+      isum += v;
+      iysum += v * yv[i];
+      imax = std::max(imax, v);
     }
     const double ybar = iysum / isum;
-    double dsum = 0.0, dmax = 0.0;
-    for (int64_t i = 0; i < m; ++i) {
-      const double v = std::fabs((yv[i] - ybar) / (dyv[i] * dyv[i]));
-      dsum += v;
-      dmax = std::max(dmax, v);
-    }
-    s.w_spread = imax / (isum / (double)m);
-    s.wd_spread = dsum > 0.0 ? dmax / (dsum / (double)m) : 0.0;
     // the running sum of w (y - ybar) and its largest magnitude (it ends near zero).
     // The device's weighted mean differs from this one by the FP64 sums' rounding,
     // below 2^-37 max|y| for 2^16 points, which moves every running sum by as much:
     // an excursion below 2^-28 max|y| is reported as 0 (no 32-bit table)
-    double run = 0.0, exc = 0.0, yabs = 0.0;
+    double dsum = 0.0, dmax = 0.0, run = 0.0, exc = 0.0, yabs = 0.0;
     for (int64_t i = 0; i < m; ++i) {
-      run += (yv[i] - ybar) / (dyv[i] * dyv[i]);
+      const double d = (yv[i] - ybar) * inv[i];
+      dsum += std::fabs(d);
+      dmax = std::max(dmax, std::fabs(d));
+      run += d;
       exc = std::max(exc, std::fabs(run));
       yabs = std::max(yabs, std::fabs(yv[i]));
     }
+    s.w_spread = imax / (isum / (double)m);
+    s.wd_spread = dsum > 0.0 ? dmax / (dsum / (double)m) : 0.0;
     s.wd_max = dmax / isum;
     s.y_exc = (exc / isum >= std::ldexp(yabs, -28)) ? exc / isum : 0.0;
   }
