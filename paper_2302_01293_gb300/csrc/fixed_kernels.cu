@@ -582,9 +582,24 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
       // histogram of block i - 1: H[x] = U[x + 1] - U[x], exact, then FP32. Lane x takes
       // U[x + 1] from lane x + 1's previous block, lane 31 from lane 0's current one.
       const int src = (lane + 1) & 31;
-      const long long nw = __shfl_sync(0xffffffffu, lane == 0 ? uw : pw, src);
-      const long long ny = __shfl_sync(0xffffffffu, lane == 0 ? uy : py, src);
-      const float2 hv = make_float2(__fmul_rn(__ll2float_rn(nw - pw), scw), __fmul_rn(__ll2float_rn(ny - py), scy));
+      float2 hv;
+      if constexpr (NARROW) {
+        // the 32-bit table's bin sums: the w sum lies in [0, 2^32) (a part of the star's
+        // total below 2^32), so the difference of the low words is exact; the w d sum
+        // goes through 32 bits when every lane's fits (the same rounding either way)
+        const uint32_t nw32 = __shfl_sync(0xffffffffu, (uint32_t)(lane == 0 ? uw : pw), src);
+        const long long ny = __shfl_sync(0xffffffffu, lane == 0 ? uy : py, src);
+        const uint32_t hw = nw32 - (uint32_t)pw;
+        const long long hy = ny - py;
+        float fy;
+        if (__all_sync(0xffffffffu, hy == (long long)(int)hy)) fy = __int2float_rn((int)hy);
+        else fy = __ll2float_rn(hy);
+        hv = make_float2(__fmul_rn(__uint2float_rn(hw), scw), __fmul_rn(fy, scy));
+      } else {
+        const long long nw = __shfl_sync(0xffffffffu, lane == 0 ? uw : pw, src);
+        const long long ny = __shfl_sync(0xffffffffu, lane == 0 ? uy : py, src);
+        hv = make_float2(__fmul_rn(__ll2float_rn(nw - pw), scw), __fmul_rn(__ll2float_rn(ny - py), scy));
+      }
       ring[(((i - 1) & 3) << 5) + lane] = hv;
     }
     pw = uw;
