@@ -39,6 +39,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "bls_device.cuh"
 #include "qlp_internal.h"
@@ -463,7 +464,11 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
         const bool idle = split ? ph >= P : x >= nb;
         const int G0 = idle ? (i << 5) : (xb == 0 ? nb : xb + ph * nb);
         const int gstep = P * nb;
-        long long aw = 0, ay = 0;
+        // the w sums of the 32-bit table in wrapping 32-bit words: every bin and box sum
+        // of w lies in [0, 2^32), so sums modulo 2^32 give them exactly
+        using WAcc = std::conditional_t<NARROW, uint32_t, long long>;
+        WAcc aw = 0;
+        long long ay = 0;
         // the smallest (dq - fr + band) mod 2^32 over the lane's edges: some edge lies
         // within the guard band of its cell's point exactly when it is <= 2 band
         uint32_t nmin = 0xffffffffu;
@@ -488,7 +493,7 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
           const int2 lc = *reinterpret_cast<const int2*>(smem + loc_off + (uint32_t)v * st8);
           if constexpr (NARROW) {  // the 32-bit prefix sums themselves
             if (valid) {
-              aw += (long long)(uint32_t)lc.x;
+              aw += (uint32_t)lc.x;
               ay += (long long)(uint32_t)lc.y;
             }
           } else {
@@ -515,7 +520,7 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
         bool near = nmin <= 2u * band_q;  // an edge within the guard band of its cell's point
         if (split) {  // warp-uniform: add the other phases of each bin into lanes 0 .. r-1
           for (int q = 1; q < P; ++q) {
-            const long long ow = __shfl_down_sync(0xffffffffu, aw, q * r);
+            const WAcc ow = __shfl_down_sync(0xffffffffu, aw, q * r);
             const long long oy = __shfl_down_sync(0xffffffffu, ay, q * r);
             const bool on = __shfl_down_sync(0xffffffffu, near ? 1 : 0, q * r) != 0;
             if (lane < r) {
@@ -547,7 +552,7 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
               const int v = u + sel;
               const int2 lc = reinterpret_cast<const int2*>(smem + loc_off)[v];
               if constexpr (NARROW) {
-                aw += (long long)(uint32_t)lc.x;
+                aw += (uint32_t)lc.x;
                 ay += (long long)(uint32_t)lc.y - kNarrowBias;
               } else {
                 const longlong2 bs = reinterpret_cast<const longlong2*>(smem + base_off)[v >> 5];
@@ -557,12 +562,12 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
             }
           }
         }
-        if (x < nb) warp_row(a)[x] = make_longlong2(aw, ay);  // S of bin x, for the rescoring below
+        if (x < nb) warp_row(a)[x] = make_longlong2((long long)aw, ay);  // S of bin x, for the rescoring below
         if (bstar < x) {
-          aw += fx.w_tot;
+          aw += (WAcc)fx.w_tot;
           ay += fx.y_tot;
         }
-        uw = aw;
+        uw = (long long)aw;
         uy = ay;
       }
     }
@@ -642,9 +647,10 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
     const longlong2* row = WS ? srow : warp_row(a);
     const longlong2 a0 = row[bk], a1 = row[k2m];
     const long long nwrap = (bstar < k2m ? 1 : 0) + (k2 >= nb ? 1 : 0) - (bstar < bk ? 1 : 0);
-    const long long dw = a1.x - a0.x + nwrap * fx.w_tot;
+    long long dw = a1.x - a0.x + nwrap * fx.w_tot;
     const long long dy = a1.y - a0.y + nwrap * fx.y_tot;
     if (NARROW) {  // r = dw / w_tot and 1 - r = (w_tot - dw) / w_tot, both sums below 2^32
+      dw = (long long)(uint32_t)dw;  // the rows hold the w sums modulo 2^32
       const DF wt = df_from_ll_scaled(fx.w_tot, 0);
       bb.xr = df_div(df_from_ll_scaled(dw, 0), wt);
       bb.xq = df_div(df_from_ll_scaled(fx.w_tot - dw, 0), wt);
