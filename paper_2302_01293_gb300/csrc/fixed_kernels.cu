@@ -725,13 +725,38 @@ __device__ void windowed_item(const FixedArgs& a, const WorkItem& wi, const Star
       const uint32_t k_lo = (uint32_t)R.K, k_hi = (uint32_t)(R.K >> 32);
       const uint32_t band_q = R.band_q;
       longlong2* row = ws + (size_t)fl * (size_t)stride;
+      // this bin's edges in [gs, ge): cycles c0 = max(0, ceil((gs - x) / nb)) .. c1 =
+      // floor((ge - 1 - x) / nb) for x = 32 i + lane. With A = gs + nb - 1 - 32 i = qa nb + ra
+      // and B = ge - 1 - 32 i = qb nb + rb (0 <= ra, rb < nb) and lane < 32 <= nb, they are
+      // qa - [lane > ra] (at least 0) and qb - [lane > rb] (below 0: no edge); (q, r) step
+      // down by 32 bins per block with at most one borrow, so the divisions are once per
+      // window and frequency
+      int qa = (gs + nb - 1) / nb, ra = (gs + nb - 1) - qa * nb;
+      int qb, rb;
+      if (ge - 1 >= 0) {
+        qb = (ge - 1) / nb;
+        rb = (ge - 1) - qb * nb;
+      } else {
+        qb = -1;
+        rb = ge - 1 + nb;
+      }
       for (int i = 0; (i << 5) < nb; ++i) {
         const int x = (i << 5) + lane;
         const bool inb = x < nb;
-        // this bin's edges in [gs, ge): cycles c0 .. c1 (the edge at t' = 0 is skipped)
-        int c0 = gs > x ? (gs - x + nb - 1) / nb : 0;
+        // the edge at t' = 0 is skipped
+        int c0 = max(0, qa - (lane > ra ? 1 : 0));
         if (x == 0 && c0 == 0) c0 = 1;
-        const int c1 = ge - 1 >= x ? (ge - 1 - x) / nb : -1;
+        const int c1 = qb - (lane > rb ? 1 : 0);
+        ra -= 32;
+        if (ra < 0) {
+          ra += nb;
+          --qa;
+        }
+        rb -= 32;
+        if (rb < 0) {
+          rb += nb;
+          --qb;
+        }
         const int cntl = inb ? max(0, c1 - c0 + 1) : 0;
         const int cmax = __reduce_max_sync(0xffffffffu, (unsigned)cntl);
         long long aw = 0, ay = 0;
