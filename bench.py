@@ -773,10 +773,9 @@ def main():
                 "ms_search": ms_search, "ms_kernel": ms_kernel,
                 "exact_path_stars": plan.n_exact_stars,
                 "exact_path_32bit_table_stars": plan.n_narrow_stars,
-                # per step: S/N, and per search path in use its preparation and search kernels
-                "gpu_launches": args.steps * (1 + 2 * (plan.work_points > 0)
-                                              + 2 * (plan.n_cell_stars > plan.n_exact_stars)
-                                              + 2 * (plan.n_exact_stars > 0)),
+                # per step: S/N and the search's launches (per path in use its preparation
+                # and search kernels, the exact one per kind of table)
+                "gpu_launches": args.steps * (1 + plan.search_launches),
                 "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "candidate_stats": cand_stats,
                 "single_star": single_line,

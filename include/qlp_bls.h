@@ -240,6 +240,16 @@ int qlp_bls_plan_narrow_stats(const qlp_bls_plan_t* plan, int32_t* n_narrow_star
                               double* narrow_bins);
 
 /*
+ * qlp_bls_plan_launches -- how many kernels one qlp_bls_search of the plan launches:
+ * per search path in use its preparation kernel and its search kernel, the exact
+ * path's search kernel as two launches when the plan has both whole-table and
+ * time-windowed stars on it (one per kind of table). S/N is not counted.
+ *  n_search_launches  output, host pointer.
+ * Returns QLP_ERR_ARG for a NULL plan or output.
+ */
+int qlp_bls_plan_launches(const qlp_bls_plan_t* plan, int32_t* n_search_launches);
+
+/*
  * qlp_bls_plan_times -- measurement aid (no counterpart in the paper): wall-clock
  * seconds the plan's construction spent in four phases, written to seconds4[0..3]:
  * the host grid and per-star plans (Sec. 2.1 rules, all stars in parallel), the

@@ -164,6 +164,7 @@ struct qlp_bls_plan {
   int f_blocks = 0;
   size_t f_smem = 0;
   int32_t f_items = 0;
+  int32_t f_whole = 0;            // the first f_whole of them on whole tables, the rest windowed
   int32_t n_fixed_stars = 0;
   int32_t fixed_max_pts = 0;
   bool fixed_windowed = false;    // some exact-path star is searched in time windows
@@ -195,7 +196,7 @@ struct qlp_bls_plan {
   FixedStar* d_fx = nullptr;
   FreqRec* d_frec = nullptr;
   int32_t* d_ctl = nullptr;       // [0] per-point queue head, [1] cell queue head, [2] error flags,
-                                  // [3] exact cell queue head
+                                  // [3] exact cell queue head (whole tables), [4] the same (windowed)
   // search + S/N captured as one CUDA graph (qlp_bls_graph_capture)
   // slot parts-1: parts = 1 search, 2 S/N, 3 both
   WinRec* d_wrec = nullptr;      // candidate statistics scratch (allocated on first use)
@@ -756,6 +757,12 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   pl->n_items = make_items(kMethodPoints, warps, pl->blocks, &sorted);
   pl->c_items = make_items(kMethodCells, cw, pl->c_blocks, &sorted);
   pl->f_items = make_items(kMethodFixed, kFixedWarps, pl->f_blocks, &sorted);
+  {  // whole-table items first, then the windowed ones (separate launches), each longest first
+    const auto fb = sorted.end() - pl->f_items;
+    const auto mid = std::stable_partition(
+        fb, sorted.end(), [&](const WorkItem& w) { return stars[(size_t)w.star].n_win <= 1; });
+    pl->f_whole = (int32_t)(mid - fb);
+  }
   if (!fixed_stars.empty())
     pl->ws_block = std::max<int64_t>((int64_t)kFixedWarps * round32(pl->fixed_nb_max), win_rows_max);
 
@@ -782,7 +789,7 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
       .add(&pl->d_fx, (size_t)n_stars)
       .add(&pl->d_frec, fixed_stars.empty() ? (size_t)1 : nf_alloc)
       .add(&pl->d_ws, fixed_stars.empty() ? (size_t)1 : (size_t)pl->f_blocks * (size_t)pl->ws_block)
-      .add(&pl->d_ctl, 4);
+      .add(&pl->d_ctl, 5);
   if ((rc = arena.commit(&pl->d_arena, &pl->arena_bytes))) {
     free_plan(pl);
     return rc;
@@ -813,7 +820,7 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
   if (e == cudaSuccess && npt_raw > 0 && !from) e = cudaMemcpyAsync(pl->d_dy, dy_all.get(), sizeof(double) * (size_t)npt_raw, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // host staging arrays die at return
   // the rest runs on the device after the uploads without the host waiting for it
-  if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_ctl, 0, 4 * sizeof(int32_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_ctl, 0, 5 * sizeof(int32_t), st);
   if (e == cudaSuccess && !fixed_stars.empty()) {  // per-frequency records of the exact path
     const int le = launch_freq_recs(fixed_args(pl), stream);
     if (le) e = (cudaError_t)le;
@@ -913,6 +920,16 @@ int qlp_bls_plan_narrow_stats(const qlp_bls_plan_t* pl, int32_t* n_narrow_stars,
   return QLP_OK;
 }
 
+int qlp_bls_plan_launches(const qlp_bls_plan_t* pl, int32_t* n_search_launches) {
+  if (!pl || !n_search_launches) return QLP_ERR_ARG;
+  int32_t n = 0;
+  if (pl->n_items > 0) n += 2;
+  if (pl->c_items > 0) n += 2;
+  if (pl->f_items > 0) n += 1 + (pl->f_whole > 0) + (pl->f_items > pl->f_whole);
+  *n_search_launches = n;
+  return QLP_OK;
+}
+
 // Orders `stream` after the plan's own device work (see `ready`). A stream capture
 // may not wait on work outside it: qlp_bls_graph_capture and qlp_bls_device_status
 // wait on the host first; a capture of the caller's own that starts before either
@@ -942,7 +959,7 @@ int qlp_bls_search(qlp_bls_plan_t* pl, void* stream, float* sr, uint8_t* qidx, u
   cudaStream_t st = (cudaStream_t)stream;
   QLP_CK(wait_plan_ready(pl, st));
   QLP_CK(cudaMemsetAsync(pl->d_ctl, 0, 2 * sizeof(int32_t), st));
-  QLP_CK(cudaMemsetAsync(pl->d_ctl + 3, 0, sizeof(int32_t), st));
+  QLP_CK(cudaMemsetAsync(pl->d_ctl + 3, 0, 2 * sizeof(int32_t), st));
   int e = 0;
   if (pl->n_items > 0) {
     PrepArgs pa{};
@@ -1036,8 +1053,6 @@ int qlp_bls_search(qlp_bls_plan_t* pl, void* stream, float* sr, uint8_t* qidx, u
     fa.fx = pl->d_fx;
     fa.fq = pl->d_fq;
     fa.frec = pl->d_frec;
-    fa.items = pl->d_items + pl->n_items + pl->c_items;
-    fa.n_items = pl->f_items;
     fa.loop_bound = pl->p.work_loop_bound;
     fa.nq = pl->nq;
     fa.tp = pl->d_tp;
@@ -1045,7 +1060,6 @@ int qlp_bls_search(qlp_bls_plan_t* pl, void* stream, float* sr, uint8_t* qidx, u
     fa.loc = reinterpret_cast<const int2*>(pl->d_loc);
     fa.base = reinterpret_cast<const longlong2*>(pl->d_base);
     fa.gidx = pl->d_gidx;
-    fa.cursor = pl->d_ctl + 3;
     fa.err = pl->d_ctl + 2;
     fa.sr = sr;
     fa.qidx = qidx;
@@ -1056,8 +1070,15 @@ int qlp_bls_search(qlp_bls_plan_t* pl, void* stream, float* sr, uint8_t* qidx, u
     fa.ws = pl->d_ws;
     fa.ws_block = pl->ws_block;
     QLP_CK(record_kev(pl, 0, st));
-    e = launch_cells_fixed(fa, pl->f_blocks, pl->f_smem, stream);
-    if (e) return cuda_fail((cudaError_t)e, "exact cell search launch");
+    for (int k = 0; k < 2; ++k) {  // whole tables, then windowed ones
+      const int32_t n_k = k ? pl->f_items - pl->f_whole : pl->f_whole;
+      if (n_k == 0) continue;
+      fa.items = pl->d_items + pl->n_items + pl->c_items + (k ? pl->f_whole : 0);
+      fa.n_items = n_k;
+      fa.cursor = pl->d_ctl + 3 + k;
+      e = launch_cells_fixed(fa, k == 1, pl->f_blocks, pl->f_smem, stream);
+      if (e) return cuda_fail((cudaError_t)e, "exact cell search launch");
+    }
     QLP_CK(record_kev(pl, 1, st));
   }
   return QLP_OK;

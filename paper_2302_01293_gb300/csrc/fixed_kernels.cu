@@ -35,7 +35,8 @@
 // (w, w d) pairs and written to a per-warp ring of four 32-bin blocks (bin x at
 // x mod 128); the sweep of the boxes starting in blocks 2j and 2j + 1 (two start
 // bins per lane) runs once block 2j + 2 is in the ring. Stars whose table does not fit in shared memory take
-// their edges window by window into a global workspace first (windowed_item).
+// their edges window by window into a global workspace first (windowed_item), in a
+// launch of their own.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -674,7 +675,7 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
 // ceil((w+1) C h F)), the same FP64 expression on both sides of each boundary, so
 // the windows partition them) to the bin's row of this block's workspace. Pass B:
 // each frequency runs the block pipeline from its row.
-template <int NW>
+template <int NW, bool STEP>
 __device__ void windowed_item(const FixedArgs& a, const WorkItem& wi, const StarDev& st, const FixedStar& fx,
                               unsigned char* smem, int warp, int lane, uint32_t st4, uint32_t st8, uint32_t st16) {
   const int nc = st.n_cells;
@@ -723,6 +724,8 @@ __device__ void windowed_item(const FixedArgs& a, const WorkItem& wi, const Star
       const int ge = (w == st.n_win - 1) ? g_end + 1
                                           : (int)ceil(__dmul_rn(__dmul_rn((double)((w + 1) * st.win_cells), h), Fq));
       const uint32_t k_lo = (uint32_t)R.K, k_hi = (uint32_t)(R.K >> 32);
+      const unsigned long long XS =  // nb K: the step from a bin's edge to its next
+          STEP ? (unsigned long long)(uint32_t)nb * k_lo + ((unsigned long long)((uint32_t)nb * k_hi) << 32) : 0ull;
       const uint32_t band_q = R.band_q;
       longlong2* row = ws + (size_t)fl * (size_t)stride;
       // this bin's edges in [gs, ge): cycles c0 = max(0, ceil((gs - x) / nb)) .. c1 =
@@ -761,11 +764,17 @@ __device__ void windowed_item(const FixedArgs& a, const WorkItem& wi, const Star
         const int cmax = __reduce_max_sync(0xffffffffu, (unsigned)cntl);
         long long aw = 0, ay = 0;
         bool near = false;
-        for (int k = 0; k < cmax; ++k) {
+        // tau_G / h in 24.40 fixed point: G K modulo 2^64, by the product (STEP false)
+        // or stepped by nb K from edge to edge (the same bits)
+        const int G0 = x + c0 * nb;
+        unsigned long long X =
+            (unsigned long long)(uint32_t)G0 * k_lo + ((unsigned long long)((uint32_t)G0 * k_hi) << 32);
+        for (int k = 0; k < cmax; ++k, X += XS) {
           const bool valid = k < cntl;
-          const int G = x + (c0 + k) * nb;
-          const unsigned long long X =
-              (unsigned long long)(uint32_t)G * k_lo + ((unsigned long long)((uint32_t)G * k_hi) << 32);
+          if constexpr (!STEP) {
+            const int G = x + (c0 + k) * nb;
+            X = (unsigned long long)(uint32_t)G * k_lo + ((unsigned long long)((uint32_t)G * k_hi) << 32);
+          }
           const int ul = min(max((int)((uint32_t)(X >> 32) >> 8) - lo, 0), n_loc - 1);  // staged cell
           const uint32_t fr = (uint32_t)(X >> 8);
           const uint32_t dq = *reinterpret_cast<const uint32_t*>(smem + (uint32_t)ul * st4);
@@ -842,7 +851,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 constexpr uint32_t kCopyWaitLimit = 1u << 24;  // polls of a table copy (each ends after ~1 us at most)
 
-template <int NW>
+// WIN: a launch of the time-windowed tables' items alone (the edge positions of
+// pass A stepped from edge to edge); else a launch that takes either kind (the plan
+// gives it the whole tables' items; pass A forms each edge's position by its product)
+template <int NW, bool WIN>
 __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5;
@@ -874,8 +886,12 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
     const WorkItem wi = a.items[it];
     const StarDev st = a.stars[wi.star];
     const FixedStar fx = a.fx[wi.star];
+    if (WIN && st.n_win <= 1) {  // block-uniform; the plan never hands this launch a whole table
+      if (threadIdx.x == 0) atomicOr(a.err, kErrNbins);
+      continue;
+    }
     if (st.n_win > 1) {  // block-uniform: a table longer than shared memory
-      windowed_item<NW>(a, wi, st, fx, smem, warp, lane, st4, st8, st16);
+      windowed_item<NW, WIN>(a, wi, st, fx, smem, warp, lane, st4, st8, st16);
       if (threadIdx.x == 0) s_star = -1;  // shared memory no longer holds a whole table
       continue;
     }
@@ -973,21 +989,25 @@ uint32_t fixed_window_smem_bytes(int ncs) {
   return fixed_ring_off(ncs) > (uint32_t)kFixedWarps * kRing * 8u ? fixed_ring_off(ncs) : (uint32_t)kFixedWarps * kRing * 8u;
 }
 
-int launch_cells_fixed(const FixedArgs& a, int blocks, size_t smem, void* stream) {
-  auto kern = cells_fixed_kernel<kFixedWarps>;
+int launch_cells_fixed(const FixedArgs& a, bool windowed, int blocks, size_t smem, void* stream) {
+  auto kern = windowed ? cells_fixed_kernel<kFixedWarps, true> : cells_fixed_kernel<kFixedWarps, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   kern<<<blocks, kFixedWarps * 32, smem, (cudaStream_t)stream>>>(a);
   return (int)cudaGetLastError();
 }
 
-int fixed_blocks_per_sm(size_t smem) {
-  auto kern = cells_fixed_kernel<kFixedWarps>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return 0;
-  int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kFixedWarps * 32, smem) != cudaSuccess) return 0;
-  return nb;
+int fixed_blocks_per_sm(size_t smem) {  // the fewer of the two instantiations'
+  int nmin = 0;
+  for (int k = 0; k < 2; ++k) {
+    auto kern = k ? cells_fixed_kernel<kFixedWarps, true> : cells_fixed_kernel<kFixedWarps, false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kFixedWarps * 32, smem) != cudaSuccess) return 0;
+    nmin = (k == 0 || nb < nmin) ? nb : nmin;
+  }
+  return nmin;
 }
 
 }  // namespace qlp

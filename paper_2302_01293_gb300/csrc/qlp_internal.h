@@ -262,7 +262,7 @@ int launch_prep_cells(const PrepCellsArgs& a, void* stream);
 int launch_cells(const CellArgs& a, int sum_mode, int warps, int blocks, size_t smem, void* stream);
 int launch_prep_fixed(const PrepFixedArgs& a, void* stream);
 int launch_freq_recs(const PrepFixedArgs& a, void* stream);
-int launch_cells_fixed(const FixedArgs& a, int blocks, size_t smem, void* stream);
+int launch_cells_fixed(const FixedArgs& a, bool windowed, int blocks, size_t smem, void* stream);
 // shared memory of the exact cell kernel for a table of ncs cells (incl. sentinel)
 uint32_t fixed_smem_bytes(int ncs);
 // shared memory of a time window of ncs cells (its table; pass B's rings overlay it)

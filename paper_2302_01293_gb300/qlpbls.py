@@ -133,6 +133,8 @@ def lib():
             L.qlp_bls_plan_exact_stats.restype = ctypes.c_int
             L.qlp_bls_plan_narrow_stats.argtypes = [_vp, _P(_i32), _P(_d), _P(_d)]
             L.qlp_bls_plan_narrow_stats.restype = ctypes.c_int
+            L.qlp_bls_plan_launches.argtypes = [_vp, _P(_i32)]
+            L.qlp_bls_plan_launches.restype = ctypes.c_int
             L.qlp_bls_plan_times.argtypes = [_vp, _P(_d)]
             L.qlp_bls_plan_times.restype = ctypes.c_int
             L.qlp_bls_kernel_timing.argtypes = [_vp, _i32]
@@ -353,6 +355,8 @@ class Plan:
         self.n_narrow_stars = int(ne.value)
         self.narrow_edges = ee.value
         self.narrow_bins = eb.value
+        _check(L.qlp_bls_plan_launches(self._h, ctypes.byref(ne)), "qlp_bls_plan_launches")
+        self.search_launches = int(ne.value)
 
     def alloc_outputs(self):
         import torch

@@ -175,6 +175,23 @@ def test_multi_sector_cell_path_in_windows(gpu_lib):
     assert g["plan"].n_exact_stars == 3  # exact sums through the windows' workspace
 
 
+def test_exact_path_whole_and_windowed_tables_in_one_batch(gpu_lib):
+    # one- and multi-sector stars: whole tables and time-windowed ones, searched as
+    # two launches of the exact kernel (one queue each), directly and from a CUDA graph
+    import torch
+    b = synth.multi_sector(n_stars=3, seed=5, max_sectors=4)
+    g, _ = _check_batch(b, qlpbls.Params())
+    plan = g["plan"]
+    assert plan.n_exact_stars == 3 and 1 <= plan.n_windowed <= 2
+    assert plan.search_launches == 3  # prep, whole tables, windowed tables
+    out = plan.graph_capture(plan.alloc_outputs(), parts=1)
+    plan.graph_launch(1)
+    torch.cuda.synchronize()
+    for k in ("sr", "qidx", "kbin"):
+        assert np.array_equal(out[k].cpu().numpy(), g[k]), k
+    assert plan.device_status() == 0
+
+
 def test_multi_sector_windows_compensated(gpu_lib):
     b = synth.multi_sector(n_stars=3, seed=4, max_sectors=4)
     g, _ = _check_batch(b, qlpbls.Params(method=qlpbls.METHOD_CELLS, sum_mode=qlpbls.SUM_COMP))
