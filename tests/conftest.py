@@ -31,11 +31,12 @@ def _parity_report():
 
 def pytest_sessionfinish(session, exitstatus):
     """Write the parity figures of every GPU comparison (near ties, SR and S/N
-    error maxima per test) to QLP_PARITY_REPORT, default gpurun_out/parity_report.json."""
+    error maxima per test) as JSON to the file QLP_PARITY_REPORT names, if it is set
+    (the terminal summary prints their totals either way)."""
     rep = _parity_report()
-    if not rep:
+    path = os.environ.get("QLP_PARITY_REPORT")
+    if not rep or not path:
         return
-    path = os.environ.get("QLP_PARITY_REPORT", os.path.join(ROOT, "gpurun_out", "parity_report.json"))
     try:
         os.makedirs(os.path.dirname(path), exist_ok=True)
         with open(path, "w") as fh:

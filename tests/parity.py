@@ -132,7 +132,7 @@ def compare_spectrum(pl, ores, g, sl, label="", tight=None, box_value=None):
     for i in mism:
         v = box_value(int(i), int(q_g[i]), int(k_g[i]))
         assert v >= ores.sr[i] * (1 - SR_RTOL), (
-            f"{label} f#{i}: GPU box (j={q_g[i]}, k={k_g[i]}) oracle value {v} vs max {ores.sr[i]} "
+            f"{label} f#{i}: the GPU's box (j={q_g[i]}, k={k_g[i]}) oracle value {v} vs max {ores.sr[i]} "
             f"at (j={ores.j[i]}, k={ores.k[i]})")
         assert abs(sr_g[i] - v) <= tol * abs(v), f"{label} f#{i}: near-tie SR {sr_g[i]} vs its box {v}"
         alt[int(i)] = v
