@@ -623,19 +623,30 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
   const int bo = bkey >> 16;
   // the lowest duration index of each width, read again here rather than kept live
   const unsigned long long jlow = a.frec[fidx].jlow;
-  int bj = none ? 255 : (int)((jlow >> (4 * bo)) & 15ull);
-  int bk = none ? -1 : (bkey & 0xffff);
-  int bm = none ? 0 : bo + 1;  // bins of the box
+  // (j, width, k) in one word: j in bits 20-23, the width index in 16-19, k in 0-15;
+  // one j has one width, so the word orders as (j, k) does
+  uint32_t key = none ? 0xffffffffu
+                      : ((uint32_t)((jlow >> (4 * bo)) & 15ull) << 20) | ((uint32_t)bo << 16) | (uint32_t)(bkey & 0xffff);
   for (int off = 16; off > 0; off >>= 1) {
     const float o_s2 = __shfl_xor_sync(0xffffffffu, bs2, off);
     const float o_d = __shfl_xor_sync(0xffffffffu, bd, off);
-    const int o_j = __shfl_xor_sync(0xffffffffu, bj, off);
-    const int o_k = __shfl_xor_sync(0xffffffffu, bk, off);
-    const int o_m = __shfl_xor_sync(0xffffffffu, bm, off);
-    if (beats(o_s2, o_d, o_j, o_k, bs2, bd, bj, bk)) {
-      bs2 = o_s2; bd = o_d; bj = o_j; bk = o_k; bm = o_m;
+    const uint32_t o_key = __shfl_xor_sync(0xffffffffu, key, off);
+    // strict: larger s^2 / d, then the lower (j, k); s^2 < 0 is no box
+    bool take;
+    if (o_s2 < 0.f) take = false;
+    else if (bs2 < 0.f) take = true;
+    else {
+      const float lhs = o_s2 * bd, rhs = bs2 * o_d;
+      take = lhs != rhs ? lhs > rhs : o_key < key;
+    }
+    if (take) {
+      bs2 = o_s2; bd = o_d; key = o_key;
     }
   }
+  const bool nobox = bs2 < 0.f;
+  const int bj = nobox ? 255 : (int)(key >> 20);
+  const int bk = nobox ? -1 : (int)(key & 0xffffu);
+  const int bm = nobox ? 0 : (int)((key >> 16) & 15u) + 1;  // bins of the box
   BoxBest bb;
   bb.s2 = bs2; bb.d = bd; bb.s = 0.f; bb.r = 0.f; bb.j = bj; bb.k = bk;
   bb.xv = false;
