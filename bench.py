@@ -719,9 +719,9 @@ def main():
         traffic = 423.0e6 * plan.n_points / 10638874
 
     if kernel_id == 2 and default_batch:
-        # cells_fixed_kernel: ncu capture on 1,024 stars of this workload (676.3 MB read +
-        # 218.6 MB written), scaled by points (tables, records and outputs grow with them)
-        traffic = 894.9e6 * plan.n_points / 10638874
+        # cells_fixed_kernel: ncu capture on 1,024 stars of this workload (702.8 MB read +
+        # 236.4 MB written), scaled by points (tables, records and outputs grow with them)
+        traffic = 939.2e6 * plan.n_points / 10638874
     # the same launch in the method's own unit: point-frequency pairs per second against
     # the FP32-issue roof of a per-point search (14 lane operations per pair: double-float
     # phase, bin index and the run sums), the unit in which the edge formulation's lower

@@ -764,7 +764,8 @@ static int plan_impl(const qlp_bls_params* pin, int32_t n_stars, const int64_t* 
     pl->f_whole = (int32_t)(mid - fb);
   }
   if (!fixed_stars.empty())
-    pl->ws_block = std::max<int64_t>((int64_t)kFixedWarps * round32(pl->fixed_nb_max), win_rows_max);
+    pl->ws_block = std::max<int64_t>((int64_t)kFixedWarps * (round32(pl->fixed_nb_max) + kFixedPendRows),
+                                     win_rows_max);
 
   // device buffers
   const auto c2 = clk::now();

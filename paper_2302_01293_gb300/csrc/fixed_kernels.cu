@@ -396,10 +396,67 @@ __device__ __forceinline__ void sweep_pair(const float2* ring, int ka, bool ain,
 // from the window passes' workspace row when WS), then per block of 32 bins U, the
 // FP32 histogram records in the ring and the sweep, the warp argmax and the store.
 // This warp's row of exact bin sums in the block's workspace: ws_block / kFixedWarps
-// entries, at least the bins of every whole-table star of the plan.
+// entries, at least the bins of every whole-table star of the plan, then the warp's
+// kFixedPendRows entries of pending boxes (pend_rows).
 __device__ __forceinline__ longlong2* warp_row(const FixedArgs& a) {
   return a.ws + (size_t)blockIdx.x * (size_t)a.ws_block +
          (size_t)(threadIdx.x >> 5) * (size_t)(a.ws_block / kFixedWarps);
+}
+__device__ __forceinline__ longlong2* pend_rows(const FixedArgs& a) {
+  return warp_row(a) + (a.ws_block / kFixedWarps - kFixedPendRows);
+}
+
+// A whole-table frequency's chosen box, left by lane 0 for rescoring: its exact
+// integer sums (w, w d) and, in the second half, (frequency in the item, the packed
+// (j, width, k) word, s^2, r (1 - r)) of the FP32 sweep; s^2 < 0 when no box counts.
+__device__ __forceinline__ void put_pending(longlong2* rows, int p, long long dw, long long dy, int fl,
+                                            uint32_t key, float s2, float d) {
+  int4* r = reinterpret_cast<int4*>(rows) + 2 * p;
+  r[0] = make_int4((int)(uint32_t)dw, (int)(dw >> 32), (int)(uint32_t)dy, (int)(dy >> 32));
+  r[1] = make_int4(fl, (int)key, __float_as_int(s2), __float_as_int(d));
+}
+
+// Lane t scores the t-th pending box again from its exact sums in double-float
+// arithmetic (r and 1 - r over the star's total on the 32-bit table, scaled by 2^-kw
+// on the 64-bit one; s scaled by 2^-ky) and stores it: the rescoring of up to 32
+// frequencies takes one instruction stream (lane 0 alone, one frequency at a time,
+// took 2.7 % of the launch). f0 is the item's first frequency.
+__device__ __forceinline__ void flush_pending(const FixedArgs& a, const FixedStar& fx, int64_t f0,
+                                           const longlong2* rows, int n, int lane) {
+  __syncwarp();  // lane 0's records are visible to the warp
+  if (lane < n) {
+    const int4 r0 = reinterpret_cast<const int4*>(rows)[2 * lane];
+    const int4 r1 = reinterpret_cast<const int4*>(rows)[2 * lane + 1];
+    const long long dw = (long long)(((unsigned long long)(uint32_t)r0.y << 32) | (uint32_t)r0.x);
+    const long long dy = (long long)(((unsigned long long)(uint32_t)r0.w << 32) | (uint32_t)r0.z);
+    const uint32_t key = (uint32_t)r1.y;
+    BoxBest bb;
+    bb.s2 = __int_as_float(r1.z);
+    bb.d = __int_as_float(r1.w);
+    bb.s = 0.f;
+    bb.r = 0.f;
+    const bool nobox = bb.s2 < 0.f;
+    bb.j = nobox ? 255 : (int)(key >> 20);
+    bb.k = nobox ? -1 : (int)(key & 0xffffu);
+    bb.xv = false;
+    if (!nobox) {
+      if (fx.narrow) {  // r = dw / w_tot and 1 - r = (w_tot - dw) / w_tot, both sums below 2^32
+        const DF wt = df_from_ll_scaled(fx.w_tot, 0);
+        bb.xr = df_div(df_from_ll_scaled(dw, 0), wt);
+        bb.xq = df_div(df_from_ll_scaled(fx.w_tot - dw, 0), wt);
+      } else {
+        // kw lies in [24, 46] on this path: the largest weight is at most 1 and at least
+        // 1/N with N <= 2^21 points, and w_max 2^kw lies in [2^24, 2^25)
+        const int kw = min(max(fx.kw, 0), 62);
+        bb.xr = df_from_ll_scaled(dw, kw);
+        bb.xq = df_from_ll_scaled((1ll << kw) - dw, kw);  // 1 - r
+      }
+      bb.xs = df_from_ll_scaled(dy, fx.ky);
+      bb.xv = true;
+    }
+    store_box(bb, 0, f0 + r1.x, a.sr, a.qidx, a.kbin, a.sbest, a.rbest);
+  }
+  __syncwarp();  // the records are read before the warp writes new ones
 }
 
 // The row srow holds the exact bin sums S of the frequency (the window passes'
@@ -411,7 +468,7 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
                                               uint32_t loc_off, uint32_t base_off, int nc, float2* ring,
                                               int lane, float scw, float scy, const double* tp,
                                               const int32_t* gidx, uint32_t st4, uint32_t st8, uint32_t st16,
-                                              longlong2* srow) {
+                                              longlong2* srow, longlong2* prow, int& pend, int fl) {
   const int nb = R.nb;
   const double f = a.fq[fidx].x;  // for the exact decision near ties
   const uint32_t wmask = R.wmask;
@@ -647,6 +704,24 @@ __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, 
   const int bj = nobox ? 255 : (int)(key >> 20);
   const int bk = nobox ? -1 : (int)(key & 0xffffu);
   const int bm = nobox ? 0 : (int)((key >> 16) & 15u) + 1;  // bins of the box
+  if constexpr (!WS) {  // whole tables: the box's exact sums wait for a batch rescoring
+    if (lane == 0) {
+      long long dw = 0, dy = 0;
+      if (bk >= 0) {  // U[bk + bm] - U[bk] as below
+        const int k2 = bk + bm;
+        const int k2m = k2 >= nb ? k2 - nb : k2;
+        const longlong2* row = warp_row(a);
+        const longlong2 a0 = row[bk], a1 = row[k2m];
+        const long long nwrap = (bstar < k2m ? 1 : 0) + (k2 >= nb ? 1 : 0) - (bstar < bk ? 1 : 0);
+        dw = a1.x - a0.x + nwrap * fx.w_tot;
+        dy = a1.y - a0.y + nwrap * fx.y_tot;
+        if (NARROW) dw = (long long)(uint32_t)dw;  // the rows hold the w sums modulo 2^32
+      }
+      put_pending(prow, pend, dw, dy, fl, key, bs2, bd);
+    }
+    ++pend;
+    return;
+  }
   BoxBest bb;
   bb.s2 = bs2; bb.d = bd; bb.s = 0.f; bb.r = 0.f; bb.j = bj; bb.k = bk;
   bb.xv = false;
@@ -846,8 +921,9 @@ __device__ void windowed_item(const FixedArgs& a, const WorkItem& wi, const Star
       }
       continue;
     }
+    int no_pend = 0;
     run_frequency<true, false>(a, fidx, R, fx, smem, loc_off, base_off, nc, ring, lane, scw, scy, tp, gidx, st4, st8,
-                        st16, ws + (size_t)fl * (size_t)stride);
+                               st16, ws + (size_t)fl * (size_t)stride, nullptr, no_pend, fl);
   }
 }
 
@@ -965,6 +1041,9 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
     const double* tp = a.tp + st.pt_off;
     const int32_t* gidx = a.gidx + st.cell_off;
 
+    longlong2* const prow = pend_rows(a);
+    const int64_t f0 = st.f_off + wi.f_begin;
+    int pend = 0;  // boxes waiting in prow for their rescoring (warp-uniform)
     for (int fi = 0; fi <= wi.f_count; ++fi) {  // bounded: each pass takes one frequency
       int fl = 0;
       if (lane == 0) fl = atomicAdd(&s_next, 1);
@@ -986,11 +1065,16 @@ __global__ void __launch_bounds__(NW * 32, 1) cells_fixed_kernel(const FixedArgs
       }
       if (fx.narrow)  // block-uniform
         run_frequency<false, true>(a, fidx, R, fx, smem, loc_off, base_off, nc, ring, lane, scw, scy, tp, gidx, st4,
-                                   st8, st16, nullptr);
+                                   st8, st16, nullptr, prow, pend, fl);
       else
         run_frequency<false, false>(a, fidx, R, fx, smem, loc_off, base_off, nc, ring, lane, scw, scy, tp, gidx, st4,
-                                    st8, st16, nullptr);
+                                    st8, st16, nullptr, prow, pend, fl);
+      if (pend == 32) {
+        flush_pending(a, fx, f0, prow, pend, lane);
+        pend = 0;
+      }
     }
+    if (pend > 0) flush_pending(a, fx, f0, prow, pend, lane);
   }
   if (!done && threadIdx.x == 0) atomicOr(a.err, kErrQueueBound);
 }

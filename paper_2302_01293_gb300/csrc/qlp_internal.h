@@ -272,6 +272,7 @@ int fixed_blocks_per_sm(size_t smem);
 constexpr int kFixedWarps = 32;
 constexpr int64_t kFixedWsBlock = 131072;  // bound on a block's whole-table rows: 32 warps x round32(nbins)
 constexpr int64_t kFixedWinRows = 524288;  // workspace entries (16 B) a windowed item may take per block
+constexpr int64_t kFixedPendRows = 64;     // workspace entries (16 B) per warp past its row: 32 pending boxes
 // bytes of shared memory before the histograms of the cell kernel for a star with
 // ncs cells (incl. sentinel) and nw warps
 // One point of a candidate's fit window: t', P n for its transit index n at the
