@@ -227,6 +227,18 @@ def test_plan_from_plan_rejects_missing_arguments():
     assert out.value is None
 
 
+def test_plan_queries_reject_a_missing_plan():
+    # the plan queries answer QLP_ERR_ARG for a NULL plan or output, with no device work
+    import ctypes
+    from paper_2302_01293_gb300 import qlpbls
+    L = qlpbls.lib()
+    n = ctypes.c_int32(-7)
+    assert L.qlp_bls_plan_launches(None, ctypes.byref(n)) == qlpbls.ERR_ARG
+    assert n.value == -7
+    assert L.qlp_bls_plan_narrow_stats(None, None, None, None) == qlpbls.ERR_ARG
+    assert L.qlp_bls_plan_exact_stats(None, None, None, None) == qlpbls.ERR_ARG
+
+
 def test_work_loop_bound_is_validated():
     from paper_2302_01293_gb300 import qlpbls
     import synth
