@@ -392,9 +392,6 @@ __device__ __forceinline__ void sweep_pair(const float2* ring, int ka, bool ain,
   }
 }
 
-// One trial frequency on a warp: the bin sums S (from the staged table's edges, or
-// from the window passes' workspace row when WS), then per block of 32 bins U, the
-// FP32 histogram records in the ring and the sweep, the warp argmax and the store.
 // This warp's row of exact bin sums in the block's workspace: ws_block / kFixedWarps
 // entries, at least the bins of every whole-table star of the plan, then the warp's
 // kFixedPendRows entries of pending boxes (pend_rows).
@@ -422,7 +419,7 @@ __device__ __forceinline__ void put_pending(longlong2* rows, int p, long long dw
 // frequencies takes one instruction stream (lane 0 alone, one frequency at a time,
 // took 2.7 % of the launch). f0 is the item's first frequency.
 __device__ __forceinline__ void flush_pending(const FixedArgs& a, const FixedStar& fx, int64_t f0,
-                                           const longlong2* rows, int n, int lane) {
+                                              const longlong2* rows, int n, int lane) {
   __syncwarp();  // lane 0's records are visible to the warp
   if (lane < n) {
     const int4 r0 = reinterpret_cast<const int4*>(rows)[2 * lane];
@@ -459,9 +456,14 @@ __device__ __forceinline__ void flush_pending(const FixedArgs& a, const FixedSta
   __syncwarp();  // the records are read before the warp writes new ones
 }
 
+// One trial frequency on a warp: the bin sums S (from the staged table's edges, or
+// from the window passes' workspace row when WS), then per block of 32 bins U, the
+// FP32 histogram records in the ring and the sweep, the warp argmax and the store.
 // The row srow holds the exact bin sums S of the frequency (the window passes'
 // workspace row when WS, else this warp's row (warp_row), written here block by block), so that
-// the box the FP32 sweep chose is scored once more from its exact integer sums.
+// the box the FP32 sweep chose is scored once more from its exact integer sums: at
+// once when WS, else from the pending record put at prow[pend] (fl: the frequency
+// within the item) and rescored in the caller's next flush_pending.
 template <bool WS, bool NARROW>
 __device__ __forceinline__ void run_frequency(const FixedArgs& a, int64_t fidx, const FreqRec& R,
                                               const FixedStar& fx, const unsigned char* smem,
